@@ -1,0 +1,190 @@
+/*
+ * nl.h -- C-ABI of the GB300 nonlocal operator library.
+ *
+ * Applies the discretised nonlocal operators of Tian & Engquist, "Fast
+ * algorithm for computing nonlocal operators with finite interaction
+ * distance" (arXiv 1905.08375) on uniform 1-D/2-D/3-D grids:
+ *
+ *   scalar nonlocal diffusion, Eq. (2.1)-(2.2):
+ *       (L u)_i = h^d sum_{j != i, |x_j - x_i| < delta_i} w_ij c_ij (u_j - u_i)
+ *       w_ij    = sigma delta_i^{-(d+2)} gamma(|x_j - x_i| / delta_i)
+ *   linear bond-based peridynamics, Eq. (1.1)-(1.2):
+ *       (L u)_i = h^d sum_{0 < |xi| < delta_i} sigma c_ij (xi xi^T / |xi|^3) (u_j - u_i)
+ *   the fast algorithm of Sec. 3 (Algorithm 1 + Steps 1-3, Eq. (3.3)-(3.5))
+ *       for polynomial kernels P = sigma C(x) delta(x)^{-(d+2)} p^{2K}(|y-x|/delta(x)),
+ *   and conjugate gradients on -L u = f (the Krylov use remarked in Sec. 4).
+ *
+ * Grid and boundary (Eq. (3.1)): Omega = [0,1]^d, n nodes per dimension,
+ * h = 1/n, node i at x_i = (i + 1/2) h, flat index x fastest
+ * (i_x + n (i_y + n i_z)).  u = 0 outside Omega (volume constraint).  For a
+ * node y outside Omega every coefficient field (a, c, delta) takes the value
+ * of the row's own node x.
+ *
+ * Horizon test: lattice offset o (integer, units of h) lies in the open ball
+ * of node i iff (double)|o|^2 < R2_i, R2_i = (delta_i n)^2 in FP64.
+ *
+ * Conventions for every entry point:
+ *   - status codes only (never exceptions); nl_last_error() returns a
+ *     thread-local message for the last failure on the calling thread.
+ *   - device pointers (u, Lu, f, x) are owned by the caller; the plan owns
+ *     its device workspaces and frees them in nl_plan_destroy().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  nl_apply / nl_apply_fast are asynchronous and stream-ordered.
+ *   - no entry point calls back into Python or uses any host-side fallback:
+ *     every step of an apply runs in this library's CUDA kernels.
+ */
+#ifndef NL_H
+#define NL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NL_OK = 0,
+    NL_EINVAL = 1,        /* bad argument (null pointer, size, horizon <= 0, ...) */
+    NL_EUNSUPPORTED = 2,  /* valid request this build does not implement */
+    NL_ENOMEM = 3,        /* device or host allocation failed */
+    NL_ECUDA = 4,         /* a CUDA call failed; message has the CUDA error string */
+    NL_ENOTCONV = 5,      /* CG hit maxit before the tolerance */
+    NL_ETIMEOUT = 6       /* a bounded device-side wait gave up */
+} nl_status;
+
+typedef enum { NL_F32 = 0, NL_F64 = 1 } nl_dtype;
+
+/* Radial profile gamma(s), s = |xi| / delta_i (Eq. (2.2)):
+ *   NL_POWER:   gamma(s) = s^{-alpha}, alpha >= 0 (alpha = 0: constant kernel)
+ *   NL_POLY:    gamma(s) = p^{2K}(s), the even polynomial of degree 2K that
+ *               matches s^{-alpha} and its first K derivatives at s = 1
+ *               (the splitting of Sec. 3; K = 0 gives p = 1)
+ *   NL_PD_BOND: linear peridynamic bond, micromodulus sigma c_ij / |xi|
+ *               (Eq. (1.2)); u and Lu then hold d component planes. */
+typedef enum { NL_POWER = 0, NL_POLY = 1, NL_PD_BOND = 2 } nl_family;
+
+/* Coefficient C(x,y) of Eq. (2.2) built from the node field `a`:
+ *   NL_COEF_NONE: C = 1
+ *   NL_COEF_X:    C = a(x)            (non-divergence type, Sec. 2 case (a))
+ *   NL_COEF_XY:   C = a(x) a(y)
+ *   NL_COEF_MEAN: C = (a(x) + a(y))/2 (peridynamic two-phase bond, NL_PD_BOND) */
+typedef enum { NL_COEF_NONE = 0, NL_COEF_X = 1, NL_COEF_XY = 2, NL_COEF_MEAN = 3 } nl_coef;
+
+/* Self term of Eq. (3.3) for nl_apply_fast:
+ *   NL_SELF_DISCRETE: h^d sum over every lattice cell (inside or outside
+ *       Omega) that meets the open ball of p(|x_k - x_i|/delta_i) b_k, with
+ *       b = a for NL_COEF_XY (exterior cells take a_i), else 1; then L 1 = 0
+ *       wherever the ball stays inside Omega.
+ *   NL_SELF_PAPER: the continuous |H_x| form, int_{B_delta} p(|xi|/delta) dxi
+ *       (Example 1 of Sec. 4); not defined for NL_COEF_XY. */
+typedef enum { NL_SELF_DISCRETE = 0, NL_SELF_PAPER = 1 } nl_self;
+
+typedef struct {
+    int dim;   /* d in {1, 2, 3} */
+    int n;     /* nodes per dimension; the fast path needs n = 2^L */
+} nl_grid;
+
+typedef struct {
+    double delta;               /* constant horizon (used when delta_field is NULL) */
+    const double *delta_field;  /* HOST pointer, n^d values, or NULL; copied at plan time */
+    int symmetric;              /* 1: divergence-type symmetrised kernel (Sec. 2 case (b)):
+                                   w^s_ij = (w_ij + w_ji)/2, each half with its own
+                                   node's horizon; NL_POWER with NL_COEF_NONE/XY only */
+} nl_horizon;
+
+typedef struct {
+    int family;        /* nl_family */
+    double alpha;      /* exponent of s^{-alpha} (NL_POWER) or of the matched profile (NL_POLY) */
+    int K;             /* polynomial order for NL_POLY, 0..3 */
+    double scale;      /* multiplies sigma */
+    int normalize;     /* 1: sigma = scale 2d(d+2-alpha)/|S^{d-1}| (L -> Laplacian);
+                          0: sigma = scale.  Ignored for NL_PD_BOND (sigma = scale). */
+    int coef;          /* nl_coef */
+    const double *a;   /* HOST pointer, n^d coefficient values (a or c), or NULL */
+    int self_term;     /* nl_self, nl_apply_fast only */
+} nl_kernel;
+
+typedef struct nl_plan nl_plan;
+
+/*
+ * Build a plan: validates Eq. (2.3) (delta > 0 and finite, coefficient > 0),
+ * derives the per-node horizon data, the offset table of the ball, the
+ * Hermite-matched polynomial (Sec. 3), the exterior and self terms, and
+ * allocates the device workspaces (the Step 2 moment pyramid for the fast
+ * path).  Host arrays are read during the call only.  Runs on `stream` and
+ * synchronises it before returning.
+ * Errors: NL_EINVAL (null, dim, n < 1, delta <= 0, coefficient <= 0, K out of
+ * range), NL_EUNSUPPORTED (radius beyond the build's limits), NL_ENOMEM, NL_ECUDA.
+ */
+nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl_horizon *horizon,
+                         const nl_kernel *kernel, void *stream);
+
+/* Free the plan and its device memory (synchronises the device).  NULL is a no-op. */
+nl_status nl_plan_destroy(nl_plan *plan);
+
+/*
+ * Direct apply (the "Original" matrix-vector product of Sec. 2/4): the plain
+ * variable-stencil sum over the open ball of every node, Eq. (2.1)-(2.2) or
+ * Eq. (1.2).  u, Lu: DEVICE pointers, nrhs stacked fields, layout
+ * [nrhs][n^d] (scalar) or [nrhs][d][n^d] (NL_PD_BOND), element type `dtype`.
+ * u and Lu must not overlap.  FP32: FP32 products and sums of differences
+ * u_j - u_i; FP64: all FP64.
+ * Errors: NL_EINVAL (null, nrhs < 1, dtype), NL_ECUDA (launch failure).
+ */
+nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, void *stream);
+
+/*
+ * Fast apply (Sec. 3): Step 2 (bottom-up moment pyramid, FP64) and Step 3
+ * (per-node sum over the panels of the Step 1 decomposition, Eq. (3.5)),
+ * then Eq. (3.3).  The decomposition of Algorithm 1 is not stored: each
+ * node enumerates it per level in closed form (the same panel set).  The
+ * result equals h^d sum over the leaf cells that meet the ball.
+ * Requires family NL_POLY, a non-symmetric horizon, n = 2^L and coefficient
+ * NL_COEF_NONE, NL_COEF_X or NL_COEF_XY; else NL_EUNSUPPORTED.
+ * Same layouts and ownership as nl_apply.
+ */
+nl_status nl_apply_fast(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, void *stream);
+
+typedef struct {
+    int iterations;       /* CG iterations of the slowest right-hand side */
+    double rel_residual;  /* max over right-hand sides of ||f + L x|| / ||f|| (FP64, true residual) */
+    int converged;        /* 1 if every right-hand side met rtol */
+} nl_cg_stats;
+
+typedef enum { NL_PRECOND_NONE = 0, NL_PRECOND_JACOBI = 1 } nl_precond;
+
+/*
+ * Preconditioned conjugate gradients for -L x = f with the plan's operator
+ * (which must be symmetric: a symmetric NL_POWER plan or NL_PD_BOND with a
+ * constant horizon).  f, x: DEVICE pointers, FP64, layout as nl_apply;
+ * x0 = 0.  Operator applies in FP32, inner products and vector updates in
+ * FP64, with the residual recomputed in FP64 (FP64 operator) every
+ * `replace_every` iterations so that the reported residual is the true FP64
+ * one.  Blocks until done; the stats are read back on the host.
+ * Errors: NL_EINVAL, NL_EUNSUPPORTED (non-symmetric plan), NL_ENOTCONV, NL_ECUDA.
+ */
+nl_status nl_cg_solve(nl_plan *plan, const void *f, void *x, int nrhs, double rtol, int maxit,
+                      int precond, nl_cg_stats *stats, void *stream);
+
+/* Plan introspection (host values computed at plan time). */
+typedef struct {
+    int dim, n, levels;        /* levels = L for n = 2^L, else -1 */
+    int max_radius;            /* max_i ceil(delta_i n) */
+    int num_offsets;           /* offsets in the largest ball */
+    int moments;               /* moments per panel, C(2K+d, d) */
+    double sigma;              /* kernel constant */
+    double poly[8];            /* p_0 .. p_K of p^{2K} (NL_POLY) */
+    size_t device_bytes;       /* device memory owned by the plan */
+} nl_plan_info;
+
+nl_status nl_get_plan_info(const nl_plan *plan, nl_plan_info *info);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *nl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NL_H */

@@ -1,0 +1,233 @@
+"""Thin ctypes binding over the C-ABI in ``include/nl.h`` (same entry-point names).
+
+Argument marshalling only: every step of an apply runs in ``_lib/libnl.so``.
+Device buffers are torch CUDA tensors (PyTorch is used for device memory and
+streams); host-side plan inputs are numpy arrays.  There is no fallback: if
+the library has not been built, or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libnl.so")
+
+NL_OK, NL_EINVAL, NL_EUNSUPPORTED, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT = range(7)
+NL_F32, NL_F64 = 0, 1
+NL_POWER, NL_POLY, NL_PD_BOND = 0, 1, 2
+NL_COEF_NONE, NL_COEF_X, NL_COEF_XY, NL_COEF_MEAN = 0, 1, 2, 3
+NL_SELF_DISCRETE, NL_SELF_PAPER = 0, 1
+NL_PRECOND_NONE, NL_PRECOND_JACOBI = 0, 1
+
+_STATUS = {0: "NL_OK", 1: "NL_EINVAL", 2: "NL_EUNSUPPORTED", 3: "NL_ENOMEM", 4: "NL_ECUDA",
+           5: "NL_ENOTCONV", 6: "NL_ETIMEOUT"}
+
+
+class NlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nl_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int)]
+
+
+class nl_horizon(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("delta_field", ctypes.c_void_p),
+                ("symmetric", ctypes.c_int)]
+
+
+class nl_kernel(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("alpha", ctypes.c_double), ("K", ctypes.c_int),
+                ("scale", ctypes.c_double), ("normalize", ctypes.c_int), ("coef", ctypes.c_int),
+                ("a", ctypes.c_void_p), ("self_term", ctypes.c_int)]
+
+
+class nl_cg_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+class nl_plan_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
+                ("max_radius", ctypes.c_int), ("num_offsets", ctypes.c_int),
+                ("moments", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("poly", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t)]
+
+
+ENTRY_POINTS = ("nl_plan_create", "nl_plan_destroy", "nl_apply", "nl_apply_fast", "nl_cg_solve",
+                "nl_get_plan_info", "nl_last_error")
+
+_lib = None
+
+
+def lib():
+    """Load libnl.so (built by ``build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.nl_plan_create.restype = i
+    L.nl_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(nl_grid),
+                                 ctypes.POINTER(nl_horizon), ctypes.POINTER(nl_kernel), vp]
+    L.nl_plan_destroy.restype = i
+    L.nl_plan_destroy.argtypes = [vp]
+    for name in ("nl_apply", "nl_apply_fast"):
+        fn = getattr(L, name)
+        fn.restype = i
+        fn.argtypes = [vp, vp, vp, i, i, vp]
+    L.nl_cg_solve.restype = i
+    L.nl_cg_solve.argtypes = [vp, vp, vp, i, d, i, i, ctypes.POINTER(nl_cg_stats), vp]
+    L.nl_get_plan_info.restype = i
+    L.nl_get_plan_info.argtypes = [vp, ctypes.POINTER(nl_plan_info)]
+    L.nl_last_error.restype = ctypes.c_char_p
+    L.nl_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def nl_last_error() -> str:
+    return lib().nl_last_error().decode()
+
+
+def _check(status):
+    if status != NL_OK:
+        raise NlError(status, nl_last_error())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return NL_F32
+    if t.dtype == torch.float64:
+        return NL_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+class Plan:
+    """Owns an ``nl_plan*``; freed by ``close()`` or garbage collection."""
+
+    def __init__(self, handle, dim, n, family):
+        self.handle = handle
+        self.dim, self.n, self.family = dim, n, family
+
+    @property
+    def N(self):
+        return self.n ** self.dim
+
+    def close(self):
+        if self.handle:
+            lib().nl_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return nl_get_plan_info(self)
+
+
+def nl_plan_create(dim, n, delta, family=NL_POWER, alpha=0.0, K=0, scale=1.0, normalize=True,
+                   coef=NL_COEF_NONE, a=None, symmetric=False, self_term=NL_SELF_DISCRETE,
+                   stream=None) -> Plan:
+    """Create a plan.  `delta`: scalar or host array of n^dim values; `a`: host array or None."""
+    g = nl_grid(dim, n)
+    keep = []
+    if np.isscalar(delta):
+        hz = nl_horizon(float(delta), None, int(bool(symmetric)))
+    else:
+        dl = np.ascontiguousarray(delta, dtype=np.float64).reshape(-1)
+        if dl.size != n ** dim:
+            raise ValueError("delta field must have n^dim values")
+        keep.append(dl)
+        hz = nl_horizon(0.0, dl.ctypes.data, int(bool(symmetric)))
+    ap = None
+    if a is not None:
+        aa = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if aa.size != n ** dim:
+            raise ValueError("coefficient field must have n^dim values")
+        keep.append(aa)
+        ap = aa.ctypes.data
+    k = nl_kernel(int(family), float(alpha), int(K), float(scale), int(bool(normalize)),
+                  int(coef), ap, int(self_term))
+    h = ctypes.c_void_p()
+    st = _stream_ptr(stream) if _cuda_ready() else ctypes.c_void_p(None)
+    _check(lib().nl_plan_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(hz),
+                                ctypes.byref(k), st))
+    return Plan(h, dim, n, family)
+
+
+def _cuda_ready():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def _apply(fn, plan, u, Lu, nrhs, stream):
+    if not (u.is_cuda and Lu.is_cuda):
+        raise ValueError("u and Lu must be CUDA tensors")
+    if not (u.is_contiguous() and Lu.is_contiguous()) or u.dtype != Lu.dtype:
+        raise ValueError("u and Lu must be contiguous with the same dtype")
+    comps = plan.dim if plan.family == NL_PD_BOND else 1
+    per = plan.N * comps
+    if nrhs is None:
+        nrhs = u.numel() // per
+    if u.numel() != nrhs * per or Lu.numel() != nrhs * per:
+        raise ValueError("u/Lu size does not match nrhs * n^d (* d)")
+    _check(fn(plan.handle, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(Lu.data_ptr()),
+              int(nrhs), _dtype_code(u), _stream_ptr(stream)))
+    return Lu
+
+
+def nl_apply(plan: Plan, u, Lu, nrhs=None, stream=None):
+    """Direct apply on device tensors; returns Lu."""
+    return _apply(lib().nl_apply, plan, u, Lu, nrhs, stream)
+
+
+def nl_apply_fast(plan: Plan, u, Lu, nrhs=None, stream=None):
+    """Fast (Sec. 3) apply on device tensors; returns Lu."""
+    return _apply(lib().nl_apply_fast, plan, u, Lu, nrhs, stream)
+
+
+def nl_cg_solve(plan: Plan, f, x, nrhs=None, rtol=1e-8, maxit=10000, precond=NL_PRECOND_JACOBI,
+                stream=None) -> dict:
+    """CG on -L x = f (FP64 device tensors).  Returns the stats as a dict."""
+    comps = plan.dim if plan.family == NL_PD_BOND else 1
+    per = plan.N * comps
+    if nrhs is None:
+        nrhs = f.numel() // per
+    st = nl_cg_stats()
+    status = lib().nl_cg_solve(plan.handle, ctypes.c_void_p(f.data_ptr()),
+                               ctypes.c_void_p(x.data_ptr()), int(nrhs), float(rtol), int(maxit),
+                               int(precond), ctypes.byref(st), _stream_ptr(stream))
+    out = dict(iterations=st.iterations, rel_residual=st.rel_residual,
+               converged=bool(st.converged), status=status)
+    if status not in (NL_OK, NL_ENOTCONV):
+        _check(status)
+    return out
+
+
+def nl_get_plan_info(plan: Plan) -> dict:
+    info = nl_plan_info()
+    _check(lib().nl_get_plan_info(plan.handle, ctypes.byref(info)))
+    return dict(dim=info.dim, n=info.n, levels=info.levels, max_radius=info.max_radius,
+                num_offsets=info.num_offsets, moments=info.moments, sigma=info.sigma,
+                poly=list(info.poly), device_bytes=int(info.device_bytes))

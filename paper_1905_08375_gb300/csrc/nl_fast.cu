@@ -1,0 +1,538 @@
+// nl_fast.cu -- the fast algorithm of Sec. 3 for polynomial kernels
+//   P(x, y) = sigma C(x) delta(x)^{-(d+2)} p^{2K}(|y - x| / delta(x)).
+//
+// Step 2 (bottom-up partial sums): a pyramid of panel moments in FP64.  At
+// the leaves (one node per leaf cell, at its centre) the moments are v_k and
+// zeros; a parent's moments are its children's re-expanded about the parent
+// centre (binomial shift, exact algebra), in the coordinates
+// t = (x - c_Q) / (w_Q / 2) so that every moment is O(|v|).
+//
+// Step 1 + Step 3: the decomposition of Algorithm 1 is not stored.  A panel Q
+// of level l is in the decomposition of node x iff its parent is not fully
+// inside the ball and either Q is fully inside (all corners strictly inside,
+// the containment test of Algorithm 1) or Q is a leaf that meets the open
+// ball (Algorithm 2).  For a fixed panel row both conditions select one
+// contiguous run of panels whose end points follow from an integer square
+// root, so each node enumerates its decomposition level by level, row by row,
+// as at most two runs per row, and sums Eq. (3.5) over those panels.
+//
+// Geometry is exact integer arithmetic in half-units of h: node i sits at
+// X = 2 i + 1, panel k of level l spans [k S, (k + 1) S] with S = 2^{L-l+1},
+// and the ball test is (squared distance) <= thr4_i, thr4_i the largest
+// integer below 4 R2_i.
+#include <cmath>
+#include <vector>
+
+#include "nl_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int floor_div(int a, int b)   // b > 0
+{
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+__device__ __forceinline__ int ceil_div(int a, int b) { return -floor_div(-a, b); }
+
+// largest r >= 0 with r*r <= x (x >= 0)
+__device__ __forceinline__ int isqrt_floor(int x)
+{
+    int r = (int)sqrtf((float)x);
+    while (r > 0 && (long long)r * r > x) --r;
+    while ((long long)(r + 1) * (r + 1) <= x) ++r;
+    return r;
+}
+
+// farthest / nearest squared distance (half-units) from X to panel [kS, (k+1)S]
+__device__ __forceinline__ int far2(int k, int S, int X)
+{
+    const int a = abs(k * S - X), b = abs((k + 1) * S - X);
+    const int m = a > b ? a : b;
+    return m * m;
+}
+__device__ __forceinline__ int near2(int k, int S, int X)
+{
+    int g = 0;
+    if (k * S > X) g = k * S - X;
+    else if ((k + 1) * S < X) g = X - (k + 1) * S;
+    return g * g;
+}
+
+struct FastArgs {
+    int d, n, L, K, M;
+    int64_t N;
+    const int *thr4;
+    const double *fastF, *selfS, *ir4;
+    const double *pyr;           // levels 0..L-1, [panel][M]
+    const double *leaf;          // level L, v_k
+    int64_t lvl_off[NL_MAX_LEVELS + 2];
+    double hd;
+    double poly[8];
+};
+
+// moment index of (a0, a1) in the compact order (a1 outer, a0 inner, a0 + a1 <= 2K)
+template <int K>
+__device__ __host__ __forceinline__ int midx2(int a0, int a1)
+{
+    return a1 * (2 * K + 1) - (a1 * (a1 - 1)) / 2 + a0;
+}
+
+// sum over x_k in panel of p(|x_k - x_i|^2 / delta_i^2) v_k from the panel moments:
+// |x_k - x_i|^2 / delta^2 = |B + H t|^2 / (4 R2), B = centre - X, H = half-width
+template <int D, int K>
+__device__ __forceinline__ double panel_poly(const double *mu, const double *pc, int Bx, int By,
+                                             int H, double ir4)
+{
+    if constexpr (K == 0) {
+        return pc[0] * mu[0];
+    } else if constexpr (D == 1) {
+        constexpr int E = 2 * K + 1;
+        const double c0 = (double)Bx * Bx * ir4, c1 = 2.0 * Bx * H * ir4, c2 = (double)H * H * ir4;
+        double q[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) q[e] = 0.0;
+        q[0] = pc[K];
+#pragma unroll
+        for (int m = K - 1; m >= 0; --m) {
+            // q <- q * (c0 + c1 t + c2 t^2) + p_m; degree grows by 2 each step
+            double nq[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                double s = c0 * q[e];
+                if (e >= 1) s += c1 * q[e - 1];
+                if (e >= 2) s += c2 * q[e - 2];
+                nq[e] = s;
+            }
+            nq[0] += pc[m];
+#pragma unroll
+            for (int e = 0; e < E; ++e) q[e] = nq[e];
+        }
+        double v = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v += q[e] * mu[e];
+        return v;
+    } else {
+        constexpr int E = 2 * K + 1;
+        const double H2 = (double)H * H * ir4;
+        const double c00 = ((double)Bx * Bx + (double)By * By) * ir4;
+        const double c10 = 2.0 * Bx * H * ir4, c01 = 2.0 * By * H * ir4;
+        double q[E][E];
+#pragma unroll
+        for (int a = 0; a < E; ++a)
+#pragma unroll
+            for (int b = 0; b < E; ++b) q[a][b] = 0.0;
+        q[0][0] = pc[K];
+#pragma unroll
+        for (int m = K - 1; m >= 0; --m) {
+            double nq[E][E];
+#pragma unroll
+            for (int a = 0; a < E; ++a)
+#pragma unroll
+                for (int b = 0; b < E; ++b) {
+                    double s = 0.0;
+                    if (a + b <= 2 * K) {
+                        s = c00 * q[a][b];
+                        if (a >= 1) s += c10 * q[a - 1][b];
+                        if (b >= 1) s += c01 * q[a][b - 1];
+                        if (a >= 2) s += H2 * q[a - 2][b];
+                        if (b >= 2) s += H2 * q[a][b - 2];
+                    }
+                    nq[a][b] = s;
+                }
+            nq[0][0] += pc[m];
+#pragma unroll
+            for (int a = 0; a < E; ++a)
+#pragma unroll
+                for (int b = 0; b < E; ++b) q[a][b] = nq[a][b];
+        }
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < E; ++b)
+#pragma unroll
+            for (int a = 0; a + b < E; ++a) v += q[a][b] * mu[midx2<K>(a, b)];
+        return v;
+    }
+}
+
+// Parent-full x-range (child units) of parent row (pky, pkz) at level l-1, or empty.
+__device__ __forceinline__ void parent_full(int D, int l, int S, int np, int X, int Y, int Z,
+                                            int ky, int kz, int T4, int &lo, int &hi)
+{
+    lo = 1; hi = 0;
+    if (l == 0) return;
+    const int S2 = 2 * S, npp = np >> 1;
+    int e = 0;
+    if (D > 1) e += far2(ky >> 1, S2, Y);
+    if (D > 2) e += far2(kz >> 1, S2, Z);
+    if (e > T4) return;
+    const int r = isqrt_floor(T4 - e);
+    const int a = max(0, ceil_div(X - r, S2));
+    const int b = min(npp - 1, floor_div(X + r, S2) - 1);
+    if (a > b) return;
+    lo = 2 * a;
+    hi = 2 * b + 1;
+}
+
+template <int D, int K>
+__device__ __forceinline__ double sum_run(const FastArgs &a, int l, int np, int S, int ka, int kb,
+                                          int ky, int kz, int X, int Y, int Z, int ix, int iy,
+                                          int iz, double ir4)
+{
+    double s = 0.0;
+    if (ka > kb) return s;
+    const int64_t rowbase = (int64_t)np * (ky + (int64_t)np * kz);
+    if (l == a.L) {
+        const double *leaf = a.leaf + rowbase;
+        if constexpr (K == 0) {
+            for (int k = ka; k <= kb; ++k) s += leaf[k];
+        } else {
+            const int oy = ky - iy, oz = kz - iz;
+            for (int k = ka; k <= kb; ++k) {
+                const int ox = k - ix;
+                const double t = (double)(ox * ox + oy * oy + oz * oz) * (4.0 * ir4);
+                double w = a.poly[K];
+#pragma unroll
+                for (int m = K - 1; m >= 0; --m) w = w * t + a.poly[m];
+                s += w * leaf[k];
+            }
+        }
+    } else {
+        const double *lev = a.pyr + a.lvl_off[l] + rowbase * a.M;
+        if constexpr (K == 0) {
+            for (int k = ka; k <= kb; ++k) s += lev[k];
+        } else {
+            const int H = S / 2;
+            const int By = (D > 1) ? ky * S + H - Y : 0;
+            for (int k = ka; k <= kb; ++k) {
+                const int Bx = k * S + H - X;
+                s += panel_poly<D, K>(lev + (int64_t)k * a.M, a.poly, Bx, By, H, ir4);
+            }
+        }
+    }
+    return s;
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(256) k_fast_gather(FastArgs a, const T *__restrict__ u,
+                                                     T *__restrict__ Lu)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)((i / n) % n) : 0;
+    const int iz = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+    const int X = 2 * ix + 1, Y = 2 * iy + 1, Z = 2 * iz + 1;
+    const int T4 = a.thr4[i];
+    const double ir4 = (K > 0) ? a.ir4[i] : 0.0;
+    const int r0 = isqrt_floor(T4);
+    double G = 0.0;
+    for (int l = 0; l <= a.L; ++l) {
+        const int np = 1 << l;
+        const int S = 2 << (a.L - l);
+        const bool leaf = (l == a.L);
+        // rows (and slabs) that can hold included panels at this level
+        int ylo = 0, yhi = 0, zlo = 0, zhi = 0;
+        if (D > 1) {
+            ylo = max(0, leaf ? ceil_div(Y - r0, S) - 1 : ceil_div(Y - r0, S));
+            yhi = min(np - 1, leaf ? floor_div(Y + r0, S) : floor_div(Y + r0, S) - 1);
+        }
+        if (D > 2) {
+            zlo = max(0, leaf ? ceil_div(Z - r0, S) - 1 : ceil_div(Z - r0, S));
+            zhi = min(np - 1, leaf ? floor_div(Z + r0, S) : floor_div(Z + r0, S) - 1);
+        }
+        for (int kz = zlo; kz <= zhi; ++kz) {
+            const int ez_far = D > 2 ? far2(kz, S, Z) : 0;
+            const int ez_near = D > 2 ? near2(kz, S, Z) : 0;
+            for (int ky = ylo; ky <= yhi; ++ky) {
+                const int e_far = ez_far + (D > 1 ? far2(ky, S, Y) : 0);
+                const int e_near = ez_near + (D > 1 ? near2(ky, S, Y) : 0);
+                int ka, kb;
+                if (leaf) {
+                    if (e_near > T4) continue;
+                    const int r = isqrt_floor(T4 - e_near);
+                    ka = max(0, ceil_div(X - r, S) - 1);
+                    kb = min(np - 1, floor_div(X + r, S));
+                } else {
+                    if (e_far > T4) continue;
+                    const int r = isqrt_floor(T4 - e_far);
+                    ka = max(0, ceil_div(X - r, S));
+                    kb = min(np - 1, floor_div(X + r, S) - 1);
+                }
+                if (ka > kb) continue;
+                int pa, pb;
+                parent_full(D, l, S, np, X, Y, Z, ky, kz, T4, pa, pb);
+                if (pa > pb) {
+                    G += sum_run<D, K>(a, l, np, S, ka, kb, ky, kz, X, Y, Z, ix, iy, iz, ir4);
+                } else {
+                    G += sum_run<D, K>(a, l, np, S, ka, min(kb, pa - 1), ky, kz, X, Y, Z, ix, iy, iz, ir4);
+                    G += sum_run<D, K>(a, l, np, S, max(ka, pb + 1), kb, ky, kz, X, Y, Z, ix, iy, iz, ir4);
+                }
+            }
+        }
+    }
+    const double ui = (double)u[i];
+    Lu[i] = (T)(a.fastF[i] * (a.hd * G - ui * a.selfS[i]));
+}
+
+// ---------------------------------------------------------------------------
+// Step 2: the moment pyramid
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_pyr_leaf(int64_t N, const T *__restrict__ u, const double *__restrict__ b,
+                           double *leaf)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) leaf[i] = (double)u[i] * b[i];
+}
+
+// one thread per parent panel of level l; children at level l+1
+__global__ void k_pyr_level(int d, int l, int L, int M, const double *__restrict__ child,
+                            double *__restrict__ parent, const double *__restrict__ shift)
+{
+    const int np = 1 << l;
+    int64_t P = np;
+    if (d > 1) P *= np;
+    if (d > 2) P *= np;
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= P) return;
+    const int kx = (int)(f % np);
+    const int ky = d > 1 ? (int)((f / np) % np) : 0;
+    const int kz = d > 2 ? (int)(f / ((int64_t)np * np)) : 0;
+    const int nc = 2 * np;
+    const bool child_leaf = (l + 1 == L);
+    const int cm = child_leaf ? 1 : M;       // leaves carry v only
+    for (int al = 0; al < M; ++al) {
+        double acc = 0.0;
+        for (int s = 0; s < (1 << d); ++s) {
+            const int cx = 2 * kx + (s & 1);
+            const int cy = d > 1 ? 2 * ky + ((s >> 1) & 1) : 0;
+            const int cz = d > 2 ? 2 * kz + ((s >> 2) & 1) : 0;
+            const int64_t fc = cx + (int64_t)nc * (cy + (int64_t)nc * cz);
+            const double *mu = child + fc * cm;
+            const double *T = shift + ((int64_t)s * M + al) * M;
+            for (int be = 0; be < cm; ++be) acc += T[be] * mu[be];
+        }
+        parent[f * M + al] = acc;
+    }
+}
+
+// self term S_i of Eq. (3.3) (plan time) and per-node factors
+__global__ void k_fast_node(int d, int n, int K, int coef, int self_mode, int64_t N, double sigma,
+                            double sphere, const double *__restrict__ delta,
+                            const double *__restrict__ acoef, const int *__restrict__ thr4,
+                            const double *__restrict__ pc, double *fastF, double *selfS,
+                            double *ir4)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double di = delta[i];
+    const double rho = di * n;
+    const double R2 = rho * rho;
+    const double ai = acoef ? acoef[i] : 1.0;
+    const double Ai = (coef == NL_COEF_NONE) ? 1.0 : ai;
+    fastF[i] = sigma * Ai * pow(di, -(d + 2.0));
+    ir4[i] = 1.0 / (4.0 * R2);
+    if (self_mode == NL_SELF_PAPER) {
+        double s = 0.0;
+        for (int m = 0; m <= K; ++m) s += pc[m] / (2.0 * m + d);
+        selfS[i] = sphere * pow(di, (double)d) * s;
+        return;
+    }
+    const int ix = (int)(i % n);
+    const int iy = d > 1 ? (int)((i / n) % n) : 0;
+    const int iz = d > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+    const int T4 = thr4[i];
+    const int B = (int)ceil(rho) + 1;
+    const int bz = d > 2 ? B : 0, by = d > 1 ? B : 0;
+    double acc = 0.0;
+    for (int oz = -bz; oz <= bz; ++oz)
+        for (int oy = -by; oy <= by; ++oy)
+            for (int ox = -B; ox <= B; ++ox) {
+                // gap from the node (cell centre) to cell i + o, half-units: 2|o| - 1
+                const int gx = ox ? 2 * abs(ox) - 1 : 0;
+                const int gy = oy ? 2 * abs(oy) - 1 : 0;
+                const int gz = oz ? 2 * abs(oz) - 1 : 0;
+                if (gx * gx + gy * gy + gz * gz > T4) continue;
+                double b = 1.0;
+                if (coef == NL_COEF_XY) {
+                    const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+                    bool in = jx >= 0 && jx < n;
+                    if (d > 1) in = in && jy >= 0 && jy < n;
+                    if (d > 2) in = in && jz >= 0 && jz < n;
+                    b = in ? acoef[jx + (int64_t)n * (jy + (int64_t)n * jz)] : ai;
+                }
+                const double t = (double)(ox * ox + oy * oy + oz * oz) / R2;
+                double w = pc[K];
+                for (int m = K - 1; m >= 0; --m) w = w * t + pc[m];
+                acc += w * b;
+            }
+    selfS[i] = pow(1.0 / n, (double)d) * acc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int moments_count(int d, int K)
+{
+    int M = 0;
+    for (int a2 = 0; a2 <= (d > 2 ? 2 * K : 0); ++a2)
+        for (int a1 = 0; a1 <= (d > 1 ? 2 * K : 0); ++a1)
+            for (int a0 = 0; a0 <= 2 * K; ++a0)
+                if (a0 + a1 + a2 <= 2 * K) ++M;
+    return M;
+}
+
+nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
+                            cudaStream_t st)
+{
+    const int d = p->d, K = p->K, L = p->L;
+    // fast path unavailable (apply reports NL_EUNSUPPORTED): 3-D with K > 0, n not a
+    // power of two, or n > 8192 (integer half-unit geometry is kept within 32 bits)
+    if ((d == 3 && K > 0) || L < 0 || p->n > 8192) return NL_OK;
+    p->M = moments_count(d, K);
+    const int M = p->M;
+    // multi-indices in the compact order (a2 outer, a1, a0 inner)
+    std::vector<int> al;
+    for (int a2 = 0; a2 <= (d > 2 ? 2 * K : 0); ++a2)
+        for (int a1 = 0; a1 <= (d > 1 ? 2 * K : 0); ++a1)
+            for (int a0 = 0; a0 <= 2 * K; ++a0)
+                if (a0 + a1 + a2 <= 2 * K) { al.push_back(a0); al.push_back(a1); al.push_back(a2); }
+    // re-centring: child s in {0,1}^d, t_parent = (t_child + 2 s - 1) / 2, so
+    // t_p^alpha = prod_k 2^{-alpha_k} sum_{beta_k} C(alpha_k, beta_k) (2s_k - 1)^{alpha_k - beta_k} t_c^{beta_k}
+    std::vector<double> shift((size_t)(1 << d) * M * M, 0.0);
+    auto binom = [](int a, int b) {
+        double r = 1.0;
+        for (int t = 0; t < b; ++t) r = r * (a - t) / (t + 1);
+        return r;
+    };
+    for (int s = 0; s < (1 << d); ++s)
+        for (int ia = 0; ia < M; ++ia)
+            for (int ib = 0; ib < M; ++ib) {
+                double c = 1.0;
+                for (int k = 0; k < d && c != 0.0; ++k) {
+                    const int A = al[3 * ia + k], Bb = al[3 * ib + k];
+                    if (Bb > A) { c = 0.0; break; }
+                    const double sg = ((s >> k) & 1) ? 1.0 : -1.0;
+                    c *= binom(A, Bb) * std::pow(sg, A - Bb) * std::ldexp(1.0, -A);
+                }
+                shift[((size_t)s * M + ia) * M + ib] = c;
+            }
+    int64_t off = 0;
+    for (int l = 0; l < L; ++l) {
+        p->lvl_off[l] = off;
+        int64_t P = 1;
+        for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
+        off += P * M;
+    }
+    p->lvl_off[L] = off;           // leaf level: N values of v
+    const int64_t total = off + p->N;
+
+    auto alloc = [&](void **ptr, size_t bytes) -> nl_status {
+        cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 1);
+        if (e != cudaSuccess) {
+            nl_set_error("cudaMalloc(%zu) for the fast path: %s", bytes, cudaGetErrorString(e));
+            return NL_ENOMEM;
+        }
+        p->device_bytes += bytes;
+        return NL_OK;
+    };
+    nl_status s;
+    if ((s = alloc((void **)&p->pyr, total * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->shift, shift.size() * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->malpha, al.size() * sizeof(int))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->fastF, p->N * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->selfS, p->N * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->ir4, p->N * sizeof(double))) != NL_OK) return s;
+    double *d_pc = nullptr;
+    if ((s = alloc((void **)&d_pc, 8 * sizeof(double))) != NL_OK) return s;
+    NL_CUDA_TRY(cudaMemcpyAsync(p->shift, shift.data(), shift.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, st));
+    NL_CUDA_TRY(cudaMemcpyAsync(p->malpha, al.data(), al.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, st));
+    NL_CUDA_TRY(cudaMemcpyAsync(d_pc, p->poly, 8 * sizeof(double), cudaMemcpyHostToDevice, st));
+    const double pi = 3.141592653589793238462643383279502884;
+    const double sphere = d == 1 ? 2.0 : (d == 2 ? 2.0 * pi : 4.0 * pi);
+    const unsigned gb = (unsigned)((p->N + 255) / 256);
+    k_fast_node<<<gb, 256, 0, st>>>(d, p->n, K, p->coef, p->self_mode, p->N, p->sigma, sphere,
+                                    delta_dev, a_dev, p->thr4, d_pc, p->fastF, p->selfS, p->ir4);
+    NL_CUDA_TRY(cudaGetLastError());
+    NL_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(d_pc);
+    p->device_bytes -= 8 * sizeof(double);
+    return NL_OK;
+}
+
+template <typename T>
+static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
+{
+    const int d = p->d, L = p->L, M = p->M;
+    double *leaf = p->pyr + p->lvl_off[L];
+    const unsigned gb = (unsigned)((p->N + 255) / 256);
+    k_pyr_leaf<T><<<gb, 256, 0, st>>>(p->N, u, p->b64, leaf);
+    for (int l = L - 1; l >= 0; --l) {
+        int64_t P = 1;
+        for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
+        const double *child = (l + 1 == L) ? leaf : p->pyr + p->lvl_off[l + 1];
+        const unsigned g = (unsigned)((P + 127) / 128);
+        k_pyr_level<<<g, 128, 0, st>>>(d, l, L, M, child, p->pyr + p->lvl_off[l], p->shift);
+    }
+    FastArgs a;
+    a.d = d; a.n = p->n; a.L = L; a.K = p->K; a.M = M; a.N = p->N;
+    a.thr4 = p->thr4; a.fastF = p->fastF; a.selfS = p->selfS; a.ir4 = p->ir4;
+    a.pyr = p->pyr; a.leaf = leaf;
+    for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
+    a.hd = std::pow(p->h, (double)d);
+    for (int m = 0; m < 8; ++m) a.poly[m] = p->poly[m];
+#define NL_GATHER(D, KK) k_fast_gather<D, KK, T><<<gb, 256, 0, st>>>(a, u, Lu)
+    if (d == 1) {
+        switch (p->K) { case 0: NL_GATHER(1, 0); break; case 1: NL_GATHER(1, 1); break;
+                        case 2: NL_GATHER(1, 2); break; default: NL_GATHER(1, 3); }
+    } else if (d == 2) {
+        switch (p->K) { case 0: NL_GATHER(2, 0); break; case 1: NL_GATHER(2, 1); break;
+                        case 2: NL_GATHER(2, 2); break; default: NL_GATHER(2, 3); }
+    } else {
+        NL_GATHER(3, 0);
+    }
+#undef NL_GATHER
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
+                         cudaStream_t st)
+{
+    for (int r = 0; r < nrhs; ++r) {
+        nl_status s;
+        if (dtype == NL_F32)
+            s = fast_one<float>(p, (const float *)u + (int64_t)r * p->N, (float *)Lu + (int64_t)r * p->N, st);
+        else
+            s = fast_one<double>(p, (const double *)u + (int64_t)r * p->N, (double *)Lu + (int64_t)r * p->N, st);
+        if (s != NL_OK) return s;
+    }
+    return NL_OK;
+}
+
+extern "C" nl_status nl_apply_fast(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
+                                   void *stream)
+{
+    if (!nl_plan_ok(p)) {
+        nl_set_error("nl_apply_fast: invalid plan");
+        return NL_EINVAL;
+    }
+    if (!u || !Lu || nrhs < 1 || (dtype != NL_F32 && dtype != NL_F64)) {
+        nl_set_error("nl_apply_fast: need non-null u/Lu, nrhs >= 1, dtype F32/F64");
+        return NL_EINVAL;
+    }
+    if (p->family != NL_POLY || p->symmetric || p->L < 0 || !p->pyr) {
+        nl_set_error("nl_apply_fast: needs a non-symmetric NL_POLY plan on n = 2^L "
+                     "(d = 3 only with K = 0)");
+        return NL_EUNSUPPORTED;
+    }
+    if (p->self_mode == NL_SELF_PAPER && p->coef == NL_COEF_XY) {
+        nl_set_error("nl_apply_fast: NL_SELF_PAPER is not defined for NL_COEF_XY");
+        return NL_EUNSUPPORTED;
+    }
+    return nl_fast_launch(p, u, Lu, nrhs, dtype, nl_stream(stream));
+}

@@ -1,0 +1,106 @@
+// nl_internal.cuh -- plan layout and helpers shared by the library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "nl.h"
+
+#define NL_PLAN_MAGIC 0x4e4c504cu  // "NLPL"
+#define NL_PLAN_VERSION 1
+
+// Largest supported ball radius (cells) and offset-table length.
+#define NL_MAX_TABLE (1 << 20)
+#define NL_MAX_LEVELS 20
+
+// Block shapes of the direct kernels: one output node per thread.
+template <int D> struct DirectBlock;
+template <> struct DirectBlock<1> { static constexpr int X = 128, Y = 1, Z = 1; };
+template <> struct DirectBlock<2> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <> struct DirectBlock<3> { static constexpr int X = 32, Y = 4, Z = 2; };
+
+// One entry of the offset table, sorted by |o|^2.  soff is the offset inside
+// the shared-memory halo tile of the direct kernels (strides fixed per plan).
+struct __align__(16) OffEntry32 { int soff; int o2; float g; int pad; };
+struct __align__(16) OffEntry64 { int soff; int o2; double g; };
+
+// Peridynamic bond table: G = o o^T / |o|^3 (units of h), upper triangle.
+struct __align__(16) PdEntry32 { int soff; float gxx, gxy, gyy; };
+struct __align__(16) PdEntry64 { int soff; int pad; double gxx, gxy, gyy; };
+
+struct nl_plan {
+    uint32_t magic;
+    int version;
+    // problem
+    int d, n, L;            // L = log2 n or -1
+    int64_t N;
+    int family, coef, symmetric, self_mode, K;
+    double alpha, scale, sigma, h;
+    double poly[8];
+    // horizon summary
+    int Rmax;               // max ceil(delta_i n)
+    int thr_max;            // max over nodes of the largest integer |o|^2 inside the ball
+    int num_off;            // table length (offsets with 0 < |o|^2 <= thr_sym_max)
+    int stage;              // 1: direct kernels stage a halo tile in shared memory
+    size_t smem_bytes32, smem_bytes64;
+    int tile_sx, tile_sy, tile_sz;   // halo tile extents
+    // per-node device arrays
+    int *thr;               // largest integer < R2_i
+    int *cnt;               // table entries with o2 <= thr_i (or the symmetric bound)
+    float *b32;   double *b64;     // summed coefficient b_j (a_j or 1)
+    float *fin32; double *fin64;   // final factor
+    float *ext32; double *ext64;   // exterior coefficient
+    float *wh32;  double *wh64;    // W_i / 2 (symmetric variant)
+    float *ir32;  double *ir64;    // 1 / R2_i (polynomial kernels)
+    // offset tables
+    int4 *off;                      // (dx, dy, dz, o2)
+    OffEntry32 *tab32; OffEntry64 *tab64;
+    PdEntry32 *pd32; PdEntry64 *pd64;
+    double *pdext;                  // [N][3] exterior G sums (xx, xy, yy) times c_i
+    // fast path (Sec. 3)
+    int M;                          // moments per panel
+    int *thr4;                      // largest integer < 4 R2_i
+    double *fastF;                  // sigma A_i delta_i^{-(d+2)}
+    double *selfS;                  // self term S_i
+    double *ir4;                    // 1 / (4 R2_i)
+    double *pyr;                    // moment pyramid, levels 0..L, [panel][M]
+    int64_t lvl_off[NL_MAX_LEVELS + 2];
+    double *shift;                  // Step 2 re-centring table [2^d][M][M]
+    int *malpha;                    // multi-indices [M][3]
+    int pyr_rhs;                    // right-hand sides the pyramid buffer holds
+    // CG workspace
+    double *cg_ws; size_t cg_ws_elems;
+    float *cg_ws32; size_t cg_ws32_elems;
+    double *cg_red; int cg_red_elems;
+    double *cg_host; int cg_host_elems;
+    size_t device_bytes;
+};
+
+// ---- error reporting (thread-local message) ----
+void nl_set_error(const char *fmt, ...);
+nl_status nl_cuda_fail(cudaError_t e, const char *what);
+
+#define NL_CUDA_TRY(call)                                                   \
+    do {                                                                    \
+        cudaError_t _e = (call);                                            \
+        if (_e != cudaSuccess) return nl_cuda_fail(_e, #call);              \
+    } while (0)
+
+static inline bool nl_plan_ok(const nl_plan *p)
+{
+    return p && p->magic == NL_PLAN_MAGIC && p->version == NL_PLAN_VERSION;
+}
+
+static inline cudaStream_t nl_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---- per-module launchers ----
+nl_status nl_direct_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
+                           cudaStream_t st);
+nl_status nl_pd_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
+                       cudaStream_t st);
+nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
+                         cudaStream_t st);
+nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
+                            cudaStream_t st);
+nl_status nl_cg_release(nl_plan *p);

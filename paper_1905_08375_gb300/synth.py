@@ -34,10 +34,11 @@ def _smooth_noise(rng, d, n, width_cells):
     normalised to zero mean and unit variance."""
     w = rng.standard_normal((n,) * d)
     k = np.fft.fftfreq(n) * n  # integer wavenumbers
-    ks = np.meshgrid(*([k] * d), indexing="ij")
+    kr = np.fft.rfftfreq(n) * n
+    ks = np.meshgrid(*([k] * (d - 1) + [kr]), indexing="ij", sparse=True)
     k2 = sum(kk.astype(np.float64) ** 2 for kk in ks)
     filt = np.exp(-2.0 * (np.pi * width_cells / n) ** 2 * k2)
-    g = np.real(np.fft.ifftn(np.fft.fftn(w) * filt))
+    g = np.fft.irfftn(np.fft.rfftn(w) * filt, s=w.shape)
     g -= g.mean()
     sd = g.std()
     return g / sd if sd > 0 else g

@@ -1,0 +1,130 @@
+"""GPU parity of the fast algorithm (nl_apply_fast, Sec. 3) against the FP64 oracle.
+
+The fast result is exact with respect to its own quadrature (the leaf cells that meet
+the ball), so it is gated against the oracle's leaf-set sum O2 (itself pinned to the
+literal tree algorithm O1) at the direct path's tolerances."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1905_08375_gb300 import binding as nl
+from paper_1905_08375_gb300 import synth
+from helpers import boundary_idx, rel_l2, sample_idx
+
+pytestmark = pytest.mark.gpu
+TOL = {torch.float64: 1e-12, torch.float32: 2e-6}
+DEV = "cuda:0"
+
+
+def run_fast(plan, u, dtype):
+    ut = torch.tensor(np.asarray(u), dtype=dtype, device=DEV).contiguous()
+    out = torch.full_like(ut, float("nan"))
+    nl.nl_apply_fast(plan, ut, out)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("K", [0, 1, 2, 3])
+def test_example2_1d_variable_horizon(dtype, K):
+    n = 512
+    f = synth.example2_1d(n=n, delta0=0.25, seed=0)
+    plan = nl.nl_plan_create(1, n, f["delta"], family=nl.NL_POLY, alpha=1.0, K=K)
+    ref = oracle.fast_leafset(f["u"], 1, 9, f["delta"], K=K, alpha=1.0)
+    assert rel_l2(run_fast(plan, f["u"], dtype), ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 3])
+@pytest.mark.parametrize("coef,self_mode", [(nl.NL_COEF_NONE, nl.NL_SELF_PAPER),
+                                            (nl.NL_COEF_X, nl.NL_SELF_DISCRETE),
+                                            (nl.NL_COEF_XY, nl.NL_SELF_DISCRETE)])
+def test_2d_all_orders(K, coef, self_mode):
+    n, L = 64, 6
+    f = synth.heterogeneous_2d(n=n, seed=5, nrhs=2)
+    a = None if coef == nl.NL_COEF_NONE else f["a"]
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=K, coef=coef,
+                             a=a, self_term=self_mode)
+    ref = oracle.fast_leafset(f["u"], 2, L, f["delta"], K=K, alpha=1.5, coef=coef, a=a,
+                              self_mode=self_mode)
+    ut = torch.tensor(f["u"], dtype=torch.float64, device=DEV)
+    out = torch.empty_like(ut)
+    nl.nl_apply_fast(plan, ut, out)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), ref) <= 1e-12
+
+
+def test_2d_literal_tree_agrees():
+    """Also against O1 (Algorithm 1 + pyramid) directly."""
+    n, L = 32, 5
+    rng = np.random.default_rng(11)
+    delta = rng.uniform(1.5, 9.0, size=n * n) / n
+    u = rng.standard_normal(n * n)
+    plan = nl.nl_plan_create(2, n, delta, family=nl.NL_POLY, alpha=1.0, K=2)
+    ref = oracle.fast_tree(u, 2, L, delta, K=2, alpha=1.0)
+    assert rel_l2(run_fast(plan, u, torch.float64), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 16])
+def test_3d_k0_and_tiny(n):
+    L = int(np.log2(n))
+    rng = np.random.default_rng(n)
+    delta = rng.uniform(0.6, 3.5, size=n ** 3) / n
+    a = np.exp(0.3 * rng.standard_normal(n ** 3))
+    u = rng.standard_normal(n ** 3)
+    plan = nl.nl_plan_create(3, n, delta, family=nl.NL_POLY, alpha=1.0, K=0,
+                             coef=nl.NL_COEF_XY, a=a)
+    ref = oracle.fast_leafset(u, 3, L, delta, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a)
+    got = run_fast(plan, u, torch.float64)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_example1_2d_full():
+    """Example 1 of Sec. 4: 128^2, delta = 1/2, K = 0, C = 1, continuous self term."""
+    n, L = 128, 7
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal(n * n)
+    plan = nl.nl_plan_create(2, n, 0.5, family=nl.NL_POLY, K=0, normalize=False,
+                             self_term=nl.NL_SELF_PAPER)
+    ref = oracle.fast_tree(u, 2, L, 0.5, K=0, normalize=False, self_mode=oracle.SELF_PAPER)
+    assert rel_l2(run_fast(plan, u, torch.float64), ref) <= 1e-12
+
+
+def test_example2_1d_4096_k3():
+    n, L = 4096, 12
+    f = synth.example2_1d(n=n, delta0=0.25, seed=1)
+    plan = nl.nl_plan_create(1, n, f["delta"], family=nl.NL_POLY, alpha=1.0, K=3,
+                             normalize=False)
+    ref = oracle.fast_tree(f["u"], 1, L, f["delta"], K=3, alpha=1.0, normalize=False)
+    assert rel_l2(run_fast(plan, f["u"], torch.float64), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_config2_full_size_sampled(dtype):
+    n, L = 1024, 10
+    f = synth.heterogeneous_2d(n=n, seed=0)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
+                             coef=nl.NL_COEF_XY, a=f["a"])
+    got = run_fast(plan, f["u"][0], dtype)
+    idx = np.concatenate([sample_idx(n * n, 1500, seed=5), boundary_idx(2, n, 18, 500, seed=6)])
+    ref = oracle.fast_leafset(f["u"][0], 2, L, f["delta"], K=0, alpha=1.5, coef=oracle.COEF_XY,
+                              a=f["a"], idx=idx)
+    assert rel_l2(got[idx], ref) <= TOL[dtype]
+    assert np.isfinite(got).all()
+
+
+def test_unsupported_requests():
+    rng = np.random.default_rng(0)
+    u = torch.zeros(24 * 24, dtype=torch.float64, device=DEV)
+    out = torch.empty_like(u)
+    p1 = nl.nl_plan_create(2, 24, 0.1, family=nl.NL_POLY, K=0)       # n not a power of 2
+    with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
+        nl.nl_apply_fast(p1, u, out)
+    p2 = nl.nl_plan_create(2, 16, 0.1, family=nl.NL_POWER, alpha=1.0)
+    u2 = torch.zeros(256, dtype=torch.float64, device=DEV)
+    with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
+        nl.nl_apply_fast(p2, u2, torch.empty_like(u2))
+    p3 = nl.nl_plan_create(3, 8, 0.2, family=nl.NL_POLY, K=1)
+    u3 = torch.zeros(512, dtype=torch.float64, device=DEV)
+    with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
+        nl.nl_apply_fast(p3, u3, torch.empty_like(u3))
