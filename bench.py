@@ -66,6 +66,9 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:   # first sample before timing
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -195,7 +198,7 @@ def run_gpu(args, peaks):
             ts.append(a.elapsed_time(b))
         return float(np.mean(ts))
 
-    reps = max(3, args.steps)
+    reps = max(3, min(args.steps, 50))
     t_direct = time_fn(lambda: nl.nl_apply(direct, u, out_d), reps)
     t_fast = time_fn(lambda: nl.nl_apply_fast(fast, u, out_f), reps)
     u64 = u.double()
@@ -341,8 +344,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
