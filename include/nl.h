@@ -167,6 +167,35 @@ typedef enum { NL_PRECOND_NONE = 0, NL_PRECOND_JACOBI = 1 } nl_precond;
 nl_status nl_cg_solve(nl_plan *plan, const void *f, void *x, int nrhs, double rtol, int maxit,
                       int precond, nl_cg_stats *stats, void *stream);
 
+/*
+ * nl_apply_fast_noalloc -- the fast apply of Sec. 3 with p^{2K} = 1 (K = 0) and C = 1, for
+ * callers that must not allocate device memory: a host whose device memory is all handed to
+ * its own pool allocator (a library cudaMalloc would fail or fragment the pool), or a caller
+ * on a latency-critical path that cannot take the implicit device synchronisation that
+ * cudaMalloc/cudaFree may cause.  It creates no plan and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The paper has no counterpart: this is a packaging variant of
+ * nl_apply_fast.  Its result equals nl_apply_fast on an NL_POLY, K = 0, NL_COEF_NONE plan.
+ *
+ * Scratch: a file-scope device array of 32 MiB inside the library, held by every GPU on
+ * which the library's module is loaded until the process exits.  It bounds the grid:
+ * n = 2^L with at most 8192 (1-D), 1024 (2-D) or 64 (3-D) nodes per dimension; larger
+ * grids are rejected with NL_EINVAL and a message giving the bytes needed.  The first call
+ * made on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls share the
+ * array and each call rewrites every part it reads, so no clearing is needed, but calls
+ * whose kernels overlap on the GPU (other streams or host threads on the same device) race
+ * on it: order them.
+ *
+ * Arguments: dim 1..3; n nodes per dimension; delta > 0 the constant horizon, used when
+ * delta_field is NULL; delta_field a DEVICE pointer to n^dim FP64 horizons (caller-owned,
+ * read only) or NULL; alpha, scale, normalize as in nl_kernel (sigma); self_term an nl_self;
+ * u, Lu DEVICE pointers, nrhs stacked fields [nrhs][n^dim] of `dtype`.  Stream-ordered and
+ * asynchronous.  Errors: NL_EINVAL, NL_EUNSUPPORTED (n not a power of two), NL_ECUDA.
+ */
+nl_status nl_apply_fast_noalloc(int dim, int n, double delta, const double *delta_field,
+                                double alpha, double scale, int normalize, int self_term,
+                                const void *u, void *Lu, int nrhs, int dtype, void *stream);
+
 /* Plan introspection (host values computed at plan time). */
 typedef struct {
     int dim, n, levels;        /* levels = L for n = 2^L, else -1 */

@@ -231,3 +231,30 @@ def nl_get_plan_info(plan: Plan) -> dict:
     return dict(dim=info.dim, n=info.n, levels=info.levels, max_radius=info.max_radius,
                 num_offsets=info.num_offsets, moments=info.moments, sigma=info.sigma,
                 poly=list(info.poly), device_bytes=int(info.device_bytes))
+
+
+def nl_apply_fast_noalloc(dim, n, delta, u, Lu, alpha=0.0, scale=1.0, normalize=True,
+                          self_term=NL_SELF_DISCRETE, nrhs=None, stream=None):
+    """The allocation-free fast apply (p = 1, C = 1).  `delta`: a float (constant horizon) or
+    a CUDA float64 tensor of n^dim horizons.  u, Lu: CUDA tensors.  Returns Lu."""
+    L = lib()
+    fn = L.nl_apply_fast_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    if isinstance(delta, (int, float)):
+        dconst, dptr = float(delta), None
+    else:
+        import torch
+        if not (delta.is_cuda and delta.dtype == torch.float64 and delta.is_contiguous()):
+            raise ValueError("delta field must be a contiguous CUDA float64 tensor")
+        dconst, dptr = 0.0, ctypes.c_void_p(delta.data_ptr())
+    if not (u.is_cuda and Lu.is_cuda and u.is_contiguous() and Lu.is_contiguous()):
+        raise ValueError("u and Lu must be contiguous CUDA tensors")
+    if nrhs is None:
+        nrhs = u.numel() // (n ** dim)
+    _check(fn(int(dim), int(n), dconst, dptr, float(alpha), float(scale), int(bool(normalize)),
+              int(self_term), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(Lu.data_ptr()),
+              int(nrhs), _dtype_code(u), _stream_ptr(stream)))
+    return Lu
