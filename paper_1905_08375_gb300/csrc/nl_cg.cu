@@ -1,24 +1,471 @@
-// nl_cg.cu -- conjugate gradients on -L x = f (placeholder until the solver lands).
+// nl_cg.cu -- preconditioned conjugate gradients on -L x = f, the Krylov use of the fast
+// matrix-vector product remarked in the paper's conclusion (Sec. 4).
+//
+// Precision: x, r, z, p and every inner product are FP64; the operator is applied in FP32
+// to an FP32 copy of p (written by the direction update), and its FP32 result enters the
+// FP64 updates.  When the recursive residual of every right-hand side is below the
+// tolerance, the true residual f + L x is recomputed with the FP64 operator; right-hand
+// sides that miss the tolerance restart from that true residual (defect correction), so
+// the reported residual is always the FP64 one.
+//
+// Execution: per right-hand side, NB blocks do grid-stride vector work and write one
+// partial sum each; the next kernel folds the NB partials in a fixed order (same value in
+// every block, deterministic).  One iteration is four launches (apply, dot, update,
+// direction); CHUNK iterations plus a convergence check are captured once into a CUDA
+// graph on a plan-owned stream.  The host reads the per-right-hand-side flags from pinned
+// memory after each chunk, with a bounded wait.
+#include <chrono>
+#include <cmath>
+#include <thread>
+
 #include "nl_internal.cuh"
+
+namespace {
+
+constexpr int RB = 256;     // threads per reduction block
+constexpr int NB = 152;     // reduction blocks per right-hand side (one per SM)
+constexpr int CHUNK = 16;   // iterations per captured graph
+
+// per right-hand side scalars
+enum { S_RZ = 0, S_FF, S_RR, S_CONV, S_IT, S_TRUE, S_COUNT = 8 };
+// partial-sum slots
+enum { P_PQ = 0, P_RZ, P_RR, P_AUX, P_COUNT };
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < RB / 32) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;   // valid in thread 0
+}
+
+// sum of the NB partials of (slot, rhs), fixed order; valid in every lane of warp 0
+__device__ __forceinline__ double fold(const double *part, int slot, int rhs, int nrhs)
+{
+    const double *q = part + ((size_t)slot * nrhs + rhs) * NB;
+    double s = 0.0;
+    for (int k = threadIdx.x & 31; k < NB; k += 32) s += q[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+struct CgArgs {
+    int64_t per;          // unknowns per right-hand side
+    int nrhs;
+    double tol;           // on the recursive relative residual
+    const double *f;
+    double *x, *r, *z, *p, *q64;
+    const double *dinv;   // [per]
+    float *p32, *q32;
+    double *part;         // [P_COUNT][nrhs][NB]
+    double *sc;           // [nrhs][S_COUNT]
+};
+
+__global__ void __launch_bounds__(RB) k_cg_init(CgArgs a)
+{
+    __shared__ double sh[RB / 32];
+    const int rhs = blockIdx.y;
+    const int64_t base = (int64_t)rhs * a.per;
+    double rz = 0.0, rr = 0.0, ff = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+        const double fv = a.f[base + k];
+        const double zv = a.dinv[k] * fv;
+        a.x[base + k] = 0.0;
+        a.r[base + k] = fv;
+        a.z[base + k] = zv;
+        a.p[base + k] = zv;
+        a.p32[base + k] = (float)zv;
+        rz += fv * zv;
+        rr += fv * fv;
+    }
+    ff = rr;
+    double s;
+    s = block_sum(rz, sh); if (threadIdx.x == 0) a.part[((size_t)P_RZ * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    s = block_sum(rr, sh); if (threadIdx.x == 0) a.part[((size_t)P_RR * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    s = block_sum(ff, sh); if (threadIdx.x == 0) a.part[((size_t)P_AUX * a.nrhs + rhs) * NB + blockIdx.x] = s;
+}
+
+__global__ void k_cg_init_scalars(CgArgs a)
+{
+    const int rhs = blockIdx.x;
+    if (threadIdx.x >= 32) return;
+    const double ff = fold(a.part, P_AUX, rhs, a.nrhs);
+    if (threadIdx.x == 0) {
+        double *sc = a.sc + (size_t)rhs * S_COUNT;
+        sc[S_FF] = ff;
+        sc[S_CONV] = (ff == 0.0) ? 1.0 : 0.0;
+        sc[S_IT] = 0.0;
+        sc[S_TRUE] = 0.0;
+    }
+}
+
+// Folds the r.z and r.r partials of the last update into rz_old and the convergence flag.
+// Idempotent: repeating it without an update in between changes nothing.
+__device__ __forceinline__ void scalars_after_update(const CgArgs &a, int rhs)
+{
+    const double rz = fold(a.part, P_RZ, rhs, a.nrhs);
+    const double rr = fold(a.part, P_RR, rhs, a.nrhs);
+    if (threadIdx.x == 0) {
+        double *sc = a.sc + (size_t)rhs * S_COUNT;
+        sc[S_RZ] = rz;
+        sc[S_RR] = rr;
+        if (sc[S_CONV] == 0.0 && rr <= a.tol * a.tol * sc[S_FF]) sc[S_CONV] = 1.0;
+    }
+}
+
+__global__ void k_cg_check(CgArgs a)
+{
+    if (threadIdx.x < 32) scalars_after_update(a, blockIdx.x);
+}
+
+// partial (p, A p) with A p = -q (q = L p in FP32)
+__global__ void __launch_bounds__(RB) k_cg_dot(CgArgs a)
+{
+    __shared__ double sh[RB / 32];
+    const int rhs = blockIdx.y;
+    if (blockIdx.x == 0 && threadIdx.x < 32) scalars_after_update(a, rhs);
+    const int64_t base = (int64_t)rhs * a.per;
+    double pq = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB)
+        pq -= a.p[base + k] * (double)a.q32[base + k];
+    const double s = block_sum(pq, sh);
+    if (threadIdx.x == 0) a.part[((size_t)P_PQ * a.nrhs + rhs) * NB + blockIdx.x] = s;
+}
+
+// x += alpha p, r -= alpha A p, z = D^{-1} r; partial r.z and r.r
+__global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
+{
+    __shared__ double sh[RB / 32];
+    __shared__ double s_alpha;
+    const int rhs = blockIdx.y;
+    const double *sc = a.sc + (size_t)rhs * S_COUNT;
+    if (threadIdx.x < 32) {
+        const double pq = fold(a.part, P_PQ, rhs, a.nrhs);
+        if (threadIdx.x == 0) {
+            const bool live = sc[S_CONV] == 0.0 && pq > 0.0 && sc[S_RZ] > 0.0;
+            s_alpha = live ? sc[S_RZ] / pq : 0.0;
+            if (live && blockIdx.x == 0) a.sc[(size_t)rhs * S_COUNT + S_IT] += 1.0;
+        }
+    }
+    __syncthreads();
+    const double alpha = s_alpha;
+    const int64_t base = (int64_t)rhs * a.per;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+        const int64_t g = base + k;
+        double rv = a.r[g];
+        if (alpha != 0.0) {
+            a.x[g] += alpha * a.p[g];
+            rv += alpha * (double)a.q32[g];
+            a.r[g] = rv;
+        }
+        const double zv = a.dinv[k] * rv;
+        a.z[g] = zv;
+        rz += rv * zv;
+        rr += rv * rv;
+    }
+    double s;
+    s = block_sum(rz, sh); if (threadIdx.x == 0) a.part[((size_t)P_RZ * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    s = block_sum(rr, sh); if (threadIdx.x == 0) a.part[((size_t)P_RR * a.nrhs + rhs) * NB + blockIdx.x] = s;
+}
+
+// p = z + beta p, p32 = (float) p
+__global__ void __launch_bounds__(RB) k_cg_dir(CgArgs a)
+{
+    __shared__ double s_beta;
+    const int rhs = blockIdx.y;
+    const double *sc = a.sc + (size_t)rhs * S_COUNT;
+    if (threadIdx.x < 32) {
+        const double rz_new = fold(a.part, P_RZ, rhs, a.nrhs);
+        if (threadIdx.x == 0) {
+            const double rz_old = sc[S_RZ];
+            s_beta = (sc[S_CONV] == 0.0 && rz_old > 0.0) ? rz_new / rz_old : 0.0;
+        }
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    const int64_t base = (int64_t)rhs * a.per;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+        const int64_t g = base + k;
+        const double pv = a.z[g] + beta * a.p[g];
+        a.p[g] = pv;
+        a.p32[g] = (float)pv;
+    }
+}
+
+// true residual f + L x (q64 = L x in FP64): partial ||.||^2 into P_AUX
+__global__ void __launch_bounds__(RB) k_cg_true(CgArgs a)
+{
+    __shared__ double sh[RB / 32];
+    const int rhs = blockIdx.y;
+    const int64_t base = (int64_t)rhs * a.per;
+    double ss = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+        const double t = a.f[base + k] + a.q64[base + k];
+        ss += t * t;
+    }
+    const double s = block_sum(ss, sh);
+    if (threadIdx.x == 0) a.part[((size_t)P_AUX * a.nrhs + rhs) * NB + blockIdx.x] = s;
+}
+
+__global__ void k_cg_true_scalars(CgArgs a)
+{
+    const int rhs = blockIdx.x;
+    if (threadIdx.x >= 32) return;
+    const double ss = fold(a.part, P_AUX, rhs, a.nrhs);
+    if (threadIdx.x == 0) {
+        double *sc = a.sc + (size_t)rhs * S_COUNT;
+        sc[S_TRUE] = sc[S_FF] > 0.0 ? sqrt(ss / sc[S_FF]) : 0.0;
+    }
+}
+
+// restart the right-hand sides whose true residual misses `goal`: r = f + L x, z, p
+__global__ void __launch_bounds__(RB) k_cg_restart(CgArgs a, double goal)
+{
+    __shared__ double sh[RB / 32];
+    const int rhs = blockIdx.y;
+    const double *sc = a.sc + (size_t)rhs * S_COUNT;
+    const bool redo = sc[S_TRUE] > goal;
+    const int64_t base = (int64_t)rhs * a.per;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+        const int64_t g = base + k;
+        double rv = a.r[g], zv = a.z[g];
+        if (redo) {
+            rv = a.f[g] + a.q64[g];
+            zv = a.dinv[k] * rv;
+            a.r[g] = rv;
+            a.z[g] = zv;
+            a.p[g] = zv;
+            a.p32[g] = (float)zv;
+        }
+        rz += rv * zv;
+        rr += rv * rv;
+    }
+    double s;
+    s = block_sum(rz, sh); if (threadIdx.x == 0) a.part[((size_t)P_RZ * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    s = block_sum(rr, sh); if (threadIdx.x == 0) a.part[((size_t)P_RR * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    __syncthreads();
+    if (redo && blockIdx.x == 0 && threadIdx.x == 0)
+        a.sc[(size_t)rhs * S_COUNT + S_CONV] = 0.0;
+}
+
+__global__ void k_invert(int64_t n, double *d, int have)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = have ? (d[i] > 0.0 ? 1.0 / d[i] : 1.0) : 1.0;
+}
+
+__global__ void k_zero(int64_t n, double *d)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = 0.0;
+}
+
+}  // namespace
 
 nl_status nl_cg_release(nl_plan *p)
 {
+    if (p->cg_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)p->cg_graph_exec);
     if (p->cg_ws) cudaFree(p->cg_ws);
     if (p->cg_ws32) cudaFree(p->cg_ws32);
     if (p->cg_red) cudaFree(p->cg_red);
     if (p->cg_host) cudaFreeHost(p->cg_host);
+    if (p->cg_ev) cudaEventDestroy(p->cg_ev);
+    if (p->cg_stream) cudaStreamDestroy(p->cg_stream);
+    p->cg_graph_exec = nullptr;
     p->cg_ws = nullptr; p->cg_ws32 = nullptr; p->cg_red = nullptr; p->cg_host = nullptr;
+    p->cg_ev = nullptr; p->cg_stream = nullptr;
+    p->cg_ws_elems = p->cg_ws32_elems = p->cg_red_elems = p->cg_host_elems = 0;
+    p->cg_graph_nrhs = 0;
+    return NL_OK;
+}
+
+static nl_status wait_bounded(nl_plan *p, double seconds)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(p->cg_ev);
+        if (e == cudaSuccess) return NL_OK;
+        if (e != cudaErrorNotReady) return nl_cuda_fail(e, "CG chunk");
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > seconds) {
+            nl_set_error("nl_cg_solve: a chunk of iterations did not finish within %.0f s", seconds);
+            return NL_ETIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+static nl_status ensure_workspace(nl_plan *p, int64_t len, int64_t per, int nrhs)
+{
+    const size_t need64 = (size_t)4 * len + per;   // r z p q64 | dinv
+    const size_t need32 = (size_t)2 * len;
+    const size_t needr = (size_t)P_COUNT * nrhs * NB + (size_t)S_COUNT * nrhs;
+    if (p->cg_ws_elems >= need64 && p->cg_ws32_elems >= need32 && p->cg_red_elems >= needr &&
+        p->cg_host_elems >= (size_t)S_COUNT * nrhs && p->cg_stream)
+        return NL_OK;
+    nl_cg_release(p);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->cg_ws, need64 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&p->cg_ws32, need32 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&p->cg_red, needr * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&p->cg_host, (size_t)S_COUNT * nrhs * sizeof(double))) != cudaSuccess) {
+        nl_cg_release(p);
+        nl_set_error("nl_cg_solve: workspace allocation failed: %s", cudaGetErrorString(e));
+        return NL_ENOMEM;
+    }
+    p->cg_ws_elems = need64; p->cg_ws32_elems = need32; p->cg_red_elems = needr;
+    p->cg_host_elems = (size_t)S_COUNT * nrhs;
+    NL_CUDA_TRY(cudaStreamCreateWithFlags(&p->cg_stream, cudaStreamNonBlocking));
+    NL_CUDA_TRY(cudaEventCreateWithFlags(&p->cg_ev, cudaEventDisableTiming));
+    return NL_OK;
+}
+
+static nl_status enqueue_chunk(nl_plan *p, const CgArgs &a, int iters, cudaStream_t st)
+{
+    const dim3 grid(NB, a.nrhs);
+    for (int it = 0; it < iters; ++it) {
+        nl_status s = nl_direct_launch(p, a.p32, a.q32, a.nrhs, NL_F32, st);
+        if (s != NL_OK) return s;
+        k_cg_dot<<<grid, RB, 0, st>>>(a);
+        k_cg_update<<<grid, RB, 0, st>>>(a);
+        k_cg_dir<<<grid, RB, 0, st>>>(a);
+    }
+    k_cg_check<<<a.nrhs, 32, 0, st>>>(a);
+    NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
 
 extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, double rtol,
                                  int maxit, int precond, nl_cg_stats *stats, void *stream)
 {
-    (void)f; (void)x; (void)nrhs; (void)rtol; (void)maxit; (void)precond; (void)stats; (void)stream;
     if (!nl_plan_ok(p)) {
         nl_set_error("nl_cg_solve: invalid plan");
         return NL_EINVAL;
     }
-    nl_set_error("nl_cg_solve: not built yet");
-    return NL_EUNSUPPORTED;
+    if (!f || !x || nrhs < 1 || nrhs > 65535 || !(rtol > 0.0) || maxit < 0 ||
+        (precond != NL_PRECOND_NONE && precond != NL_PRECOND_JACOBI)) {
+        nl_set_error("nl_cg_solve: bad argument");
+        return NL_EINVAL;
+    }
+    const bool pd = p->family == NL_PD_BOND;
+    if (!(p->symmetric || (pd && p->const_horizon))) {
+        nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER plan, or "
+                     "NL_PD_BOND with a constant horizon)");
+        return NL_EUNSUPPORTED;
+    }
+    const int64_t per = pd ? 2 * p->N : p->N;
+    const int64_t len = per * nrhs;
+    nl_status s = ensure_workspace(p, len, per, nrhs);
+    if (s != NL_OK) return s;
+    CgArgs a;
+    a.per = per; a.nrhs = nrhs;
+    a.tol = 0.5 * rtol;
+    a.f = (const double *)f; a.x = (double *)x;
+    a.r = p->cg_ws; a.z = a.r + len; a.p = a.z + len; a.q64 = a.p + len;
+    double *dinv = a.q64 + len;          // [per], after the four vectors
+    a.dinv = dinv;
+    a.p32 = p->cg_ws32; a.q32 = a.p32 + len;
+    a.part = p->cg_red; a.sc = p->cg_red + (size_t)P_COUNT * nrhs * NB;
+
+    cudaStream_t caller = nl_stream(stream), st = p->cg_stream;
+    NL_CUDA_TRY(cudaEventRecord(p->cg_ev, caller));
+    NL_CUDA_TRY(cudaStreamWaitEvent(st, p->cg_ev, 0));
+
+    const unsigned g1 = (unsigned)((per + 255) / 256);
+    k_zero<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(len, a.x);
+    if (precond == NL_PRECOND_JACOBI) {
+        s = nl_diag_launch(p, a.x, dinv, st);
+        if (s != NL_OK) return s;
+    }
+    k_invert<<<g1, 256, 0, st>>>(per, dinv, precond == NL_PRECOND_JACOBI);
+    const dim3 grid(NB, nrhs);
+    k_cg_init<<<grid, RB, 0, st>>>(a);
+    k_cg_init_scalars<<<nrhs, 32, 0, st>>>(a);
+    NL_CUDA_TRY(cudaGetLastError());
+    // one plain apply so that kernel attributes are set before capture
+    s = nl_direct_launch(p, a.p32, a.q32, nrhs, NL_F32, st);
+    if (s != NL_OK) return s;
+
+    // capture one chunk of iterations (the graph bakes in f, x, nrhs and the tolerance)
+    if (p->cg_graph_exec && (p->cg_graph_nrhs != nrhs || p->cg_graph_f != f ||
+                             p->cg_graph_x != x || p->cg_graph_tol != rtol)) {
+        cudaGraphExecDestroy((cudaGraphExec_t)p->cg_graph_exec);
+        p->cg_graph_exec = nullptr;
+    }
+    if (!p->cg_graph_exec) {
+        cudaGraph_t g = nullptr;
+        NL_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        nl_status cs = enqueue_chunk(p, a, CHUNK, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (cs != NL_OK) { if (g) cudaGraphDestroy(g); return cs; }
+        if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaStreamEndCapture");
+        cudaGraphExec_t ge = nullptr;
+        ce = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaGraphInstantiate");
+        p->cg_graph_exec = ge;
+        p->cg_graph_nrhs = nrhs;
+        p->cg_graph_f = f;
+        p->cg_graph_x = x;
+        p->cg_graph_tol = rtol;
+    }
+
+    double *h = p->cg_host;
+    int iters = 0, restarts = 0;
+    bool done = false, conv_all = false;
+    while (!done) {
+        NL_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)p->cg_graph_exec, st));
+        iters += CHUNK;
+        NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        NL_CUDA_TRY(cudaEventRecord(p->cg_ev, st));
+        if ((s = wait_bounded(p, 600.0)) != NL_OK) return s;
+        bool all = true;
+        for (int r = 0; r < nrhs; ++r) all = all && h[r * S_COUNT + S_CONV] != 0.0;
+        const bool out_of_budget = iters >= maxit;
+        if (!all && !out_of_budget) continue;
+        // true FP64 residual f + L x
+        s = nl_direct_launch(p, a.x, a.q64, nrhs, NL_F64, st);
+        if (s != NL_OK) return s;
+        k_cg_true<<<grid, RB, 0, st>>>(a);
+        k_cg_true_scalars<<<nrhs, 32, 0, st>>>(a);
+        NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        NL_CUDA_TRY(cudaEventRecord(p->cg_ev, st));
+        if ((s = wait_bounded(p, 600.0)) != NL_OK) return s;
+        double worst = 0.0;
+        for (int r = 0; r < nrhs; ++r) worst = fmax(worst, h[r * S_COUNT + S_TRUE]);
+        if (worst <= rtol) { conv_all = true; break; }
+        if (out_of_budget || restarts >= 50) break;
+        // defect correction: restart the right-hand sides that missed
+        k_cg_restart<<<grid, RB, 0, st>>>(a, rtol);
+        NL_CUDA_TRY(cudaGetLastError());
+        ++restarts;
+    }
+    NL_CUDA_TRY(cudaStreamSynchronize(st));
+    if (stats) {
+        int itmax = 0;
+        double worst = 0.0;
+        for (int r = 0; r < nrhs; ++r) {
+            itmax = (int)fmax((double)itmax, h[r * S_COUNT + S_IT]);
+            worst = fmax(worst, h[r * S_COUNT + S_TRUE]);
+        }
+        stats->iterations = itmax;
+        stats->rel_residual = worst;
+        stats->converged = conv_all ? 1 : 0;
+    }
+    if (!conv_all) {
+        nl_set_error("nl_cg_solve: not converged to %g within %d iterations", rtol, maxit);
+        return NL_ENOTCONV;
+    }
+    return NL_OK;
 }

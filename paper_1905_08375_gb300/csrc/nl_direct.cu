@@ -10,6 +10,8 @@
 // ragged per-node horizon costs nothing beyond its own ball.  Table entries
 // are warp-uniform (broadcast loads); tile reads are consecutive in x across a
 // warp (conflict-free).
+#include <mutex>
+
 #include "nl_internal.cuh"
 
 template <typename T> struct V2 { T u, b; };
@@ -67,7 +69,8 @@ __device__ __forceinline__ T poly_weight(const double *pc, int K, T t)
 // ---------------------------------------------------------------------------
 // scalar kernel
 // ---------------------------------------------------------------------------
-template <int D, typename T, int MODE, bool STAGE>
+// DIAG = true writes the diagonal of -L instead: fin_i (sum_o wgt(o) + ext_i).
+template <int D, typename T, int MODE, bool STAGE, bool DIAG = false>
 __global__ void __launch_bounds__(DirectBlock<D>::X * DirectBlock<D>::Y * DirectBlock<D>::Z)
 k_direct_scalar(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
 {
@@ -162,12 +165,15 @@ k_direct_scalar(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
             const T wj = (en.o2 <= thrj) ? whj : T(0);
             w = (T)en.g * bj * (wi + wj);
         }
-        const T term = w * (uj - ui);
+        const T term = DIAG ? w : w * (uj - ui);
         if (t & 1) acc1 += term; else acc0 += term;
     }
     const T fin = ((const T *)a.fin)[i];
     const T ext = ((const T *)a.ext)[i];
-    Lu[(int64_t)blockIdx.z * N + i] = fin * ((acc0 + acc1) - ui * ext);
+    if (DIAG)
+        Lu[(int64_t)blockIdx.z * N + i] = fin * ((acc0 + acc1) + ext);
+    else
+        Lu[(int64_t)blockIdx.z * N + i] = fin * ((acc0 + acc1) - ui * ext);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,7 +181,8 @@ k_direct_scalar(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
 // Lu = sigma h^{d-1} (acc/2 - E_i u_i), E_i = c_i sum_{exterior o} G(o).
 // FP32: FP32 products, FP32 partial sums over 32 bonds, FP64 running sum.
 // ---------------------------------------------------------------------------
-template <typename T, bool STAGE>
+// DIAG = true writes the per-component diagonal of -L_PD instead.
+template <typename T, bool STAGE, bool DIAG = false>
 __global__ void __launch_bounds__(256)
 k_direct_pd(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
 {
@@ -233,16 +240,27 @@ k_direct_pd(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
             }
         }
         const T w = ci * inj + cj;
-        const T dx = uxj - uxi, dy = uyj - uyi;
-        px += w * ((T)en.gxx * dx + (T)en.gxy * dy);
-        py += w * ((T)en.gxy * dx + (T)en.gyy * dy);
+        if (DIAG) {
+            px += w * (T)en.gxx;
+            py += w * (T)en.gyy;
+        } else {
+            const T dx = uxj - uxi, dy = uyj - uyi;
+            px += w * ((T)en.gxx * dx + (T)en.gxy * dy);
+            py += w * ((T)en.gxy * dx + (T)en.gyy * dy);
+        }
         if ((t & 31) == 31) { sx += (double)px; sy += (double)py; px = T(0); py = T(0); }
     }
     sx += (double)px;
     sy += (double)py;
     const double *E = a.pdext + 3 * i;
-    const double ox = a.pd_scale * (0.5 * sx - (E[0] * (double)uxi + E[1] * (double)uyi));
-    const double oy = a.pd_scale * (0.5 * sy - (E[1] * (double)uxi + E[2] * (double)uyi));
+    double ox, oy;
+    if (DIAG) {
+        ox = a.pd_scale * (0.5 * sx + E[0]);
+        oy = a.pd_scale * (0.5 * sy + E[2]);
+    } else {
+        ox = a.pd_scale * (0.5 * sx - (E[0] * (double)uxi + E[1] * (double)uyi));
+        oy = a.pd_scale * (0.5 * sy - (E[1] * (double)uxi + E[2] * (double)uyi));
+    }
     T *out = Lu + (int64_t)blockIdx.z * 2 * N;
     out[i] = (T)ox;
     out[N + i] = (T)oy;
@@ -251,11 +269,29 @@ k_direct_pd(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Raise a kernel's dynamic shared-memory limit once per (kernel, size): repeated calls
+// (and calls while a stream is being captured) then issue no runtime call at all.
+static std::mutex g_smem_mu;
+static const void *g_smem_fn[256];
+static size_t g_smem_bytes[256];
+static int g_smem_count = 0;
+
 template <typename K>
 static cudaError_t prep_smem(K kernel, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const void *key = (const void *)kernel;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    int slot = -1;
+    for (int k = 0; k < g_smem_count; ++k)
+        if (g_smem_fn[k] == key) { slot = k; break; }
+    if (slot >= 0 && g_smem_bytes[slot] >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (slot < 0 && g_smem_count < 256) { slot = g_smem_count++; g_smem_fn[slot] = key; }
+    if (slot >= 0) g_smem_bytes[slot] = bytes;
+    return e;
 }
 
 template <int D>
@@ -356,6 +392,50 @@ nl_status nl_direct_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dt
     if (dtype == NL_F32)
         return launch_scalar<float>(p, a, (const float *)u, (float *)Lu, nrhs, st, p->smem_bytes32);
     return launch_scalar<double>(p, a, (const double *)u, (double *)Lu, nrhs, st, p->smem_bytes64);
+}
+
+template <int D>
+static nl_status diag_scalar(nl_plan *p, const DirectArgs &a, const double *zin, double *diag,
+                             cudaStream_t st)
+{
+    const dim3 blk(DirectBlock<D>::X, DirectBlock<D>::Y, DirectBlock<D>::Z);
+    const dim3 grd = direct_grid<D>(p->n, 1);
+    if (p->stage) {
+        auto kern = k_direct_scalar<D, double, MODE_SYM, true, true>;
+        NL_CUDA_TRY(prep_smem(kern, p->smem_bytes64));
+        kern<<<grd, blk, p->smem_bytes64, st>>>(a, zin, diag);
+    } else {
+        k_direct_scalar<D, double, MODE_SYM, false, true><<<grd, blk, 0, st>>>(a, zin, diag);
+    }
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+// Diagonal of -L (FP64), for the Jacobi preconditioner: [N] scalar, [2][N] peridynamic.
+// `zin` is any readable input of the operator's length (its values are not used).
+nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st)
+{
+    const DirectArgs a = make_args(p, NL_F64);
+    if (p->family == NL_PD_BOND) {
+        const dim3 blk(DirectBlock<2>::X, DirectBlock<2>::Y, 1);
+        const dim3 grd = direct_grid<2>(p->n, 1);
+        if (p->stage) {
+            auto kern = k_direct_pd<double, true, true>;
+            NL_CUDA_TRY(prep_smem(kern, p->smem_bytes64));
+            kern<<<grd, blk, p->smem_bytes64, st>>>(a, zin, diag);
+        } else {
+            k_direct_pd<double, false, true><<<grd, blk, 0, st>>>(a, zin, diag);
+        }
+        NL_CUDA_TRY(cudaGetLastError());
+        return NL_OK;
+    }
+    if (!p->symmetric) {
+        nl_set_error("diagonal: built for the symmetric scalar operator and peridynamics");
+        return NL_EUNSUPPORTED;
+    }
+    if (p->d == 1) return diag_scalar<1>(p, a, zin, diag, st);
+    if (p->d == 2) return diag_scalar<2>(p, a, zin, diag, st);
+    return diag_scalar<3>(p, a, zin, diag, st);
 }
 
 extern "C" nl_status nl_apply(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,

@@ -40,6 +40,7 @@ struct nl_plan {
     double poly[8];
     // horizon summary
     int Rmax;               // max ceil(delta_i n)
+    int const_horizon;      // 1 if every node has the same horizon
     int thr_max;            // max over nodes of the largest integer |o|^2 inside the ball
     int num_off;            // table length (offsets with 0 < |o|^2 <= thr_sym_max)
     int stage;              // 1: direct kernels stage a halo tile in shared memory
@@ -69,11 +70,17 @@ struct nl_plan {
     double *shift;                  // Step 2 re-centring table [2^d][M][M]
     int *malpha;                    // multi-indices [M][3]
     int pyr_rhs;                    // right-hand sides the pyramid buffer holds
-    // CG workspace
+    // CG workspace (allocated on the first nl_cg_solve, grown for more right-hand sides)
     double *cg_ws; size_t cg_ws_elems;
     float *cg_ws32; size_t cg_ws32_elems;
-    double *cg_red; int cg_red_elems;
-    double *cg_host; int cg_host_elems;
+    double *cg_red; size_t cg_red_elems;
+    double *cg_host; size_t cg_host_elems;
+    cudaStream_t cg_stream;
+    cudaEvent_t cg_ev;
+    void *cg_graph_exec;            // cudaGraphExec_t of one chunk of iterations
+    int cg_graph_nrhs;
+    const void *cg_graph_f, *cg_graph_x;
+    double cg_graph_tol;
     size_t device_bytes;
 };
 
@@ -103,4 +110,5 @@ nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtyp
                          cudaStream_t st);
 nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
                             cudaStream_t st);
+nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st);
 nl_status nl_cg_release(nl_plan *p);

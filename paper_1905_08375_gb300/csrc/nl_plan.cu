@@ -377,6 +377,9 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     if (k->family == NL_POLY) hermite_poly(p->K, k->alpha, p->poly);
     p->Rmax = Rmax;
     p->thr_max = (int)thr_max;
+    p->const_horizon = 1;
+    for (int64_t i = 1; i < N; ++i)
+        if (delta[i] != delta[0]) { p->const_horizon = 0; break; }
 
     cudaStream_t st = nl_stream(stream);
 

@@ -1,0 +1,90 @@
+"""GPU conjugate gradients (nl_cg_solve) on -L x = f, judged by the FP64 oracle residual."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1905_08375_gb300 import binding as nl
+from paper_1905_08375_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def oracle_residual_scalar(x, f, n, fld):
+    Lx = oracle.direct_scalar(x, 2, n, fld["delta"], alpha=1.5, coef=oracle.COEF_XY, a=fld["a"],
+                              symmetric=True)
+    return np.linalg.norm(f + Lx, axis=-1) / np.linalg.norm(f, axis=-1)
+
+
+@pytest.mark.parametrize("n,nrhs", [(64, 1), (96, 3)])
+def test_scalar_symmetric_jacobi(n, nrhs):
+    fld = synth.heterogeneous_2d(n=n, seed=7)
+    f = synth.cg_rhs(n, seed=8, count=nrhs)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    ft = torch.tensor(f, dtype=torch.float64, device=DEV)
+    xt = torch.empty_like(ft)
+    st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000)
+    assert st["converged"] and st["rel_residual"] <= 1e-8, st
+    res = oracle_residual_scalar(xt.cpu().numpy(), f, n, fld)
+    assert np.all(res <= 1.01e-8), res
+    # same number of iterations as the oracle's FP64 Jacobi-PCG, up to the restarts
+    _, it_o, _ = oracle.cg(f[0], 2, n, fld["delta"], alpha=1.5, coef=oracle.COEF_XY, a=fld["a"],
+                           rtol=1e-8)
+    assert st["iterations"] <= 1.5 * it_o + 32, (st["iterations"], it_o)
+
+
+def test_unpreconditioned_and_not_converged():
+    n = 48
+    fld = synth.heterogeneous_2d(n=n, seed=9)
+    f = synth.cg_rhs(n, seed=10)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    ft = torch.tensor(f, dtype=torch.float64, device=DEV)
+    xt = torch.empty_like(ft)
+    st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000, precond=nl.NL_PRECOND_NONE)
+    assert st["converged"]
+    assert oracle_residual_scalar(xt.cpu().numpy(), f, n, fld)[0] <= 1.01e-8
+    st2 = nl.nl_cg_solve(plan, ft, xt, rtol=1e-12, maxit=16)
+    assert not st2["converged"] and st2["status"] == nl.NL_ENOTCONV
+
+
+def test_non_symmetric_plan_rejected():
+    n = 32
+    fld = synth.heterogeneous_2d(n=n, seed=11)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5)
+    ft = torch.ones(n * n, dtype=torch.float64, device=DEV)
+    with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
+        nl.nl_cg_solve(plan, ft, torch.empty_like(ft))
+
+
+def test_peridynamics_two_phase():
+    n = 40
+    fld = synth.pd_2d(n=n, seed=12, radius_cells=6)
+    rng = np.random.default_rng(13)
+    f = rng.standard_normal((2, 2, n * n))
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_PD_BOND, coef=nl.NL_COEF_MEAN,
+                             a=fld["c"])
+    ft = torch.tensor(f, dtype=torch.float64, device=DEV)
+    xt = torch.empty_like(ft)
+    st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000)
+    assert st["converged"], st
+    x = xt.cpu().numpy()
+    Lx = oracle.pd_direct(x, 2, n, fld["delta"], fld["c"])
+    res = np.linalg.norm((f + Lx).reshape(2, -1), axis=1) / np.linalg.norm(f.reshape(2, -1), axis=1)
+    assert np.all(res <= 1.01e-8), res
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_config4_sizes(n):
+    """Learned-preconditioner workload sizes, Jacobi-CG to 1e-8 with the FP64 oracle residual."""
+    fld = synth.heterogeneous_2d(n=n, seed=0)
+    f = synth.cg_rhs(n, seed=1)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    ft = torch.tensor(f, dtype=torch.float64, device=DEV)
+    xt = torch.empty_like(ft)
+    st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=50000)
+    assert st["converged"] and st["rel_residual"] <= 1e-8, st
+    assert oracle_residual_scalar(xt.cpu().numpy(), f, n, fld)[0] <= 1.01e-8
