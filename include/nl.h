@@ -152,7 +152,9 @@ typedef struct {
     int converged;        /* 1 if every right-hand side met rtol */
 } nl_cg_stats;
 
-typedef enum { NL_PRECOND_NONE = 0, NL_PRECOND_JACOBI = 1 } nl_precond;
+/* NL_PRECOND_LEARNED: the network attached with nl_plan_set_net (flexible CG, since the
+ * network is nonlinear); it builds on the Jacobi scaling, which stays the fallback. */
+typedef enum { NL_PRECOND_NONE = 0, NL_PRECOND_JACOBI = 1, NL_PRECOND_LEARNED = 2 } nl_precond;
 
 /*
  * Preconditioned conjugate gradients for -L x = f with the plan's operator
@@ -195,6 +197,56 @@ nl_status nl_cg_solve(nl_plan *plan, const void *f, void *x, int nrhs, double rt
 nl_status nl_apply_fast_noalloc(int dim, int n, double delta, const double *delta_field,
                                 double alpha, double scale, int normalize, int self_term,
                                 const void *u, void *Lu, int nrhs, int dtype, void *stream);
+
+/*
+ * Learned CG preconditioner (a project addition; the paper only remarks, in its conclusion,
+ * that the fast product can serve a Krylov method).  For the symmetric 2-D scalar operator:
+ *     x = D^{-1} r / s, s = RMS(D^{-1} r) per right-hand side (D = diagonal of -L)
+ *     y1 = relu(conv1 x), y2 = relu(conv2 y1), o = conv3 y2, M(r) = s (x + o)
+ * with 3x3 convolutions (zero padding, no bias) of 1 -> 32 -> 32 -> 1 channels.  Weights are
+ * FP32 masters used as bfloat16; activations and sums are FP32.
+ * Weight layout (NL_NET_PARAMS floats): conv1 [32][1][3][3], conv2 [32][32][3][3],
+ * conv3 [1][32][3][3], concatenated, each [out][in][ky][kx].
+ */
+#define NL_NET_PARAMS 9792
+typedef struct nl_net nl_net;
+
+/* Create a network from HOST weights (copied).  Synchronises `stream`. */
+nl_status nl_net_create(nl_net **out, const float *weights, void *stream);
+nl_status nl_net_destroy(nl_net *net);
+/* Copy the FP32 master weights to HOST memory (synchronises `stream`). */
+nl_status nl_net_get_weights(nl_net *net, float *weights, void *stream);
+/* Copy the last training step's gradient (FP32, weight layout) to HOST memory. */
+nl_status nl_net_gradient(nl_net *net, float *grad, void *stream);
+/* o = conv3(relu(conv2(relu(conv1 x)))) on DEVICE x, o: [batch][H][W] FP32. */
+nl_status nl_net_forward(nl_net *net, const float *x, float *o, int batch, int H, int W, void *stream);
+/*
+ * One Adam step (beta 0.9/0.999, eps 1e-8, learning rate lr) on `batch` crops of S x S
+ * gathered from DEVICE fields x, e ([nfields][n][n] FP32) at DEVICE offsets
+ * crops[batch][3] = (field, y0, x0) (a crop outside the fields reads zeros).
+ * Loss per crop over the interior (margin pixels dropped): sum (x + o - e)^2 / sum e^2,
+ * averaged over the batch; written to *loss (HOST, may be NULL: then no synchronisation).
+ */
+nl_status nl_net_train_step(nl_net *net, const float *x, const float *e, int nfields, int n,
+                            const int *crops, int batch, int S, int margin, float lr, float *loss,
+                            void *stream);
+/* Training pairs from CG iterates: DEVICE r, e [count][n^2] FP64 (residual f + L x_k and
+ * error x* - x_k) -> x_out = D^{-1} r / s, e_out = e / s (FP32), s = RMS(D^{-1} r) per field. */
+nl_status nl_net_prepare_pairs(nl_plan *plan, const double *r, const double *e, int count,
+                               float *x_out, float *e_out, void *stream);
+/* z = M(r) on DEVICE FP64 [nrhs][n^2]. */
+nl_status nl_net_apply(nl_net *net, nl_plan *plan, const double *r, double *z, int nrhs, void *stream);
+/* Attach (or detach with NULL) the network used by nl_cg_solve with NL_PRECOND_LEARNED. */
+nl_status nl_plan_set_net(nl_plan *plan, nl_net *net);
+
+/*
+ * nl_cg_solve for one right-hand side that also records the iterate x after every
+ * `chunk` iterations (chunk = 16) into DEVICE history[cap][n^d] (FP64); *count receives the
+ * number of snapshots written.  Used to build the network's training pairs.
+ */
+nl_status nl_cg_history(nl_plan *plan, const void *f, void *x, double rtol, int maxit,
+                        int precond, double *history, int cap, int *count, nl_cg_stats *stats,
+                        void *stream);
 
 /* Plan introspection (host values computed at plan time). */
 typedef struct {

@@ -258,3 +258,138 @@ def nl_apply_fast_noalloc(dim, n, delta, u, Lu, alpha=0.0, scale=1.0, normalize=
               int(self_term), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(Lu.data_ptr()),
               int(nrhs), _dtype_code(u), _stream_ptr(stream)))
     return Lu
+
+
+# ---------------------------------------------------------------------------
+# learned CG preconditioner
+# ---------------------------------------------------------------------------
+NL_PRECOND_LEARNED = 2
+NL_NET_PARAMS = 9792
+
+
+def _net_fns():
+    L = lib()
+    if getattr(L, "_net_ready", False):
+        return L
+    vp, i, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    L.nl_net_create.restype = i
+    L.nl_net_create.argtypes = [ctypes.POINTER(vp), vp, vp]
+    L.nl_net_destroy.restype = i
+    L.nl_net_destroy.argtypes = [vp]
+    L.nl_net_get_weights.restype = i
+    L.nl_net_get_weights.argtypes = [vp, vp, vp]
+    L.nl_net_gradient.restype = i
+    L.nl_net_gradient.argtypes = [vp, vp, vp]
+    L.nl_net_forward.restype = i
+    L.nl_net_forward.argtypes = [vp, vp, vp, i, i, i, vp]
+    L.nl_net_train_step.restype = i
+    L.nl_net_train_step.argtypes = [vp, vp, vp, i, i, vp, i, i, i, f, ctypes.POINTER(f), vp]
+    L.nl_net_prepare_pairs.restype = i
+    L.nl_net_prepare_pairs.argtypes = [vp, vp, vp, i, vp, vp, vp]
+    L.nl_net_apply.restype = i
+    L.nl_net_apply.argtypes = [vp, vp, vp, vp, i, vp]
+    L.nl_plan_set_net.restype = i
+    L.nl_plan_set_net.argtypes = [vp, vp]
+    L.nl_cg_history.restype = i
+    L.nl_cg_history.argtypes = [vp, vp, vp, ctypes.c_double, i, i, vp, i,
+                                ctypes.POINTER(i), ctypes.POINTER(nl_cg_stats), vp]
+    L._net_ready = True
+    return L
+
+
+class Net:
+    """Owns an ``nl_net*``."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _net_fns().nl_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nl_net_create(weights, stream=None) -> Net:
+    w = np.ascontiguousarray(weights, dtype=np.float32).reshape(-1)
+    if w.size != NL_NET_PARAMS:
+        raise ValueError(f"need {NL_NET_PARAMS} weights")
+    h = ctypes.c_void_p()
+    _check(_net_fns().nl_net_create(ctypes.byref(h), w.ctypes.data, _stream_ptr(stream)))
+    return Net(h)
+
+
+def nl_net_get_weights(net: Net, stream=None) -> np.ndarray:
+    w = np.zeros(NL_NET_PARAMS, dtype=np.float32)
+    _check(_net_fns().nl_net_get_weights(net.handle, w.ctypes.data, _stream_ptr(stream)))
+    return w
+
+
+def nl_net_gradient(net: Net, stream=None) -> np.ndarray:
+    g = np.zeros(NL_NET_PARAMS, dtype=np.float32)
+    _check(_net_fns().nl_net_gradient(net.handle, g.ctypes.data, _stream_ptr(stream)))
+    return g
+
+
+def nl_net_forward(net: Net, x, o, stream=None):
+    """x, o: CUDA float32 [batch, H, W]."""
+    B, H, W = x.shape
+    _check(_net_fns().nl_net_forward(net.handle, ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(o.data_ptr()), B, H, W,
+                                     _stream_ptr(stream)))
+    return o
+
+
+def nl_net_train_step(net: Net, x, e, crops, S, margin, lr, want_loss=True, stream=None):
+    """x, e: CUDA float32 [nfields, n, n]; crops: CUDA int32 [batch, 3].  Returns the loss."""
+    nf, n, _ = x.shape
+    loss = ctypes.c_float(0.0)
+    _check(_net_fns().nl_net_train_step(net.handle, ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(e.data_ptr()), nf, n,
+                                        ctypes.c_void_p(crops.data_ptr()), crops.shape[0], S,
+                                        margin, float(lr),
+                                        ctypes.byref(loss) if want_loss else None,
+                                        _stream_ptr(stream)))
+    return float(loss.value) if want_loss else None
+
+
+def nl_net_prepare_pairs(plan: Plan, r, e, xo, eo, stream=None):
+    """r, e: CUDA float64 [count, N]; xo, eo: CUDA float32 [count, N]."""
+    _check(_net_fns().nl_net_prepare_pairs(plan.handle, ctypes.c_void_p(r.data_ptr()),
+                                           ctypes.c_void_p(e.data_ptr()), r.shape[0],
+                                           ctypes.c_void_p(xo.data_ptr()),
+                                           ctypes.c_void_p(eo.data_ptr()), _stream_ptr(stream)))
+
+
+def nl_net_apply(net: Net, plan: Plan, r, z, nrhs=None, stream=None):
+    if nrhs is None:
+        nrhs = r.numel() // plan.N
+    _check(_net_fns().nl_net_apply(net.handle, plan.handle, ctypes.c_void_p(r.data_ptr()),
+                                   ctypes.c_void_p(z.data_ptr()), int(nrhs), _stream_ptr(stream)))
+    return z
+
+
+def nl_plan_set_net(plan: Plan, net):
+    _check(_net_fns().nl_plan_set_net(plan.handle, net.handle if net is not None else None))
+    plan._net = net      # keep the network alive while attached
+
+
+def nl_cg_history(plan: Plan, f, x, history, rtol=1e-8, maxit=10000,
+                  precond=NL_PRECOND_JACOBI, stream=None):
+    """CG for one right-hand side recording x every 16 iterations into history [cap, N]."""
+    cnt = ctypes.c_int(0)
+    st = nl_cg_stats()
+    status = _net_fns().nl_cg_history(plan.handle, ctypes.c_void_p(f.data_ptr()),
+                                      ctypes.c_void_p(x.data_ptr()), float(rtol), int(maxit),
+                                      int(precond), ctypes.c_void_p(history.data_ptr()),
+                                      history.shape[0], ctypes.byref(cnt), ctypes.byref(st),
+                                      _stream_ptr(stream))
+    if status not in (NL_OK, NL_ENOTCONV):
+        _check(status)
+    return cnt.value, dict(iterations=st.iterations, rel_residual=st.rel_residual,
+                           converged=bool(st.converged), status=status)

@@ -68,28 +68,35 @@ struct CgArgs {
     double *sc;           // [nrhs][S_COUNT]
 };
 
+__device__ __forceinline__ void store_partial(const CgArgs &a, int slot, int rhs, double v)
+{
+    a.part[((size_t)slot * a.nrhs + rhs) * NB + blockIdx.x] = v;
+}
+
+// r = f, x = 0; z = D^{-1} r and p = z unless FLEX (the network computes z afterwards)
+template <bool FLEX>
 __global__ void __launch_bounds__(RB) k_cg_init(CgArgs a)
 {
     __shared__ double sh[RB / 32];
     const int rhs = blockIdx.y;
     const int64_t base = (int64_t)rhs * a.per;
-    double rz = 0.0, rr = 0.0, ff = 0.0;
+    double rz = 0.0, rr = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
         const double fv = a.f[base + k];
-        const double zv = a.dinv[k] * fv;
         a.x[base + k] = 0.0;
         a.r[base + k] = fv;
-        a.z[base + k] = zv;
-        a.p[base + k] = zv;
-        a.p32[base + k] = (float)zv;
-        rz += fv * zv;
+        if (!FLEX) {
+            const double zv = a.dinv[k] * fv;
+            a.z[base + k] = zv;
+            a.p[base + k] = zv;
+            a.p32[base + k] = (float)zv;
+            rz += fv * zv;
+        }
         rr += fv * fv;
     }
-    ff = rr;
     double s;
-    s = block_sum(rz, sh); if (threadIdx.x == 0) a.part[((size_t)P_RZ * a.nrhs + rhs) * NB + blockIdx.x] = s;
-    s = block_sum(rr, sh); if (threadIdx.x == 0) a.part[((size_t)P_RR * a.nrhs + rhs) * NB + blockIdx.x] = s;
-    s = block_sum(ff, sh); if (threadIdx.x == 0) a.part[((size_t)P_AUX * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    s = block_sum(rz, sh); if (threadIdx.x == 0) store_partial(a, P_RZ, rhs, s);
+    s = block_sum(rr, sh); if (threadIdx.x == 0) { store_partial(a, P_RR, rhs, s); store_partial(a, P_AUX, rhs, s); }
 }
 
 __global__ void k_cg_init_scalars(CgArgs a)
@@ -104,6 +111,28 @@ __global__ void k_cg_init_scalars(CgArgs a)
         sc[S_IT] = 0.0;
         sc[S_TRUE] = 0.0;
     }
+}
+
+// FLEX: after the network wrote z = M(r): for right-hand sides selected by `only`
+// (all when only < 0; else those with sc[S_TRUE] > goal) set p = z; partial r.z
+__global__ void __launch_bounds__(RB) k_cg_pz(CgArgs a, int only, double goal)
+{
+    __shared__ double sh[RB / 32];
+    const int rhs = blockIdx.y;
+    const bool redo = only < 0 || a.sc[(size_t)rhs * S_COUNT + S_TRUE] > goal;
+    const int64_t base = (int64_t)rhs * a.per;
+    double rz = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+        const int64_t g = base + k;
+        const double zv = a.z[g];
+        if (redo) {
+            a.p[g] = zv;
+            a.p32[g] = (float)zv;
+        }
+        rz += a.r[g] * zv;
+    }
+    const double s = block_sum(rz, sh);
+    if (threadIdx.x == 0) store_partial(a, P_RZ, rhs, s);
 }
 
 // Folds the r.z and r.r partials of the last update into rz_old and the convergence flag.
@@ -136,10 +165,12 @@ __global__ void __launch_bounds__(RB) k_cg_dot(CgArgs a)
     for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB)
         pq -= a.p[base + k] * (double)a.q32[base + k];
     const double s = block_sum(pq, sh);
-    if (threadIdx.x == 0) a.part[((size_t)P_PQ * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    if (threadIdx.x == 0) store_partial(a, P_PQ, rhs, s);
 }
 
-// x += alpha p, r -= alpha A p, z = D^{-1} r; partial r.z and r.r
+// x += alpha p, r -= alpha A p; then z = D^{-1} r with partial r.z, or (FLEX) partial
+// r_new . z_old for the flexible beta; partial r.r either way
+template <bool FLEX>
 __global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
 {
     __shared__ double sh[RB / 32];
@@ -166,17 +197,36 @@ __global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
             rv += alpha * (double)a.q32[g];
             a.r[g] = rv;
         }
-        const double zv = a.dinv[k] * rv;
-        a.z[g] = zv;
-        rz += rv * zv;
+        if (FLEX) {
+            rz += rv * a.z[g];
+        } else {
+            const double zv = a.dinv[k] * rv;
+            a.z[g] = zv;
+            rz += rv * zv;
+        }
         rr += rv * rv;
     }
     double s;
-    s = block_sum(rz, sh); if (threadIdx.x == 0) a.part[((size_t)P_RZ * a.nrhs + rhs) * NB + blockIdx.x] = s;
-    s = block_sum(rr, sh); if (threadIdx.x == 0) a.part[((size_t)P_RR * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    s = block_sum(rz, sh); if (threadIdx.x == 0) store_partial(a, FLEX ? P_AUX : P_RZ, rhs, s);
+    s = block_sum(rr, sh); if (threadIdx.x == 0) store_partial(a, P_RR, rhs, s);
 }
 
-// p = z + beta p, p32 = (float) p
+// FLEX: partial r.z after the network wrote the new z
+__global__ void __launch_bounds__(RB) k_cg_rz(CgArgs a)
+{
+    __shared__ double sh[RB / 32];
+    const int rhs = blockIdx.y;
+    const int64_t base = (int64_t)rhs * a.per;
+    double rz = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB)
+        rz += a.r[base + k] * a.z[base + k];
+    const double s = block_sum(rz, sh);
+    if (threadIdx.x == 0) store_partial(a, P_RZ, rhs, s);
+}
+
+// p = z + beta p, p32 = (float) p.  beta = r+.z+ / r.z, or for the flexible method
+// (r+.z+ - r+.z) / r.z (Polak-Ribiere form, exact for a fixed linear preconditioner)
+template <bool FLEX>
 __global__ void __launch_bounds__(RB) k_cg_dir(CgArgs a)
 {
     __shared__ double s_beta;
@@ -184,9 +234,10 @@ __global__ void __launch_bounds__(RB) k_cg_dir(CgArgs a)
     const double *sc = a.sc + (size_t)rhs * S_COUNT;
     if (threadIdx.x < 32) {
         const double rz_new = fold(a.part, P_RZ, rhs, a.nrhs);
+        const double rz_mix = FLEX ? fold(a.part, P_AUX, rhs, a.nrhs) : 0.0;
         if (threadIdx.x == 0) {
             const double rz_old = sc[S_RZ];
-            s_beta = (sc[S_CONV] == 0.0 && rz_old > 0.0) ? rz_new / rz_old : 0.0;
+            s_beta = (sc[S_CONV] == 0.0 && rz_old > 0.0) ? (rz_new - rz_mix) / rz_old : 0.0;
         }
     }
     __syncthreads();
@@ -212,7 +263,7 @@ __global__ void __launch_bounds__(RB) k_cg_true(CgArgs a)
         ss += t * t;
     }
     const double s = block_sum(ss, sh);
-    if (threadIdx.x == 0) a.part[((size_t)P_AUX * a.nrhs + rhs) * NB + blockIdx.x] = s;
+    if (threadIdx.x == 0) store_partial(a, P_AUX, rhs, s);
 }
 
 __global__ void k_cg_true_scalars(CgArgs a)
@@ -226,7 +277,9 @@ __global__ void k_cg_true_scalars(CgArgs a)
     }
 }
 
-// restart the right-hand sides whose true residual misses `goal`: r = f + L x, z, p
+// restart the right-hand sides whose true residual misses `goal`: r = f + L x and, unless
+// FLEX (the network then recomputes z and k_cg_pz resets p), z = D^{-1} r, p = z
+template <bool FLEX>
 __global__ void __launch_bounds__(RB) k_cg_restart(CgArgs a, double goal)
 {
     __shared__ double sh[RB / 32];
@@ -237,22 +290,26 @@ __global__ void __launch_bounds__(RB) k_cg_restart(CgArgs a, double goal)
     double rz = 0.0, rr = 0.0;
     for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
         const int64_t g = base + k;
-        double rv = a.r[g], zv = a.z[g];
+        double rv = a.r[g];
         if (redo) {
             rv = a.f[g] + a.q64[g];
-            zv = a.dinv[k] * rv;
             a.r[g] = rv;
-            a.z[g] = zv;
-            a.p[g] = zv;
-            a.p32[g] = (float)zv;
         }
-        rz += rv * zv;
+        if (!FLEX) {
+            double zv = a.z[g];
+            if (redo) {
+                zv = a.dinv[k] * rv;
+                a.z[g] = zv;
+                a.p[g] = zv;
+                a.p32[g] = (float)zv;
+            }
+            rz += rv * zv;
+        }
         rr += rv * rv;
     }
     double s;
-    s = block_sum(rz, sh); if (threadIdx.x == 0) a.part[((size_t)P_RZ * a.nrhs + rhs) * NB + blockIdx.x] = s;
-    s = block_sum(rr, sh); if (threadIdx.x == 0) a.part[((size_t)P_RR * a.nrhs + rhs) * NB + blockIdx.x] = s;
-    __syncthreads();
+    s = block_sum(rz, sh); if (threadIdx.x == 0 && !FLEX) store_partial(a, P_RZ, rhs, s);
+    s = block_sum(rr, sh); if (threadIdx.x == 0) store_partial(a, P_RR, rhs, s);
     if (redo && blockIdx.x == 0 && threadIdx.x == 0)
         a.sc[(size_t)rhs * S_COUNT + S_CONV] = 0.0;
 }
@@ -270,6 +327,11 @@ __global__ void k_zero(int64_t n, double *d)
 }
 
 }  // namespace
+
+void nl_invert_launch(int64_t n, double *d, cudaStream_t st)
+{
+    k_invert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d, 1);
+}
 
 nl_status nl_cg_release(nl_plan *p)
 {
@@ -329,30 +391,40 @@ static nl_status ensure_workspace(nl_plan *p, int64_t len, int64_t per, int nrhs
     return NL_OK;
 }
 
-static nl_status enqueue_chunk(nl_plan *p, const CgArgs &a, int iters, cudaStream_t st)
+static nl_status enqueue_chunk(nl_plan *p, const CgArgs &a, bool flex, int iters, cudaStream_t st)
 {
     const dim3 grid(NB, a.nrhs);
     for (int it = 0; it < iters; ++it) {
         nl_status s = nl_direct_launch(p, a.p32, a.q32, a.nrhs, NL_F32, st);
         if (s != NL_OK) return s;
         k_cg_dot<<<grid, RB, 0, st>>>(a);
-        k_cg_update<<<grid, RB, 0, st>>>(a);
-        k_cg_dir<<<grid, RB, 0, st>>>(a);
+        if (flex) {
+            k_cg_update<true><<<grid, RB, 0, st>>>(a);
+            s = nl_net_apply_launch(p->net, p, a.r, a.z, a.nrhs, st);
+            if (s != NL_OK) return s;
+            k_cg_rz<<<grid, RB, 0, st>>>(a);
+            k_cg_dir<true><<<grid, RB, 0, st>>>(a);
+        } else {
+            k_cg_update<false><<<grid, RB, 0, st>>>(a);
+            k_cg_dir<false><<<grid, RB, 0, st>>>(a);
+        }
     }
     k_cg_check<<<a.nrhs, 32, 0, st>>>(a);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
 
-extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, double rtol,
-                                 int maxit, int precond, nl_cg_stats *stats, void *stream)
+// The solver shared by nl_cg_solve and nl_cg_history.
+static nl_status cg_run(nl_plan *p, const void *f, void *x, int nrhs, double rtol, int maxit,
+                        int precond, double *hist, int cap, int *count, nl_cg_stats *stats,
+                        void *stream)
 {
     if (!nl_plan_ok(p)) {
         nl_set_error("nl_cg_solve: invalid plan");
         return NL_EINVAL;
     }
     if (!f || !x || nrhs < 1 || nrhs > 65535 || !(rtol > 0.0) || maxit < 0 ||
-        (precond != NL_PRECOND_NONE && precond != NL_PRECOND_JACOBI)) {
+        precond < NL_PRECOND_NONE || precond > NL_PRECOND_LEARNED) {
         nl_set_error("nl_cg_solve: bad argument");
         return NL_EINVAL;
     }
@@ -360,6 +432,12 @@ extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, d
     if (!(p->symmetric || (pd && p->const_horizon))) {
         nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER plan, or "
                      "NL_PD_BOND with a constant horizon)");
+        return NL_EUNSUPPORTED;
+    }
+    const bool flex = precond == NL_PRECOND_LEARNED;
+    if (flex && (!nl_net_valid(p->net) || pd || p->d != 2)) {
+        nl_set_error("nl_cg_solve: NL_PRECOND_LEARNED needs a network attached with "
+                     "nl_plan_set_net on a symmetric 2-D scalar plan");
         return NL_EUNSUPPORTED;
     }
     const int64_t per = pd ? 2 * p->N : p->N;
@@ -382,29 +460,39 @@ extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, d
 
     const unsigned g1 = (unsigned)((per + 255) / 256);
     k_zero<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(len, a.x);
-    if (precond == NL_PRECOND_JACOBI) {
+    if (precond != NL_PRECOND_NONE) {
         s = nl_diag_launch(p, a.x, dinv, st);
         if (s != NL_OK) return s;
     }
-    k_invert<<<g1, 256, 0, st>>>(per, dinv, precond == NL_PRECOND_JACOBI);
+    k_invert<<<g1, 256, 0, st>>>(per, dinv, precond != NL_PRECOND_NONE);
+    if (flex && (s = nl_net_reserve(p->net, p, nrhs, st)) != NL_OK) return s;
     const dim3 grid(NB, nrhs);
-    k_cg_init<<<grid, RB, 0, st>>>(a);
-    k_cg_init_scalars<<<nrhs, 32, 0, st>>>(a);
+    if (flex) {
+        k_cg_init<true><<<grid, RB, 0, st>>>(a);
+        k_cg_init_scalars<<<nrhs, 32, 0, st>>>(a);
+        if ((s = nl_net_apply_launch(p->net, p, a.r, a.z, nrhs, st)) != NL_OK) return s;
+        k_cg_pz<<<grid, RB, 0, st>>>(a, -1, 0.0);
+    } else {
+        k_cg_init<false><<<grid, RB, 0, st>>>(a);
+        k_cg_init_scalars<<<nrhs, 32, 0, st>>>(a);
+    }
     NL_CUDA_TRY(cudaGetLastError());
     // one plain apply so that kernel attributes are set before capture
     s = nl_direct_launch(p, a.p32, a.q32, nrhs, NL_F32, st);
     if (s != NL_OK) return s;
 
-    // capture one chunk of iterations (the graph bakes in f, x, nrhs and the tolerance)
+    // capture one chunk of iterations (the graph bakes in f, x, nrhs, the tolerance and the
+    // preconditioner)
     if (p->cg_graph_exec && (p->cg_graph_nrhs != nrhs || p->cg_graph_f != f ||
-                             p->cg_graph_x != x || p->cg_graph_tol != rtol)) {
+                             p->cg_graph_x != x || p->cg_graph_tol != rtol ||
+                             p->cg_graph_precond != precond)) {
         cudaGraphExecDestroy((cudaGraphExec_t)p->cg_graph_exec);
         p->cg_graph_exec = nullptr;
     }
     if (!p->cg_graph_exec) {
         cudaGraph_t g = nullptr;
         NL_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        nl_status cs = enqueue_chunk(p, a, CHUNK, st);
+        nl_status cs = enqueue_chunk(p, a, flex, CHUNK, st);
         cudaError_t ce = cudaStreamEndCapture(st, &g);
         if (cs != NL_OK) { if (g) cudaGraphDestroy(g); return cs; }
         if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaStreamEndCapture");
@@ -417,14 +505,20 @@ extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, d
         p->cg_graph_f = f;
         p->cg_graph_x = x;
         p->cg_graph_tol = rtol;
+        p->cg_graph_precond = precond;
     }
 
     double *h = p->cg_host;
-    int iters = 0, restarts = 0;
-    bool done = false, conv_all = false;
-    while (!done) {
+    int iters = 0, restarts = 0, snaps = 0;
+    bool conv_all = false;
+    for (;;) {
         NL_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)p->cg_graph_exec, st));
         iters += CHUNK;
+        if (hist && snaps < cap) {
+            NL_CUDA_TRY(cudaMemcpyAsync(hist + (size_t)snaps * per, a.x, per * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+            ++snaps;
+        }
         NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
         NL_CUDA_TRY(cudaEventRecord(p->cg_ev, st));
@@ -447,11 +541,18 @@ extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, d
         if (worst <= rtol) { conv_all = true; break; }
         if (out_of_budget || restarts >= 50) break;
         // defect correction: restart the right-hand sides that missed
-        k_cg_restart<<<grid, RB, 0, st>>>(a, rtol);
+        if (flex) {
+            k_cg_restart<true><<<grid, RB, 0, st>>>(a, rtol);
+            if ((s = nl_net_apply_launch(p->net, p, a.r, a.z, nrhs, st)) != NL_OK) return s;
+            k_cg_pz<<<grid, RB, 0, st>>>(a, 1, rtol);
+        } else {
+            k_cg_restart<false><<<grid, RB, 0, st>>>(a, rtol);
+        }
         NL_CUDA_TRY(cudaGetLastError());
         ++restarts;
     }
     NL_CUDA_TRY(cudaStreamSynchronize(st));
+    if (count) *count = snaps;
     if (stats) {
         int itmax = 0;
         double worst = 0.0;
@@ -468,4 +569,21 @@ extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, d
         return NL_ENOTCONV;
     }
     return NL_OK;
+}
+
+extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, double rtol,
+                                 int maxit, int precond, nl_cg_stats *stats, void *stream)
+{
+    return cg_run(p, f, x, nrhs, rtol, maxit, precond, nullptr, 0, nullptr, stats, stream);
+}
+
+extern "C" nl_status nl_cg_history(nl_plan *p, const void *f, void *x, double rtol, int maxit,
+                                   int precond, double *history, int cap, int *count,
+                                   nl_cg_stats *stats, void *stream)
+{
+    if (!history || cap < 1) {
+        nl_set_error("nl_cg_history: need a history buffer with cap >= 1");
+        return NL_EINVAL;
+    }
+    return cg_run(p, f, x, 1, rtol, maxit, precond, history, cap, count, stats, stream);
 }

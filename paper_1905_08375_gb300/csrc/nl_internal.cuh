@@ -81,6 +81,9 @@ struct nl_plan {
     int cg_graph_nrhs;
     const void *cg_graph_f, *cg_graph_x;
     double cg_graph_tol;
+    int cg_graph_precond;
+    double *dinv64;                 // inverse Jacobi diagonal (computed on first use)
+    nl_net *net;                    // learned preconditioner (not owned)
     size_t device_bytes;
 };
 
@@ -112,3 +115,8 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
                             cudaStream_t st);
 nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st);
 nl_status nl_cg_release(nl_plan *p);
+void nl_invert_launch(int64_t n, double *d, cudaStream_t st);
+nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,
+                              cudaStream_t st);
+nl_status nl_net_reserve(nl_net *n, nl_plan *p, int nrhs, cudaStream_t st);
+bool nl_net_valid(const nl_net *n);

@@ -569,7 +569,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
     void *ptrs[] = { p->thr, p->cnt, p->b32, p->b64, p->fin32, p->fin64, p->ext32, p->ext64,
                      p->wh32, p->wh64, p->ir32, p->ir64, p->off, p->tab32, p->tab64, p->pd32,
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
-                     p->malpha };
+                     p->malpha, p->dinv64 };
     for (void *q : ptrs) if (q) cudaFree(q);
     nl_cg_release(p);
     p->magic = 0;

@@ -38,7 +38,8 @@ def _smooth_noise(rng, d, n, width_cells):
     ks = np.meshgrid(*([k] * (d - 1) + [kr]), indexing="ij", sparse=True)
     k2 = sum(kk.astype(np.float64) ** 2 for kk in ks)
     filt = np.exp(-2.0 * (np.pi * width_cells / n) ** 2 * k2)
-    g = np.fft.irfftn(np.fft.rfftn(w) * filt, s=w.shape)
+    axes = list(range(d))
+    g = np.fft.irfftn(np.fft.rfftn(w, axes=axes) * filt, s=w.shape, axes=axes)
     g -= g.mean()
     sd = g.std()
     return g / sd if sd > 0 else g

@@ -1,0 +1,95 @@
+"""GPU parity of the learned-preconditioner kernels against the numpy oracle, and
+flexible CG with the network (FP64 oracle residual as the judge)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import convnet
+from paper_1905_08375_gb300 import binding as nl
+from paper_1905_08375_gb300 import precond, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _w(seed, scale=0.15):
+    return (np.random.default_rng(seed).standard_normal(convnet.NPARAM) * scale).astype(np.float32)
+
+
+@pytest.mark.parametrize("H,W", [(16, 16), (37, 50)])
+def test_forward_matches_oracle(H, W):
+    w = _w(1)
+    x = np.random.default_rng(2).standard_normal((3, H, W)).astype(np.float32)
+    net = nl.nl_net_create(w)
+    xt = torch.tensor(x, device=DEV)
+    ot = torch.full_like(xt, float("nan"))
+    nl.nl_net_forward(net, xt, ot)
+    torch.cuda.synchronize()
+    ref, _ = convnet.forward(w, x.astype(np.float64))
+    err = np.abs(ot.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < 2e-5, err
+
+
+def test_train_step_gradient_and_adam_match_oracle():
+    n, S, B, margin, lr = 40, 32, 5, 3, 1e-3
+    rng = np.random.default_rng(3)
+    w = _w(4)
+    x = rng.standard_normal((2, n, n)).astype(np.float32)
+    e = rng.standard_normal((2, n, n)).astype(np.float32)
+    crops = np.array([[0, 0, 0], [1, 8, 3], [0, 5, 8], [1, 0, 8], [0, 8, 8]], dtype=np.int32)
+    net = nl.nl_net_create(w)
+    loss = nl.nl_net_train_step(net, torch.tensor(x, device=DEV), torch.tensor(e, device=DEV),
+                                torch.tensor(crops, device=DEV), S, margin, lr)
+    g = nl.nl_net_gradient(net)
+    xb = np.stack([x[f, y0:y0 + S, x0:x0 + S] for f, y0, x0 in crops]).astype(np.float64)
+    eb = np.stack([e[f, y0:y0 + S, x0:x0 + S] for f, y0, x0 in crops]).astype(np.float64)
+    ref_loss, ref_g = convnet.loss_and_grad(w, xb, eb, margin=margin)
+    assert abs(loss - ref_loss) < 1e-5 * max(1.0, ref_loss)
+    assert np.linalg.norm(g - ref_g) / np.linalg.norm(ref_g) < 1e-4
+    w1 = nl.nl_net_get_weights(net)
+    ref_w1, _, _ = convnet.adam(w.astype(np.float64), g.astype(np.float64), np.zeros_like(g),
+                                np.zeros_like(g), 1, lr)
+    np.testing.assert_allclose(w1, ref_w1, rtol=0, atol=1e-6)
+
+
+def test_apply_matches_oracle_preconditioner():
+    n = 64
+    fld = synth.heterogeneous_2d(n=n, seed=5)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    w = _w(6, 0.1)
+    net = nl.nl_net_create(w)
+    r = synth.cg_rhs(n, seed=7, count=2)
+    rt = torch.tensor(r, device=DEV)
+    zt = torch.empty_like(rt)
+    nl.nl_net_apply(net, plan, rt, zt)
+    torch.cuda.synchronize()
+    dinv = 1.0 / oracle.direct_diag(2, n, fld["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                                    a=fld["a"], symmetric=True)
+    for k in range(2):
+        ref = convnet.apply_preconditioner(w, r[k], dinv, n)
+        err = np.linalg.norm(zt[k].cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < 2e-5, err
+
+
+def test_flexible_cg_with_trained_network_converges():
+    n = 64
+    fld = synth.heterogeneous_2d(n=n, seed=8)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    x, e = precond.collect_pairs(plan, n, seeds=range(100, 106), cap=32)
+    net = nl.nl_net_create(precond.init_weights(0))
+    hist = precond.train(net, x, e, pairs=2048, crop=32, batch=32, epochs=2, lr=2e-3,
+                         log_every=16)
+    assert hist[-1][2] < hist[0][2]                    # the loss went down
+    nl.nl_plan_set_net(plan, net)
+    f = synth.cg_rhs(n, seed=999, count=2)
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.empty_like(ft)
+    st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000, precond=nl.NL_PRECOND_LEARNED)
+    assert st["converged"], st
+    Lx = oracle.direct_scalar(xt.cpu().numpy(), 2, n, fld["delta"], alpha=1.5,
+                              coef=oracle.COEF_XY, a=fld["a"], symmetric=True)
+    res = np.linalg.norm(f + Lx, axis=1) / np.linalg.norm(f, axis=1)
+    assert np.all(res <= 1.01e-8), res
