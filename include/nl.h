@@ -230,6 +230,17 @@ nl_status nl_net_forward(nl_net *net, const float *x, float *o, int batch, int H
 nl_status nl_net_train_step(nl_net *net, const float *x, const float *e, int nfields, int n,
                             const int *crops, int batch, int S, int margin, float lr, float *loss,
                             void *stream);
+/*
+ * One Adam step on the energy norm of the preconditioned step's error, on whole fields:
+ * for each field b in DEVICE fields[batch] of x, e ([nfields][n^2] FP32 from
+ * nl_net_prepare_pairs), with r = x / D^{-1} (the scaled residual), z = x + o(x) and
+ * A = -L applied by the plan (FP32):
+ *     loss_b = (z - e)^T A (z - e) / e^T A e = (z.Az - 2 z.r + e.r) / e.r,
+ * averaged over the batch; *loss (HOST, may be NULL).  Needs the symmetric 2-D scalar plan.
+ */
+nl_status nl_net_train_step_energy(nl_net *net, nl_plan *plan, const float *x, const float *e,
+                                   int nfields, const int *fields, int batch, float lr,
+                                   float *loss, void *stream);
 /* Training pairs from CG iterates: DEVICE r, e [count][n^2] FP64 (residual f + L x_k and
  * error x* - x_k) -> x_out = D^{-1} r / s, e_out = e / s (FP32), s = RMS(D^{-1} r) per field. */
 nl_status nl_net_prepare_pairs(nl_plan *plan, const double *r, const double *e, int count,

@@ -284,6 +284,8 @@ def _net_fns():
     L.nl_net_forward.argtypes = [vp, vp, vp, i, i, i, vp]
     L.nl_net_train_step.restype = i
     L.nl_net_train_step.argtypes = [vp, vp, vp, i, i, vp, i, i, i, f, ctypes.POINTER(f), vp]
+    L.nl_net_train_step_energy.restype = i
+    L.nl_net_train_step_energy.argtypes = [vp, vp, vp, vp, i, vp, i, f, ctypes.POINTER(f), vp]
     L.nl_net_prepare_pairs.restype = i
     L.nl_net_prepare_pairs.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.nl_net_apply.restype = i
@@ -355,6 +357,17 @@ def nl_net_train_step(net: Net, x, e, crops, S, margin, lr, want_loss=True, stre
                                         margin, float(lr),
                                         ctypes.byref(loss) if want_loss else None,
                                         _stream_ptr(stream)))
+    return float(loss.value) if want_loss else None
+
+
+def nl_net_train_step_energy(net: Net, plan: Plan, x, e, fields, lr, want_loss=True,
+                             stream=None):
+    """x, e: CUDA float32 [nfields, N]; fields: CUDA int32 [batch].  Returns the loss."""
+    loss = ctypes.c_float(0.0)
+    _check(_net_fns().nl_net_train_step_energy(
+        net.handle, plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+        x.shape[0], ctypes.c_void_p(fields.data_ptr()), fields.shape[0], float(lr),
+        ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)))
     return float(loss.value) if want_loss else None
 
 

@@ -327,6 +327,89 @@ __global__ void k_pairs(const double *__restrict__ r, const double *__restrict__
     }
 }
 
+// energy-norm training: gather whole fields, r~ = x / dinv (the scaled residual)
+__global__ void k_gather_fields(const float *__restrict__ x, const float *__restrict__ e,
+                                const int *__restrict__ fields, int nfields, int64_t N,
+                                const double *__restrict__ dinv, float *xb, float *eb, float *rb)
+{
+    const int b = blockIdx.y;
+    const int f = fields[b];
+    const bool ok = f >= 0 && f < nfields;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        float xv = 0.f, ev = 0.f;
+        if (ok) { xv = x[(size_t)f * N + k]; ev = e[(size_t)f * N + k]; }
+        xb[(size_t)b * N + k] = xv;
+        eb[(size_t)b * N + k] = ev;
+        rb[(size_t)b * N + k] = (float)((double)xv / dinv[k]);
+    }
+}
+
+// z = x + o (the preconditioned step, scaled units)
+__global__ void k_add(int64_t n, const float *__restrict__ a, const float *__restrict__ b, float *c)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] + b[i];
+}
+
+// partial sums per field: z.Az (Az = -Lz), z.r, e.r
+__global__ void __launch_bounds__(RB) k_energy_partial(const float *__restrict__ z,
+                                                       const float *__restrict__ Lz,
+                                                       const float *__restrict__ r,
+                                                       const float *__restrict__ e, int64_t N,
+                                                       double *__restrict__ part)
+{
+    __shared__ double sh[3][RB / 32];
+    const int b = blockIdx.y;
+    double zaz = 0.0, zr = 0.0, er = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < N; k += (int64_t)NB * RB) {
+        const size_t g = (size_t)b * N + k;
+        zaz -= (double)z[g] * Lz[g];
+        zr += (double)z[g] * r[g];
+        er += (double)e[g] * r[g];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        zaz += __shfl_down_sync(0xffffffffu, zaz, o);
+        zr += __shfl_down_sync(0xffffffffu, zr, o);
+        er += __shfl_down_sync(0xffffffffu, er, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = zaz; sh[1][threadIdx.x >> 5] = zr; sh[2][threadIdx.x >> 5] = er;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, c = 0, d = 0;
+        for (int w = 0; w < RB / 32; ++w) { a += sh[0][w]; c += sh[1][w]; d += sh[2][w]; }
+        double *q = part + ((size_t)b * NB + blockIdx.x) * 3;
+        q[0] = a; q[1] = c; q[2] = d;
+    }
+}
+
+// loss_b = (z.Az - 2 z.r + e.r) / e.r ;  go = 2 (Az - r) / (e.r B)
+__global__ void k_energy_grad(const float *__restrict__ Lz, const float *__restrict__ r, int64_t N,
+                              const double *__restrict__ part, int B, float *__restrict__ go,
+                              float *__restrict__ loss)
+{
+    const int b = blockIdx.y;
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) {
+        double a = 0, c = 0, d = 0;
+        for (int k = 0; k < NB; ++k) {
+            const double *q = part + ((size_t)b * NB + k) * 3;
+            a += q[0]; c += q[1]; d += q[2];
+        }
+        s_inv = d > 0.0 ? 1.0 / d : 0.0;
+        if (blockIdx.x == 0) loss[b] = (float)((a - 2.0 * c + d) * s_inv);
+    }
+    __syncthreads();
+    const double scale = 2.0 * s_inv / B;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const size_t g = (size_t)b * N + k;
+        go[g] = (float)(scale * (-(double)Lz[g] - (double)r[g]));
+    }
+}
+
 }  // namespace
 
 struct nl_net {
@@ -536,18 +619,6 @@ extern "C" nl_status nl_net_train_step(nl_net *n, const float *x, const float *e
     return NL_OK;
 }
 
-extern "C" nl_status nl_net_gradient(nl_net *n, float *grad_host, void *stream)
-{
-    if (!net_ok(n) || !grad_host) {
-        nl_set_error("nl_net_gradient: bad argument");
-        return NL_EINVAL;
-    }
-    cudaStream_t st = nl_stream(stream);
-    NL_CUDA_TRY(cudaMemcpyAsync(grad_host, n->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, st));
-    NL_CUDA_TRY(cudaStreamSynchronize(st));
-    return NL_OK;
-}
-
 // plan-owned inverse Jacobi diagonal (FP64), computed once
 static nl_status plan_dinv(nl_plan *p, cudaStream_t st, const double **out)
 {
@@ -566,6 +637,95 @@ static nl_status plan_dinv(nl_plan *p, cudaStream_t st, const double **out)
         p->device_bytes += per * sizeof(double);
     }
     *out = p->dinv64;
+    return NL_OK;
+}
+
+// shared backward pass + Adam for a batch of B planes of H x W
+static nl_status net_backward_adam(nl_net *n, const float *xb, const float *y1, const float *y2,
+                                   const float *go, float *g2, float *g1, int B, int H, int W,
+                                   float lr, cudaStream_t st)
+{
+    const int tiles = ((H + TILE - 1) / TILE) * ((W + TILE - 1) / TILE);
+    const size_t nblk = (size_t)tiles * B;
+    nl_status s = grow(&n->part, &n->part_elems, nblk * NP2);
+    if (s != NL_OK) return s;
+    const dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE, B);
+    k_conv3_wgrad<32, 1><<<grid, 256, wgrad_smem(32, 1), st>>>(y2, go, n->part, H, W);
+    k_wgrad_reduce<<<(NP3 + 255) / 256, 256, 0, st>>>(n->part, (int)nblk, 32, 1, n->grad + OFF3);
+    k_conv3<1, 32, 2><<<grid, 256, conv_smem(1, 32), st>>>(go, n->wkt + OFF3, g2, y2, H, W);
+    k_conv3_wgrad<32, 32><<<grid, 256, wgrad_smem(32, 32), st>>>(y1, g2, n->part, H, W);
+    k_wgrad_reduce<<<(NP2 + 255) / 256, 256, 0, st>>>(n->part, (int)nblk, 32, 32, n->grad + OFF2);
+    k_conv3<32, 32, 2><<<grid, 256, conv_smem(32, 32), st>>>(g2, n->wkt + OFF2, g1, y1, H, W);
+    k_conv3_wgrad<1, 32><<<grid, 256, wgrad_smem(1, 32), st>>>(xb, g1, n->part, H, W);
+    k_wgrad_reduce<<<(NP1 + 255) / 256, 256, 0, st>>>(n->part, (int)nblk, 1, 32, n->grad + OFF1);
+    n->t += 1;
+    const float c1 = 1.f - powf(0.9f, (float)n->t), c2 = 1.f - powf(0.999f, (float)n->t);
+    k_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->w32, n->m, n->v, n->grad, n->wb, lr, c1, c2);
+    k_layouts<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->wb, n->wk, n->wkt);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+extern "C" nl_status nl_net_train_step_energy(nl_net *n, nl_plan *p, const float *x,
+                                              const float *e, int nfields, const int *fields,
+                                              int batch, float lr, float *loss_host,
+                                              void *stream)
+{
+    if (!net_ok(n) || !nl_plan_ok(p) || !x || !e || !fields || batch < 1 || batch > 1024 ||
+        nfields < 1 || !(lr > 0.f)) {
+        nl_set_error("nl_net_train_step_energy: bad argument");
+        return NL_EINVAL;
+    }
+    if (p->d != 2 || p->family == NL_PD_BOND || !p->symmetric) {
+        nl_set_error("nl_net_train_step_energy: needs the symmetric 2-D scalar operator");
+        return NL_EUNSUPPORTED;
+    }
+    cudaStream_t st = nl_stream(stream);
+    const double *dinv = nullptr;
+    nl_status s = plan_dinv(p, st, &dinv);
+    if (s != NL_OK) return s;
+    const int64_t N = p->N;
+    const int H = p->n, W = p->n;
+    const size_t f = (size_t)N * batch;
+    // xb eb rb o z Lz go | y1 y2 g2 g1 (32 channels each)
+    s = grow(&n->train, &n->train_elems, f * (7 + 4 * 32));
+    if (s != NL_OK) return s;
+    size_t le = (size_t)n->loss_elems;
+    if ((s = grow(&n->loss, &le, (size_t)batch)) != NL_OK) return s;
+    n->loss_elems = (int)le;
+    size_t re = (size_t)n->red_elems;
+    if ((s = grow(&n->red, &re, (size_t)NB * batch * 3)) != NL_OK) return s;
+    n->red_elems = (int)re;
+    float *xb = n->train, *eb = xb + f, *rb = eb + f, *o = rb + f, *z = o + f, *Lz = z + f;
+    float *go = Lz + f, *y1 = go + f, *y2 = y1 + 32 * f, *g2 = y2 + 32 * f, *g1 = g2 + 32 * f;
+    const unsigned gx = (unsigned)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
+    k_gather_fields<<<dim3(gx, batch), 256, 0, st>>>(x, e, fields, nfields, N, dinv, xb, eb, rb);
+    if ((s = net_forward(n, xb, y1, y2, o, batch, H, W, st)) != NL_OK) return s;
+    k_add<<<(unsigned)((f + 255) / 256), 256, 0, st>>>((int64_t)f, xb, o, z);
+    if ((s = nl_direct_launch(p, z, Lz, batch, NL_F32, st)) != NL_OK) return s;
+    k_energy_partial<<<dim3(NB, batch), RB, 0, st>>>(z, Lz, rb, eb, N, n->red);
+    k_energy_grad<<<dim3(gx, batch), 256, 0, st>>>(Lz, rb, N, n->red, batch, go, n->loss);
+    if ((s = net_backward_adam(n, xb, y1, y2, go, g2, g1, batch, H, W, lr, st)) != NL_OK) return s;
+    if (loss_host) {
+        float tmp[1024];
+        NL_CUDA_TRY(cudaMemcpyAsync(tmp, n->loss, batch * sizeof(float), cudaMemcpyDeviceToHost, st));
+        NL_CUDA_TRY(cudaStreamSynchronize(st));
+        double sum = 0.0;
+        for (int b = 0; b < batch; ++b) sum += tmp[b];
+        *loss_host = (float)(sum / batch);
+    }
+    return NL_OK;
+}
+
+extern "C" nl_status nl_net_gradient(nl_net *n, float *grad_host, void *stream)
+{
+    if (!net_ok(n) || !grad_host) {
+        nl_set_error("nl_net_gradient: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = nl_stream(stream);
+    NL_CUDA_TRY(cudaMemcpyAsync(grad_host, n->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, st));
+    NL_CUDA_TRY(cudaStreamSynchronize(st));
     return NL_OK;
 }
 

@@ -51,6 +51,24 @@ def collect_pairs(plan, n, seeds, cap=64, rtol=1e-10, device="cuda"):
     return x, e
 
 
+def train_energy(net, plan, x, e, pairs=20000, batch=8, lr=1e-3, seed=0, log_every=0):
+    """Adam on the energy-norm loss over whole fields; `pairs` field samples in total."""
+    import torch
+    rng = np.random.default_rng(seed)
+    nf = x.shape[0]
+    xf = x.reshape(nf, -1)
+    ef = e.reshape(nf, -1)
+    losses = []
+    steps = max(1, pairs // batch)
+    for s in range(steps):
+        idx = torch.tensor(rng.integers(0, nf, batch).astype(np.int32), device=x.device)
+        want = log_every and (s % log_every == 0 or s == steps - 1)
+        loss = nl.nl_net_train_step_energy(net, plan, xf, ef, idx, lr, want_loss=bool(want))
+        if want:
+            losses.append((0, s, loss))
+    return losses
+
+
 def train(net, x, e, pairs=20000, crop=64, margin=3, batch=64, epochs=2, lr=1e-3, seed=0,
           log_every=0):
     """Adam on `pairs` random crops (field, y0, x0) per epoch; returns the loss history."""
