@@ -26,6 +26,7 @@ struct DirectArgs {
     int n, R, sx, sy, sz, K;
     int64_t N;
     const int *cnt, *thr;
+    const int *cnt_thr;       // symmetric variant: largest |o|^2 a node's loop must reach
     const void *b, *fin, *ext, *wh, *ir;
     const void *tab;
     const int4 *off;
@@ -267,6 +268,417 @@ k_direct_pd(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
 }
 
 // ---------------------------------------------------------------------------
+// 2-D register-blocked scalar kernel.  A block of 32 x RB_TY threads covers 32 columns and
+// RB_TY * RB_P rows; each thread owns RB_P consecutive rows of one column.  The block stages
+// its halo tile in shared memory (plus RB_P spare rows), then for every stencil column ox
+// slides a register window down the tile: one shared load and one weight per row offset oy
+// serve all RB_P outputs, each with its own exact horizon mask ox^2 + oy^2 <= thr_p.  The sum
+// is accumulated column by column in the difference form g b_j (u_j - u_i).
+// ---------------------------------------------------------------------------
+constexpr int RB_TY = 4, RB_P = 8;
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(32 * RB_TY)
+k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u, T *__restrict__ Lu)
+{
+    using Elem = typename std::conditional<MODE == MODE_SYM, V4<T>, V2<T>>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, R = a.R;
+    const int SX = 32 + 2 * R;                       // tile width
+    const int SY = RB_TY * RB_P + 2 * R + RB_P;      // tile height (RB_P spare rows)
+    const int GW = 2 * R + 1;
+    Elem *tile = reinterpret_cast<Elem *>(smem_raw);
+    T *s_g = reinterpret_cast<T *>(smem_raw + sizeof(Elem) * SX * SY);
+    const int64_t N = a.N;
+    const T *__restrict__ ur = u + (int64_t)blockIdx.z * N;
+    const T *__restrict__ bb = (const T *)a.b;
+    const T *__restrict__ whv = (const T *)a.wh;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * (RB_TY * RB_P);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int e = tid; e < SX * SY; e += 32 * RB_TY) {
+        const int gx = x0 - R + e % SX, gy = y0 - R + e / SX;
+        Elem v;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+            const int64_t j = gx + (int64_t)n * gy;
+            v.u = ur[j];
+            v.b = bb[j];
+            if constexpr (MODE == MODE_SYM) { v.wh = whv[j]; v.thr = a.thr[j]; }
+        } else {
+            v.u = T(0);
+            v.b = T(0);
+            if constexpr (MODE == MODE_SYM) { v.wh = T(0); v.thr = -1; }
+        }
+        tile[e] = v;
+    }
+    if (MODE != MODE_POLY)
+        for (int e = tid; e < GW * GW; e += 32 * RB_TY) s_g[e] = gtab[e];
+    __syncthreads();
+
+    const int x = x0 + threadIdx.x;
+    const int ybase = y0 + threadIdx.y * RB_P;
+    T ui[RB_P], acc[RB_P], irp[RB_P], whp[RB_P];
+    int thr[RB_P];
+    int tmax = -1;
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int y = ybase + p;
+        const bool own = x < n && y < n;
+        const int64_t i = own ? x + (int64_t)n * y : 0;
+        ui[p] = tile[(threadIdx.y * RB_P + p + R) * SX + threadIdx.x + R].u;
+        thr[p] = own ? a.thr[i] : -1;
+        irp[p] = (MODE == MODE_POLY && own) ? ((const T *)a.ir)[i] : T(0);
+        whp[p] = (MODE == MODE_SYM && own) ? whv[i] : T(0);
+        acc[p] = T(0);
+    }
+    // the symmetric kernel also reaches offsets inside the neighbours' balls
+    int reach[RB_P];
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int y = ybase + p;
+        reach[p] = (MODE == MODE_SYM) ? ((x < n && y < n) ? a.cnt_thr[x + (int64_t)n * y] : -1)
+                                      : thr[p];
+        tmax = max(tmax, reach[p]);
+    }
+    const int rx = min(R, (int)sqrtf((float)max(tmax, 0)) + 1);
+    const int col0 = threadIdx.x + R;
+    const int row0 = threadIdx.y * RB_P + R;        // tile row of output p = row0 + p
+
+    // one output's term for the window element v at offset (ox, oy); MASKED checks the
+    // horizon, the unmasked core is only entered where every output's ball holds the row
+    auto term = [&](int p, const Elem &v, int o2, T g, bool masked) {
+        if constexpr (MODE == MODE_SYM) {
+            const T wi = (o2 <= thr[p]) ? whp[p] : T(0);
+            const T wj = (o2 <= v.thr) ? v.wh : T(0);
+            acc[p] += g * v.b * (wi + wj) * (v.u - ui[p]);
+        } else if constexpr (MODE == MODE_POLY) {
+            if (!masked || o2 <= thr[p])
+                acc[p] += poly_weight<T>(a.poly, a.K, (T)o2 * irp[p]) * v.b * (v.u - ui[p]);
+        } else {
+            if (!masked || o2 <= thr[p]) acc[p] += g * v.b * (v.u - ui[p]);
+        }
+    };
+
+    for (int ox = -rx; ox <= rx; ++ox) {
+        const int ox2 = ox * ox;
+        if (ox2 > tmax) continue;
+        // per-output half-heights of this column: |oy| <= h_p  <=>  ox^2 + oy^2 <= reach_p
+        int hmin = R, hmax = -1;
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            int h = -1;
+            const int rest = reach[p] - ox2;
+            if (rest >= 0) {
+                h = (int)sqrtf((float)rest);
+                while (h * h > rest) --h;
+                while ((h + 1) * (h + 1) <= rest) ++h;
+            }
+            hmin = min(hmin, h);
+            hmax = max(hmax, h);
+        }
+        if (hmax < 0) continue;
+        hmax = min(hmax, R);
+        if (MODE == MODE_SYM) hmin = -1;            // every term carries its own masks
+        const Elem *colp = tile + col0 + ox;
+        const T *gcol = s_g + (ox + R) * GW + R;
+        Elem W[RB_P];
+        int oy = -hmax;
+#pragma unroll
+        for (int k = 0; k < RB_P; ++k) W[k] = colp[(row0 + oy + k) * SX];
+        // rows where some output's ball ends: single masked steps
+        auto single = [&](int oyv) {
+            const int o2 = ox2 + oyv * oyv;
+            const T g = (MODE == MODE_POLY) ? T(1) : gcol[oyv];
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) term(p, W[p], o2, g, true);
+#pragma unroll
+            for (int k = 0; k < RB_P - 1; ++k) W[k] = W[k + 1];
+            W[RB_P - 1] = colp[(row0 + oyv + RB_P) * SX];
+        };
+        for (; oy < -hmin && oy <= hmax; ++oy) single(oy);
+        // core: every output's ball holds rows -hmin .. hmin; unmasked chunks of RB_P rows
+        for (; oy + RB_P - 1 <= hmin; oy += RB_P) {
+            Elem X[RB_P - 1];
+#pragma unroll
+            for (int k = 0; k < RB_P - 1; ++k) X[k] = colp[(row0 + oy + RB_P + k) * SX];
+#pragma unroll
+            for (int j = 0; j < RB_P; ++j) {
+                const int oyj = oy + j;
+                const int o2 = ox2 + oyj * oyj;
+                const T g = (MODE == MODE_POLY) ? T(1) : gcol[oyj];
+#pragma unroll
+                for (int p = 0; p < RB_P; ++p) {
+                    const int k = p + j;
+                    term(p, k < RB_P ? W[k] : X[k - RB_P], o2, g, false);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RB_P - 1; ++k) W[k] = X[k];
+            W[RB_P - 1] = colp[(row0 + oy + 2 * RB_P - 1) * SX];
+        }
+        for (; oy <= hmax; ++oy) single(oy);
+    }
+    const T *__restrict__ finv = (const T *)a.fin;
+    const T *__restrict__ extv = (const T *)a.ext;
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int y = ybase + p;
+        if (x < n && y < n) {
+            const int64_t i = x + (int64_t)n * y;
+            Lu[(int64_t)blockIdx.z * N + i] = finv[i] * (acc[p] - ui[p] * extv[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D register-blocked FP32 kernel with paired FP32 arithmetic (POWER kernels).  Same
+// traversal as k_direct2d_rb, but each thread owns two columns, c and c + 32, of RB_P rows,
+// and every multiply/add runs as one paired f32x2 instruction on the two columns (per element
+// IEEE round-to-nearest, so each column's result is bitwise the single-column one).  A block of
+// 32 x X2_TY threads covers 64 columns and X2_TY * RB_P rows; the tile is kept as separate u
+// and b planes so that a warp's loads are 32 consecutive floats.
+// ---------------------------------------------------------------------------
+constexpr int X2_TY = 4;
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+__device__ __forceinline__ int isqrt_small(int x)   // floor(sqrt(x)), 0 <= x < 2^24
+{
+    int h = (int)sqrtf((float)x);
+    h -= (h * h > x);
+    h += ((h + 1) * (h + 1) <= x);
+    return h;
+}
+
+// RM: compile-time halo (>= the plan's largest radius) so that every shared-memory offset
+// is an immediate
+template <int RM>
+__global__ void __launch_bounds__(32 * X2_TY, 4)
+k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
+              float *__restrict__ Lu)
+{
+    constexpr int SX = 64 + 2 * RM;
+    constexpr int SY = X2_TY * RB_P + 2 * RM + RB_P;
+    constexpr int GW = 2 * RM + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, R = a.R;                      // R <= RM
+    float *su = reinterpret_cast<float *>(smem_raw);
+    float *sb = su + SX * SY;
+    const int64_t N = a.N;
+    const float *__restrict__ ur = u + (int64_t)blockIdx.z * N;
+    const float *__restrict__ bb = (const float *)a.b;
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * (X2_TY * RB_P);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int e = tid; e < SX * SY; e += 32 * X2_TY) {
+        const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
+        float uv = 0.f, bv = 0.f;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+            const int64_t j = gx + (int64_t)n * gy;
+            uv = ur[j];
+            bv = bb[j];
+        }
+        su[e] = uv;
+        sb[e] = bv;
+    }
+    __syncthreads();
+
+    const int xa = x0 + threadIdx.x, xb = xa + 32;
+    const int ybase = y0 + threadIdx.y * RB_P;
+    f2_t ui[RB_P], acc[RB_P];
+    int thra[RB_P], thrb[RB_P];
+    int tmax = -1, tmin = 1 << 30;
+    // tile position of output (p, column a): row row0 + p, column col0
+    const float *ua = su + (threadIdx.y * RB_P + RM) * SX + threadIdx.x + RM;
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int y = ybase + p;
+        const bool oa = xa < n && y < n, ob = xb < n && y < n;
+        thra[p] = oa ? a.thr[xa + (int64_t)n * y] : -1;
+        thrb[p] = ob ? a.thr[xb + (int64_t)n * y] : -1;
+        tmax = max(tmax, max(thra[p], thrb[p]));
+        tmin = min(tmin, min(oa ? thra[p] : tmin, ob ? thrb[p] : tmin));
+        ui[p] = f2_pack(ua[p * SX], ua[p * SX + 32]);
+        acc[p] = f2_pack(0.f, 0.f);
+    }
+    if (tmin == (1 << 30)) tmin = -1;
+    const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
+
+    for (int ox = -rx; ox <= rx; ++ox) {
+        const int ox2 = ox * ox;
+        if (ox2 > tmax) continue;
+        const int hmax = min(R, isqrt_small(tmax - ox2));
+        const int hmin = (tmin >= ox2) ? isqrt_small(tmin - ox2) : -1;
+        // column base: tile row of (p = 0, oy = 0) is row0; base points at row row0
+        const float *cu = ua + ox;
+        const float *cb = cu + SX * SY;
+        const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
+        f2_t Wu[RB_P], Wb[RB_P];
+        int oy = -hmax;
+#pragma unroll
+        for (int k = 0; k < RB_P; ++k) {
+            Wu[k] = f2_pack(cu[(oy + k) * SX], cu[(oy + k) * SX + 32]);
+            Wb[k] = f2_pack(cb[(oy + k) * SX], cb[(oy + k) * SX + 32]);
+        }
+        // top rim (rows outside some output's ball): single masked rows
+        for (; oy < -hmin && oy <= hmax; ++oy) {
+            const int o2 = ox2 + oy * oy;
+            const float g = gcol[oy];
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) {
+                float b0, b1;
+                f2_unpack(Wb[p], b0, b1);
+                b0 = (o2 <= thra[p]) ? b0 * g : 0.f;
+                b1 = (o2 <= thrb[p]) ? b1 * g : 0.f;
+                acc[p] = f2_fma(f2_pack(b0, b1), f2_sub(Wu[p], ui[p]), acc[p]);
+            }
+#pragma unroll
+            for (int k = 0; k < RB_P - 1; ++k) { Wu[k] = Wu[k + 1]; Wb[k] = Wb[k + 1]; }
+            const float *rp = cu + (oy + RB_P) * SX;
+            Wu[RB_P - 1] = f2_pack(rp[0], rp[32]);
+            Wb[RB_P - 1] = f2_pack(rp[SX * SY], rp[SX * SY + 32]);
+        }
+        // full chunks of RB_P rows inside every output's ball: unmasked
+        for (; oy + RB_P - 1 <= hmin; oy += RB_P) {
+            f2_t Xu[RB_P - 1], Xb[RB_P - 1];
+            const float *rp = cu + (oy + RB_P) * SX;
+#pragma unroll
+            for (int k = 0; k < RB_P - 1; ++k) {
+                Xu[k] = f2_pack(rp[k * SX], rp[k * SX + 32]);
+                Xb[k] = f2_pack(rp[k * SX + SX * SY], rp[k * SX + SX * SY + 32]);
+            }
+#pragma unroll
+            for (int j = 0; j < RB_P; ++j) {
+                const float g = gcol[oy + j];
+                const f2_t gg = f2_pack(g, g);
+#pragma unroll
+                for (int p = 0; p < RB_P; ++p) {
+                    const int k = p + j;
+                    const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
+                    const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
+                    acc[p] = f2_fma(f2_mul(vb, gg), f2_sub(vu, ui[p]), acc[p]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RB_P - 1; ++k) { Wu[k] = Xu[k]; Wb[k] = Xb[k]; }
+            const float *rq = cu + (oy + 2 * RB_P - 1) * SX;
+            Wu[RB_P - 1] = f2_pack(rq[0], rq[32]);
+            Wb[RB_P - 1] = f2_pack(rq[SX * SY], rq[SX * SY + 32]);
+        }
+        // the rest in half chunks of RB_P / 2 rows, unmasked where still inside every ball
+        constexpr int HC = RB_P / 2;
+        for (; oy <= hmax; oy += HC) {
+            const bool core = oy + HC - 1 <= hmin;
+            f2_t Xu[HC], Xb[HC];
+            const float *rp = cu + (oy + RB_P) * SX;
+#pragma unroll
+            for (int k = 0; k < HC; ++k) {
+                Xu[k] = f2_pack(rp[k * SX], rp[k * SX + 32]);
+                Xb[k] = f2_pack(rp[k * SX + SX * SY], rp[k * SX + SX * SY + 32]);
+            }
+            if (core) {
+#pragma unroll
+                for (int j = 0; j < HC; ++j) {
+                    const float g = gcol[oy + j];
+                    const f2_t gg = f2_pack(g, g);
+#pragma unroll
+                    for (int p = 0; p < RB_P; ++p) {
+                        const int k = p + j;
+                        const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
+                        const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
+                        acc[p] = f2_fma(f2_mul(vb, gg), f2_sub(vu, ui[p]), acc[p]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < HC; ++j) {
+                    const int oyj = oy + j;
+                    const int o2 = ox2 + oyj * oyj;
+                    const float g = gcol[min(oyj, R)];
+#pragma unroll
+                    for (int p = 0; p < RB_P; ++p) {
+                        const int k = p + j;
+                        const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
+                        const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
+                        float b0, b1;
+                        f2_unpack(vb, b0, b1);
+                        b0 = (o2 <= thra[p]) ? b0 * g : 0.f;
+                        b1 = (o2 <= thrb[p]) ? b1 * g : 0.f;
+                        acc[p] = f2_fma(f2_pack(b0, b1), f2_sub(vu, ui[p]), acc[p]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < HC; ++k) { Wu[k] = Wu[k + HC]; Wb[k] = Wb[k + HC]; }
+#pragma unroll
+            for (int k = 0; k < HC; ++k) { Wu[HC + k] = Xu[k]; Wb[HC + k] = Xb[k]; }
+        }
+    }
+    const float *__restrict__ finv = (const float *)a.fin;
+    const float *__restrict__ extv = (const float *)a.ext;
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int y = ybase + p;
+        float s0, s1, u0, u1;
+        f2_unpack(acc[p], s0, s1);
+        f2_unpack(ui[p], u0, u1);
+        if (y < n && xa < n) {
+            const int64_t i = xa + (int64_t)n * y;
+            Lu[(int64_t)blockIdx.z * N + i] = finv[i] * (s0 - u0 * extv[i]);
+        }
+        if (y < n && xb < n) {
+            const int64_t i = xb + (int64_t)n * y;
+            Lu[(int64_t)blockIdx.z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+        }
+    }
+}
+
+template <int RM>
+static size_t x2_smem_bytes()
+{
+    return sizeof(float) * (size_t)2 * (64 + 2 * RM) * (X2_TY * RB_P + 2 * RM + RB_P);
+}
+
+template <int RM>
+static nl_status launch_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu, int nrhs,
+                           cudaStream_t st)
+{
+    const dim3 blk(32, X2_TY, 1);
+    const dim3 grd((p->n + 63) / 64, (p->n + X2_TY * RB_P - 1) / (X2_TY * RB_P), nrhs);
+    const size_t smem = x2_smem_bytes<RM>();
+    NL_CUDA_TRY(prep_smem(k_direct2d_x2<RM>, smem));
+    k_direct2d_x2<RM><<<grd, blk, smem, st>>>(a, p->rb_g32, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 // Raise a kernel's dynamic shared-memory limit once per (kernel, size): repeated calls
@@ -323,11 +735,40 @@ static nl_status launch_scalar_t(nl_plan *p, const DirectArgs &a, const T *u, T 
     return NL_OK;
 }
 
+template <typename T, int MODE>
+static nl_status launch_rb_t(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
+                             cudaStream_t st)
+{
+    const dim3 blk(32, RB_TY, 1);
+    const dim3 grd((p->n + 31) / 32, (p->n + RB_TY * RB_P - 1) / (RB_TY * RB_P), nrhs);
+    const size_t smem = sizeof(T) == 4 ? p->rb_smem32 : p->rb_smem64;
+    const T *g = sizeof(T) == 4 ? (const T *)p->rb_g32 : (const T *)p->rb_g64;
+    auto kern = k_direct2d_rb<T, MODE>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    kern<<<grd, blk, smem, st>>>(a, g, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
 template <typename T>
 static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
                                cudaStream_t st, size_t smem)
 {
     const int mode = p->symmetric ? MODE_SYM : (p->family == NL_POLY ? MODE_POLY : MODE_POWER);
+    if (p->d == 2 && p->rb2d && sizeof(T) == 4) {
+        if (mode == MODE_POWER && p->Rmax <= 32) {
+            const float *uf = (const float *)u;
+            float *lf = (float *)Lu;
+            if (p->Rmax <= 4) return launch_x2<4>(p, a, uf, lf, nrhs, st);
+            if (p->Rmax <= 8) return launch_x2<8>(p, a, uf, lf, nrhs, st);
+            if (p->Rmax <= 16) return launch_x2<16>(p, a, uf, lf, nrhs, st);
+            if (p->Rmax <= 24) return launch_x2<24>(p, a, uf, lf, nrhs, st);
+            return launch_x2<32>(p, a, uf, lf, nrhs, st);
+        }
+        if (mode == MODE_POWER) return launch_rb_t<T, MODE_POWER>(p, a, u, Lu, nrhs, st);
+        if (mode == MODE_POLY) return launch_rb_t<T, MODE_POLY>(p, a, u, Lu, nrhs, st);
+        return launch_rb_t<T, MODE_SYM>(p, a, u, Lu, nrhs, st);
+    }
 #define NL_DISPATCH_MODE(D)                                                                  \
     do {                                                                                     \
         if (mode == MODE_POWER) return launch_scalar_t<D, T, MODE_POWER>(p, a, u, Lu, nrhs, st, smem); \
@@ -362,7 +803,7 @@ static DirectArgs make_args(const nl_plan *p, int dtype)
     DirectArgs a;
     a.n = p->n; a.R = p->Rmax; a.sx = p->tile_sx; a.sy = p->tile_sy; a.sz = p->tile_sz;
     a.K = p->K; a.N = p->N;
-    a.cnt = p->cnt; a.thr = p->thr;
+    a.cnt = p->cnt; a.thr = p->thr; a.cnt_thr = p->thr_reach;
     const bool f32 = dtype == NL_F32;
     a.b = f32 ? (const void *)p->b32 : (const void *)p->b64;
     a.fin = f32 ? (const void *)p->fin32 : (const void *)p->fin64;

@@ -369,6 +369,166 @@ __global__ void k_fast_node(int d, int n, int K, int coef, int self_mode, int64_
     selfS[i] = pow(1.0 / n, (double)d) * acc;
 }
 
+// ---------------------------------------------------------------------------
+// p^0 = 1 with FP32 data: Step 2 partial sums in 64-bit fixed point.  One reduction finds
+// m = max |v|; with S = 62 - ceil(log2(N m)) every leaf value is rounded once to an integer
+// multiple of 2^-S and every partial sum of any set of leaves is then exact (|sum| < 2^62).
+// Step 3 adds the integer panel sums of the decomposition exactly, panel by panel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int isqrt_fast(int x)     // floor(sqrt(x)) for 0 <= x < 2^30
+{
+    int h = (int)sqrtf((float)x);
+    h -= (h * h > x);
+    h -= (h * h > x);
+    h += ((h + 1) * (h + 1) <= x);
+    h += ((h + 1) * (h + 1) <= x);
+    return h;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(int64_t N, const T *__restrict__ u,
+                                                const double *__restrict__ b,
+                                                unsigned long long *out)
+{
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)u[i] * b[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__device__ __forceinline__ int fixed_shift(int64_t N, const unsigned long long *mx)
+{
+    const double m = __longlong_as_double((long long)*mx);
+    if (!(m > 0.0)) return 62;
+    int e;
+    frexp((double)N * m, &e);          // N m < 2^e
+    return 62 - e;
+}
+
+template <typename T>
+__global__ void k_pyr_leaf_i64(int64_t N, const T *__restrict__ u, const double *__restrict__ b,
+                               const unsigned long long *mx, long long *leaf)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int sh = fixed_shift(N, mx);
+    leaf[i] = __double2ll_rn(ldexp((double)u[i] * b[i], sh));
+}
+
+__global__ void k_pyr_level_i64(int d, int l, const long long *__restrict__ child,
+                                long long *__restrict__ parent)
+{
+    const int np = 1 << l;
+    int64_t P = np;
+    if (d > 1) P *= np;
+    if (d > 2) P *= np;
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= P) return;
+    const int kx = (int)(f % np);
+    const int ky = d > 1 ? (int)((f / np) % np) : 0;
+    const int kz = d > 2 ? (int)(f / ((int64_t)np * np)) : 0;
+    const int nc = 2 * np;
+    long long s = 0;
+    for (int c = 0; c < (1 << d); ++c) {
+        const int cx = 2 * kx + (c & 1);
+        const int cy = d > 1 ? 2 * ky + ((c >> 1) & 1) : 0;
+        const int cz = d > 2 ? 2 * kz + ((c >> 2) & 1) : 0;
+        s += child[cx + (int64_t)nc * (cy + (int64_t)nc * cz)];
+    }
+    parent[f] = s;
+}
+
+struct FastI64Args {
+    int n, L;
+    int64_t N;
+    const int *thr4;
+    const double *fastF, *selfS;
+    const long long *pyr;                  // levels 0..L (leaf level last), panel-major
+    int64_t lvl_off[NL_MAX_LEVELS + 2];
+    double hd;
+    const unsigned long long *mx;
+};
+
+__device__ __forceinline__ int sq(int v) { return v * v; }
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T *__restrict__ u,
+                                                         T *__restrict__ Lu)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n, L = a.L;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)((i / n) % n) : 0;
+    const int iz = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+    const int X = 2 * ix + 1, Y = 2 * iy + 1, Z = 2 * iz + 1;
+    const int T4 = a.thr4[i];
+    const int r0 = isqrt_fast(T4);
+    long long G = 0;
+    for (int l = 0; l <= L; ++l) {
+        const int np = 1 << l;
+        const int sh = L - l + 1;          // panel size 2^sh half-units
+        const bool leaf = (l == L);
+        const long long *lev = a.pyr + a.lvl_off[l];
+        // distances from the node to panel k's interval along one axis (half-units):
+        //   far(k) = max(|k S - X|, |(k+1) S - X|), near(k) = gap or 0
+        int ylo = 0, yhi = 0, zlo = 0, zhi = 0;
+        if (D > 1) {
+            ylo = max(0, leaf ? ((Y - r0) >> sh) : -((r0 - Y) >> sh));
+            yhi = min(np - 1, ((Y + r0) >> sh) - (leaf ? 0 : 1));
+            if (leaf) ylo = max(0, -((r0 - Y) >> sh) - 1);
+        }
+        if (D > 2) {
+            zlo = leaf ? max(0, -((r0 - Z) >> sh) - 1) : max(0, -((r0 - Z) >> sh));
+            zhi = min(np - 1, ((Z + r0) >> sh) - (leaf ? 0 : 1));
+        }
+        for (int kz = zlo; kz <= zhi; ++kz) {
+            const int z0 = (kz << sh) - Z, z1 = z0 + (1 << sh);
+            const int ez = D > 2 ? (leaf ? (z0 > 0 ? sq(z0) : (z1 < 0 ? sq(z1) : 0))
+                                         : max(sq(z0), sq(z1))) : 0;
+            const int pz0 = ((kz >> 1) << (sh + 1)) - Z, pz1 = pz0 + (2 << sh);
+            const int epz = D > 2 ? max(sq(pz0), sq(pz1)) : 0;
+            for (int ky = ylo; ky <= yhi; ++ky) {
+                const int y0 = (ky << sh) - Y, y1 = y0 + (1 << sh);
+                int e = ez;
+                if (D > 1) e += leaf ? (y0 > 0 ? sq(y0) : (y1 < 0 ? sq(y1) : 0))
+                                     : max(sq(y0), sq(y1));
+                if (e > T4) continue;
+                const int r = isqrt_fast(T4 - e);
+                int ka, kb;
+                if (leaf) {
+                    ka = max(0, -((r - X) >> sh) - 1);
+                    kb = min(np - 1, (X + r) >> sh);
+                } else {
+                    ka = max(0, -((r - X) >> sh));
+                    kb = min(np - 1, ((X + r) >> sh) - 1);
+                }
+                if (ka > kb) continue;
+                int pa = 1, pb = 0;               // parent row's fully-inside panels
+                if (l > 0) {
+                    const int py0 = ((ky >> 1) << (sh + 1)) - Y, py1 = py0 + (2 << sh);
+                    const int ep = epz + (D > 1 ? max(sq(py0), sq(py1)) : 0);
+                    if (ep <= T4) {
+                        const int rp = isqrt_fast(T4 - ep);
+                        const int qa = max(0, -((rp - X) >> (sh + 1)));
+                        const int qb = min((np >> 1) - 1, ((X + rp) >> (sh + 1)) - 1);
+                        if (qa <= qb) { pa = 2 * qa; pb = 2 * qb + 1; }
+                    }
+                }
+                const long long *row = lev + (int64_t)np * (ky + (int64_t)np * kz);
+                const int e1 = min(kb, pa - 1);
+                for (int k = ka; k <= e1; ++k) G += row[k];
+                for (int k = max(ka, pb + 1); k <= kb; ++k) G += row[k];
+            }
+        }
+    }
+    const int sh = fixed_shift(a.N, a.mx);
+    const double Gd = ldexp((double)G, -sh);
+    Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -445,6 +605,7 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     if ((s = alloc((void **)&p->fastF, p->N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->selfS, p->N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->ir4, p->N * sizeof(double))) != NL_OK) return s;
+    if (K == 0 && (s = alloc((void **)&p->fast_mx, sizeof(unsigned long long))) != NL_OK) return s;
     double *d_pc = nullptr;
     if ((s = alloc((void **)&d_pc, 8 * sizeof(double))) != NL_OK) return s;
     NL_CUDA_TRY(cudaMemcpyAsync(p->shift, shift.data(), shift.size() * sizeof(double),
@@ -464,9 +625,42 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     return NL_OK;
 }
 
+static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_t st)
+{
+    const int d = p->d, L = p->L;
+    long long *pyr = (long long *)p->pyr;           // same buffer, 8-byte entries (M = 1)
+    unsigned long long *mx = p->fast_mx;
+    const unsigned gb = (unsigned)((p->N + 255) / 256);
+    NL_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    const unsigned gm = (unsigned)((p->N + 255) / 256 < 1216 ? (p->N + 255) / 256 : 1216);
+    k_absmax<float><<<gm, 256, 0, st>>>(p->N, u, p->b64, mx);
+    long long *leaf = pyr + p->lvl_off[L];
+    k_pyr_leaf_i64<float><<<gb, 256, 0, st>>>(p->N, u, p->b64, mx, leaf);
+    for (int l = L - 1; l >= 0; --l) {
+        int64_t P = 1;
+        for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
+        const long long *child = pyr + p->lvl_off[l + 1];
+        k_pyr_level_i64<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(d, l, child, pyr + p->lvl_off[l]);
+    }
+    FastI64Args a;
+    a.n = p->n; a.L = L; a.N = p->N;
+    a.thr4 = p->thr4; a.fastF = p->fastF; a.selfS = p->selfS;
+    a.pyr = pyr;
+    for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
+    a.hd = std::pow(p->h, (double)d);
+    a.mx = mx;
+    if (d == 1) k_fast_gather_i64<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    else if (d == 2) k_fast_gather_i64<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
 template <typename T>
 static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
 {
+    if (sizeof(T) == 4 && p->K == 0 && p->fast_mx)
+        return fast_one_i64(p, (const float *)u, (float *)Lu, st);
     const int d = p->d, L = p->L, M = p->M;
     double *leaf = p->pyr + p->lvl_off[L];
     const unsigned gb = (unsigned)((p->N + 255) / 256);

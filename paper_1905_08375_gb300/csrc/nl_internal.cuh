@@ -46,6 +46,10 @@ struct nl_plan {
     int stage;              // 1: direct kernels stage a halo tile in shared memory
     size_t smem_bytes32, smem_bytes64;
     int tile_sx, tile_sy, tile_sz;   // halo tile extents
+    int rb2d;                       // 2-D register-blocked direct kernel usable
+    size_t rb_smem32, rb_smem64, x2_smem;
+    float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
+    int *thr_reach;                 // symmetric variant: max threshold over the window
     // per-node device arrays
     int *thr;               // largest integer < R2_i
     int *cnt;               // table entries with o2 <= thr_i (or the symmetric bound)
@@ -70,6 +74,7 @@ struct nl_plan {
     double *shift;                  // Step 2 re-centring table [2^d][M][M]
     int *malpha;                    // multi-indices [M][3]
     int pyr_rhs;                    // right-hand sides the pyramid buffer holds
+    unsigned long long *fast_mx;    // max |v| of the last FP32 apply (fixed-point scale)
     // CG workspace (allocated on the first nl_cg_solve, grown for more right-hand sides)
     double *cg_ws; size_t cg_ws_elems;
     float *cg_ws32; size_t cg_ws32_elems;

@@ -425,6 +425,16 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     p->smem_bytes32 = tile_elems * e32;
     p->smem_bytes64 = tile_elems * e64;
     p->stage = (p->smem_bytes64 <= 200 * 1024) ? 1 : 0;
+    if (d == 2 && k->family != NL_PD_BOND) {
+        // register-blocked kernel: (32 + 2R) x (32 + 2R + 8) tile + (2R+1)^2 weights
+        const size_t t = (size_t)(32 + 2 * B) * (32 + 2 * B + 8);
+        const size_t gw = (size_t)(2 * B + 1) * (2 * B + 1);
+        p->rb_smem32 = t * e32 + gw * sizeof(float);
+        p->rb_smem64 = t * e64 + gw * sizeof(double);
+        p->rb2d = (p->rb_smem64 <= 200 * 1024) ? 1 : 0;
+        // paired-column FP32 kernel: u and b planes of (64 + 2R) x (32 + 2R + 8) + weights
+        p->x2_smem = (size_t)(64 + 2 * B) * (32 + 2 * B + 8) * 2 * sizeof(float) + gw * sizeof(float);
+    }
 
     std::vector<OffEntry32> t32(offs.size());
     std::vector<OffEntry64> t64(offs.size());
@@ -456,7 +466,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     double *d_delta = nullptr, *d_a = nullptr, *d_g = nullptr;
     int *d_win = nullptr;
     auto fail_tmp = [&](nl_status s) {
-        free_tmp(d_delta, d_a, d_win, nullptr);
+        free_tmp(d_delta, d_a, nullptr, nullptr);
         if (d_g) cudaFree(d_g);
         nl_plan_destroy(p);
         return s;
@@ -523,6 +533,25 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         }
     }
 
+    if (p->rb2d) {
+        const int GW = 2 * B + 1;
+        std::vector<float> g32(GW * GW);
+        std::vector<double> gd(GW * GW);
+        for (int oy = -B; oy <= B; ++oy)
+            for (int ox = -B; ox <= B; ++ox) {
+                const int o2 = ox * ox + oy * oy;
+                const double g = (o2 == 0) ? 0.0 : std::pow((double)o2, -k->alpha / 2.0);
+                gd[(ox + B) * GW + oy + B] = g;
+                g32[(ox + B) * GW + oy + B] = (float)g;
+            }
+        NL_TMP_TRY(dev_alloc(p, &p->rb_g32, gd.size()));
+        NL_TMP_TRY(dev_alloc(p, &p->rb_g64, gd.size()));
+        ce = cudaMemcpyAsync(p->rb_g32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(p->rb_g64, gd.data(), gd.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "weight table upload"));
+    }
+
     PlanArgs pa;
     pa.d = d; pa.n = n; pa.family = k->family; pa.coef = k->coef; pa.symmetric = p->symmetric;
     pa.K = p->K; pa.N = N; pa.alpha = k->alpha; pa.sigma = p->sigma; pa.h = p->h;
@@ -535,10 +564,8 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     if (want_fast) NL_TMP_TRY(dev_alloc(p, &p->thr4, N));
     k_thresholds<<<GB, TB, 0, st>>>(pa, d_delta, p->thr, want_fast ? p->thr4 : nullptr);
     if (p->symmetric) {
-        if (cudaMalloc(&d_win, N * sizeof(int)) != cudaSuccess) {
-            nl_set_error("cudaMalloc failed for the window bound");
-            return fail_tmp(NL_ENOMEM);
-        }
+        NL_TMP_TRY(dev_alloc(p, &p->thr_reach, N));
+        d_win = p->thr_reach;
         k_window_max<<<GB, TB, 0, st>>>(pa, p->thr, d_win);
     }
     k_node_factors<<<GB, TB, 0, st>>>(pa, d_delta, d_a, p->thr, d_win, p->off, d_g, p->cnt,
@@ -551,7 +578,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     if (want_fast) NL_TMP_TRY(nl_fast_plan_init(p, d_delta, d_a, st));
     ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan synchronise"));
-    free_tmp(d_delta, d_a, d_win, nullptr);
+    free_tmp(d_delta, d_a, nullptr, nullptr);
     cudaFree(d_g);
     *out = p;
     return NL_OK;
@@ -569,7 +596,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
     void *ptrs[] = { p->thr, p->cnt, p->b32, p->b64, p->fin32, p->fin64, p->ext32, p->ext64,
                      p->wh32, p->wh64, p->ir32, p->ir64, p->off, p->tab32, p->tab64, p->pd32,
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
-                     p->malpha, p->dinv64 };
+                     p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx };
     for (void *q : ptrs) if (q) cudaFree(q);
     nl_cg_release(p);
     p->magic = 0;
