@@ -201,6 +201,14 @@ def run_gpu(args, peaks):
     reps = max(3, min(args.steps, 50))
     t_direct = time_fn(lambda: nl.nl_apply(direct, u, out_d), reps)
     t_fast = time_fn(lambda: nl.nl_apply_fast(fast, u, out_f), reps)
+    fast_pan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
+                                 coef=nl.NL_COEF_XY, a=f["a"], fast_variant=nl.NL_FAST_PANELS)
+    fast_f64 = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
+                                 coef=nl.NL_COEF_XY, a=f["a"],
+                                 fast_variant=nl.NL_FAST_FP64_PANELS)
+    t_fast_pan = time_fn(lambda: nl.nl_apply_fast(fast_pan, u, out_f), reps)
+    t_fast_f64 = time_fn(lambda: nl.nl_apply_fast(fast_f64, u, out_f), reps)
+    nl.nl_apply_fast(fast, u, out_f)
     u64 = u.double()
     o64 = torch.empty_like(u64)
     t_direct64 = time_fn(lambda: nl.nl_apply(direct, u64, o64), max(3, reps // 2))
@@ -248,9 +256,13 @@ def run_gpu(args, peaks):
                 "n": n, "points": N, "l2": "flushed (256 MiB write) before every timed step",
                 "parallelism": f"replicas x{ws}"},
         per_path_gpts={"direct_fp32": round(N / (t_direct * 1e-3) / 1e9, 4),
-                       "fast_k0": round(N / (t_fast * 1e-3) / 1e9, 4),
+                       "fast_k0_rowprefix": round(N / (t_fast * 1e-3) / 1e9, 4),
+                       "fast_k0_panels_int": round(N / (t_fast_pan * 1e-3) / 1e9, 4),
+                       "fast_k0_panels_fp64": round(N / (t_fast_f64 * 1e-3) / 1e9, 4),
                        "direct_fp64": round(N / (t_direct64 * 1e-3) / 1e9, 4)},
-        per_path_ms={"direct_fp32": round(t_direct, 4), "fast_k0": round(t_fast, 4),
+        per_path_ms={"direct_fp32": round(t_direct, 4), "fast_k0_rowprefix": round(t_fast, 4),
+                     "fast_k0_panels_int": round(t_fast_pan, 4),
+                     "fast_k0_panels_fp64": round(t_fast_f64, 4),
                      "direct_fp64": round(t_direct64, 4)},
         roofline=roofline, e2e=e2e,
         gpu_launches=args.steps * (1 + 2 + fast.info()["levels"]),

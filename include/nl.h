@@ -80,6 +80,17 @@ typedef enum { NL_COEF_NONE = 0, NL_COEF_X = 1, NL_COEF_XY = 2, NL_COEF_MEAN = 3
  *       (Example 1 of Sec. 4); not defined for NL_COEF_XY. */
 typedef enum { NL_SELF_DISCRETE = 0, NL_SELF_PAPER = 1 } nl_self;
 
+/* How nl_apply_fast forms the Step 2/3 sums for K = 0 with FP32 data (FP64 data and K > 0
+ * always use FP64 panel moments summed panel by panel):
+ *   NL_FAST_AUTO (0) = NL_FAST_ROWPREFIX
+ *   NL_FAST_PANELS (1): exact 64-bit fixed-point panel sums (one rounding of each leaf value
+ *       to a multiple of 2^-S chosen from max |a u|), added panel by panel;
+ *   NL_FAST_ROWPREFIX (2): the same integers kept as prefix sums along each panel row, so the
+ *       panels of a run are added as one difference -- bitwise the same result;
+ *   NL_FAST_FP64_PANELS (3): FP64 panel sums added panel by panel, as for FP64 data. */
+typedef enum { NL_FAST_AUTO = 0, NL_FAST_PANELS = 1, NL_FAST_ROWPREFIX = 2,
+               NL_FAST_FP64_PANELS = 3 } nl_fast_variant;
+
 typedef struct {
     int dim;   /* d in {1, 2, 3} */
     int n;     /* nodes per dimension; the fast path needs n = 2^L */
@@ -103,6 +114,7 @@ typedef struct {
     int coef;          /* nl_coef */
     const double *a;   /* HOST pointer, n^d coefficient values (a or c), or NULL */
     int self_term;     /* nl_self, nl_apply_fast only */
+    int fast_variant;  /* nl_fast_variant, nl_apply_fast only */
 } nl_kernel;
 
 typedef struct nl_plan nl_plan;

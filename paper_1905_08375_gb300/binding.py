@@ -20,6 +20,7 @@ NL_F32, NL_F64 = 0, 1
 NL_POWER, NL_POLY, NL_PD_BOND = 0, 1, 2
 NL_COEF_NONE, NL_COEF_X, NL_COEF_XY, NL_COEF_MEAN = 0, 1, 2, 3
 NL_SELF_DISCRETE, NL_SELF_PAPER = 0, 1
+NL_FAST_AUTO, NL_FAST_PANELS, NL_FAST_ROWPREFIX, NL_FAST_FP64_PANELS = 0, 1, 2, 3
 NL_PRECOND_NONE, NL_PRECOND_JACOBI = 0, 1
 
 _STATUS = {0: "NL_OK", 1: "NL_EINVAL", 2: "NL_EUNSUPPORTED", 3: "NL_ENOMEM", 4: "NL_ECUDA",
@@ -44,7 +45,8 @@ class nl_horizon(ctypes.Structure):
 class nl_kernel(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int), ("alpha", ctypes.c_double), ("K", ctypes.c_int),
                 ("scale", ctypes.c_double), ("normalize", ctypes.c_int), ("coef", ctypes.c_int),
-                ("a", ctypes.c_void_p), ("self_term", ctypes.c_int)]
+                ("a", ctypes.c_void_p), ("self_term", ctypes.c_int),
+                ("fast_variant", ctypes.c_int)]
 
 
 class nl_cg_stats(ctypes.Structure):
@@ -145,7 +147,7 @@ class Plan:
 
 def nl_plan_create(dim, n, delta, family=NL_POWER, alpha=0.0, K=0, scale=1.0, normalize=True,
                    coef=NL_COEF_NONE, a=None, symmetric=False, self_term=NL_SELF_DISCRETE,
-                   stream=None) -> Plan:
+                   fast_variant=NL_FAST_AUTO, stream=None) -> Plan:
     """Create a plan.  `delta`: scalar or host array of n^dim values; `a`: host array or None."""
     g = nl_grid(dim, n)
     keep = []
@@ -165,7 +167,7 @@ def nl_plan_create(dim, n, delta, family=NL_POWER, alpha=0.0, K=0, scale=1.0, no
         keep.append(aa)
         ap = aa.ctypes.data
     k = nl_kernel(int(family), float(alpha), int(K), float(scale), int(bool(normalize)),
-                  int(coef), ap, int(self_term))
+                  int(coef), ap, int(self_term), int(fast_variant))
     h = ctypes.c_void_p()
     st = _stream_ptr(stream) if _cuda_ready() else ctypes.c_void_p(None)
     _check(lib().nl_plan_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(hz),

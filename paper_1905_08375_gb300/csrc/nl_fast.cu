@@ -529,6 +529,131 @@ __global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T 
     Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
 }
 
+// ---------------------------------------------------------------------------
+// Row-prefix form of the integer partial sums: at every level, P[k] holds the sum of the
+// panels 0..k of its panel row, so the panels ka..kb of a run add up to P[kb] - P[ka-1],
+// exactly the same integer as adding them one by one.  The leaf rows are scanned; a
+// parent's prefix is the sum of its child rows' prefixes at the odd positions.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_leaf_scan_i64(int n, long long *rows)
+{
+    __shared__ long long s_warp[8];
+    long long *row = rows + (int64_t)blockIdx.x * n;
+    const int per = (n + 255) / 256;
+    const int beg = threadIdx.x * per, end = min(n, beg + per);
+    long long tot = 0;
+    for (int k = beg; k < end; ++k) tot += row[k];
+    // exclusive scan of the thread totals (warp shuffles, then warp totals)
+    long long incl = tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    long long off = incl - tot;
+    for (int k = 0; k < w; ++k) off += s_warp[k];
+    for (int k = beg; k < end; ++k) { off += row[k]; row[k] = off; }
+}
+
+__global__ void k_level_prefix_i64(int d, int l, const long long *__restrict__ child,
+                                   long long *__restrict__ parent)
+{
+    const int np = 1 << l;
+    int64_t P = np;
+    if (d > 1) P *= np;
+    if (d > 2) P *= np;
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= P) return;
+    const int kx = (int)(f % np);
+    const int ky = d > 1 ? (int)((f / np) % np) : 0;
+    const int kz = d > 2 ? (int)(f / ((int64_t)np * np)) : 0;
+    const int nc = 2 * np;
+    long long s = 0;
+    for (int c = 0; c < (1 << (d - 1)); ++c) {
+        const int cy = d > 1 ? 2 * ky + (c & 1) : 0;
+        const int cz = d > 2 ? 2 * kz + ((c >> 1) & 1) : 0;
+        s += child[(2 * kx + 1) + (int64_t)nc * (cy + (int64_t)nc * cz)];
+    }
+    parent[f] = s;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
+                                                               const T *__restrict__ u,
+                                                               T *__restrict__ Lu)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n, L = a.L;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)((i / n) % n) : 0;
+    const int iz = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+    const int X = 2 * ix + 1, Y = 2 * iy + 1, Z = 2 * iz + 1;
+    const int T4 = a.thr4[i];
+    const int r0 = isqrt_fast(T4);
+    long long G = 0;
+    for (int l = 0; l <= L; ++l) {
+        const int np = 1 << l;
+        const int sh = L - l + 1;
+        const bool leaf = (l == L);
+        const long long *lev = a.pyr + a.lvl_off[l];
+        int ylo = 0, yhi = 0, zlo = 0, zhi = 0;
+        if (D > 1) {
+            ylo = max(0, -((r0 - Y) >> sh) - (leaf ? 1 : 0));
+            yhi = min(np - 1, ((Y + r0) >> sh) - (leaf ? 0 : 1));
+        }
+        if (D > 2) {
+            zlo = max(0, -((r0 - Z) >> sh) - (leaf ? 1 : 0));
+            zhi = min(np - 1, ((Z + r0) >> sh) - (leaf ? 0 : 1));
+        }
+        for (int kz = zlo; kz <= zhi; ++kz) {
+            const int z0 = (kz << sh) - Z, z1 = z0 + (1 << sh);
+            const int ez = D > 2 ? (leaf ? (z0 > 0 ? sq(z0) : (z1 < 0 ? sq(z1) : 0))
+                                         : max(sq(z0), sq(z1))) : 0;
+            const int pz0 = ((kz >> 1) << (sh + 1)) - Z, pz1 = pz0 + (2 << sh);
+            const int epz = D > 2 ? max(sq(pz0), sq(pz1)) : 0;
+            for (int ky = ylo; ky <= yhi; ++ky) {
+                const int y0 = (ky << sh) - Y, y1 = y0 + (1 << sh);
+                int e = ez;
+                if (D > 1) e += leaf ? (y0 > 0 ? sq(y0) : (y1 < 0 ? sq(y1) : 0))
+                                     : max(sq(y0), sq(y1));
+                if (e > T4) continue;
+                const int r = isqrt_fast(T4 - e);
+                int ka, kb;
+                if (leaf) {
+                    ka = max(0, -((r - X) >> sh) - 1);
+                    kb = min(np - 1, (X + r) >> sh);
+                } else {
+                    ka = max(0, -((r - X) >> sh));
+                    kb = min(np - 1, ((X + r) >> sh) - 1);
+                }
+                int pa = kb + 1, pb = kb;           // parent-full panels (empty: beyond kb)
+                if (l > 0) {
+                    const int py0 = ((ky >> 1) << (sh + 1)) - Y, py1 = py0 + (2 << sh);
+                    const int ep = epz + (D > 1 ? max(sq(py0), sq(py1)) : 0);
+                    if (ep <= T4) {
+                        const int rp = isqrt_fast(T4 - ep);
+                        const int qa = max(0, -((rp - X) >> (sh + 1)));
+                        const int qb = min((np >> 1) - 1, ((X + rp) >> (sh + 1)) - 1);
+                        if (qa <= qb) { pa = 2 * qa; pb = 2 * qb + 1; }
+                    }
+                }
+                const long long *row = lev + (int64_t)np * (ky + (int64_t)np * kz);
+                // runs [ka, min(kb, pa-1)] and [max(ka, pb+1), kb], summed as prefix differences
+                const int a1 = ka, b1 = min(kb, pa - 1);
+                const int a2 = max(ka, pb + 1), b2 = kb;
+                if (a1 <= b1) G += row[b1] - (a1 > 0 ? row[a1 - 1] : 0LL);
+                if (a2 <= b2) G += row[b2] - (a2 > 0 ? row[a2 - 1] : 0LL);
+            }
+        }
+    }
+    const int sh = fixed_shift(a.N, a.mx);
+    const double Gd = ldexp((double)G, -sh);
+    Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -636,11 +761,23 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     k_absmax<float><<<gm, 256, 0, st>>>(p->N, u, p->b64, mx);
     long long *leaf = pyr + p->lvl_off[L];
     k_pyr_leaf_i64<float><<<gb, 256, 0, st>>>(p->N, u, p->b64, mx, leaf);
-    for (int l = L - 1; l >= 0; --l) {
+    for (int l = L - 1; l >= 0 && p->fast_variant == NL_FAST_PANELS; --l) {
         int64_t P = 1;
         for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
         const long long *child = pyr + p->lvl_off[l + 1];
         k_pyr_level_i64<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(d, l, child, pyr + p->lvl_off[l]);
+    }
+    const bool prefix = p->fast_variant != NL_FAST_PANELS;
+    if (prefix) {
+        // leaf rows scanned in place, then each level from its children's prefixes
+        const int64_t rows = p->N / p->n;
+        k_leaf_scan_i64<<<(unsigned)rows, 256, 0, st>>>(p->n, leaf);
+        for (int l = L - 1; l >= 0; --l) {
+            int64_t P = 1;
+            for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
+            k_level_prefix_i64<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
+                d, l, pyr + p->lvl_off[l + 1], pyr + p->lvl_off[l]);
+        }
     }
     FastI64Args a;
     a.n = p->n; a.L = L; a.N = p->N;
@@ -649,9 +786,15 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     a.hd = std::pow(p->h, (double)d);
     a.mx = mx;
-    if (d == 1) k_fast_gather_i64<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
-    else if (d == 2) k_fast_gather_i64<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
-    else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    if (prefix) {
+        if (d == 1) k_fast_gather_rowprefix<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else if (d == 2) k_fast_gather_rowprefix<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else k_fast_gather_rowprefix<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    } else {
+        if (d == 1) k_fast_gather_i64<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else if (d == 2) k_fast_gather_i64<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    }
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
@@ -659,7 +802,7 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
 template <typename T>
 static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
 {
-    if (sizeof(T) == 4 && p->K == 0 && p->fast_mx)
+    if (sizeof(T) == 4 && p->K == 0 && p->fast_mx && p->fast_variant != NL_FAST_FP64_PANELS)
         return fast_one_i64(p, (const float *)u, (float *)Lu, st);
     const int d = p->d, L = p->L, M = p->M;
     double *leaf = p->pyr + p->lvl_off[L];

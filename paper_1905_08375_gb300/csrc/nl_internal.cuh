@@ -35,7 +35,7 @@ struct nl_plan {
     // problem
     int d, n, L;            // L = log2 n or -1
     int64_t N;
-    int family, coef, symmetric, self_mode, K;
+    int family, coef, symmetric, self_mode, K, fast_variant;
     double alpha, scale, sigma, h;
     double poly[8];
     // horizon summary

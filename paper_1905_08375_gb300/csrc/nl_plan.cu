@@ -369,6 +369,12 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     for (int l = 0; l <= NL_MAX_LEVELS; ++l) if ((1 << l) == n) p->L = l;
     p->family = k->family; p->coef = k->coef; p->symmetric = hz->symmetric ? 1 : 0;
     p->self_mode = k->self_term; p->K = (k->family == NL_POLY) ? k->K : 0;
+    if (k->fast_variant < NL_FAST_AUTO || k->fast_variant > NL_FAST_FP64_PANELS) {
+        nl_set_error("nl_plan_create: unknown fast variant %d", k->fast_variant);
+        free(p);
+        return NL_EINVAL;
+    }
+    p->fast_variant = k->fast_variant == NL_FAST_AUTO ? NL_FAST_ROWPREFIX : k->fast_variant;
     p->alpha = k->alpha; p->scale = k->scale; p->h = 1.0 / n;
     if (k->family == NL_PD_BOND || !k->normalize)
         p->sigma = k->scale;

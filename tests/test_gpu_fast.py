@@ -128,3 +128,24 @@ def test_unsupported_requests():
     u3 = torch.zeros(512, dtype=torch.float64, device=DEV)
     with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
         nl.nl_apply_fast(p3, u3, torch.empty_like(u3))
+
+
+@pytest.mark.parametrize("d,n", [(1, 2048), (2, 128), (2, 256), (3, 32)])
+def test_integer_routes_bitwise_equal_and_match_oracle(d, n):
+    """FP32, K = 0: the row-prefix and the panel-by-panel fixed-point routes add the same
+    integers, so their outputs are bitwise equal; both match the FP64 oracle."""
+    L = int(np.log2(n))
+    rng = np.random.default_rng(40 + d)
+    N = n ** d
+    rho = rng.uniform(1.5, 0.25 * n if d < 3 else 3.5, size=N)
+    a = np.exp(0.3 * rng.standard_normal(N))
+    u = rng.standard_normal(N)
+    outs = []
+    for variant in (nl.NL_FAST_ROWPREFIX, nl.NL_FAST_PANELS, nl.NL_FAST_FP64_PANELS):
+        plan = nl.nl_plan_create(d, n, rho / n, family=nl.NL_POLY, alpha=1.0, K=0,
+                                 coef=nl.NL_COEF_XY, a=a, fast_variant=variant)
+        outs.append(run_fast(plan, u, torch.float32))
+    np.testing.assert_array_equal(outs[0], outs[1])
+    ref = oracle.fast_leafset(u, d, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a)
+    for o in outs:
+        assert rel_l2(o, ref) <= 2e-6
