@@ -375,47 +375,53 @@ __global__ void k_fast_node(int d, int n, int K, int coef, int self_mode, int64_
 // multiple of 2^-S and every partial sum of any set of leaves is then exact (|sum| < 2^62).
 // Step 3 adds the integer panel sums of the decomposition exactly, panel by panel.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int isqrt_fast(int x)     // floor(sqrt(x)) for 0 <= x < 2^30
+// floor(sqrt(x)) for 0 <= x < 2^30: one approximate reciprocal square root (relative error
+// well below 2^-20, so the estimate is within 1 of the answer), then exact integer corrections
+__device__ __forceinline__ int isqrt_fast(int x)
 {
-    int h = (int)sqrtf((float)x);
+    const float f = (float)max(x, 1);
+    int h = __float2int_rz(f * rsqrtf(f));
     h -= (h * h > x);
-    h -= (h * h > x);
-    h += ((h + 1) * (h + 1) <= x);
     h += ((h + 1) * (h + 1) <= x);
     return h;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_absmax(int64_t N, const T *__restrict__ u,
-                                                const double *__restrict__ b,
-                                                unsigned long long *out)
+// max |u b| in FP32 (b32 = b rounded to FP32), enlarged by 2^-20 relative so that it bounds
+// the FP32 products used below
+__global__ void __launch_bounds__(256) k_absmax_f32(int64_t N, const float *__restrict__ u,
+                                                    const float *__restrict__ b,
+                                                    unsigned int *out)
 {
-    double m = 0.0;
+    float m = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs((double)u[i] * b[i]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+        m = fmaxf(m, fabsf(u[i] * b[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m * (1.f + 0x1p-20f)));
 }
 
-__device__ __forceinline__ int fixed_shift(int64_t N, const unsigned long long *mx)
+// scale exponent S with N * max|v| * 2^S < 2^62, from the FP32 bound
+__device__ __forceinline__ int fixed_shift_f32(int64_t N, const unsigned int *mx)
 {
-    const double m = __longlong_as_double((long long)*mx);
-    if (!(m > 0.0)) return 62;
-    int e;
-    frexp((double)N * m, &e);          // N m < 2^e
-    return 62 - e;
+    const float m = __uint_as_float(*mx);
+    if (!(m > 0.f)) return 62;
+    int e1, e2;
+    frexpf(m, &e1);                     // m < 2^e1
+    frexpf((float)N, &e2);              // N < 2^e2
+    return 62 - e1 - e2;
 }
 
-template <typename T>
-__global__ void k_pyr_leaf_i64(int64_t N, const T *__restrict__ u, const double *__restrict__ b,
-                               const unsigned long long *mx, long long *leaf)
+// leaf value v = fl32(u b32) as the integer round(v 2^S) (the product 2^S v is exact in FP32)
+__global__ void k_pyr_leaf_f32i64(int64_t N, const float *__restrict__ u,
+                                  const float *__restrict__ b, const unsigned int *mx,
+                                  long long *leaf)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int sh = fixed_shift(N, mx);
-    leaf[i] = __double2ll_rn(ldexp((double)u[i] * b[i], sh));
+    const int sh = fixed_shift_f32(N, mx);
+    leaf[i] = __float2ll_rn(ldexpf(u[i] * b[i], sh));
 }
+
 
 __global__ void k_pyr_level_i64(int d, int l, const long long *__restrict__ child,
                                 long long *__restrict__ parent)
@@ -448,7 +454,7 @@ struct FastI64Args {
     const long long *pyr;                  // levels 0..L (leaf level last), panel-major
     int64_t lvl_off[NL_MAX_LEVELS + 2];
     double hd;
-    const unsigned long long *mx;
+    const unsigned int *mx;
 };
 
 __device__ __forceinline__ int sq(int v) { return v * v; }
@@ -524,7 +530,7 @@ __global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T 
             }
         }
     }
-    const int sh = fixed_shift(a.N, a.mx);
+    const int sh = fixed_shift_f32(a.N, a.mx);
     const double Gd = ldexp((double)G, -sh);
     Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
 }
@@ -594,7 +600,10 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
     const int T4 = a.thr4[i];
     const int r0 = isqrt_fast(T4);
     long long G = 0;
-    for (int l = 0; l <= L; ++l) {
+    // a panel of side 2^sh half-units fits in the ball only if 2^sh <= 2 r0
+    int lmin = 0;
+    while (lmin < L && (1 << (L - lmin + 1)) > 2 * r0) ++lmin;
+    for (int l = lmin; l <= L; ++l) {
         const int np = 1 << l;
         const int sh = L - l + 1;
         const bool leaf = (l == L);
@@ -614,6 +623,7 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
                                          : max(sq(z0), sq(z1))) : 0;
             const int pz0 = ((kz >> 1) << (sh + 1)) - Z, pz1 = pz0 + (2 << sh);
             const int epz = D > 2 ? max(sq(pz0), sq(pz1)) : 0;
+            int pm = -1, ppa = 1 << 30, ppb = -1;
             for (int ky = ylo; ky <= yhi; ++ky) {
                 const int y0 = (ky << sh) - Y, y1 = y0 + (1 << sh);
                 int e = ez;
@@ -629,17 +639,21 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
                     ka = max(0, -((r - X) >> sh));
                     kb = min(np - 1, ((X + r) >> sh) - 1);
                 }
-                int pa = kb + 1, pb = kb;           // parent-full panels (empty: beyond kb)
-                if (l > 0) {
-                    const int py0 = ((ky >> 1) << (sh + 1)) - Y, py1 = py0 + (2 << sh);
+                // parent row's fully-inside panels (child units); shared by the two child rows
+                if (l > 0 && (ky >> 1) != pm) {
+                    pm = ky >> 1;
+                    ppa = 1 << 30; ppb = -1;
+                    const int py0 = (pm << (sh + 1)) - Y, py1 = py0 + (2 << sh);
                     const int ep = epz + (D > 1 ? max(sq(py0), sq(py1)) : 0);
                     if (ep <= T4) {
                         const int rp = isqrt_fast(T4 - ep);
                         const int qa = max(0, -((rp - X) >> (sh + 1)));
                         const int qb = min((np >> 1) - 1, ((X + rp) >> (sh + 1)) - 1);
-                        if (qa <= qb) { pa = 2 * qa; pb = 2 * qb + 1; }
+                        if (qa <= qb) { ppa = 2 * qa; ppb = 2 * qb + 1; }
                     }
                 }
+                int pa = kb + 1, pb = kb;           // empty: beyond kb
+                if (l > 0 && ppa <= ppb) { pa = ppa; pb = ppb; }
                 const long long *row = lev + (int64_t)np * (ky + (int64_t)np * kz);
                 // runs [ka, min(kb, pa-1)] and [max(ka, pb+1), kb], summed as prefix differences
                 const int a1 = ka, b1 = min(kb, pa - 1);
@@ -649,7 +663,7 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
             }
         }
     }
-    const int sh = fixed_shift(a.N, a.mx);
+    const int sh = fixed_shift_f32(a.N, a.mx);
     const double Gd = ldexp((double)G, -sh);
     Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
 }
@@ -754,13 +768,13 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
 {
     const int d = p->d, L = p->L;
     long long *pyr = (long long *)p->pyr;           // same buffer, 8-byte entries (M = 1)
-    unsigned long long *mx = p->fast_mx;
+    unsigned int *mx = (unsigned int *)p->fast_mx;
     const unsigned gb = (unsigned)((p->N + 255) / 256);
-    NL_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    NL_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), st));
     const unsigned gm = (unsigned)((p->N + 255) / 256 < 1216 ? (p->N + 255) / 256 : 1216);
-    k_absmax<float><<<gm, 256, 0, st>>>(p->N, u, p->b64, mx);
+    k_absmax_f32<<<gm, 256, 0, st>>>(p->N, u, p->b32, mx);
     long long *leaf = pyr + p->lvl_off[L];
-    k_pyr_leaf_i64<float><<<gb, 256, 0, st>>>(p->N, u, p->b64, mx, leaf);
+    k_pyr_leaf_f32i64<<<gb, 256, 0, st>>>(p->N, u, p->b32, mx, leaf);
     for (int l = L - 1; l >= 0 && p->fast_variant == NL_FAST_PANELS; --l) {
         int64_t P = 1;
         for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
