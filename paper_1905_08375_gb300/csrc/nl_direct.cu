@@ -277,7 +277,7 @@ k_direct_pd(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
 // ---------------------------------------------------------------------------
 constexpr int RB_TY = 4, RB_P = 8;
 
-template <typename T, int MODE>
+template <typename T, int MODE, int RP>
 __global__ void __launch_bounds__(32 * RB_TY)
 k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u, T *__restrict__ Lu)
 {
@@ -285,7 +285,7 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, R = a.R;
     const int SX = 32 + 2 * R;                       // tile width
-    const int SY = RB_TY * RB_P + 2 * R + RB_P;      // tile height (RB_P spare rows)
+    const int SY = RB_TY * RP + 2 * R + RP;      // tile height (RP spare rows)
     const int GW = 2 * R + 1;
     Elem *tile = reinterpret_cast<Elem *>(smem_raw);
     T *s_g = reinterpret_cast<T *>(smem_raw + sizeof(Elem) * SX * SY);
@@ -293,7 +293,7 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
     const T *__restrict__ ur = u + (int64_t)blockIdx.z * N;
     const T *__restrict__ bb = (const T *)a.b;
     const T *__restrict__ whv = (const T *)a.wh;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * (RB_TY * RB_P);
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * (RB_TY * RP);
     const int tid = threadIdx.x + 32 * threadIdx.y;
     for (int e = tid; e < SX * SY; e += 32 * RB_TY) {
         const int gx = x0 - R + e % SX, gy = y0 - R + e / SX;
@@ -315,25 +315,25 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
     __syncthreads();
 
     const int x = x0 + threadIdx.x;
-    const int ybase = y0 + threadIdx.y * RB_P;
-    T ui[RB_P], acc[RB_P], irp[RB_P], whp[RB_P];
-    int thr[RB_P];
+    const int ybase = y0 + threadIdx.y * RP;
+    T ui[RP], acc[RP], irp[RP], whp[RP];
+    int thr[RP];
     int tmax = -1;
 #pragma unroll
-    for (int p = 0; p < RB_P; ++p) {
+    for (int p = 0; p < RP; ++p) {
         const int y = ybase + p;
         const bool own = x < n && y < n;
         const int64_t i = own ? x + (int64_t)n * y : 0;
-        ui[p] = tile[(threadIdx.y * RB_P + p + R) * SX + threadIdx.x + R].u;
+        ui[p] = tile[(threadIdx.y * RP + p + R) * SX + threadIdx.x + R].u;
         thr[p] = own ? a.thr[i] : -1;
         irp[p] = (MODE == MODE_POLY && own) ? ((const T *)a.ir)[i] : T(0);
         whp[p] = (MODE == MODE_SYM && own) ? whv[i] : T(0);
         acc[p] = T(0);
     }
     // the symmetric kernel also reaches offsets inside the neighbours' balls
-    int reach[RB_P];
+    int reach[RP];
 #pragma unroll
-    for (int p = 0; p < RB_P; ++p) {
+    for (int p = 0; p < RP; ++p) {
         const int y = ybase + p;
         reach[p] = (MODE == MODE_SYM) ? ((x < n && y < n) ? a.cnt_thr[x + (int64_t)n * y] : -1)
                                       : thr[p];
@@ -341,7 +341,7 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
     }
     const int rx = min(R, (int)sqrtf((float)max(tmax, 0)) + 1);
     const int col0 = threadIdx.x + R;
-    const int row0 = threadIdx.y * RB_P + R;        // tile row of output p = row0 + p
+    const int row0 = threadIdx.y * RP + R;        // tile row of output p = row0 + p
 
     // one output's term for the window element v at offset (ox, oy); MASKED checks the
     // horizon, the unmasked core is only entered where every output's ball holds the row
@@ -364,7 +364,7 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
         // per-output half-heights of this column: |oy| <= h_p  <=>  ox^2 + oy^2 <= reach_p
         int hmin = R, hmax = -1;
 #pragma unroll
-        for (int p = 0; p < RB_P; ++p) {
+        for (int p = 0; p < RP; ++p) {
             int h = -1;
             const int rest = reach[p] - ox2;
             if (rest >= 0) {
@@ -380,47 +380,47 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
         if (MODE == MODE_SYM) hmin = -1;            // every term carries its own masks
         const Elem *colp = tile + col0 + ox;
         const T *gcol = s_g + (ox + R) * GW + R;
-        Elem W[RB_P];
+        Elem W[RP];
         int oy = -hmax;
 #pragma unroll
-        for (int k = 0; k < RB_P; ++k) W[k] = colp[(row0 + oy + k) * SX];
+        for (int k = 0; k < RP; ++k) W[k] = colp[(row0 + oy + k) * SX];
         // rows where some output's ball ends: single masked steps
         auto single = [&](int oyv) {
             const int o2 = ox2 + oyv * oyv;
             const T g = (MODE == MODE_POLY) ? T(1) : gcol[oyv];
 #pragma unroll
-            for (int p = 0; p < RB_P; ++p) term(p, W[p], o2, g, true);
+            for (int p = 0; p < RP; ++p) term(p, W[p], o2, g, true);
 #pragma unroll
-            for (int k = 0; k < RB_P - 1; ++k) W[k] = W[k + 1];
-            W[RB_P - 1] = colp[(row0 + oyv + RB_P) * SX];
+            for (int k = 0; k < RP - 1; ++k) W[k] = W[k + 1];
+            W[RP - 1] = colp[(row0 + oyv + RP) * SX];
         };
         for (; oy < -hmin && oy <= hmax; ++oy) single(oy);
-        // core: every output's ball holds rows -hmin .. hmin; unmasked chunks of RB_P rows
-        for (; oy + RB_P - 1 <= hmin; oy += RB_P) {
-            Elem X[RB_P - 1];
+        // core: every output's ball holds rows -hmin .. hmin; unmasked chunks of RP rows
+        for (; oy + RP - 1 <= hmin; oy += RP) {
+            Elem X[RP - 1];
 #pragma unroll
-            for (int k = 0; k < RB_P - 1; ++k) X[k] = colp[(row0 + oy + RB_P + k) * SX];
+            for (int k = 0; k < RP - 1; ++k) X[k] = colp[(row0 + oy + RP + k) * SX];
 #pragma unroll
-            for (int j = 0; j < RB_P; ++j) {
+            for (int j = 0; j < RP; ++j) {
                 const int oyj = oy + j;
                 const int o2 = ox2 + oyj * oyj;
                 const T g = (MODE == MODE_POLY) ? T(1) : gcol[oyj];
 #pragma unroll
-                for (int p = 0; p < RB_P; ++p) {
+                for (int p = 0; p < RP; ++p) {
                     const int k = p + j;
-                    term(p, k < RB_P ? W[k] : X[k - RB_P], o2, g, false);
+                    term(p, k < RP ? W[k] : X[k - RP], o2, g, false);
                 }
             }
 #pragma unroll
-            for (int k = 0; k < RB_P - 1; ++k) W[k] = X[k];
-            W[RB_P - 1] = colp[(row0 + oy + 2 * RB_P - 1) * SX];
+            for (int k = 0; k < RP - 1; ++k) W[k] = X[k];
+            W[RP - 1] = colp[(row0 + oy + 2 * RP - 1) * SX];
         }
         for (; oy <= hmax; ++oy) single(oy);
     }
     const T *__restrict__ finv = (const T *)a.fin;
     const T *__restrict__ extv = (const T *)a.ext;
 #pragma unroll
-    for (int p = 0; p < RB_P; ++p) {
+    for (int p = 0; p < RP; ++p) {
         const int y = ybase + p;
         if (x < n && y < n) {
             const int64_t i = x + (int64_t)n * y;
@@ -679,6 +679,77 @@ static nl_status launch_x2(nl_plan *p, const DirectArgs &a, const float *u, floa
 }
 
 // ---------------------------------------------------------------------------
+// Small grids: a group of SPLIT consecutive lanes shares one node; lane g takes the table
+// entries g, g + SPLIT, ... of the node's ball (neighbours read through L1), and the group's
+// partial sums are combined with shuffles (fixed order).
+// ---------------------------------------------------------------------------
+template <int D, typename T, int MODE, int SPLIT>
+__global__ void __launch_bounds__(256) k_direct_split(DirectArgs a, const T *__restrict__ u,
+                                                      T *__restrict__ Lu)
+{
+    using Entry = typename Tab<T>::type;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = gid / SPLIT;
+    const int lane = (int)(gid % SPLIT);
+    const bool own = i < a.N;
+    const int n = a.n;
+    const int64_t N = a.N;
+    const T *__restrict__ ur = u + (int64_t)blockIdx.y * N;
+    const T *__restrict__ bb = (const T *)a.b;
+    const T *__restrict__ whv = (const T *)a.wh;
+    const Entry *__restrict__ tab = (const Entry *)a.tab;
+    T acc = T(0), ui = T(0);
+    if (own) {
+        const int x = (int)(i % n);
+        const int y = D > 1 ? (int)((i / n) % n) : 0;
+        const int z = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+        ui = ur[i];
+        const int cnt = a.cnt[i];
+        const T ir = (MODE == MODE_POLY) ? ((const T *)a.ir)[i] : T(0);
+        const T whi = (MODE == MODE_SYM) ? whv[i] : T(0);
+        const int thri = a.thr[i];
+        for (int t = lane; t < cnt; t += SPLIT) {
+            const int4 o = a.off[t];
+            const Entry en = tab[t];
+            const int gx = x + o.x, gy = y + o.y, gz = z + o.z;
+            if (!in_grid<D>(n, gx, gy, gz)) continue;
+            const int64_t j = gx + (int64_t)n * (gy + (int64_t)n * gz);
+            const T uj = ur[j], bj = bb[j];
+            T w;
+            if constexpr (MODE == MODE_POWER) {
+                w = (T)en.g * bj;
+            } else if constexpr (MODE == MODE_POLY) {
+                w = poly_weight<T>(a.poly, a.K, (T)en.o2 * ir) * bj;
+            } else {
+                const T wi = (en.o2 <= thri) ? whi : T(0);
+                const T wj = (en.o2 <= a.thr[j]) ? whv[j] : T(0);
+                w = (T)en.g * bj * (wi + wj);
+            }
+            acc += w * (uj - ui);
+        }
+    }
+#pragma unroll
+    for (int o = SPLIT / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, SPLIT);
+    if (own && lane == 0) {
+        const T fin = ((const T *)a.fin)[i];
+        const T ext = ((const T *)a.ext)[i];
+        Lu[(int64_t)blockIdx.y * N + i] = fin * (acc - ui * ext);
+    }
+}
+
+template <int D, typename T, int MODE>
+static nl_status launch_split(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
+                              cudaStream_t st)
+{
+    constexpr int SPLIT = 32;
+    const int64_t threads = p->N * SPLIT;
+    const dim3 grd((unsigned)((threads + 255) / 256), nrhs, 1);
+    k_direct_split<D, T, MODE, SPLIT><<<grd, 256, 0, st>>>(a, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 // Raise a kernel's dynamic shared-memory limit once per (kernel, size): repeated calls
@@ -735,19 +806,29 @@ static nl_status launch_scalar_t(nl_plan *p, const DirectArgs &a, const T *u, T 
     return NL_OK;
 }
 
-template <typename T, int MODE>
-static nl_status launch_rb_t(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
-                             cudaStream_t st)
+template <typename T, int MODE, int RP>
+static nl_status launch_rb_tp(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
+                              cudaStream_t st)
 {
     const dim3 blk(32, RB_TY, 1);
-    const dim3 grd((p->n + 31) / 32, (p->n + RB_TY * RB_P - 1) / (RB_TY * RB_P), nrhs);
-    const size_t smem = sizeof(T) == 4 ? p->rb_smem32 : p->rb_smem64;
+    const dim3 grd((p->n + 31) / 32, (p->n + RB_TY * RP - 1) / (RB_TY * RP), nrhs);
+    const size_t smem = sizeof(T) == 4 ? p->rb_smem32 : p->rb_smem64;   // sized for RB_P >= RP
     const T *g = sizeof(T) == 4 ? (const T *)p->rb_g32 : (const T *)p->rb_g64;
-    auto kern = k_direct2d_rb<T, MODE>;
+    auto kern = k_direct2d_rb<T, MODE, RP>;
     NL_CUDA_TRY(prep_smem(kern, smem));
     kern<<<grd, blk, smem, st>>>(a, g, u, Lu);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
+}
+
+// Rows per thread: 8 when the grid gives every SM several blocks, else 2.
+template <typename T, int MODE>
+static nl_status launch_rb_t(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
+                             cudaStream_t st)
+{
+    const int64_t blocks8 = (int64_t)((p->n + 31) / 32) * ((p->n + RB_TY * RB_P - 1) / (RB_TY * RB_P)) * nrhs;
+    if (blocks8 >= 4 * 152) return launch_rb_tp<T, MODE, RB_P>(p, a, u, Lu, nrhs, st);
+    return launch_rb_tp<T, MODE, 2>(p, a, u, Lu, nrhs, st);
 }
 
 template <typename T>
@@ -755,6 +836,19 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
                                cudaStream_t st, size_t smem)
 {
     const int mode = p->symmetric ? MODE_SYM : (p->family == NL_POLY ? MODE_POLY : MODE_POWER);
+    // few nodes with large balls: split each node's ball over a group of lanes
+    if (p->N * nrhs < 32 * 1024 && p->num_off >= 64 && nrhs <= 65535) {
+#define NL_SPLIT(D)                                                                                \
+        do {                                                                                       \
+            if (mode == MODE_POWER) return launch_split<D, T, MODE_POWER>(p, a, u, Lu, nrhs, st); \
+            if (mode == MODE_POLY) return launch_split<D, T, MODE_POLY>(p, a, u, Lu, nrhs, st);   \
+            return launch_split<D, T, MODE_SYM>(p, a, u, Lu, nrhs, st);                           \
+        } while (0)
+        if (p->d == 1) NL_SPLIT(1);
+        if (p->d == 2) NL_SPLIT(2);
+        NL_SPLIT(3);
+#undef NL_SPLIT
+    }
     if (p->d == 2 && p->rb2d && sizeof(T) == 4) {
         if (mode == MODE_POWER && p->Rmax <= 32) {
             const float *uf = (const float *)u;
