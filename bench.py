@@ -1,16 +1,20 @@
 """Benchmark of the nonlocal-operator hot path on one GB300.
 
-Workload (one step): on the 2-D heterogeneous 1024^2 grid (variable horizon
-delta = h (4 + 12 s), lognormal coefficient a(x) a(y), Gaussian random field u):
+Default workload (c2, one step): on the 2-D heterogeneous 1024^2 grid (variable horizon
+delta = h (4 + 12 s), lognormal coefficient a(x) a(y), Gaussian random field u)
   * one direct apply  (nl_apply, FP32, gamma = C_delta |xi|^{-1.5}), and
-  * one fast apply    (nl_apply_fast, Sec. 3 algorithm, p^0 = 1, same fields).
+  * one fast apply    (nl_apply_fast, the Sec. 3 algorithm with p^0 = 1, same fields);
 value = grid points processed per second over both applies (2 N per step), Gpts/s.
 
-Timing: W untimed warm-up steps, then K steps timed with CUDA events on the
-launching stream; the L2 is flushed (a 256 MiB write) before every timed step,
-outside the events.  Rank 0 prints one JSON line.  Under torchrun every rank
-runs an independent replica of the workload (the operator needs no exchange
-on one GPU: replicas only); value sums the replicas over max-over-ranks time.
+Other workloads (--workload): c1 1-D FP64 direct (4096 nodes); c3 2-D peridynamics 512^2
+FP32; c4 CG to relative residual 1e-8 on 256^2 (Jacobi; time per solve); c5 3-D 256^3 with
+8 right-hand sides, direct + fast FP32; ex1 / ex2 the paper's Example 1 (2-D, delta = 1/2,
+128^2) and Example 2 (1-D, K = 3, 4096 nodes), fast vs direct in FP64.
+
+Timing: W untimed warm-up steps, then K steps timed with CUDA events on the launching stream;
+the L2 is flushed (a 256 MiB write) before every timed step, outside the events.  Rank 0
+prints one JSON line.  Under torchrun every rank runs an independent replica (the operator
+needs no exchange on one GPU: replicas only); value sums the replicas over max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -32,6 +36,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -111,82 +116,37 @@ def dist_env():
     return ws, rank, local
 
 
-def build_workload(n=1024, seed=0):
-    from paper_1905_08375_gb300 import synth
-    return synth.heterogeneous_2d(n=n, seed=seed)
-
-
-def algorithmic_counts(f, n):
-    """Neighbour count of the direct sum (sum over nodes of |ball|) from the horizon field."""
-    rho = f["delta"] * n
-    R2 = rho * rho
-    thr = np.ceil(R2) - 1.0
+def ball_counts(delta, n, d):
+    """Per-node number of lattice offsets 0 < |o|^2 < (delta n)^2 (the direct sum's terms)."""
+    rho = np.asarray(delta) * n
+    thr = np.ceil(rho * rho) - 1.0
     rmax = int(np.ceil(rho.max()))
     o = np.arange(-rmax, rmax + 1)
-    o2 = np.sort((o[:, None] ** 2 + o[None, :] ** 2).reshape(-1))
+    grids = np.meshgrid(*([o] * d), indexing="ij")
+    o2 = np.sort(sum(g.astype(np.int64) ** 2 for g in grids).reshape(-1))
     o2 = o2[o2 > 0]
-    cnt = np.searchsorted(o2, thr, side="right")
-    return int(cnt.sum())
+    return np.searchsorted(o2, thr, side="right")
 
 
-def run_gpu(args, peaks):
-    import torch
-    import torch.distributed as dist
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+class Workload:
+    name = ""
+    metric = ""
+    unit = "Gpts/s"
+    higher_is_better = True
+    dtype = "f32"
+    launches = None
 
-    from paper_1905_08375_gb300 import binding as nl
+    def __init__(self, dev, seed):
+        import torch
+        from paper_1905_08375_gb300 import binding as nl
+        self.torch, self.nl, self.dev, self.seed = torch, nl, dev, seed
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
-    n = args.n
-    N = n * n
-    f = build_workload(n, seed=args.seed + rank)
-    direct = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
-                               coef=nl.NL_COEF_XY, a=f["a"])
-    fast = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
-                             coef=nl.NL_COEF_XY, a=f["a"])
-    u = torch.tensor(f["u"][0], dtype=torch.float32, device=dev)
-    out_d = torch.empty_like(u)
-    out_f = torch.empty_like(u)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        nl.nl_apply(direct, u, out_d)
-        nl.nl_apply_fast(fast, u, out_f)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- timed steps (events on the launching stream, L2 flushed before each) ----
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = float(np.mean(ms))
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ws * 2 * N / (ms_step * 1e-3) / 1e9
-
-    # ---- per-kernel timing for the roofline (same stream, flushed) ----
-    def time_fn(fn, reps):
+    def time_fn(self, fn, reps, flush):
+        torch = self.torch
+        stream = torch.cuda.current_stream()
         ts = []
         for r in range(reps):
             flush.fill_(float(r))
@@ -198,137 +158,589 @@ def run_gpu(args, peaks):
             ts.append(a.elapsed_time(b))
         return float(np.mean(ts))
 
-    reps = max(3, min(args.steps, 50))
-    t_direct = time_fn(lambda: nl.nl_apply(direct, u, out_d), reps)
-    t_fast = time_fn(lambda: nl.nl_apply_fast(fast, u, out_f), reps)
-    fast_pan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
-                                 coef=nl.NL_COEF_XY, a=f["a"], fast_variant=nl.NL_FAST_PANELS)
-    fast_f64 = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
-                                 coef=nl.NL_COEF_XY, a=f["a"],
-                                 fast_variant=nl.NL_FAST_FP64_PANELS)
-    t_fast_pan = time_fn(lambda: nl.nl_apply_fast(fast_pan, u, out_f), reps)
-    t_fast_f64 = time_fn(lambda: nl.nl_apply_fast(fast_f64, u, out_f), reps)
-    nl.nl_apply_fast(fast, u, out_f)
-    u64 = u.double()
-    o64 = torch.empty_like(u64)
-    t_direct64 = time_fn(lambda: nl.nl_apply(direct, u64, o64), max(3, reps // 2))
-    nb = algorithmic_counts(f, n)
-    flops_direct = 4.0 * nb                    # per neighbour: b_j g, u_j - u_i, fma
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops_direct / (t_direct * 1e-3) / 1e12
-    roofline = {"kernel": "k_direct_scalar<2,float,POWER,staged>", "bound": "alu",
-                "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "algorithmic_flops_per_launch": flops_direct}
-
-    # ---- end to end through the public API with host buffers ----
-    uh = torch.tensor(f["u"][0], dtype=torch.float32).pin_memory()
-    res_d = torch.empty(N, dtype=torch.float32).pin_memory()
-    res_f = torch.empty(N, dtype=torch.float32).pin_memory()
-    ud = torch.empty_like(u)
-    e_ts = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ud.copy_(uh, non_blocking=True)
-        nl.nl_apply(direct, ud, out_d)
-        nl.nl_apply_fast(fast, ud, out_f)
-        res_d.copy_(out_d, non_blocking=True)
-        res_f.copy_(out_f, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e_ts.append(a.elapsed_time(b))
-    e2e_ms = float(np.mean(e_ts))
-    e2e = {"value": round(ws * 2 * N / (e2e_ms * 1e-3) / 1e9, 4), "unit": "Gpts/s",
-           "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": 2 * N * 4, "ms_per_step": e2e_ms}
-
-    result = dict(
-        metric="L_delta u applies (direct + fast) in Gpts/s on the 2-D heterogeneous 1024^2 grid",
-        value=round(value, 4), unit="Gpts/s", n_gpus=ws, steps=args.steps,
-        warmup=args.warmup, ms_per_step=round(ms_step, 4), higher_is_better=True,
-        scaling="weak", vs_baseline=None, dtype="f32 (direct) / f64 sums (fast)",
-        data="synthetic",
-        config={"workload": "2D heterogeneous nonlocal diffusion 1024x1024, delta=h(4+12s), "
-                            "a lognormal sigma 0.5 smoothed 8h, gamma=a(x)a(y)C_delta|xi|^-1.5; "
-                            "direct FP32 apply + fast (Sec. 3, K=0) apply per step",
-                "n": n, "points": N, "l2": "flushed (256 MiB write) before every timed step",
-                "parallelism": f"replicas x{ws}"},
-        per_path_gpts={"direct_fp32": round(N / (t_direct * 1e-3) / 1e9, 4),
-                       "fast_k0_rowprefix": round(N / (t_fast * 1e-3) / 1e9, 4),
-                       "fast_k0_panels_int": round(N / (t_fast_pan * 1e-3) / 1e9, 4),
-                       "fast_k0_panels_fp64": round(N / (t_fast_f64 * 1e-3) / 1e9, 4),
-                       "direct_fp64": round(N / (t_direct64 * 1e-3) / 1e9, 4)},
-        per_path_ms={"direct_fp32": round(t_direct, 4), "fast_k0_rowprefix": round(t_fast, 4),
-                     "fast_k0_panels_int": round(t_fast_pan, 4),
-                     "fast_k0_panels_fp64": round(t_fast_f64, 4),
-                     "direct_fp64": round(t_direct64, 4)},
-        roofline=roofline, e2e=e2e,
-        gpu_launches=args.steps * (1 + 2 + fast.info()["levels"]),
-        peaks_source=peaks["_source"],
-    )
-    clocks = clk.summary()
-    result["clocks"] = clocks
-    outs = dict(direct=out_d.double().cpu().numpy(), fast=out_f.double().cpu().numpy())
-    return result, f, outs, rank, ws
+    def value(self, ms):
+        return self.units / (ms * 1e-3) / 1e9
 
 
-def cpu_baseline(f, n, outs, budget_s=20.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+def _alu_roof(kernel, flops, ms, peak, src):
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None, "peak_source": src}
+
+
+FP32_SRC = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+FP64_SRC = "nominal FP64 1.25 TFLOP/s (profiling recipe)"
+
+
+class C2(Workload):
+    """2-D heterogeneous 1024^2: direct FP32 + fast (K = 0) per step."""
+    name = "c2"
+    metric = "L_delta u applies (direct + fast) in Gpts/s on the 2-D heterogeneous 1024^2 grid"
+    dtype = "f32 data; exact 64-bit integer partial sums (fast)"
+
+    def setup(self, n=1024):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.n = n
+        self.f = synth.heterogeneous_2d(n=n, seed=self.seed)
+        f = self.f
+        self.direct = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
+                                        coef=nl.NL_COEF_XY, a=f["a"])
+        self.fast = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
+                                      coef=nl.NL_COEF_XY, a=f["a"])
+        self.u = torch.tensor(f["u"][0], dtype=torch.float32, device=self.dev)
+        self.out_d = torch.empty_like(self.u)
+        self.out_f = torch.empty_like(self.u)
+        self.units = 2 * n * n
+        self.launches = 1 + 4 + self.fast.info()["levels"]
+        self.config = {"workload": "2D heterogeneous nonlocal diffusion 1024x1024, "
+                                   "delta=h(4+12s), a lognormal sigma 0.5 smoothed 8h, "
+                                   "gamma=a(x)a(y)C_delta|xi|^-1.5; direct FP32 apply + fast "
+                                   "(Sec. 3, K=0, p=1) apply per step", "n": n, "points": n * n}
+
+    def step(self):
+        self.nl.nl_apply(self.direct, self.u, self.out_d)
+        self.nl.nl_apply_fast(self.fast, self.u, self.out_f)
+
+    def kernels(self, flush, reps):
+        nl = self.nl
+        t_direct = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
+        nl.nl_plan_profile(self.fast, True)
+        t_fast = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u, self.out_f),
+                              min(reps, 60), flush)
+        prof = nl.nl_plan_profile_read(self.fast)
+        nl.nl_plan_profile(self.fast, False)
+        t_s2 = prof["step2_ms"] / max(prof["applies"], 1)
+        t_s3 = prof["step3_ms"] / max(prof["applies"], 1)
+        n = self.n
+        nb = float(ball_counts(self.f["delta"], n, 2).sum())
+        flops = 4.0 * nb
+        per = {"direct_fp32_ms": round(t_direct, 4), "fast_ms": round(t_fast, 4),
+               "fast_step2_ms": round(t_s2, 4), "fast_step3_gather_ms": round(t_s3, 4),
+               "direct_gpts": round(n * n / (t_direct * 1e-3) / 1e9, 4),
+               "fast_gpts": round(n * n / (t_fast * 1e-3) / 1e9, 4)}
+        if t_direct >= t_s3:
+            roof = _alu_roof("k_direct2d_x2<16> (direct FP32)", flops, t_direct,
+                             FP32_PEAK_TFLOPS, FP32_SRC)
+            roof["algorithmic_per_launch"] = f"{flops:.4g} flop (4 per neighbour term)"
+        else:
+            # Step 3 reads per node: thr4 4 + fastF 8 + selfS 8 + u 4 and writes 4 B; the
+            # prefix sums it gathers (8 B each, 4N/3 of them) come from DRAM once
+            byts = n * n * (4 + 8 + 8 + 4 + 4) + 8.0 * (4.0 / 3.0) * n * n
+            ach = byts / (t_s3 * 1e-3) / 1e9
+            pk = self.peaks["hbm_gbs"]
+            roof = {"kernel": "k_fast_gather_rowprefix<2> (Step 3)", "bound": "hbm",
+                    "achieved": round(ach, 2), "peak": pk, "unit": "GB/s",
+                    "frac": round(ach / pk, 4), "traffic": None,
+                    "peak_source": f"{self.peaks['_source']} hbm_gbs",
+                    "algorithmic_per_launch": f"{byts:.4g} B (38.7 B per node)"}
+        return roof, per
+
+    def e2e(self, flush, steps):
+        torch, nl = self.torch, self.nl
+        N = self.n * self.n
+        uh = torch.tensor(self.f["u"][0], dtype=torch.float32).pin_memory()
+        rd = torch.empty(N, dtype=torch.float32).pin_memory()
+        rf = torch.empty(N, dtype=torch.float32).pin_memory()
+        ud = torch.empty_like(self.u)
+
+        def one():
+            ud.copy_(uh, non_blocking=True)
+            nl.nl_apply(self.direct, ud, self.out_d)
+            nl.nl_apply_fast(self.fast, ud, self.out_f)
+            rd.copy_(self.out_d, non_blocking=True)
+            rf.copy_(self.out_f, non_blocking=True)
+        ms = self.time_fn(one, steps, flush)
+        return {"value": round(self.value(ms), 4), "unit": self.unit, "h2d_bytes_per_step": N * 4,
+                "d2h_bytes_per_step": 2 * N * 4, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"direct": self.out_d.double().cpu().numpy(),
+                "fast": self.out_f.double().cpu().numpy()}
+
+    @staticmethod
+    def oracle_step(f, n, idx):
+        import oracle
+        d = oracle.direct_scalar(f["u"][0], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                                 a=f["a"], idx=idx)
+        fs = oracle.fast_leafset(f["u"][0], 2, int(np.log2(n)), f["delta"], K=0, alpha=1.5,
+                                 coef=oracle.COEF_XY, a=f["a"], idx=idx)
+        return {"direct": d, "fast": fs}, 2 * len(idx)
+
+
+class C1(Workload):
+    name = "c1"
+    metric = "1-D nonlocal diffusion direct apply (FP64) in Gpts/s, N=4096, delta=0.05"
+    dtype = "f64"
+
+    def setup(self):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.n = 4096
+        self.f = synth.diffusion_1d(n=4096, delta=0.05, seed=self.seed)
+        self.plan = nl.nl_plan_create(1, 4096, 0.05, family=nl.NL_POWER, alpha=0.0)
+        self.u = torch.tensor(self.f["u"], dtype=torch.float64, device=self.dev)
+        self.out = torch.empty_like(self.u)
+        self.units = 4096
+        self.launches = 1
+        self.config = {"workload": "1D nonlocal diffusion, N=4096, delta=0.05, gamma=3/delta^3, "
+                                   "u=sin(2 pi x)+0.01 N(0,1), FP64 direct apply", "n": 4096}
+
+    def step(self):
+        self.nl.nl_apply(self.plan, self.u, self.out)
+
+    def kernels(self, flush, reps):
+        t = self.time_fn(self.step, reps, flush)
+        nb = float(ball_counts(self.f["delta"], self.n, 1).sum())
+        roof = _alu_roof("k_direct_split<1,double,POWER>", 4.0 * nb, t, FP64_NOMINAL_TFLOPS,
+                         FP64_SRC)
+        roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term)"
+        return roof, {"direct_fp64_ms": round(t, 4)}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        uh = torch.tensor(self.f["u"], dtype=torch.float64).pin_memory()
+        rh = torch.empty(self.n, dtype=torch.float64).pin_memory()
+        ud = torch.empty_like(self.u)
+
+        def one():
+            ud.copy_(uh, non_blocking=True)
+            self.nl.nl_apply(self.plan, ud, self.out)
+            rh.copy_(self.out, non_blocking=True)
+        ms = self.time_fn(one, steps, flush)
+        return {"value": round(self.value(ms), 6), "unit": self.unit,
+                "h2d_bytes_per_step": self.n * 8, "d2h_bytes_per_step": self.n * 8,
+                "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"direct": self.out.cpu().numpy()}
+
+    @staticmethod
+    def oracle_step(f, n, idx):
+        import oracle
+        return {"direct": oracle.direct_scalar(f["u"], 1, n, 0.05, alpha=0.0, idx=idx)}, len(idx)
+
+
+class C3(Workload):
+    name = "c3"
+    metric = "2-D linear bond-based peridynamics direct apply (FP32) in Gpts/s, 512^2, delta=8h"
+
+    def setup(self):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.n = 512
+        self.f = synth.pd_2d(n=512, seed=self.seed)
+        f = self.f
+        self.plan = nl.nl_plan_create(2, 512, f["delta"], family=nl.NL_PD_BOND,
+                                      coef=nl.NL_COEF_MEAN, a=f["c"])
+        self.u = torch.tensor(f["u"], dtype=torch.float32, device=self.dev)
+        self.out = torch.empty_like(self.u)
+        self.units = 512 * 512
+        self.launches = 1
+        self.config = {"workload": "2D linear bond-based PD, 512x512, delta=8h, micromodulus "
+                                   "c(x,y) xi xi^T/|xi|^3, two-phase Voronoi (64 cells, c in "
+                                   "{1,10}), FP32 apply with FP64 accumulation", "n": 512}
+
+    def step(self):
+        self.nl.nl_apply(self.plan, self.u, self.out)
+
+    def kernels(self, flush, reps):
+        t = self.time_fn(self.step, reps, flush)
+        nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
+        roof = _alu_roof("k_direct_pd<float,staged>", 14.0 * nb, t, FP32_PEAK_TFLOPS, FP32_SRC)
+        roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
+        return roof, {"pd_fp32_ms": round(t, 4)}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        uh = torch.tensor(self.f["u"], dtype=torch.float32).pin_memory()
+        rh = torch.empty_like(uh).pin_memory()
+        ud = torch.empty_like(self.u)
+
+        def one():
+            ud.copy_(uh, non_blocking=True)
+            self.nl.nl_apply(self.plan, ud, self.out)
+            rh.copy_(self.out, non_blocking=True)
+        ms = self.time_fn(one, steps, flush)
+        b = int(uh.numel()) * 4
+        return {"value": round(self.value(ms), 4), "unit": self.unit, "h2d_bytes_per_step": b,
+                "d2h_bytes_per_step": b, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"pd": self.out.double().cpu().numpy().reshape(2, -1)}
+
+    @staticmethod
+    def oracle_step(f, n, idx):
+        import oracle
+        return {"pd": oracle.pd_direct(f["u"], 2, n, f["delta"], f["c"], idx=idx)[0]}, len(idx)
+
+
+class C4(Workload):
+    name = "c4"
+    metric = "CG time to relative residual 1e-8 (FP64 true residual) on -L u = f, 256^2, ms"
+    unit = "ms"
+    higher_is_better = False
+    dtype = "f32 operator, f64 vectors and reductions"
+
+    def setup(self, n=256):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.n = n
+        self.f = synth.heterogeneous_2d(n=n, seed=self.seed)
+        f = self.f
+        self.plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
+                                      coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+        self.rhs = synth.cg_rhs(n, seed=self.seed + 1)[0]
+        self.fr = torch.tensor(self.rhs, dtype=torch.float64, device=self.dev)
+        self.x = torch.empty_like(self.fr)
+        self.units = 1
+        self.config = {"workload": f"CG on -L u = f, {n}x{n}, kernel and horizon of the 2-D "
+                                   "heterogeneous workload symmetrised (divergence form), "
+                                   "f Gaussian random field, Jacobi preconditioner, rtol 1e-8 "
+                                   "(FP64 true residual)", "n": n}
+        self.last = None
+
+    def step(self):
+        self.last = self.nl.nl_cg_solve(self.plan, self.fr, self.x, rtol=1e-8, maxit=100000)
+
+    def value(self, ms):
+        return ms
+
+    def kernels(self, flush, reps):
+        nl = self.nl
+        u = self.torch.randn(self.n * self.n, device=self.dev)
+        o = self.torch.empty_like(u)
+        t = self.time_fn(lambda: nl.nl_apply(self.plan, u, o), reps, flush)
+        nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
+        if self.last:
+            self.launches = 4 * self.last["iterations"] + 8
+        roof = _alu_roof("k_direct2d_rb<float,SYM,2> (CG operator)", 6.0 * nb, t,
+                         FP32_PEAK_TFLOPS, FP32_SRC)
+        roof["algorithmic_per_launch"] = f"{6 * nb:.4g} flop (6 per one-sided ball term)"
+        return roof, {"sym_apply_fp32_ms": round(t, 4), "cg": self.last}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        fh = torch.tensor(self.rhs, dtype=torch.float64).pin_memory()
+        xh = torch.empty_like(fh).pin_memory()
+        fd = torch.empty_like(self.fr)
+
+        def one():
+            fd.copy_(fh, non_blocking=True)
+            self.nl.nl_cg_solve(self.plan, fd, self.x, rtol=1e-8, maxit=100000)
+            xh.copy_(self.x, non_blocking=True)
+        ms = self.time_fn(one, max(1, steps), flush)
+        b = self.n * self.n * 8
+        return {"value": round(ms, 4), "unit": "ms", "h2d_bytes_per_step": b,
+                "d2h_bytes_per_step": b, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"x": self.x.cpu().numpy()}
+
+
+class C5(Workload):
+    name = "c5"
+    metric = ("3-D nonlocal diffusion 256^3 x 8 right-hand sides, direct + fast applies (FP32) "
+              "in Gpts/s")
+
+    def setup(self):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.n = 256
+        self.f = synth.diffusion_3d(n=256, seed=self.seed, nrhs=8, radius_cells=4)
+        f = self.f
+        self.direct = nl.nl_plan_create(3, 256, f["delta"], family=nl.NL_POWER, alpha=1.0,
+                                        coef=nl.NL_COEF_XY, a=f["a"])
+        self.fast = nl.nl_plan_create(3, 256, f["delta"], family=nl.NL_POLY, alpha=1.0, K=0,
+                                      coef=nl.NL_COEF_XY, a=f["a"])
+        self.u = torch.tensor(f["u"], dtype=torch.float32, device=self.dev)
+        self.out_d = torch.empty_like(self.u)
+        self.out_f = torch.empty_like(self.u)
+        self.units = 2 * 8 * 256 ** 3
+        self.launches = 1 + 8 * (4 + self.fast.info()["levels"])
+        self.config = {"workload": "3D nonlocal diffusion 256^3, delta=4h, a lognormal sigma "
+                                   "0.3, gamma=a(x)a(y)C_delta/|xi|, 8 RHS; direct + fast (K=0) "
+                                   "FP32 applies per step", "n": 256, "rhs": 8}
+
+    def step(self):
+        self.nl.nl_apply(self.direct, self.u, self.out_d)
+        self.nl.nl_apply_fast(self.fast, self.u, self.out_f)
+
+    def kernels(self, flush, reps):
+        nl = self.nl
+        t_d = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
+        t_f = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u, self.out_f), reps, flush)
+        nb = 8.0 * float(ball_counts(np.full(1, 4.0 / 256), 256, 3)[0]) * 256 ** 3
+        roof = _alu_roof("k_direct_scalar<3,float,POWER,staged>", 4.0 * nb, t_d,
+                         FP32_PEAK_TFLOPS, FP32_SRC)
+        roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term, 8 RHS)"
+        return roof, {"direct_fp32_8rhs_ms": round(t_d, 4), "fast_fp32_8rhs_ms": round(t_f, 4)}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        uh = torch.tensor(self.f["u"], dtype=torch.float32).pin_memory()
+        rd = torch.empty_like(uh).pin_memory()
+        rf = torch.empty_like(uh).pin_memory()
+        ud = torch.empty_like(self.u)
+
+        def one():
+            ud.copy_(uh, non_blocking=True)
+            self.nl.nl_apply(self.direct, ud, self.out_d)
+            self.nl.nl_apply_fast(self.fast, ud, self.out_f)
+            rd.copy_(self.out_d, non_blocking=True)
+            rf.copy_(self.out_f, non_blocking=True)
+        ms = self.time_fn(one, max(1, steps), flush)
+        b = int(uh.numel()) * 4
+        return {"value": round(self.value(ms), 4), "unit": self.unit, "h2d_bytes_per_step": b,
+                "d2h_bytes_per_step": 2 * b, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"direct": self.out_d.double().cpu().numpy().reshape(8, -1),
+                "fast": self.out_f.double().cpu().numpy().reshape(8, -1)}
+
+
+class EX(Workload):
+    """The paper's examples (Sec. 4): fast vs direct in FP64."""
+    dtype = "f64"
+
+    def __init__(self, dev, seed, which):
+        super().__init__(dev, seed)
+        self.which = which
+        self.name = which
+        self.metric = ("Example 1 (2-D, delta=1/2, 128^2, K=0): fast + direct FP64 applies, "
+                       "Gpts/s" if which == "ex1" else
+                       "Example 2 (1-D, K=3, delta0=1/4 variable, 4096): fast + direct FP64 "
+                       "applies, Gpts/s")
+
+    def setup(self):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        if self.which == "ex1":
+            self.d, self.n = 2, 128
+            self.delta = 0.5
+            kw = dict(family=nl.NL_POLY, K=0, normalize=False, self_term=nl.NL_SELF_PAPER)
+            u = np.random.default_rng(self.seed).standard_normal(128 * 128)
+        else:
+            self.d, self.n = 1, 4096
+            f = synth.example2_1d(n=4096, seed=self.seed)
+            self.delta = f["delta"]
+            kw = dict(family=nl.NL_POLY, K=3, alpha=1.0, normalize=False)
+            u = f["u"]
+        self.uh = u
+        self.plan = nl.nl_plan_create(self.d, self.n, self.delta, **kw)
+        self.u = torch.tensor(u, dtype=torch.float64, device=self.dev)
+        self.out_d = torch.empty_like(self.u)
+        self.out_f = torch.empty_like(self.u)
+        N = self.n ** self.d
+        self.units = 2 * N
+        self.launches = 2 + self.plan.info()["levels"] + 1
+        self.config = {"workload": self.metric, "n": self.n, "dim": self.d}
+
+    def step(self):
+        self.nl.nl_apply(self.plan, self.u, self.out_d)
+        self.nl.nl_apply_fast(self.plan, self.u, self.out_f)
+
+    def kernels(self, flush, reps):
+        nl = self.nl
+        t_d = self.time_fn(lambda: nl.nl_apply(self.plan, self.u, self.out_d), reps, flush)
+        t_f = self.time_fn(lambda: nl.nl_apply_fast(self.plan, self.u, self.out_f), reps, flush)
+        dl = self.delta if not np.isscalar(self.delta) else np.full(self.n ** self.d, self.delta)
+        nb = float(ball_counts(dl, self.n, self.d).sum())
+        roof = _alu_roof("k_direct_split (direct FP64)", 4.0 * nb, t_d, FP64_NOMINAL_TFLOPS,
+                         FP64_SRC)
+        roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term)"
+        return roof, {"direct_fp64_ms": round(t_d, 4), "fast_fp64_ms": round(t_f, 4),
+                      "fast_over_direct_speedup": round(t_d / t_f, 2)}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        uh = torch.tensor(self.uh, dtype=torch.float64).pin_memory()
+        rd = torch.empty_like(uh).pin_memory()
+        rf = torch.empty_like(uh).pin_memory()
+        ud = torch.empty_like(self.u)
+
+        def one():
+            ud.copy_(uh, non_blocking=True)
+            self.nl.nl_apply(self.plan, ud, self.out_d)
+            self.nl.nl_apply_fast(self.plan, ud, self.out_f)
+            rd.copy_(self.out_d, non_blocking=True)
+            rf.copy_(self.out_f, non_blocking=True)
+        ms = self.time_fn(one, steps, flush)
+        b = int(uh.numel()) * 8
+        return {"value": round(self.value(ms), 6), "unit": self.unit, "h2d_bytes_per_step": b,
+                "d2h_bytes_per_step": 2 * b, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"direct": self.out_d.cpu().numpy(), "fast": self.out_f.cpu().numpy()}
+
+
+def make_workload(name, dev, seed):
+    if name in ("ex1", "ex2"):
+        return EX(dev, seed, name)
+    return {"c1": C1, "c2": C2, "c3": C3, "c4": C4, "c5": C5}[name](dev, seed)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+def _rel(x, r):
+    return float(np.linalg.norm(x - r) / np.linalg.norm(r))
+
+
+def oracle_sample(w, outs, budget_s=20.0):
     import oracle
     rng = np.random.default_rng(123)
-    N = n * n
+    name = w.name
+    if name == "c4":
+        t0 = time.perf_counter()
+        _, it, _ = oracle.cg(w.rhs, 2, w.n, w.f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                             a=w.f["a"], rtol=1e-8)
+        dt = time.perf_counter() - t0
+        Lx = oracle.direct_scalar(outs["x"], 2, w.n, w.f["delta"], alpha=1.5,
+                                  coef=oracle.COEF_XY, a=w.f["a"], symmetric=True)
+        res = float(np.linalg.norm(w.rhs + Lx) / np.linalg.norm(w.rhs))
+        return ({"value": round(dt * 1e3, 2), "unit": "ms", "cores": oracle.num_threads(),
+                 "kind": "oracle", "sample": f"one full FP64 Jacobi-CG solve at {w.n}^2 "
+                                             f"({it} iterations)"},
+                {"gpu_solution_fp64_oracle_residual": res})
+    if name == "c5":
+        n, N = 256, 256 ** 3
+        f = w.f
+        t0 = time.perf_counter()
+        idx = rng.choice(N, size=2000, replace=False)
+        ref_d = oracle.direct_scalar(f["u"], 3, n, f["delta"], alpha=1.0, coef=oracle.COEF_XY,
+                                     a=f["a"], idx=idx)
+        ref_f = oracle.fast_leafset(f["u"], 3, 8, f["delta"], K=0, alpha=1.0,
+                                    coef=oracle.COEF_XY, a=f["a"], idx=idx)
+        dt = time.perf_counter() - t0
+        pts = 2 * 8 * len(idx)
+        par = {"direct_rel_l2": _rel(outs["direct"][:, idx], ref_d),
+               "fast_rel_l2": _rel(outs["fast"][:, idx], ref_f), "sampled_points": len(idx)}
+        return ({"value": round(pts / dt / 1e9, 9), "unit": "Gpts/s",
+                 "cores": oracle.num_threads(), "kind": "oracle",
+                 "sample": f"{len(idx)} random nodes x 8 RHS, direct + fast leaf-set sums "
+                           f"({dt:.1f} s)"}, par)
+    if name in ("ex1", "ex2"):
+        N = w.n ** w.d
+        m = min(N, 4096 if name == "ex2" else 2048)
+        idx = rng.choice(N, size=m, replace=False)
+        L = int(np.log2(w.n))
+        t0 = time.perf_counter()
+        if name == "ex1":
+            rd = oracle.direct_scalar(w.uh, 2, w.n, 0.5, family=oracle.POLY, K=0, normalize=False,
+                                      idx=idx)
+            rf = oracle.fast_tree(w.uh, 2, L, 0.5, K=0, normalize=False,
+                                  self_mode=oracle.SELF_PAPER, idx=idx)
+        else:
+            rd = oracle.direct_scalar(w.uh, 1, w.n, w.delta, family=oracle.POLY, K=3, alpha=1.0,
+                                      normalize=False, idx=idx)
+            rf = oracle.fast_tree(w.uh, 1, L, w.delta, K=3, alpha=1.0, normalize=False, idx=idx)
+        dt = time.perf_counter() - t0
+        par = {"direct_rel_l2": _rel(outs["direct"][idx], rd),
+               "fast_rel_l2": _rel(outs["fast"][idx], rf), "sampled_points": m}
+        return ({"value": round(2 * m / dt / 1e9, 9), "unit": "Gpts/s",
+                 "cores": oracle.num_threads(), "kind": "oracle",
+                 "sample": f"{m} nodes, direct + literal tree algorithm ({dt:.1f} s)"}, par)
+    # c1, c2, c3: grow a random node sample to fill the budget
+    cls = type(w)
+    f, n = w.f, w.n
+    d = 1 if name == "c1" else 2
+    N = n ** d
     t0 = time.perf_counter()
-    idx = rng.choice(N, size=256, replace=False)
-    ref_d = oracle.direct_scalar(f["u"][0], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
-                                 a=f["a"], idx=idx)
-    t1 = time.perf_counter()
-    ref_f = oracle.fast_leafset(f["u"][0], 2, 10, f["delta"], K=0, alpha=1.5,
-                                coef=oracle.COEF_XY, a=f["a"], idx=idx)
-    t2 = time.perf_counter()
-    # grow the sample to fill the budget
-    per_pt = (t2 - t0) / len(idx)
+    idx = rng.choice(N, size=min(N, 256), replace=False)
+    cls.oracle_step(f, n, idx)
+    per_pt = (time.perf_counter() - t0) / len(idx)
     m = int(min(N, max(len(idx), budget_s / max(per_pt, 1e-9))))
     idx2 = rng.choice(N, size=m, replace=False)
     t0 = time.perf_counter()
-    ref_d2 = oracle.direct_scalar(f["u"][0], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
-                                  a=f["a"], idx=idx2)
-    t1 = time.perf_counter()
-    ref_f2 = oracle.fast_leafset(f["u"][0], 2, 10, f["delta"], K=0, alpha=1.5,
-                                 coef=oracle.COEF_XY, a=f["a"], idx=idx2)
-    t2 = time.perf_counter()
-    pts_per_s = 2 * m / (t2 - t0)
-    parity = None
-    if outs is not None:
-        def rel(x, r):
-            return float(np.linalg.norm(x - r) / np.linalg.norm(r))
-        parity = {"direct_fp32_rel_l2": rel(outs["direct"][idx2], ref_d2),
-                  "fast_rel_l2": rel(outs["fast"][idx2], ref_f2), "sampled_points": m}
-    return {"value": round(pts_per_s / 1e9, 9), "unit": "Gpts/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{m} random nodes of the 1024^2 workload, direct + fast leaf-set sums "
-                      f"({t2 - t0:.1f} s)"}, parity
+    refs, units = cls.oracle_step(f, n, idx2)
+    dt = time.perf_counter() - t0
+    par = {"sampled_points": m}
+    for k, ref in refs.items():
+        got = outs[k][..., idx2] if outs[k].ndim > 1 else outs[k][idx2]
+        par[f"{k}_rel_l2"] = _rel(got, ref)
+    return ({"value": round(units / dt / 1e9, 9), "unit": "Gpts/s", "cores": oracle.num_threads(),
+             "kind": "oracle", "sample": f"{m} random nodes of the workload ({dt:.1f} s)"}, par)
+
+
+# ---------------------------------------------------------------------------
+# drivers
+# ---------------------------------------------------------------------------
+def run_gpu(args, peaks):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload, dev, args.seed + rank)
+    w.peaks = peaks
+    w.setup()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    steps = args.steps
+    if w.name == "c4":
+        steps = max(3, min(steps, 20))       # one step is a whole solve
+    if w.name == "c5":
+        steps = max(3, min(steps, 30))
+    for _ in range(args.warmup):
+        w.step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            w.step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_step = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = w.value(ms_step) * (ws if w.higher_is_better else 1)
+    reps = max(3, min(steps, 50))
+    roof, per = w.kernels(flush, reps)
+    e2e = w.e2e(flush, min(steps, 20))
+    result = dict(metric=w.metric, value=round(value, 6), unit=w.unit, n_gpus=ws, steps=steps,
+                  warmup=args.warmup, ms_per_step=round(ms_step, 4),
+                  higher_is_better=w.higher_is_better,
+                  scaling="weak", vs_baseline=None, dtype=w.dtype, data="synthetic",
+                  config=dict(w.config, l2="flushed (256 MiB write) before every timed step",
+                              parallelism=f"replicas x{ws}"),
+                  per_path=per, roofline=roof, e2e=e2e,
+                  gpu_launches=(w.launches * steps) if w.launches else None,
+                  peaks_source=peaks["_source"])
+    result["clocks"] = clk.summary()
+    return result, w, rank, ws
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, bounded sample per step."""
+    """--impl reference: the FP64 oracle on the host cores, a bounded sample per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    n = args.n
-    f = build_workload(n, seed=args.seed)
+    from paper_1905_08375_gb300 import synth
+    n = 1024
+    f = synth.heterogeneous_2d(n=n, seed=args.seed)
     rng = np.random.default_rng(7)
     m = 512
     N = n * n
 
     def step():
         idx = rng.choice(N, size=m, replace=False)
-        oracle.direct_scalar(f["u"][0], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
-                             a=f["a"], idx=idx)
-        oracle.fast_leafset(f["u"][0], 2, 10, f["delta"], K=0, alpha=1.5,
-                            coef=oracle.COEF_XY, a=f["a"], idx=idx)
+        C2.oracle_step(f, n, idx)
 
     for _ in range(args.warmup):
         step()
@@ -337,14 +749,13 @@ def run_reference(args):
         step()
     dt = (time.perf_counter() - t0) / args.steps
     value = 2 * m / dt / 1e9
-    line = dict(impl="reference",
-                metric="L_delta u applies (direct + fast) in Gpts/s on the 2-D heterogeneous "
-                       "1024^2 grid",
-                value=value, unit="Gpts/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
-                ms_per_step=dt * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic",
-                config={"workload": "2D heterogeneous nonlocal diffusion 1024x1024 (oracle on "
-                                    f"{m} sampled nodes per step)", "n": n},
+    line = dict(impl="reference", metric=C2.metric, value=value, unit="Gpts/s", n_gpus=ws,
+                steps=args.steps, warmup=args.warmup, ms_per_step=dt * 1e3,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic",
+                config={"workload": "2D heterogeneous nonlocal diffusion 1024x1024 (FP64 oracle "
+                                    f"on {m} sampled nodes per step, direct + fast leaf-set)",
+                        "n": n},
                 cpu_baseline={"value": value, "unit": "Gpts/s", "cores": oracle.num_threads(),
                               "kind": "oracle",
                               "sample": f"{m} random nodes per step, direct + fast leaf-set"},
@@ -359,7 +770,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--workload", default="c2",
+                    choices=["c1", "c2", "c3", "c4", "c5", "ex1", "ex2"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -369,10 +781,10 @@ def main():
         run_reference(args)
         return
     peaks = load_peaks()
-    result, f, outs, rank, ws = run_gpu(args, peaks)
+    result, w, rank, ws = run_gpu(args, peaks)
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
-            cb, parity = cpu_baseline(f, args.n, outs)
+            cb, parity = oracle_sample(w, w.outputs())
             result["cpu_baseline"] = cb
             result["parity"] = parity
         print(json.dumps(result))

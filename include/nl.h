@@ -271,6 +271,16 @@ nl_status nl_cg_history(nl_plan *plan, const void *f, void *x, double rtol, int 
                         int precond, double *history, int cap, int *count, nl_cg_stats *stats,
                         void *stream);
 
+/*
+ * Per-phase timing of nl_apply_fast (tracing): when enabled, each fast apply records CUDA
+ * events on its stream before Step 2, between Step 2 and Step 3, and after Step 3 (up to 64
+ * applies between reads).  nl_plan_profile_read synchronises those events, returns the summed
+ * Step 2 (partial sums) and Step 3 (gather) milliseconds and the number of applies, and
+ * clears the record.  Disabled by default; costs two event records per apply when enabled.
+ */
+nl_status nl_plan_profile(nl_plan *plan, int enable);
+nl_status nl_plan_profile_read(nl_plan *plan, double *step2_ms, double *step3_ms, int *applies);
+
 /* Plan introspection (host values computed at plan time). */
 typedef struct {
     int dim, n, levels;        /* levels = L for n = 2^L, else -1 */

@@ -408,3 +408,22 @@ def nl_cg_history(plan: Plan, f, x, history, rtol=1e-8, maxit=10000,
         _check(status)
     return cnt.value, dict(iterations=st.iterations, rel_residual=st.rel_residual,
                            converged=bool(st.converged), status=status)
+
+
+def nl_plan_profile(plan: Plan, enable=True):
+    L = lib()
+    L.nl_plan_profile.restype = ctypes.c_int
+    L.nl_plan_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    _check(L.nl_plan_profile(plan.handle, int(bool(enable))))
+
+
+def nl_plan_profile_read(plan: Plan) -> dict:
+    """Summed Step 2 / Step 3 milliseconds of the fast applies since the last read."""
+    L = lib()
+    L.nl_plan_profile_read.restype = ctypes.c_int
+    L.nl_plan_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int)]
+    a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int(0)
+    _check(L.nl_plan_profile_read(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(step2_ms=a.value, step3_ms=b.value, applies=c.value)

@@ -764,8 +764,19 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     return NL_OK;
 }
 
+// tracing: event k (0: before Step 2, 1: before Step 3, 2: after Step 3) of this apply
+static void prof_mark(nl_plan *p, int k, cudaStream_t st)
+{
+    if (!p->prof_on || p->prof_count >= 64) return;
+    cudaEvent_t &e = p->prof_ev[p->prof_count][k];
+    if (!e && cudaEventCreate(&e) != cudaSuccess) { e = nullptr; return; }
+    cudaEventRecord(e, st);
+    if (k == 2) p->prof_count++;
+}
+
 static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_t st)
 {
+    prof_mark(p, 0, st);
     const int d = p->d, L = p->L;
     long long *pyr = (long long *)p->pyr;           // same buffer, 8-byte entries (M = 1)
     unsigned int *mx = (unsigned int *)p->fast_mx;
@@ -800,6 +811,7 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     a.hd = std::pow(p->h, (double)d);
     a.mx = mx;
+    prof_mark(p, 1, st);
     if (prefix) {
         if (d == 1) k_fast_gather_rowprefix<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_rowprefix<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
@@ -809,6 +821,7 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         else if (d == 2) k_fast_gather_i64<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     }
+    prof_mark(p, 2, st);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
@@ -818,6 +831,7 @@ static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
 {
     if (sizeof(T) == 4 && p->K == 0 && p->fast_mx && p->fast_variant != NL_FAST_FP64_PANELS)
         return fast_one_i64(p, (const float *)u, (float *)Lu, st);
+    prof_mark(p, 0, st);
     const int d = p->d, L = p->L, M = p->M;
     double *leaf = p->pyr + p->lvl_off[L];
     const unsigned gb = (unsigned)((p->N + 255) / 256);
@@ -836,6 +850,7 @@ static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     a.hd = std::pow(p->h, (double)d);
     for (int m = 0; m < 8; ++m) a.poly[m] = p->poly[m];
+    prof_mark(p, 1, st);
 #define NL_GATHER(D, KK) k_fast_gather<D, KK, T><<<gb, 256, 0, st>>>(a, u, Lu)
     if (d == 1) {
         switch (p->K) { case 0: NL_GATHER(1, 0); break; case 1: NL_GATHER(1, 1); break;
@@ -847,7 +862,42 @@ static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
         NL_GATHER(3, 0);
     }
 #undef NL_GATHER
+    prof_mark(p, 2, st);
     NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+extern "C" nl_status nl_plan_profile(nl_plan *p, int enable)
+{
+    if (!nl_plan_ok(p)) {
+        nl_set_error("nl_plan_profile: invalid plan");
+        return NL_EINVAL;
+    }
+    p->prof_on = enable ? 1 : 0;
+    p->prof_count = 0;
+    return NL_OK;
+}
+
+extern "C" nl_status nl_plan_profile_read(nl_plan *p, double *step2_ms, double *step3_ms,
+                                          int *applies)
+{
+    if (!nl_plan_ok(p) || !step2_ms || !step3_ms || !applies) {
+        nl_set_error("nl_plan_profile_read: bad argument");
+        return NL_EINVAL;
+    }
+    double s2 = 0.0, s3 = 0.0;
+    for (int k = 0; k < p->prof_count; ++k) {
+        float a = 0.f, b = 0.f;
+        NL_CUDA_TRY(cudaEventSynchronize(p->prof_ev[k][2]));
+        NL_CUDA_TRY(cudaEventElapsedTime(&a, p->prof_ev[k][0], p->prof_ev[k][1]));
+        NL_CUDA_TRY(cudaEventElapsedTime(&b, p->prof_ev[k][1], p->prof_ev[k][2]));
+        s2 += a;
+        s3 += b;
+    }
+    *step2_ms = s2;
+    *step3_ms = s3;
+    *applies = p->prof_count;
+    p->prof_count = 0;
     return NL_OK;
 }
 

@@ -75,6 +75,8 @@ struct nl_plan {
     int *malpha;                    // multi-indices [M][3]
     int pyr_rhs;                    // right-hand sides the pyramid buffer holds
     unsigned long long *fast_mx;    // max |v| of the last FP32 apply (fixed-point scale)
+    int prof_on, prof_count;        // per-phase timing of the fast apply
+    cudaEvent_t prof_ev[64][3];
     // CG workspace (allocated on the first nl_cg_solve, grown for more right-hand sides)
     double *cg_ws; size_t cg_ws_elems;
     float *cg_ws32; size_t cg_ws32_elems;

@@ -604,6 +604,9 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
                      p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx };
     for (void *q : ptrs) if (q) cudaFree(q);
+    for (int k = 0; k < 64; ++k)
+        for (int j = 0; j < 3; ++j)
+            if (p->prof_ev[k][j]) cudaEventDestroy(p->prof_ev[k][j]);
     nl_cg_release(p);
     p->magic = 0;
     free(p);
