@@ -281,6 +281,31 @@ nl_status nl_cg_history(nl_plan *plan, const void *f, void *x, double rtol, int 
 nl_status nl_plan_profile(nl_plan *plan, int enable);
 nl_status nl_plan_profile_read(nl_plan *plan, double *step2_ms, double *step3_ms, int *applies);
 
+/*
+ * Batches of uneven 2-D instances (each its own n, horizon and coefficient fields; all of one
+ * family, NL_POWER or NL_PD_BOND, and one symmetric flag).  A batch owns one plan per
+ * instance; its vectors concatenate the instances' fields: instance k occupies elements
+ * offsets[k] .. offsets[k+1]-1 (two component planes for NL_PD_BOND).  nl_batch_apply runs
+ * the direct apply of every instance in ONE persistent launch whose blocks take
+ * (instance, tile) work items from an atomic counter; a tile is 32 x 4, 32 x 8 or 32 x 16
+ * output nodes, one per thread.  tile_shape = NL_TILE_AUTO times the three shapes on the
+ * batch at creation (the autotuner) and keeps the fastest; 0..2 fixes the shape.
+ * nl_batch_cg_solve solves -L_k x_k = f_k for all instances together (each instance one CG
+ * segment, one captured graph, Jacobi or no preconditioner); the stats are the worst over
+ * instances.  Errors: NL_EINVAL, NL_EUNSUPPORTED, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV.
+ */
+typedef struct nl_batch nl_batch;
+enum { NL_TILE_AUTO = -1, NL_TILE_32x4 = 0, NL_TILE_32x8 = 1, NL_TILE_32x16 = 2 };
+nl_status nl_batch_create(nl_batch **out, int count, const nl_grid *grids,
+                          const nl_horizon *horizons, const nl_kernel *kernels, int tile_shape,
+                          void *stream);
+nl_status nl_batch_destroy(nl_batch *batch);
+/* offsets: HOST array of count + 1 elements; tile_shape (may be NULL): 0, 1 or 2. */
+nl_status nl_batch_layout(const nl_batch *batch, int64_t *offsets, int *tile_shape);
+nl_status nl_batch_apply(nl_batch *batch, const void *u, void *Lu, int dtype, void *stream);
+nl_status nl_batch_cg_solve(nl_batch *batch, const void *f, void *x, double rtol, int maxit,
+                            int precond, nl_cg_stats *stats, void *stream);
+
 /* Plan introspection (host values computed at plan time). */
 typedef struct {
     int dim, n, levels;        /* levels = L for n = 2^L, else -1 */

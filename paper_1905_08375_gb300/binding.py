@@ -62,7 +62,8 @@ class nl_plan_info(ctypes.Structure):
 
 
 ENTRY_POINTS = ("nl_plan_create", "nl_plan_destroy", "nl_apply", "nl_apply_fast", "nl_cg_solve",
-                "nl_get_plan_info", "nl_last_error")
+                "nl_get_plan_info", "nl_last_error", "nl_batch_create", "nl_batch_destroy",
+                "nl_batch_layout", "nl_batch_apply", "nl_batch_cg_solve")
 
 _lib = None
 
@@ -427,3 +428,121 @@ def nl_plan_profile_read(plan: Plan) -> dict:
     a, b, c = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int(0)
     _check(L.nl_plan_profile_read(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return dict(step2_ms=a.value, step3_ms=b.value, applies=c.value)
+
+
+NL_TILE_AUTO, NL_TILE_32x4, NL_TILE_32x8, NL_TILE_32x16 = -1, 0, 1, 2
+
+
+class Batch:
+    """Owns an ``nl_batch*`` (many uneven 2-D instances applied and solved together)."""
+
+    def __init__(self, handle, sizes, family, offsets, tile_shape):
+        self.handle = handle
+        self.sizes = list(sizes)
+        self.family = family
+        self.offsets = offsets
+        self.tile_shape = tile_shape
+
+    @property
+    def total(self):
+        return int(self.offsets[-1])
+
+    def close(self):
+        if self.handle:
+            lib().nl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch_sigs(L):
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.nl_batch_create.restype = i
+    L.nl_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(nl_grid),
+                                  ctypes.POINTER(nl_horizon), ctypes.POINTER(nl_kernel), i, vp]
+    L.nl_batch_destroy.restype = i
+    L.nl_batch_destroy.argtypes = [vp]
+    L.nl_batch_layout.restype = i
+    L.nl_batch_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i)]
+    L.nl_batch_apply.restype = i
+    L.nl_batch_apply.argtypes = [vp, vp, vp, i, vp]
+    L.nl_batch_cg_solve.restype = i
+    L.nl_batch_cg_solve.argtypes = [vp, vp, vp, d, i, i, ctypes.POINTER(nl_cg_stats), vp]
+
+
+def nl_batch_create(instances, family=NL_POWER, alpha=0.0, scale=1.0, normalize=True,
+                    coef=NL_COEF_NONE, symmetric=False, tile_shape=NL_TILE_AUTO,
+                    stream=None) -> Batch:
+    """instances: list of (n, delta, a) with delta a float or a host array of n*n horizons and
+    a None or a host array of n*n coefficient values (all instances 2-D).  tile_shape:
+    NL_TILE_AUTO (time the three shapes and keep the fastest) or 0, 1, 2 (32x4, 32x8, 32x16)."""
+    L = lib()
+    _batch_sigs(L)
+    cnt = len(instances)
+    grids = (nl_grid * cnt)()
+    hzs = (nl_horizon * cnt)()
+    kers = (nl_kernel * cnt)()
+    keep = []
+    for k, (n, delta, a) in enumerate(instances):
+        grids[k] = nl_grid(2, int(n))
+        if np.isscalar(delta):
+            hzs[k] = nl_horizon(float(delta), None, int(bool(symmetric)))
+        else:
+            dl = np.ascontiguousarray(delta, dtype=np.float64).reshape(-1)
+            if dl.size != n * n:
+                raise ValueError("delta field must have n*n values")
+            keep.append(dl)
+            hzs[k] = nl_horizon(0.0, dl.ctypes.data, int(bool(symmetric)))
+        ap = None
+        if a is not None:
+            aa = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            if aa.size != n * n:
+                raise ValueError("coefficient field must have n*n values")
+            keep.append(aa)
+            ap = aa.ctypes.data
+        kers[k] = nl_kernel(int(family), float(alpha), 0, float(scale), int(bool(normalize)),
+                            int(coef) if a is not None else NL_COEF_NONE, ap,
+                            NL_SELF_DISCRETE, NL_FAST_AUTO)
+    h = ctypes.c_void_p()
+    _check(L.nl_batch_create(ctypes.byref(h), cnt, grids, hzs, kers, int(tile_shape),
+                             _stream_ptr(stream)))
+    offs = (ctypes.c_int64 * (cnt + 1))()
+    shape = ctypes.c_int()
+    _check(L.nl_batch_layout(h, offs, ctypes.byref(shape)))
+    return Batch(h, [inst[0] for inst in instances], family, np.array(list(offs), dtype=np.int64),
+                 shape.value)
+
+
+def nl_batch_apply(batch: Batch, u, Lu, stream=None):
+    """Direct apply of every instance in one launch (concatenated device tensors)."""
+    L = lib()
+    _batch_sigs(L)
+    if not (u.is_cuda and Lu.is_cuda and u.is_contiguous() and Lu.is_contiguous()):
+        raise ValueError("u and Lu must be contiguous CUDA tensors")
+    if u.dtype != Lu.dtype or u.numel() != batch.total or Lu.numel() != batch.total:
+        raise ValueError("u/Lu must hold the batch's concatenated fields (same dtype)")
+    _check(L.nl_batch_apply(batch.handle, ctypes.c_void_p(u.data_ptr()),
+                            ctypes.c_void_p(Lu.data_ptr()), _dtype_code(u), _stream_ptr(stream)))
+    return Lu
+
+
+def nl_batch_cg_solve(batch: Batch, f, x, rtol=1e-8, maxit=10000, precond=NL_PRECOND_JACOBI,
+                      stream=None) -> dict:
+    """CG on -L_k x_k = f_k for every instance together (FP64 device tensors)."""
+    L = lib()
+    _batch_sigs(L)
+    if f.numel() != batch.total or x.numel() != batch.total:
+        raise ValueError("f/x must hold the batch's concatenated fields")
+    st = nl_cg_stats()
+    status = L.nl_batch_cg_solve(batch.handle, ctypes.c_void_p(f.data_ptr()),
+                                 ctypes.c_void_p(x.data_ptr()), float(rtol), int(maxit),
+                                 int(precond), ctypes.byref(st), _stream_ptr(stream))
+    out = dict(iterations=st.iterations, rel_residual=st.rel_residual,
+               converged=bool(st.converged), status=status)
+    if status not in (NL_OK, NL_ENOTCONV):
+        _check(status)
+    return out

@@ -15,6 +15,7 @@
 // graph on a plan-owned stream.  The host reads the per-right-hand-side flags from pinned
 // memory after each chunk, with a bounded wait.
 #include <chrono>
+#include <cstring>
 #include <cmath>
 #include <thread>
 
@@ -57,7 +58,9 @@ __device__ __forceinline__ double fold(const double *part, int slot, int rhs, in
 }
 
 struct CgArgs {
-    int64_t per;          // unknowns per right-hand side
+    int64_t per;          // unknowns per right-hand side (uniform segments)
+    const int64_t *seg_off, *seg_len;   // per-segment offsets/lengths, or nullptr
+    int dinv_global;      // dinv indexed by the global position (else by k)
     int nrhs;
     double tol;           // on the recursive relative residual
     const double *f;
@@ -67,6 +70,19 @@ struct CgArgs {
     double *part;         // [P_COUNT][nrhs][NB]
     double *sc;           // [nrhs][S_COUNT]
 };
+
+__device__ __forceinline__ int64_t seg_base(const CgArgs &a, int rhs)
+{
+    return a.seg_off ? a.seg_off[rhs] : (int64_t)rhs * a.per;
+}
+__device__ __forceinline__ int64_t seg_len(const CgArgs &a, int rhs)
+{
+    return a.seg_len ? a.seg_len[rhs] : a.per;
+}
+__device__ __forceinline__ double dinv_at(const CgArgs &a, int64_t base, int64_t k)
+{
+    return a.dinv[a.dinv_global ? base + k : k];
+}
 
 __device__ __forceinline__ void store_partial(const CgArgs &a, int slot, int rhs, double v)
 {
@@ -79,14 +95,14 @@ __global__ void __launch_bounds__(RB) k_cg_init(CgArgs a)
 {
     __shared__ double sh[RB / 32];
     const int rhs = blockIdx.y;
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0, rr = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
         const double fv = a.f[base + k];
         a.x[base + k] = 0.0;
         a.r[base + k] = fv;
         if (!FLEX) {
-            const double zv = a.dinv[k] * fv;
+            const double zv = dinv_at(a, base, k) * fv;
             a.z[base + k] = zv;
             a.p[base + k] = zv;
             a.p32[base + k] = (float)zv;
@@ -120,9 +136,9 @@ __global__ void __launch_bounds__(RB) k_cg_pz(CgArgs a, int only, double goal)
     __shared__ double sh[RB / 32];
     const int rhs = blockIdx.y;
     const bool redo = only < 0 || a.sc[(size_t)rhs * S_COUNT + S_TRUE] > goal;
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
         const int64_t g = base + k;
         const double zv = a.z[g];
         if (redo) {
@@ -160,9 +176,9 @@ __global__ void __launch_bounds__(RB) k_cg_dot(CgArgs a)
     __shared__ double sh[RB / 32];
     const int rhs = blockIdx.y;
     if (blockIdx.x == 0 && threadIdx.x < 32) scalars_after_update(a, rhs);
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double pq = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB)
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB)
         pq -= a.p[base + k] * (double)a.q32[base + k];
     const double s = block_sum(pq, sh);
     if (threadIdx.x == 0) store_partial(a, P_PQ, rhs, s);
@@ -187,9 +203,9 @@ __global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
     }
     __syncthreads();
     const double alpha = s_alpha;
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0, rr = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
         const int64_t g = base + k;
         double rv = a.r[g];
         if (alpha != 0.0) {
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
         if (FLEX) {
             rz += rv * a.z[g];
         } else {
-            const double zv = a.dinv[k] * rv;
+            const double zv = dinv_at(a, base, k) * rv;
             a.z[g] = zv;
             rz += rv * zv;
         }
@@ -216,9 +232,9 @@ __global__ void __launch_bounds__(RB) k_cg_rz(CgArgs a)
 {
     __shared__ double sh[RB / 32];
     const int rhs = blockIdx.y;
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB)
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB)
         rz += a.r[base + k] * a.z[base + k];
     const double s = block_sum(rz, sh);
     if (threadIdx.x == 0) store_partial(a, P_RZ, rhs, s);
@@ -242,8 +258,8 @@ __global__ void __launch_bounds__(RB) k_cg_dir(CgArgs a)
     }
     __syncthreads();
     const double beta = s_beta;
-    const int64_t base = (int64_t)rhs * a.per;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
         const int64_t g = base + k;
         const double pv = a.z[g] + beta * a.p[g];
         a.p[g] = pv;
@@ -256,9 +272,9 @@ __global__ void __launch_bounds__(RB) k_cg_true(CgArgs a)
 {
     __shared__ double sh[RB / 32];
     const int rhs = blockIdx.y;
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double ss = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
         const double t = a.f[base + k] + a.q64[base + k];
         ss += t * t;
     }
@@ -286,9 +302,9 @@ __global__ void __launch_bounds__(RB) k_cg_restart(CgArgs a, double goal)
     const int rhs = blockIdx.y;
     const double *sc = a.sc + (size_t)rhs * S_COUNT;
     const bool redo = sc[S_TRUE] > goal;
-    const int64_t base = (int64_t)rhs * a.per;
+    const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0, rr = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < a.per; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
         const int64_t g = base + k;
         double rv = a.r[g];
         if (redo) {
@@ -298,7 +314,7 @@ __global__ void __launch_bounds__(RB) k_cg_restart(CgArgs a, double goal)
         if (!FLEX) {
             double zv = a.z[g];
             if (redo) {
-                zv = a.dinv[k] * rv;
+                zv = dinv_at(a, base, k) * rv;
                 a.z[g] = zv;
                 a.p[g] = zv;
                 a.p32[g] = (float)zv;
@@ -333,28 +349,26 @@ void nl_invert_launch(int64_t n, double *d, cudaStream_t st)
     k_invert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, d, 1);
 }
 
-nl_status nl_cg_release(nl_plan *p)
+nl_status nl_cg_state_release(nl_cg_state *c)
 {
-    if (p->cg_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)p->cg_graph_exec);
-    if (p->cg_ws) cudaFree(p->cg_ws);
-    if (p->cg_ws32) cudaFree(p->cg_ws32);
-    if (p->cg_red) cudaFree(p->cg_red);
-    if (p->cg_host) cudaFreeHost(p->cg_host);
-    if (p->cg_ev) cudaEventDestroy(p->cg_ev);
-    if (p->cg_stream) cudaStreamDestroy(p->cg_stream);
-    p->cg_graph_exec = nullptr;
-    p->cg_ws = nullptr; p->cg_ws32 = nullptr; p->cg_red = nullptr; p->cg_host = nullptr;
-    p->cg_ev = nullptr; p->cg_stream = nullptr;
-    p->cg_ws_elems = p->cg_ws32_elems = p->cg_red_elems = p->cg_host_elems = 0;
-    p->cg_graph_nrhs = 0;
+    if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+    if (c->ws) cudaFree(c->ws);
+    if (c->ws32) cudaFree(c->ws32);
+    if (c->red) cudaFree(c->red);
+    if (c->host) cudaFreeHost(c->host);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    memset(c, 0, sizeof(*c));
     return NL_OK;
 }
 
-static nl_status wait_bounded(nl_plan *p, double seconds)
+nl_status nl_cg_release(nl_plan *p) { return nl_cg_state_release(&p->cg); }
+
+static nl_status wait_bounded(nl_cg_state *c, double seconds)
 {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        cudaError_t e = cudaEventQuery(p->cg_ev);
+        cudaError_t e = cudaEventQuery(c->ev);
         if (e == cudaSuccess) return NL_OK;
         if (e != cudaErrorNotReady) return nl_cuda_fail(e, "CG chunk");
         const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -366,41 +380,42 @@ static nl_status wait_bounded(nl_plan *p, double seconds)
     }
 }
 
-static nl_status ensure_workspace(nl_plan *p, int64_t len, int64_t per, int nrhs)
+static nl_status ensure_workspace(nl_cg_state *c, int64_t len, int64_t dlen, int nrhs)
 {
-    const size_t need64 = (size_t)4 * len + per;   // r z p q64 | dinv
+    const size_t need64 = (size_t)4 * len + dlen;   // r z p q64 | dinv
     const size_t need32 = (size_t)2 * len;
     const size_t needr = (size_t)P_COUNT * nrhs * NB + (size_t)S_COUNT * nrhs;
-    if (p->cg_ws_elems >= need64 && p->cg_ws32_elems >= need32 && p->cg_red_elems >= needr &&
-        p->cg_host_elems >= (size_t)S_COUNT * nrhs && p->cg_stream)
+    if (c->ws_elems >= need64 && c->ws32_elems >= need32 && c->red_elems >= needr &&
+        c->host_elems >= (size_t)S_COUNT * nrhs && c->stream)
         return NL_OK;
-    nl_cg_release(p);
+    nl_cg_state_release(c);
     cudaError_t e;
-    if ((e = cudaMalloc(&p->cg_ws, need64 * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&p->cg_ws32, need32 * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&p->cg_red, needr * sizeof(double))) != cudaSuccess ||
-        (e = cudaMallocHost(&p->cg_host, (size_t)S_COUNT * nrhs * sizeof(double))) != cudaSuccess) {
-        nl_cg_release(p);
+    if ((e = cudaMalloc(&c->ws, need64 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&c->ws32, need32 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&c->red, needr * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->host, (size_t)S_COUNT * nrhs * sizeof(double))) != cudaSuccess) {
+        nl_cg_state_release(c);
         nl_set_error("nl_cg_solve: workspace allocation failed: %s", cudaGetErrorString(e));
         return NL_ENOMEM;
     }
-    p->cg_ws_elems = need64; p->cg_ws32_elems = need32; p->cg_red_elems = needr;
-    p->cg_host_elems = (size_t)S_COUNT * nrhs;
-    NL_CUDA_TRY(cudaStreamCreateWithFlags(&p->cg_stream, cudaStreamNonBlocking));
-    NL_CUDA_TRY(cudaEventCreateWithFlags(&p->cg_ev, cudaEventDisableTiming));
+    c->ws_elems = need64; c->ws32_elems = need32; c->red_elems = needr;
+    c->host_elems = (size_t)S_COUNT * nrhs;
+    NL_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    NL_CUDA_TRY(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
     return NL_OK;
 }
 
-static nl_status enqueue_chunk(nl_plan *p, const CgArgs &a, bool flex, int iters, cudaStream_t st)
+static nl_status enqueue_chunk(nl_cg_op &op, const CgArgs &a, bool flex, int iters,
+                               cudaStream_t st)
 {
     const dim3 grid(NB, a.nrhs);
     for (int it = 0; it < iters; ++it) {
-        nl_status s = nl_direct_launch(p, a.p32, a.q32, a.nrhs, NL_F32, st);
+        nl_status s = op.apply(op.ctx, a.p32, a.q32, NL_F32, st);
         if (s != NL_OK) return s;
         k_cg_dot<<<grid, RB, 0, st>>>(a);
         if (flex) {
             k_cg_update<true><<<grid, RB, 0, st>>>(a);
-            s = nl_net_apply_launch(p->net, p, a.r, a.z, a.nrhs, st);
+            s = nl_net_apply_launch(op.net, op.net_plan, a.r, a.z, a.nrhs, st);
             if (s != NL_OK) return s;
             k_cg_rz<<<grid, RB, 0, st>>>(a);
             k_cg_dir<true><<<grid, RB, 0, st>>>(a);
@@ -414,63 +429,55 @@ static nl_status enqueue_chunk(nl_plan *p, const CgArgs &a, bool flex, int iters
     return NL_OK;
 }
 
-// The solver shared by nl_cg_solve and nl_cg_history.
-static nl_status cg_run(nl_plan *p, const void *f, void *x, int nrhs, double rtol, int maxit,
-                        int precond, double *hist, int cap, int *count, nl_cg_stats *stats,
-                        void *stream)
+// The solver shared by nl_cg_solve, nl_cg_history and nl_batch_cg_solve.
+nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit, int precond,
+                    double *hist, int cap, int *count, nl_cg_stats *stats, void *stream)
 {
-    if (!nl_plan_ok(p)) {
-        nl_set_error("nl_cg_solve: invalid plan");
-        return NL_EINVAL;
-    }
+    const int nrhs = op.nrhs;
     if (!f || !x || nrhs < 1 || nrhs > 65535 || !(rtol > 0.0) || maxit < 0 ||
         precond < NL_PRECOND_NONE || precond > NL_PRECOND_LEARNED) {
         nl_set_error("nl_cg_solve: bad argument");
         return NL_EINVAL;
     }
-    const bool pd = p->family == NL_PD_BOND;
-    if (!(p->symmetric || (pd && p->const_horizon))) {
-        nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER plan, or "
-                     "NL_PD_BOND with a constant horizon)");
-        return NL_EUNSUPPORTED;
-    }
     const bool flex = precond == NL_PRECOND_LEARNED;
-    if (flex && (!nl_net_valid(p->net) || pd || p->d != 2)) {
+    if (flex && (!op.net || !nl_net_valid(op.net))) {
         nl_set_error("nl_cg_solve: NL_PRECOND_LEARNED needs a network attached with "
                      "nl_plan_set_net on a symmetric 2-D scalar plan");
         return NL_EUNSUPPORTED;
     }
-    const int64_t per = pd ? 2 * p->N : p->N;
-    const int64_t len = per * nrhs;
-    nl_status s = ensure_workspace(p, len, per, nrhs);
+    nl_cg_state *c = op.state;
+    const int64_t len = op.total;
+    nl_status s = ensure_workspace(c, len, op.dinv_len, nrhs);
     if (s != NL_OK) return s;
     CgArgs a;
-    a.per = per; a.nrhs = nrhs;
+    a.per = op.per; a.seg_off = op.seg_off; a.seg_len = op.seg_len;
+    a.dinv_global = op.seg_off ? 1 : 0;
+    a.nrhs = nrhs;
     a.tol = 0.5 * rtol;
     a.f = (const double *)f; a.x = (double *)x;
-    a.r = p->cg_ws; a.z = a.r + len; a.p = a.z + len; a.q64 = a.p + len;
-    double *dinv = a.q64 + len;          // [per], after the four vectors
+    a.r = c->ws; a.z = a.r + len; a.p = a.z + len; a.q64 = a.p + len;
+    double *dinv = a.q64 + len;          // [dinv_len], after the four vectors
     a.dinv = dinv;
-    a.p32 = p->cg_ws32; a.q32 = a.p32 + len;
-    a.part = p->cg_red; a.sc = p->cg_red + (size_t)P_COUNT * nrhs * NB;
+    a.p32 = c->ws32; a.q32 = a.p32 + len;
+    a.part = c->red; a.sc = c->red + (size_t)P_COUNT * nrhs * NB;
 
-    cudaStream_t caller = nl_stream(stream), st = p->cg_stream;
-    NL_CUDA_TRY(cudaEventRecord(p->cg_ev, caller));
-    NL_CUDA_TRY(cudaStreamWaitEvent(st, p->cg_ev, 0));
+    cudaStream_t caller = nl_stream(stream), st = c->stream;
+    NL_CUDA_TRY(cudaEventRecord(c->ev, caller));
+    NL_CUDA_TRY(cudaStreamWaitEvent(st, c->ev, 0));
 
-    const unsigned g1 = (unsigned)((per + 255) / 256);
+    const unsigned g1 = (unsigned)((op.dinv_len + 255) / 256);
     k_zero<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(len, a.x);
     if (precond != NL_PRECOND_NONE) {
-        s = nl_diag_launch(p, a.x, dinv, st);
+        s = op.diag(op.ctx, a.x, dinv, st);
         if (s != NL_OK) return s;
     }
-    k_invert<<<g1, 256, 0, st>>>(per, dinv, precond != NL_PRECOND_NONE);
-    if (flex && (s = nl_net_reserve(p->net, p, nrhs, st)) != NL_OK) return s;
+    k_invert<<<g1, 256, 0, st>>>(op.dinv_len, dinv, precond != NL_PRECOND_NONE);
+    if (flex && (s = nl_net_reserve(op.net, op.net_plan, nrhs, st)) != NL_OK) return s;
     const dim3 grid(NB, nrhs);
     if (flex) {
         k_cg_init<true><<<grid, RB, 0, st>>>(a);
         k_cg_init_scalars<<<nrhs, 32, 0, st>>>(a);
-        if ((s = nl_net_apply_launch(p->net, p, a.r, a.z, nrhs, st)) != NL_OK) return s;
+        if ((s = nl_net_apply_launch(op.net, op.net_plan, a.r, a.z, nrhs, st)) != NL_OK) return s;
         k_cg_pz<<<grid, RB, 0, st>>>(a, -1, 0.0);
     } else {
         k_cg_init<false><<<grid, RB, 0, st>>>(a);
@@ -478,21 +485,21 @@ static nl_status cg_run(nl_plan *p, const void *f, void *x, int nrhs, double rto
     }
     NL_CUDA_TRY(cudaGetLastError());
     // one plain apply so that kernel attributes are set before capture
-    s = nl_direct_launch(p, a.p32, a.q32, nrhs, NL_F32, st);
+    s = op.apply(op.ctx, a.p32, a.q32, NL_F32, st);
     if (s != NL_OK) return s;
 
     // capture one chunk of iterations (the graph bakes in f, x, nrhs, the tolerance and the
     // preconditioner)
-    if (p->cg_graph_exec && (p->cg_graph_nrhs != nrhs || p->cg_graph_f != f ||
-                             p->cg_graph_x != x || p->cg_graph_tol != rtol ||
-                             p->cg_graph_precond != precond)) {
-        cudaGraphExecDestroy((cudaGraphExec_t)p->cg_graph_exec);
-        p->cg_graph_exec = nullptr;
+    if (c->graph_exec && (c->graph_nrhs != nrhs || c->graph_f != f || c->graph_x != x ||
+                          c->graph_tol != rtol || c->graph_precond != precond ||
+                          c->graph_net != (const void *)op.net)) {
+        cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+        c->graph_exec = nullptr;
     }
-    if (!p->cg_graph_exec) {
+    if (!c->graph_exec) {
         cudaGraph_t g = nullptr;
         NL_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        nl_status cs = enqueue_chunk(p, a, flex, CHUNK, st);
+        nl_status cs = enqueue_chunk(op, a, flex, CHUNK, st);
         cudaError_t ce = cudaStreamEndCapture(st, &g);
         if (cs != NL_OK) { if (g) cudaGraphDestroy(g); return cs; }
         if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaStreamEndCapture");
@@ -500,42 +507,44 @@ static nl_status cg_run(nl_plan *p, const void *f, void *x, int nrhs, double rto
         ce = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaGraphInstantiate");
-        p->cg_graph_exec = ge;
-        p->cg_graph_nrhs = nrhs;
-        p->cg_graph_f = f;
-        p->cg_graph_x = x;
-        p->cg_graph_tol = rtol;
-        p->cg_graph_precond = precond;
+        c->graph_exec = ge;
+        c->graph_nrhs = nrhs;
+        c->graph_f = f;
+        c->graph_x = x;
+        c->graph_tol = rtol;
+        c->graph_precond = precond;
+        c->graph_net = op.net;
     }
 
-    double *h = p->cg_host;
+    double *h = c->host;
     int iters = 0, restarts = 0, snaps = 0;
     bool conv_all = false;
+    const int64_t snap_len = op.per ? op.per : len;
     for (;;) {
-        NL_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)p->cg_graph_exec, st));
+        NL_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, st));
         iters += CHUNK;
         if (hist && snaps < cap) {
-            NL_CUDA_TRY(cudaMemcpyAsync(hist + (size_t)snaps * per, a.x, per * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
+            NL_CUDA_TRY(cudaMemcpyAsync(hist + (size_t)snaps * snap_len, a.x,
+                                        snap_len * sizeof(double), cudaMemcpyDeviceToDevice, st));
             ++snaps;
         }
         NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
-        NL_CUDA_TRY(cudaEventRecord(p->cg_ev, st));
-        if ((s = wait_bounded(p, 600.0)) != NL_OK) return s;
+        NL_CUDA_TRY(cudaEventRecord(c->ev, st));
+        if ((s = wait_bounded(c, 600.0)) != NL_OK) return s;
         bool all = true;
         for (int r = 0; r < nrhs; ++r) all = all && h[r * S_COUNT + S_CONV] != 0.0;
         const bool out_of_budget = iters >= maxit;
         if (!all && !out_of_budget) continue;
         // true FP64 residual f + L x
-        s = nl_direct_launch(p, a.x, a.q64, nrhs, NL_F64, st);
+        s = op.apply(op.ctx, a.x, a.q64, NL_F64, st);
         if (s != NL_OK) return s;
         k_cg_true<<<grid, RB, 0, st>>>(a);
         k_cg_true_scalars<<<nrhs, 32, 0, st>>>(a);
         NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
-        NL_CUDA_TRY(cudaEventRecord(p->cg_ev, st));
-        if ((s = wait_bounded(p, 600.0)) != NL_OK) return s;
+        NL_CUDA_TRY(cudaEventRecord(c->ev, st));
+        if ((s = wait_bounded(c, 600.0)) != NL_OK) return s;
         double worst = 0.0;
         for (int r = 0; r < nrhs; ++r) worst = fmax(worst, h[r * S_COUNT + S_TRUE]);
         if (worst <= rtol) { conv_all = true; break; }
@@ -543,7 +552,7 @@ static nl_status cg_run(nl_plan *p, const void *f, void *x, int nrhs, double rto
         // defect correction: restart the right-hand sides that missed
         if (flex) {
             k_cg_restart<true><<<grid, RB, 0, st>>>(a, rtol);
-            if ((s = nl_net_apply_launch(p->net, p, a.r, a.z, nrhs, st)) != NL_OK) return s;
+            if ((s = nl_net_apply_launch(op.net, op.net_plan, a.r, a.z, nrhs, st)) != NL_OK) return s;
             k_cg_pz<<<grid, RB, 0, st>>>(a, 1, rtol);
         } else {
             k_cg_restart<false><<<grid, RB, 0, st>>>(a, rtol);
@@ -571,10 +580,62 @@ static nl_status cg_run(nl_plan *p, const void *f, void *x, int nrhs, double rto
     return NL_OK;
 }
 
+// ---- the plan's operator ----
+struct PlanOpCtx { nl_plan *p; int nrhs; };
+
+static nl_status plan_apply(void *ctx, const void *in, void *out, int dtype, cudaStream_t st)
+{
+    PlanOpCtx *c = (PlanOpCtx *)ctx;
+    return nl_direct_launch(c->p, in, out, c->nrhs, dtype, st);
+}
+
+static nl_status plan_diag(void *ctx, const double *zin, double *d, cudaStream_t st)
+{
+    return nl_diag_launch(((PlanOpCtx *)ctx)->p, zin, d, st);
+}
+
+static nl_status plan_cg(nl_plan *p, const void *f, void *x, int nrhs, double rtol, int maxit,
+                         int precond, double *hist, int cap, int *count, nl_cg_stats *stats,
+                         void *stream)
+{
+    if (!nl_plan_ok(p)) {
+        nl_set_error("nl_cg_solve: invalid plan");
+        return NL_EINVAL;
+    }
+    const bool pd = p->family == NL_PD_BOND;
+    if (!(p->symmetric || (pd && p->const_horizon))) {
+        nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER plan, or "
+                     "NL_PD_BOND with a constant horizon)");
+        return NL_EUNSUPPORTED;
+    }
+    if (precond == NL_PRECOND_LEARNED && (pd || p->d != 2)) {
+        nl_set_error("nl_cg_solve: NL_PRECOND_LEARNED needs a symmetric 2-D scalar plan");
+        return NL_EUNSUPPORTED;
+    }
+    if (nrhs < 1 || nrhs > 65535) {
+        nl_set_error("nl_cg_solve: bad argument");
+        return NL_EINVAL;
+    }
+    PlanOpCtx ctx{ p, nrhs };
+    nl_cg_op op;
+    memset(&op, 0, sizeof(op));
+    op.nrhs = nrhs;
+    op.per = pd ? 2 * p->N : p->N;
+    op.total = op.per * nrhs;
+    op.dinv_len = op.per;
+    op.apply = plan_apply;
+    op.diag = plan_diag;
+    op.ctx = &ctx;
+    op.state = &p->cg;
+    op.net = p->net;
+    op.net_plan = p;
+    return nl_cg_run(op, f, x, rtol, maxit, precond, hist, cap, count, stats, stream);
+}
+
 extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, double rtol,
                                  int maxit, int precond, nl_cg_stats *stats, void *stream)
 {
-    return cg_run(p, f, x, nrhs, rtol, maxit, precond, nullptr, 0, nullptr, stats, stream);
+    return plan_cg(p, f, x, nrhs, rtol, maxit, precond, nullptr, 0, nullptr, stats, stream);
 }
 
 extern "C" nl_status nl_cg_history(nl_plan *p, const void *f, void *x, double rtol, int maxit,
@@ -585,5 +646,5 @@ extern "C" nl_status nl_cg_history(nl_plan *p, const void *f, void *x, double rt
         nl_set_error("nl_cg_history: need a history buffer with cap >= 1");
         return NL_EINVAL;
     }
-    return cg_run(p, f, x, 1, rtol, maxit, precond, history, cap, count, stats, stream);
+    return plan_cg(p, f, x, 1, rtol, maxit, precond, history, cap, count, stats, stream);
 }

@@ -750,6 +750,154 @@ static nl_status launch_split(nl_plan *p, const DirectArgs &a, const T *u, T *Lu
 }
 
 // ---------------------------------------------------------------------------
+// Batched instances in one persistent launch.  Work items are (instance, tile) pairs
+// numbered instance by instance; each block takes the next item from an atomic counter,
+// stages that instance's halo tile (its own n, R and fields) and applies the instance's
+// operator to the tile.  The shared-memory offset of a neighbour is computed from its
+// lattice offset, so the tile shape (BX, BY) is free (chosen by the autotuner).
+// ---------------------------------------------------------------------------
+struct BatchInst {
+    DirectArgs a;
+    int64_t off;        // element offset of the instance's fields in the concatenated vectors
+    int64_t tile0;      // first work item of the instance
+    int tiles_x;
+};
+
+enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2 };
+
+template <typename T, int KIND, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+k_batch_persistent(const BatchInst *__restrict__ inst, int ninst, int64_t total,
+                   int *__restrict__ counter, const T *__restrict__ u, T *__restrict__ Lu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    __shared__ int s_inst;
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    for (;;) {
+        if (tid == 0) {
+            const long long it = atomicAdd(counter, 1);
+            int k = 0;
+            if (it < total) {           // last instance whose first item is <= it
+                int hi = ninst - 1;
+                while (k < hi) {
+                    const int mid = (k + hi + 1) >> 1;
+                    if (inst[mid].tile0 <= it) k = mid; else hi = mid - 1;
+                }
+            }
+            s_item = it;
+            s_inst = k;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        const BatchInst &bi = inst[s_inst];
+        const DirectArgs &a = bi.a;
+        const int n = a.n, R = a.R;
+        const int64_t N = a.N;
+        const int64_t local = item - bi.tile0;
+        const int x0 = (int)(local % bi.tiles_x) * BX, y0 = (int)(local / bi.tiles_x) * BY;
+        const int sx = BX + 2 * R, sy = BY + 2 * R;
+        const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+        const bool own = x < n && y < n;
+        const int64_t i = own ? x + (int64_t)n * y : 0;
+        const int centre = (threadIdx.x + R) + sx * (threadIdx.y + R);
+        const T *__restrict__ bb = (const T *)a.b;
+        if constexpr (KIND == BK_PD) {
+            PdV<T> *tile = reinterpret_cast<PdV<T> *>(smem_raw);
+            const T *__restrict__ ux = u + bi.off;
+            const T *__restrict__ uy = ux + N;
+            for (int e = tid; e < sx * sy; e += BX * BY) {
+                const int gx = x0 - R + e % sx, gy = y0 - R + e / sx;
+                PdV<T> v;
+                if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                    const int64_t j = gx + (int64_t)n * gy;
+                    v.ux = ux[j]; v.uy = uy[j]; v.c = bb[j]; v.in = T(1);
+                } else {
+                    v.ux = T(0); v.uy = T(0); v.c = T(0); v.in = T(0);
+                }
+                tile[e] = v;
+            }
+            __syncthreads();
+            if (own) {
+                using Entry = typename Tab<T>::pd;
+                const Entry *__restrict__ tab = (const Entry *)a.tab;
+                const T uxi = ux[i], uyi = uy[i], ci = bb[i];
+                const int cnt = a.cnt[i];
+                double sxa = 0.0, sya = 0.0;
+                T px = T(0), py = T(0);
+                for (int t = 0; t < cnt; ++t) {
+                    const int4 o = a.off[t];
+                    const Entry en = tab[t];
+                    const PdV<T> v = tile[centre + o.x + sx * o.y];
+                    const T w = ci * v.in + v.c;
+                    const T dx = v.ux - uxi, dy = v.uy - uyi;
+                    px += w * ((T)en.gxx * dx + (T)en.gxy * dy);
+                    py += w * ((T)en.gxy * dx + (T)en.gyy * dy);
+                    if ((t & 31) == 31) { sxa += (double)px; sya += (double)py; px = T(0); py = T(0); }
+                }
+                sxa += (double)px;
+                sya += (double)py;
+                const double *E = a.pdext + 3 * i;
+                const double ox = a.pd_scale * (0.5 * sxa - (E[0] * (double)uxi + E[1] * (double)uyi));
+                const double oy = a.pd_scale * (0.5 * sya - (E[1] * (double)uxi + E[2] * (double)uyi));
+                T *out = Lu + bi.off;
+                out[i] = (T)ox;
+                out[N + i] = (T)oy;
+            }
+        } else {
+            using Elem = typename std::conditional<KIND == BK_SYM, V4<T>, V2<T>>::type;
+            using Entry = typename Tab<T>::type;
+            Elem *tile = reinterpret_cast<Elem *>(smem_raw);
+            const T *__restrict__ ur = u + bi.off;
+            const T *__restrict__ whv = (const T *)a.wh;
+            for (int e = tid; e < sx * sy; e += BX * BY) {
+                const int gx = x0 - R + e % sx, gy = y0 - R + e / sx;
+                Elem v;
+                if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                    const int64_t j = gx + (int64_t)n * gy;
+                    v.u = ur[j];
+                    v.b = bb[j];
+                    if constexpr (KIND == BK_SYM) { v.wh = whv[j]; v.thr = a.thr[j]; }
+                } else {
+                    v.u = T(0);
+                    v.b = T(0);
+                    if constexpr (KIND == BK_SYM) { v.wh = T(0); v.thr = -1; }
+                }
+                tile[e] = v;
+            }
+            __syncthreads();
+            if (own) {
+                const Entry *__restrict__ tab = (const Entry *)a.tab;
+                const T ui = ur[i];
+                const int cnt = a.cnt[i];
+                const T whi = (KIND == BK_SYM) ? whv[i] : T(0);
+                const int thri = a.thr[i];
+                T acc = T(0);
+                for (int t = 0; t < cnt; ++t) {
+                    const int4 o = a.off[t];
+                    const Entry en = tab[t];
+                    const Elem v = tile[centre + o.x + sx * o.y];
+                    T w;
+                    if constexpr (KIND == BK_SYM) {
+                        const T wi = (en.o2 <= thri) ? whi : T(0);
+                        const T wj = (en.o2 <= v.thr) ? v.wh : T(0);
+                        w = (T)en.g * v.b * (wi + wj);
+                    } else {
+                        w = (T)en.g * v.b;
+                    }
+                    acc += w * (v.u - ui);
+                }
+                const T fin = ((const T *)a.fin)[i];
+                const T ext = ((const T *)a.ext)[i];
+                Lu[bi.off + i] = fin * (acc - ui * ext);
+            }
+        }
+        __syncthreads();               // the tile and s_item are reused by the next item
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 // Raise a kernel's dynamic shared-memory limit once per (kernel, size): repeated calls
@@ -762,7 +910,9 @@ static int g_smem_count = 0;
 template <typename K>
 static cudaError_t prep_smem(K kernel, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    // below 32 KB no opt-in is needed even with a kernel's static shared arrays (the
+    // default limit covers static + dynamic <= 48 KB)
+    if (bytes <= 32 * 1024) return cudaSuccess;
     const void *key = (const void *)kernel;
     std::lock_guard<std::mutex> lock(g_smem_mu);
     int slot = -1;
@@ -985,4 +1135,80 @@ extern "C" nl_status nl_apply(nl_plan *p, const void *u, void *Lu, int nrhs, int
         return NL_EINVAL;
     }
     return nl_direct_launch(p, u, Lu, nrhs, dtype, nl_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// batch launcher (used by nl_batch.cu)
+// ---------------------------------------------------------------------------
+nl_status nl_batch_fill_inst(nl_plan *const *plans, int count, const int64_t *offsets, int shape,
+                             int dtype, void *host_out, int64_t *total_out)
+{
+    static const int bxs[3] = { 32, 32, 32 }, bys[3] = { 4, 8, 16 };
+    BatchInst *bi = reinterpret_cast<BatchInst *>(host_out);
+    int64_t t = 0;
+    for (int k = 0; k < count; ++k) {
+        bi[k].a = make_args(plans[k], dtype);
+        bi[k].off = offsets[k];
+        bi[k].tile0 = t;
+        bi[k].tiles_x = (plans[k]->n + bxs[shape] - 1) / bxs[shape];
+        t += (int64_t)bi[k].tiles_x * ((plans[k]->n + bys[shape] - 1) / bys[shape]);
+    }
+    *total_out = t;
+    return NL_OK;
+}
+
+size_t nl_batch_inst_bytes() { return sizeof(BatchInst); }
+
+template <typename T, int KIND, int BX, int BY>
+static nl_status launch_batch_t(const void *inst, int ninst, int64_t total, int *counter,
+                                const T *u, T *Lu, int Rmax, cudaStream_t st)
+{
+    size_t elem;
+    if (KIND == BK_PD) elem = sizeof(PdV<T>);
+    else if (KIND == BK_SYM) elem = sizeof(V4<T>);
+    else elem = sizeof(V2<T>);
+    const size_t smem = elem * (size_t)(BX + 2 * Rmax) * (BY + 2 * Rmax);
+    if (smem > 200 * 1024) {
+        nl_set_error("batched apply: halo tile of %zu bytes exceeds shared memory", smem);
+        return NL_EUNSUPPORTED;
+    }
+    auto kern = k_batch_persistent<T, KIND, BX, BY>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    int per_sm = 0;
+    NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX * BY, smem));
+    int dev = 0, sms = 0;
+    NL_CUDA_TRY(cudaGetDevice(&dev));
+    NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t blocks = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
+    if (blocks > total) blocks = total;
+    if (blocks < 1) blocks = 1;
+    NL_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    kern<<<(unsigned)blocks, dim3(BX, BY), smem, st>>>((const BatchInst *)inst, ninst, total,
+                                                       counter, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, int ninst,
+                          int64_t total, int *counter, const void *u, void *Lu, int Rmax,
+                          cudaStream_t st)
+{
+#define NL_BATCH_SHAPES(T, KIND)                                                                   \
+    do {                                                                                           \
+        if (shape == 0) return launch_batch_t<T, KIND, 32, 4>(inst_dev, ninst, total, counter,    \
+                                                              (const T *)u, (T *)Lu, Rmax, st);   \
+        if (shape == 1) return launch_batch_t<T, KIND, 32, 8>(inst_dev, ninst, total, counter,    \
+                                                              (const T *)u, (T *)Lu, Rmax, st);   \
+        return launch_batch_t<T, KIND, 32, 16>(inst_dev, ninst, total, counter, (const T *)u,     \
+                                               (T *)Lu, Rmax, st);                                 \
+    } while (0)
+    if (dtype == NL_F32) {
+        if (kind == BK_PD) NL_BATCH_SHAPES(float, BK_PD);
+        if (kind == BK_SYM) NL_BATCH_SHAPES(float, BK_SYM);
+        NL_BATCH_SHAPES(float, BK_SCALAR);
+    }
+    if (kind == BK_PD) NL_BATCH_SHAPES(double, BK_PD);
+    if (kind == BK_SYM) NL_BATCH_SHAPES(double, BK_SYM);
+    NL_BATCH_SHAPES(double, BK_SCALAR);
+#undef NL_BATCH_SHAPES
 }

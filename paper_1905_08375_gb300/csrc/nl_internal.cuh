@@ -29,6 +29,41 @@ struct __align__(16) OffEntry64 { int soff; int o2; double g; };
 struct __align__(16) PdEntry32 { int soff; float gxx, gxy, gyy; };
 struct __align__(16) PdEntry64 { int soff; int pad; double gxx, gxy, gyy; };
 
+// CG workspace and the captured graph of one chunk of iterations (owned by a plan or batch)
+struct nl_cg_state {
+    double *ws; size_t ws_elems;
+    float *ws32; size_t ws32_elems;
+    double *red; size_t red_elems;
+    double *host; size_t host_elems;
+    cudaStream_t stream;
+    cudaEvent_t ev;
+    void *graph_exec;               // cudaGraphExec_t
+    int graph_nrhs;
+    const void *graph_f, *graph_x;
+    double graph_tol;
+    int graph_precond;
+    const void *graph_net;
+};
+
+// The operator CG works with: nrhs segments (right-hand sides or batch instances) of the
+// concatenated vectors; apply writes L in (FP32 or FP64), diag the FP64 diagonal of -L.
+struct nl_cg_op {
+    int nrhs;
+    int64_t per;                    // uniform segment length (0 when seg_off/seg_len are used)
+    int64_t total;                  // total length of the concatenated vectors
+    const int64_t *seg_off, *seg_len;   // device arrays [nrhs], or nullptr for uniform
+    int64_t dinv_len;               // per (uniform) or total
+    nl_status (*apply)(void *ctx, const void *in, void *out, int dtype, cudaStream_t st);
+    nl_status (*diag)(void *ctx, const double *zin, double *d, cudaStream_t st);
+    void *ctx;
+    nl_cg_state *state;
+    nl_net *net;                    // flexible preconditioner (plan operators only)
+    nl_plan *net_plan;
+};
+nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit, int precond,
+                    double *hist, int cap, int *count, nl_cg_stats *stats, void *stream);
+nl_status nl_cg_state_release(nl_cg_state *c);
+
 struct nl_plan {
     uint32_t magic;
     int version;
@@ -77,18 +112,7 @@ struct nl_plan {
     unsigned long long *fast_mx;    // max |v| of the last FP32 apply (fixed-point scale)
     int prof_on, prof_count;        // per-phase timing of the fast apply
     cudaEvent_t prof_ev[64][3];
-    // CG workspace (allocated on the first nl_cg_solve, grown for more right-hand sides)
-    double *cg_ws; size_t cg_ws_elems;
-    float *cg_ws32; size_t cg_ws32_elems;
-    double *cg_red; size_t cg_red_elems;
-    double *cg_host; size_t cg_host_elems;
-    cudaStream_t cg_stream;
-    cudaEvent_t cg_ev;
-    void *cg_graph_exec;            // cudaGraphExec_t of one chunk of iterations
-    int cg_graph_nrhs;
-    const void *cg_graph_f, *cg_graph_x;
-    double cg_graph_tol;
-    int cg_graph_precond;
+    nl_cg_state cg;                 // CG workspace (allocated on the first solve)
     double *dinv64;                 // inverse Jacobi diagonal (computed on first use)
     nl_net *net;                    // learned preconditioner (not owned)
     size_t device_bytes;
@@ -122,6 +146,12 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
                             cudaStream_t st);
 nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st);
 nl_status nl_cg_release(nl_plan *p);
+nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, int ninst,
+                          int64_t total, int *counter, const void *u, void *Lu, int Rmax,
+                          cudaStream_t st);
+nl_status nl_batch_fill_inst(nl_plan *const *plans, int count, const int64_t *offsets, int shape,
+                             int dtype, void *host_out, int64_t *total_out);
+size_t nl_batch_inst_bytes();
 void nl_invert_launch(int64_t n, double *d, cudaStream_t st);
 nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,
                               cudaStream_t st);
