@@ -7,7 +7,8 @@ delta = h (4 + 12 s), lognormal coefficient a(x) a(y), Gaussian random field u)
 value = grid points processed per second over both applies (2 N per step), Gpts/s.
 
 Other workloads (--workload): c1 1-D FP64 direct (4096 nodes); c3 2-D peridynamics 512^2
-FP32; c4 CG to relative residual 1e-8 on 256^2 (Jacobi; time per solve); c5 3-D 256^3 with
+FP32; c3b batched Jacobi-CG to 1e-8 over 64 uneven peridynamic instances 128^2..512^2 (the
+operator one persistent launch over all instances; time per solve); c4 CG to relative residual 1e-8 on 256^2 (Jacobi; time per solve); c5 3-D 256^3 with
 8 right-hand sides, direct + fast FP32; ex1 / ex2 the paper's Example 1 (2-D, delta = 1/2,
 128^2) and Example 2 (1-D, K = 3, 4096 nodes), fast vs direct in FP64.
 
@@ -375,6 +376,80 @@ class C3(Workload):
         return {"pd": oracle.pd_direct(f["u"], 2, n, f["delta"], f["c"], idx=idx)[0]}, len(idx)
 
 
+class C3B(Workload):
+    """64 uneven peridynamic instances, 128^2 .. 512^2: batched Jacobi-CG to 1e-8 per step."""
+    name = "c3b"
+    metric = ("batched CG time to relative residual 1e-8 (FP64 true residual, worst instance) "
+              "over 64 uneven 2-D peridynamic instances 128^2..512^2, ms")
+    unit = "ms"
+    higher_is_better = False
+    dtype = "f32 operator, f64 vectors and reductions"
+
+    def setup(self, count=64):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.sizes = synth.pd_batch_sizes(count, 128, 512)
+        self.inst = []
+        for k, n in enumerate(self.sizes):
+            f = synth.pd_2d(n=n, seed=self.seed * 1000 + k, radius_cells=8)
+            self.inst.append((n, f["delta"], f["c"], f["u"][0].reshape(-1)))
+        self.batch = nl.nl_batch_create([(n, d, c) for n, d, c, _ in self.inst],
+                                        family=nl.NL_PD_BOND, coef=nl.NL_COEF_MEAN,
+                                        tile_shape=nl.NL_TILE_AUTO)
+        self.rhs = np.concatenate([u for *_, u in self.inst])
+        self.fr = torch.tensor(self.rhs, dtype=torch.float64, device=self.dev)
+        self.x = torch.empty_like(self.fr)
+        self.units = 1
+        self.points = int(sum(n * n for n in self.sizes))
+        self.config = {"workload": "64 uneven 2D linear bond-based PD instances, n_k = 128 + "
+                                   "round(384 k/63), delta=8h, two-phase Voronoi c in {1,10}; "
+                                   "one batched Jacobi-CG to rtol 1e-8 (FP64 true residual) per "
+                                   "step, operator = one persistent launch over all instances",
+                       "instances": count, "points": self.points,
+                       "tile_shape": ["32x4", "32x8", "32x16"][self.batch.tile_shape]}
+        self.last = None
+
+    def step(self):
+        self.last = self.nl.nl_batch_cg_solve(self.batch, self.fr, self.x, rtol=1e-8,
+                                              maxit=100000)
+
+    def value(self, ms):
+        return ms
+
+    def kernels(self, flush, reps):
+        torch, nl = self.torch, self.nl
+        u = torch.randn(self.batch.total, device=self.dev)
+        o = torch.empty_like(u)
+        t = self.time_fn(lambda: nl.nl_batch_apply(self.batch, u, o), reps, flush)
+        nb = float(sum(ball_counts(d, n, 2).sum() for n, d, _, _ in self.inst))
+        if self.last:
+            self.launches = 5 * self.last["iterations"] + 8
+        roof = _alu_roof("k_batch_persistent<float,PD> (all 64 instances, one launch)",
+                         14.0 * nb, t, FP32_PEAK_TFLOPS, FP32_SRC)
+        roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond, all instances)"
+        return roof, {"batch_apply_fp32_ms": round(t, 4),
+                      "batch_apply_gpts_s": round(self.points / (t * 1e-3) / 1e9, 3),
+                      "cg": self.last}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        fh = torch.tensor(self.rhs, dtype=torch.float64).pin_memory()
+        xh = torch.empty_like(fh).pin_memory()
+        fd = torch.empty_like(self.fr)
+
+        def one():
+            fd.copy_(fh, non_blocking=True)
+            self.nl.nl_batch_cg_solve(self.batch, fd, self.x, rtol=1e-8, maxit=100000)
+            xh.copy_(self.x, non_blocking=True)
+        ms = self.time_fn(one, max(1, steps), flush)
+        b = int(fh.numel()) * 8
+        return {"value": round(ms, 4), "unit": "ms", "h2d_bytes_per_step": b,
+                "d2h_bytes_per_step": b, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"x": self.x.cpu().numpy()}
+
+
 class C4(Workload):
     name = "c4"
     metric = "CG time to relative residual 1e-8 (FP64 true residual) on -L u = f, 256^2, ms"
@@ -577,7 +652,7 @@ class EX(Workload):
 def make_workload(name, dev, seed):
     if name in ("ex1", "ex2"):
         return EX(dev, seed, name)
-    return {"c1": C1, "c2": C2, "c3": C3, "c4": C4, "c5": C5}[name](dev, seed)
+    return {"c1": C1, "c2": C2, "c3": C3, "c3b": C3B, "c4": C4, "c5": C5}[name](dev, seed)
 
 
 # ---------------------------------------------------------------------------
@@ -603,6 +678,24 @@ def oracle_sample(w, outs, budget_s=20.0):
                  "kind": "oracle", "sample": f"one full FP64 Jacobi-CG solve at {w.n}^2 "
                                              f"({it} iterations)"},
                 {"gpu_solution_fp64_oracle_residual": res})
+    if name == "c3b":
+        n, d, c, f0 = w.inst[0]
+        t0 = time.perf_counter()
+        _, it, _ = oracle.cg(f0, 2, n, d, kind="pd", c=c, rtol=1e-8)
+        dt = time.perf_counter() - t0
+        scale = w.points / float(n * n)
+        par = {}
+        for k in (0, len(w.inst) // 2, len(w.inst) - 1):
+            nk, dk, ck, fk = w.inst[k]
+            sl = slice(int(w.batch.offsets[k]), int(w.batch.offsets[k + 1]))
+            Lx = oracle.pd_direct(outs["x"][sl].reshape(1, 2, -1), 2, nk, dk, ck).reshape(-1)
+            par[f"instance{k}_n{nk}_fp64_oracle_residual"] = float(
+                np.linalg.norm(fk + Lx) / np.linalg.norm(fk))
+        return ({"value": round(dt * 1e3 * scale, 1), "unit": "ms", "cores": oracle.num_threads(),
+                 "kind": "oracle",
+                 "sample": f"one FP64 Jacobi-CG solve of the 128^2 instance ({it} iterations, "
+                           f"{dt * 1e3:.0f} ms), scaled by total points / 128^2 = {scale:.1f} "
+                           "(a lower bound: larger instances need more iterations)"}, par)
     if name == "c5":
         n, N = 256, 256 ** 3
         f = w.f
@@ -682,8 +775,8 @@ def run_gpu(args, peaks):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     steps = args.steps
-    if w.name == "c4":
-        steps = max(3, min(steps, 20))       # one step is a whole solve
+    if w.name in ("c4", "c3b"):
+        steps = max(3, min(steps, 20 if w.name == "c4" else 5))   # one step is a whole solve
     if w.name == "c5":
         steps = max(3, min(steps, 30))
     for _ in range(args.warmup):
@@ -771,7 +864,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c4", "c5", "ex1", "ex2"])
+                    choices=["c1", "c2", "c3", "c3b", "c4", "c5", "ex1", "ex2"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
