@@ -82,14 +82,17 @@ typedef enum { NL_SELF_DISCRETE = 0, NL_SELF_PAPER = 1 } nl_self;
 
 /* How nl_apply_fast forms the Step 2/3 sums for K = 0 with FP32 data (FP64 data and K > 0
  * always use FP64 panel moments summed panel by panel):
- *   NL_FAST_AUTO (0) = NL_FAST_ROWPREFIX
+ *   NL_FAST_AUTO (0) = NL_FAST_LEAFROWS
  *   NL_FAST_PANELS (1): exact 64-bit fixed-point panel sums (one rounding of each leaf value
- *       to a multiple of 2^-S chosen from max |a u|), added panel by panel;
- *   NL_FAST_ROWPREFIX (2): the same integers kept as prefix sums along each panel row, so the
- *       panels of a run are added as one difference -- bitwise the same result;
- *   NL_FAST_FP64_PANELS (3): FP64 panel sums added panel by panel, as for FP64 data. */
+ *       to a multiple of 2^-S chosen from max |a u|), added panel by panel (Sec. 3, Steps 1-3);
+ *   NL_FAST_ROWPREFIX (2): the same integers kept as prefix sums along each panel row of every
+ *       level, so the panels of a run are added as one difference -- bitwise the same result;
+ *   NL_FAST_FP64_PANELS (3): FP64 panel sums added panel by panel, as for FP64 data;
+ *   NL_FAST_LEAFROWS (4): the panels of Algorithm 1 tile exactly the leaf cells that meet the
+ *       ball, so their sum is taken row by row from the leaf-row prefix sums, one difference
+ *       per leaf row -- the same integers again, bitwise the same result. */
 typedef enum { NL_FAST_AUTO = 0, NL_FAST_PANELS = 1, NL_FAST_ROWPREFIX = 2,
-               NL_FAST_FP64_PANELS = 3 } nl_fast_variant;
+               NL_FAST_FP64_PANELS = 3, NL_FAST_LEAFROWS = 4 } nl_fast_variant;
 
 typedef struct {
     int dim;   /* d in {1, 2, 3} */

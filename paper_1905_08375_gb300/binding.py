@@ -20,7 +20,7 @@ NL_F32, NL_F64 = 0, 1
 NL_POWER, NL_POLY, NL_PD_BOND = 0, 1, 2
 NL_COEF_NONE, NL_COEF_X, NL_COEF_XY, NL_COEF_MEAN = 0, 1, 2, 3
 NL_SELF_DISCRETE, NL_SELF_PAPER = 0, 1
-NL_FAST_AUTO, NL_FAST_PANELS, NL_FAST_ROWPREFIX, NL_FAST_FP64_PANELS = 0, 1, 2, 3
+NL_FAST_AUTO, NL_FAST_PANELS, NL_FAST_ROWPREFIX, NL_FAST_FP64_PANELS, NL_FAST_LEAFROWS = 0, 1, 2, 3, 4
 NL_PRECOND_NONE, NL_PRECOND_JACOBI = 0, 1
 
 _STATUS = {0: "NL_OK", 1: "NL_EINVAL", 2: "NL_EUNSUPPORTED", 3: "NL_ENOMEM", 4: "NL_ECUDA",

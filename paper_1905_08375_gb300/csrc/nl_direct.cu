@@ -10,7 +10,9 @@
 // ragged per-node horizon costs nothing beyond its own ball.  Table entries
 // are warp-uniform (broadcast loads); tile reads are consecutive in x across a
 // warp (conflict-free).
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "nl_internal.cuh"
 
@@ -434,10 +436,10 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
 // traversal as k_direct2d_rb, but each thread owns two columns, c and c + 32, of RB_P rows,
 // and every multiply/add runs as one paired f32x2 instruction on the two columns (per element
 // IEEE round-to-nearest, so each column's result is bitwise the single-column one).  A block of
-// 32 x X2_TY threads covers 64 columns and X2_TY * RB_P rows; the tile is kept as separate u
-// and b planes so that a warp's loads are 32 consecutive floats.
+// 32 x TY threads covers 64 columns and TY * RB_P rows (TY = 2 or 4, chosen per plan by timing
+// both); the tile is kept as separate u and b planes so that a warp's loads are 32 consecutive
+// floats.  A thread's outputs and its summation order do not depend on TY.
 // ---------------------------------------------------------------------------
-constexpr int X2_TY = 4;
 typedef unsigned long long f2_t;
 
 __device__ __forceinline__ f2_t f2_pack(float lo, float hi)
@@ -477,204 +479,260 @@ __device__ __forceinline__ int isqrt_small(int x)   // floor(sqrt(x)), 0 <= x < 
     return h;
 }
 
+// One masked chunk of HC rows (offsets oy .. oy + HC - 1 of column ox) for the RB_P outputs
+// of each column pair; rows outside an output's ball get weight 0.
+template <int HC, bool MASK>
+__device__ __forceinline__ void x2_chunk(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                         f2_t (&Wu)[RB_P], f2_t (&Wb)[RB_P],
+                                         const int (&thra)[RB_P], const int (&thrb)[RB_P],
+                                         const float *cu, int SX, int plane, const float *gcol,
+                                         int oy, int ox2, int R)
+{
+    f2_t Xu[HC], Xb[HC];
+    const float *rp = cu + (oy + RB_P) * SX;
+#pragma unroll
+    for (int k = 0; k < HC; ++k) {
+        Xu[k] = f2_pack(rp[k * SX], rp[k * SX + 32]);
+        Xb[k] = f2_pack(rp[k * SX + plane], rp[k * SX + plane + 32]);
+    }
+#pragma unroll
+    for (int j = 0; j < HC; ++j) {
+        const int oyj = oy + j;
+        const float g = gcol[MASK ? min(oyj, R) : oyj];
+        const int o2 = ox2 + oyj * oyj;
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int k = p + j;
+            const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
+            const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
+            f2_t w;
+            if (MASK) {
+                w = f2_mul(vb, f2_pack(o2 <= thra[p] ? g : 0.f, o2 <= thrb[p] ? g : 0.f));
+            } else {
+                w = f2_mul(vb, f2_pack(g, g));
+            }
+            acc[p] = f2_fma(w, f2_sub(vu, ui[p]), acc[p]);
+        }
+    }
+    if (HC < RB_P) {
+#pragma unroll
+        for (int k = 0; k < RB_P - HC; ++k) { Wu[k] = Wu[k + HC]; Wb[k] = Wb[k + HC]; }
+#pragma unroll
+        for (int k = 0; k < HC; ++k) { Wu[RB_P - HC + k] = Xu[k]; Wb[RB_P - HC + k] = Xb[k]; }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RB_P; ++k) { Wu[k] = Xu[k]; Wb[k] = Xb[k]; }
+    }
+}
+
 // RM: compile-time halo (>= the plan's largest radius) so that every shared-memory offset
-// is an immediate
-template <int RM>
-__global__ void __launch_bounds__(32 * X2_TY, 4)
+// is an immediate.  Persistent: each block takes 64 x 32 tiles (times right-hand sides) from a
+// queue ordered by decreasing cost (the sum of the tile's ball sizes, largest first); the
+// last block to finish resets the queue for the next launch on the stream.
+template <int RM, int TY>
+__global__ void __launch_bounds__(32 * TY, 16 / TY)
 k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
-              float *__restrict__ Lu)
+              float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
+              int nrhs, int *__restrict__ queue)
 {
     constexpr int SX = 64 + 2 * RM;
-    constexpr int SY = X2_TY * RB_P + 2 * RM + RB_P;
-    constexpr int GW = 2 * RM + 1;
+    constexpr int SY = TY * RB_P + 2 * RM + RB_P;
+    constexpr int HC = RB_P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
     const int n = a.n, R = a.R;                      // R <= RM
     float *su = reinterpret_cast<float *>(smem_raw);
     float *sb = su + SX * SY;
     const int64_t N = a.N;
-    const float *__restrict__ ur = u + (int64_t)blockIdx.z * N;
     const float *__restrict__ bb = (const float *)a.b;
-    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * (X2_TY * RB_P);
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    for (int e = tid; e < SX * SY; e += 32 * X2_TY) {
-        const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
-        float uv = 0.f, bv = 0.f;
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-            const int64_t j = gx + (int64_t)n * gy;
-            uv = ur[j];
-            bv = bb[j];
-        }
-        su[e] = uv;
-        sb[e] = bv;
-    }
-    __syncthreads();
-
-    const int xa = x0 + threadIdx.x, xb = xa + 32;
-    const int ybase = y0 + threadIdx.y * RB_P;
-    f2_t ui[RB_P], acc[RB_P];
-    int thra[RB_P], thrb[RB_P];
-    int tmax = -1, tmin = 1 << 30;
-    // tile position of output (p, column a): row row0 + p, column col0
-    const float *ua = su + (threadIdx.y * RB_P + RM) * SX + threadIdx.x + RM;
-#pragma unroll
-    for (int p = 0; p < RB_P; ++p) {
-        const int y = ybase + p;
-        const bool oa = xa < n && y < n, ob = xb < n && y < n;
-        thra[p] = oa ? a.thr[xa + (int64_t)n * y] : -1;
-        thrb[p] = ob ? a.thr[xb + (int64_t)n * y] : -1;
-        tmax = max(tmax, max(thra[p], thrb[p]));
-        tmin = min(tmin, min(oa ? thra[p] : tmin, ob ? thrb[p] : tmin));
-        ui[p] = f2_pack(ua[p * SX], ua[p * SX + 32]);
-        acc[p] = f2_pack(0.f, 0.f);
-    }
-    if (tmin == (1 << 30)) tmin = -1;
-    const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-
-    for (int ox = -rx; ox <= rx; ++ox) {
-        const int ox2 = ox * ox;
-        if (ox2 > tmax) continue;
-        const int hmax = min(R, isqrt_small(tmax - ox2));
-        const int hmin = (tmin >= ox2) ? isqrt_small(tmin - ox2) : -1;
-        // column base: tile row of (p = 0, oy = 0) is row0; base points at row row0
-        const float *cu = ua + ox;
-        const float *cb = cu + SX * SY;
-        const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
-        f2_t Wu[RB_P], Wb[RB_P];
-        int oy = -hmax;
-#pragma unroll
-        for (int k = 0; k < RB_P; ++k) {
-            Wu[k] = f2_pack(cu[(oy + k) * SX], cu[(oy + k) * SX + 32]);
-            Wb[k] = f2_pack(cb[(oy + k) * SX], cb[(oy + k) * SX + 32]);
-        }
-        // top rim (rows outside some output's ball): single masked rows
-        for (; oy < -hmin && oy <= hmax; ++oy) {
-            const int o2 = ox2 + oy * oy;
-            const float g = gcol[oy];
-#pragma unroll
-            for (int p = 0; p < RB_P; ++p) {
-                float b0, b1;
-                f2_unpack(Wb[p], b0, b1);
-                b0 = (o2 <= thra[p]) ? b0 * g : 0.f;
-                b1 = (o2 <= thrb[p]) ? b1 * g : 0.f;
-                acc[p] = f2_fma(f2_pack(b0, b1), f2_sub(Wu[p], ui[p]), acc[p]);
-            }
-#pragma unroll
-            for (int k = 0; k < RB_P - 1; ++k) { Wu[k] = Wu[k + 1]; Wb[k] = Wb[k + 1]; }
-            const float *rp = cu + (oy + RB_P) * SX;
-            Wu[RB_P - 1] = f2_pack(rp[0], rp[32]);
-            Wb[RB_P - 1] = f2_pack(rp[SX * SY], rp[SX * SY + 32]);
-        }
-        // full chunks of RB_P rows inside every output's ball: unmasked
-        for (; oy + RB_P - 1 <= hmin; oy += RB_P) {
-            f2_t Xu[RB_P - 1], Xb[RB_P - 1];
-            const float *rp = cu + (oy + RB_P) * SX;
-#pragma unroll
-            for (int k = 0; k < RB_P - 1; ++k) {
-                Xu[k] = f2_pack(rp[k * SX], rp[k * SX + 32]);
-                Xb[k] = f2_pack(rp[k * SX + SX * SY], rp[k * SX + SX * SY + 32]);
-            }
-#pragma unroll
-            for (int j = 0; j < RB_P; ++j) {
-                const float g = gcol[oy + j];
-                const f2_t gg = f2_pack(g, g);
-#pragma unroll
-                for (int p = 0; p < RB_P; ++p) {
-                    const int k = p + j;
-                    const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
-                    const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
-                    acc[p] = f2_fma(f2_mul(vb, gg), f2_sub(vu, ui[p]), acc[p]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < RB_P - 1; ++k) { Wu[k] = Xu[k]; Wb[k] = Xb[k]; }
-            const float *rq = cu + (oy + 2 * RB_P - 1) * SX;
-            Wu[RB_P - 1] = f2_pack(rq[0], rq[32]);
-            Wb[RB_P - 1] = f2_pack(rq[SX * SY], rq[SX * SY + 32]);
-        }
-        // the rest in half chunks of RB_P / 2 rows, unmasked where still inside every ball
-        constexpr int HC = RB_P / 2;
-        for (; oy <= hmax; oy += HC) {
-            const bool core = oy + HC - 1 <= hmin;
-            f2_t Xu[HC], Xb[HC];
-            const float *rp = cu + (oy + RB_P) * SX;
-#pragma unroll
-            for (int k = 0; k < HC; ++k) {
-                Xu[k] = f2_pack(rp[k * SX], rp[k * SX + 32]);
-                Xb[k] = f2_pack(rp[k * SX + SX * SY], rp[k * SX + SX * SY + 32]);
-            }
-            if (core) {
-#pragma unroll
-                for (int j = 0; j < HC; ++j) {
-                    const float g = gcol[oy + j];
-                    const f2_t gg = f2_pack(g, g);
-#pragma unroll
-                    for (int p = 0; p < RB_P; ++p) {
-                        const int k = p + j;
-                        const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
-                        const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
-                        acc[p] = f2_fma(f2_mul(vb, gg), f2_sub(vu, ui[p]), acc[p]);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < HC; ++j) {
-                    const int oyj = oy + j;
-                    const int o2 = ox2 + oyj * oyj;
-                    const float g = gcol[min(oyj, R)];
-#pragma unroll
-                    for (int p = 0; p < RB_P; ++p) {
-                        const int k = p + j;
-                        const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
-                        const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
-                        float b0, b1;
-                        f2_unpack(vb, b0, b1);
-                        b0 = (o2 <= thra[p]) ? b0 * g : 0.f;
-                        b1 = (o2 <= thrb[p]) ? b1 * g : 0.f;
-                        acc[p] = f2_fma(f2_pack(b0, b1), f2_sub(vu, ui[p]), acc[p]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < HC; ++k) { Wu[k] = Wu[k + HC]; Wb[k] = Wb[k + HC]; }
-#pragma unroll
-            for (int k = 0; k < HC; ++k) { Wu[HC + k] = Xu[k]; Wb[HC + k] = Xb[k]; }
-        }
-    }
     const float *__restrict__ finv = (const float *)a.fin;
     const float *__restrict__ extv = (const float *)a.ext;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int total = ntiles * nrhs;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int tile = order[item / nrhs], z = item % nrhs;
+        const float *__restrict__ ur = u + (int64_t)z * N;
+        const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * (TY * RB_P);
+        for (int e = tid; e < SX * SY; e += 32 * TY) {
+            const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
+            float uv = 0.f, bv = 0.f;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                const int64_t j = gx + (int64_t)n * gy;
+                uv = ur[j];
+                bv = bb[j];
+            }
+            su[e] = uv;
+            sb[e] = bv;
+        }
+        __syncthreads();
+
+        const int xa = x0 + threadIdx.x, xb = xa + 32;
+        const int ybase = y0 + threadIdx.y * RB_P;
+        f2_t ui[RB_P], acc[RB_P];
+        int thra[RB_P], thrb[RB_P];
+        int tmax = -1, tmin = 1 << 30;
+        const float *ua = su + (threadIdx.y * RB_P + RM) * SX + threadIdx.x + RM;
 #pragma unroll
-    for (int p = 0; p < RB_P; ++p) {
-        const int y = ybase + p;
-        float s0, s1, u0, u1;
-        f2_unpack(acc[p], s0, s1);
-        f2_unpack(ui[p], u0, u1);
-        if (y < n && xa < n) {
-            const int64_t i = xa + (int64_t)n * y;
-            Lu[(int64_t)blockIdx.z * N + i] = finv[i] * (s0 - u0 * extv[i]);
+        for (int p = 0; p < RB_P; ++p) {
+            const int y = ybase + p;
+            const bool oa = xa < n && y < n, ob = xb < n && y < n;
+            thra[p] = oa ? a.thr[xa + (int64_t)n * y] : -1;
+            thrb[p] = ob ? a.thr[xb + (int64_t)n * y] : -1;
+            tmax = max(tmax, max(thra[p], thrb[p]));
+            tmin = min(tmin, min(oa ? thra[p] : tmin, ob ? thrb[p] : tmin));
+            ui[p] = f2_pack(ua[p * SX], ua[p * SX + 32]);
+            acc[p] = f2_pack(0.f, 0.f);
         }
-        if (y < n && xb < n) {
-            const int64_t i = xb + (int64_t)n * y;
-            Lu[(int64_t)blockIdx.z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+        if (tmin == (1 << 30)) tmin = -1;
+        const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
+
+        for (int ox = -rx; ox <= rx; ++ox) {
+            const int ox2 = ox * ox;
+            if (ox2 > tmax) continue;
+            const int hmax = min(R, isqrt_small(tmax - ox2));
+            const int hmin = (tmin >= ox2) ? isqrt_small(tmin - ox2) : -1;
+            const float *cu = ua + ox;
+            const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
+            f2_t Wu[RB_P], Wb[RB_P];
+            int oy = -hmax;
+#pragma unroll
+            for (int k = 0; k < RB_P; ++k) {
+                Wu[k] = f2_pack(cu[(oy + k) * SX], cu[(oy + k) * SX + 32]);
+                Wb[k] = f2_pack(cu[(oy + k) * SX + SX * SY], cu[(oy + k) * SX + SX * SY + 32]);
+            }
+            // top rim: masked half chunks until every output's ball covers the rows
+            for (; oy < -hmin && oy <= hmax; oy += HC)
+                x2_chunk<HC, true>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
+            // core: full chunks inside every output's ball
+            for (; oy + RB_P - 1 <= hmin; oy += RB_P)
+                x2_chunk<RB_P, false>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
+            // the rest: half chunks, unmasked while still inside every ball
+            for (; oy <= hmax; oy += HC) {
+                if (oy + HC - 1 <= hmin)
+                    x2_chunk<HC, false>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
+                else
+                    x2_chunk<HC, true>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
+            }
         }
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int y = ybase + p;
+            float s0, s1, u0, u1;
+            f2_unpack(acc[p], s0, s1);
+            f2_unpack(ui[p], u0, u1);
+            if (y < n && xa < n) {
+                const int64_t i = xa + (int64_t)n * y;
+                Lu[(int64_t)z * N + i] = finv[i] * (s0 - u0 * extv[i]);
+            }
+            if (y < n && xb < n) {
+                const int64_t i = xb + (int64_t)n * y;
+                Lu[(int64_t)z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+            }
+        }
+        __syncthreads();               // the tile and s_item are reused by the next item
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) { queue[0] = 0; queue[1] = 0; }
     }
 }
 
-template <int RM>
+template <int RM, int TY>
 static size_t x2_smem_bytes()
 {
-    return sizeof(float) * (size_t)2 * (64 + 2 * RM) * (X2_TY * RB_P + 2 * RM + RB_P);
+    return sizeof(float) * (size_t)2 * (64 + 2 * RM) * (TY * RB_P + 2 * RM + RB_P);
+}
+
+template <int RM, int TY>
+static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                             int nrhs, const int *order, int ntiles, int *blocks_cache,
+                             cudaStream_t st)
+{
+    const dim3 blk(32, TY, 1);
+    const size_t smem = x2_smem_bytes<RM, TY>();
+    auto kern = k_direct2d_x2<RM, TY>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    const int tiles_x = (p->n + 63) / 64;
+    const int64_t items = (int64_t)ntiles * nrhs;
+    if (items >= (int64_t)1 << 31) {
+        nl_set_error("nl_apply: %lld tiles x right-hand sides exceed the tile queue", (long long)items);
+        return NL_EUNSUPPORTED;
+    }
+    if (items == 0) return NL_OK;
+    if (*blocks_cache == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem));
+        NL_CUDA_TRY(cudaGetDevice(&dev));
+        NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        *blocks_cache = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int64_t blocks = std::min<int64_t>(*blocks_cache, items);
+    kern<<<(unsigned)blocks, blk, smem, st>>>(a, p->rb_g32, u, Lu, order, ntiles, tiles_x, nrhs,
+                                              p->x2_queue);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
 }
 
 template <int RM>
 static nl_status launch_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu, int nrhs,
                            cudaStream_t st)
 {
-    const dim3 blk(32, X2_TY, 1);
-    const dim3 grd((p->n + 63) / 64, (p->n + X2_TY * RB_P - 1) / (X2_TY * RB_P), nrhs);
-    const size_t smem = x2_smem_bytes<RM>();
-    NL_CUDA_TRY(prep_smem(k_direct2d_x2<RM>, smem));
-    k_direct2d_x2<RM><<<grd, blk, smem, st>>>(a, p->rb_g32, u, Lu);
-    NL_CUDA_TRY(cudaGetLastError());
+    if (p->x2_ty == 2)
+        return launch_x2_t<RM, 2>(p, a, u, Lu, nrhs, p->x2_order, p->x2_tiles, &p->x2_blocks, st);
+    return launch_x2_t<RM, 4>(p, a, u, Lu, nrhs, p->x2_order, p->x2_tiles, &p->x2_blocks, st);
+}
+
+// Tile order for the paired-column kernel: the cost of a 64 x rows tile is the sum of its
+// nodes' ball sizes; tiles are queued largest first.
+__global__ void k_x2_tile_cost(int n, int tiles_x, int rows, const int *__restrict__ cnt,
+                               long long *__restrict__ cost)
+{
+    __shared__ long long s_w[8];
+    const int tile = blockIdx.x;
+    const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * rows;
+    long long c = 0;
+    for (int e = threadIdx.x; e < 64 * rows; e += blockDim.x) {
+        const int x = x0 + e % 64, y = y0 + e / 64;
+        if (x < n && y < n) c += cnt[x + (int64_t)n * y];
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) c += s_w[w];
+        cost[tile] = c;
+    }
+}
+
+// largest-first order of the 64 x (TY * RB_P) tiles, uploaded to *order_dev
+static nl_status x2_order_for(nl_plan *p, int ty, int **order_dev, int *ntiles, cudaStream_t st)
+{
+    const int rows = ty * RB_P;
+    const int tiles_x = (p->n + 63) / 64, tiles_y = (p->n + rows - 1) / rows;
+    const int64_t tiles = (int64_t)tiles_x * tiles_y;
+    if (tiles >= (int64_t)1 << 30) return NL_EUNSUPPORTED;
+    long long *d_cost = nullptr;
+    NL_CUDA_TRY(cudaMalloc(&d_cost, tiles * sizeof(long long)));
+    std::vector<long long> cost(tiles);
+    k_x2_tile_cost<<<(unsigned)tiles, 256, 0, st>>>(p->n, tiles_x, rows, p->cnt, d_cost);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cost.data(), d_cost, tiles * sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_cost);
+    if (e != cudaSuccess) return nl_cuda_fail(e, "tile costs");
+    std::vector<int> order(tiles);
+    for (int64_t t = 0; t < tiles; ++t) order[t] = (int)t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    NL_CUDA_TRY(cudaMalloc(order_dev, tiles * sizeof(int)));
+    NL_CUDA_TRY(cudaMemcpyAsync(*order_dev, order.data(), tiles * sizeof(int),
+                                cudaMemcpyHostToDevice, st));
+    NL_CUDA_TRY(cudaStreamSynchronize(st));
+    *ntiles = (int)tiles;
     return NL_OK;
 }
 
@@ -1000,7 +1058,7 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
 #undef NL_SPLIT
     }
     if (p->d == 2 && p->rb2d && sizeof(T) == 4) {
-        if (mode == MODE_POWER && p->Rmax <= 32) {
+        if (mode == MODE_POWER && p->Rmax <= 32 && p->x2_order) {
             const float *uf = (const float *)u;
             float *lf = (float *)Lu;
             if (p->Rmax <= 4) return launch_x2<4>(p, a, uf, lf, nrhs, st);
@@ -1211,4 +1269,74 @@ nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, 
     if (kind == BK_SYM) NL_BATCH_SHAPES(double, BK_SYM);
     NL_BATCH_SHAPES(double, BK_SCALAR);
 #undef NL_BATCH_SHAPES
+}
+
+// ---------------------------------------------------------------------------
+// plan-time set-up of the paired-column FP32 kernel: the tile queue and its order, and the
+// tile height (TY = 2 or 4 warps of 8 rows) chosen by timing both on the plan itself
+// ---------------------------------------------------------------------------
+template <int TY>
+static nl_status x2_launch_rm(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                              const int *order, int ntiles, int *bc, cudaStream_t st)
+{
+    if (p->Rmax <= 4) return launch_x2_t<4, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
+    if (p->Rmax <= 8) return launch_x2_t<8, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
+    if (p->Rmax <= 16) return launch_x2_t<16, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
+    if (p->Rmax <= 24) return launch_x2_t<24, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
+    return launch_x2_t<32, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
+}
+
+nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
+{
+    if (!(p->d == 2 && p->rb2d && p->family == NL_POWER && !p->symmetric && p->Rmax <= 32))
+        return NL_OK;
+    NL_CUDA_TRY(cudaMalloc(&p->x2_queue, 2 * sizeof(int)));
+    NL_CUDA_TRY(cudaMemsetAsync(p->x2_queue, 0, 2 * sizeof(int), st));
+    int *ord[2] = { nullptr, nullptr };
+    int nt[2] = { 0, 0 }, bc[2] = { 0, 0 };
+    float ms[2] = { 0.f, 0.f };
+    float *u = nullptr, *lu = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool tune = p->N <= ((int64_t)1 << 24);
+    nl_status s = NL_OK;
+    for (int k = tune ? 0 : 1; k < 2 && s == NL_OK; ++k)
+        s = x2_order_for(p, k == 0 ? 2 : 4, &ord[k], &nt[k], st);
+    int best = 1;
+    if (s == NL_OK && tune) {
+        const DirectArgs a = make_args(p, NL_F32);
+        if (cudaMalloc(&u, p->N * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&lu, p->N * sizeof(float)) != cudaSuccess ||
+            cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+            cudaMemsetAsync(u, 0, p->N * sizeof(float), st) != cudaSuccess) {
+            s = nl_cuda_fail(cudaErrorMemoryAllocation, "direct kernel tuning");
+        }
+        for (int k = 0; k < 2 && s == NL_OK; ++k) {
+            auto run = [&]() {
+                return k == 0 ? x2_launch_rm<2>(p, a, u, lu, ord[k], nt[k], &bc[k], st)
+                              : x2_launch_rm<4>(p, a, u, lu, ord[k], nt[k], &bc[k], st);
+            };
+            if ((s = run()) != NL_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && s == NL_OK; ++r) s = run();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms[k], e0, e1);
+        }
+        if (s == NL_OK && ms[0] < ms[1]) best = 0;
+    }
+    if (u) cudaFree(u);
+    if (lu) cudaFree(lu);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ord[1 - best]) cudaFree(ord[1 - best]);
+    if (s != NL_OK) {
+        if (ord[best]) cudaFree(ord[best]);
+        return s;
+    }
+    p->x2_order = ord[best];
+    p->x2_tiles = nt[best];
+    p->x2_blocks = bc[best];
+    p->x2_ty = best == 0 ? 2 : 4;
+    p->device_bytes += (size_t)nt[best] * sizeof(int) + 2 * sizeof(int);
+    return NL_OK;
 }

@@ -20,6 +20,7 @@
 // X = 2 i + 1, panel k of level l spans [k S, (k + 1) S] with S = 2^{L-l+1},
 // and the ball test is (squared distance) <= thr4_i, thr4_i the largest
 // integer below 4 R2_i.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -540,49 +541,158 @@ __global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T 
 // panels 0..k of its panel row, so the panels ka..kb of a run add up to P[kb] - P[ka-1],
 // exactly the same integer as adding them one by one.  The leaf rows are scanned; a
 // parent's prefix is the sum of its child rows' prefixes at the odd positions.
+// k_step2_rowprefix (below) builds all the levels in one launch.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_leaf_scan_i64(int n, long long *rows)
+
+// ---------------------------------------------------------------------------
+// Step 2 of the row-prefix form in two launches.  k_absmax_parts writes one bound of |u b| per
+// block and zeroes the coarse levels 0 .. lf-1.  k_step2_rowprefix, one block per band (a
+// band is the set of leaf rows of one panel row of level lf), then (1) reduces the bounds to
+// the scale exponent, quantises and scans the band's leaf rows (a warp per row), (2) builds
+// the levels L-1 .. lf of the band, and (3) adds the band's part of every coarser prefix,
+// P_l[row][k] += P_lf[band][(k + 1) 2^(lf-l) - 1], with integer atomics.  Every value is the
+// same integer that the level-by-level kernels produce (integer sums are exact and do not
+// depend on the order).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_absmax_parts(int64_t N, const float *__restrict__ u,
+                                                      const float *__restrict__ b,
+                                                      float *__restrict__ part,
+                                                      long long *__restrict__ zero,
+                                                      int64_t nzero)
 {
-    __shared__ long long s_warp[8];
-    long long *row = rows + (int64_t)blockIdx.x * n;
-    const int per = (n + 255) / 256;
-    const int beg = threadIdx.x * per, end = min(n, beg + per);
-    long long tot = 0;
-    for (int k = beg; k < end; ++k) tot += row[k];
-    // exclusive scan of the thread totals (warp shuffles, then warp totals)
-    long long incl = tot;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) s_warp[w] = incl;
+    __shared__ float s_w[8];
+    float m = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < nzero; i += stride) zero[i] = 0;
+    for (int64_t i = t0; i < N; i += stride) m = fmaxf(m, fabsf(u[i] * b[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
     __syncthreads();
-    long long off = incl - tot;
-    for (int k = 0; k < w; ++k) off += s_warp[k];
-    for (int k = beg; k < end; ++k) { off += row[k]; row[k] = off; }
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, s_w[w]);
+        part[blockIdx.x] = m * (1.f + 0x1p-20f);
+    }
 }
 
-__global__ void k_level_prefix_i64(int d, int l, const long long *__restrict__ child,
-                                   long long *__restrict__ parent)
+struct Step2Args {
+    int d, n, L, c, lf;              // band: 2^c leaf rows per axis = one panel row of level lf
+    int leaf_only;                   // 1: the leaf rows only (leaf-row gather)
+    int64_t N;
+    const float *u, *b;
+    const float *part;
+    int nparts;
+    unsigned int *mx;
+    long long *pyr;
+    int64_t lvl_off[NL_MAX_LEVELS + 2];
+};
+
+__device__ __forceinline__ long long warp_incl_scan_ll(long long v, int lane)
 {
-    const int np = 1 << l;
-    int64_t P = np;
-    if (d > 1) P *= np;
-    if (d > 2) P *= np;
-    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= P) return;
-    const int kx = (int)(f % np);
-    const int ky = d > 1 ? (int)((f / np) % np) : 0;
-    const int kz = d > 2 ? (int)(f / ((int64_t)np * np)) : 0;
-    const int nc = 2 * np;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// parent prefix at (kx, ky, kz) of level l from level l + 1 (child rows at odd positions)
+__device__ __forceinline__ long long level_prefix_at(int d, int l, const long long *child,
+                                                     int kx, int ky, int kz)
+{
+    const int nc = 2 << l;
     long long s = 0;
     for (int c = 0; c < (1 << (d - 1)); ++c) {
         const int cy = d > 1 ? 2 * ky + (c & 1) : 0;
         const int cz = d > 2 ? 2 * kz + ((c >> 1) & 1) : 0;
-        s += child[(2 * kx + 1) + (int64_t)nc * (cy + (int64_t)nc * cz)];
+        s += __ldcg(child + (2 * kx + 1) + (int64_t)nc * (cy + (int64_t)nc * cz));
     }
-    parent[f] = s;
+    return s;
+}
+
+constexpr int STEP2_THREADS = 512;
+
+__global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
+{
+    __shared__ float s_w[STEP2_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = STEP2_THREADS / 32;
+    // scale exponent from the per-block bounds (same arithmetic as fixed_shift_f32)
+    float m = 0.f;
+    for (int k = tid; k < a.nparts; k += STEP2_THREADS) m = fmaxf(m, a.part[k]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_w[warp] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < nw; ++w) m = fmaxf(m, s_w[w]);
+    if (blockIdx.x == 0 && tid == 0) *a.mx = __float_as_uint(m);
+    int sh = 62;
+    if (m > 0.f) {
+        int e1, e2;
+        frexpf(m, &e1);
+        frexpf((float)a.N, &e2);
+        sh = 62 - e1 - e2;
+    }
+    const int n = a.n, d = a.d, L = a.L, lf = a.lf;
+    const int S = 1 << a.c;                    // band side in leaf rows (per axis)
+    const int bands_y = d > 1 ? n / S : 1;
+    const int by = d > 1 ? (int)(blockIdx.x % bands_y) : 0;
+    const int bz = d > 2 ? (int)(blockIdx.x / bands_y) : 0;
+    const int rows_y = d > 1 ? S : 1, rows_z = d > 2 ? S : 1;
+    long long *leaf = a.pyr + a.lvl_off[L];
+    // (1) quantise and scan the band's leaf rows: the 32 loads of a page are issued first,
+    // then the page is scanned 32 nodes at a time
+    for (int r = warp; r < rows_y * rows_z; r += nw) {
+        const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
+        const int64_t row = (int64_t)n * (iy + (int64_t)n * iz);
+        const float *__restrict__ ur = a.u + row;
+        const float *__restrict__ br = a.b + row;
+        long long carry = 0;
+        for (int p0 = 0; p0 < n; p0 += 1024) {
+            float v[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int x = p0 + 32 * k + lane;
+                v[k] = x < n ? ur[x] * br[x] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                if (p0 + 32 * k >= n) break;
+                const int x = p0 + 32 * k + lane;
+                long long q = x < n ? __float2ll_rn(ldexpf(v[k], sh)) : 0LL;
+                q = warp_incl_scan_ll(q, lane) + carry;
+                if (x < n) leaf[row + x] = q;
+                carry = __shfl_sync(0xffffffffu, q, 31);
+            }
+        }
+    }
+    if (a.leaf_only) return;
+    __syncthreads();
+    // (2) levels L-1 .. lf inside the band
+    for (int l = L - 1; l >= lf; --l) {
+        const int np = 1 << l, s = 1 << (L - l);
+        const int pr_y = d > 1 ? S / s : 1, pr_z = d > 2 ? S / s : 1;
+        const int items = pr_y * pr_z * np;
+        const long long *child = a.pyr + a.lvl_off[l + 1];
+        long long *par = a.pyr + a.lvl_off[l];
+        for (int t = tid; t < items; t += STEP2_THREADS) {
+            const int kx = t % np, q = t / np;
+            const int ky = d > 1 ? by * pr_y + q % pr_y : 0;
+            const int kz = d > 2 ? bz * pr_z + q / pr_y : 0;
+            par[kx + (int64_t)np * (ky + (int64_t)np * kz)] = level_prefix_at(d, l, child, kx, ky, kz);
+        }
+        __syncthreads();
+    }
+    // (3) the band's part of the coarser levels (zeroed by k_absmax_parts)
+    const int npf = 1 << lf;
+    const long long *pf = a.pyr + a.lvl_off[lf] + (int64_t)npf * (by + (int64_t)npf * bz);
+    for (int l = lf - 1; l >= 0; --l) {
+        const int np = 1 << l, step = 1 << (lf - l);
+        const int ky = by >> (lf - l), kz = bz >> (lf - l);
+        unsigned long long *par = reinterpret_cast<unsigned long long *>(
+            a.pyr + a.lvl_off[l] + (int64_t)np * (ky + (int64_t)np * kz));
+        for (int kx = tid; kx < np; kx += STEP2_THREADS)
+            atomicAdd(par + kx, (unsigned long long)__ldcg(pf + (int64_t)(kx + 1) * step - 1));
+    }
 }
 
 template <int D, typename T>
@@ -668,6 +778,68 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
     Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
 }
 
+// ---------------------------------------------------------------------------
+// Leaf-row form of Step 3 (K = 0, integer route).  The panels of Algorithm 1 tile exactly the
+// leaf cells that meet the open ball, so their sum is, row by row, the run of leaf cells of
+// that row that meets the ball: one difference of the leaf-row prefix sums per row.  The
+// integer total is the one the panel-by-panel and per-level routes add.  Rows iy + t and
+// iy - t (and likewise in z) have the same vertical gap, so they share one chord.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long leaf_run(const long long *__restrict__ row, int n, int X,
+                                              int r)
+{
+    const int ka = max(0, -((r - X) >> 1) - 1);
+    const int kb = min(n - 1, (X + r) >> 1);
+    return __ldg(row + kb) - (ka > 0 ? __ldg(row + ka - 1) : 0LL);
+}
+
+template <int D>
+__device__ __forceinline__ long long leaf_plane(const long long *__restrict__ plane, int n,
+                                                int X, int iy, int T4)
+{
+    if (D == 1) return leaf_run(plane, n, X, isqrt_fast(T4));
+    long long G = 0;
+    for (int t = 0;; ++t) {
+        const int e = t == 0 ? 0 : sq(2 * t - 1);
+        if (e > T4) break;
+        const int r = isqrt_fast(T4 - e);
+        if (iy + t < n) G += leaf_run(plane + (int64_t)n * (iy + t), n, X, r);
+        if (t > 0 && iy - t >= 0) G += leaf_run(plane + (int64_t)n * (iy - t), n, X, r);
+    }
+    return G;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_fast_gather_leafrows(FastI64Args a,
+                                                              const T *__restrict__ u,
+                                                              T *__restrict__ Lu)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)((i / n) % n) : 0;
+    const int iz = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    const long long *leaf = a.pyr + a.lvl_off[a.L];
+    long long G = 0;
+    if (D < 3) {
+        G = leaf_plane<D>(leaf, n, X, iy, T4);
+    } else {
+        const int64_t pl = (int64_t)n * n;
+        for (int t = 0;; ++t) {
+            const int ez = t == 0 ? 0 : sq(2 * t - 1);
+            if (ez > T4) break;
+            if (iz + t < n) G += leaf_plane<2>(leaf + pl * (iz + t), n, X, iy, T4 - ez);
+            if (t > 0 && iz - t >= 0) G += leaf_plane<2>(leaf + pl * (iz - t), n, X, iy, T4 - ez);
+        }
+    }
+    const int sh = fixed_shift_f32(a.N, a.mx);
+    const double Gd = ldexp((double)G, -sh);
+    Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -744,7 +916,11 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     if ((s = alloc((void **)&p->fastF, p->N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->selfS, p->N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->ir4, p->N * sizeof(double))) != NL_OK) return s;
-    if (K == 0 && (s = alloc((void **)&p->fast_mx, sizeof(unsigned long long))) != NL_OK) return s;
+    if (K == 0) {
+        const size_t aux = 16 + NL_FAST_PARTS * sizeof(float);
+        if ((s = alloc((void **)&p->fast_mx, aux)) != NL_OK) return s;
+        NL_CUDA_TRY(cudaMemsetAsync(p->fast_mx, 0, aux, st));     // the ticket starts at 0
+    }
     double *d_pc = nullptr;
     if ((s = alloc((void **)&d_pc, 8 * sizeof(double))) != NL_OK) return s;
     NL_CUDA_TRY(cudaMemcpyAsync(p->shift, shift.data(), shift.size() * sizeof(double),
@@ -774,6 +950,34 @@ static void prof_mark(nl_plan *p, int k, cudaStream_t st)
     if (k == 2) p->prof_count++;
 }
 
+// Step 2 of the row-prefix form: per-block bounds (and the coarse levels zeroed), then one
+// fused build (see k_step2_rowprefix).  The band side 2^c is 16 leaf rows in 2-D and 8 per
+// axis in 3-D (capped by the grid); in 1-D the single row is the band.
+static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, cudaStream_t st)
+{
+    const int d = p->d, L = p->L;
+    long long *pyr = (long long *)p->pyr;
+    unsigned int *mx = (unsigned int *)p->fast_mx;
+    float *part = (float *)((unsigned char *)p->fast_mx + 16);
+    int64_t per = (p->N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
+    if (per < 2048) per = 2048;
+    const int nparts = (int)((p->N + per - 1) / per);
+    int c = 0;
+    if (d == 2) c = std::min(4, L);
+    if (d == 3) c = std::min(3, L);
+    Step2Args a;
+    a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
+    a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
+    a.mx = mx; a.pyr = pyr; a.leaf_only = leaf_only ? 1 : 0;
+    for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
+    k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr,
+                                           leaf_only ? 0 : p->lvl_off[a.lf]);
+    int64_t bands = 1;
+    for (int q = 1; q < d; ++q) bands *= p->n >> c;
+    k_step2_rowprefix<<<(unsigned)bands, STEP2_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_t st)
 {
     prof_mark(p, 0, st);
@@ -781,11 +985,12 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     long long *pyr = (long long *)p->pyr;           // same buffer, 8-byte entries (M = 1)
     unsigned int *mx = (unsigned int *)p->fast_mx;
     const unsigned gb = (unsigned)((p->N + 255) / 256);
-    NL_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), st));
-    const unsigned gm = (unsigned)((p->N + 255) / 256 < 1216 ? (p->N + 255) / 256 : 1216);
-    k_absmax_f32<<<gm, 256, 0, st>>>(p->N, u, p->b32, mx);
-    long long *leaf = pyr + p->lvl_off[L];
-    k_pyr_leaf_f32i64<<<gb, 256, 0, st>>>(p->N, u, p->b32, mx, leaf);
+    if (p->fast_variant == NL_FAST_PANELS) {
+        NL_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), st));
+        const unsigned gm = (unsigned)((p->N + 255) / 256 < 1216 ? (p->N + 255) / 256 : 1216);
+        k_absmax_f32<<<gm, 256, 0, st>>>(p->N, u, p->b32, mx);
+        k_pyr_leaf_f32i64<<<gb, 256, 0, st>>>(p->N, u, p->b32, mx, pyr + p->lvl_off[L]);
+    }
     for (int l = L - 1; l >= 0 && p->fast_variant == NL_FAST_PANELS; --l) {
         int64_t P = 1;
         for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
@@ -793,16 +998,9 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         k_pyr_level_i64<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(d, l, child, pyr + p->lvl_off[l]);
     }
     const bool prefix = p->fast_variant != NL_FAST_PANELS;
+    const bool leafrows = p->fast_variant == NL_FAST_LEAFROWS;
     if (prefix) {
-        // leaf rows scanned in place, then each level from its children's prefixes
-        const int64_t rows = p->N / p->n;
-        k_leaf_scan_i64<<<(unsigned)rows, 256, 0, st>>>(p->n, leaf);
-        for (int l = L - 1; l >= 0; --l) {
-            int64_t P = 1;
-            for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
-            k_level_prefix_i64<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(
-                d, l, pyr + p->lvl_off[l + 1], pyr + p->lvl_off[l]);
-        }
+        NL_CUDA_TRY(step2_rowprefix(p, u, leafrows, st));
     }
     FastI64Args a;
     a.n = p->n; a.L = L; a.N = p->N;
@@ -812,7 +1010,11 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     a.hd = std::pow(p->h, (double)d);
     a.mx = mx;
     prof_mark(p, 1, st);
-    if (prefix) {
+    if (leafrows) {
+        if (d == 1) k_fast_gather_leafrows<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else if (d == 2) k_fast_gather_leafrows<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else k_fast_gather_leafrows<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
+    } else if (prefix) {
         if (d == 1) k_fast_gather_rowprefix<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_rowprefix<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else k_fast_gather_rowprefix<3, float><<<gb, 256, 0, st>>>(a, u, Lu);

@@ -13,6 +13,7 @@
 // Largest supported ball radius (cells) and offset-table length.
 #define NL_MAX_TABLE (1 << 20)
 #define NL_MAX_LEVELS 20
+#define NL_FAST_PARTS 1024
 
 // Block shapes of the direct kernels: one output node per thread.
 template <int D> struct DirectBlock;
@@ -85,6 +86,9 @@ struct nl_plan {
     size_t rb_smem32, rb_smem64, x2_smem;
     float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
     int *thr_reach;                 // symmetric variant: max threshold over the window
+    int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
+    int x2_tiles, x2_blocks, x2_ty; // work-queue counter + exit ticket; persistent grid size;
+                                    // tile height in warps of 8 rows (timed at plan creation)
     // per-node device arrays
     int *thr;               // largest integer < R2_i
     int *cnt;               // table entries with o2 <= thr_i (or the symmetric bound)
@@ -109,7 +113,9 @@ struct nl_plan {
     double *shift;                  // Step 2 re-centring table [2^d][M][M]
     int *malpha;                    // multi-indices [M][3]
     int pyr_rhs;                    // right-hand sides the pyramid buffer holds
-    unsigned long long *fast_mx;    // max |v| of the last FP32 apply (fixed-point scale)
+    unsigned long long *fast_mx;    // FP32 integer route scratch: word 0 max |v| of the last
+                                    // apply (fixed-point scale), word 1 a block ticket, then
+                                    // NL_FAST_PARTS per-block maxima (floats, from byte 16)
     int prof_on, prof_count;        // per-phase timing of the fast apply
     cudaEvent_t prof_ev[64][3];
     nl_cg_state cg;                 // CG workspace (allocated on the first solve)
@@ -142,6 +148,7 @@ nl_status nl_pd_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                        cudaStream_t st);
 nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                          cudaStream_t st);
+nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st);
 nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
                             cudaStream_t st);
 nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st);

@@ -369,12 +369,12 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     for (int l = 0; l <= NL_MAX_LEVELS; ++l) if ((1 << l) == n) p->L = l;
     p->family = k->family; p->coef = k->coef; p->symmetric = hz->symmetric ? 1 : 0;
     p->self_mode = k->self_term; p->K = (k->family == NL_POLY) ? k->K : 0;
-    if (k->fast_variant < NL_FAST_AUTO || k->fast_variant > NL_FAST_FP64_PANELS) {
+    if (k->fast_variant < NL_FAST_AUTO || k->fast_variant > NL_FAST_LEAFROWS) {
         nl_set_error("nl_plan_create: unknown fast variant %d", k->fast_variant);
         free(p);
         return NL_EINVAL;
     }
-    p->fast_variant = k->fast_variant == NL_FAST_AUTO ? NL_FAST_ROWPREFIX : k->fast_variant;
+    p->fast_variant = k->fast_variant == NL_FAST_AUTO ? NL_FAST_LEAFROWS : k->fast_variant;
     p->alpha = k->alpha; p->scale = k->scale; p->h = 1.0 / n;
     if (k->family == NL_PD_BOND || !k->normalize)
         p->sigma = k->scale;
@@ -582,6 +582,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan kernels"));
     if (want_fast) NL_TMP_TRY(nl_fast_plan_init(p, d_delta, d_a, st));
+    NL_TMP_TRY(nl_direct_plan_init(p, st));
     ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan synchronise"));
     free_tmp(d_delta, d_a, nullptr, nullptr);
@@ -602,7 +603,8 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
     void *ptrs[] = { p->thr, p->cnt, p->b32, p->b64, p->fin32, p->fin64, p->ext32, p->ext64,
                      p->wh32, p->wh64, p->ir32, p->ir64, p->off, p->tab32, p->tab64, p->pd32,
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
-                     p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx };
+                     p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx,
+                     p->x2_order, p->x2_queue };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)

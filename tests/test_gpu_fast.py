@@ -132,8 +132,8 @@ def test_unsupported_requests():
 
 @pytest.mark.parametrize("d,n", [(1, 2048), (2, 128), (2, 256), (3, 32)])
 def test_integer_routes_bitwise_equal_and_match_oracle(d, n):
-    """FP32, K = 0: the row-prefix and the panel-by-panel fixed-point routes add the same
-    integers, so their outputs are bitwise equal; both match the FP64 oracle."""
+    """FP32, K = 0: the row-prefix, leaf-row and panel-by-panel fixed-point routes add the
+    same integers, so their outputs are bitwise equal; all match the FP64 oracle."""
     L = int(np.log2(n))
     rng = np.random.default_rng(40 + d)
     N = n ** d
@@ -141,11 +141,39 @@ def test_integer_routes_bitwise_equal_and_match_oracle(d, n):
     a = np.exp(0.3 * rng.standard_normal(N))
     u = rng.standard_normal(N)
     outs = []
-    for variant in (nl.NL_FAST_ROWPREFIX, nl.NL_FAST_PANELS, nl.NL_FAST_FP64_PANELS):
+    for variant in (nl.NL_FAST_ROWPREFIX, nl.NL_FAST_PANELS, nl.NL_FAST_FP64_PANELS,
+                    nl.NL_FAST_LEAFROWS):
         plan = nl.nl_plan_create(d, n, rho / n, family=nl.NL_POLY, alpha=1.0, K=0,
                                  coef=nl.NL_COEF_XY, a=a, fast_variant=variant)
         outs.append(run_fast(plan, u, torch.float32))
     np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[3], outs[1])
     ref = oracle.fast_leafset(u, d, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a)
     for o in outs:
         assert rel_l2(o, ref) <= 2e-6
+
+
+@pytest.mark.parametrize("d,n", [(1, 2), (1, 8192), (2, 2), (2, 8), (2, 32), (2, 1024),
+                                 (2, 4096), (3, 2), (3, 8), (3, 64)])
+def test_fused_step2_bitwise_equal_to_panels(d, n):
+    """The fused Step 2 build (one launch for every level; for 2-D 4096^2 the coarse levels
+    come from per-level launches) gives the row-prefix gather the same integers as the
+    panel-by-panel route, at band and level edge cases; sampled against the oracle."""
+    L = int(np.log2(n))
+    rng = np.random.default_rng(7 * n + d)
+    N = n ** d
+    rho = rng.uniform(0.6, max(0.7, min(6.0, n / 4)), size=N)
+    a = np.exp(0.3 * rng.standard_normal(N))
+    u = rng.standard_normal(N)
+    outs = []
+    for variant in (nl.NL_FAST_ROWPREFIX, nl.NL_FAST_PANELS, nl.NL_FAST_LEAFROWS):
+        plan = nl.nl_plan_create(d, n, rho / n, family=nl.NL_POLY, alpha=1.0, K=0,
+                                 coef=nl.NL_COEF_XY, a=a, fast_variant=variant)
+        outs.append(run_fast(plan, u, torch.float32))
+        plan.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[2], outs[1])
+    idx = sample_idx(N, 400, seed=d) if N > 4096 else np.arange(N)
+    ref = oracle.fast_leafset(u, d, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a,
+                              idx=idx)
+    assert rel_l2(outs[0][idx], ref) <= 2e-6
