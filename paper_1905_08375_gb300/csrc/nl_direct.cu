@@ -433,12 +433,13 @@ k_direct2d_rb(DirectArgs a, const T *__restrict__ gtab, const T *__restrict__ u,
 
 // ---------------------------------------------------------------------------
 // 2-D register-blocked FP32 kernel with paired FP32 arithmetic (POWER kernels).  Same
-// traversal as k_direct2d_rb, but each thread owns two columns, c and c + 32, of RB_P rows,
+// traversal as k_direct2d_rb, but each thread owns two adjacent columns of RB_P rows,
 // and every multiply/add runs as one paired f32x2 instruction on the two columns (per element
 // IEEE round-to-nearest, so each column's result is bitwise the single-column one).  A block of
 // 32 x TY threads covers 64 columns and TY * RB_P rows (TY = 2 or 4, chosen per plan by timing
-// both); the tile is kept as separate u and b planes so that a warp's loads are 32 consecutive
-// floats.  A thread's outputs and its summation order do not depend on TY.
+// both); the tile is kept as separate u and b planes so that a warp's pair loads cover 64
+// consecutive floats.  A thread's outputs and its summation order do not depend on TY.
+// Adjacent columns have close horizons, so few rows of a column offset need per-output masks.
 // ---------------------------------------------------------------------------
 typedef unsigned long long f2_t;
 
@@ -479,65 +480,131 @@ __device__ __forceinline__ int isqrt_small(int x)   // floor(sqrt(x)), 0 <= x < 
     return h;
 }
 
-// One masked chunk of HC rows (offsets oy .. oy + HC - 1 of column ox) for the RB_P outputs
-// of each column pair; rows outside an output's ball get weight 0.
-template <int HC, bool MASK>
-__device__ __forceinline__ void x2_chunk(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
-                                         f2_t (&Wu)[RB_P], f2_t (&Wb)[RB_P],
-                                         const int (&thra)[RB_P], const int (&thrb)[RB_P],
-                                         const float *cu, int SX, int plane, const float *gcol,
-                                         int oy, int ox2, int R)
+// Row pairs of the tile: lane l owns the adjacent columns 2l and 2l + 1 (two 4-byte loads, as
+// the column offset may be odd).
+__device__ __forceinline__ f2_t ld_pair(const float *p) { return f2_pack(p[0], p[1]); }
+
+// four consecutive tile rows of the u and b planes at one column offset
+struct X2Grp { f2_t u[4], b[4]; };
+
+__device__ __forceinline__ void x2_load_grp(X2Grp &g, const float *cu, int plane, int SX, int row)
 {
-    f2_t Xu[HC], Xb[HC];
-    const float *rp = cu + (oy + RB_P) * SX;
 #pragma unroll
-    for (int k = 0; k < HC; ++k) {
-        Xu[k] = f2_pack(rp[k * SX], rp[k * SX + 32]);
-        Xb[k] = f2_pack(rp[k * SX + plane], rp[k * SX + plane + 32]);
-    }
-#pragma unroll
-    for (int j = 0; j < HC; ++j) {
-        const int oyj = oy + j;
-        const float g = gcol[MASK ? min(oyj, R) : oyj];
-        const int o2 = ox2 + oyj * oyj;
-#pragma unroll
-        for (int p = 0; p < RB_P; ++p) {
-            const int k = p + j;
-            const f2_t vu = k < RB_P ? Wu[k] : Xu[k - RB_P];
-            const f2_t vb = k < RB_P ? Wb[k] : Xb[k - RB_P];
-            f2_t w;
-            if (MASK) {
-                w = f2_mul(vb, f2_pack(o2 <= thra[p] ? g : 0.f, o2 <= thrb[p] ? g : 0.f));
-            } else {
-                w = f2_mul(vb, f2_pack(g, g));
-            }
-            acc[p] = f2_fma(w, f2_sub(vu, ui[p]), acc[p]);
-        }
-    }
-    if (HC < RB_P) {
-#pragma unroll
-        for (int k = 0; k < RB_P - HC; ++k) { Wu[k] = Wu[k + HC]; Wb[k] = Wb[k + HC]; }
-#pragma unroll
-        for (int k = 0; k < HC; ++k) { Wu[RB_P - HC + k] = Xu[k]; Wb[RB_P - HC + k] = Xb[k]; }
-    } else {
-#pragma unroll
-        for (int k = 0; k < RB_P; ++k) { Wu[k] = Xu[k]; Wb[k] = Xb[k]; }
+    for (int k = 0; k < 4; ++k) {
+        g.u[k] = ld_pair(cu + (row + k) * SX);
+        g.b[k] = ld_pair(cu + (row + k) * SX + plane);
     }
 }
 
-// RM: compile-time halo (>= the plan's largest radius) so that every shared-memory offset
-// is an immediate.  Persistent: each block takes 64 x 32 tiles (times right-hand sides) from a
-// queue ordered by decreasing cost (the sum of the tile's ball sizes, largest first); the
-// last block to finish resets the queue for the next launch on the stream.
-template <int RM, int TY>
-__global__ void __launch_bounds__(32 * TY, 16 / TY)
+// rows oy .. oy + 3 for the RB_P (= 8) outputs; the window is (G0, G1) = rows oy .. oy + 7
+// and G2 holds rows oy + 8 .. oy + 11; every output is inside its ball
+__device__ __forceinline__ void x2_core4(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                         const X2Grp &G0, const X2Grp &G1, const X2Grp &G2,
+                                         const float *gcol, int oy)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float g = gcol[oy + j];
+        const f2_t gg = f2_pack(g, g);
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int k = p + j;
+            const X2Grp &G = k < 4 ? G0 : (k < 8 ? G1 : G2);
+            acc[p] = f2_fma(f2_mul(G.b[k & 3], gg), f2_sub(G.u[k & 3], ui[p]), acc[p]);
+        }
+    }
+}
+
+// one row (offset oy) for the RB_P outputs from the window (G0, G1); MASK: outputs whose ball
+// does not hold the offset get weight 0
+template <bool MASK>
+__device__ __forceinline__ void x2_row(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                       const X2Grp &G0, const X2Grp &G1,
+                                       const unsigned (&thr2)[RB_P], float g, int o2)
+{
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const X2Grp &G = p < 4 ? G0 : G1;
+        const f2_t gm = MASK ? f2_pack(o2 <= (int)(thr2[p] & 0xffffu) ? g : 0.f,
+                                       o2 <= (int)(thr2[p] >> 16) ? g : 0.f)
+                             : f2_pack(g, g);
+        acc[p] = f2_fma(f2_mul(G.b[p & 3], gm), f2_sub(G.u[p & 3], ui[p]), acc[p]);
+    }
+}
+
+// slide the window (G0, G1) down one row, loading row `row` + 8 when `more`
+__device__ __forceinline__ void x2_slide(X2Grp &G0, X2Grp &G1, const float *cu, int plane,
+                                         int SX, int row, bool more)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { G0.u[k] = G0.u[k + 1]; G0.b[k] = G0.b[k + 1]; }
+    G0.u[3] = G1.u[0]; G0.b[3] = G1.b[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { G1.u[k] = G1.u[k + 1]; G1.b[k] = G1.b[k + 1]; }
+    if (more) {
+        G1.u[3] = ld_pair(cu + (row + 8) * SX);
+        G1.b[3] = ld_pair(cu + (row + 8) * SX + plane);
+    }
+}
+
+// one column offset ox: rows -hmax .. hmax in increasing order (the same order for every
+// output), masked single rows at the rims, unmasked groups of four rows in the core with the
+// three row groups rotated instead of copied.  hmin and hmax are the same for the whole warp
+// (its 64 x 8 outputs), so every lane runs the same loops.
+__device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                          const unsigned (&thr2)[RB_P], const float *cu, int plane, int SX, const float *gcol,
+                                          int ox2, int hmin, int hmax)
+{
+    X2Grp G0, G1, G2;
+    int oy = -hmax;
+    x2_load_grp(G0, cu, plane, SX, oy);
+    x2_load_grp(G1, cu, plane, SX, oy + 4);
+    // top rim (or every row when no output's ball covers the centre row of this column)
+    const int core_lo = hmin >= 0 ? -hmin : hmax + 1;
+    for (; oy < core_lo; ++oy) {
+        x2_row<true>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy);
+        x2_slide(G0, G1, cu, plane, SX, oy, oy < hmax);
+    }
+    if (hmin >= 0) {
+        int rem = hmin - oy + 1;
+        for (;;) {
+            if (rem < 4) break;
+            x2_load_grp(G2, cu, plane, SX, oy + 8);
+            x2_core4(acc, ui, G0, G1, G2, gcol, oy);
+            oy += 4; rem -= 4;                      // the window is (G1, G2)
+            if (rem < 4) { G0 = G1; G1 = G2; break; }
+            x2_load_grp(G0, cu, plane, SX, oy + 8);
+            x2_core4(acc, ui, G1, G2, G0, gcol, oy);
+            oy += 4; rem -= 4;                      // the window is (G2, G0)
+            if (rem < 4) { G1 = G0; G0 = G2; break; }
+            x2_load_grp(G1, cu, plane, SX, oy + 8);
+            x2_core4(acc, ui, G2, G0, G1, gcol, oy);
+            oy += 4; rem -= 4;                      // the window is (G0, G1) again
+        }
+        for (; oy <= hmin; ++oy) {
+            x2_row<false>(acc, ui, G0, G1, thr2, gcol[oy], 0);
+            x2_slide(G0, G1, cu, plane, SX, oy, oy < hmax);
+        }
+    }
+    // bottom rim
+    for (; oy <= hmax; ++oy) {
+        x2_row<true>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy);
+        x2_slide(G0, G1, cu, plane, SX, oy, oy < hmax);
+    }
+}
+
+// RM: compile-time halo (>= the plan's largest radius) so that the tile geometry is constant.
+// Persistent: each block takes 64 x (TY * RB_P) tiles (times right-hand sides) from a queue
+// ordered by decreasing cost (the sum of the tile's ball sizes, largest first); the last
+// block to finish resets the queue for the next launch on the stream.
+template <int RM, int TY, int MB>
+__global__ void __launch_bounds__(32 * TY, MB)
 k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
               float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
               int nrhs, int *__restrict__ queue)
 {
-    constexpr int SX = 64 + 2 * RM;
-    constexpr int SY = TY * RB_P + 2 * RM + RB_P;
-    constexpr int HC = RB_P / 2;
+    constexpr int SX = 64 + 2 * RM;                  // even: pair loads stay 8-byte aligned
+    constexpr int SY = TY * RB_P + 2 * RM + 1;       // one spare row below the halo
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
     const int n = a.n, R = a.R;                      // R <= RM
@@ -570,53 +637,39 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         }
         __syncthreads();
 
-        const int xa = x0 + threadIdx.x, xb = xa + 32;
+        const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
         const int ybase = y0 + threadIdx.y * RB_P;
         f2_t ui[RB_P], acc[RB_P];
-        int thra[RB_P], thrb[RB_P];
+        unsigned thr2[RB_P];          // the two outputs' thresholds (< 2^10 as R <= 32; 0 off grid)
         int tmax = -1, tmin = 1 << 30;
-        const float *ua = su + (threadIdx.y * RB_P + RM) * SX + threadIdx.x + RM;
+        // tile position of output (p = 0, columns xa, xb)
+        const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
             const int y = ybase + p;
             const bool oa = xa < n && y < n, ob = xb < n && y < n;
-            thra[p] = oa ? a.thr[xa + (int64_t)n * y] : -1;
-            thrb[p] = ob ? a.thr[xb + (int64_t)n * y] : -1;
-            tmax = max(tmax, max(thra[p], thrb[p]));
-            tmin = min(tmin, min(oa ? thra[p] : tmin, ob ? thrb[p] : tmin));
-            ui[p] = f2_pack(ua[p * SX], ua[p * SX + 32]);
+            const int ta = oa ? a.thr[xa + (int64_t)n * y] : -1;
+            const int tb = ob ? a.thr[xb + (int64_t)n * y] : -1;
+            thr2[p] = (unsigned)max(ta, 0) | ((unsigned)max(tb, 0) << 16);
+            tmax = max(tmax, max(ta, tb));
+            tmin = min(tmin, min(oa ? ta : tmin, ob ? tb : tmin));
+            ui[p] = ld_pair(ua + p * SX);
             acc[p] = f2_pack(0.f, 0.f);
+        }
+        // warp-wide threshold range: every lane takes the same rows of every column offset
+        for (int o = 16; o > 0; o >>= 1) {
+            tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
         }
         if (tmin == (1 << 30)) tmin = -1;
         const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-
         for (int ox = -rx; ox <= rx; ++ox) {
             const int ox2 = ox * ox;
             if (ox2 > tmax) continue;
             const int hmax = min(R, isqrt_small(tmax - ox2));
-            const int hmin = (tmin >= ox2) ? isqrt_small(tmin - ox2) : -1;
-            const float *cu = ua + ox;
+            const int hmin = (tmin >= ox2) ? min(hmax, isqrt_small(tmin - ox2)) : -1;
             const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
-            f2_t Wu[RB_P], Wb[RB_P];
-            int oy = -hmax;
-#pragma unroll
-            for (int k = 0; k < RB_P; ++k) {
-                Wu[k] = f2_pack(cu[(oy + k) * SX], cu[(oy + k) * SX + 32]);
-                Wb[k] = f2_pack(cu[(oy + k) * SX + SX * SY], cu[(oy + k) * SX + SX * SY + 32]);
-            }
-            // top rim: masked half chunks until every output's ball covers the rows
-            for (; oy < -hmin && oy <= hmax; oy += HC)
-                x2_chunk<HC, true>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
-            // core: full chunks inside every output's ball
-            for (; oy + RB_P - 1 <= hmin; oy += RB_P)
-                x2_chunk<RB_P, false>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
-            // the rest: half chunks, unmasked while still inside every ball
-            for (; oy <= hmax; oy += HC) {
-                if (oy + HC - 1 <= hmin)
-                    x2_chunk<HC, false>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
-                else
-                    x2_chunk<HC, true>(acc, ui, Wu, Wb, thra, thrb, cu, SX, SX * SY, gcol, oy, ox2, R);
-            }
+            x2_column(acc, ui, thr2, ua + ox, SX * SY, SX, gcol, ox2, hmin, hmax);
         }
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
@@ -644,17 +697,21 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
 template <int RM, int TY>
 static size_t x2_smem_bytes()
 {
-    return sizeof(float) * (size_t)2 * (64 + 2 * RM) * (TY * RB_P + 2 * RM + RB_P);
+    return sizeof(float) * (size_t)2 * (64 + 2 * RM) * (TY * RB_P + 2 * RM + 1);
 }
 
-template <int RM, int TY>
+// kernel variants: (TY warps per tile, minimum resident blocks per SM for the register budget)
+constexpr int X2_VARIANTS = 4;
+static const int x2_var_ty[X2_VARIANTS] = { 2, 2, 4, 4 };
+
+template <int RM, int TY, int MB>
 static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
                              int nrhs, const int *order, int ntiles, int *blocks_cache,
                              cudaStream_t st)
 {
     const dim3 blk(32, TY, 1);
     const size_t smem = x2_smem_bytes<RM, TY>();
-    auto kern = k_direct2d_x2<RM, TY>;
+    auto kern = k_direct2d_x2<RM, TY, MB>;
     NL_CUDA_TRY(prep_smem(kern, smem));
     const int tiles_x = (p->n + 63) / 64;
     const int64_t items = (int64_t)ntiles * nrhs;
@@ -678,12 +735,27 @@ static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, fl
 }
 
 template <int RM>
-static nl_status launch_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu, int nrhs,
-                           cudaStream_t st)
+static nl_status launch_x2_var(nl_plan *p, int var, const DirectArgs &a, const float *u,
+                               float *Lu, int nrhs, const int *order, int ntiles, int *bc,
+                               cudaStream_t st)
 {
-    if (p->x2_ty == 2)
-        return launch_x2_t<RM, 2>(p, a, u, Lu, nrhs, p->x2_order, p->x2_tiles, &p->x2_blocks, st);
-    return launch_x2_t<RM, 4>(p, a, u, Lu, nrhs, p->x2_order, p->x2_tiles, &p->x2_blocks, st);
+    switch (var) {
+    case 0: return launch_x2_t<RM, 2, 8>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 1: return launch_x2_t<RM, 2, 5>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 2: return launch_x2_t<RM, 4, 4>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    default: return launch_x2_t<RM, 4, 3>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    }
+}
+
+static nl_status x2_launch_any(nl_plan *p, int var, const DirectArgs &a, const float *u,
+                               float *Lu, int nrhs, const int *order, int ntiles, int *bc,
+                               cudaStream_t st)
+{
+    if (p->Rmax <= 4) return launch_x2_var<4>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 8) return launch_x2_var<8>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 16) return launch_x2_var<16>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 24) return launch_x2_var<24>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    return launch_x2_var<32>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
 }
 
 // Tile order for the paired-column kernel: the cost of a 64 x rows tile is the sum of its
@@ -1061,11 +1133,8 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
         if (mode == MODE_POWER && p->Rmax <= 32 && p->x2_order) {
             const float *uf = (const float *)u;
             float *lf = (float *)Lu;
-            if (p->Rmax <= 4) return launch_x2<4>(p, a, uf, lf, nrhs, st);
-            if (p->Rmax <= 8) return launch_x2<8>(p, a, uf, lf, nrhs, st);
-            if (p->Rmax <= 16) return launch_x2<16>(p, a, uf, lf, nrhs, st);
-            if (p->Rmax <= 24) return launch_x2<24>(p, a, uf, lf, nrhs, st);
-            return launch_x2<32>(p, a, uf, lf, nrhs, st);
+            return x2_launch_any(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
+                                 &p->x2_blocks, st);
         }
         if (mode == MODE_POWER) return launch_rb_t<T, MODE_POWER>(p, a, u, Lu, nrhs, st);
         if (mode == MODE_POLY) return launch_rb_t<T, MODE_POLY>(p, a, u, Lu, nrhs, st);
@@ -1272,36 +1341,25 @@ nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, 
 }
 
 // ---------------------------------------------------------------------------
-// plan-time set-up of the paired-column FP32 kernel: the tile queue and its order, and the
-// tile height (TY = 2 or 4 warps of 8 rows) chosen by timing both on the plan itself
+// plan-time set-up of the paired-column FP32 kernel: the tile queue and its orders, and the
+// kernel variant (tile height and register budget) chosen by timing each on the plan itself
 // ---------------------------------------------------------------------------
-template <int TY>
-static nl_status x2_launch_rm(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
-                              const int *order, int ntiles, int *bc, cudaStream_t st)
-{
-    if (p->Rmax <= 4) return launch_x2_t<4, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
-    if (p->Rmax <= 8) return launch_x2_t<8, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
-    if (p->Rmax <= 16) return launch_x2_t<16, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
-    if (p->Rmax <= 24) return launch_x2_t<24, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
-    return launch_x2_t<32, TY>(p, a, u, Lu, 1, order, ntiles, bc, st);
-}
-
 nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
 {
     if (!(p->d == 2 && p->rb2d && p->family == NL_POWER && !p->symmetric && p->Rmax <= 32))
         return NL_OK;
     NL_CUDA_TRY(cudaMalloc(&p->x2_queue, 2 * sizeof(int)));
     NL_CUDA_TRY(cudaMemsetAsync(p->x2_queue, 0, 2 * sizeof(int), st));
-    int *ord[2] = { nullptr, nullptr };
-    int nt[2] = { 0, 0 }, bc[2] = { 0, 0 };
-    float ms[2] = { 0.f, 0.f };
+    int *ord[2] = { nullptr, nullptr };              // orders for TY = 2 and TY = 4
+    int nt[2] = { 0, 0 }, bc[X2_VARIANTS] = { 0, 0, 0, 0 };
+    float ms[X2_VARIANTS] = { 0.f, 0.f, 0.f, 0.f };
     float *u = nullptr, *lu = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool tune = p->N <= ((int64_t)1 << 24);
     nl_status s = NL_OK;
     for (int k = tune ? 0 : 1; k < 2 && s == NL_OK; ++k)
         s = x2_order_for(p, k == 0 ? 2 : 4, &ord[k], &nt[k], st);
-    int best = 1;
+    int best = 2;                                     // TY = 4, four blocks per SM
     if (s == NL_OK && tune) {
         const DirectArgs a = make_args(p, NL_F32);
         if (cudaMalloc(&u, p->N * sizeof(float)) != cudaSuccess ||
@@ -1310,33 +1368,35 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
             cudaMemsetAsync(u, 0, p->N * sizeof(float), st) != cudaSuccess) {
             s = nl_cuda_fail(cudaErrorMemoryAllocation, "direct kernel tuning");
         }
-        for (int k = 0; k < 2 && s == NL_OK; ++k) {
+        for (int v = 0; v < X2_VARIANTS && s == NL_OK; ++v) {
+            const int k = x2_var_ty[v] == 2 ? 0 : 1;
             auto run = [&]() {
-                return k == 0 ? x2_launch_rm<2>(p, a, u, lu, ord[k], nt[k], &bc[k], st)
-                              : x2_launch_rm<4>(p, a, u, lu, ord[k], nt[k], &bc[k], st);
+                return x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
             };
             if ((s = run()) != NL_OK) break;
             cudaEventRecord(e0, st);
             for (int r = 0; r < 3 && s == NL_OK; ++r) s = run();
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&ms[k], e0, e1);
+            cudaEventElapsedTime(&ms[v], e0, e1);
         }
-        if (s == NL_OK && ms[0] < ms[1]) best = 0;
+        best = 0;
+        for (int v = 1; v < X2_VARIANTS; ++v) if (ms[v] < ms[best]) best = v;
     }
     if (u) cudaFree(u);
     if (lu) cudaFree(lu);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (ord[1 - best]) cudaFree(ord[1 - best]);
+    const int kb = x2_var_ty[best] == 2 ? 0 : 1;
+    if (ord[1 - kb]) cudaFree(ord[1 - kb]);
     if (s != NL_OK) {
-        if (ord[best]) cudaFree(ord[best]);
+        if (ord[kb]) cudaFree(ord[kb]);
         return s;
     }
-    p->x2_order = ord[best];
-    p->x2_tiles = nt[best];
+    p->x2_order = ord[kb];
+    p->x2_tiles = nt[kb];
     p->x2_blocks = bc[best];
-    p->x2_ty = best == 0 ? 2 : 4;
-    p->device_bytes += (size_t)nt[best] * sizeof(int) + 2 * sizeof(int);
+    p->x2_var = best;
+    p->device_bytes += (size_t)nt[kb] * sizeof(int) + 2 * sizeof(int);
     return NL_OK;
 }

@@ -87,8 +87,8 @@ struct nl_plan {
     float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
     int *thr_reach;                 // symmetric variant: max threshold over the window
     int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
-    int x2_tiles, x2_blocks, x2_ty; // work-queue counter + exit ticket; persistent grid size;
-                                    // tile height in warps of 8 rows (timed at plan creation)
+    int x2_tiles, x2_blocks, x2_var;// work-queue counter + exit ticket; persistent grid size;
+                                    // kernel variant (timed at plan creation)
     // per-node device arrays
     int *thr;               // largest integer < R2_i
     int *cnt;               // table entries with o2 <= thr_i (or the symmetric bound)
