@@ -359,7 +359,8 @@ class C3(Workload):
     def kernels(self, flush, reps):
         t = self.time_fn(self.step, reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
-        roof = _alu_roof("k_direct_pd<float,staged>", 14.0 * nb, t, FP32_PEAK_TFLOPS, FP32_SRC)
+        roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, FP32_PEAK_TFLOPS,
+                         FP32_SRC)
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
         return roof, {"pd_fp32_ms": round(t, 4)}
 
@@ -435,7 +436,7 @@ class C3B(Workload):
         nb = float(sum(ball_counts(d, n, 2).sum() for n, d, _, _ in self.inst))
         if self.last:
             self.launches = 5 * self.last["iterations"] + 8
-        roof = _alu_roof("k_batch_persistent<float,PD> (all 64 instances, one launch)",
+        roof = _alu_roof("k_batch_pdx2<8,TY> (all 64 instances, one launch)",
                          14.0 * nb, t, FP32_PEAK_TFLOPS, FP32_SRC)
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond, all instances)"
         return roof, {"batch_apply_fp32_ms": round(t, 4),

@@ -16,17 +16,17 @@
 
 #define NL_BATCH_MAGIC 0x4e4c4254u   // "NLBT"
 
-enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2 };
+enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2, BK_PDX2 = 3 };
 
 struct nl_batch {
     uint32_t magic;
-    int count, kind, Rmax, shape;
+    int count, kind, kind32, Rmax, shape;   // kind32: kernel of FP32 applies
     int all_symmetric;
     nl_plan **plans;
     int64_t *off;                 // host [count + 1]
     int64_t *seg_off, *seg_len;   // device [count]
     void *inst[2];                // device instance tables for FP32 and FP64
-    int64_t total_tiles;
+    int64_t total_tiles[2];       // FP32 and FP64 tables
     int *counter;
     nl_cg_state cg;
 };
@@ -40,8 +40,8 @@ static nl_status build_tables(nl_batch *b, int shape, cudaStream_t st)
     for (int t = 0; t < 2; ++t) {
         int64_t total = 0;
         nl_batch_fill_inst(b->plans, b->count, b->off, shape, t == 0 ? NL_F32 : NL_F64,
-                           host.data(), &total);
-        b->total_tiles = total;
+                           t == 0 ? b->kind32 : b->kind, host.data(), &total);
+        b->total_tiles[t] = total;
         if (!b->inst[t]) {
             if (cudaMalloc(&b->inst[t], bytes) != cudaSuccess) {
                 nl_set_error("nl_batch_create: device allocation failed");
@@ -57,8 +57,9 @@ static nl_status build_tables(nl_batch *b, int shape, cudaStream_t st)
 
 static nl_status batch_launch(nl_batch *b, const void *u, void *Lu, int dtype, cudaStream_t st)
 {
-    return nl_batch_launch(b->kind, b->shape, dtype, b->inst[dtype == NL_F32 ? 0 : 1], b->count,
-                           b->total_tiles, b->counter, u, Lu, b->Rmax, st);
+    const int t = dtype == NL_F32 ? 0 : 1;
+    return nl_batch_launch(t == 0 ? b->kind32 : b->kind, b->shape, dtype, b->inst[t], b->count,
+                           b->total_tiles[t], b->counter, u, Lu, b->Rmax, st);
 }
 
 extern "C" nl_status nl_batch_destroy(nl_batch *b)
@@ -117,6 +118,13 @@ extern "C" nl_status nl_batch_create(nl_batch **out, int count, const nl_grid *g
         b->Rmax = p->Rmax > b->Rmax ? p->Rmax : b->Rmax;
         b->off[k + 1] = b->off[k] + (pd ? 2 : 1) * p->N;
         if (!(p->symmetric || (pd && p->const_horizon))) b->all_symmetric = 0;
+    }
+    // FP32 peridynamic applies take the paired-column kernel when every horizon is constant
+    b->kind32 = b->kind;
+    if (pd && b->Rmax <= 32) {
+        bool x2 = true;
+        for (int k = 0; k < count && x2; ++k) x2 = b->plans[k]->pd_dense32 != nullptr;
+        if (x2) b->kind32 = BK_PDX2;
     }
     std::vector<int64_t> so(count), sl(count);
     for (int k = 0; k < count; ++k) { so[k] = b->off[k]; sl[k] = b->off[k + 1] - b->off[k]; }

@@ -35,6 +35,7 @@ struct DirectArgs {
     double poly[8];
     double pd_scale;
     const double *pdext;
+    const float *pdg;         // PD, constant horizon: dense [2R+1][2R+1][3] bond tensors
 };
 
 enum { MODE_POWER = 0, MODE_POLY = 1, MODE_SYM = 2 };
@@ -893,7 +894,7 @@ struct BatchInst {
     int tiles_x;
 };
 
-enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2 };
+enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2, BK_PDX2 = 3 };
 
 template <typename T, int KIND, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
@@ -1152,6 +1153,271 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
 #undef NL_DISPATCH_MODE
 }
 
+// ---------------------------------------------------------------------------
+// Peridynamic FP32 kernel for a constant horizon, paired columns (as k_direct2d_x2): lane l
+// owns the adjacent columns 2l, 2l + 1 of PD_RB rows; a tile is 64 x (TY PD_RB) nodes.  Every
+// node has the same ball, so each column offset ox covers rows |oy| <= h(ox) for all outputs
+// (exterior neighbours are zero in the tile with in = 0).  Per bond and output pair:
+// w = c_i in_j + c_j, d = u_j - u_i, p += w (G d), nine f32x2 instructions.  FP32 partial
+// sums over four column offsets at a time (at most 4 (2R+1) bonds) go into FP64 sums.
+// ---------------------------------------------------------------------------
+constexpr int PD_RB = 4;
+
+struct PdGrp { f2_t ux[4], uy[4], c[4], in[4]; };   // four tile rows of the four planes
+
+__device__ __forceinline__ void pd_load_grp(PdGrp &g, const float *cu, int plane, int SX, int row)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float *r = cu + (row + k) * SX;
+        g.ux[k] = ld_pair(r);
+        g.uy[k] = ld_pair(r + plane);
+        g.c[k] = ld_pair(r + 2 * plane);
+        g.in[k] = ld_pair(r + 3 * plane);
+    }
+}
+
+__device__ __forceinline__ void pd_term(f2_t &px, f2_t &py, f2_t uxi, f2_t uyi, f2_t ci,
+                                        f2_t uxj, f2_t uyj, f2_t cj, f2_t inj, f2_t gxx,
+                                        f2_t gxy, f2_t gyy)
+{
+    const f2_t w = f2_fma(ci, inj, cj);
+    const f2_t dx = f2_sub(uxj, uxi), dy = f2_sub(uyj, uyi);
+    px = f2_fma(w, f2_fma(gxy, dy, f2_mul(gxx, dx)), px);
+    py = f2_fma(w, f2_fma(gyy, dy, f2_mul(gxy, dx)), py);
+}
+
+// rows oy .. oy + 3 for the PD_RB outputs: window G0 = rows oy .. oy + 3, G1 = the next four
+__device__ __forceinline__ void pd_chunk4(f2_t (&px)[PD_RB], f2_t (&py)[PD_RB],
+                                          const f2_t (&uxi)[PD_RB], const f2_t (&uyi)[PD_RB],
+                                          const f2_t (&ci)[PD_RB], const PdGrp &G0,
+                                          const PdGrp &G1, const float *gcol, int oy)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float *g = gcol + 3 * (oy + j);
+        const f2_t gxx = f2_pack(g[0], g[0]), gxy = f2_pack(g[1], g[1]), gyy = f2_pack(g[2], g[2]);
+#pragma unroll
+        for (int p = 0; p < PD_RB; ++p) {
+            const int k = p + j;
+            const PdGrp &G = k < 4 ? G0 : G1;
+            pd_term(px[p], py[p], uxi[p], uyi[p], ci[p], G.ux[k & 3], G.uy[k & 3], G.c[k & 3],
+                    G.in[k & 3], gxx, gxy, gyy);
+        }
+    }
+}
+
+__device__ __forceinline__ void pd_flush(f2_t (&px)[PD_RB], f2_t (&py)[PD_RB],
+                                         double (&sxa)[PD_RB], double (&sxb)[PD_RB],
+                                         double (&sya)[PD_RB], double (&syb)[PD_RB])
+{
+#pragma unroll
+    for (int p = 0; p < PD_RB; ++p) {
+        float a0, a1, b0, b1;
+        f2_unpack(px[p], a0, a1);
+        f2_unpack(py[p], b0, b1);
+        sxa[p] += (double)a0; sxb[p] += (double)a1;
+        sya[p] += (double)b0; syb[p] += (double)b1;
+        px[p] = f2_pack(0.f, 0.f);
+        py[p] = px[p];
+    }
+}
+
+// one 64 x (TY PD_RB) tile whose halo is staged at `sm` (four planes ux, uy, c, in of
+// SX x SY); writes both components of every output of the tile
+template <int RM, int TY>
+__device__ __forceinline__ void pd_x2_tile(const DirectArgs &a, const float *sm, int x0, int y0,
+                                           const float *__restrict__ ux,
+                                           const float *__restrict__ uy,
+                                           float *__restrict__ outx, float *__restrict__ outy)
+{
+    constexpr int SX = 64 + 2 * RM, SY = TY * PD_RB + 2 * RM + 1, PL = SX * SY;
+    const int n = a.n, R = a.R;
+    const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
+    const int ybase = y0 + threadIdx.y * PD_RB;
+    const float *ua = sm + (threadIdx.y * PD_RB + RM) * SX + 2 * threadIdx.x + RM;
+    f2_t uxi[PD_RB], uyi[PD_RB], ci[PD_RB], px[PD_RB], py[PD_RB];
+    double sxa[PD_RB], sxb[PD_RB], sya[PD_RB], syb[PD_RB];
+#pragma unroll
+    for (int p = 0; p < PD_RB; ++p) {
+        uxi[p] = ld_pair(ua + p * SX);
+        uyi[p] = ld_pair(ua + p * SX + PL);
+        ci[p] = ld_pair(ua + p * SX + 2 * PL);
+        px[p] = f2_pack(0.f, 0.f);
+        py[p] = px[p];
+        sxa[p] = sxb[p] = sya[p] = syb[p] = 0.0;
+    }
+    const int thr = a.thr[0];                        // the common threshold
+    const int gw = 2 * R + 1;
+    int cols = 0;
+    for (int ox = -R; ox <= R; ++ox) {
+        const int ox2 = ox * ox;
+        if (ox2 > thr) continue;
+        const int h = min(R, isqrt_small(thr - ox2));
+        const float *gcol = a.pdg + 3 * ((ox + R) * gw + R);    // row oy at gcol[3 oy]
+        const float *cu = ua + ox;
+        PdGrp G0, G1;
+        int oy = -h, rem = 2 * h + 1;
+        pd_load_grp(G0, cu, PL, SX, oy);
+        for (;;) {
+            if (rem < 4) break;
+            pd_load_grp(G1, cu, PL, SX, oy + 4);
+            pd_chunk4(px, py, uxi, uyi, ci, G0, G1, gcol, oy);
+            oy += 4; rem -= 4;                       // the window is G1
+            if (rem < 4) { G0 = G1; break; }
+            pd_load_grp(G0, cu, PL, SX, oy + 4);
+            pd_chunk4(px, py, uxi, uyi, ci, G1, G0, gcol, oy);
+            oy += 4; rem -= 4;                       // the window is G0 again
+        }
+        for (; rem > 0; --rem, ++oy) {
+            const float *g = gcol + 3 * oy;
+            const f2_t gxx = f2_pack(g[0], g[0]), gxy = f2_pack(g[1], g[1]),
+                       gyy = f2_pack(g[2], g[2]);
+#pragma unroll
+            for (int p = 0; p < PD_RB; ++p)
+                pd_term(px[p], py[p], uxi[p], uyi[p], ci[p], G0.ux[p], G0.uy[p], G0.c[p],
+                        G0.in[p], gxx, gxy, gyy);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                G0.ux[k] = G0.ux[k + 1]; G0.uy[k] = G0.uy[k + 1];
+                G0.c[k] = G0.c[k + 1]; G0.in[k] = G0.in[k + 1];
+            }
+            if (rem > 1) {
+                const float *r = cu + (oy + 4) * SX;
+                G0.ux[3] = ld_pair(r); G0.uy[3] = ld_pair(r + PL);
+                G0.c[3] = ld_pair(r + 2 * PL); G0.in[3] = ld_pair(r + 3 * PL);
+            }
+        }
+        if (++cols == 4) {                           // FP32 partials into the FP64 sums
+            cols = 0;
+            pd_flush(px, py, sxa, sxb, sya, syb);
+        }
+    }
+    pd_flush(px, py, sxa, sxb, sya, syb);
+#pragma unroll
+    for (int p = 0; p < PD_RB; ++p) {
+        const int y = ybase + p;
+        if (y >= n) continue;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int x = c ? xb : xa;
+            if (x >= n) continue;
+            const int64_t i = x + (int64_t)n * y;
+            const double *E = a.pdext + 3 * i;
+            const double uxv = (double)ux[i], uyv = (double)uy[i];
+            const double sx = c ? sxb[p] : sxa[p], sy = c ? syb[p] : sya[p];
+            outx[i] = (float)(a.pd_scale * (0.5 * sx - (E[0] * uxv + E[1] * uyv)));
+            outy[i] = (float)(a.pd_scale * (0.5 * sy - (E[1] * uxv + E[2] * uyv)));
+        }
+    }
+}
+
+// stage the 64 x (TY PD_RB) tile at (x0, y0) with its halo: planes ux, uy, c, in
+template <int RM, int TY>
+__device__ __forceinline__ void pd_x2_stage(const DirectArgs &a, float *sm, int x0, int y0,
+                                            const float *__restrict__ ux,
+                                            const float *__restrict__ uy)
+{
+    constexpr int SX = 64 + 2 * RM, SY = TY * PD_RB + 2 * RM + 1, PL = SX * SY;
+    const int n = a.n;
+    const float *__restrict__ cc = (const float *)a.b;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int e = tid; e < PL; e += 32 * TY) {
+        const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
+        float vx = 0.f, vy = 0.f, vc = 0.f, vi = 0.f;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+            const int64_t j = gx + (int64_t)n * gy;
+            vx = ux[j]; vy = uy[j]; vc = cc[j]; vi = 1.f;
+        }
+        sm[e] = vx; sm[e + PL] = vy; sm[e + 2 * PL] = vc; sm[e + 3 * PL] = vi;
+    }
+}
+
+template <int RM, int TY>
+__global__ void __launch_bounds__(32 * TY)
+k_direct_pd_x2(DirectArgs a, const float *__restrict__ u, float *__restrict__ Lu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    const int64_t N = a.N;
+    const float *ux = u + (int64_t)blockIdx.z * 2 * N, *uy = ux + N;
+    float *ox = Lu + (int64_t)blockIdx.z * 2 * N, *oy = ox + N;
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * (TY * PD_RB);
+    pd_x2_stage<RM, TY>(a, sm, x0, y0, ux, uy);
+    __syncthreads();
+    pd_x2_tile<RM, TY>(a, sm, x0, y0, ux, uy, ox, oy);
+}
+
+template <int RM, int TY>
+static size_t pd_x2_smem()
+{
+    return sizeof(float) * 4 * (size_t)(64 + 2 * RM) * (TY * PD_RB + 2 * RM + 1);
+}
+
+template <int RM>
+static nl_status launch_pd_x2_rm(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                                 int nrhs, cudaStream_t st)
+{
+    constexpr int TY = 2;
+    const size_t smem = pd_x2_smem<RM, TY>();
+    auto kern = k_direct_pd_x2<RM, TY>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    const dim3 grd((p->n + 63) / 64, (p->n + TY * PD_RB - 1) / (TY * PD_RB), nrhs);
+    kern<<<grd, dim3(32, TY, 1), smem, st>>>(a, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+static nl_status launch_pd_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                              int nrhs, cudaStream_t st)
+{
+    if (p->Rmax <= 4) return launch_pd_x2_rm<4>(p, a, u, Lu, nrhs, st);
+    if (p->Rmax <= 8) return launch_pd_x2_rm<8>(p, a, u, Lu, nrhs, st);
+    if (p->Rmax <= 16) return launch_pd_x2_rm<16>(p, a, u, Lu, nrhs, st);
+    return launch_pd_x2_rm<32>(p, a, u, Lu, nrhs, st);
+}
+
+// Batched peridynamic instances (constant horizons, FP32): the persistent (instance, tile)
+// queue of k_batch_persistent with the paired-column tile above; tiles are 64 x (TY PD_RB).
+template <int RM, int TY>
+__global__ void __launch_bounds__(32 * TY)
+k_batch_pdx2(const BatchInst *__restrict__ inst, int ninst, int64_t total,
+             int *__restrict__ counter, const float *__restrict__ u, float *__restrict__ Lu)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    __shared__ int s_inst;
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (;;) {
+        if (tid == 0) {
+            const long long it = atomicAdd(counter, 1);
+            int k = 0;
+            if (it < total) {
+                int hi = ninst - 1;
+                while (k < hi) {
+                    const int mid = (k + hi + 1) >> 1;
+                    if (inst[mid].tile0 <= it) k = mid; else hi = mid - 1;
+                }
+            }
+            s_item = it;
+            s_inst = k;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        const BatchInst &bi = inst[s_inst];
+        const int64_t local = item - bi.tile0;
+        const int x0 = (int)(local % bi.tiles_x) * 64, y0 = (int)(local / bi.tiles_x) * (TY * PD_RB);
+        const float *ux = u + bi.off, *uy = ux + bi.a.N;
+        float *ox = Lu + bi.off, *oy = ox + bi.a.N;
+        pd_x2_stage<RM, TY>(bi.a, sm, x0, y0, ux, uy);
+        __syncthreads();
+        pd_x2_tile<RM, TY>(bi.a, sm, x0, y0, ux, uy, ox, oy);
+        __syncthreads();               // the tile and s_item are reused by the next item
+    }
+}
+
 template <typename T>
 static nl_status launch_pd(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
                            cudaStream_t st, size_t smem)
@@ -1181,6 +1447,7 @@ static DirectArgs make_args(const nl_plan *p, int dtype)
     a.ext = f32 ? (const void *)p->ext32 : (const void *)p->ext64;
     a.wh = f32 ? (const void *)p->wh32 : (const void *)p->wh64;
     a.ir = f32 ? (const void *)p->ir32 : (const void *)p->ir64;
+    a.pdg = p->pd_dense32;
     if (p->family == NL_PD_BOND)
         a.tab = f32 ? (const void *)p->pd32 : (const void *)p->pd64;
     else
@@ -1197,6 +1464,8 @@ nl_status nl_direct_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dt
 {
     const DirectArgs a = make_args(p, dtype);
     if (p->family == NL_PD_BOND) {
+        if (dtype == NL_F32 && p->pd_dense32 && p->Rmax <= 32)
+            return launch_pd_x2(p, a, (const float *)u, (float *)Lu, nrhs, st);
         if (dtype == NL_F32)
             return launch_pd<float>(p, a, (const float *)u, (float *)Lu, nrhs, st, p->smem_bytes32);
         return launch_pd<double>(p, a, (const double *)u, (double *)Lu, nrhs, st, p->smem_bytes64);
@@ -1268,17 +1537,21 @@ extern "C" nl_status nl_apply(nl_plan *p, const void *u, void *Lu, int nrhs, int
 // batch launcher (used by nl_batch.cu)
 // ---------------------------------------------------------------------------
 nl_status nl_batch_fill_inst(nl_plan *const *plans, int count, const int64_t *offsets, int shape,
-                             int dtype, void *host_out, int64_t *total_out)
+                             int dtype, int kind, void *host_out, int64_t *total_out)
 {
+    // generic kernels: 32 x {4, 8, 16} nodes; paired-column PD: 64 x {1, 2, 4} PD_RB nodes
     static const int bxs[3] = { 32, 32, 32 }, bys[3] = { 4, 8, 16 };
+    static const int pys[3] = { PD_RB, 2 * PD_RB, 4 * PD_RB };
+    const int bx = kind == BK_PDX2 ? 64 : bxs[shape];
+    const int by = kind == BK_PDX2 ? pys[shape] : bys[shape];
     BatchInst *bi = reinterpret_cast<BatchInst *>(host_out);
     int64_t t = 0;
     for (int k = 0; k < count; ++k) {
         bi[k].a = make_args(plans[k], dtype);
         bi[k].off = offsets[k];
         bi[k].tile0 = t;
-        bi[k].tiles_x = (plans[k]->n + bxs[shape] - 1) / bxs[shape];
-        t += (int64_t)bi[k].tiles_x * ((plans[k]->n + bys[shape] - 1) / bys[shape]);
+        bi[k].tiles_x = (plans[k]->n + bx - 1) / bx;
+        t += (int64_t)bi[k].tiles_x * ((plans[k]->n + by - 1) / by);
     }
     *total_out = t;
     return NL_OK;
@@ -1316,10 +1589,52 @@ static nl_status launch_batch_t(const void *inst, int ninst, int64_t total, int 
     return NL_OK;
 }
 
+template <int RM, int TY>
+static nl_status launch_batch_pdx2_t(const void *inst, int ninst, int64_t total, int *counter,
+                                     const float *u, float *Lu, cudaStream_t st)
+{
+    const size_t smem = pd_x2_smem<RM, TY>();
+    auto kern = k_batch_pdx2<RM, TY>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem));
+    NL_CUDA_TRY(cudaGetDevice(&dev));
+    NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t blocks = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
+    if (blocks > total) blocks = total;
+    if (blocks < 1) blocks = 1;
+    NL_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    kern<<<(unsigned)blocks, dim3(32, TY), smem, st>>>((const BatchInst *)inst, ninst, total,
+                                                     counter, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+template <int RM>
+static nl_status launch_batch_pdx2_rm(int shape, const void *inst, int ninst, int64_t total,
+                                      int *counter, const float *u, float *Lu, cudaStream_t st)
+{
+    if (shape == 0) return launch_batch_pdx2_t<RM, 1>(inst, ninst, total, counter, u, Lu, st);
+    if (shape == 1) return launch_batch_pdx2_t<RM, 2>(inst, ninst, total, counter, u, Lu, st);
+    return launch_batch_pdx2_t<RM, 4>(inst, ninst, total, counter, u, Lu, st);
+}
+
 nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, int ninst,
                           int64_t total, int *counter, const void *u, void *Lu, int Rmax,
                           cudaStream_t st)
 {
+    if (kind == BK_PDX2) {
+        if (dtype != NL_F32 || Rmax > 32) {
+            nl_set_error("batched apply: paired-column PD needs FP32 and radius <= 32");
+            return NL_EINVAL;
+        }
+        const float *uf = (const float *)u;
+        float *lf = (float *)Lu;
+        if (Rmax <= 4) return launch_batch_pdx2_rm<4>(shape, inst_dev, ninst, total, counter, uf, lf, st);
+        if (Rmax <= 8) return launch_batch_pdx2_rm<8>(shape, inst_dev, ninst, total, counter, uf, lf, st);
+        if (Rmax <= 16) return launch_batch_pdx2_rm<16>(shape, inst_dev, ninst, total, counter, uf, lf, st);
+        return launch_batch_pdx2_rm<32>(shape, inst_dev, ninst, total, counter, uf, lf, st);
+    }
 #define NL_BATCH_SHAPES(T, KIND)                                                                   \
     do {                                                                                           \
         if (shape == 0) return launch_batch_t<T, KIND, 32, 4>(inst_dev, ninst, total, counter,    \

@@ -85,6 +85,7 @@ struct nl_plan {
     int rb2d;                       // 2-D register-blocked direct kernel usable
     size_t rb_smem32, rb_smem64, x2_smem;
     float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
+    float *pd_dense32;              // PD, 2-D, constant horizon: [2R+1][2R+1][3] bond tensors
     int *thr_reach;                 // symmetric variant: max threshold over the window
     int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
     int x2_tiles, x2_blocks, x2_var;// work-queue counter + exit ticket; persistent grid size;
@@ -157,7 +158,7 @@ nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, 
                           int64_t total, int *counter, const void *u, void *Lu, int Rmax,
                           cudaStream_t st);
 nl_status nl_batch_fill_inst(nl_plan *const *plans, int count, const int64_t *offsets, int shape,
-                             int dtype, void *host_out, int64_t *total_out);
+                             int dtype, int kind, void *host_out, int64_t *total_out);
 size_t nl_batch_inst_bytes();
 void nl_invert_launch(int64_t n, double *d, cudaStream_t st);
 nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,

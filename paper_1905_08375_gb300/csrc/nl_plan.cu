@@ -558,6 +558,26 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "weight table upload"));
     }
 
+    if (k->family == NL_PD_BOND && d == 2 && p->const_horizon && B <= 32) {
+        // dense bond table for the paired-column FP32 kernel: (gxx, gxy, gyy) of every offset
+        // of the (common) ball, zero outside it and at o = 0
+        const int GW = 2 * B + 1;
+        std::vector<float> gp((size_t)GW * GW * 3, 0.f);
+        for (int ox = -B; ox <= B; ++ox)
+            for (int oy = -B; oy <= B; ++oy) {
+                const int o2 = ox * ox + oy * oy;
+                if (o2 == 0 || o2 > p->thr_max) continue;
+                const double r = std::sqrt((double)o2), r3 = r * r * r;
+                float *e = &gp[((size_t)(ox + B) * GW + (oy + B)) * 3];
+                e[0] = (float)(ox * (double)ox / r3);
+                e[1] = (float)(ox * (double)oy / r3);
+                e[2] = (float)(oy * (double)oy / r3);
+            }
+        NL_TMP_TRY(dev_alloc(p, &p->pd_dense32, gp.size()));
+        ce = cudaMemcpyAsync(p->pd_dense32, gp.data(), gp.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "bond table upload"));
+    }
+
     PlanArgs pa;
     pa.d = d; pa.n = n; pa.family = k->family; pa.coef = k->coef; pa.symmetric = p->symmetric;
     pa.K = p->K; pa.N = N; pa.alpha = k->alpha; pa.sigma = p->sigma; pa.h = p->h;
@@ -604,7 +624,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->wh32, p->wh64, p->ir32, p->ir64, p->off, p->tab32, p->tab64, p->pd32,
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
                      p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx,
-                     p->x2_order, p->x2_queue };
+                     p->x2_order, p->x2_queue, p->pd_dense32 };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)
