@@ -163,10 +163,21 @@ class Workload:
         return self.units / (ms * 1e-3) / 1e9
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the roofline
+# kernel, from one ncu --set full capture of that kernel on the workload; None where no capture
+# of the current kernel exists
+PROFILED_TRAFFIC = {
+    "k_direct2d_x2": 21.03e6,          # c2, variant <16, 2, 8>
+    "k_direct_pd_x2": 9.48e6,          # c3, <8, 2>
+}
+
+
 def _alu_roof(kernel, flops, ms, peak, src):
     ach = flops / (ms * 1e-3) / 1e12
+    traffic = next((v for k, v in PROFILED_TRAFFIC.items() if kernel.startswith(k)), None)
     return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None, "peak_source": src}
+            "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
+            "peak_source": src}
 
 
 FP32_SRC = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
