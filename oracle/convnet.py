@@ -17,8 +17,18 @@ Training loss per sample b over the interior (a margin of `margin` pixels droppe
     L_b = sum (x + o - e)^2 / sum e^2,  loss = mean_b L_b.
 Gradients are the adjoint of each step, written out below; Adam is the usual update.
 
+Two-level form (the preconditioner the CG uses with a coarse block size b >= 2).  The same
+three layers without activations make one linear map K (1 -> 32 -> 32 -> 1 channels) applied
+on a coarse grid of ceil(n/b)^2 cells; with R the sum over each b x b block (cells cut by the
+grid edge sum what they hold) and P = R^T the piecewise-constant prolongation,
+    M(r) = D^{-1} r + gamma P K^T K R r,    gamma = 1 / (b^2 mean(diag A)),   A = -L,
+which is symmetric positive definite for any weights (K^T K is positive semi-definite).
+Training minimises the energy norm of the preconditioned step's error over pairs (r, e),
+A e = r:  loss = (z - e)^T A (z - e) / e^T A e  with z = M r, averaged over the batch.
+
 Parity pins (tests/test_oracle_convnet.py): forward against torch.nn.functional.conv2d
-(an independent library routine) and the gradients against central finite differences.
+(an independent library routine), the gradients against central finite differences, the
+two-level map against a dense matrix built from its definition (symmetry, definiteness).
 """
 from __future__ import annotations
 
@@ -127,3 +137,97 @@ def apply_preconditioner(w, r, dinv, n):
         return np.zeros_like(r)
     o, _ = forward(w, (xin / s).reshape(1, n, n))
     return s * (xin / s + o.reshape(-1))
+
+
+# ---------------------------------------------------------------------------
+# two-level form
+# ---------------------------------------------------------------------------
+def coarse_size(n, b):
+    return -(-n // b)
+
+
+def restrict(r, n, b):
+    """R r: sums over b x b blocks.  r: [..., n*n] -> [..., nc, nc]."""
+    nc = coarse_size(n, b)
+    r = np.asarray(r, dtype=np.float64)
+    lead = r.shape[:-1]
+    pad = np.zeros(lead + (nc * b, nc * b))
+    pad[..., :n, :n] = r.reshape(lead + (n, n))
+    return pad.reshape(lead + (nc, b, nc, b)).sum(axis=(-3, -1))
+
+
+def prolong(zc, n, b):
+    """P zc = R^T zc: each fine node takes its block's value.  [..., nc, nc] -> [..., n*n]."""
+    zc = np.asarray(zc, dtype=np.float64)
+    full = np.repeat(np.repeat(zc, b, axis=-2), b, axis=-1)
+    return full[..., :n, :n].reshape(zc.shape[:-2] + (n * n,))
+
+
+def linear_chain(Ws, x):
+    """K x for x [B, H, W] (no activations); returns the activations too."""
+    a0 = np.asarray(x, dtype=np.float64)[:, None]
+    a1 = conv(a0, Ws[0])
+    a2 = conv(a1, Ws[1])
+    u = conv(a2, Ws[2])
+    return u[:, 0], (a0, a1, a2)
+
+
+def linear_chain_adjoint(Ws, y):
+    """K^T y for y [B, H, W]."""
+    g = np.asarray(y, dtype=np.float64)[:, None]
+    g = conv_adjoint_input(g, Ws[2])
+    g = conv_adjoint_input(g, Ws[1])
+    g = conv_adjoint_input(g, Ws[0])
+    return g[:, 0]
+
+
+def chain_weight_grad(Ws, acts, gy):
+    """Gradient of sum(gy * K x) w.r.t. the three weights, given the chain's activations."""
+    a0, a1, a2 = acts
+    g3 = np.asarray(gy, dtype=np.float64)[:, None]
+    dW3 = conv_adjoint_weight(a2, g3)
+    g2 = conv_adjoint_input(g3, Ws[2])
+    dW2 = conv_adjoint_weight(a1, g2)
+    g1 = conv_adjoint_input(g2, Ws[1])
+    dW1 = conv_adjoint_weight(a0, g1)
+    return np.concatenate([dW1.ravel(), dW2.ravel(), dW3.ravel()])
+
+
+def two_level_gamma(dinv, b):
+    """gamma = 1 / (b^2 mean(diag A)) from the inverse diagonal."""
+    return 1.0 / (b * b * float(np.mean(1.0 / np.asarray(dinv, dtype=np.float64))))
+
+
+def apply_two_level(w, r, dinv, n, b, round_bf16=True):
+    """M(r) = D^{-1} r + gamma P K^T K R r for r [..., n*n]."""
+    Ws = split(bf16_round(w) if round_bf16 else np.asarray(w, dtype=np.float64))
+    r = np.asarray(r, dtype=np.float64)
+    lead = r.shape[:-1]
+    rc = restrict(r.reshape((-1, n * n)), n, b)
+    u, _ = linear_chain(Ws, rc)
+    zc = linear_chain_adjoint(Ws, u)
+    z = np.asarray(dinv) * r.reshape((-1, n * n)) + two_level_gamma(dinv, b) * prolong(zc, n, b)
+    return z.reshape(lead + (n * n,))
+
+
+def two_level_energy_loss_and_grad(w, r, e, dinv, n, b, apply_A, round_bf16=True):
+    """Mean over samples of (z - e)^T A (z - e) / e^T r with z = M r, A e = r, and its
+    gradient.  r, e: [B, n*n]; apply_A(v) applies A = -L to [B, n*n]."""
+    Ws = split(bf16_round(w) if round_bf16 else np.asarray(w, dtype=np.float64))
+    r = np.asarray(r, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    B = r.shape[0]
+    gam = two_level_gamma(dinv, b)
+    rc = restrict(r, n, b)
+    u, acts_r = linear_chain(Ws, rc)
+    zc = linear_chain_adjoint(Ws, u)
+    z = np.asarray(dinv) * r + gam * prolong(zc, n, b)
+    Az = apply_A(z)
+    er = np.sum(e * r, axis=1)
+    loss = float(np.mean((np.sum(z * Az, axis=1) - 2 * np.sum(z * r, axis=1) + er) / er))
+    go = 2.0 * (Az - r) / er[:, None] / B                 # d loss / d z (A symmetric)
+    g = gam * restrict(go, n, b)                          # d loss / d (K^T K rc)
+    v, acts_g = linear_chain(Ws, g)
+    # d <g, K^T K rc> = <v, dK rc> + <u, dK g>
+    grad = chain_weight_grad(Ws, acts_r, v) + chain_weight_grad(Ws, acts_g, u)
+    return loss, grad
