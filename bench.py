@@ -8,9 +8,11 @@ value = grid points processed per second over both applies (2 N per step), Gpts/
 
 Other workloads (--workload): c1 1-D FP64 direct (4096 nodes); c3 2-D peridynamics 512^2
 FP32; c3b batched Jacobi-CG to 1e-8 over 64 uneven peridynamic instances 128^2..512^2 (the
-operator one persistent launch over all instances; time per solve); c4 CG to relative residual 1e-8 on 256^2 (Jacobi; time per solve); c5 3-D 256^3 with
-8 right-hand sides, direct + fast FP32; ex1 / ex2 the paper's Example 1 (2-D, delta = 1/2,
-128^2) and Example 2 (1-D, K = 3, 4096 nodes), fast vs direct in FP64.
+operator one persistent launch over all instances; time per solve); c4 (c4_512) CG to
+relative residual 1e-8 on 256^2 (512^2), 8 right-hand sides, with the learned two-level
+preconditioner trained at set-up (Jacobi-CG timed beside it; time per solve); c5 3-D 256^3
+with 8 right-hand sides, direct + fast FP32; ex1 / ex2 the paper's Example 1 (2-D,
+delta = 1/2, 128^2) and Example 2 (1-D, K = 3, 4096 nodes), fast vs direct in FP64.
 
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the launching stream;
 the L2 is flushed (a 256 MiB write) before every timed step, outside the events.  Rank 0
@@ -474,48 +476,87 @@ class C3B(Workload):
 
 
 class C4(Workload):
+    """Batched CG on -L u = f with the learned two-level preconditioner (trained at set-up on
+    pairs from the method's own Jacobi-CG runs), Jacobi-CG timed beside it."""
     name = "c4"
-    metric = "CG time to relative residual 1e-8 (FP64 true residual) on -L u = f, 256^2, ms"
     unit = "ms"
     higher_is_better = False
-    dtype = "f32 operator, f64 vectors and reductions"
+    dtype = "f32 operator, f64 vectors and reductions, bf16 network weights"
+    N_DEFAULT = 256
 
-    def setup(self, n=256):
+    def setup(self, nrhs=8):
         nl, torch = self.nl, self.torch
-        from paper_1905_08375_gb300 import synth
-        self.n = n
+        from paper_1905_08375_gb300 import precond, synth
+        n = self.n = self.N_DEFAULT
+        self.nrhs = nrhs
+        self.metric = (f"batched CG time to relative residual 1e-8 (FP64 true residual) on "
+                       f"-L u = f, {nrhs} right-hand sides, {n}^2, learned two-level "
+                       f"preconditioner, ms")
         self.f = synth.heterogeneous_2d(n=n, seed=self.seed)
         f = self.f
         self.plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
                                       coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
-        self.rhs = synth.cg_rhs(n, seed=self.seed + 1)[0]
+        self.rhs = synth.cg_rhs(n, seed=self.seed + 1, count=nrhs)
         self.fr = torch.tensor(self.rhs, dtype=torch.float64, device=self.dev)
         self.x = torch.empty_like(self.fr)
+        # training (set-up, not timed): (r, e) pairs from Jacobi-CG runs of 64 other
+        # right-hand sides, 20k field samples of the energy-norm loss
+        t0 = time.perf_counter()
+        xp, ep = precond.collect_pairs(self.plan, n, seeds=range(1000, 1064), cap=64)
+        t1 = time.perf_counter()
+        self.net = nl.nl_net_create(precond.init_weights(0, two_level=True))
+        block = precond.coarse_block(n)
+        nl.nl_net_set_coarse(self.net, block)
+        hist = precond.train_energy(self.net, self.plan, xp, ep, pairs=20000, batch=8, lr=3e-3,
+                                    log_every=500)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        nl.nl_plan_set_net(self.plan, self.net)
+        self.train_info = {"pair_fields": int(xp.shape[0]), "samples": 20000, "block": block,
+                           "coarse_cells": (-(-n // block)) ** 2,
+                           "collect_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2),
+                           "loss_first_last": [round(hist[0][2], 4), round(hist[-1][2], 4)]}
+        del xp, ep
         self.units = 1
         self.config = {"workload": f"CG on -L u = f, {n}x{n}, kernel and horizon of the 2-D "
                                    "heterogeneous workload symmetrised (divergence form), "
-                                   "f Gaussian random field, Jacobi preconditioner, rtol 1e-8 "
-                                   "(FP64 true residual)", "n": n}
+                                   f"{nrhs} Gaussian random field right-hand sides solved "
+                                   "together, rtol 1e-8 (FP64 true residual); preconditioner "
+                                   "M = D^-1 + gamma P K^T K R with K the 3-layer 32-channel "
+                                   "conv net (bf16 weights) on a coarse grid", "n": n,
+                       "rhs": nrhs}
         self.last = None
 
+    def solve(self, pc):
+        return self.nl.nl_cg_solve(self.plan, self.fr, self.x, rtol=1e-8, maxit=100000,
+                                   precond=pc)
+
     def step(self):
-        self.last = self.nl.nl_cg_solve(self.plan, self.fr, self.x, rtol=1e-8, maxit=100000)
+        self.last = self.solve(self.nl.NL_PRECOND_LEARNED)
 
     def value(self, ms):
         return ms
 
     def kernels(self, flush, reps):
         nl = self.nl
+        reps = max(3, min(reps, 10))
+        sj = self.solve(nl.NL_PRECOND_JACOBI)
+        self.jacobi_its = sj["iterations"]
+        t_j = self.time_fn(lambda: self.solve(nl.NL_PRECOND_JACOBI), reps, flush)
+        t_l = self.time_fn(lambda: self.solve(nl.NL_PRECOND_LEARNED), reps, flush)
         u = self.torch.randn(self.n * self.n, device=self.dev)
         o = self.torch.empty_like(u)
         t = self.time_fn(lambda: nl.nl_apply(self.plan, u, o), reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
-        if self.last:
-            self.launches = 4 * self.last["iterations"] + 8
+        self.launches = None
         roof = _alu_roof("k_direct2d_rb<float,SYM,2> (CG operator)", 6.0 * nb, t,
                          FP32_PEAK_TFLOPS, FP32_SRC)
         roof["algorithmic_per_launch"] = f"{6 * nb:.4g} flop (6 per one-sided ball term)"
-        return roof, {"sym_apply_fp32_ms": round(t, 4), "cg": self.last}
+        self.solve(nl.NL_PRECOND_LEARNED)          # leave the learned solution in x
+        return roof, {"learned_ms": round(t_l, 3), "learned": self.last,
+                      "jacobi_ms": round(t_j, 3), "jacobi": sj,
+                      "learned_speedup_over_jacobi": round(t_j / t_l, 3),
+                      "sym_apply_fp32_ms": round(t, 4), "training": self.train_info}
 
     def e2e(self, flush, steps):
         torch = self.torch
@@ -525,15 +566,22 @@ class C4(Workload):
 
         def one():
             fd.copy_(fh, non_blocking=True)
-            self.nl.nl_cg_solve(self.plan, fd, self.x, rtol=1e-8, maxit=100000)
+            self.nl.nl_cg_solve(self.plan, fd, self.x, rtol=1e-8, maxit=100000,
+                                precond=self.nl.NL_PRECOND_LEARNED)
             xh.copy_(self.x, non_blocking=True)
-        ms = self.time_fn(one, max(1, steps), flush)
-        b = self.n * self.n * 8
+        ms = self.time_fn(one, max(1, min(steps, 10)), flush)
+        b = int(fh.numel()) * 8
         return {"value": round(ms, 4), "unit": "ms", "h2d_bytes_per_step": b,
                 "d2h_bytes_per_step": b, "ms_per_step": round(ms, 4)}
 
     def outputs(self):
         return {"x": self.x.cpu().numpy()}
+
+
+class C4L(C4):
+    """The same at 512^2."""
+    name = "c4_512"
+    N_DEFAULT = 512
 
 
 class C5(Workload):
@@ -675,7 +723,8 @@ class EX(Workload):
 def make_workload(name, dev, seed):
     if name in ("ex1", "ex2"):
         return EX(dev, seed, name)
-    return {"c1": C1, "c2": C2, "c3": C3, "c3b": C3B, "c4": C4, "c5": C5}[name](dev, seed)
+    return {"c1": C1, "c2": C2, "c3": C3, "c3b": C3B, "c4": C4, "c4_512": C4L,
+            "c5": C5}[name](dev, seed)
 
 
 # ---------------------------------------------------------------------------
@@ -689,18 +738,31 @@ def oracle_sample(w, outs, budget_s=20.0):
     import oracle
     rng = np.random.default_rng(123)
     name = w.name
-    if name == "c4":
-        t0 = time.perf_counter()
-        _, it, _ = oracle.cg(w.rhs, 2, w.n, w.f["delta"], alpha=1.5, coef=oracle.COEF_XY,
-                             a=w.f["a"], rtol=1e-8)
-        dt = time.perf_counter() - t0
+    if name in ("c4", "c4_512"):
         Lx = oracle.direct_scalar(outs["x"], 2, w.n, w.f["delta"], alpha=1.5,
                                   coef=oracle.COEF_XY, a=w.f["a"], symmetric=True)
-        res = float(np.linalg.norm(w.rhs + Lx) / np.linalg.norm(w.rhs))
-        return ({"value": round(dt * 1e3, 2), "unit": "ms", "cores": oracle.num_threads(),
-                 "kind": "oracle", "sample": f"one full FP64 Jacobi-CG solve at {w.n}^2 "
-                                             f"({it} iterations)"},
-                {"gpu_solution_fp64_oracle_residual": res})
+        res = np.linalg.norm(w.rhs + Lx, axis=1) / np.linalg.norm(w.rhs, axis=1)
+        par = {"gpu_learned_solution_fp64_oracle_residual_max": float(res.max())}
+        if w.n <= 256:
+            t0 = time.perf_counter()
+            _, it, _ = oracle.cg(w.rhs[0], 2, w.n, w.f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                                 a=w.f["a"], rtol=1e-8)
+            dt = time.perf_counter() - t0
+            return ({"value": round(dt * 1e3 * w.nrhs, 1), "unit": "ms",
+                     "cores": oracle.num_threads(), "kind": "oracle",
+                     "sample": f"one full FP64 Jacobi-CG solve at {w.n}^2 ({it} iterations, "
+                               f"{dt:.1f} s) times {w.nrhs} right-hand sides"}, par)
+        t0 = time.perf_counter()
+        oracle.direct_scalar(w.rhs[0], 2, w.n, w.f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                             a=w.f["a"], symmetric=True)
+        dt = time.perf_counter() - t0
+        its = w.last["iterations"] if w.last else 0
+        jits = getattr(w, "jacobi_its", None) or its
+        return ({"value": round(dt * 1e3 * jits * w.nrhs, 1), "unit": "ms",
+                 "cores": oracle.num_threads(), "kind": "oracle",
+                 "sample": f"one FP64 oracle operator apply at {w.n}^2 ({dt:.2f} s) times "
+                           f"{jits} Jacobi-CG iterations times {w.nrhs} right-hand sides "
+                           "(operator time only; a lower bound)"}, par)
     if name == "c3b":
         n, d, c, f0 = w.inst[0]
         t0 = time.perf_counter()
@@ -798,7 +860,7 @@ def run_gpu(args, peaks):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     steps = args.steps
-    if w.name in ("c4", "c3b"):
+    if w.name in ("c4", "c4_512", "c3b"):
         steps = max(3, min(steps, 20 if w.name == "c4" else 5))   # one step is a whole solve
     if w.name == "c5":
         steps = max(3, min(steps, 30))
@@ -887,7 +949,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c3b", "c4", "c5", "ex1", "ex2"])
+                    choices=["c1", "c2", "c3", "c3b", "c4", "c4_512", "c5", "ex1", "ex2"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

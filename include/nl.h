@@ -264,6 +264,17 @@ nl_status nl_net_prepare_pairs(nl_plan *plan, const double *r, const double *e, 
 nl_status nl_net_apply(nl_net *net, nl_plan *plan, const double *r, double *z, int nrhs, void *stream);
 /* Attach (or detach with NULL) the network used by nl_cg_solve with NL_PRECOND_LEARNED. */
 nl_status nl_plan_set_net(nl_plan *plan, nl_net *net);
+/*
+ * Two-level form (block >= 2; block = 0 restores the local form above).  The three layers
+ * without activations are one linear map K (1 -> 32 -> 32 -> 1 channels) applied on a coarse
+ * grid of ceil(n/block)^2 cells; R sums each block x block block of a field (cells cut by the
+ * grid edge sum what they hold), P = R^T copies a cell's value to its block, and
+ *     M(r) = D^{-1} r + gamma P K^T K R r,   gamma = 1 / (block^2 mean(diag(-L))),
+ * symmetric positive definite for any weights, used by nl_net_apply and by CG with
+ * NL_PRECOND_LEARNED.  nl_net_train_step_energy then minimises the same energy-norm loss with
+ * z = M r.  Errors: NL_EINVAL (block 1, negative or above 65536).
+ */
+nl_status nl_net_set_coarse(nl_net *net, int block);
 
 /*
  * nl_cg_solve for one right-hand side that also records the iterate x after every

@@ -295,6 +295,8 @@ def _net_fns():
     L.nl_net_apply.argtypes = [vp, vp, vp, vp, i, vp]
     L.nl_plan_set_net.restype = i
     L.nl_plan_set_net.argtypes = [vp, vp]
+    L.nl_net_set_coarse.restype = i
+    L.nl_net_set_coarse.argtypes = [vp, i]
     L.nl_cg_history.restype = i
     L.nl_cg_history.argtypes = [vp, vp, vp, ctypes.c_double, i, i, vp, i,
                                 ctypes.POINTER(i), ctypes.POINTER(nl_cg_stats), vp]
@@ -318,6 +320,11 @@ class Net:
             self.close()
         except Exception:
             pass
+
+
+def nl_net_set_coarse(net: Net, block: int):
+    """0: the local form; block >= 2: the two-level form on ceil(n/block)^2 coarse cells."""
+    _check(_net_fns().nl_net_set_coarse(net.handle, int(block)))
 
 
 def nl_net_create(weights, stream=None) -> Net:

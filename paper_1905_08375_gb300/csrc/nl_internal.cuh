@@ -121,6 +121,7 @@ struct nl_plan {
     cudaEvent_t prof_ev[64][3];
     nl_cg_state cg;                 // CG workspace (allocated on the first solve)
     double *dinv64;                 // inverse Jacobi diagonal (computed on first use)
+    double diag_mean;               // mean of the Jacobi diagonal (with dinv64)
     nl_net *net;                    // learned preconditioner (not owned)
     size_t device_bytes;
 };

@@ -5,6 +5,14 @@
 //   y1 = relu(conv1 x), y2 = relu(conv2 y1), o = conv3 y2     (3x3, zero padding, no bias,
 //   M(r) = s (x + o)                                           channels 1 -> 32 -> 32 -> 1)
 //
+// Two-level form (nl_net_set_coarse with a block size b >= 2): the three layers without
+// activations are one linear map K on a coarse grid of ceil(n/b)^2 cells, R sums each b x b
+// block, P = R^T copies a cell to its block, and
+//   M(r) = D^{-1} r + gamma P K^T K R r,   gamma = 1 / (b^2 mean(diag A)),
+// symmetric positive definite for any weights.  K^T is the adjoint chain (the transposed
+// weight layouts); training on the energy norm needs K applied to R r and to the coarse
+// gradient, and one backward pass over both (d <g, K^T K x> = <K g, dK x> + <K x, dK g>).
+//
 // Weights are kept as FP32 masters (Adam) and used as bfloat16 (rounded to nearest even);
 // activations and accumulation are FP32.  A 3x3 convolution tile of 16 x 16 pixels stages its
 // (16+2)^2 x CIN input halo and its CIN x 9 x COUT weights in shared memory; each thread owns
@@ -410,10 +418,65 @@ __global__ void k_energy_grad(const float *__restrict__ Lz, const float *__restr
     }
 }
 
+// ---- two-level form ----
+// rc[b][cell] = sum of v over the cell's b x b block (FP64 sum in a fixed order), times scale
+template <typename T>
+__global__ void __launch_bounds__(RB) k_restrict(const T *__restrict__ v, int n, int blk, int nc,
+                                                 double scale, float *__restrict__ rc)
+{
+    __shared__ double sh[RB / 32];
+    const int cell = blockIdx.x, b = blockIdx.y;
+    const int cy = cell / nc, cx = cell % nc;
+    const int y0 = cy * blk, x0 = cx * blk;
+    const int hy = min(blk, n - y0), hx = min(blk, n - x0);
+    const T *vb = v + (size_t)b * n * n;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < hy * hx; k += RB)
+        s += (double)vb[(size_t)(y0 + k / hx) * n + x0 + k % hx];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RB / 32; ++w) t += sh[w];
+        rc[(size_t)b * nc * nc + cell] = (float)(t * scale);
+    }
+}
+
+// z = D^{-1} r + gamma P zc (FP64, inference)
+__global__ void k_prolong_jacobi(const double *__restrict__ r, const double *__restrict__ dinv,
+                                 const float *__restrict__ zc, int n, int blk, int nc,
+                                 double gamma, double *__restrict__ z)
+{
+    const int b = blockIdx.y;
+    const int64_t N = (int64_t)n * n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / n), x = (int)(k % n);
+        const size_t g = (size_t)b * N + k;
+        z[g] = dinv[k] * r[g] + gamma * (double)zc[(size_t)b * nc * nc + (y / blk) * nc + x / blk];
+    }
+}
+
+// z = x + gamma P zc (FP32, training; x = D^{-1} r in scaled units)
+__global__ void k_prolong_add(const float *__restrict__ x, const float *__restrict__ zc, int n,
+                              int blk, int nc, float gamma, float *__restrict__ z)
+{
+    const int b = blockIdx.y;
+    const int64_t N = (int64_t)n * n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(k / n), xx = (int)(k % n);
+        const size_t g = (size_t)b * N + k;
+        z[g] = x[g] + gamma * zc[(size_t)b * nc * nc + (y / blk) * nc + xx / blk];
+    }
+}
+
 }  // namespace
 
 struct nl_net {
     uint32_t magic;
+    int block;                           // 0: local form; >= 2: two-level with b x b blocks
     float *w32, *m, *v, *grad;
     __nv_bfloat16 *wb;
     float *wk, *wkt;
@@ -441,6 +504,7 @@ static nl_status net_attrs()
     if (done) return NL_OK;
     NL_CUDA_TRY(smem_attr(k_conv3<32, 32, 1>, conv_smem(32, 32)));
     NL_CUDA_TRY(smem_attr(k_conv3<32, 32, 2>, conv_smem(32, 32)));
+    NL_CUDA_TRY(smem_attr(k_conv3<32, 32, 0>, conv_smem(32, 32)));
     NL_CUDA_TRY(smem_attr(k_conv3<32, 1, 0>, conv_smem(32, 1)));
     NL_CUDA_TRY(smem_attr(k_conv3_wgrad<32, 32>, wgrad_smem(32, 32)));
     NL_CUDA_TRY(smem_attr(k_conv3_wgrad<32, 1>, wgrad_smem(32, 1)));
@@ -630,6 +694,16 @@ static nl_status plan_dinv(nl_plan *p, cudaStream_t st, const double **out)
         NL_CUDA_TRY(cudaMemsetAsync(z, 0, per * sizeof(double), st));
         nl_status s = nl_diag_launch(p, z, d, st);
         if (s != NL_OK) { cudaFree(d); cudaFree(z); return s; }
+        // mean of the diagonal on the host (fixed order), then invert in place
+        double *h = (double *)malloc(per * sizeof(double));
+        if (!h) { cudaFree(d); cudaFree(z); return NL_ENOMEM; }
+        cudaError_t ce = cudaMemcpyAsync(h, d, per * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) { free(h); cudaFree(d); cudaFree(z); return nl_cuda_fail(ce, "diagonal"); }
+        double sum = 0.0;
+        for (int64_t k = 0; k < per; ++k) sum += h[k];
+        free(h);
+        p->diag_mean = sum / (double)per;
         nl_invert_launch(per, d, st);
         NL_CUDA_TRY(cudaStreamSynchronize(st));
         cudaFree(z);
@@ -643,7 +717,7 @@ static nl_status plan_dinv(nl_plan *p, cudaStream_t st, const double **out)
 // shared backward pass + Adam for a batch of B planes of H x W
 static nl_status net_backward_adam(nl_net *n, const float *xb, const float *y1, const float *y2,
                                    const float *go, float *g2, float *g1, int B, int H, int W,
-                                   float lr, cudaStream_t st)
+                                   float lr, cudaStream_t st, bool relu = true)
 {
     const int tiles = ((H + TILE - 1) / TILE) * ((W + TILE - 1) / TILE);
     const size_t nblk = (size_t)tiles * B;
@@ -652,10 +726,12 @@ static nl_status net_backward_adam(nl_net *n, const float *xb, const float *y1, 
     const dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE, B);
     k_conv3_wgrad<32, 1><<<grid, 256, wgrad_smem(32, 1), st>>>(y2, go, n->part, H, W);
     k_wgrad_reduce<<<(NP3 + 255) / 256, 256, 0, st>>>(n->part, (int)nblk, 32, 1, n->grad + OFF3);
-    k_conv3<1, 32, 2><<<grid, 256, conv_smem(1, 32), st>>>(go, n->wkt + OFF3, g2, y2, H, W);
+    if (relu) k_conv3<1, 32, 2><<<grid, 256, conv_smem(1, 32), st>>>(go, n->wkt + OFF3, g2, y2, H, W);
+    else k_conv3<1, 32, 0><<<grid, 256, conv_smem(1, 32), st>>>(go, n->wkt + OFF3, g2, nullptr, H, W);
     k_conv3_wgrad<32, 32><<<grid, 256, wgrad_smem(32, 32), st>>>(y1, g2, n->part, H, W);
     k_wgrad_reduce<<<(NP2 + 255) / 256, 256, 0, st>>>(n->part, (int)nblk, 32, 32, n->grad + OFF2);
-    k_conv3<32, 32, 2><<<grid, 256, conv_smem(32, 32), st>>>(g2, n->wkt + OFF2, g1, y1, H, W);
+    if (relu) k_conv3<32, 32, 2><<<grid, 256, conv_smem(32, 32), st>>>(g2, n->wkt + OFF2, g1, y1, H, W);
+    else k_conv3<32, 32, 0><<<grid, 256, conv_smem(32, 32), st>>>(g2, n->wkt + OFF2, g1, nullptr, H, W);
     k_conv3_wgrad<1, 32><<<grid, 256, wgrad_smem(1, 32), st>>>(xb, g1, n->part, H, W);
     k_wgrad_reduce<<<(NP1 + 255) / 256, 256, 0, st>>>(n->part, (int)nblk, 1, 32, n->grad + OFF1);
     n->t += 1;
@@ -665,6 +741,73 @@ static nl_status net_backward_adam(nl_net *n, const float *xb, const float *y1, 
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
+
+// ---- two-level form: coarse geometry, K and K^T on [B][nc][nc] ----
+static int coarse_n(const nl_net *n, const nl_plan *p) { return (p->n + n->block - 1) / n->block; }
+
+static double two_level_gamma(const nl_net *n, const nl_plan *p)
+{
+    return 1.0 / ((double)n->block * n->block * p->diag_mean);
+}
+
+// u = K x, keeping the activations a1, a2 ([B][32][nc][nc])
+static void chain_forward(nl_net *n, const float *x, float *a1, float *a2, float *u, int B, int nc,
+                          cudaStream_t st)
+{
+    const dim3 grid((nc + TILE - 1) / TILE, (nc + TILE - 1) / TILE, B);
+    k_conv3<1, 32, 0><<<grid, 256, conv_smem(1, 32), st>>>(x, n->wk + OFF1, a1, nullptr, nc, nc);
+    k_conv3<32, 32, 0><<<grid, 256, conv_smem(32, 32), st>>>(a1, n->wk + OFF2, a2, nullptr, nc, nc);
+    k_conv3<32, 1, 0><<<grid, 256, conv_smem(32, 1), st>>>(a2, n->wk + OFF3, u, nullptr, nc, nc);
+}
+
+// zc = K^T u (t2, t1: [B][32][nc][nc] scratch)
+static void chain_adjoint(nl_net *n, const float *u, float *t2, float *t1, float *zc, int B, int nc,
+                          cudaStream_t st)
+{
+    const dim3 grid((nc + TILE - 1) / TILE, (nc + TILE - 1) / TILE, B);
+    k_conv3<1, 32, 0><<<grid, 256, conv_smem(1, 32), st>>>(u, n->wkt + OFF3, t2, nullptr, nc, nc);
+    k_conv3<32, 32, 0><<<grid, 256, conv_smem(32, 32), st>>>(t2, n->wkt + OFF2, t1, nullptr, nc, nc);
+    k_conv3<32, 1, 0><<<grid, 256, conv_smem(32, 1), st>>>(t1, n->wkt + OFF1, zc, nullptr, nc, nc);
+}
+
+// one energy-norm Adam step of the two-level form (see the header of this file)
+static nl_status train_energy_two_level(nl_net *n, nl_plan *p, const float *x, const float *e,
+                                        int nfields, const int *fields, int batch, float lr,
+                                        const double *dinv, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const int nn = p->n, blk = n->block, nc = coarse_n(n, p);
+    const size_t f = (size_t)N * batch, c = (size_t)nc * nc, cb = c * batch;
+    // fine: xb eb rb z Lz go | coarse: in[2B] a1[2B][32] a2[2B][32] uv[2B] up[2B] t2 t1 zc
+    //        g2[2B][32] g1[2B][32]
+    const size_t need = f * 6 + cb * (2 + 64 + 64 + 2 + 2 + 32 + 32 + 1 + 64 + 64);
+    nl_status s = grow(&n->train, &n->train_elems, need);
+    if (s != NL_OK) return s;
+    float *xb = n->train, *eb = xb + f, *rb = eb + f, *z = rb + f, *Lz = z + f, *go = Lz + f;
+    float *cin = go + f, *a1 = cin + 2 * cb, *a2 = a1 + 64 * cb, *uv = a2 + 64 * cb;
+    float *up = uv + 2 * cb, *t2 = up + 2 * cb, *t1 = t2 + 32 * cb, *zc = t1 + 32 * cb;
+    float *g2 = zc + cb, *g1 = g2 + 64 * cb;
+    const double gam = two_level_gamma(n, p);
+    const unsigned gx = (unsigned)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
+    k_gather_fields<<<dim3(gx, batch), 256, 0, st>>>(x, e, fields, nfields, N, dinv, xb, eb, rb);
+    k_restrict<float><<<dim3((unsigned)c, batch), RB, 0, st>>>(rb, nn, blk, nc, 1.0, cin);
+    chain_forward(n, cin, a1, a2, uv, batch, nc, st);                       // u = K R r
+    chain_adjoint(n, uv, t2, t1, zc, batch, nc, st);                        // K^T u
+    k_prolong_add<<<dim3(gx, batch), 256, 0, st>>>(xb, zc, nn, blk, nc, (float)gam, z);
+    if ((s = nl_direct_launch(p, z, Lz, batch, NL_F32, st)) != NL_OK) return s;
+    k_energy_partial<<<dim3(NB, batch), RB, 0, st>>>(z, Lz, rb, eb, N, n->red);
+    k_energy_grad<<<dim3(gx, batch), 256, 0, st>>>(Lz, rb, N, n->red, batch, go, n->loss);
+    k_restrict<float><<<dim3((unsigned)c, batch), RB, 0, st>>>(go, nn, blk, nc, gam, cin + cb);
+    chain_forward(n, cin + cb, a1 + 32 * cb, a2 + 32 * cb, uv + cb, batch, nc, st);   // v = K g
+    // upstream: the first half (inputs R r) takes v, the second (inputs g) takes u
+    NL_CUDA_TRY(cudaMemcpyAsync(up, uv + cb, cb * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    NL_CUDA_TRY(cudaMemcpyAsync(up + cb, uv, cb * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return net_backward_adam(n, cin, a1, a2, up, g2, g1, 2 * batch, nc, nc, lr, st, false);
+}
+
+static nl_status train_energy_local(nl_net *n, nl_plan *p, const float *x, const float *e,
+                                    int nfields, const int *fields, int batch, float lr,
+                                    const double *dinv, cudaStream_t st);
 
 extern "C" nl_status nl_net_train_step_energy(nl_net *n, nl_plan *p, const float *x,
                                               const float *e, int nfields, const int *fields,
@@ -684,28 +827,21 @@ extern "C" nl_status nl_net_train_step_energy(nl_net *n, nl_plan *p, const float
     const double *dinv = nullptr;
     nl_status s = plan_dinv(p, st, &dinv);
     if (s != NL_OK) return s;
-    const int64_t N = p->N;
-    const int H = p->n, W = p->n;
-    const size_t f = (size_t)N * batch;
-    // xb eb rb o z Lz go | y1 y2 g2 g1 (32 channels each)
-    s = grow(&n->train, &n->train_elems, f * (7 + 4 * 32));
-    if (s != NL_OK) return s;
+    const size_t f = (size_t)p->N * batch;
     size_t le = (size_t)n->loss_elems;
     if ((s = grow(&n->loss, &le, (size_t)batch)) != NL_OK) return s;
     n->loss_elems = (int)le;
     size_t re = (size_t)n->red_elems;
     if ((s = grow(&n->red, &re, (size_t)NB * batch * 3)) != NL_OK) return s;
     n->red_elems = (int)re;
-    float *xb = n->train, *eb = xb + f, *rb = eb + f, *o = rb + f, *z = o + f, *Lz = z + f;
-    float *go = Lz + f, *y1 = go + f, *y2 = y1 + 32 * f, *g2 = y2 + 32 * f, *g1 = g2 + 32 * f;
-    const unsigned gx = (unsigned)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
-    k_gather_fields<<<dim3(gx, batch), 256, 0, st>>>(x, e, fields, nfields, N, dinv, xb, eb, rb);
-    if ((s = net_forward(n, xb, y1, y2, o, batch, H, W, st)) != NL_OK) return s;
-    k_add<<<(unsigned)((f + 255) / 256), 256, 0, st>>>((int64_t)f, xb, o, z);
-    if ((s = nl_direct_launch(p, z, Lz, batch, NL_F32, st)) != NL_OK) return s;
-    k_energy_partial<<<dim3(NB, batch), RB, 0, st>>>(z, Lz, rb, eb, N, n->red);
-    k_energy_grad<<<dim3(gx, batch), 256, 0, st>>>(Lz, rb, N, n->red, batch, go, n->loss);
-    if ((s = net_backward_adam(n, xb, y1, y2, go, g2, g1, batch, H, W, lr, st)) != NL_OK) return s;
+    if (n->block >= 2) {
+        s = train_energy_two_level(n, p, x, e, nfields, fields, batch, lr, dinv, st);
+    } else {
+        // xb eb rb o z Lz go | y1 y2 g2 g1 (32 channels each)
+        if ((s = grow(&n->train, &n->train_elems, f * (7 + 4 * 32))) != NL_OK) return s;
+        s = train_energy_local(n, p, x, e, nfields, fields, batch, lr, dinv, st);
+    }
+    if (s != NL_OK) return s;
     if (loss_host) {
         float tmp[1024];
         NL_CUDA_TRY(cudaMemcpyAsync(tmp, n->loss, batch * sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -715,6 +851,27 @@ extern "C" nl_status nl_net_train_step_energy(nl_net *n, nl_plan *p, const float
         *loss_host = (float)(sum / batch);
     }
     return NL_OK;
+}
+
+// one energy-norm Adam step of the local form on whole fields
+static nl_status train_energy_local(nl_net *n, nl_plan *p, const float *x, const float *e,
+                                    int nfields, const int *fields, int batch, float lr,
+                                    const double *dinv, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const int H = p->n, W = p->n;
+    const size_t f = (size_t)N * batch;
+    nl_status s;
+    float *xb = n->train, *eb = xb + f, *rb = eb + f, *o = rb + f, *z = o + f, *Lz = z + f;
+    float *go = Lz + f, *y1 = go + f, *y2 = y1 + 32 * f, *g2 = y2 + 32 * f, *g1 = g2 + 32 * f;
+    const unsigned gx = (unsigned)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
+    k_gather_fields<<<dim3(gx, batch), 256, 0, st>>>(x, e, fields, nfields, N, dinv, xb, eb, rb);
+    if ((s = net_forward(n, xb, y1, y2, o, batch, H, W, st)) != NL_OK) return s;
+    k_add<<<(unsigned)((f + 255) / 256), 256, 0, st>>>((int64_t)f, xb, o, z);
+    if ((s = nl_direct_launch(p, z, Lz, batch, NL_F32, st)) != NL_OK) return s;
+    k_energy_partial<<<dim3(NB, batch), RB, 0, st>>>(z, Lz, rb, eb, N, n->red);
+    k_energy_grad<<<dim3(gx, batch), 256, 0, st>>>(Lz, rb, N, n->red, batch, go, n->loss);
+    return net_backward_adam(n, xb, y1, y2, go, g2, g1, batch, H, W, lr, st);
 }
 
 extern "C" nl_status nl_net_gradient(nl_net *n, float *grad_host, void *stream)
@@ -729,12 +886,35 @@ extern "C" nl_status nl_net_gradient(nl_net *n, float *grad_host, void *stream)
     return NL_OK;
 }
 
+static size_t two_level_inf_elems(const nl_net *n, const nl_plan *p, int nrhs)
+{
+    const size_t c = (size_t)coarse_n(n, p) * coarse_n(n, p);
+    return c * nrhs * (1 + 32 + 32 + 1 + 32 + 32 + 1);     // rc a1 a2 u t2 t1 zc
+}
+
 nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,
                               cudaStream_t st)
 {
     const double *dinv = nullptr;
     nl_status s = plan_dinv(p, st, &dinv);
     if (s != NL_OK) return s;
+    if (n->block >= 2) {
+        const int nc = coarse_n(n, p);
+        const size_t cb = (size_t)nc * nc * nrhs;
+        s = grow(&n->inf, &n->inf_elems, two_level_inf_elems(n, p, nrhs));
+        if (s != NL_OK) return s;
+        float *rc = n->inf, *a1 = rc + cb, *a2 = a1 + 32 * cb, *u = a2 + 32 * cb;
+        float *t2 = u + cb, *t1 = t2 + 32 * cb, *zc = t1 + 32 * cb;
+        k_restrict<double><<<dim3((unsigned)(nc * nc), nrhs), RB, 0, st>>>(r, p->n, n->block, nc,
+                                                                            1.0, rc);
+        chain_forward(n, rc, a1, a2, u, nrhs, nc, st);
+        chain_adjoint(n, u, t2, t1, zc, nrhs, nc, st);
+        const unsigned gx = (unsigned)((p->N + 255) / 256 < 1024 ? (p->N + 255) / 256 : 1024);
+        k_prolong_jacobi<<<dim3(gx, nrhs), 256, 0, st>>>(r, dinv, zc, p->n, n->block, nc,
+                                                         two_level_gamma(n, p), z);
+        NL_CUDA_TRY(cudaGetLastError());
+        return NL_OK;
+    }
     const int64_t N = p->N;
     const int H = p->n, W = p->n;
     s = grow(&n->inf, &n->inf_elems, (size_t)(66) * N * nrhs);
@@ -760,7 +940,8 @@ nl_status nl_net_reserve(nl_net *n, nl_plan *p, int nrhs, cudaStream_t st)
     const double *dinv = nullptr;
     nl_status s = plan_dinv(p, st, &dinv);
     if (s != NL_OK) return s;
-    s = grow(&n->inf, &n->inf_elems, (size_t)66 * p->N * nrhs);
+    s = grow(&n->inf, &n->inf_elems, n->block >= 2 ? two_level_inf_elems(n, p, nrhs)
+                                                   : (size_t)66 * p->N * nrhs);
     if (s != NL_OK) return s;
     size_t re = (size_t)n->red_elems;
     s = grow(&n->red, &re, (size_t)NB * nrhs);
@@ -819,5 +1000,15 @@ extern "C" nl_status nl_plan_set_net(nl_plan *p, nl_net *n)
         return NL_EINVAL;
     }
     p->net = n;
+    return NL_OK;
+}
+
+extern "C" nl_status nl_net_set_coarse(nl_net *n, int block)
+{
+    if (!net_ok(n) || block < 0 || block == 1 || block > 65536) {
+        nl_set_error("nl_net_set_coarse: bad argument (block 0 or 2 .. 65536)");
+        return NL_EINVAL;
+    }
+    n->block = block;
     return NL_OK;
 }

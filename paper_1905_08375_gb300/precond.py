@@ -15,14 +15,25 @@ from . import binding as nl
 from . import synth
 
 
-def init_weights(seed=0):
-    """Seeded He-style initial weights; the last layer starts at zero so that the
-    preconditioner starts as plain Jacobi."""
+def init_weights(seed=0, two_level=False, scale=1.0):
+    """Seeded initial weights.  Local form: He-style, the last layer zero (the preconditioner
+    starts as plain Jacobi).  Two-level form: variance-preserving for a linear chain in every
+    layer (K = 0 would be a stationary point of the K^T K loss), times `scale`."""
     rng = np.random.default_rng(seed)
+    if two_level:
+        w1 = rng.standard_normal(32 * 1 * 9) * np.sqrt(1.0 / 9) * scale
+        w2 = rng.standard_normal(32 * 32 * 9) * np.sqrt(1.0 / (32 * 9)) * scale
+        w3 = rng.standard_normal(32 * 9) * np.sqrt(1.0 / (32 * 9)) * scale
+        return np.concatenate([w1, w2, w3]).astype(np.float32)
     w1 = rng.standard_normal(32 * 1 * 9) * np.sqrt(2.0 / 9)
     w2 = rng.standard_normal(32 * 32 * 9) * np.sqrt(2.0 / (32 * 9))
     w3 = np.zeros(32 * 9)
     return np.concatenate([w1, w2, w3]).astype(np.float32)
+
+
+def coarse_block(n, cells=16):
+    """Block size giving about `cells` x `cells` coarse cells."""
+    return max(2, -(-n // cells))
 
 
 def collect_pairs(plan, n, seeds, cap=64, rtol=1e-10, device="cuda"):

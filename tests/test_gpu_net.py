@@ -93,3 +93,77 @@ def test_flexible_cg_with_trained_network_converges():
                               coef=oracle.COEF_XY, a=fld["a"], symmetric=True)
     res = np.linalg.norm(f + Lx, axis=1) / np.linalg.norm(f, axis=1)
     assert np.all(res <= 1.01e-8), res
+
+
+# ---------------------------------------------------------------------------
+# two-level form: M = D^-1 + gamma P K^T K R
+# ---------------------------------------------------------------------------
+def _sym_plan(n, seed):
+    fld = synth.heterogeneous_2d(n=n, seed=seed)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    dinv = 1.0 / oracle.direct_diag(2, n, fld["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                                    a=fld["a"], symmetric=True)
+    return fld, plan, dinv
+
+
+@pytest.mark.parametrize("n,block", [(50, 8), (64, 16), (33, 2)])
+def test_two_level_apply_matches_oracle(n, block):
+    fld, plan, dinv = _sym_plan(n, 21)
+    w = precond.init_weights(3, two_level=True)
+    net = nl.nl_net_create(w)
+    nl.nl_net_set_coarse(net, block)
+    r = synth.cg_rhs(n, seed=22, count=2)
+    rt = torch.tensor(r, device=DEV)
+    zt = torch.full_like(rt, float("nan"))
+    nl.nl_net_apply(net, plan, rt, zt)
+    torch.cuda.synchronize()
+    ref = convnet.apply_two_level(w, r, dinv, n, block)
+    err = np.linalg.norm(zt.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < 1e-5, err
+
+
+def test_two_level_energy_gradient_matches_oracle():
+    n, block, B = 32, 4, 3
+    fld, plan, dinv = _sym_plan(n, 23)
+    apply_A = lambda v: -oracle.direct_scalar(v, 2, n, fld["delta"], alpha=1.5,
+                                              coef=oracle.COEF_XY, a=fld["a"], symmetric=True)
+    rng = np.random.default_rng(24)
+    e64 = np.stack([synth.gaussian_field(rng, 2, n).reshape(-1) for _ in range(B)])
+    r64 = apply_A(e64)
+    xo = torch.empty((B, n * n), dtype=torch.float32, device=DEV)
+    eo = torch.empty_like(xo)
+    nl.nl_net_prepare_pairs(plan, torch.tensor(r64, device=DEV), torch.tensor(e64, device=DEV),
+                            xo, eo)
+    w = precond.init_weights(5, two_level=True)
+    net = nl.nl_net_create(w)
+    nl.nl_net_set_coarse(net, block)
+    idx = torch.arange(B, dtype=torch.int32, device=DEV)
+    loss = nl.nl_net_train_step_energy(net, plan, xo, eo, idx, 1e-9)
+    g = nl.nl_net_gradient(net)
+    x = xo.double().cpu().numpy()
+    ref_loss, ref_g = convnet.two_level_energy_loss_and_grad(w, x / dinv, eo.double().cpu().numpy(),
+                                                             dinv, n, block, apply_A)
+    assert abs(loss - ref_loss) < 1e-4 * max(1.0, abs(ref_loss)), (loss, ref_loss)
+    assert np.linalg.norm(g - ref_g) / np.linalg.norm(ref_g) < 2e-3
+
+
+def test_two_level_learned_cg_fewer_iterations_than_jacobi():
+    n = 128
+    fld, plan, dinv = _sym_plan(n, 0)
+    x, e = precond.collect_pairs(plan, n, seeds=range(100, 112), cap=64)
+    net = nl.nl_net_create(precond.init_weights(0, two_level=True))
+    nl.nl_net_set_coarse(net, precond.coarse_block(n))
+    precond.train_energy(net, plan, x, e, pairs=3200, batch=8, lr=3e-3)
+    f = synth.cg_rhs(n, seed=998, count=3)
+    ft = torch.tensor(f, device=DEV)
+    xt = torch.empty_like(ft)
+    sj = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000, precond=nl.NL_PRECOND_JACOBI)
+    nl.nl_plan_set_net(plan, net)
+    sl = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000, precond=nl.NL_PRECOND_LEARNED)
+    assert sj["converged"] and sl["converged"], (sj, sl)
+    assert sl["iterations"] < 0.75 * sj["iterations"], (sl, sj)
+    Lx = oracle.direct_scalar(xt.cpu().numpy(), 2, n, fld["delta"], alpha=1.5,
+                              coef=oracle.COEF_XY, a=fld["a"], symmetric=True)
+    res = np.linalg.norm(f + Lx, axis=1) / np.linalg.norm(f, axis=1)
+    assert np.all(res <= 1.01e-8), res
