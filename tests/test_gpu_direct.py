@@ -67,6 +67,30 @@ def test_2d_symmetric_variant(dtype):
     assert rel_l2(run_direct(plan, f["u"][0], dtype), ref) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("n,nrhs", [(203, 2), (181, 1), (77, 8)])
+def test_2d_symmetric_paired_columns_fp32(n, nrhs):
+    """Grids large enough for the paired-column symmetrised kernel, ragged tails, several
+    right-hand sides."""
+    f = synth.heterogeneous_2d(n=n, seed=n, nrhs=nrhs)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+    ref = oracle.direct_scalar(f["u"], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                               a=f["a"], symmetric=True)
+    assert rel_l2(run_direct(plan, f["u"], torch.float32), ref) <= 2e-6
+
+
+def test_2d_symmetric_512_sampled():
+    n = 512
+    f = synth.heterogeneous_2d(n=n, seed=1)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+    got = run_direct(plan, f["u"][0], torch.float32)
+    idx = np.concatenate([sample_idx(n * n, 1500, seed=3), boundary_idx(2, n, 18, 500, seed=4)])
+    ref = oracle.direct_scalar(f["u"][0], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                               a=f["a"], symmetric=True, idx=idx)
+    assert rel_l2(got[idx], ref) <= 2e-6
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_3d_multi_rhs_ragged(dtype):
     n = 29
