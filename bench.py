@@ -617,7 +617,7 @@ class C5(Workload):
         t_d = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
         t_f = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u, self.out_f), reps, flush)
         nb = 8.0 * float(ball_counts(np.full(1, 4.0 / 256), 256, 3)[0]) * 256 ** 3
-        roof = _alu_roof("k_direct_scalar<3,float,POWER,staged>", 4.0 * nb, t_d,
+        roof = _alu_roof("k_direct3d_x2<4,4> (slab sweep)", 4.0 * nb, t_d,
                          FP32_PEAK_TFLOPS, FP32_SRC)
         roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term, 8 RHS)"
         return roof, {"direct_fp32_8rhs_ms": round(t_d, 4), "fast_fp32_8rhs_ms": round(t_f, 4)}

@@ -810,6 +810,119 @@ static nl_status x2_order_for(nl_plan *p, int ty, int **order_dev, int *ntiles, 
 }
 
 // ---------------------------------------------------------------------------
+// 3-D FP32 kernel for a constant horizon (POWER kernels): the sum over the ball splits into
+// slabs of fixed y offset oy; each slab is the 2-D paired-column sweep above in the x-z plane
+// (z the sliding axis, every row inside the common ball, no masks) over the disk of radius^2
+// thr - oy^2.  A block of TZ warps covers 64 x 1 x (TZ RB_P) outputs (x, y, z) and stages one
+// x-z slab of u and b at a time in shared memory.
+// ---------------------------------------------------------------------------
+template <int RM, int TZ>
+__global__ void __launch_bounds__(32 * TZ)
+k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restrict__ u,
+              float *__restrict__ Lu, int ztiles)
+{
+    constexpr int SX = 64 + 2 * RM, SZ = TZ * RB_P + 2 * RM + 1, PL = SX * SZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *su = reinterpret_cast<float *>(smem_raw);          // u | b
+    const int n = a.n, R = a.R;
+    const int64_t N = a.N, plane_n = (int64_t)n * n;
+    const int rhs = blockIdx.z;
+    const float *__restrict__ ur = u + (int64_t)rhs * N;
+    const float *__restrict__ bb = (const float *)a.b;
+    const int x0 = blockIdx.x * 64;
+    const int y = blockIdx.y / ztiles, z0 = (blockIdx.y % ztiles) * (TZ * RB_P);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int thr = a.thr[0];                                   // the common threshold
+    const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
+    const int zbase = z0 + threadIdx.y * RB_P;
+    f2_t ui[RB_P], acc[RB_P];
+    unsigned thr2[RB_P];                                        // unused (no masked rows)
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int z = zbase + p;
+        const float va = (xa < n && z < n) ? ur[xa + n * (y + (int64_t)n * z)] : 0.f;
+        const float vb = (xb < n && z < n) ? ur[xb + n * (y + (int64_t)n * z)] : 0.f;
+        ui[p] = f2_pack(va, vb);
+        acc[p] = f2_pack(0.f, 0.f);
+        thr2[p] = 0u;
+    }
+    const int gw = 2 * R + 1;
+    const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
+    for (int oy = -R; oy <= R; ++oy) {
+        const int t2 = thr - oy * oy;
+        const int yy = y + oy;
+        if (t2 < 0 || yy < 0 || yy >= n) continue;              // slab empty or outside
+        __syncthreads();                                         // previous slab consumed
+        for (int e = tid; e < PL; e += 32 * TZ) {
+            const int gx = x0 - RM + e % SX, gz = z0 - RM + e / SX;
+            float uv = 0.f, bv = 0.f;
+            if (gx >= 0 && gx < n && gz >= 0 && gz < n) {
+                const int64_t j = gx + (int64_t)n * yy + plane_n * gz;
+                uv = ur[j];
+                bv = bb[j];
+            }
+            su[e] = uv;
+            su[e + PL] = bv;
+        }
+        __syncthreads();
+        const int rx = min(R, isqrt_small(t2));
+        for (int ox = -rx; ox <= rx; ++ox) {
+            const int ox2 = ox * ox;
+            if (ox2 > t2) continue;
+            const int h = min(R, isqrt_small(t2 - ox2));
+            const float *gcol = g3 + ((oy + R) * gw + (ox + R)) * gw + R;   // oz at gcol[oz]
+            x2_column(acc, ui, thr2, ua + ox, PL, SX, gcol, ox2, h, h);
+        }
+    }
+    const float *__restrict__ finv = (const float *)a.fin;
+    const float *__restrict__ extv = (const float *)a.ext;
+#pragma unroll
+    for (int p = 0; p < RB_P; ++p) {
+        const int z = zbase + p;
+        if (z >= n) continue;
+        float s0, s1, u0, u1;
+        f2_unpack(acc[p], s0, s1);
+        f2_unpack(ui[p], u0, u1);
+        if (xa < n) {
+            const int64_t i = xa + n * (y + (int64_t)n * z);
+            Lu[(int64_t)rhs * N + i] = finv[i] * (s0 - u0 * extv[i]);
+        }
+        if (xb < n) {
+            const int64_t i = xb + n * (y + (int64_t)n * z);
+            Lu[(int64_t)rhs * N + i] = finv[i] * (s1 - u1 * extv[i]);
+        }
+    }
+    (void)tid;
+}
+
+template <int RM>
+static nl_status launch_3d_x2_rm(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                                 int nrhs, cudaStream_t st)
+{
+    constexpr int TZ = 4;
+    const size_t smem = sizeof(float) * 2 * (size_t)(64 + 2 * RM) * (TZ * RB_P + 2 * RM + 1);
+    auto kern = k_direct3d_x2<RM, TZ>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    const int ztiles = (p->n + TZ * RB_P - 1) / (TZ * RB_P);
+    const int64_t gy = (int64_t)p->n * ztiles;
+    if (gy > 65535 * 1024LL || nrhs > 65535) {
+        nl_set_error("nl_apply: grid too large for the 3-D slab kernel");
+        return NL_EUNSUPPORTED;
+    }
+    const dim3 grd((p->n + 63) / 64, (unsigned)gy, nrhs);
+    kern<<<grd, dim3(32, TZ, 1), smem, st>>>(a, p->g3d32, u, Lu, ztiles);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+static nl_status launch_3d_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                              int nrhs, cudaStream_t st)
+{
+    if (p->Rmax <= 4) return launch_3d_x2_rm<4>(p, a, u, Lu, nrhs, st);
+    return launch_3d_x2_rm<8>(p, a, u, Lu, nrhs, st);
+}
+
+// ---------------------------------------------------------------------------
 // Small grids: a group of SPLIT consecutive lanes shares one node; lane g takes the table
 // entries g, g + SPLIT, ... of the node's ball (neighbours read through L1), and the group's
 // partial sums are combined with shuffles (fixed order).
@@ -1130,6 +1243,8 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
         NL_SPLIT(3);
 #undef NL_SPLIT
     }
+    if (p->d == 3 && sizeof(T) == 4 && mode == MODE_POWER && p->g3d32 && p->Rmax <= 8)
+        return launch_3d_x2(p, a, (const float *)u, (float *)Lu, nrhs, st);
     if (p->d == 2 && p->rb2d && sizeof(T) == 4) {
         if (mode == MODE_POWER && p->Rmax <= 32 && p->x2_order) {
             const float *uf = (const float *)u;

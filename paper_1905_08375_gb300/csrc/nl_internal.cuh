@@ -86,6 +86,7 @@ struct nl_plan {
     size_t rb_smem32, rb_smem64, x2_smem;
     float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
     float *pd_dense32;              // PD, 2-D, constant horizon: [2R+1][2R+1][3] bond tensors
+    float *g3d32;                   // 3-D POWER, constant horizon: [2R+1]^3 weights (oy, ox, oz)
     int *thr_reach;                 // symmetric variant: max threshold over the window
     int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
     int x2_tiles, x2_blocks, x2_var;// work-queue counter + exit ticket; persistent grid size;

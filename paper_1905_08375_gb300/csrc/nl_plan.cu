@@ -558,6 +558,23 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "weight table upload"));
     }
 
+    if (k->family == NL_POWER && d == 3 && p->const_horizon && !p->symmetric && B <= 8) {
+        // dense 3-D weight table |o|^{-alpha} for the slab kernel (0 at o = 0 and outside
+        // the common ball), [oy][ox][oz]
+        const int GW = 2 * B + 1;
+        std::vector<float> g3((size_t)GW * GW * GW, 0.f);
+        for (int oy = -B; oy <= B; ++oy)
+            for (int ox = -B; ox <= B; ++ox)
+                for (int oz = -B; oz <= B; ++oz) {
+                    const int o2 = ox * ox + oy * oy + oz * oz;
+                    if (o2 == 0 || o2 > p->thr_max) continue;
+                    g3[((size_t)(oy + B) * GW + (ox + B)) * GW + (oz + B)] =
+                        (float)std::pow((double)o2, -k->alpha / 2.0);
+                }
+        NL_TMP_TRY(dev_alloc(p, &p->g3d32, g3.size()));
+        ce = cudaMemcpyAsync(p->g3d32, g3.data(), g3.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "3-D weight table upload"));
+    }
     if (k->family == NL_PD_BOND && d == 2 && p->const_horizon && B <= 32) {
         // dense bond table for the paired-column FP32 kernel: (gxx, gxy, gyy) of every offset
         // of the (common) ball, zero outside it and at o = 0
@@ -624,7 +641,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->wh32, p->wh64, p->ir32, p->ir64, p->off, p->tab32, p->tab64, p->pd32,
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
                      p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx,
-                     p->x2_order, p->x2_queue, p->pd_dense32 };
+                     p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32 };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)
