@@ -584,6 +584,7 @@ struct Step2Args {
     int nparts;
     unsigned int *mx;
     long long *pyr;
+    long long *leaf;                 // the leaf level (pyr + lvl_off[L], or a separate buffer)
     int64_t lvl_off[NL_MAX_LEVELS + 2];
 };
 
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
     const int by = d > 1 ? (int)(blockIdx.x % bands_y) : 0;
     const int bz = d > 2 ? (int)(blockIdx.x / bands_y) : 0;
     const int rows_y = d > 1 ? S : 1, rows_z = d > 2 ? S : 1;
-    long long *leaf = a.pyr + a.lvl_off[L];
+    long long *leaf = a.leaf;
     // (1) quantise and scan the band's leaf rows: the 32 loads of a page are issued first,
     // then the page is scanned 32 nodes at a time
     for (int r = warp; r < rows_y * rows_z; r += nw) {
@@ -840,6 +841,88 @@ __global__ void __launch_bounds__(256) k_fast_gather_leafrows(FastI64Args a,
     Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
 }
 
+// Several right-hand sides at once (leaf-row form): the run bounds of a row are computed once
+// and applied to every right-hand side's leaf-row prefix sums (leaf + r * N, scale mx[r]).
+constexpr int LEAF_MULTI = 8;
+constexpr int AUX_STRIDE = 16 + NL_FAST_PARTS * 4;     // bytes of one right-hand side's aux
+
+struct LeafMultiArgs {
+    int n, count;
+    int64_t N;
+    const int *thr4;
+    const double *fastF, *selfS;
+    const long long *leaf;               // [count][N]
+    const unsigned char *aux;            // [count][AUX_STRIDE], max |v| in the first word
+    double hd;
+};
+
+template <int D>
+__device__ __forceinline__ void leaf_runs_multi(long long (&G)[LEAF_MULTI], const long long *leaf,
+                                                int64_t N, int count, int64_t rowoff, int n,
+                                                int X, int r)
+{
+    const int ka = max(0, -((r - X) >> 1) - 1);
+    const int kb = min(n - 1, (X + r) >> 1);
+#pragma unroll
+    for (int q = 0; q < LEAF_MULTI; ++q) {
+        if (q < count) {
+            const long long *row = leaf + (int64_t)q * N + rowoff;
+            G[q] += __ldg(row + kb) - (ka > 0 ? __ldg(row + ka - 1) : 0LL);
+        }
+    }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_fast_gather_leafrows_multi(LeafMultiArgs a,
+                                                                    const T *__restrict__ u,
+                                                                    T *__restrict__ Lu)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)((i / n) % n) : 0;
+    const int iz = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    long long G[LEAF_MULTI];
+#pragma unroll
+    for (int q = 0; q < LEAF_MULTI; ++q) G[q] = 0;
+    if (D == 1) {
+        leaf_runs_multi<D>(G, a.leaf, a.N, a.count, 0, n, X, isqrt_fast(T4));
+    } else {
+        const int64_t pl = (int64_t)n * n;
+        for (int tz = 0; tz <= (D > 2 ? n : 0); ++tz) {
+            const int ez = tz == 0 ? 0 : sq(2 * tz - 1);
+            if (ez > T4) break;
+            for (int sz = 0; sz < (D > 2 && tz > 0 ? 2 : 1); ++sz) {
+                const int z = D > 2 ? (sz ? iz - tz : iz + tz) : 0;
+                if (z < 0 || z >= (D > 2 ? n : 1)) continue;
+                const int64_t zoff = pl * z;
+                for (int ty = 0;; ++ty) {
+                    const int e = ez + (ty == 0 ? 0 : sq(2 * ty - 1));
+                    if (e > T4) break;
+                    const int r = isqrt_fast(T4 - e);
+                    if (iy + ty < n)
+                        leaf_runs_multi<D>(G, a.leaf, a.N, a.count, zoff + (int64_t)n * (iy + ty), n, X, r);
+                    if (ty > 0 && iy - ty >= 0)
+                        leaf_runs_multi<D>(G, a.leaf, a.N, a.count, zoff + (int64_t)n * (iy - ty), n, X, r);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < LEAF_MULTI; ++q) {
+        if (q < a.count) {
+            const unsigned int *mx = (const unsigned int *)(a.aux + (size_t)q * AUX_STRIDE);
+            const int sh = fixed_shift_f32(a.N, mx);
+            const double Gd = ldexp((double)G[q], -sh);
+            const int64_t g = (int64_t)q * a.N + i;
+            Lu[g] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[g] * a.selfS[i]));
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -953,12 +1036,14 @@ static void prof_mark(nl_plan *p, int k, cudaStream_t st)
 // Step 2 of the row-prefix form: per-block bounds (and the coarse levels zeroed), then one
 // fused build (see k_step2_rowprefix).  The band side 2^c is 16 leaf rows in 2-D and 8 per
 // axis in 3-D (capped by the grid); in 1-D the single row is the band.
-static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, cudaStream_t st)
+static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, cudaStream_t st,
+                                   long long *leaf_out = nullptr, unsigned char *aux = nullptr)
 {
     const int d = p->d, L = p->L;
     long long *pyr = (long long *)p->pyr;
-    unsigned int *mx = (unsigned int *)p->fast_mx;
-    float *part = (float *)((unsigned char *)p->fast_mx + 16);
+    if (!aux) aux = (unsigned char *)p->fast_mx;
+    unsigned int *mx = (unsigned int *)aux;
+    float *part = (float *)(aux + 16);
     int64_t per = (p->N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
     if (per < 2048) per = 2048;
     const int nparts = (int)((p->N + per - 1) / per);
@@ -969,6 +1054,7 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
     a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
     a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
     a.mx = mx; a.pyr = pyr; a.leaf_only = leaf_only ? 1 : 0;
+    a.leaf = leaf_out ? leaf_out : pyr + p->lvl_off[L];
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr,
                                            leaf_only ? 0 : p->lvl_off[a.lf]);
@@ -1103,9 +1189,54 @@ extern "C" nl_status nl_plan_profile_read(nl_plan *p, double *step2_ms, double *
     return NL_OK;
 }
 
+// several FP32 right-hand sides through the leaf-row route: Step 2 per right-hand side into
+// its own leaf buffer, then one gather for up to LEAF_MULTI of them
+static nl_status fast_multi_leafrows(nl_plan *p, const float *u, float *Lu, int nrhs,
+                                     cudaStream_t st)
+{
+    const int G = std::min(nrhs, LEAF_MULTI);
+    if (p->leaf_multi_cap < G) {
+        if (p->leaf_multi) cudaFree(p->leaf_multi);
+        if (p->aux_multi) cudaFree(p->aux_multi);
+        p->leaf_multi = nullptr; p->aux_multi = nullptr; p->leaf_multi_cap = 0;
+        if (cudaMalloc(&p->leaf_multi, (size_t)G * p->N * sizeof(long long)) != cudaSuccess ||
+            cudaMalloc(&p->aux_multi, (size_t)G * AUX_STRIDE) != cudaSuccess) {
+            nl_set_error("nl_apply_fast: allocation of %d leaf buffers failed", G);
+            return NL_ENOMEM;
+        }
+        p->leaf_multi_cap = G;
+    }
+    const unsigned gb = (unsigned)((p->N + 255) / 256);
+    for (int r0 = 0; r0 < nrhs; r0 += LEAF_MULTI) {
+        const int cnt = std::min(LEAF_MULTI, nrhs - r0);
+        prof_mark(p, 0, st);
+        for (int q = 0; q < cnt; ++q)
+            NL_CUDA_TRY(step2_rowprefix(p, u + (int64_t)(r0 + q) * p->N, true, st,
+                                        p->leaf_multi + (int64_t)q * p->N,
+                                        p->aux_multi + (size_t)q * AUX_STRIDE));
+        prof_mark(p, 1, st);
+        LeafMultiArgs a;
+        a.n = p->n; a.count = cnt; a.N = p->N;
+        a.thr4 = p->thr4; a.fastF = p->fastF; a.selfS = p->selfS;
+        a.leaf = p->leaf_multi; a.aux = p->aux_multi;
+        a.hd = std::pow(p->h, (double)p->d);
+        const float *ur = u + (int64_t)r0 * p->N;
+        float *lr = Lu + (int64_t)r0 * p->N;
+        if (p->d == 1) k_fast_gather_leafrows_multi<1, float><<<gb, 256, 0, st>>>(a, ur, lr);
+        else if (p->d == 2) k_fast_gather_leafrows_multi<2, float><<<gb, 256, 0, st>>>(a, ur, lr);
+        else k_fast_gather_leafrows_multi<3, float><<<gb, 256, 0, st>>>(a, ur, lr);
+        NL_CUDA_TRY(cudaGetLastError());
+        prof_mark(p, 2, st);
+    }
+    return NL_OK;
+}
+
 nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                          cudaStream_t st)
 {
+    if (nrhs > 1 && dtype == NL_F32 && p->K == 0 && p->fast_mx &&
+        p->fast_variant == NL_FAST_LEAFROWS)
+        return fast_multi_leafrows(p, (const float *)u, (float *)Lu, nrhs, st);
     for (int r = 0; r < nrhs; ++r) {
         nl_status s;
         if (dtype == NL_F32)

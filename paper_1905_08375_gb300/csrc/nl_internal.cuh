@@ -118,6 +118,9 @@ struct nl_plan {
     unsigned long long *fast_mx;    // FP32 integer route scratch: word 0 max |v| of the last
                                     // apply (fixed-point scale), word 1 a block ticket, then
                                     // NL_FAST_PARTS per-block maxima (floats, from byte 16)
+    long long *leaf_multi;          // leaf-row prefixes of several right-hand sides (grown on
+    unsigned char *aux_multi;       // the first apply that needs them) and their scale words
+    int leaf_multi_cap;
     int prof_on, prof_count;        // per-phase timing of the fast apply
     cudaEvent_t prof_ev[64][3];
     nl_cg_state cg;                 // CG workspace (allocated on the first solve)
