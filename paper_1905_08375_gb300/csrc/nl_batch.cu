@@ -20,6 +20,8 @@ enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2, BK_PDX2 = 3 };
 
 struct nl_batch {
     uint32_t magic;
+    const double *skip;           // CG convergence flags while a batched CG runs, else null
+    int skip_stride;
     int count, kind, kind32, Rmax, shape;   // kind32: kernel of FP32 applies
     int all_symmetric;
     nl_plan **plans;
@@ -207,7 +209,18 @@ struct BatchOpCtx { nl_batch *b; };
 
 static nl_status bop_apply(void *ctx, const void *in, void *out, int dtype, cudaStream_t st)
 {
-    return batch_launch(((BatchOpCtx *)ctx)->b, in, out, dtype, st);
+    nl_batch *b = ((BatchOpCtx *)ctx)->b;
+    if (dtype != NL_F32 || !b->skip) return batch_launch(b, in, out, dtype, st);
+    // inside the iterations (FP32): converged instances are skipped
+    return nl_batch_launch(b->kind32, b->shape, dtype, b->inst[0], b->count, b->total_tiles[0],
+                           b->counter, in, out, b->Rmax, st, b->skip, b->skip_stride);
+}
+
+static void bop_set_skip(void *ctx, const double *flags, int stride)
+{
+    nl_batch *b = ((BatchOpCtx *)ctx)->b;
+    b->skip = flags;
+    b->skip_stride = stride;
 }
 
 static nl_status bop_diag(void *ctx, const double *zin, double *d, cudaStream_t st)
@@ -243,7 +256,10 @@ extern "C" nl_status nl_batch_cg_solve(nl_batch *b, const void *f, void *x, doub
     op.dinv_len = op.total;
     op.apply = bop_apply;
     op.diag = bop_diag;
+    op.set_skip = bop_set_skip;
     op.ctx = &ctx;
     op.state = &b->cg;
-    return nl_cg_run(op, f, x, rtol, maxit, precond, nullptr, 0, nullptr, stats, stream);
+    const nl_status s = nl_cg_run(op, f, x, rtol, maxit, precond, nullptr, 0, nullptr, stats, stream);
+    bop_set_skip(&ctx, nullptr, 0);
+    return s;
 }

@@ -488,6 +488,9 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
     s = op.apply(op.ctx, a.p32, a.q32, NL_F32, st);
     if (s != NL_OK) return s;
 
+    // converged segments need no operator result inside the iterations (alpha = 0 freezes
+    // them; a restart clears the flag before the next chunk reads it)
+    if (op.set_skip) op.set_skip(op.ctx, a.sc + S_CONV, S_COUNT);
     // capture one chunk of iterations (the graph bakes in f, x, nrhs, the tolerance and the
     // preconditioner)
     if (c->graph_exec && (c->graph_nrhs != nrhs || c->graph_f != f || c->graph_x != x ||

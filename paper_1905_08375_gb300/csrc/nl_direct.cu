@@ -1012,7 +1012,8 @@ enum { BK_SCALAR = 0, BK_SYM = 1, BK_PD = 2, BK_PDX2 = 3 };
 template <typename T, int KIND, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
 k_batch_persistent(const BatchInst *__restrict__ inst, int ninst, int64_t total,
-                   int *__restrict__ counter, const T *__restrict__ u, T *__restrict__ Lu)
+                   int *__restrict__ counter, const T *__restrict__ u, T *__restrict__ Lu,
+                   const double *__restrict__ skip, int skip_stride)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_item;
@@ -1035,6 +1036,10 @@ k_batch_persistent(const BatchInst *__restrict__ inst, int ninst, int64_t total,
         __syncthreads();
         const long long item = s_item;
         if (item >= total) break;
+        if (skip && skip[(size_t)s_inst * skip_stride] != 0.0) {   // instance needs no result
+            __syncthreads();
+            continue;
+        }
         const BatchInst &bi = inst[s_inst];
         const DirectArgs &a = bi.a;
         const int n = a.n, R = a.R;
@@ -1497,7 +1502,8 @@ static nl_status launch_pd_x2(nl_plan *p, const DirectArgs &a, const float *u, f
 template <int RM, int TY>
 __global__ void __launch_bounds__(32 * TY)
 k_batch_pdx2(const BatchInst *__restrict__ inst, int ninst, int64_t total,
-             int *__restrict__ counter, const float *__restrict__ u, float *__restrict__ Lu)
+             int *__restrict__ counter, const float *__restrict__ u, float *__restrict__ Lu,
+             const double *__restrict__ skip, int skip_stride)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long s_item;
@@ -1521,6 +1527,10 @@ k_batch_pdx2(const BatchInst *__restrict__ inst, int ninst, int64_t total,
         __syncthreads();
         const long long item = s_item;
         if (item >= total) break;
+        if (skip && skip[(size_t)s_inst * skip_stride] != 0.0) {   // instance needs no result
+            __syncthreads();
+            continue;
+        }
         const BatchInst &bi = inst[s_inst];
         const int64_t local = item - bi.tile0;
         const int x0 = (int)(local % bi.tiles_x) * 64, y0 = (int)(local / bi.tiles_x) * (TY * PD_RB);
@@ -1676,7 +1686,8 @@ size_t nl_batch_inst_bytes() { return sizeof(BatchInst); }
 
 template <typename T, int KIND, int BX, int BY>
 static nl_status launch_batch_t(const void *inst, int ninst, int64_t total, int *counter,
-                                const T *u, T *Lu, int Rmax, cudaStream_t st)
+                                const T *u, T *Lu, int Rmax, cudaStream_t st,
+                                const double *skip, int skip_stride)
 {
     size_t elem;
     if (KIND == BK_PD) elem = sizeof(PdV<T>);
@@ -1699,14 +1710,15 @@ static nl_status launch_batch_t(const void *inst, int ninst, int64_t total, int 
     if (blocks < 1) blocks = 1;
     NL_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     kern<<<(unsigned)blocks, dim3(BX, BY), smem, st>>>((const BatchInst *)inst, ninst, total,
-                                                       counter, u, Lu);
+                                                       counter, u, Lu, skip, skip_stride);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
 
 template <int RM, int TY>
 static nl_status launch_batch_pdx2_t(const void *inst, int ninst, int64_t total, int *counter,
-                                     const float *u, float *Lu, cudaStream_t st)
+                                     const float *u, float *Lu, const double *skip,
+                                     int skip_stride, cudaStream_t st)
 {
     const size_t smem = pd_x2_smem<RM, TY>();
     auto kern = k_batch_pdx2<RM, TY>;
@@ -1720,23 +1732,24 @@ static nl_status launch_batch_pdx2_t(const void *inst, int ninst, int64_t total,
     if (blocks < 1) blocks = 1;
     NL_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     kern<<<(unsigned)blocks, dim3(32, TY), smem, st>>>((const BatchInst *)inst, ninst, total,
-                                                     counter, u, Lu);
+                                                     counter, u, Lu, skip, skip_stride);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
 
 template <int RM>
 static nl_status launch_batch_pdx2_rm(int shape, const void *inst, int ninst, int64_t total,
-                                      int *counter, const float *u, float *Lu, cudaStream_t st)
+                                      int *counter, const float *u, float *Lu,
+                                      const double *skip, int ss, cudaStream_t st)
 {
-    if (shape == 0) return launch_batch_pdx2_t<RM, 1>(inst, ninst, total, counter, u, Lu, st);
-    if (shape == 1) return launch_batch_pdx2_t<RM, 2>(inst, ninst, total, counter, u, Lu, st);
-    return launch_batch_pdx2_t<RM, 4>(inst, ninst, total, counter, u, Lu, st);
+    if (shape == 0) return launch_batch_pdx2_t<RM, 1>(inst, ninst, total, counter, u, Lu, skip, ss, st);
+    if (shape == 1) return launch_batch_pdx2_t<RM, 2>(inst, ninst, total, counter, u, Lu, skip, ss, st);
+    return launch_batch_pdx2_t<RM, 4>(inst, ninst, total, counter, u, Lu, skip, ss, st);
 }
 
 nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, int ninst,
                           int64_t total, int *counter, const void *u, void *Lu, int Rmax,
-                          cudaStream_t st)
+                          cudaStream_t st, const double *skip, int skip_stride)
 {
     if (kind == BK_PDX2) {
         if (dtype != NL_F32 || Rmax > 32) {
@@ -1745,19 +1758,19 @@ nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, 
         }
         const float *uf = (const float *)u;
         float *lf = (float *)Lu;
-        if (Rmax <= 4) return launch_batch_pdx2_rm<4>(shape, inst_dev, ninst, total, counter, uf, lf, st);
-        if (Rmax <= 8) return launch_batch_pdx2_rm<8>(shape, inst_dev, ninst, total, counter, uf, lf, st);
-        if (Rmax <= 16) return launch_batch_pdx2_rm<16>(shape, inst_dev, ninst, total, counter, uf, lf, st);
-        return launch_batch_pdx2_rm<32>(shape, inst_dev, ninst, total, counter, uf, lf, st);
+        if (Rmax <= 4) return launch_batch_pdx2_rm<4>(shape, inst_dev, ninst, total, counter, uf, lf, skip, skip_stride, st);
+        if (Rmax <= 8) return launch_batch_pdx2_rm<8>(shape, inst_dev, ninst, total, counter, uf, lf, skip, skip_stride, st);
+        if (Rmax <= 16) return launch_batch_pdx2_rm<16>(shape, inst_dev, ninst, total, counter, uf, lf, skip, skip_stride, st);
+        return launch_batch_pdx2_rm<32>(shape, inst_dev, ninst, total, counter, uf, lf, skip, skip_stride, st);
     }
 #define NL_BATCH_SHAPES(T, KIND)                                                                   \
     do {                                                                                           \
         if (shape == 0) return launch_batch_t<T, KIND, 32, 4>(inst_dev, ninst, total, counter,    \
-                                                              (const T *)u, (T *)Lu, Rmax, st);   \
+                                                              (const T *)u, (T *)Lu, Rmax, st, skip, skip_stride); \
         if (shape == 1) return launch_batch_t<T, KIND, 32, 8>(inst_dev, ninst, total, counter,    \
-                                                              (const T *)u, (T *)Lu, Rmax, st);   \
+                                                              (const T *)u, (T *)Lu, Rmax, st, skip, skip_stride); \
         return launch_batch_t<T, KIND, 32, 16>(inst_dev, ninst, total, counter, (const T *)u,     \
-                                               (T *)Lu, Rmax, st);                                 \
+                                               (T *)Lu, Rmax, st, skip, skip_stride);              \
     } while (0)
     if (dtype == NL_F32) {
         if (kind == BK_PD) NL_BATCH_SHAPES(float, BK_PD);

@@ -616,10 +616,11 @@ constexpr int STEP2_THREADS = 512;
 __global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
 {
     __shared__ float s_w[STEP2_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = STEP2_THREADS / 32;
+    const int nt = blockDim.x;                   // STEP2_THREADS, or 128 for the leaf rows only
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nt / 32;
     // scale exponent from the per-block bounds (same arithmetic as fixed_shift_f32)
     float m = 0.f;
-    for (int k = tid; k < a.nparts; k += STEP2_THREADS) m = fmaxf(m, a.part[k]);
+    for (int k = tid; k < a.nparts; k += nt) m = fmaxf(m, a.part[k]);
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) s_w[warp] = m;
     __syncthreads();
@@ -675,7 +676,7 @@ __global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
         const int items = pr_y * pr_z * np;
         const long long *child = a.pyr + a.lvl_off[l + 1];
         long long *par = a.pyr + a.lvl_off[l];
-        for (int t = tid; t < items; t += STEP2_THREADS) {
+        for (int t = tid; t < items; t += nt) {
             const int kx = t % np, q = t / np;
             const int ky = d > 1 ? by * pr_y + q % pr_y : 0;
             const int kz = d > 2 ? bz * pr_z + q / pr_y : 0;
@@ -691,7 +692,7 @@ __global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
         const int ky = by >> (lf - l), kz = bz >> (lf - l);
         unsigned long long *par = reinterpret_cast<unsigned long long *>(
             a.pyr + a.lvl_off[l] + (int64_t)np * (ky + (int64_t)np * kz));
-        for (int kx = tid; kx < np; kx += STEP2_THREADS)
+        for (int kx = tid; kx < np; kx += nt)
             atomicAdd(par + kx, (unsigned long long)__ldcg(pf + (int64_t)(kx + 1) * step - 1));
     }
 }
@@ -1047,9 +1048,14 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
     int64_t per = (p->N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
     if (per < 2048) per = 2048;
     const int nparts = (int)((p->N + per - 1) / per);
+    // bands: one panel row of level lf = L - c; the leaf rows alone need no levels, so they
+    // take bands of four rows (a warp each) for more blocks
     int c = 0;
-    if (d == 2) c = std::min(4, L);
-    if (d == 3) c = std::min(3, L);
+    if (d == 2) c = std::min(leaf_only ? 2 : 4, L);
+    if (d == 3) c = std::min(leaf_only ? 1 : 3, L);
+    int rows = 1;
+    for (int q = 1; q < d; ++q) rows <<= c;
+    const int threads = leaf_only ? std::max(32, std::min(STEP2_THREADS, 32 * rows)) : STEP2_THREADS;
     Step2Args a;
     a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
     a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
@@ -1060,7 +1066,7 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
                                            leaf_only ? 0 : p->lvl_off[a.lf]);
     int64_t bands = 1;
     for (int q = 1; q < d; ++q) bands *= p->n >> c;
-    k_step2_rowprefix<<<(unsigned)bands, STEP2_THREADS, 0, st>>>(a);
+    k_step2_rowprefix<<<(unsigned)bands, threads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

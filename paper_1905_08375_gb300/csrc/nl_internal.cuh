@@ -58,6 +58,9 @@ struct nl_cg_op {
     nl_status (*diag)(void *ctx, const double *zin, double *d, cudaStream_t st);
     void *ctx;
     nl_cg_state *state;
+    // optional: segments whose flags[k * stride] is non-zero need no FP32 operator result
+    // (called with the CG's convergence flags before the iterations, with null after)
+    void (*set_skip)(void *ctx, const double *flags, int stride);
     nl_net *net;                    // flexible preconditioner (plan operators only)
     nl_plan *net_plan;
 };
@@ -161,7 +164,7 @@ nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream
 nl_status nl_cg_release(nl_plan *p);
 nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, int ninst,
                           int64_t total, int *counter, const void *u, void *Lu, int Rmax,
-                          cudaStream_t st);
+                          cudaStream_t st, const double *skip = nullptr, int skip_stride = 0);
 nl_status nl_batch_fill_inst(nl_plan *const *plans, int count, const int64_t *offsets, int shape,
                              int dtype, int kind, void *host_out, int64_t *total_out);
 size_t nl_batch_inst_bytes();
