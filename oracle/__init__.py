@@ -76,6 +76,8 @@ def lib():
         L.or_direct_diag.argtypes = [i, i, vp, i, d, i, vp, d, i, vp, i, vp]
         L.or_pd_direct.restype = i
         L.or_pd_direct.argtypes = [i, i, vp, vp, d, i, vp, vp, vp, i64]
+        L.or_fast_pd_leafset.restype = i
+        L.or_fast_pd_leafset.argtypes = [i, i, vp, vp, d, i, vp, vp, vp, i64]
         L.or_tree_decompose.restype = i64
         L.or_tree_decompose.argtypes = [i, i, d, i64, vp, vp, i64, vp]
         L.or_fast_tree.restype = i
@@ -240,6 +242,27 @@ def fast_leafset(u, d, L, delta, K=0, alpha=1.0, scale=1.0, normalize=True, coef
     out, cnt = _fast(lib().or_fast_leafset, u, d, L, delta, K, alpha, scale, normalize, coef, a,
                      self_mode, idx)
     return (out, cnt) if return_counts else out
+
+
+def fast_pd_leafset(u, d, L, delta, c, scale=1.0, idx=None):
+    """Fast-path peridynamics of degree 0 over the leaf set of Algorithm 1:
+    h^d sum_{k in LS(i)} scale c_ik (xi xi^T / delta_i^3) (u_k - u_i).
+    u: [nrhs, d, N] or [d, N]."""
+    u = _f64(u)
+    n = 1 << L
+    squeeze = u.ndim == 2
+    u3 = u.reshape(1, d, -1) if squeeze else u.reshape(u.shape[0], d, -1)
+    nrhs = u3.shape[0]
+    dl = _delta_field(delta, d, n)
+    c_ = _delta_field(c, d, n)
+    ix, nix = _idx(idx)
+    M = nix if ix is not None else n ** d
+    out = np.zeros((nrhs, d, M))
+    rc = lib().or_fast_pd_leafset(d, L, _ptr(dl), _ptr(c_), float(scale), nrhs, _ptr(u3),
+                                  _ptr(out), _ptr(ix), nix)
+    if rc != 0:
+        raise ValueError(f"or_fast_pd_leafset failed ({rc})")
+    return out[0] if squeeze else out
 
 
 def cg(f, d, n, delta, kind="scalar", family=POWER, alpha=0.0, K=0, scale=1.0, normalize=True,

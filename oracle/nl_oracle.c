@@ -14,6 +14,8 @@
  *   Eq. (3.1)  volume constraint u = 0 outside Omega = [0,1]^d
  *   Eq. (3.3)  L^P u = C/delta^{d+2} ( int_{H_x cap Omega} u - |H_x| u(x) )
  *   Algorithm 1 (recur), Algorithm 2 (cube/ball test), Steps 1-3, Eq. (3.5)
+ *   Sec. 4     outlook: a fast algorithm for peridynamics (here: degree 0 over the
+ *              leaf set, or_fast_pd_leafset)
  *
  * Conventions (readings of the paper, stated once here):
  *   - grid: n nodes per dimension, h = 1/n, node i at x_i = (i + 1/2) h
@@ -712,6 +714,68 @@ int or_fast_leafset(int d, int L, const double *delta, int K, const double *p, d
                     }
             if (cells && r == 0) cells[q] = count;
             out[(int64_t)r * M + q] = sigma * Ax * pow(di, -(d + 2.0)) * (hd * G - ur[fi] * Sx);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Fast-path peridynamics (the polynomial micromodulus of the paper's outlook, degree 0):
+ * the bond tensor xi xi^T / |xi|^3 of Eq. (1.2) is replaced by xi xi^T p(|xi|/delta_i) /
+ * delta_i^3 with p = 1 (p matches s^{-3} at the horizon, as p^{2K} with K = 0 matches
+ * gamma), and the sum runs over the leaf set of Algorithm 1 (every leaf cell, inside Omega
+ * or not, that meets the open ball of x_i):
+ *   (L u)_i = h^d sum_{k in LS(i), k != i} sigma c_ik (xi xi^T / delta_i^3) (u_k - u_i),
+ * c_ik = (c_i + c_k)/2, with u_k = 0 and c_k = c_i for cells outside Omega.
+ * u, out: [nrhs][d][N].  idx as above.
+ */
+int or_fast_pd_leafset(int d, int L, const double *delta, const double *c, double sigma,
+                       int nrhs, const double *u, double *out, const int64_t *idx, int64_t nidx)
+{
+    if (d < 1 || d > 3 || L < 0 || L > 20) return 1;
+    const int n = 1 << L;
+    const int64_t N = num_nodes(d, n);
+    const int64_t M = idx ? nidx : N;
+    const double h = 1.0 / n, hd = pow(h, d);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < M; ++q) {
+        const int64_t fi = idx ? idx[q] : q;
+        int64_t ci[3];
+        unflatten(fi, d, n, ci);
+        const double di = delta[fi];
+        const double R2x4 = 4.0 * ((di * n) * (di * n));
+        const int64_t B = (int64_t)ceil(di * n) + 1;
+        const int64_t bz = d > 2 ? B : 0, by = d > 1 ? B : 0;
+        const double pre = sigma * hd / (di * di * di);
+        for (int r = 0; r < nrhs; ++r) {
+            const double *ur = u + (int64_t)r * d * N;
+            double acc[3] = { 0, 0, 0 };
+            for (int64_t oz = -bz; oz <= bz; ++oz)
+                for (int64_t oy = -by; oy <= by; ++oy)
+                    for (int64_t ox = -B; ox <= B; ++ox) {
+                        int64_t o[3] = { ox, oy, oz }, cj[3];
+                        int64_t dmin = 0;
+                        int inside = 1;
+                        for (int k = 0; k < d; ++k) {
+                            int64_t lo = 2 * (ci[k] + o[k]), hi = lo + 2, X = 2 * ci[k] + 1;
+                            if (lo > X) dmin += (lo - X) * (lo - X);
+                            else if (hi < X) dmin += (hi - X) * (hi - X);
+                            cj[k] = ci[k] + o[k];
+                            if (cj[k] < 0 || cj[k] >= n) inside = 0;
+                        }
+                        if (!((double)dmin < R2x4)) continue;
+                        if (ox == 0 && oy == 0 && oz == 0) continue;
+                        const int64_t fj = inside ? flatten(cj, d, n) : -1;
+                        double xi[3], xdu = 0.0;
+                        for (int k = 0; k < d; ++k) {
+                            xi[k] = (double)o[k] * h;
+                            const double uj = inside ? ur[(int64_t)k * N + fj] : 0.0;
+                            xdu += xi[k] * (uj - ur[(int64_t)k * N + fi]);
+                        }
+                        const double cik = 0.5 * (c[fi] + (inside ? c[fj] : c[fi]));
+                        for (int k = 0; k < d; ++k) acc[k] += cik * xdu * xi[k];
+                    }
+            for (int k = 0; k < d; ++k) out[((int64_t)r * d + k) * M + q] = pre * acc[k];
         }
     }
     return 0;

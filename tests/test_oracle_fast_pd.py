@@ -1,0 +1,93 @@
+"""Pins for the oracle of the degree-0 fast-path peridynamic operator: the bond tensor
+xi xi^T p(|xi|/delta)/delta^3 with p = 1, summed over the leaf set of Algorithm 1."""
+import numpy as np
+
+import oracle
+from paper_1905_08375_gb300 import synth
+
+
+def _interior(d, n, R):
+    idx = np.arange(n ** d)
+    ok = np.ones(n ** d, dtype=bool)
+    rest = idx.copy()
+    for _ in range(d):
+        c = rest % n
+        rest //= n
+        ok &= (c >= R) & (c < n - R)
+    return idx[ok]
+
+
+def test_rigid_motions_annihilated():
+    """Constant displacements and u = W x with W antisymmetric stretch no bond:
+    xi^T W xi = 0 term by term, for any c."""
+    n, L = 32, 5
+    f = synth.pd_2d(n=n, seed=2)
+    X = synth.node_coords(2, n)
+    x, y = X[0].reshape(-1), X[1].reshape(-1)
+    inner = _interior(2, n, 6)
+    for u in (np.stack([np.full(n * n, 0.7), np.full(n * n, -1.3)]),
+              np.stack([-0.4 * y, 0.4 * x])):
+        Lu = oracle.fast_pd_leafset(u, 2, L, 4.0 / n, f["c"], idx=inner)
+        assert np.abs(Lu).max() < 1e-10
+
+
+def test_quadratic_field_continuum_limit():
+    """c = 1, delta fixed: for u = (x^2, 0) the x-component tends to
+    delta^-3 int_{B_delta} xi_x^4 = pi delta^3 / 8, for u = (x y, 0) the y-component to
+    delta^-3 int xi_x^2 xi_y^2 = pi delta^3 / 24; the leaf set exceeds the ball by a rim of
+    cells, so the error falls like h."""
+    delta = 0.25
+    errs = []
+    for L in (6, 7, 8):
+        n = 1 << L
+        X = synth.node_coords(2, n)
+        x, y = X[0].reshape(-1), X[1].reshape(-1)
+        c = np.ones(n * n)
+        node = np.array([(n // 2) * n + n // 2])
+        Lu = oracle.fast_pd_leafset(np.stack([x * x, 0 * x]), 2, L, delta, c, idx=node)
+        e1 = abs(Lu[0, 0] - np.pi * delta ** 3 / 8) / (np.pi * delta ** 3 / 8)
+        Lu = oracle.fast_pd_leafset(np.stack([x * y, 0 * x]), 2, L, delta, c, idx=node)
+        e2 = abs(Lu[1, 0] - np.pi * delta ** 3 / 24) / (np.pi * delta ** 3 / 24)
+        errs.append(max(e1, e2))
+    assert errs[-1] < 0.08
+    for k in (1, 2):                                    # first order: halves per doubling
+        assert 0.4 < errs[k] / errs[k - 1] < 0.6, errs
+
+
+def test_symmetric_negative_semidefinite():
+    """Constant delta: cell k meets the ball of x_i iff cell i meets the ball of x_k, and
+    c_ik = c_ki, so the operator is symmetric; each bond adds -c (xi.v)^2 to <L v, v>."""
+    n, L = 8, 3
+    rng = np.random.default_rng(5)
+    c = rng.uniform(1.0, 10.0, n * n)
+    N2 = 2 * n * n
+    A = np.zeros((N2, N2))
+    for k in range(N2):
+        e = np.zeros(N2)
+        e[k] = 1.0
+        A[:, k] = oracle.fast_pd_leafset(e.reshape(2, -1), 2, L, 2.5 / n, c).reshape(-1)
+    np.testing.assert_allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).max() < 1e-12 * np.abs(A).max()
+
+
+def test_leaf_set_is_the_fast_scalar_set():
+    """The sum runs over the leaf cells the scalar fast oracle counts: with u = (e_k, 0) the
+    x-component at x_i is non-zero iff cell k is in the leaf set and xi_x != 0, with
+    u = (0, e_k) the y-component iff xi_y != 0; together, every leaf cell but x_i's own."""
+    n, L = 16, 4
+    rng = np.random.default_rng(6)
+    delta = np.ascontiguousarray(rng.uniform(1.2, 3.5, n * n) / n)
+    node = 5 * n + 7
+    _, cnt = oracle.fast_leafset(np.zeros(n * n), 2, L, delta, idx=np.array([node]),
+                                 return_counts=True)
+    support = 0
+    for k in range(n * n):
+        ux = np.zeros((2, n * n))
+        ux[0, k] = 1.0
+        uy = np.zeros((2, n * n))
+        uy[1, k] = 1.0
+        a = oracle.fast_pd_leafset(ux, 2, L, delta, np.ones(n * n), idx=np.array([node]))
+        b = oracle.fast_pd_leafset(uy, 2, L, delta, np.ones(n * n), idx=np.array([node]))
+        if k != node and (a[0, 0] != 0 or b[1, 0] != 0):
+            support += 1
+    assert support == cnt[0] - 1
