@@ -360,6 +360,7 @@ class C3(Workload):
                                       coef=nl.NL_COEF_MEAN, a=f["c"])
         self.u = torch.tensor(f["u"], dtype=torch.float32, device=self.dev)
         self.out = torch.empty_like(self.u)
+        self.out_f = torch.empty_like(self.u)
         self.units = 512 * 512
         self.launches = 1
         self.config = {"workload": "2D linear bond-based PD, 512x512, delta=8h, micromodulus "
@@ -371,11 +372,16 @@ class C3(Workload):
 
     def kernels(self, flush, reps):
         t = self.time_fn(self.step, reps, flush)
+        t_f = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan, self.u, self.out_f), reps,
+                           flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, FP32_PEAK_TFLOPS,
                          FP32_SRC)
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
-        return roof, {"pd_fp32_ms": round(t, 4)}
+        return roof, {"pd_fp32_ms": round(t, 4), "pd_fast_deg0_fp32_ms": round(t_f, 4),
+                      "pd_fast_note": "nl_apply_fast on the PD plan: degree-0 bond tensor "
+                                      "xi xi^T / delta^3 over the leaf set (a different "
+                                      "operator), exact 64-bit leaf-row moment sums"}
 
     def e2e(self, flush, steps):
         torch = self.torch
@@ -393,12 +399,15 @@ class C3(Workload):
                 "d2h_bytes_per_step": b, "ms_per_step": round(ms, 4)}
 
     def outputs(self):
-        return {"pd": self.out.double().cpu().numpy().reshape(2, -1)}
+        return {"pd": self.out.double().cpu().numpy().reshape(2, -1),
+                "pd_fast": self.out_f.double().cpu().numpy().reshape(2, -1)}
 
     @staticmethod
     def oracle_step(f, n, idx):
         import oracle
-        return {"pd": oracle.pd_direct(f["u"], 2, n, f["delta"], f["c"], idx=idx)[0]}, len(idx)
+        return {"pd": oracle.pd_direct(f["u"], 2, n, f["delta"], f["c"], idx=idx)[0],
+                "pd_fast": oracle.fast_pd_leafset(f["u"][0], 2, 9, f["delta"], f["c"],
+                                                  idx=idx)}, 2 * len(idx)
 
 
 class C3B(Workload):

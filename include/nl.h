@@ -157,6 +157,14 @@ nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, 
  * result equals h^d sum over the leaf cells that meet the ball.
  * Requires family NL_POLY, a non-symmetric horizon, n = 2^L and coefficient
  * NL_COEF_NONE, NL_COEF_X or NL_COEF_XY; else NL_EUNSUPPORTED.
+ *
+ * On a 2-D NL_PD_BOND plan (n = 2^L <= 8192, FP32 data) it applies the fast-path
+ * peridynamic operator of degree 0 (the paper's outlook, Sec. 4): the bond tensor
+ * xi xi^T / |xi|^3 replaced by xi xi^T / delta_i^3 (p = 1 matched at the horizon) and the
+ * sum taken over the same leaf set,
+ *     (L u)_i = h^2 sum_{k in LS(i)} sigma c_ik (xi xi^T / delta_i^3) (u_k - u_i),
+ * c_ik = (c_i + c_k)/2, u_k = 0 and c_k = c_i outside Omega; a different operator from
+ * nl_apply's, computed from exact 64-bit leaf-row moment sums.
  * Same layouts and ownership as nl_apply.
  */
 nl_status nl_apply_fast(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, void *stream);

@@ -1265,6 +1265,13 @@ extern "C" nl_status nl_apply_fast(nl_plan *p, const void *u, void *Lu, int nrhs
         nl_set_error("nl_apply_fast: need non-null u/Lu, nrhs >= 1, dtype F32/F64");
         return NL_EINVAL;
     }
+    if (p->family == NL_PD_BOND) {
+        if (dtype != NL_F32) {
+            nl_set_error("nl_apply_fast: the fast peridynamic path takes FP32 data");
+            return NL_EUNSUPPORTED;
+        }
+        return nl_fast_pd_launch(p, (const float *)u, (float *)Lu, nrhs, nl_stream(stream));
+    }
     if (p->family != NL_POLY || p->symmetric || p->L < 0 || !p->pyr) {
         nl_set_error("nl_apply_fast: needs a non-symmetric NL_POLY plan on n = 2^L "
                      "(d = 3 only with K = 0)");

@@ -1,0 +1,326 @@
+// nl_fast_pd.cu -- fast-path peridynamics of degree 0 (the outlook of Sec. 4: a fast
+// algorithm for the linear peridynamic operator).  The bond tensor xi xi^T / |xi|^3 of
+// Eq. (1.2) is replaced by xi xi^T p(|xi|/delta_i) / delta_i^3 with p = 1 (the degree-0
+// member of the p^{2K} family, matched at the horizon), summed over the leaf set of
+// Algorithm 1 -- every leaf cell meeting the open ball, inside Omega or not (outside:
+// u = 0, c = c_i).  In lattice offsets o (xi = o h):
+//   (L u)_i = F_i [ c_i A_i + B_i - M_i u_i ],   F_i = sigma h^{d+2} / (2 delta_i^3)
+//   A_i = sum_{k in LS(i), in Omega} o o^T u_k,   B_i = the same with (c u)_k,
+//   M_i = sum_{k in LS(i)} (c_i + c_k) o o^T      (plan-time constant, FP64).
+// A and B are exact integer sums: each of u_x, u_y, c u_x, c u_y is rounded once to a
+// multiple of 2^-S (S per field and apply, from its max |.|), and along every leaf row the
+// prefix sums of q, k q and k^2 q (k the column) give, for the run of a row, the sums of
+// o_x^2 q, o_x q and q by differences.  Rows and runs are those of the scalar leaf-row gather
+// (the same half-unit geometry).  2-D, FP32 data.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "nl_internal.cuh"
+
+namespace {
+
+constexpr int FPD_FIELDS = 4;                   // u_x, u_y, c u_x, c u_y
+constexpr int FPD_ARRAYS = 10;                  // ux: P0 P1 P2, uy: P0 P1, cux: P0 P1 P2, cuy: P0 P1
+constexpr int FPD_PARTS = 1024;
+
+__device__ __forceinline__ int isqrt_pd(int x)   // floor(sqrt(x)), 0 <= x < 2^30
+{
+    const float f = (float)max(x, 1);
+    int h = __float2int_rz(f * rsqrtf(f));
+    h -= (h * h > x);
+    h += ((h + 1) * (h + 1) <= x);
+    return h;
+}
+__device__ __forceinline__ int sqi(int v) { return v * v; }
+
+// plan time: F_i and M_i (FP64) over the whole leaf set
+__global__ void k_fpd_node(int n, int64_t N, double sigma, double h, const double *__restrict__ delta,
+                           const double *__restrict__ c, const int *__restrict__ thr4,
+                           double *__restrict__ F, double *__restrict__ M)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int ix = (int)(i % n), iy = (int)(i / n);
+    const int X = 2 * ix + 1, Y = 2 * iy + 1;
+    const int T4 = thr4[i];
+    const double ci = c ? c[i] : 1.0;
+    double mxx = 0.0, mxy = 0.0, myy = 0.0;
+    const int r0 = isqrt_pd(T4);
+    const int ylo = -((r0 - Y) >> 1) - 1, yhi = (Y + r0) >> 1;       // rows meeting the ball
+    for (int ky = ylo; ky <= yhi; ++ky) {
+        const int y0 = 2 * ky - Y, y1 = y0 + 2;
+        const int e = y0 > 0 ? sqi(y0) : (y1 < 0 ? sqi(y1) : 0);
+        if (e > T4) continue;
+        const int r = isqrt_pd(T4 - e);
+        const int ka = -((r - X) >> 1) - 1, kb = (X + r) >> 1;
+        const int dy = ky - iy;
+        const bool row_in = ky >= 0 && ky < n;
+        for (int kx = ka; kx <= kb; ++kx) {
+            const int dx = kx - ix;
+            if (dx == 0 && dy == 0) continue;
+            const bool in = row_in && kx >= 0 && kx < n;
+            const double w = ci + (in ? (c ? c[(int64_t)ky * n + kx] : 1.0) : ci);
+            mxx += w * dx * dx;
+            mxy += w * dx * dy;
+            myy += w * dy * dy;
+        }
+    }
+    const double di = delta[i];
+    F[i] = sigma * h * h * h * h / (2.0 * di * di * di);
+    M[3 * i] = mxx; M[3 * i + 1] = mxy; M[3 * i + 2] = myy;
+}
+
+// per-block bounds of |u_x|, |u_y|, |c u_x|, |c u_y| (FP32 products), enlarged by 2^-20
+__global__ void __launch_bounds__(256) k_fpd_absmax(int64_t N, const float *__restrict__ ux,
+                                                    const float *__restrict__ uy,
+                                                    const float *__restrict__ c,
+                                                    float *__restrict__ part)
+{
+    __shared__ float s_w[FPD_FIELDS][8];
+    float m[FPD_FIELDS] = { 0.f, 0.f, 0.f, 0.f };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = ux[i], b = uy[i], cc = c[i];
+        m[0] = fmaxf(m[0], fabsf(a));
+        m[1] = fmaxf(m[1], fabsf(b));
+        m[2] = fmaxf(m[2], fabsf(cc * a));
+        m[3] = fmaxf(m[3], fabsf(cc * b));
+    }
+#pragma unroll
+    for (int f = 0; f < FPD_FIELDS; ++f) {
+        for (int o = 16; o > 0; o >>= 1) m[f] = fmaxf(m[f], __shfl_xor_sync(0xffffffffu, m[f], o));
+        if ((threadIdx.x & 31) == 0) s_w[f][threadIdx.x >> 5] = m[f];
+    }
+    __syncthreads();
+    if (threadIdx.x < FPD_FIELDS) {
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v = fmaxf(v, s_w[threadIdx.x][w]);
+        part[threadIdx.x * FPD_PARTS + blockIdx.x] = v * (1.f + 0x1p-20f);
+    }
+}
+
+// scale exponent of a field: q = round(v 2^S) with n^3 max|q| < 2^62 (row sums of k^2 q)
+__device__ __forceinline__ int fpd_shift(float m, int L)
+{
+    if (!(m > 0.f)) return 62 - 3 * L - 1;
+    int e1;
+    frexpf(m, &e1);                      // m < 2^e1
+    return 62 - 3 * L - 1 - e1;
+}
+
+struct FpdScanArgs {
+    int n, L, nparts;
+    const float *ux, *uy, *c, *part;
+    int *shifts;                         // [4], written by block 0
+    long long *P;                        // [FPD_ARRAYS][N]
+    int64_t N;
+};
+
+__device__ __forceinline__ long long warp_scan_ll(long long v, int lane)
+{
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// one warp per row: the ten prefix arrays of the row (quantise, multiply by k and k^2, scan)
+__global__ void __launch_bounds__(128) k_fpd_scan(FpdScanArgs a)
+{
+    __shared__ int s_sh[FPD_FIELDS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        for (int f = 0; f < FPD_FIELDS; ++f) {
+            float m = 0.f;
+            for (int k = lane; k < a.nparts; k += 32) m = fmaxf(m, a.part[f * FPD_PARTS + k]);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) s_sh[f] = fpd_shift(m, a.L);
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x < FPD_FIELDS) a.shifts[threadIdx.x] = s_sh[threadIdx.x];
+    const int n = a.n;
+    const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (row >= n) return;
+    const int64_t base = (int64_t)row * n;
+    long long carry[FPD_ARRAYS];
+#pragma unroll
+    for (int t = 0; t < FPD_ARRAYS; ++t) carry[t] = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        long long v[FPD_ARRAYS];
+        if (k < n) {
+            const float x = a.ux[base + k], y = a.uy[base + k], cc = a.c[base + k];
+            const long long qx = __float2ll_rn(ldexpf(x, s_sh[0]));
+            const long long qy = __float2ll_rn(ldexpf(y, s_sh[1]));
+            const long long qcx = __float2ll_rn(ldexpf(cc * x, s_sh[2]));
+            const long long qcy = __float2ll_rn(ldexpf(cc * y, s_sh[3]));
+            const long long kk = k;
+            v[0] = qx;  v[1] = kk * qx;  v[2] = kk * kk * qx;
+            v[3] = qy;  v[4] = kk * qy;
+            v[5] = qcx; v[6] = kk * qcx; v[7] = kk * kk * qcx;
+            v[8] = qcy; v[9] = kk * qcy;
+        } else {
+#pragma unroll
+            for (int t = 0; t < FPD_ARRAYS; ++t) v[t] = 0;
+        }
+#pragma unroll
+        for (int t = 0; t < FPD_ARRAYS; ++t) {
+            v[t] = warp_scan_ll(v[t], lane) + carry[t];
+            if (k < n) a.P[(int64_t)t * a.N + base + k] = v[t];
+            carry[t] = __shfl_sync(0xffffffffu, v[t], 31);
+        }
+    }
+}
+
+struct FpdGatherArgs {
+    int n;
+    int64_t N;
+    const int *thr4;
+    const double *c;                     // c_i for the factor c_i A (FP64)
+    const double *F, *M;
+    const long long *P;                  // [FPD_ARRAYS][N]
+    const int *shifts;
+};
+
+__device__ __forceinline__ long long pdiff(const long long *P, int64_t row, int ka, int kb)
+{
+    return __ldg(P + row + kb) - (ka > 0 ? __ldg(P + row + ka - 1) : 0LL);
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 v)
+{
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    return ldexp((double)hi, 64) + (double)lo;
+}
+
+__global__ void __launch_bounds__(256) k_fpd_gather(FpdGatherArgs a, const float *__restrict__ ux,
+                                                    const float *__restrict__ uy,
+                                                    float *__restrict__ outx,
+                                                    float *__restrict__ outy)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int ix = (int)(i % n), iy = (int)(i / n);
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    const int64_t N = a.N;
+    // A = (Axx + Axy, Ayx + Ayy), B likewise: xx = sum o_x^2 f_x, xy = sum o_x o_y f_y,
+    // yx = sum o_x o_y f_x, yy = sum o_y^2 f_y
+    __int128 Axx = 0, Axy = 0, Ayx = 0, Ayy = 0, Bxx = 0, Bxy = 0, Byx = 0, Byy = 0;
+    const __int128 kx = ix;
+    for (int t = 0;; ++t) {
+        const int e = t == 0 ? 0 : sqi(2 * t - 1);
+        if (e > T4) break;
+        const int r = isqrt_pd(T4 - e);
+        const int ka = max(0, -((r - X) >> 1) - 1);
+        const int kb = min(n - 1, (X + r) >> 1);
+        for (int s = 0; s < (t > 0 ? 2 : 1); ++s) {
+            const int ky = s ? iy - t : iy + t;
+            if (ky < 0 || ky >= n) continue;
+            const int dy = ky - iy;
+            const int64_t row = (int64_t)ky * n;
+            // u_x: P0 P1 P2 -> sum q, sum o_x q, sum o_x^2 q
+            {
+                const __int128 p0 = pdiff(a.P, row, ka, kb), p1 = pdiff(a.P + N, row, ka, kb),
+                               p2 = pdiff(a.P + 2 * N, row, ka, kb);
+                const __int128 s1 = p1 - kx * p0;
+                Axx += p2 - 2 * kx * p1 + kx * kx * p0;
+                Ayx += s1 * dy;
+            }
+            {
+                const __int128 p0 = pdiff(a.P + 3 * N, row, ka, kb), p1 = pdiff(a.P + 4 * N, row, ka, kb);
+                const __int128 s1 = p1 - kx * p0;
+                Axy += s1 * dy;
+                Ayy += p0 * (dy * dy);
+            }
+            {
+                const __int128 p0 = pdiff(a.P + 5 * N, row, ka, kb), p1 = pdiff(a.P + 6 * N, row, ka, kb),
+                               p2 = pdiff(a.P + 7 * N, row, ka, kb);
+                const __int128 s1 = p1 - kx * p0;
+                Bxx += p2 - 2 * kx * p1 + kx * kx * p0;
+                Byx += s1 * dy;
+            }
+            {
+                const __int128 p0 = pdiff(a.P + 8 * N, row, ka, kb), p1 = pdiff(a.P + 9 * N, row, ka, kb);
+                const __int128 s1 = p1 - kx * p0;
+                Bxy += s1 * dy;
+                Byy += p0 * (dy * dy);
+            }
+        }
+    }
+    const int s0 = a.shifts[0], s1 = a.shifts[1], s2 = a.shifts[2], s3 = a.shifts[3];
+    const double Ax = ldexp(i128_to_double(Axx), -s0) + ldexp(i128_to_double(Axy), -s1);
+    const double Ay = ldexp(i128_to_double(Ayx), -s0) + ldexp(i128_to_double(Ayy), -s1);
+    const double Bx = ldexp(i128_to_double(Bxx), -s2) + ldexp(i128_to_double(Bxy), -s3);
+    const double By = ldexp(i128_to_double(Byx), -s2) + ldexp(i128_to_double(Byy), -s3);
+    const double ci = a.c[i];
+    const double uxi = (double)ux[i], uyi = (double)uy[i];
+    const double *Mi = a.M + 3 * i;
+    const double Fi = a.F[i];
+    outx[i] = (float)(Fi * (ci * Ax + Bx - (Mi[0] * uxi + Mi[1] * uyi)));
+    outy[i] = (float)(Fi * (ci * Ay + By - (Mi[1] * uxi + Mi[2] * uyi)));
+}
+
+}  // namespace
+
+// plan-time set-up (2-D NL_PD_BOND plans with n = 2^L <= 8192)
+nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double *c_dev,
+                               cudaStream_t st)
+{
+    if (p->d != 2 || p->L < 0 || p->n > 8192 || !p->thr4) return NL_OK;
+    const int64_t N = p->N;
+    auto alloc = [&](void **ptr, size_t bytes) -> nl_status {
+        if (cudaMalloc(ptr, bytes ? bytes : 1) != cudaSuccess) {
+            nl_set_error("cudaMalloc(%zu) for the fast peridynamic path failed", bytes);
+            return NL_ENOMEM;
+        }
+        p->device_bytes += bytes;
+        return NL_OK;
+    };
+    nl_status s;
+    if ((s = alloc((void **)&p->fpd_F, N * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->fpd_M, 3 * N * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->fpd_P, (size_t)FPD_ARRAYS * N * sizeof(long long))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->fpd_aux, FPD_FIELDS * FPD_PARTS * sizeof(float) + 64)) != NL_OK) return s;
+    k_fpd_node<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(p->n, N, p->sigma, p->h, delta_dev,
+                                                           c_dev, p->thr4, p->fpd_F, p->fpd_M);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+// one FP32 right-hand side: bounds, the ten prefix arrays, the gather
+nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cudaStream_t st)
+{
+    if (!p->fpd_P) {
+        nl_set_error("nl_apply_fast: the fast peridynamic path needs a 2-D plan with n = 2^L "
+                     "<= 8192");
+        return NL_EUNSUPPORTED;
+    }
+    const int64_t N = p->N;
+    float *part = (float *)p->fpd_aux;
+    int *shifts = (int *)((unsigned char *)p->fpd_aux + FPD_FIELDS * FPD_PARTS * sizeof(float));
+    int64_t per = (N + FPD_PARTS - 1) / FPD_PARTS;
+    if (per < 2048) per = 2048;
+    const int nparts = (int)((N + per - 1) / per);
+    for (int r = 0; r < nrhs; ++r) {
+        const float *ux = u + (int64_t)r * 2 * N, *uy = ux + N;
+        float *ox = Lu + (int64_t)r * 2 * N, *oy = ox + N;
+        k_fpd_absmax<<<nparts, 256, 0, st>>>(N, ux, uy, p->b32, part);
+        FpdScanArgs sa;
+        sa.n = p->n; sa.L = p->L; sa.nparts = nparts;
+        sa.ux = ux; sa.uy = uy; sa.c = p->b32; sa.part = part; sa.shifts = shifts;
+        sa.P = p->fpd_P; sa.N = N;
+        k_fpd_scan<<<(unsigned)((p->n + 3) / 4), 128, 0, st>>>(sa);
+        FpdGatherArgs ga;
+        ga.n = p->n; ga.N = N; ga.thr4 = p->thr4; ga.c = p->b64;
+        ga.F = p->fpd_F; ga.M = p->fpd_M; ga.P = p->fpd_P; ga.shifts = shifts;
+        k_fpd_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(ga, ux, uy, ox, oy);
+        NL_CUDA_TRY(cudaGetLastError());
+    }
+    return NL_OK;
+}

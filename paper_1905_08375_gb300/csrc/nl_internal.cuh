@@ -90,6 +90,9 @@ struct nl_plan {
     float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
     float *pd_dense32;              // PD, 2-D, constant horizon: [2R+1][2R+1][3] bond tensors
     float *g3d32;                   // 3-D POWER, constant horizon: [2R+1]^3 weights (oy, ox, oz)
+    double *fpd_F, *fpd_M;          // fast-path PD: F_i and M_i (3 per node)
+    long long *fpd_P;               // fast-path PD: ten leaf-row prefix arrays [10][N]
+    void *fpd_aux;                  // fast-path PD: per-block bounds and the four scale exponents
     int *thr_reach;                 // symmetric variant: max threshold over the window
     int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
     int x2_tiles, x2_blocks, x2_var;// work-queue counter + exit ticket; persistent grid size;
@@ -158,6 +161,9 @@ nl_status nl_pd_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
 nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                          cudaStream_t st);
 nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st);
+nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double *c_dev,
+                               cudaStream_t st);
+nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cudaStream_t st);
 nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
                             cudaStream_t st);
 nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st);

@@ -604,8 +604,9 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     const int TB = 256;
     const unsigned GB = (unsigned)((N + TB - 1) / TB);
     const bool want_fast = (k->family == NL_POLY && p->L >= 0 && !p->symmetric);
-    if (want_fast) NL_TMP_TRY(dev_alloc(p, &p->thr4, N));
-    k_thresholds<<<GB, TB, 0, st>>>(pa, d_delta, p->thr, want_fast ? p->thr4 : nullptr);
+    const bool want_fast_pd = (k->family == NL_PD_BOND && d == 2 && p->L >= 0 && n <= 8192);
+    if (want_fast || want_fast_pd) NL_TMP_TRY(dev_alloc(p, &p->thr4, N));
+    k_thresholds<<<GB, TB, 0, st>>>(pa, d_delta, p->thr, p->thr4);
     if (p->symmetric) {
         NL_TMP_TRY(dev_alloc(p, &p->thr_reach, N));
         d_win = p->thr_reach;
@@ -619,6 +620,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan kernels"));
     if (want_fast) NL_TMP_TRY(nl_fast_plan_init(p, d_delta, d_a, st));
+    if (want_fast_pd) NL_TMP_TRY(nl_fast_pd_plan_init(p, d_delta, d_a, st));
     NL_TMP_TRY(nl_direct_plan_init(p, st));
     ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan synchronise"));
@@ -642,7 +644,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
                      p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx,
                      p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32, p->leaf_multi,
-                     p->aux_multi };
+                     p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)
