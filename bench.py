@@ -361,6 +361,10 @@ class C3(Workload):
         self.u = torch.tensor(f["u"], dtype=torch.float32, device=self.dev)
         self.out = torch.empty_like(self.u)
         self.out_f = torch.empty_like(self.u)
+        # the same fields with a four times larger horizon (32h): the fast path's cost grows
+        # like the horizon, the direct sum's like its square
+        self.plan32 = nl.nl_plan_create(2, 512, 4.0 * f["delta"], family=nl.NL_PD_BOND,
+                                        coef=nl.NL_COEF_MEAN, a=f["c"])
         self.units = 512 * 512
         self.launches = 1
         self.config = {"workload": "2D linear bond-based PD, 512x512, delta=8h, micromodulus "
@@ -374,11 +378,16 @@ class C3(Workload):
         t = self.time_fn(self.step, reps, flush)
         t_f = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan, self.u, self.out_f), reps,
                            flush)
+        o32 = self.torch.empty_like(self.u)
+        t_d32 = self.time_fn(lambda: self.nl.nl_apply(self.plan32, self.u, o32), reps, flush)
+        t_f32 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan32, self.u, o32), reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, FP32_PEAK_TFLOPS,
                          FP32_SRC)
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
         return roof, {"pd_fp32_ms": round(t, 4), "pd_fast_deg0_fp32_ms": round(t_f, 4),
+                      "pd_delta32h_direct_fp32_ms": round(t_d32, 4),
+                      "pd_delta32h_fast_deg0_fp32_ms": round(t_f32, 4),
                       "pd_fast_note": "nl_apply_fast on the PD plan: degree-0 bond tensor "
                                       "xi xi^T / delta^3 over the leaf set (a different "
                                       "operator), exact 64-bit leaf-row moment sums"}
@@ -601,21 +610,21 @@ class C5(Workload):
     def setup(self):
         nl, torch = self.nl, self.torch
         from paper_1905_08375_gb300 import synth
-        self.n = 256
-        self.f = synth.diffusion_3d(n=256, seed=self.seed, nrhs=8, radius_cells=4)
+        n = self.n = getattr(self, "size", None) or 256
+        self.f = synth.diffusion_3d(n=n, seed=self.seed, nrhs=8, radius_cells=4)
         f = self.f
-        self.direct = nl.nl_plan_create(3, 256, f["delta"], family=nl.NL_POWER, alpha=1.0,
+        self.direct = nl.nl_plan_create(3, n, f["delta"], family=nl.NL_POWER, alpha=1.0,
                                         coef=nl.NL_COEF_XY, a=f["a"])
-        self.fast = nl.nl_plan_create(3, 256, f["delta"], family=nl.NL_POLY, alpha=1.0, K=0,
+        self.fast = nl.nl_plan_create(3, n, f["delta"], family=nl.NL_POLY, alpha=1.0, K=0,
                                       coef=nl.NL_COEF_XY, a=f["a"])
         self.u = torch.tensor(f["u"], dtype=torch.float32, device=self.dev)
         self.out_d = torch.empty_like(self.u)
         self.out_f = torch.empty_like(self.u)
-        self.units = 2 * 8 * 256 ** 3
+        self.units = 2 * 8 * n ** 3
         self.launches = 1 + 8 * 3
-        self.config = {"workload": "3D nonlocal diffusion 256^3, delta=4h, a lognormal sigma "
+        self.config = {"workload": f"3D nonlocal diffusion {n}^3, delta=4h, a lognormal sigma "
                                    "0.3, gamma=a(x)a(y)C_delta/|xi|, 8 RHS; direct + fast (K=0) "
-                                   "FP32 applies per step", "n": 256, "rhs": 8}
+                                   "FP32 applies per step", "n": n, "rhs": 8}
 
     def step(self):
         self.nl.nl_apply(self.direct, self.u, self.out_d)
@@ -625,7 +634,8 @@ class C5(Workload):
         nl = self.nl
         t_d = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
         t_f = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u, self.out_f), reps, flush)
-        nb = 8.0 * float(ball_counts(np.full(1, 4.0 / 256), 256, 3)[0]) * 256 ** 3
+        n = self.n
+        nb = 8.0 * float(ball_counts(np.full(1, 4.0 / n), n, 3)[0]) * n ** 3
         roof = _alu_roof("k_direct3d_x2<4,4> (slab sweep)", 4.0 * nb, t_d,
                          FP32_PEAK_TFLOPS, FP32_SRC)
         roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term, 8 RHS)"
@@ -791,13 +801,14 @@ def oracle_sample(w, outs, budget_s=20.0):
                            f"{dt * 1e3:.0f} ms), scaled by total points / 128^2 = {scale:.1f} "
                            "(a lower bound: larger instances need more iterations)"}, par)
     if name == "c5":
-        n, N = 256, 256 ** 3
+        n = w.n
+        N = n ** 3
         f = w.f
         t0 = time.perf_counter()
         idx = rng.choice(N, size=2000, replace=False)
         ref_d = oracle.direct_scalar(f["u"], 3, n, f["delta"], alpha=1.0, coef=oracle.COEF_XY,
                                      a=f["a"], idx=idx)
-        ref_f = oracle.fast_leafset(f["u"], 3, 8, f["delta"], K=0, alpha=1.0,
+        ref_f = oracle.fast_leafset(f["u"], 3, int(np.log2(n)), f["delta"], K=0, alpha=1.0,
                                     coef=oracle.COEF_XY, a=f["a"], idx=idx)
         dt = time.perf_counter() - t0
         pts = 2 * 8 * len(idx)
@@ -864,6 +875,8 @@ def run_gpu(args, peaks):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     w = make_workload(args.workload, dev, args.seed + rank)
+    if args.size:
+        w.size = args.size
     w.peaks = peaks
     w.setup()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -960,6 +973,8 @@ def main():
     ap.add_argument("--workload", default="c2",
                     choices=["c1", "c2", "c3", "c3b", "c4", "c4_512", "c5", "ex1", "ex2"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--size", type=int, default=0,
+                    help="grid size override for c5 (a smaller case for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -9,9 +9,13 @@
 //   M_i = sum_{k in LS(i)} (c_i + c_k) o o^T      (plan-time constant, FP64).
 // A and B are exact integer sums: each of u_x, u_y, c u_x, c u_y is rounded once to a
 // multiple of 2^-S (S per field and apply, from its max |.|), and along every leaf row the
-// prefix sums of q, k q and k^2 q (k the column) give, for the run of a row, the sums of
-// o_x^2 q, o_x q and q by differences.  Rows and runs are those of the scalar leaf-row gather
-// (the same half-unit geometry).  2-D, FP32 data.
+// prefix sums of q, k q and k^2 q (k the column) give, for the run of a row, the sums of q,
+// k q and k^2 q by differences.  The prefix sums wrap modulo 2^64 (only differences over
+// runs of at most 2R + 3 cells are used, and those fit); S is chosen so that, with C the
+// bound (2R + 3)^2 on a leaf set's cells, n^2 C max|q| < 2^61: every per-node sum of
+// differences (over rows, times dy or dy^2) and the final combination with the node's column
+// (o_x = k - kx) then fit in 64-bit integers.  Rows and runs are those of the scalar leaf-row
+// gather (the same half-unit geometry).  2-D, FP32 data.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -100,33 +104,26 @@ __global__ void __launch_bounds__(256) k_fpd_absmax(int64_t N, const float *__re
     }
 }
 
-// scale exponent of a field: q = round(v 2^S) with n^3 max|q| < 2^62 (row sums of k^2 q)
-__device__ __forceinline__ int fpd_shift(float m, int L)
+// scale exponent of a field: q = round(v 2^S) with 2^bits max|q| <= 2^61, where
+// 2^bits >= n^2 (2R + 3)^2 (see the header)
+__device__ __forceinline__ int fpd_shift(float m, int bits)
 {
-    if (!(m > 0.f)) return 62 - 3 * L - 1;
+    if (!(m > 0.f)) return 61 - bits;
     int e1;
     frexpf(m, &e1);                      // m < 2^e1
-    return 62 - 3 * L - 1 - e1;
+    return 61 - bits - e1;
 }
 
 struct FpdScanArgs {
-    int n, L, nparts;
+    int n, bits, nparts;
     const float *ux, *uy, *c, *part;
     int *shifts;                         // [4], written by block 0
     long long *P;                        // [FPD_ARRAYS][N]
     int64_t N;
 };
 
-__device__ __forceinline__ long long warp_scan_ll(long long v, int lane)
-{
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
-}
-
-// one warp per row: the ten prefix arrays of the row (quantise, multiply by k and k^2, scan)
+// one warp per row: the ten prefix arrays of the row (quantise, multiply by k and k^2, scan
+// with wrapping 64-bit sums); the ten scans advance together, one shuffle each per step
 __global__ void __launch_bounds__(128) k_fpd_scan(FpdScanArgs a)
 {
     __shared__ int s_sh[FPD_FIELDS];
@@ -136,7 +133,7 @@ __global__ void __launch_bounds__(128) k_fpd_scan(FpdScanArgs a)
             float m = 0.f;
             for (int k = lane; k < a.nparts; k += 32) m = fmaxf(m, a.part[f * FPD_PARTS + k]);
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) s_sh[f] = fpd_shift(m, a.L);
+            if (lane == 0) s_sh[f] = fpd_shift(m, a.bits);
         }
     }
     __syncthreads();
@@ -145,12 +142,12 @@ __global__ void __launch_bounds__(128) k_fpd_scan(FpdScanArgs a)
     const int row = blockIdx.x * (blockDim.x >> 5) + warp;
     if (row >= n) return;
     const int64_t base = (int64_t)row * n;
-    long long carry[FPD_ARRAYS];
+    unsigned long long carry[FPD_ARRAYS];
 #pragma unroll
-    for (int t = 0; t < FPD_ARRAYS; ++t) carry[t] = 0;
+    for (int t = 0; t < FPD_ARRAYS; ++t) carry[t] = 0ull;
     for (int k0 = 0; k0 < n; k0 += 32) {
         const int k = k0 + lane;
-        long long v[FPD_ARRAYS];
+        unsigned long long v[FPD_ARRAYS];
         if (k < n) {
             const float x = a.ux[base + k], y = a.uy[base + k], cc = a.c[base + k];
             const long long qx = __float2ll_rn(ldexpf(x, s_sh[0]));
@@ -158,18 +155,30 @@ __global__ void __launch_bounds__(128) k_fpd_scan(FpdScanArgs a)
             const long long qcx = __float2ll_rn(ldexpf(cc * x, s_sh[2]));
             const long long qcy = __float2ll_rn(ldexpf(cc * y, s_sh[3]));
             const long long kk = k;
-            v[0] = qx;  v[1] = kk * qx;  v[2] = kk * kk * qx;
-            v[3] = qy;  v[4] = kk * qy;
-            v[5] = qcx; v[6] = kk * qcx; v[7] = kk * kk * qcx;
-            v[8] = qcy; v[9] = kk * qcy;
+            v[0] = (unsigned long long)qx;  v[1] = (unsigned long long)(kk * qx);
+            v[2] = (unsigned long long)(kk * kk * qx);
+            v[3] = (unsigned long long)qy;  v[4] = (unsigned long long)(kk * qy);
+            v[5] = (unsigned long long)qcx; v[6] = (unsigned long long)(kk * qcx);
+            v[7] = (unsigned long long)(kk * kk * qcx);
+            v[8] = (unsigned long long)qcy; v[9] = (unsigned long long)(kk * qcy);
         } else {
 #pragma unroll
-            for (int t = 0; t < FPD_ARRAYS; ++t) v[t] = 0;
+            for (int t = 0; t < FPD_ARRAYS; ++t) v[t] = 0ull;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long w[FPD_ARRAYS];
+#pragma unroll
+            for (int t = 0; t < FPD_ARRAYS; ++t) w[t] = __shfl_up_sync(0xffffffffu, v[t], o);
+            if (lane >= o) {
+#pragma unroll
+                for (int t = 0; t < FPD_ARRAYS; ++t) v[t] += w[t];
+            }
         }
 #pragma unroll
         for (int t = 0; t < FPD_ARRAYS; ++t) {
-            v[t] = warp_scan_ll(v[t], lane) + carry[t];
-            if (k < n) a.P[(int64_t)t * a.N + base + k] = v[t];
+            v[t] += carry[t];
+            if (k < n) a.P[(int64_t)t * a.N + base + k] = (long long)v[t];
             carry[t] = __shfl_sync(0xffffffffu, v[t], 31);
         }
     }
@@ -185,16 +194,12 @@ struct FpdGatherArgs {
     const int *shifts;
 };
 
-__device__ __forceinline__ long long pdiff(const long long *P, int64_t row, int ka, int kb)
+__device__ __forceinline__ unsigned long long pdiff(const long long *P, int64_t row, int ka,
+                                                    int kb)
 {
-    return __ldg(P + row + kb) - (ka > 0 ? __ldg(P + row + ka - 1) : 0LL);
-}
-
-__device__ __forceinline__ double i128_to_double(__int128 v)
-{
-    const long long hi = (long long)(v >> 64);
-    const unsigned long long lo = (unsigned long long)v;
-    return ldexp((double)hi, 64) + (double)lo;
+    const unsigned long long hi = (unsigned long long)__ldg(P + row + kb);
+    const unsigned long long lo = ka > 0 ? (unsigned long long)__ldg(P + row + ka - 1) : 0ull;
+    return hi - lo;                              // the run's sum, modulo 2^64
 }
 
 __global__ void __launch_bounds__(256) k_fpd_gather(FpdGatherArgs a, const float *__restrict__ ux,
@@ -209,10 +214,13 @@ __global__ void __launch_bounds__(256) k_fpd_gather(FpdGatherArgs a, const float
     const int X = 2 * ix + 1;
     const int T4 = a.thr4[i];
     const int64_t N = a.N;
-    // A = (Axx + Axy, Ayx + Ayy), B likewise: xx = sum o_x^2 f_x, xy = sum o_x o_y f_y,
-    // yx = sum o_x o_y f_x, yy = sum o_y^2 f_y
-    __int128 Axx = 0, Axy = 0, Ayx = 0, Ayy = 0, Bxx = 0, Bxy = 0, Byx = 0, Byy = 0;
-    const __int128 kx = ix;
+    // per group g (0: u, 1: c u) sums over the rows of the run differences of the x-type
+    // field (P0 P1 P2): S0, S1, S2, T0 = sum dy P0, T1 = sum dy P1; of the y-type field
+    // (P0 P1): U0 = sum dy P0, U1 = sum dy P1, V0 = sum dy^2 P0.  All wrap modulo 2^64: the
+    // combinations below are small (sums of o^2 q over one leaf set) and come out exact.
+    typedef unsigned long long u64;
+    u64 S0[2] = { 0, 0 }, S1[2] = { 0, 0 }, S2[2] = { 0, 0 }, T0[2] = { 0, 0 };
+    u64 T1[2] = { 0, 0 }, U0[2] = { 0, 0 }, U1[2] = { 0, 0 }, V0[2] = { 0, 0 };
     for (int t = 0;; ++t) {
         const int e = t == 0 ? 0 : sqi(2 * t - 1);
         if (e > T4) break;
@@ -220,50 +228,42 @@ __global__ void __launch_bounds__(256) k_fpd_gather(FpdGatherArgs a, const float
         const int ka = max(0, -((r - X) >> 1) - 1);
         const int kb = min(n - 1, (X + r) >> 1);
         for (int s = 0; s < (t > 0 ? 2 : 1); ++s) {
-            const int ky = s ? iy - t : iy + t;
+            const int dy = s ? -t : t;
+            const int ky = iy + dy;
             if (ky < 0 || ky >= n) continue;
-            const int dy = ky - iy;
             const int64_t row = (int64_t)ky * n;
-            // u_x: P0 P1 P2 -> sum q, sum o_x q, sum o_x^2 q
-            {
-                const __int128 p0 = pdiff(a.P, row, ka, kb), p1 = pdiff(a.P + N, row, ka, kb),
-                               p2 = pdiff(a.P + 2 * N, row, ka, kb);
-                const __int128 s1 = p1 - kx * p0;
-                Axx += p2 - 2 * kx * p1 + kx * kx * p0;
-                Ayx += s1 * dy;
-            }
-            {
-                const __int128 p0 = pdiff(a.P + 3 * N, row, ka, kb), p1 = pdiff(a.P + 4 * N, row, ka, kb);
-                const __int128 s1 = p1 - kx * p0;
-                Axy += s1 * dy;
-                Ayy += p0 * (dy * dy);
-            }
-            {
-                const __int128 p0 = pdiff(a.P + 5 * N, row, ka, kb), p1 = pdiff(a.P + 6 * N, row, ka, kb),
-                               p2 = pdiff(a.P + 7 * N, row, ka, kb);
-                const __int128 s1 = p1 - kx * p0;
-                Bxx += p2 - 2 * kx * p1 + kx * kx * p0;
-                Byx += s1 * dy;
-            }
-            {
-                const __int128 p0 = pdiff(a.P + 8 * N, row, ka, kb), p1 = pdiff(a.P + 9 * N, row, ka, kb);
-                const __int128 s1 = p1 - kx * p0;
-                Bxy += s1 * dy;
-                Byy += p0 * (dy * dy);
+            const u64 udy = (u64)(long long)dy, udy2 = (u64)(long long)(dy * dy);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const long long *Px = a.P + (int64_t)(5 * g) * N;
+                const long long *Py = Px + 3 * N;
+                const u64 p0 = pdiff(Px, row, ka, kb), p1 = pdiff(Px + N, row, ka, kb),
+                          p2 = pdiff(Px + 2 * N, row, ka, kb);
+                S0[g] += p0; S1[g] += p1; S2[g] += p2;
+                T0[g] += udy * p0; T1[g] += udy * p1;
+                const u64 q0 = pdiff(Py, row, ka, kb), q1 = pdiff(Py + N, row, ka, kb);
+                U0[g] += udy * q0; U1[g] += udy * q1; V0[g] += udy2 * q0;
             }
         }
     }
-    const int s0 = a.shifts[0], s1 = a.shifts[1], s2 = a.shifts[2], s3 = a.shifts[3];
-    const double Ax = ldexp(i128_to_double(Axx), -s0) + ldexp(i128_to_double(Axy), -s1);
-    const double Ay = ldexp(i128_to_double(Ayx), -s0) + ldexp(i128_to_double(Ayy), -s1);
-    const double Bx = ldexp(i128_to_double(Bxx), -s2) + ldexp(i128_to_double(Bxy), -s3);
-    const double By = ldexp(i128_to_double(Byx), -s2) + ldexp(i128_to_double(Byy), -s3);
+    const u64 kx = (u64)ix;
+    double A[2][2];                              // [g][component]
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const int sx = a.shifts[2 * g], sy = a.shifts[2 * g + 1];
+        const long long xx = (long long)(S2[g] - 2 * kx * S1[g] + kx * kx * S0[g]);  // o_x^2 f_x
+        const long long yx = (long long)(T1[g] - kx * T0[g]);                         // o_x o_y f_x
+        const long long xy = (long long)(U1[g] - kx * U0[g]);                         // o_x o_y f_y
+        const long long yy = (long long)V0[g];                                        // o_y^2 f_y
+        A[g][0] = ldexp((double)xx, -sx) + ldexp((double)xy, -sy);
+        A[g][1] = ldexp((double)yx, -sx) + ldexp((double)yy, -sy);
+    }
     const double ci = a.c[i];
     const double uxi = (double)ux[i], uyi = (double)uy[i];
     const double *Mi = a.M + 3 * i;
     const double Fi = a.F[i];
-    outx[i] = (float)(Fi * (ci * Ax + Bx - (Mi[0] * uxi + Mi[1] * uyi)));
-    outy[i] = (float)(Fi * (ci * Ay + By - (Mi[1] * uxi + Mi[2] * uyi)));
+    outx[i] = (float)(Fi * (ci * A[0][0] + A[1][0] - (Mi[0] * uxi + Mi[1] * uyi)));
+    outy[i] = (float)(Fi * (ci * A[0][1] + A[1][1] - (Mi[1] * uxi + Mi[2] * uyi)));
 }
 
 }  // namespace
@@ -273,6 +273,8 @@ nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double
                                cudaStream_t st)
 {
     if (p->d != 2 || p->L < 0 || p->n > 8192 || !p->thr4) return NL_OK;
+    // the sums' range (n^2 (2R + 3)^2) leaves at least 2^13 levels for max|v|
+    if ((double)p->n * p->n * (2.0 * p->Rmax + 3) * (2.0 * p->Rmax + 3) > 0x1p48) return NL_OK;
     const int64_t N = p->N;
     auto alloc = [&](void **ptr, size_t bytes) -> nl_status {
         if (cudaMalloc(ptr, bytes ? bytes : 1) != cudaSuccess) {
@@ -287,6 +289,9 @@ nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double
     if ((s = alloc((void **)&p->fpd_M, 3 * N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->fpd_P, (size_t)FPD_ARRAYS * N * sizeof(long long))) != NL_OK) return s;
     if ((s = alloc((void **)&p->fpd_aux, FPD_FIELDS * FPD_PARTS * sizeof(float) + 64)) != NL_OK) return s;
+    // 2^bits >= n^2 (2 Rmax + 3)^2 bounds every per-node sum (see the header)
+    const double bound = (double)p->n * p->n * (2.0 * p->Rmax + 3) * (2.0 * p->Rmax + 3);
+    p->fpd_bits = (int)std::ceil(std::log2(bound));
     k_fpd_node<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(p->n, N, p->sigma, p->h, delta_dev,
                                                            c_dev, p->thr4, p->fpd_F, p->fpd_M);
     NL_CUDA_TRY(cudaGetLastError());
@@ -312,7 +317,7 @@ nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cud
         float *ox = Lu + (int64_t)r * 2 * N, *oy = ox + N;
         k_fpd_absmax<<<nparts, 256, 0, st>>>(N, ux, uy, p->b32, part);
         FpdScanArgs sa;
-        sa.n = p->n; sa.L = p->L; sa.nparts = nparts;
+        sa.n = p->n; sa.bits = p->fpd_bits; sa.nparts = nparts;
         sa.ux = ux; sa.uy = uy; sa.c = p->b32; sa.part = part; sa.shifts = shifts;
         sa.P = p->fpd_P; sa.N = N;
         k_fpd_scan<<<(unsigned)((p->n + 3) / 4), 128, 0, st>>>(sa);

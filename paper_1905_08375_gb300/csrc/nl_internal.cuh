@@ -93,6 +93,7 @@ struct nl_plan {
     double *fpd_F, *fpd_M;          // fast-path PD: F_i and M_i (3 per node)
     long long *fpd_P;               // fast-path PD: ten leaf-row prefix arrays [10][N]
     void *fpd_aux;                  // fast-path PD: per-block bounds and the four scale exponents
+    int fpd_bits;                   // fast-path PD: 2^bits >= n^2 (2 Rmax + 3)^2
     int *thr_reach;                 // symmetric variant: max threshold over the window
     int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
     int x2_tiles, x2_blocks, x2_var;// work-queue counter + exit ticket; persistent grid size;
