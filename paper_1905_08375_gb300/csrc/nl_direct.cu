@@ -816,8 +816,8 @@ static nl_status x2_order_for(nl_plan *p, int ty, int **order_dev, int *ntiles, 
 // thr - oy^2.  A block of TZ warps covers 64 x 1 x (TZ RB_P) outputs (x, y, z) and stages one
 // x-z slab of u and b at a time in shared memory.
 // ---------------------------------------------------------------------------
-template <int RM, int TZ>
-__global__ void __launch_bounds__(32 * TZ)
+template <int RM, int TZ, int MB>
+__global__ void __launch_bounds__(32 * TZ, MB)
 k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restrict__ u,
               float *__restrict__ Lu, int ztiles)
 {
@@ -895,13 +895,16 @@ k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restric
     (void)tid;
 }
 
-template <int RM>
-static nl_status launch_3d_x2_rm(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
-                                 int nrhs, cudaStream_t st)
+// variants (warps per block along z, minimum resident blocks for the register budget),
+// timed at plan creation
+constexpr int X3_VARIANTS = 4;
+
+template <int RM, int TZ, int MB>
+static nl_status launch_3d_x2_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                                int nrhs, cudaStream_t st)
 {
-    constexpr int TZ = 4;
     const size_t smem = sizeof(float) * 2 * (size_t)(64 + 2 * RM) * (TZ * RB_P + 2 * RM + 1);
-    auto kern = k_direct3d_x2<RM, TZ>;
+    auto kern = k_direct3d_x2<RM, TZ, MB>;
     NL_CUDA_TRY(prep_smem(kern, smem));
     const int ztiles = (p->n + TZ * RB_P - 1) / (TZ * RB_P);
     const int64_t gy = (int64_t)p->n * ztiles;
@@ -915,11 +918,24 @@ static nl_status launch_3d_x2_rm(nl_plan *p, const DirectArgs &a, const float *u
     return NL_OK;
 }
 
-static nl_status launch_3d_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
-                              int nrhs, cudaStream_t st)
+template <int RM>
+static nl_status launch_3d_x2_rm(nl_plan *p, int var, const DirectArgs &a, const float *u,
+                                 float *Lu, int nrhs, cudaStream_t st)
 {
-    if (p->Rmax <= 4) return launch_3d_x2_rm<4>(p, a, u, Lu, nrhs, st);
-    return launch_3d_x2_rm<8>(p, a, u, Lu, nrhs, st);
+    switch (var) {
+    case 0: return launch_3d_x2_t<RM, 4, 1>(p, a, u, Lu, nrhs, st);
+    case 1: return launch_3d_x2_t<RM, 4, 4>(p, a, u, Lu, nrhs, st);
+    case 2: return launch_3d_x2_t<RM, 8, 1>(p, a, u, Lu, nrhs, st);
+    default: return launch_3d_x2_t<RM, 8, 2>(p, a, u, Lu, nrhs, st);
+    }
+}
+
+static nl_status launch_3d_x2(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                              int nrhs, cudaStream_t st, int var = -1)
+{
+    if (var < 0) var = p->x3_var;
+    if (p->Rmax <= 4) return launch_3d_x2_rm<4>(p, var, a, u, Lu, nrhs, st);
+    return launch_3d_x2_rm<8>(p, var, a, u, Lu, nrhs, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1787,8 +1803,40 @@ nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, 
 // plan-time set-up of the paired-column FP32 kernel: the tile queue and its orders, and the
 // kernel variant (tile height and register budget) chosen by timing each on the plan itself
 // ---------------------------------------------------------------------------
+static nl_status x3_tune(nl_plan *p, cudaStream_t st)
+{
+    p->x3_var = 0;
+    if (!(p->d == 3 && p->g3d32 && p->Rmax <= 8) || p->N > ((int64_t)1 << 24)) return NL_OK;
+    const DirectArgs a = make_args(p, NL_F32);
+    float *u = nullptr, *lu = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    nl_status s = NL_OK;
+    if (cudaMalloc(&u, p->N * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&lu, p->N * sizeof(float)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(u, 0, p->N * sizeof(float), st) != cudaSuccess)
+        s = nl_cuda_fail(cudaErrorMemoryAllocation, "3-D kernel tuning");
+    float best = 1e30f;
+    for (int v = 0; v < X3_VARIANTS && s == NL_OK; ++v) {
+        if ((s = launch_3d_x2(p, a, u, lu, 1, st, v)) != NL_OK) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && s == NL_OK; ++r) s = launch_3d_x2(p, a, u, lu, 1, st, v);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; p->x3_var = v; }
+    }
+    if (u) cudaFree(u);
+    if (lu) cudaFree(lu);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return s;
+}
+
 nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
 {
+    if (p->d == 3) return x3_tune(p, st);
     if (!(p->d == 2 && p->rb2d && p->family == NL_POWER && !p->symmetric && p->Rmax <= 32))
         return NL_OK;
     NL_CUDA_TRY(cudaMalloc(&p->x2_queue, 2 * sizeof(int)));

@@ -90,6 +90,7 @@ struct nl_plan {
     float *rb_g32; double *rb_g64;  // [2R+1][2R+1] kernel weights |o|^{-alpha} (0 at o = 0)
     float *pd_dense32;              // PD, 2-D, constant horizon: [2R+1][2R+1][3] bond tensors
     float *g3d32;                   // 3-D POWER, constant horizon: [2R+1]^3 weights (oy, ox, oz)
+    int x3_var;                     // 3-D slab kernel variant (timed at plan creation)
     double *fpd_F, *fpd_M;          // fast-path PD: F_i and M_i (3 per node)
     long long *fpd_P;               // fast-path PD: ten leaf-row prefix arrays [10][N]
     void *fpd_aux;                  // fast-path PD: per-block bounds and the four scale exponents
