@@ -578,6 +578,7 @@ __global__ void __launch_bounds__(256) k_absmax_parts(int64_t N, const float *__
 struct Step2Args {
     int d, n, L, c, lf;              // band: 2^c leaf rows per axis = one panel row of level lf
     int leaf_only;                   // 1: the leaf rows only (leaf-row gather)
+    int wpr;                         // warps per leaf row (leaf rows only; n / 256 when > 1)
     int64_t N;
     const float *u, *b;
     const float *part;
@@ -613,9 +614,9 @@ __device__ __forceinline__ long long level_prefix_at(int d, int l, const long lo
 
 constexpr int STEP2_THREADS = 512;
 
-__global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
+__global__ void __launch_bounds__(1024) k_step2_rowprefix(Step2Args a)
 {
-    __shared__ float s_w[STEP2_THREADS / 32];
+    __shared__ float s_w[32];                    // one bound per warp (up to 1024 threads)
     const int nt = blockDim.x;                   // STEP2_THREADS, or 128 for the leaf rows only
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nt / 32;
     // scale exponent from the per-block bounds (same arithmetic as fixed_shift_f32)
@@ -641,8 +642,39 @@ __global__ void __launch_bounds__(STEP2_THREADS) k_step2_rowprefix(Step2Args a)
     const int bz = d > 2 ? (int)(blockIdx.x / bands_y) : 0;
     const int rows_y = d > 1 ? S : 1, rows_z = d > 2 ? S : 1;
     long long *leaf = a.leaf;
-    // (1) quantise and scan the band's leaf rows: the 32 loads of a page are issued first,
-    // then the page is scanned 32 nodes at a time
+    // (1) quantise and scan the band's leaf rows.  a.wpr > 1 (the leaf rows alone, n >= 512):
+    // a row is split among wpr warps of 256 nodes (eight 32-node pages each, kept in
+    // registers); each warp's total goes to shared memory and the later segments add the
+    // earlier ones' totals before storing.  Otherwise one warp per row, the 32 loads of a
+    // 1024-node page issued first, the page scanned 32 nodes at a time.
+    if (a.wpr > 1) {
+        __shared__ long long s_tot[32];
+        const int W = a.wpr, part = warp % W, r = warp / W;     // one row per W warps
+        const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
+        const int64_t row = (int64_t)n * (iy + (int64_t)n * iz) + 256 * part;
+        const float *__restrict__ ur = a.u + row;
+        const float *__restrict__ br = a.b + row;
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = ur[32 * k + lane] * br[32 * k + lane];
+        long long q[8], carry = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            long long t = __float2ll_rn(ldexpf(v[k], sh));
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long w = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += w;
+            }
+            q[k] = t + carry;
+            carry = __shfl_sync(0xffffffffu, q[k], 31);
+        }
+        if (lane == 0) s_tot[warp] = carry;
+        __syncthreads();
+        long long off = 0;
+        for (int w = warp - part; w < warp; ++w) off += s_tot[w];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) leaf[row + 32 * k + lane] = q[k] + off;
+    } else
     for (int r = warp; r < rows_y * rows_z; r += nw) {
         const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
         const int64_t row = (int64_t)n * (iy + (int64_t)n * iz);
@@ -1053,13 +1085,22 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
     int c = 0;
     if (d == 2) c = std::min(leaf_only ? 2 : 4, L);
     if (d == 3) c = std::min(leaf_only ? 1 : 3, L);
+    // the leaf rows alone of 2-D or 1-D grids with n >= 512: n / 256 warps per row, 16 / wpr
+    // rows (at least one) per block
+    int wpr = 1;
+    if (leaf_only && d <= 2 && p->n >= 512) {
+        wpr = p->n / 256;
+        const int rb = std::max(1, 16 / wpr);
+        c = 0;
+        while (d == 2 && (1 << (c + 1)) <= rb) ++c;
+    }
     int rows = 1;
     for (int q = 1; q < d; ++q) rows <<= c;
-    const int threads = leaf_only ? std::max(32, std::min(STEP2_THREADS, 32 * rows)) : STEP2_THREADS;
+    const int threads = leaf_only ? std::max(32, std::min(1024, 32 * rows * wpr)) : STEP2_THREADS;
     Step2Args a;
     a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
     a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
-    a.mx = mx; a.pyr = pyr; a.leaf_only = leaf_only ? 1 : 0;
+    a.mx = mx; a.pyr = pyr; a.leaf_only = leaf_only ? 1 : 0; a.wpr = wpr;
     a.leaf = leaf_out ? leaf_out : pyr + p->lvl_off[L];
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr,
