@@ -412,6 +412,32 @@ __device__ __forceinline__ int fixed_shift_f32(int64_t N, const unsigned int *mx
     return 62 - e1 - e2;
 }
 
+// The self term joins the exact integer sum: with selfQ = selfS / h^d and Fh = fastF h^d,
+//   out = fastF (h^d G 2^-S - u selfS) = Fh 2^-S (G - u selfQ 2^S),
+// T = round(u selfQ 2^S) (one more rounding at the scale of the leaf values), D = G - T exact,
+// then D is scaled in FP32.  Where |u selfQ 2^S| could leave 64 bits the FP64 form is used.
+__device__ __forceinline__ float fixed_epilogue(long long G, float u, double selfQ, float Fh,
+                                                double fastF, double selfS, double hd, int sh)
+{
+    const double s2 = __longlong_as_double((long long)(sh + 1023) << 52);     // 2^sh
+    const double t = (double)u * selfQ * s2;
+    if (fabs(t) < 0x1p62) {
+        const long long D = G - __double2ll_rn(t);
+        return ldexpf(Fh * (float)D, -sh);
+    }
+    return (float)(fastF * (hd * ldexp((double)G, -sh) - (double)u * selfS));
+}
+
+__global__ void k_fixed_consts(int64_t N, double hd, const double *__restrict__ fastF,
+                               const double *__restrict__ selfS, double *__restrict__ selfQ,
+                               float *__restrict__ Fh)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    selfQ[i] = selfS[i] / hd;
+    Fh[i] = (float)(fastF[i] * hd);
+}
+
 // leaf value v = fl32(u b32) as the integer round(v 2^S) (the product 2^S v is exact in FP32)
 __global__ void k_pyr_leaf_f32i64(int64_t N, const float *__restrict__ u,
                                   const float *__restrict__ b, const unsigned int *mx,
@@ -451,7 +477,8 @@ struct FastI64Args {
     int n, L;
     int64_t N;
     const int *thr4;
-    const double *fastF, *selfS;
+    const double *fastF, *selfS, *selfQ;
+    const float *Fh;
     const long long *pyr;                  // levels 0..L (leaf level last), panel-major
     int64_t lvl_off[NL_MAX_LEVELS + 2];
     double hd;
@@ -532,8 +559,7 @@ __global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T 
         }
     }
     const int sh = fixed_shift_f32(a.N, a.mx);
-    const double Gd = ldexp((double)G, -sh);
-    Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
+    Lu[i] = (T)fixed_epilogue(G, (float)u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -808,8 +834,7 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
         }
     }
     const int sh = fixed_shift_f32(a.N, a.mx);
-    const double Gd = ldexp((double)G, -sh);
-    Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
+    Lu[i] = (T)fixed_epilogue(G, (float)u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -870,8 +895,7 @@ __global__ void __launch_bounds__(256) k_fast_gather_leafrows(FastI64Args a,
         }
     }
     const int sh = fixed_shift_f32(a.N, a.mx);
-    const double Gd = ldexp((double)G, -sh);
-    Lu[i] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[i] * a.selfS[i]));
+    Lu[i] = (T)fixed_epilogue(G, (float)u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
 // Several right-hand sides at once (leaf-row form): the run bounds of a row are computed once
@@ -883,7 +907,8 @@ struct LeafMultiArgs {
     int n, count;
     int64_t N;
     const int *thr4;
-    const double *fastF, *selfS;
+    const double *fastF, *selfS, *selfQ;
+    const float *Fh;
     const long long *leaf;               // [count][N]
     const unsigned char *aux;            // [count][AUX_STRIDE], max |v| in the first word
     double hd;
@@ -949,9 +974,9 @@ __global__ void __launch_bounds__(256) k_fast_gather_leafrows_multi(LeafMultiArg
         if (q < a.count) {
             const unsigned int *mx = (const unsigned int *)(a.aux + (size_t)q * AUX_STRIDE);
             const int sh = fixed_shift_f32(a.N, mx);
-            const double Gd = ldexp((double)G[q], -sh);
             const int64_t g = (int64_t)q * a.N + i;
-            Lu[g] = (T)(a.fastF[i] * (a.hd * Gd - (double)u[g] * a.selfS[i]));
+            Lu[g] = (T)fixed_epilogue(G[q], (float)u[g], a.selfQ[i], a.Fh[i], a.fastF[i],
+                                      a.selfS[i], a.hd, sh);
         }
     }
 }
@@ -1036,6 +1061,8 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
         const size_t aux = 16 + NL_FAST_PARTS * sizeof(float);
         if ((s = alloc((void **)&p->fast_mx, aux)) != NL_OK) return s;
         NL_CUDA_TRY(cudaMemsetAsync(p->fast_mx, 0, aux, st));     // the ticket starts at 0
+        if ((s = alloc((void **)&p->selfQ, p->N * sizeof(double))) != NL_OK) return s;
+        if ((s = alloc((void **)&p->fastFh32, p->N * sizeof(float))) != NL_OK) return s;
     }
     double *d_pc = nullptr;
     if ((s = alloc((void **)&d_pc, 8 * sizeof(double))) != NL_OK) return s;
@@ -1049,6 +1076,10 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     const unsigned gb = (unsigned)((p->N + 255) / 256);
     k_fast_node<<<gb, 256, 0, st>>>(d, p->n, K, p->coef, p->self_mode, p->N, p->sigma, sphere,
                                     delta_dev, a_dev, p->thr4, d_pc, p->fastF, p->selfS, p->ir4);
+    NL_CUDA_TRY(cudaGetLastError());
+    if (K == 0)
+        k_fixed_consts<<<gb, 256, 0, st>>>(p->N, std::pow(p->h, (double)d), p->fastF, p->selfS,
+                                           p->selfQ, p->fastFh32);
     NL_CUDA_TRY(cudaGetLastError());
     NL_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_pc);
@@ -1138,6 +1169,7 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     FastI64Args a;
     a.n = p->n; a.L = L; a.N = p->N;
     a.thr4 = p->thr4; a.fastF = p->fastF; a.selfS = p->selfS;
+    a.selfQ = p->selfQ; a.Fh = p->fastFh32;
     a.pyr = pyr;
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     a.hd = std::pow(p->h, (double)d);
@@ -1265,6 +1297,7 @@ static nl_status fast_multi_leafrows(nl_plan *p, const float *u, float *Lu, int 
         LeafMultiArgs a;
         a.n = p->n; a.count = cnt; a.N = p->N;
         a.thr4 = p->thr4; a.fastF = p->fastF; a.selfS = p->selfS;
+        a.selfQ = p->selfQ; a.Fh = p->fastFh32;
         a.leaf = p->leaf_multi; a.aux = p->aux_multi;
         a.hd = std::pow(p->h, (double)p->d);
         const float *ur = u + (int64_t)r0 * p->N;

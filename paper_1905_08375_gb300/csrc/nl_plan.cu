@@ -644,7 +644,8 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->pd64, p->pdext, p->thr4, p->fastF, p->selfS, p->ir4, p->pyr, p->shift,
                      p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx,
                      p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32, p->leaf_multi,
-                     p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux };
+                     p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux, p->selfQ,
+                     p->fastFh32 };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)
