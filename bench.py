@@ -565,6 +565,13 @@ class C4(Workload):
         u = self.torch.randn(self.n * self.n, device=self.dev)
         o = self.torch.empty_like(u)
         t = self.time_fn(lambda: nl.nl_apply(self.plan, u, o), reps, flush)
+        # the pieces of one iteration for all right-hand sides: operator and preconditioner
+        r8 = self.torch.randn(self.nrhs, self.n * self.n, device=self.dev, dtype=self.torch.float64)
+        z8 = self.torch.empty_like(r8)
+        u8 = r8.float()
+        o8 = self.torch.empty_like(u8)
+        t_op8 = self.time_fn(lambda: nl.nl_apply(self.plan, u8, o8), reps, flush)
+        t_net8 = self.time_fn(lambda: nl.nl_net_apply(self.net, self.plan, r8, z8), reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         self.launches = None
         roof = _alu_roof("k_direct2d_rb<float,SYM,2> (CG operator)", 6.0 * nb, t,
@@ -574,7 +581,10 @@ class C4(Workload):
         return roof, {"learned_ms": round(t_l, 3), "learned": self.last,
                       "jacobi_ms": round(t_j, 3), "jacobi": sj,
                       "learned_speedup_over_jacobi": round(t_j / t_l, 3),
-                      "sym_apply_fp32_ms": round(t, 4), "training": self.train_info}
+                      "sym_apply_fp32_ms": round(t, 4),
+                      f"sym_apply_fp32_{self.nrhs}rhs_ms": round(t_op8, 4),
+                      f"learned_precond_apply_{self.nrhs}rhs_ms": round(t_net8, 4),
+                      "training": self.train_info}
 
     def e2e(self, flush, steps):
         torch = self.torch

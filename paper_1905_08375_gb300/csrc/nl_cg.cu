@@ -495,7 +495,8 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
     // preconditioner)
     if (c->graph_exec && (c->graph_nrhs != nrhs || c->graph_f != f || c->graph_x != x ||
                           c->graph_tol != rtol || c->graph_precond != precond ||
-                          c->graph_net != (const void *)op.net)) {
+                          c->graph_net != (const void *)op.net ||
+                          (op.net && c->graph_net_gen != nl_net_generation(op.net)))) {
         cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
         c->graph_exec = nullptr;
     }
@@ -517,6 +518,7 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
         c->graph_tol = rtol;
         c->graph_precond = precond;
         c->graph_net = op.net;
+        c->graph_net_gen = op.net ? nl_net_generation(op.net) : 0;
     }
 
     double *h = c->host;

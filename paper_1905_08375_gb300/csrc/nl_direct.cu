@@ -759,6 +759,306 @@ static nl_status x2_launch_any(nl_plan *p, int var, const DirectArgs &a, const f
     return launch_x2_var<32>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric (divergence-form) FP32 kernel with paired columns, on the traversal of
+// k_direct2d_x2.  The term of output i and neighbour j at offset o is
+//   g(o) b_j (w_i [o^2 <= thr_i] + w_j [o^2 <= thr_j]) (u_j - u_i),
+// evaluated as fma(w_i m_i, b_j, c_j m_j) g (u_j - u_i) with c_j = w_j b_j staged per tile and
+// the 0/1 masks m = sat(thr + 1 - o^2) (exact: small integers in FP32).  A column offset covers
+// the rows up to the warp's largest reach; rows inside the ball of every staged node skip both
+// masks, rows inside the ball of every output of the warp skip the output mask.  A mask equal
+// to 1 leaves each product bitwise unchanged, so the banding never changes a result.  The tile
+// holds four planes: u, b, c and thr + 1 (0 off the grid, where b = c = 0 as well).
+// ---------------------------------------------------------------------------
+struct X2sGrp { f2_t u[4], b[4], c[4], t[4]; };
+
+// rows row .. row + NR - 1 of the four planes into g (NR < 4 leaves the other entries unset)
+template <int NR = 4>
+__device__ __forceinline__ void x2s_load_grp(X2sGrp &g, const float *cu, int plane, int SX, int row)
+{
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const float *q = cu + (row + k) * SX;
+        g.u[k] = ld_pair(q);
+        g.b[k] = ld_pair(q + plane);
+        g.c[k] = ld_pair(q + 2 * plane);
+        g.t[k] = ld_pair(q + 3 * plane);
+    }
+}
+
+// 0/1 per column of the pair: [o2 <= thr] from t = thr + 1
+__device__ __forceinline__ f2_t f2_mask(f2_t t, float o2)
+{
+    float lo, hi;
+    f2_unpack(t, lo, hi);
+    return f2_pack(__saturatef(lo - o2), __saturatef(hi - o2));
+}
+
+// NJ rows oy .. oy + NJ - 1 for the RB_P outputs; output p at row j reads window entry p + j of
+// (A, B, C) = rows oy .. oy + 11.  LVL 0: no masks, 1: node masks, 2: node and output masks.
+template <int LVL, int NJ>
+__device__ __forceinline__ void x2s_rows(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                         const f2_t (&wi)[RB_P], const f2_t (&ti)[RB_P],
+                                         const X2sGrp &A, const X2sGrp &B, const X2sGrp &C,
+                                         const float *gcol, int oy, float fo)
+{
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const float g = gcol[oy + j];
+        const f2_t gg = f2_pack(g, g);
+        const float o2 = fo + (float)((oy + j) * (oy + j));
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int k = p + j;
+            const X2sGrp &G = k < 4 ? A : (k < 8 ? B : C);
+            const f2_t c = LVL >= 1 ? f2_mul(G.c[k & 3], f2_mask(G.t[k & 3], o2)) : G.c[k & 3];
+            const f2_t w = LVL >= 2 ? f2_mul(wi[p], f2_mask(ti[p], o2)) : wi[p];
+            acc[p] = f2_fma(f2_mul(f2_fma(w, G.b[k & 3], c), gg), f2_sub(G.u[k & 3], ui[p]),
+                            acc[p]);
+        }
+    }
+}
+
+// a chunk of four rows at the mask level of its outermost row
+__device__ __forceinline__ void x2s_chunk4(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                           const f2_t (&wi)[RB_P], const f2_t (&ti)[RB_P],
+                                           const X2sGrp &A, const X2sGrp &B, const X2sGrp &C,
+                                           const float *gcol, int oy, float fo, int hcore,
+                                           int hmid)
+{
+    const int m = max(abs(oy), abs(oy + 3));
+    if (m <= hcore) x2s_rows<0, 4>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    else if (m <= hmid) x2s_rows<1, 4>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    else x2s_rows<2, 4>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+}
+
+// the last rem (< 4) rows oy .. oy + rem - 1 = hmax with all masks; (A, B) = rows oy .. oy + 7
+// are loaded, C receives rows oy + 8 .. hmax + 7 (the last row any output reads)
+__device__ __forceinline__ void x2s_tail(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                         const f2_t (&wi)[RB_P], const f2_t (&ti)[RB_P],
+                                         const X2sGrp &A, const X2sGrp &B, X2sGrp &C,
+                                         const float *cu, int plane, int SX, const float *gcol,
+                                         int oy, float fo, int rem)
+{
+    if (rem == 1) {
+        x2s_rows<2, 1>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    } else if (rem == 2) {
+        x2s_load_grp<1>(C, cu, plane, SX, oy + 8);
+        x2s_rows<2, 2>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    } else if (rem == 3) {
+        x2s_load_grp<2>(C, cu, plane, SX, oy + 8);
+        x2s_rows<2, 3>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    }
+}
+
+// one column offset: rows -hmax .. hmax in increasing order, in chunks of four rows with the
+// three register groups rotated (no register shifting), then at most three tail rows.  Band
+// limits by |oy|: <= hcore no masks, <= hmid node masks (-1: empty; hcore <= hmid <= hmax).
+// hcore, hmid and hmax are the same for the whole warp, so every lane runs the same loops.
+__device__ __forceinline__ void x2s_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                           const f2_t (&wi)[RB_P], const f2_t (&ti)[RB_P],
+                                           const float *cu, int plane, int SX, const float *gcol,
+                                           int ox2, int hcore, int hmid, int hmax)
+{
+    X2sGrp G0, G1, G2;
+    int oy = -hmax;
+    const float fo = (float)ox2;
+    x2s_load_grp(G0, cu, plane, SX, oy);
+    x2s_load_grp(G1, cu, plane, SX, oy + 4);
+    for (;;) {
+        if (hmax - oy + 1 < 4) {
+            x2s_tail(acc, ui, wi, ti, G0, G1, G2, cu, plane, SX, gcol, oy, fo, hmax - oy + 1);
+            break;
+        }
+        x2s_load_grp(G2, cu, plane, SX, oy + 8);
+        x2s_chunk4(acc, ui, wi, ti, G0, G1, G2, gcol, oy, fo, hcore, hmid);
+        oy += 4;                                        // the window is (G1, G2)
+        if (hmax - oy + 1 < 4) {
+            x2s_tail(acc, ui, wi, ti, G1, G2, G0, cu, plane, SX, gcol, oy, fo, hmax - oy + 1);
+            break;
+        }
+        x2s_load_grp(G0, cu, plane, SX, oy + 8);
+        x2s_chunk4(acc, ui, wi, ti, G1, G2, G0, gcol, oy, fo, hcore, hmid);
+        oy += 4;                                        // the window is (G2, G0)
+        if (hmax - oy + 1 < 4) {
+            x2s_tail(acc, ui, wi, ti, G2, G0, G1, cu, plane, SX, gcol, oy, fo, hmax - oy + 1);
+            break;
+        }
+        x2s_load_grp(G1, cu, plane, SX, oy + 8);
+        x2s_chunk4(acc, ui, wi, ti, G2, G0, G1, gcol, oy, fo, hcore, hmid);
+        oy += 4;                                        // the window is (G0, G1) again
+    }
+}
+
+// Persistent over a largest-first queue of 64 x (TY * RB_P) tiles, as k_direct2d_x2.
+template <int RM, int TY>
+__global__ void __launch_bounds__(32 * TY)
+k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
+               float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
+               int nrhs, int *__restrict__ queue)
+{
+    constexpr int SX = 64 + 2 * RM;
+    constexpr int SY = TY * RB_P + 2 * RM + 1;
+    constexpr int PL = SX * SY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item, s_jmin[TY];
+    const int n = a.n, R = a.R;
+    float *su = reinterpret_cast<float *>(smem_raw);          // u | b | c | thr + 1
+    const int64_t N = a.N;
+    const float *__restrict__ bb = (const float *)a.b;
+    const float *__restrict__ whv = (const float *)a.wh;
+    const float *__restrict__ finv = (const float *)a.fin;
+    const float *__restrict__ extv = (const float *)a.ext;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int total = ntiles * nrhs;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int tile = order[item / nrhs], z = item % nrhs;
+        const float *__restrict__ ur = u + (int64_t)z * N;
+        const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * (TY * RB_P);
+        int jmin = 1 << 30;                          // smallest thr of the staged nodes
+        for (int e = tid; e < PL; e += 32 * TY) {
+            const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
+            float uv = 0.f, bv = 0.f, cv = 0.f, tv = 0.f;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                const int64_t j = gx + (int64_t)n * gy;
+                const int tj = a.thr[j];
+                uv = ur[j];
+                bv = bb[j];
+                cv = whv[j] * bv;
+                tv = (float)(tj + 1);
+                jmin = min(jmin, tj);
+            }
+            su[e] = uv;
+            su[e + PL] = bv;
+            su[e + 2 * PL] = cv;
+            su[e + 3 * PL] = tv;
+        }
+        jmin = __reduce_min_sync(0xffffffffu, jmin);
+        if (threadIdx.x == 0) s_jmin[threadIdx.y] = jmin;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < TY; ++w) jmin = min(jmin, s_jmin[w]);
+        const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
+        const int ybase = y0 + threadIdx.y * RB_P;
+        f2_t ui[RB_P], acc[RB_P], wi[RB_P], ti[RB_P];
+        int tmax = -1, tmin = 1 << 30;
+        const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int y = ybase + p;
+            const bool oa = xa < n && y < n, ob = xb < n && y < n;
+            const int64_t ia = xa + (int64_t)n * y, ib = ia + 1;
+            const int ta = oa ? a.thr[ia] : -1, tb = ob ? a.thr[ib] : -1;
+            const int ra = oa ? a.cnt_thr[ia] : -1, rb = ob ? a.cnt_thr[ib] : -1;
+            wi[p] = f2_pack(oa ? whv[ia] : 0.f, ob ? whv[ib] : 0.f);
+            ti[p] = f2_pack((float)(ta + 1), (float)(tb + 1));
+            tmax = max(tmax, max(ra, rb));
+            if (oa) tmin = min(tmin, ta);
+            if (ob) tmin = min(tmin, tb);
+            ui[p] = ld_pair(ua + p * SX);
+            acc[p] = f2_pack(0.f, 0.f);
+        }
+        tmax = __reduce_max_sync(0xffffffffu, tmax);
+        tmin = __reduce_min_sync(0xffffffffu, tmin);
+        if (tmin == (1 << 30)) tmin = -1;
+        const int cmin = min(tmin, jmin);
+        const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
+        for (int ox = -rx; ox <= rx; ++ox) {
+            const int ox2 = ox * ox;
+            if (ox2 > tmax) continue;
+            const int hmax = min(R, isqrt_small(tmax - ox2));
+            const int hmid = (tmin >= ox2) ? min(hmax, isqrt_small(tmin - ox2)) : -1;
+            const int hcore = (cmin >= ox2) ? min(hmid, isqrt_small(cmin - ox2)) : -1;
+            const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
+            x2s_column(acc, ui, wi, ti, ua + ox, PL, SX, gcol, ox2, hcore, hmid, hmax);
+        }
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int y = ybase + p;
+            float s0, s1, u0, u1;
+            f2_unpack(acc[p], s0, s1);
+            f2_unpack(ui[p], u0, u1);
+            if (y < n && xa < n) {
+                const int64_t i = xa + (int64_t)n * y;
+                Lu[(int64_t)z * N + i] = finv[i] * (s0 - u0 * extv[i]);
+            }
+            if (y < n && xb < n) {
+                const int64_t i = xb + (int64_t)n * y;
+                Lu[(int64_t)z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+            }
+        }
+        __syncthreads();               // the tile, s_item and s_jmin are reused by the next item
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) { queue[0] = 0; queue[1] = 0; }
+    }
+}
+
+template <int RM, int TY>
+static size_t x2s_smem_bytes()
+{
+    return sizeof(float) * (size_t)4 * (64 + 2 * RM) * (TY * RB_P + 2 * RM + 1);
+}
+
+// symmetric kernel variants: TY warps per tile (shared memory bounds the residency)
+constexpr int X2S_VARIANTS = 2;
+static const int x2s_var_ty[X2S_VARIANTS] = { 2, 4 };
+
+template <int RM, int TY>
+static nl_status launch_x2s_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                              int nrhs, const int *order, int ntiles, int *blocks_cache,
+                              cudaStream_t st)
+{
+    const dim3 blk(32, TY, 1);
+    const size_t smem = x2s_smem_bytes<RM, TY>();
+    auto kern = k_direct2d_x2s<RM, TY>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    const int tiles_x = (p->n + 63) / 64;
+    const int64_t items = (int64_t)ntiles * nrhs;
+    if (items >= (int64_t)1 << 31) {
+        nl_set_error("nl_apply: %lld tiles x right-hand sides exceed the tile queue", (long long)items);
+        return NL_EUNSUPPORTED;
+    }
+    if (items == 0) return NL_OK;
+    if (*blocks_cache == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem));
+        NL_CUDA_TRY(cudaGetDevice(&dev));
+        NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        *blocks_cache = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int64_t blocks = std::min<int64_t>(*blocks_cache, items);
+    kern<<<(unsigned)blocks, blk, smem, st>>>(a, p->rb_g32, u, Lu, order, ntiles, tiles_x, nrhs,
+                                              p->x2_queue);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+template <int RM>
+static nl_status launch_x2s_var(nl_plan *p, int var, const DirectArgs &a, const float *u,
+                                float *Lu, int nrhs, const int *order, int ntiles, int *bc,
+                                cudaStream_t st)
+{
+    if (var == 0) return launch_x2s_t<RM, 2>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    return launch_x2s_t<RM, 4>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+}
+
+static nl_status x2s_launch_any(nl_plan *p, int var, const DirectArgs &a, const float *u,
+                                float *Lu, int nrhs, const int *order, int ntiles, int *bc,
+                                cudaStream_t st)
+{
+    if (p->Rmax <= 4) return launch_x2s_var<4>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 8) return launch_x2s_var<8>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 16) return launch_x2s_var<16>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 24) return launch_x2s_var<24>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    return launch_x2s_var<32>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+}
+
 // Tile order for the paired-column kernel: the cost of a 64 x rows tile is the sum of its
 // nodes' ball sizes; tiles are queued largest first.
 __global__ void k_x2_tile_cost(int n, int tiles_x, int rows, const int *__restrict__ cnt,
@@ -1273,6 +1573,9 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
             return x2_launch_any(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
                                  &p->x2_blocks, st);
         }
+        if (mode == MODE_SYM && p->Rmax <= 32 && p->x2_order)
+            return x2s_launch_any(p, p->x2_var, a, (const float *)u, (float *)Lu, nrhs,
+                                  p->x2_order, p->x2_tiles, &p->x2_blocks, st);
         if (mode == MODE_POWER) return launch_rb_t<T, MODE_POWER>(p, a, u, Lu, nrhs, st);
         if (mode == MODE_POLY) return launch_rb_t<T, MODE_POLY>(p, a, u, Lu, nrhs, st);
         return launch_rb_t<T, MODE_SYM>(p, a, u, Lu, nrhs, st);
@@ -1837,8 +2140,10 @@ static nl_status x3_tune(nl_plan *p, cudaStream_t st)
 nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
 {
     if (p->d == 3) return x3_tune(p, st);
-    if (!(p->d == 2 && p->rb2d && p->family == NL_POWER && !p->symmetric && p->Rmax <= 32))
-        return NL_OK;
+    if (!(p->d == 2 && p->rb2d && p->family == NL_POWER && p->Rmax <= 32)) return NL_OK;
+    const bool sym = p->symmetric != 0;
+    const int nvar = sym ? X2S_VARIANTS : X2_VARIANTS;
+    const int *var_ty = sym ? x2s_var_ty : x2_var_ty;
     NL_CUDA_TRY(cudaMalloc(&p->x2_queue, 2 * sizeof(int)));
     NL_CUDA_TRY(cudaMemsetAsync(p->x2_queue, 0, 2 * sizeof(int), st));
     int *ord[2] = { nullptr, nullptr };              // orders for TY = 2 and TY = 4
@@ -1850,7 +2155,7 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
     nl_status s = NL_OK;
     for (int k = tune ? 0 : 1; k < 2 && s == NL_OK; ++k)
         s = x2_order_for(p, k == 0 ? 2 : 4, &ord[k], &nt[k], st);
-    int best = 2;                                     // TY = 4, four blocks per SM
+    int best = sym ? 1 : 2;                           // TY = 4 (four blocks per SM)
     if (s == NL_OK && tune) {
         const DirectArgs a = make_args(p, NL_F32);
         if (cudaMalloc(&u, p->N * sizeof(float)) != cudaSuccess ||
@@ -1859,10 +2164,11 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
             cudaMemsetAsync(u, 0, p->N * sizeof(float), st) != cudaSuccess) {
             s = nl_cuda_fail(cudaErrorMemoryAllocation, "direct kernel tuning");
         }
-        for (int v = 0; v < X2_VARIANTS && s == NL_OK; ++v) {
-            const int k = x2_var_ty[v] == 2 ? 0 : 1;
+        for (int v = 0; v < nvar && s == NL_OK; ++v) {
+            const int k = var_ty[v] == 2 ? 0 : 1;
             auto run = [&]() {
-                return x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
+                return sym ? x2s_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st)
+                           : x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
             };
             if ((s = run()) != NL_OK) break;
             cudaEventRecord(e0, st);
@@ -1872,13 +2178,13 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
             cudaEventElapsedTime(&ms[v], e0, e1);
         }
         best = 0;
-        for (int v = 1; v < X2_VARIANTS; ++v) if (ms[v] < ms[best]) best = v;
+        for (int v = 1; v < nvar; ++v) if (ms[v] < ms[best]) best = v;
     }
     if (u) cudaFree(u);
     if (lu) cudaFree(lu);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    const int kb = x2_var_ty[best] == 2 ? 0 : 1;
+    const int kb = var_ty[best] == 2 ? 0 : 1;
     if (ord[1 - kb]) cudaFree(ord[1 - kb]);
     if (s != NL_OK) {
         if (ord[kb]) cudaFree(ord[kb]);

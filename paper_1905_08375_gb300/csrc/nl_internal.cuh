@@ -44,6 +44,7 @@ struct nl_cg_state {
     double graph_tol;
     int graph_precond;
     const void *graph_net;
+    uint64_t graph_net_gen;
 };
 
 // The operator CG works with: nrhs segments (right-hand sides or batch instances) of the
@@ -183,3 +184,5 @@ nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z,
                               cudaStream_t st);
 nl_status nl_net_reserve(nl_net *n, nl_plan *p, int nrhs, cudaStream_t st);
 bool nl_net_valid(const nl_net *n);
+// changes whenever a buffer address or a launch argument of the network's apply changes
+uint64_t nl_net_generation(const nl_net *n);

@@ -21,6 +21,7 @@
 // reduction over tiles (deterministic).
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -472,6 +473,86 @@ __global__ void k_prolong_add(const float *__restrict__ x, const float *__restri
     }
 }
 
+// Restriction by columns for n <= RC_MAXN: block (cy, b) sums each fine column over the
+// cell row's blk rows (coalesced, thread per column), then each cell's blk column sums in
+// order.  Same values as k_restrict up to the order of the FP64 sums.
+constexpr int RC_MAXN = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_rows(const T *__restrict__ v, int n, int blk,
+                                                       int nc, double scale,
+                                                       float *__restrict__ rc)
+{
+    __shared__ double col[RC_MAXN];
+    const int cy = blockIdx.x, b = blockIdx.y;
+    const int y0 = cy * blk, y1 = min(n, y0 + blk);
+    const T *vb = v + (size_t)b * n * n;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        double s = 0.0;
+#pragma unroll 8
+        for (int y = y0; y < y1; ++y) s += (double)vb[(size_t)y * n + x];
+        col[x] = s;
+    }
+    __syncthreads();
+    for (int cx = threadIdx.x; cx < nc; cx += blockDim.x) {
+        const int x0 = cx * blk, x1 = min(n, x0 + blk);
+        double s = 0.0;
+        for (int x = x0; x < x1; ++x) s += col[x];
+        rc[(size_t)b * nc * nc + cy * nc + cx] = (float)(s * scale);
+    }
+}
+
+// Coarse operator of the two-level form as a matrix: the network K is linear, so K^T K is a
+// fixed m x m matrix on the coarse grid (m = nc^2 cells).  With H[i] = K e_i (the forward
+// chain applied to the unit vectors) G[i][j] = H[i] . H[j]; both entries of a symmetric pair
+// run the same products in the same order, so G is exactly symmetric.  FP64 sums.
+constexpr int GRAM_MAXNC = 16;
+
+__global__ void k_eye(float *__restrict__ e, int m)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m * m; k += gridDim.x * blockDim.x)
+        e[k] = (k / m == k % m) ? 1.f : 0.f;
+}
+
+__global__ void k_gram(const float *__restrict__ h, int m, float *__restrict__ g)
+{
+    const int i = blockIdx.x;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s = fma((double)h[(size_t)i * m + k], (double)h[(size_t)j * m + k], s);
+        g[(size_t)i * m + j] = (float)s;
+    }
+}
+
+// zc[b] = G rc[b]: one warp per row of G (held in registers), eight right-hand sides per block
+__global__ void __launch_bounds__(256) k_coarse_gemv(const float *__restrict__ g,
+                                                     const float *__restrict__ rc, int m, int nrhs,
+                                                     float *__restrict__ zc)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= m) return;
+    float gr[GRAM_MAXNC * GRAM_MAXNC / 32];
+#pragma unroll
+    for (int q = 0; q < GRAM_MAXNC * GRAM_MAXNC / 32; ++q) {
+        const int k = lane + 32 * q;
+        gr[q] = k < m ? g[(size_t)i * m + k] : 0.f;
+    }
+    const int b1 = min(nrhs, (int)(blockIdx.y + 1) * 8);
+    for (int b = blockIdx.y * 8; b < b1; ++b) {
+        const float *x = rc + (size_t)b * m;
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < GRAM_MAXNC * GRAM_MAXNC / 32; ++q) {
+            const int k = lane + 32 * q;
+            if (k < m) s = fmaf(gr[q], x[k], s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) zc[(size_t)b * m + i] = s;
+    }
+}
+
 }  // namespace
 
 struct nl_net {
@@ -486,7 +567,20 @@ struct nl_net {
     float *loss;   int loss_elems;
     float *inf;    size_t inf_elems;     // inference activations
     double *red;   int red_elems;
+    float *gram;   size_t gram_elems;    // G = K^T K on the coarse grid (two-level form)
+    int gram_nc;                         // coarse size G was built for (0: none)
+    uint64_t gram_ver;                   // weight version G was built from
+    uint64_t wver;                       // weight version (bumped whenever wk/wkt change)
+    uint64_t gen;                        // bumped whenever a buffer an apply uses moves
 };
+
+// Generations are unique across networks, so a network created at a freed one's address
+// never matches a graph captured over the old one.
+static uint64_t next_generation()
+{
+    static std::atomic<uint64_t> counter{0};
+    return ++counter;
+}
 
 template <typename K>
 static cudaError_t smem_attr(K kern, size_t bytes)
@@ -547,6 +641,7 @@ extern "C" nl_status nl_net_create(nl_net **out, const float *weights, void *str
     nl_net *n = (nl_net *)calloc(1, sizeof(nl_net));
     if (!n) return NL_ENOMEM;
     n->magic = NL_NET_MAGIC;
+    n->gen = next_generation();
     cudaError_t e = cudaSuccess;
     void **bufs[] = { (void **)&n->w32, (void **)&n->m, (void **)&n->v, (void **)&n->grad,
                       (void **)&n->wk, (void **)&n->wkt };
@@ -564,6 +659,7 @@ extern "C" nl_status nl_net_create(nl_net **out, const float *weights, void *str
     NL_CUDA_TRY(cudaMemsetAsync(n->v, 0, NPARAM * sizeof(float), st));
     k_to_bf16<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->w32, n->wb);
     k_layouts<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->wb, n->wk, n->wkt);
+    ++n->wver;
     NL_CUDA_TRY(cudaGetLastError());
     NL_CUDA_TRY(cudaStreamSynchronize(st));
     *out = n;
@@ -579,7 +675,7 @@ extern "C" nl_status nl_net_destroy(nl_net *n)
     }
     cudaDeviceSynchronize();
     void *ptrs[] = { n->w32, n->m, n->v, n->grad, n->wb, n->wk, n->wkt, n->train, n->part,
-                     n->loss, n->inf, n->red };
+                     n->loss, n->inf, n->red, n->gram };
     for (void *q : ptrs) if (q) cudaFree(q);
     n->magic = 0;
     free(n);
@@ -670,6 +766,7 @@ extern "C" nl_status nl_net_train_step(nl_net *n, const float *x, const float *e
     const float c1 = 1.f - powf(0.9f, (float)n->t), c2 = 1.f - powf(0.999f, (float)n->t);
     k_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->w32, n->m, n->v, n->grad, n->wb, lr, c1, c2);
     k_layouts<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->wb, n->wk, n->wkt);
+    ++n->wver;
     NL_CUDA_TRY(cudaGetLastError());
     if (loss_host) {
         float tmp[1024];
@@ -738,6 +835,7 @@ static nl_status net_backward_adam(nl_net *n, const float *xb, const float *y1, 
     const float c1 = 1.f - powf(0.9f, (float)n->t), c2 = 1.f - powf(0.999f, (float)n->t);
     k_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->w32, n->m, n->v, n->grad, n->wb, lr, c1, c2);
     k_layouts<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->wb, n->wk, n->wkt);
+    ++n->wver;
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
@@ -748,6 +846,26 @@ static int coarse_n(const nl_net *n, const nl_plan *p) { return (p->n + n->block
 static double two_level_gamma(const nl_net *n, const nl_plan *p)
 {
     return 1.0 / ((double)n->block * n->block * p->diag_mean);
+}
+
+template <typename T>
+static void launch_restrict(const T *v, int nn, int blk, int nc, double scale, float *rc, int B,
+                            cudaStream_t st)
+{
+    if (nn <= RC_MAXN)
+        k_restrict_rows<T><<<dim3((unsigned)nc, B), 256, 0, st>>>(v, nn, blk, nc, scale, rc);
+    else
+        k_restrict<T><<<dim3((unsigned)(nc * nc), B), RB, 0, st>>>(v, nn, blk, nc, scale, rc);
+}
+
+// grow() for buffers an apply reads: a move invalidates graphs captured over the old address
+template <typename T>
+static nl_status grow_tracked(nl_net *n, T **buf, size_t *have, size_t need)
+{
+    T *const old = *buf;
+    const nl_status s = grow(buf, have, need);
+    if (*buf != old) n->gen = next_generation();
+    return s;
 }
 
 // u = K x, keeping the activations a1, a2 ([B][32][nc][nc])
@@ -790,14 +908,14 @@ static nl_status train_energy_two_level(nl_net *n, nl_plan *p, const float *x, c
     const double gam = two_level_gamma(n, p);
     const unsigned gx = (unsigned)((N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024);
     k_gather_fields<<<dim3(gx, batch), 256, 0, st>>>(x, e, fields, nfields, N, dinv, xb, eb, rb);
-    k_restrict<float><<<dim3((unsigned)c, batch), RB, 0, st>>>(rb, nn, blk, nc, 1.0, cin);
+    launch_restrict<float>(rb, nn, blk, nc, 1.0, cin, batch, st);
     chain_forward(n, cin, a1, a2, uv, batch, nc, st);                       // u = K R r
     chain_adjoint(n, uv, t2, t1, zc, batch, nc, st);                        // K^T u
     k_prolong_add<<<dim3(gx, batch), 256, 0, st>>>(xb, zc, nn, blk, nc, (float)gam, z);
     if ((s = nl_direct_launch(p, z, Lz, batch, NL_F32, st)) != NL_OK) return s;
     k_energy_partial<<<dim3(NB, batch), RB, 0, st>>>(z, Lz, rb, eb, N, n->red);
     k_energy_grad<<<dim3(gx, batch), 256, 0, st>>>(Lz, rb, N, n->red, batch, go, n->loss);
-    k_restrict<float><<<dim3((unsigned)c, batch), RB, 0, st>>>(go, nn, blk, nc, gam, cin + cb);
+    launch_restrict<float>(go, nn, blk, nc, gam, cin + cb, batch, st);
     chain_forward(n, cin + cb, a1 + 32 * cb, a2 + 32 * cb, uv + cb, batch, nc, st);   // v = K g
     // upstream: the first half (inputs R r) takes v, the second (inputs g) takes u
     NL_CUDA_TRY(cudaMemcpyAsync(up, uv + cb, cb * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -888,8 +1006,30 @@ extern "C" nl_status nl_net_gradient(nl_net *n, float *grad_host, void *stream)
 
 static size_t two_level_inf_elems(const nl_net *n, const nl_plan *p, int nrhs)
 {
-    const size_t c = (size_t)coarse_n(n, p) * coarse_n(n, p);
+    const int nc = coarse_n(n, p);
+    const size_t c = (size_t)nc * nc;
+    if (nc <= GRAM_MAXNC) return c * nrhs * 2;              // rc zc
     return c * nrhs * (1 + 32 + 32 + 1 + 32 + 32 + 1);     // rc a1 a2 u t2 t1 zc
+}
+
+// Build G = K^T K for the current weights and coarse size (nothing to do when up to date).
+// Allocates and synchronises: runs before a CG chunk is captured, never inside one.
+static nl_status ensure_gram(nl_net *n, int nc, cudaStream_t st)
+{
+    if (n->gram_nc == nc && n->gram_ver == n->wver) return NL_OK;
+    const size_t m = (size_t)nc * nc;
+    nl_status s = grow_tracked(n, &n->gram, &n->gram_elems, m * m);
+    if (s != NL_OK) return s;
+    s = grow(&n->train, &n->train_elems, m * m * (1 + 32 + 32 + 1));
+    if (s != NL_OK) return s;
+    float *e = n->train, *a1 = e + m * m, *a2 = a1 + 32 * m * m, *h = a2 + 32 * m * m;
+    k_eye<<<(unsigned)((m * m + 255) / 256), 256, 0, st>>>(e, (int)m);
+    chain_forward(n, e, a1, a2, h, (int)m, nc, st);                         // H[i] = K e_i
+    k_gram<<<(unsigned)m, 256, 0, st>>>(h, (int)m, n->gram);
+    NL_CUDA_TRY(cudaGetLastError());
+    n->gram_nc = nc;
+    n->gram_ver = n->wver;
+    return NL_OK;
 }
 
 nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,
@@ -901,14 +1041,23 @@ nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z,
     if (n->block >= 2) {
         const int nc = coarse_n(n, p);
         const size_t cb = (size_t)nc * nc * nrhs;
-        s = grow(&n->inf, &n->inf_elems, two_level_inf_elems(n, p, nrhs));
+        s = grow_tracked(n, &n->inf, &n->inf_elems, two_level_inf_elems(n, p, nrhs));
         if (s != NL_OK) return s;
-        float *rc = n->inf, *a1 = rc + cb, *a2 = a1 + 32 * cb, *u = a2 + 32 * cb;
-        float *t2 = u + cb, *t1 = t2 + 32 * cb, *zc = t1 + 32 * cb;
-        k_restrict<double><<<dim3((unsigned)(nc * nc), nrhs), RB, 0, st>>>(r, p->n, n->block, nc,
-                                                                            1.0, rc);
-        chain_forward(n, rc, a1, a2, u, nrhs, nc, st);
-        chain_adjoint(n, u, t2, t1, zc, nrhs, nc, st);
+        float *rc = n->inf, *zc;
+        launch_restrict<double>(r, p->n, n->block, nc, 1.0, rc, nrhs, st);
+        if (nc <= GRAM_MAXNC) {
+            if ((s = ensure_gram(n, nc, st)) != NL_OK) return s;
+            zc = rc + cb;
+            const int m = nc * nc;
+            k_coarse_gemv<<<dim3((unsigned)((m + 7) / 8), (unsigned)((nrhs + 7) / 8)), 256, 0, st>>>(
+                n->gram, rc, m, nrhs, zc);
+        } else {
+            float *a1 = rc + cb, *a2 = a1 + 32 * cb, *u = a2 + 32 * cb;
+            float *t2 = u + cb, *t1 = t2 + 32 * cb;
+            zc = t1 + 32 * cb;
+            chain_forward(n, rc, a1, a2, u, nrhs, nc, st);
+            chain_adjoint(n, u, t2, t1, zc, nrhs, nc, st);
+        }
         const unsigned gx = (unsigned)((p->N + 255) / 256 < 1024 ? (p->N + 255) / 256 : 1024);
         k_prolong_jacobi<<<dim3(gx, nrhs), 256, 0, st>>>(r, dinv, zc, p->n, n->block, nc,
                                                          two_level_gamma(n, p), z);
@@ -917,10 +1066,10 @@ nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z,
     }
     const int64_t N = p->N;
     const int H = p->n, W = p->n;
-    s = grow(&n->inf, &n->inf_elems, (size_t)(66) * N * nrhs);
+    s = grow_tracked(n, &n->inf, &n->inf_elems, (size_t)(66) * N * nrhs);
     if (s != NL_OK) return s;
     size_t re = (size_t)n->red_elems;
-    s = grow(&n->red, &re, (size_t)NB * nrhs);
+    s = grow_tracked(n, &n->red, &re, (size_t)NB * nrhs);
     if (s != NL_OK) return s;
     n->red_elems = (int)re;
     float *xf = n->inf, *o = xf + (size_t)N * nrhs, *y1 = o + (size_t)N * nrhs;
@@ -940,14 +1089,18 @@ nl_status nl_net_reserve(nl_net *n, nl_plan *p, int nrhs, cudaStream_t st)
     const double *dinv = nullptr;
     nl_status s = plan_dinv(p, st, &dinv);
     if (s != NL_OK) return s;
-    s = grow(&n->inf, &n->inf_elems, n->block >= 2 ? two_level_inf_elems(n, p, nrhs)
-                                                   : (size_t)66 * p->N * nrhs);
+    s = grow_tracked(n, &n->inf, &n->inf_elems, n->block >= 2 ? two_level_inf_elems(n, p, nrhs)
+                                                               : (size_t)66 * p->N * nrhs);
     if (s != NL_OK) return s;
     size_t re = (size_t)n->red_elems;
-    s = grow(&n->red, &re, (size_t)NB * nrhs);
+    s = grow_tracked(n, &n->red, &re, (size_t)NB * nrhs);
     n->red_elems = (int)re;
+    if (s == NL_OK && n->block >= 2 && coarse_n(n, p) <= GRAM_MAXNC)
+        s = ensure_gram(n, coarse_n(n, p), st);
     return s;
 }
+
+uint64_t nl_net_generation(const nl_net *n) { return n->gen; }
 
 bool nl_net_valid(const nl_net *n) { return net_ok(n); }
 
@@ -1009,6 +1162,7 @@ extern "C" nl_status nl_net_set_coarse(nl_net *n, int block)
         nl_set_error("nl_net_set_coarse: bad argument (block 0 or 2 .. 65536)");
         return NL_EINVAL;
     }
+    if (n->block != block) n->gen = next_generation();   // captured launch arguments change
     n->block = block;
     return NL_OK;
 }

@@ -79,6 +79,36 @@ def test_2d_symmetric_paired_columns_fp32(n, nrhs):
     assert rel_l2(run_direct(plan, f["u"], torch.float32), ref) <= 2e-6
 
 
+@pytest.mark.parametrize("n,rmin,rspan", [(190, 2.0, 19.0), (184, 9.0, 0.0), (200, 19.0, 1.5)])
+def test_2d_symmetric_paired_columns_horizon_mixes(n, rmin, rspan):
+    """Horizons from 2 to 21 cells (most rows need masks), a constant horizon (no masks) and
+    radii above 16 cells (the 24-cell halo); FP32 against the FP64 oracle and each right-hand
+    side of a batch equal bit for bit to its own apply (n^2 > 32768 nodes, so that one
+    right-hand side takes the same kernel as three)."""
+    f = synth.heterogeneous_2d(n=n, seed=n + 7, nrhs=3, rmin=rmin, rspan=rspan)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+    ref = oracle.direct_scalar(f["u"], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                               a=f["a"], symmetric=True)
+    got = run_direct(plan, f["u"], torch.float32)
+    assert rel_l2(got, ref) <= 2e-6
+    for r in range(3):
+        one = run_direct(plan, f["u"][r], torch.float32)
+        assert np.array_equal(one.reshape(-1), got[r].reshape(-1))
+
+
+def test_2d_symmetric_fp32_operator_is_symmetric():
+    """<v, L u> = <u, L v> for the divergence-form operator, up to FP32 rounding."""
+    n = 140
+    f = synth.heterogeneous_2d(n=n, seed=5, nrhs=2)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+    Lw = run_direct(plan, f["u"], torch.float32)
+    u, v = f["u"][0], f["u"][1]
+    a, b = float(np.dot(v, Lw[0])), float(np.dot(u, Lw[1]))
+    assert abs(a - b) <= 1e-5 * np.linalg.norm(Lw) * np.linalg.norm(u), (a, b)
+
+
 def test_2d_symmetric_512_sampled():
     n = 512
     f = synth.heterogeneous_2d(n=n, seed=1)

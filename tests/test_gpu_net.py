@@ -167,3 +167,35 @@ def test_two_level_learned_cg_fewer_iterations_than_jacobi():
                               coef=oracle.COEF_XY, a=fld["a"], symmetric=True)
     res = np.linalg.norm(f + Lx, axis=1) / np.linalg.norm(f, axis=1)
     assert np.all(res <= 1.01e-8), res
+
+
+def test_two_level_cg_follows_buffer_moves_and_weight_updates():
+    """A captured CG chunk must not outlive the network's buffers or weights: growing the
+    apply workspace between solves gives the same solve bit for bit, and after a training
+    step the solve equals that of a fresh network holding the updated weights."""
+    n, block = 64, 8
+    fld, plan, dinv = _sym_plan(n, 31)
+    net = nl.nl_net_create(precond.init_weights(2, two_level=True))
+    nl.nl_net_set_coarse(net, block)
+    nl.nl_plan_set_net(plan, net)
+    ft = torch.tensor(synth.cg_rhs(n, seed=32, count=2), device=DEV)
+    x1 = torch.empty_like(ft)
+    s1 = nl.nl_cg_solve(plan, ft, x1, rtol=1e-8, maxit=5000, precond=nl.NL_PRECOND_LEARNED)
+    big = torch.tensor(synth.cg_rhs(n, seed=33, count=6), device=DEV)
+    nl.nl_net_apply(net, plan, big, torch.empty_like(big))          # moves the workspace
+    x2 = torch.empty_like(ft)
+    s2 = nl.nl_cg_solve(plan, ft, x2, rtol=1e-8, maxit=5000, precond=nl.NL_PRECOND_LEARNED)
+    assert s1["converged"] and s1["iterations"] == s2["iterations"], (s1, s2)
+    assert torch.equal(x1, x2)
+    xp, ep = precond.collect_pairs(plan, n, seeds=range(40, 42), cap=8)
+    precond.train_energy(net, plan, xp, ep, pairs=16, batch=8, lr=1e-2)
+    x3 = torch.empty_like(ft)
+    s3 = nl.nl_cg_solve(plan, ft, x3, rtol=1e-8, maxit=5000, precond=nl.NL_PRECOND_LEARNED)
+    net2 = nl.nl_net_create(nl.nl_net_get_weights(net))
+    nl.nl_net_set_coarse(net2, block)
+    nl.nl_plan_set_net(plan, net2)
+    x4 = torch.empty_like(ft)
+    s4 = nl.nl_cg_solve(plan, ft, x4, rtol=1e-8, maxit=5000, precond=nl.NL_PRECOND_LEARNED)
+    assert s3["converged"] and s3["iterations"] == s4["iterations"], (s3, s4)
+    assert torch.equal(x3, x4)
+    assert not torch.equal(x1, x3)                                 # the weights did change
