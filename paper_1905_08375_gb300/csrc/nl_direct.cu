@@ -454,6 +454,12 @@ __device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi)
 {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
+{
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
 {
     f2_t r;
@@ -497,15 +503,15 @@ __device__ __forceinline__ void x2_load_grp(X2Grp &g, const float *cu, int plane
     }
 }
 
-// rows oy .. oy + 3 for the RB_P (= 8) outputs; the window is (G0, G1) = rows oy .. oy + 7
-// and G2 holds rows oy + 8 .. oy + 11; every output is inside its ball
+// rows oy .. oy + 3 (weights g4) for the RB_P (= 8) outputs; the window is (G0, G1) = rows
+// oy .. oy + 7 and G2 holds rows oy + 8 .. oy + 11; every output is inside its ball
 __device__ __forceinline__ void x2_core4(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
                                          const X2Grp &G0, const X2Grp &G1, const X2Grp &G2,
-                                         const float *gcol, int oy)
+                                         const float (&g4)[4])
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float g = gcol[oy + j];
+        const float g = g4[j];
         const f2_t gg = f2_pack(g, g);
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
@@ -516,18 +522,20 @@ __device__ __forceinline__ void x2_core4(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_
     }
 }
 
+// thresholds of a thread's two output columns (0 off the grid)
+struct X2Thr { int a[RB_P], b[RB_P]; };
+
 // one row (offset oy) for the RB_P outputs from the window (G0, G1); MASK: outputs whose ball
 // does not hold the offset get weight 0
 template <bool MASK>
 __device__ __forceinline__ void x2_row(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
                                        const X2Grp &G0, const X2Grp &G1,
-                                       const unsigned (&thr2)[RB_P], float g, int o2)
+                                       const X2Thr &thr2, float g, int o2)
 {
 #pragma unroll
     for (int p = 0; p < RB_P; ++p) {
         const X2Grp &G = p < 4 ? G0 : G1;
-        const f2_t gm = MASK ? f2_pack(o2 <= (int)(thr2[p] & 0xffffu) ? g : 0.f,
-                                       o2 <= (int)(thr2[p] >> 16) ? g : 0.f)
+        const f2_t gm = MASK ? f2_pack(o2 <= thr2.a[p] ? g : 0.f, o2 <= thr2.b[p] ? g : 0.f)
                              : f2_pack(g, g);
         acc[p] = f2_fma(f2_mul(G.b[p & 3], gm), f2_sub(G.u[p & 3], ui[p]), acc[p]);
     }
@@ -550,11 +558,12 @@ __device__ __forceinline__ void x2_slide(X2Grp &G0, X2Grp &G1, const float *cu, 
 
 // one column offset ox: rows -hmax .. hmax in increasing order (the same order for every
 // output), masked single rows at the rims, unmasked groups of four rows in the core with the
-// three row groups rotated instead of copied.  hmin and hmax are the same for the whole warp
-// (its 64 x 8 outputs), so every lane runs the same loops.
+// three row groups rotated instead of copied, and each group's four weights loaded one group
+// ahead (indices clamped to the column's last row, so no read leaves the column).  hmin and
+// hmax are the same for the whole warp (its 64 x 8 outputs), so every lane runs the same loops.
 __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
-                                          const unsigned (&thr2)[RB_P], const float *cu, int plane, int SX, const float *gcol,
-                                          int ox2, int hmin, int hmax)
+                                          const X2Thr &thr2, const float *cu, int plane, int SX,
+                                          const float *gcol, int ox2, int hmin, int hmax)
 {
     X2Grp G0, G1, G2;
     int oy = -hmax;
@@ -568,18 +577,35 @@ __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB
     }
     if (hmin >= 0) {
         int rem = hmin - oy + 1;
+        float gc[4], gn[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gc[j] = gcol[min(oy + j, hmax)];
+        auto next_g = [&]() {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gn[j] = gcol[min(oy + 4 + j, hmax)];
+        };
+        auto rotate_g = [&]() {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) gc[j] = gn[j];
+        };
         for (;;) {
             if (rem < 4) break;
             x2_load_grp(G2, cu, plane, SX, oy + 8);
-            x2_core4(acc, ui, G0, G1, G2, gcol, oy);
+            next_g();
+            x2_core4(acc, ui, G0, G1, G2, gc);
+            rotate_g();
             oy += 4; rem -= 4;                      // the window is (G1, G2)
             if (rem < 4) { G0 = G1; G1 = G2; break; }
             x2_load_grp(G0, cu, plane, SX, oy + 8);
-            x2_core4(acc, ui, G1, G2, G0, gcol, oy);
+            next_g();
+            x2_core4(acc, ui, G1, G2, G0, gc);
+            rotate_g();
             oy += 4; rem -= 4;                      // the window is (G2, G0)
             if (rem < 4) { G1 = G0; G0 = G2; break; }
             x2_load_grp(G1, cu, plane, SX, oy + 8);
-            x2_core4(acc, ui, G2, G0, G1, gcol, oy);
+            next_g();
+            x2_core4(acc, ui, G2, G0, G1, gc);
+            rotate_g();
             oy += 4; rem -= 4;                      // the window is (G0, G1) again
         }
         for (; oy <= hmin; ++oy) {
@@ -597,9 +623,15 @@ __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB
 // RM: compile-time halo (>= the plan's largest radius) so that the tile geometry is constant.
 // Persistent: each block takes 64 x (TY * RB_P) tiles (times right-hand sides) from a queue
 // ordered by decreasing cost (the sum of the tile's ball sizes, largest first); the last
-// block to finish resets the queue for the next launch on the stream.
+// block to finish resets the queue for the next launch on the stream.  A block has 2 TY
+// warps: warp w takes rows 8 (w / 2) .. 8 (w / 2) + 7 of the tile and the column offsets
+// ox < 0 (w even) or ox >= 0 (w odd), so a tile is half the size of one with a warp per row
+// group and the per-item costs even out across the SMs.  The two partial sums of an output
+// (each over its column offsets in increasing order) are added once, ox < 0 part + ox >= 0
+// part, through shared memory.  The weight table |o|^{-alpha} is copied to shared memory once
+// per block.
 template <int RM, int TY, int MB>
-__global__ void __launch_bounds__(32 * TY, MB)
+__global__ void __launch_bounds__(64 * TY, MB)
 k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
               float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
               int nrhs, int *__restrict__ queue)
@@ -611,12 +643,16 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
     const int n = a.n, R = a.R;                      // R <= RM
     float *su = reinterpret_cast<float *>(smem_raw);
     float *sb = su + SX * SY;
+    float *sg = sb + SX * SY;                        // [2R+1][2R+1] weights
+    f2_t *sx = reinterpret_cast<f2_t *>(smem_raw);   // partial sums, over the tile once read
     const int64_t N = a.N;
     const float *__restrict__ bb = (const float *)a.b;
     const float *__restrict__ finv = (const float *)a.fin;
     const float *__restrict__ extv = (const float *)a.ext;
     const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int grp = threadIdx.y >> 1, half = threadIdx.y & 1;
     const int total = ntiles * nrhs;
+    for (int e = tid; e < (2 * R + 1) * (2 * R + 1); e += 64 * TY) sg[e] = gtab[e];
     for (;;) {
         if (tid == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
@@ -625,7 +661,7 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         const int tile = order[item / nrhs], z = item % nrhs;
         const float *__restrict__ ur = u + (int64_t)z * N;
         const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * (TY * RB_P);
-        for (int e = tid; e < SX * SY; e += 32 * TY) {
+        for (int e = tid; e < SX * SY; e += 64 * TY) {
             const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
             float uv = 0.f, bv = 0.f;
             if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
@@ -639,19 +675,20 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         __syncthreads();
 
         const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
-        const int ybase = y0 + threadIdx.y * RB_P;
+        const int ybase = y0 + grp * RB_P;
         f2_t ui[RB_P], acc[RB_P];
-        unsigned thr2[RB_P];          // the two outputs' thresholds (< 2^10 as R <= 32; 0 off grid)
+        X2Thr thr2;
         int tmax = -1, tmin = 1 << 30;
         // tile position of output (p = 0, columns xa, xb)
-        const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
+        const float *ua = su + (grp * RB_P + RM) * SX + 2 * threadIdx.x + RM;
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
             const int y = ybase + p;
             const bool oa = xa < n && y < n, ob = xb < n && y < n;
             const int ta = oa ? a.thr[xa + (int64_t)n * y] : -1;
             const int tb = ob ? a.thr[xb + (int64_t)n * y] : -1;
-            thr2[p] = (unsigned)max(ta, 0) | ((unsigned)max(tb, 0) << 16);
+            thr2.a[p] = max(ta, 0);
+            thr2.b[p] = max(tb, 0);
             tmax = max(tmax, max(ta, tb));
             tmin = min(tmin, min(oa ? ta : tmin, ob ? tb : tmin));
             ui[p] = ld_pair(ua + p * SX);
@@ -664,30 +701,40 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         }
         if (tmin == (1 << 30)) tmin = -1;
         const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-        for (int ox = -rx; ox <= rx; ++ox) {
+        const int ox_lo = half ? 0 : -rx, ox_hi = half ? rx : -1;
+        for (int ox = ox_lo; ox <= ox_hi; ++ox) {
             const int ox2 = ox * ox;
             if (ox2 > tmax) continue;
             const int hmax = min(R, isqrt_small(tmax - ox2));
             const int hmin = (tmin >= ox2) ? min(hmax, isqrt_small(tmin - ox2)) : -1;
-            const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
+            const float *gcol = sg + (ox + R) * (2 * R + 1) + R;       // |oy| <= R
             x2_column(acc, ui, thr2, ua + ox, SX * SY, SX, gcol, ox2, hmin, hmax);
         }
+        __syncthreads();               // every warp is done with the tile
+        f2_t *xs = sx + grp * RB_P * 32 + threadIdx.x;
+        if (half) {
 #pragma unroll
-        for (int p = 0; p < RB_P; ++p) {
-            const int y = ybase + p;
-            float s0, s1, u0, u1;
-            f2_unpack(acc[p], s0, s1);
-            f2_unpack(ui[p], u0, u1);
-            if (y < n && xa < n) {
-                const int64_t i = xa + (int64_t)n * y;
-                Lu[(int64_t)z * N + i] = finv[i] * (s0 - u0 * extv[i]);
-            }
-            if (y < n && xb < n) {
-                const int64_t i = xb + (int64_t)n * y;
-                Lu[(int64_t)z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+            for (int p = 0; p < RB_P; ++p) xs[p * 32] = acc[p];
+        }
+        __syncthreads();
+        if (!half) {
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) {
+                const int y = ybase + p;
+                float s0, s1, u0, u1;
+                f2_unpack(f2_add(acc[p], xs[p * 32]), s0, s1);
+                f2_unpack(ui[p], u0, u1);
+                if (y < n && xa < n) {
+                    const int64_t i = xa + (int64_t)n * y;
+                    Lu[(int64_t)z * N + i] = finv[i] * (s0 - u0 * extv[i]);
+                }
+                if (y < n && xb < n) {
+                    const int64_t i = xb + (int64_t)n * y;
+                    Lu[(int64_t)z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+                }
             }
         }
-        __syncthreads();               // the tile and s_item are reused by the next item
+        __syncthreads();               // the tile, the partial sums and s_item are reused
     }
     if (tid == 0) {
         __threadfence();
@@ -698,19 +745,21 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
 template <int RM, int TY>
 static size_t x2_smem_bytes()
 {
-    return sizeof(float) * (size_t)2 * (64 + 2 * RM) * (TY * RB_P + 2 * RM + 1);
+    return sizeof(float) * ((size_t)2 * (64 + 2 * RM) * (TY * RB_P + 2 * RM + 1) +
+                            (size_t)(2 * RM + 1) * (2 * RM + 1));
 }
 
-// kernel variants: (TY warps per tile, minimum resident blocks per SM for the register budget)
+// kernel variants: (TY row groups of 8 rows per tile, 2 TY warps per block; minimum resident
+// blocks per SM for the register budget)
 constexpr int X2_VARIANTS = 4;
-static const int x2_var_ty[X2_VARIANTS] = { 2, 2, 4, 4 };
+static const int x2_var_ty[X2_VARIANTS] = { 1, 1, 2, 2 };
 
 template <int RM, int TY, int MB>
 static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
                              int nrhs, const int *order, int ntiles, int *blocks_cache,
                              cudaStream_t st)
 {
-    const dim3 blk(32, TY, 1);
+    const dim3 blk(32, 2 * TY, 1);
     const size_t smem = x2_smem_bytes<RM, TY>();
     auto kern = k_direct2d_x2<RM, TY, MB>;
     NL_CUDA_TRY(prep_smem(kern, smem));
@@ -723,7 +772,7 @@ static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, fl
     if (items == 0) return NL_OK;
     if (*blocks_cache == 0) {
         int per_sm = 0, dev = 0, sms = 0;
-        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem));
+        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64 * TY, smem));
         NL_CUDA_TRY(cudaGetDevice(&dev));
         NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         *blocks_cache = (per_sm > 0 ? per_sm : 1) * sms;
@@ -741,10 +790,10 @@ static nl_status launch_x2_var(nl_plan *p, int var, const DirectArgs &a, const f
                                cudaStream_t st)
 {
     switch (var) {
-    case 0: return launch_x2_t<RM, 2, 8>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    case 1: return launch_x2_t<RM, 2, 5>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    case 2: return launch_x2_t<RM, 4, 4>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    default: return launch_x2_t<RM, 4, 3>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 0: return launch_x2_t<RM, 1, 6>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 1: return launch_x2_t<RM, 1, 8>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 2: return launch_x2_t<RM, 2, 3>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    default: return launch_x2_t<RM, 2, 4>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
     }
 }
 
@@ -1136,7 +1185,7 @@ k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restric
     const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
     const int zbase = z0 + threadIdx.y * RB_P;
     f2_t ui[RB_P], acc[RB_P];
-    unsigned thr2[RB_P];                                        // unused (no masked rows)
+    X2Thr thr2;                                                 // unused (no masked rows)
 #pragma unroll
     for (int p = 0; p < RB_P; ++p) {
         const int z = zbase + p;
@@ -1144,7 +1193,8 @@ k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restric
         const float vb = (xb < n && z < n) ? ur[xb + n * (y + (int64_t)n * z)] : 0.f;
         ui[p] = f2_pack(va, vb);
         acc[p] = f2_pack(0.f, 0.f);
-        thr2[p] = 0u;
+        thr2.a[p] = 0;
+        thr2.b[p] = 0;
     }
     const int gw = 2 * R + 1;
     const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
@@ -2146,16 +2196,20 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
     const int *var_ty = sym ? x2s_var_ty : x2_var_ty;
     NL_CUDA_TRY(cudaMalloc(&p->x2_queue, 2 * sizeof(int)));
     NL_CUDA_TRY(cudaMemsetAsync(p->x2_queue, 0, 2 * sizeof(int), st));
-    int *ord[2] = { nullptr, nullptr };              // orders for TY = 2 and TY = 4
+    // tile heights (row groups of 8) of the two kinds of variant: 1 and 2 row groups for
+    // k_direct2d_x2, 2 and 4 for k_direct2d_x2s
+    const int ty_k[2] = { sym ? 2 : 1, sym ? 4 : 2 };
+    int *ord[2] = { nullptr, nullptr };              // tile orders for ty_k[0] and ty_k[1]
     int nt[2] = { 0, 0 }, bc[X2_VARIANTS] = { 0, 0, 0, 0 };
     float ms[X2_VARIANTS] = { 0.f, 0.f, 0.f, 0.f };
     float *u = nullptr, *lu = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool tune = p->N <= ((int64_t)1 << 24);
     nl_status s = NL_OK;
-    for (int k = tune ? 0 : 1; k < 2 && s == NL_OK; ++k)
-        s = x2_order_for(p, k == 0 ? 2 : 4, &ord[k], &nt[k], st);
-    int best = sym ? 1 : 2;                           // TY = 4 (four blocks per SM)
+    // untuned (very large grids): x2s with TY = 4 (variant 1), x2 with TY = 1 (variant 0)
+    int best = sym ? 1 : 0;
+    for (int k = 0; k < 2 && s == NL_OK; ++k)
+        if (tune || ty_k[k] == var_ty[best]) s = x2_order_for(p, ty_k[k], &ord[k], &nt[k], st);
     if (s == NL_OK && tune) {
         const DirectArgs a = make_args(p, NL_F32);
         if (cudaMalloc(&u, p->N * sizeof(float)) != cudaSuccess ||
@@ -2165,14 +2219,14 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
             s = nl_cuda_fail(cudaErrorMemoryAllocation, "direct kernel tuning");
         }
         for (int v = 0; v < nvar && s == NL_OK; ++v) {
-            const int k = var_ty[v] == 2 ? 0 : 1;
+            const int k = var_ty[v] == ty_k[0] ? 0 : 1;
             auto run = [&]() {
                 return sym ? x2s_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st)
                            : x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
             };
             if ((s = run()) != NL_OK) break;
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 3 && s == NL_OK; ++r) s = run();
+            for (int r = 0; r < 5 && s == NL_OK; ++r) s = run();
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms[v], e0, e1);
@@ -2184,7 +2238,7 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
     if (lu) cudaFree(lu);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    const int kb = var_ty[best] == 2 ? 0 : 1;
+    const int kb = var_ty[best] == ty_k[0] ? 0 : 1;
     if (ord[1 - kb]) cudaFree(ord[1 - kb]);
     if (s != NL_OK) {
         if (ord[kb]) cudaFree(ord[kb]);
