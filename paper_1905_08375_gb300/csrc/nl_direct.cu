@@ -2153,6 +2153,36 @@ nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, 
 }
 
 // ---------------------------------------------------------------------------
+// plan-time variant timing: TUNE_ROUNDS rounds over all variants (one untimed launch, then
+// TUNE_REPS timed back to back); a variant's time is its fastest round, so one slow round
+// (another process on the GPU, a clock change) does not decide the choice.  run(v) launches
+// variant v once; ms[v] receives its time.
+// ---------------------------------------------------------------------------
+constexpr int TUNE_ROUNDS = 3, TUNE_REPS = 3;
+
+template <typename Run>
+static nl_status time_variants(int nvar, Run run, float *ms, cudaEvent_t e0, cudaEvent_t e1,
+                               cudaStream_t st)
+{
+    for (int v = 0; v < nvar; ++v) ms[v] = 3.0e38f;
+    for (int r = 0; r < TUNE_ROUNDS; ++r) {
+        for (int v = 0; v < nvar; ++v) {
+            nl_status s = run(v);
+            if (s != NL_OK) return s;
+            NL_CUDA_TRY(cudaEventRecord(e0, st));
+            for (int k = 0; k < TUNE_REPS; ++k)
+                if ((s = run(v)) != NL_OK) return s;
+            NL_CUDA_TRY(cudaEventRecord(e1, st));
+            NL_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            NL_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            ms[v] = fminf(ms[v], t);
+        }
+    }
+    return NL_OK;
+}
+
+// ---------------------------------------------------------------------------
 // plan-time set-up of the paired-column FP32 kernel: the tile queue and its orders, and the
 // kernel variant (tile height and register budget) chosen by timing each on the plan itself
 // ---------------------------------------------------------------------------
@@ -2169,17 +2199,12 @@ static nl_status x3_tune(nl_plan *p, cudaStream_t st)
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaMemsetAsync(u, 0, p->N * sizeof(float), st) != cudaSuccess)
         s = nl_cuda_fail(cudaErrorMemoryAllocation, "3-D kernel tuning");
-    float best = 1e30f;
-    for (int v = 0; v < X3_VARIANTS && s == NL_OK; ++v) {
-        if ((s = launch_3d_x2(p, a, u, lu, 1, st, v)) != NL_OK) break;
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && s == NL_OK; ++r) s = launch_3d_x2(p, a, u, lu, 1, st, v);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; p->x3_var = v; }
-    }
+    float ms[X3_VARIANTS];
+    if (s == NL_OK)
+        s = time_variants(X3_VARIANTS, [&](int v) { return launch_3d_x2(p, a, u, lu, 1, st, v); },
+                          ms, e0, e1, st);
+    if (s == NL_OK)
+        for (int v = 1; v < X3_VARIANTS; ++v) if (ms[v] < ms[p->x3_var]) p->x3_var = v;
     if (u) cudaFree(u);
     if (lu) cudaFree(lu);
     if (e0) cudaEventDestroy(e0);
@@ -2218,19 +2243,12 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
             cudaMemsetAsync(u, 0, p->N * sizeof(float), st) != cudaSuccess) {
             s = nl_cuda_fail(cudaErrorMemoryAllocation, "direct kernel tuning");
         }
-        for (int v = 0; v < nvar && s == NL_OK; ++v) {
+        auto run = [&](int v) {
             const int k = var_ty[v] == ty_k[0] ? 0 : 1;
-            auto run = [&]() {
-                return sym ? x2s_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st)
-                           : x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
-            };
-            if ((s = run()) != NL_OK) break;
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 5 && s == NL_OK; ++r) s = run();
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&ms[v], e0, e1);
-        }
+            return sym ? x2s_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st)
+                       : x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
+        };
+        if (s == NL_OK) s = time_variants(nvar, run, ms, e0, e1, st);
         best = 0;
         for (int v = 1; v < nvar; ++v) if (ms[v] < ms[best]) best = v;
     }
