@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <mutex>
 #include <vector>
+#include <type_traits>
 
 #include "nl_internal.cuh"
 
@@ -620,6 +621,93 @@ __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB
     }
 }
 
+// rows oy .. oy + NJ - 1 (NJ <= 4, weights g4) for the RB_P (= 8) outputs, every output
+// inside its ball; the window is (G0, G1) = rows oy .. oy + 7 and G2 holds rows oy + 8 ..
+// oy + NJ + 6
+template <int NJ>
+__device__ __forceinline__ void x2_chunk_full(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                              const X2Grp &G0, const X2Grp &G1, const X2Grp &G2,
+                                              const float (&g4)[4])
+{
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const float g = g4[j];
+        const f2_t gg = f2_pack(g, g);
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int k = p + j;
+            const X2Grp &G = k < 4 ? G0 : (k < 8 ? G1 : G2);
+            acc[p] = f2_fma(f2_mul(G.b[k & 3], gg), f2_sub(G.u[k & 3], ui[p]), acc[p]);
+        }
+    }
+}
+
+// the first NR rows (row .. row + NR - 1) of a group
+template <int NR>
+__device__ __forceinline__ void x2_load_rows(X2Grp &g, const float *cu, int plane, int SX, int row)
+{
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        g.u[k] = ld_pair(cu + (row + k) * SX);
+        g.b[k] = ld_pair(cu + (row + k) * SX + plane);
+    }
+}
+
+// one column offset whose rows -h .. h are inside every output's ball (constant horizon): the
+// rows in increasing order in chunks of four, the three row groups rotated, each chunk's
+// weights loaded one chunk ahead, then the last 0..3 rows as one short chunk (no per-row
+// window shifts).  Tile rows read: -h .. h + 7 (relative to the thread's first output).
+__device__ __forceinline__ void x2_column_full(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                               const float *cu, int plane, int SX,
+                                               const float *gcol, int h)
+{
+    X2Grp G0, G1, G2;
+    int oy = -h, rem = 2 * h + 1;
+    x2_load_grp(G0, cu, plane, SX, oy);
+    x2_load_grp(G1, cu, plane, SX, oy + 4);
+    float gc[4], gn[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gc[j] = gcol[min(oy + j, h)];
+    auto next_g = [&]() {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gn[j] = gcol[min(oy + 4 + j, h)];
+    };
+    auto rotate_g = [&]() {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gc[j] = gn[j];
+    };
+    for (;;) {
+        if (rem < 4) break;
+        x2_load_grp(G2, cu, plane, SX, oy + 8);
+        next_g();
+        x2_chunk_full<4>(acc, ui, G0, G1, G2, gc);
+        rotate_g();
+        oy += 4; rem -= 4;                      // the window is (G1, G2)
+        if (rem < 4) { G0 = G1; G1 = G2; break; }
+        x2_load_grp(G0, cu, plane, SX, oy + 8);
+        next_g();
+        x2_chunk_full<4>(acc, ui, G1, G2, G0, gc);
+        rotate_g();
+        oy += 4; rem -= 4;                      // the window is (G2, G0)
+        if (rem < 4) { G1 = G0; G0 = G2; break; }
+        x2_load_grp(G1, cu, plane, SX, oy + 8);
+        next_g();
+        x2_chunk_full<4>(acc, ui, G2, G0, G1, gc);
+        rotate_g();
+        oy += 4; rem -= 4;                      // the window is (G0, G1) again
+    }
+    // the last rem rows oy .. h: G2 needs rows oy + 8 .. h + 7 only
+    if (rem == 3) {
+        x2_load_rows<2>(G2, cu, plane, SX, oy + 8);
+        x2_chunk_full<3>(acc, ui, G0, G1, G2, gc);
+    } else if (rem == 2) {
+        x2_load_rows<1>(G2, cu, plane, SX, oy + 8);
+        x2_chunk_full<2>(acc, ui, G0, G1, G2, gc);
+    } else if (rem == 1) {
+        x2_chunk_full<1>(acc, ui, G0, G1, G2, gc);
+    }
+}
+
 // RM: compile-time halo (>= the plan's largest radius) so that the tile geometry is constant.
 // Persistent: each block takes 64 x (TY * RB_P) tiles (times right-hand sides) from a queue
 // ordered by decreasing cost (the sum of the tile's ball sizes, largest first); the last
@@ -1185,7 +1273,6 @@ k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restric
     const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
     const int zbase = z0 + threadIdx.y * RB_P;
     f2_t ui[RB_P], acc[RB_P];
-    X2Thr thr2;                                                 // unused (no masked rows)
 #pragma unroll
     for (int p = 0; p < RB_P; ++p) {
         const int z = zbase + p;
@@ -1193,8 +1280,6 @@ k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restric
         const float vb = (xb < n && z < n) ? ur[xb + n * (y + (int64_t)n * z)] : 0.f;
         ui[p] = f2_pack(va, vb);
         acc[p] = f2_pack(0.f, 0.f);
-        thr2.a[p] = 0;
-        thr2.b[p] = 0;
     }
     const int gw = 2 * R + 1;
     const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
@@ -1221,7 +1306,7 @@ k_direct3d_x2(DirectArgs a, const float *__restrict__ g3, const float *__restric
             if (ox2 > t2) continue;
             const int h = min(R, isqrt_small(t2 - ox2));
             const float *gcol = g3 + ((oy + R) * gw + (ox + R)) * gw + R;   // oz at gcol[oz]
-            x2_column(acc, ui, thr2, ua + ox, PL, SX, gcol, ox2, h, h);
+            x2_column_full(acc, ui, ua + ox, PL, SX, gcol, h);
         }
     }
     const float *__restrict__ finv = (const float *)a.fin;
