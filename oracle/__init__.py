@@ -7,7 +7,9 @@ and the two share no code: this package holds its own C source
 (``nl_oracle.c``), its own constants and its own polynomial solver, written
 from the paper (Tian & Engquist, arXiv 1905.08375):
 
-* ``direct_scalar``  -- Eq. (2.1)-(2.2), nodal Riemann sum over the open ball.
+* ``direct_scalar``  -- Eq. (2.1)-(2.2), nodal Riemann sum over the open ball, for the
+  profiles s^-alpha (POWER), p^{2K} (POLY) and the Sec. 3 splitting remainder
+  kappa = s^-alpha - p^{2K} (KAPPA).
 * ``pd_direct``      -- Eq. (1.1)-(1.2), linear bond-based peridynamics.
 * ``fast_tree``      -- Sec. 3: Algorithm 1 (recur) with Algorithm 2, the Step 2
   moment pyramid and the Step 3 sum of Eq. (3.5), then Eq. (3.3).
@@ -36,7 +38,7 @@ _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _SRC = os.path.join(_HERE, "nl_oracle.c")
 
-POWER, POLY = 0, 1
+POWER, POLY, KAPPA = 0, 1, 2   # KAPPA: kappa = s^-alpha - p^{2K} (Sec. 3 splitting)
 COEF_NONE, COEF_X, COEF_XY = 0, 1, 2
 SELF_DISCRETE, SELF_PAPER = 0, 1
 
@@ -147,7 +149,7 @@ def direct_scalar(u, d, n, delta, family=POWER, alpha=0.0, K=0, scale=1.0, norma
     u2 = u.reshape(1, -1) if squeeze else u.reshape(u.shape[0], -1)
     nrhs = u2.shape[0]
     dl = _delta_field(delta, d, n)
-    p = poly_coeffs(K, alpha) if family == POLY else np.zeros(1)
+    p = poly_coeffs(K, alpha) if family in (POLY, KAPPA) else np.zeros(1)
     sg = sigma(d, alpha, scale, normalize)
     a_ = None if a is None else _f64(a).reshape(-1)
     ix, nix = _idx(idx)
@@ -164,7 +166,7 @@ def direct_diag(d, n, delta, family=POWER, alpha=0.0, K=0, scale=1.0, normalize=
                 coef=COEF_NONE, a=None, symmetric=False):
     """Diagonal of -L (h^d sum_j w_ij c_ij)."""
     dl = _delta_field(delta, d, n)
-    p = poly_coeffs(K, alpha) if family == POLY else np.zeros(1)
+    p = poly_coeffs(K, alpha) if family in (POLY, KAPPA) else np.zeros(1)
     sg = sigma(d, alpha, scale, normalize)
     a_ = None if a is None else _f64(a).reshape(-1)
     out = np.zeros(n ** d)
@@ -271,7 +273,7 @@ def cg(f, d, n, delta, kind="scalar", family=POWER, alpha=0.0, K=0, scale=1.0, n
     f = _f64(f).reshape(-1)
     dl = _delta_field(delta, d, n)
     k = 0 if kind == "scalar" else 1
-    p = poly_coeffs(K, alpha) if family == POLY else np.zeros(1)
+    p = poly_coeffs(K, alpha) if family in (POLY, KAPPA) else np.zeros(1)
     sg = sigma(d, alpha, scale, normalize) if k == 0 else float(scale)
     a_ = None if a is None else _f64(a).reshape(-1)
     c_ = None if c is None else _delta_field(c, d, n)

@@ -10,7 +10,8 @@
  *   Eq. (2.1)  nonlocal diffusion  L u(x) = int_{H_x} w(x,y) (u(y)-u(x)) dy
  *   Eq. (2.2)  kernel  w = C(x,y) / delta^{d+2} * gamma(|y-x| / delta)
  *   Eq. (1.2)  linear bond force  f = w(x,y) [e.(u(y)-u(x))] e
- *   Sec. 3     splitting gamma = kappa + p^{2K} chi, Hermite-matched p^{2K}
+ *   Sec. 3     splitting gamma = kappa + p^{2K} chi, Hermite-matched p^{2K}; the direct
+ *              sum serves all three profiles (gamma, kappa and p^{2K})
  *   Eq. (3.1)  volume constraint u = 0 outside Omega = [0,1]^d
  *   Eq. (3.3)  L^P u = C/delta^{d+2} ( int_{H_x cap Omega} u - |H_x| u(x) )
  *   Algorithm 1 (recur), Algorithm 2 (cube/ball test), Steps 1-3, Eq. (3.5)
@@ -40,7 +41,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-enum { OR_POWER = 0, OR_POLY = 1 };
+enum { OR_POWER = 0, OR_POLY = 1, OR_KAPPA = 2 };
 enum { OR_COEF_NONE = 0, OR_COEF_X = 1, OR_COEF_XY = 2 };
 enum { OR_SELF_DISCRETE = 0, OR_SELF_PAPER = 1 };
 
@@ -137,12 +138,15 @@ int or_poly_coeffs(int K, double alpha, double *p)
     return 0;
 }
 
-/* Radial profile gamma(s) of Eq. (2.2): s^{-alpha} (POWER) or p^{2K}(s). */
+/* Radial profile gamma(s) of Eq. (2.2) for 0 < s < 1: s^{-alpha} (POWER), p^{2K}(s) (POLY), or
+ * the other part of the splitting of Sec. 3, gamma = kappa + p^{2K} chi:
+ * kappa(s) = s^{-alpha} - p^{2K}(s) (KAPPA). */
 static double profile(int family, double alpha, int K, const double *p, double s)
 {
     if (family == OR_POWER) return pow(s, -alpha);
     double r = 0.0, s2 = s * s, sp = 1.0;
     for (int m = 0; m <= K; ++m) { r += p[m] * sp; sp *= s2; }
+    if (family == OR_KAPPA) return pow(s, -alpha) - r;
     return r;
 }
 
