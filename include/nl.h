@@ -61,8 +61,12 @@ typedef enum { NL_F32 = 0, NL_F64 = 1 } nl_dtype;
  *               matches s^{-alpha} and its first K derivatives at s = 1
  *               (the splitting of Sec. 3; K = 0 gives p = 1)
  *   NL_PD_BOND: linear peridynamic bond, micromodulus sigma c_ij / |xi|
- *               (Eq. (1.2)); u and Lu then hold d component planes. */
-typedef enum { NL_POWER = 0, NL_POLY = 1, NL_PD_BOND = 2 } nl_family;
+ *               (Eq. (1.2)); u and Lu then hold d component planes.
+ *   NL_KAPPA:   gamma(s) = kappa(s) = s^{-alpha} - p^{2K}(s), the other part of the
+ *               splitting of Sec. 3 (s^{-alpha} chi = kappa + p^{2K} chi): singular at
+ *               s = 0, C^K at the horizon.  nl_apply only (the direct sum, any d); with the
+ *               same sigma, the NL_POWER result is the NL_KAPPA one plus the NL_POLY one. */
+typedef enum { NL_POWER = 0, NL_POLY = 1, NL_PD_BOND = 2, NL_KAPPA = 3 } nl_family;
 
 /* Coefficient C(x,y) of Eq. (2.2) built from the node field `a`:
  *   NL_COEF_NONE: C = 1
@@ -109,8 +113,9 @@ typedef struct {
 
 typedef struct {
     int family;        /* nl_family */
-    double alpha;      /* exponent of s^{-alpha} (NL_POWER) or of the matched profile (NL_POLY) */
-    int K;             /* polynomial order for NL_POLY, 0..3 */
+    double alpha;      /* exponent of s^{-alpha} (NL_POWER, NL_KAPPA) or of the matched
+                          profile (NL_POLY) */
+    int K;             /* polynomial order for NL_POLY and NL_KAPPA, 0..3 */
     double scale;      /* multiplies sigma */
     int normalize;     /* 1: sigma = scale 2d(d+2-alpha)/|S^{d-1}| (L -> Laplacian);
                           0: sigma = scale.  Ignored for NL_PD_BOND (sigma = scale). */

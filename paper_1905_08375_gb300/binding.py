@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libnl.so")
 
 NL_OK, NL_EINVAL, NL_EUNSUPPORTED, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT = range(7)
 NL_F32, NL_F64 = 0, 1
-NL_POWER, NL_POLY, NL_PD_BOND = 0, 1, 2
+NL_POWER, NL_POLY, NL_PD_BOND, NL_KAPPA = 0, 1, 2, 3
 NL_COEF_NONE, NL_COEF_X, NL_COEF_XY, NL_COEF_MEAN = 0, 1, 2, 3
 NL_SELF_DISCRETE, NL_SELF_PAPER = 0, 1
 NL_FAST_AUTO, NL_FAST_PANELS, NL_FAST_ROWPREFIX, NL_FAST_FP64_PANELS, NL_FAST_LEAFROWS = 0, 1, 2, 3, 4

@@ -39,7 +39,8 @@ struct DirectArgs {
     const float *pdg;         // PD, constant horizon: dense [2R+1][2R+1][3] bond tensors
 };
 
-enum { MODE_POWER = 0, MODE_POLY = 1, MODE_SYM = 2 };
+// MODE_KAPPA: the kappa part of the splitting of Sec. 3, weight ra_i |o|^{-alpha} - p(|o|^2/R2_i)
+enum { MODE_POWER = 0, MODE_POLY = 1, MODE_SYM = 2, MODE_KAPPA = 3 };
 
 template <int D>
 __device__ __forceinline__ void block_origin(int n, int &x0, int &y0, int &z0)
@@ -136,8 +137,9 @@ k_direct_scalar(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
     }
     T ir = T(0), whi = T(0);
     int thri = 0;
-    if constexpr (MODE == MODE_POLY) ir = ((const T *)a.ir)[i];
+    if constexpr (MODE == MODE_POLY || MODE == MODE_KAPPA) ir = ((const T *)a.ir)[i];
     if constexpr (MODE == MODE_SYM) { whi = whv[i]; thri = a.thr[i]; }
+    if constexpr (MODE == MODE_KAPPA) whi = whv[i];           // ra_i = (delta_i / h)^alpha
 
     T acc0 = T(0), acc1 = T(0);
 #pragma unroll 2
@@ -165,6 +167,8 @@ k_direct_scalar(DirectArgs a, const T *__restrict__ u, T *__restrict__ Lu)
             w = (T)en.g * bj;
         } else if constexpr (MODE == MODE_POLY) {
             w = poly_weight<T>(a.poly, a.K, (T)en.o2 * ir) * bj;
+        } else if constexpr (MODE == MODE_KAPPA) {
+            w = ((T)en.g * whi - poly_weight<T>(a.poly, a.K, (T)en.o2 * ir)) * bj;
         } else {
             const T wi = (en.o2 <= thri) ? whi : T(0);
             const T wj = (en.o2 <= thrj) ? whj : T(0);
@@ -1400,8 +1404,8 @@ __global__ void __launch_bounds__(256) k_direct_split(DirectArgs a, const T *__r
         const int z = D > 2 ? (int)(i / ((int64_t)n * n)) : 0;
         ui = ur[i];
         const int cnt = a.cnt[i];
-        const T ir = (MODE == MODE_POLY) ? ((const T *)a.ir)[i] : T(0);
-        const T whi = (MODE == MODE_SYM) ? whv[i] : T(0);
+        const T ir = (MODE == MODE_POLY || MODE == MODE_KAPPA) ? ((const T *)a.ir)[i] : T(0);
+        const T whi = (MODE == MODE_SYM || MODE == MODE_KAPPA) ? whv[i] : T(0);
         const int thri = a.thr[i];
         for (int t = lane; t < cnt; t += SPLIT) {
             const int4 o = a.off[t];
@@ -1415,6 +1419,8 @@ __global__ void __launch_bounds__(256) k_direct_split(DirectArgs a, const T *__r
                 w = (T)en.g * bj;
             } else if constexpr (MODE == MODE_POLY) {
                 w = poly_weight<T>(a.poly, a.K, (T)en.o2 * ir) * bj;
+            } else if constexpr (MODE == MODE_KAPPA) {
+                w = ((T)en.g * whi - poly_weight<T>(a.poly, a.K, (T)en.o2 * ir)) * bj;
             } else {
                 const T wi = (en.o2 <= thri) ? whi : T(0);
                 const T wj = (en.o2 <= a.thr[j]) ? whv[j] : T(0);
@@ -1685,13 +1691,16 @@ template <typename T>
 static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *Lu, int nrhs,
                                cudaStream_t st, size_t smem)
 {
-    const int mode = p->symmetric ? MODE_SYM : (p->family == NL_POLY ? MODE_POLY : MODE_POWER);
+    const int mode = p->symmetric ? MODE_SYM
+                   : (p->family == NL_POLY ? MODE_POLY
+                      : (p->family == NL_KAPPA ? MODE_KAPPA : MODE_POWER));
     // few nodes with large balls: split each node's ball over a group of lanes
     if (p->N * nrhs < 32 * 1024 && p->num_off >= 64 && nrhs <= 65535) {
 #define NL_SPLIT(D)                                                                                \
         do {                                                                                       \
             if (mode == MODE_POWER) return launch_split<D, T, MODE_POWER>(p, a, u, Lu, nrhs, st); \
             if (mode == MODE_POLY) return launch_split<D, T, MODE_POLY>(p, a, u, Lu, nrhs, st);   \
+            if (mode == MODE_KAPPA) return launch_split<D, T, MODE_KAPPA>(p, a, u, Lu, nrhs, st); \
             return launch_split<D, T, MODE_SYM>(p, a, u, Lu, nrhs, st);                           \
         } while (0)
         if (p->d == 1) NL_SPLIT(1);
@@ -1719,6 +1728,7 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
     do {                                                                                     \
         if (mode == MODE_POWER) return launch_scalar_t<D, T, MODE_POWER>(p, a, u, Lu, nrhs, st, smem); \
         if (mode == MODE_POLY) return launch_scalar_t<D, T, MODE_POLY>(p, a, u, Lu, nrhs, st, smem);   \
+        if (mode == MODE_KAPPA) return launch_scalar_t<D, T, MODE_KAPPA>(p, a, u, Lu, nrhs, st, smem); \
         return launch_scalar_t<D, T, MODE_SYM>(p, a, u, Lu, nrhs, st, smem);                 \
     } while (0)
     if (p->d == 1) NL_DISPATCH_MODE(1);

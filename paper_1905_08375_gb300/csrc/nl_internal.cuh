@@ -106,7 +106,7 @@ struct nl_plan {
     float *b32;   double *b64;     // summed coefficient b_j (a_j or 1)
     float *fin32; double *fin64;   // final factor
     float *ext32; double *ext64;   // exterior coefficient
-    float *wh32;  double *wh64;    // W_i / 2 (symmetric variant)
+    float *wh32;  double *wh64;    // W_i / 2 (symmetric variant); (delta_i/h)^alpha (NL_KAPPA)
     float *ir32;  double *ir64;    // 1 / R2_i (polynomial kernels)
     // offset tables
     int4 *off;                      // (dx, dy, dz, o2)

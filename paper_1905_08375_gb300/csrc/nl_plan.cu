@@ -131,6 +131,8 @@ __global__ void k_window_max(PlanArgs a, const int *__restrict__ thr, int *thr_w
 //   Lu_i = fin_i (sum_o wgt(o) (u_j - u_i) - u_i ext_i)
 // POWER:  W_i = sigma h^{d-alpha} delta_i^{alpha-d-2},  g(o) = |o|^{-alpha}
 // POLY:   W_i = sigma h^d delta_i^{-(d+2)},             g_i(o) = p(|o|^2 / R2_i)
+// KAPPA:  W_i = sigma h^d delta_i^{-(d+2)},             g_i(o) = ra_i |o|^{-alpha} - p(|o|^2 / R2_i)
+//         with ra_i = (delta_i / h)^alpha = R2_i^{alpha/2}, stored in the wh arrays
 // one-sided: fin = A_i W_i, ext = b_ext E_i;  symmetric: fin = b_i, ext = b_i W_i E_i,
 // with E_i = sum of g over the ball offsets whose node lies outside Omega.
 __global__ void k_node_factors(PlanArgs a, const double *__restrict__ delta,
@@ -178,7 +180,10 @@ __global__ void k_node_factors(PlanArgs a, const double *__restrict__ delta,
             if (a.d > 1) out = out || (c[1] + o.y < 0) || (c[1] + o.y >= a.n);
             if (a.d > 2) out = out || (c[2] + o.z < 0) || (c[2] + o.z >= a.n);
             if (!out) continue;
-            E += (a.family == NL_POWER) ? gtab[t] : poly_eval_t(a.poly, a.K, o.w / R2);
+            if (a.family == NL_POWER) E += gtab[t];
+            else if (a.family == NL_KAPPA)
+                E += pow(R2, 0.5 * a.alpha) * gtab[t] - poly_eval_t(a.poly, a.K, o.w / R2);
+            else E += poly_eval_t(a.poly, a.K, o.w / R2);
         }
     }
     double fin, ext, wh = 0.0;
@@ -189,6 +194,7 @@ __global__ void k_node_factors(PlanArgs a, const double *__restrict__ delta,
     } else {
         fin = Ai * W;
         ext = bi * E;
+        if (a.family == NL_KAPPA) wh = pow(R2, 0.5 * a.alpha);
     }
     b32[i] = (float)bi; b64[i] = bi;
     fin32[i] = (float)fin; fin64[i] = fin;
@@ -283,7 +289,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         nl_set_error("nl_plan_create: dim must be 1..3 and n >= 1 (got dim=%d n=%d)", d, n);
         return NL_EINVAL;
     }
-    if (k->family < NL_POWER || k->family > NL_PD_BOND) {
+    if (k->family < NL_POWER || k->family > NL_KAPPA) {
         nl_set_error("nl_plan_create: unknown kernel family %d", k->family);
         return NL_EINVAL;
     }
@@ -295,7 +301,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         nl_set_error("nl_plan_create: coefficient mode %d needs the field a", k->coef);
         return NL_EINVAL;
     }
-    if (k->family == NL_POLY && (k->K < 0 || k->K > 3)) {
+    if ((k->family == NL_POLY || k->family == NL_KAPPA) && (k->K < 0 || k->K > 3)) {
         nl_set_error("nl_plan_create: K must be 0..3 (got %d)", k->K);
         return NL_EINVAL;
     }
@@ -368,7 +374,8 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     p->L = -1;
     for (int l = 0; l <= NL_MAX_LEVELS; ++l) if ((1 << l) == n) p->L = l;
     p->family = k->family; p->coef = k->coef; p->symmetric = hz->symmetric ? 1 : 0;
-    p->self_mode = k->self_term; p->K = (k->family == NL_POLY) ? k->K : 0;
+    p->self_mode = k->self_term;
+    p->K = (k->family == NL_POLY || k->family == NL_KAPPA) ? k->K : 0;
     if (k->fast_variant < NL_FAST_AUTO || k->fast_variant > NL_FAST_LEAFROWS) {
         nl_set_error("nl_plan_create: unknown fast variant %d", k->fast_variant);
         free(p);
@@ -380,7 +387,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         p->sigma = k->scale;
     else
         p->sigma = k->scale * 2.0 * d * (d + 2.0 - k->alpha) / unit_sphere_measure(d);
-    if (k->family == NL_POLY) hermite_poly(p->K, k->alpha, p->poly);
+    if (k->family == NL_POLY || k->family == NL_KAPPA) hermite_poly(p->K, k->alpha, p->poly);
     p->Rmax = Rmax;
     p->thr_max = (int)thr_max;
     p->const_horizon = 1;
@@ -431,7 +438,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     p->smem_bytes32 = tile_elems * e32;
     p->smem_bytes64 = tile_elems * e64;
     p->stage = (p->smem_bytes64 <= 200 * 1024) ? 1 : 0;
-    if (d == 2 && k->family != NL_PD_BOND) {
+    if (d == 2 && k->family != NL_PD_BOND && k->family != NL_KAPPA) {
         // register-blocked kernel: (32 + 2R) x (32 + 2R + 8) tile + (2R+1)^2 weights
         const size_t t = (size_t)(32 + 2 * B) * (32 + 2 * B + 8);
         const size_t gw = (size_t)(2 * B + 1) * (2 * B + 1);
@@ -450,7 +457,8 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     for (size_t t = 0; t < offs.size(); ++t) {
         const int4 o = offs[t];
         int soff = o.x + p->tile_sx * (o.y + p->tile_sy * o.z);
-        double g = (k->family == NL_POWER) ? std::pow((double)o.w, -k->alpha / 2.0) : 0.0;
+        double g = (k->family == NL_POWER || k->family == NL_KAPPA)
+                       ? std::pow((double)o.w, -k->alpha / 2.0) : 0.0;
         g64[t] = g;
         t32[t] = OffEntry32{ soff, o.w, (float)g, 0 };
         t64[t] = OffEntry64{ soff, o.w, g };
