@@ -6,7 +6,8 @@ delta = h (4 + 12 s), lognormal coefficient a(x) a(y), Gaussian random field u)
   * one fast apply    (nl_apply_fast, the Sec. 3 algorithm with p^0 = 1, same fields);
 value = grid points processed per second over both applies (2 N per step), Gpts/s.
 
-Other workloads (--workload): c1 1-D FP64 direct (4096 nodes); c3 2-D peridynamics 512^2
+Other workloads (--workload): c1 1-D FP64 direct (4096 nodes); c2k the kappa part of the
+Sec. 3 splitting (kappa = s^-1.5 - p^2, direct FP32) on the c2 fields; c3 2-D peridynamics 512^2
 FP32; c3b batched Jacobi-CG to 1e-8 over 64 uneven peridynamic instances 128^2..512^2 (the
 operator one persistent launch over all instances; time per solve); c4 (c4_512) CG to
 relative residual 1e-8 on 256^2 (512^2), 8 right-hand sides, with the learned two-level
@@ -293,6 +294,69 @@ class C2(Workload):
         return {"direct": d, "fast": fs}, 2 * len(idx)
 
 
+class C2K(Workload):
+    """The kappa part of the splitting of Sec. 3 on the 2-D heterogeneous 1024^2 fields: one
+    direct FP32 apply with kappa(s) = s^-1.5 - p^2(s) (K = 1) per step."""
+    name = "c2k"
+    metric = ("L_delta u kappa-part direct apply (Sec. 3 splitting, K=1) in Gpts/s on the 2-D "
+              "heterogeneous 1024^2 grid")
+
+    def setup(self, n=1024):
+        nl, torch = self.nl, self.torch
+        from paper_1905_08375_gb300 import synth
+        self.n = n
+        self.f = synth.heterogeneous_2d(n=n, seed=self.seed)
+        f = self.f
+        self.plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_KAPPA, alpha=1.5, K=1,
+                                      coef=nl.NL_COEF_XY, a=f["a"])
+        self.u = torch.tensor(f["u"][0], dtype=torch.float32, device=self.dev)
+        self.out = torch.empty_like(self.u)
+        self.units = n * n
+        self.launches = 1
+        self.config = {"workload": "2D heterogeneous nonlocal diffusion 1024x1024, "
+                                   "delta=h(4+12s), a lognormal sigma 0.5 smoothed 8h, "
+                                   "kappa(s)=s^-1.5-(7/4-3/4 s^2) inside the ball (the Sec. 3 "
+                                   "splitting remainder, K=1), C=a(x)a(y); direct FP32 apply",
+                       "n": n, "points": n * n}
+
+    def step(self):
+        self.nl.nl_apply(self.plan, self.u, self.out)
+
+    def kernels(self, flush, reps):
+        t = self.time_fn(self.step, reps, flush)
+        nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
+        # per term: t = o2/R2, p = p0 + p1 t, ra g - p, times b_j, u_j - u_i, times, add
+        roof = _alu_roof("k_direct_scalar<2,float,KAPPA> (staged tile)", 9.0 * nb, t,
+                         FP32_PEAK_TFLOPS, FP32_SRC)
+        roof["algorithmic_per_launch"] = f"{9 * nb:.4g} flop (9 per neighbour term)"
+        return roof, {"kappa_direct_fp32_ms": round(t, 4)}
+
+    def e2e(self, flush, steps):
+        torch = self.torch
+        N = self.n * self.n
+        uh = torch.tensor(self.f["u"][0], dtype=torch.float32).pin_memory()
+        rh = torch.empty(N, dtype=torch.float32).pin_memory()
+        ud = torch.empty_like(self.u)
+
+        def one():
+            ud.copy_(uh, non_blocking=True)
+            self.nl.nl_apply(self.plan, ud, self.out)
+            rh.copy_(self.out, non_blocking=True)
+        ms = self.time_fn(one, steps, flush)
+        return {"value": round(self.value(ms), 4), "unit": self.unit, "h2d_bytes_per_step": N * 4,
+                "d2h_bytes_per_step": N * 4, "ms_per_step": round(ms, 4)}
+
+    def outputs(self):
+        return {"kappa": self.out.double().cpu().numpy()}
+
+    @staticmethod
+    def oracle_step(f, n, idx):
+        import oracle
+        return {"kappa": oracle.direct_scalar(f["u"][0], 2, n, f["delta"], family=oracle.KAPPA,
+                                              alpha=1.5, K=1, coef=oracle.COEF_XY, a=f["a"],
+                                              idx=idx)}, len(idx)
+
+
 class C1(Workload):
     name = "c1"
     metric = "1-D nonlocal diffusion direct apply (FP64) in Gpts/s, N=4096, delta=0.05"
@@ -574,9 +638,11 @@ class C4(Workload):
         t_net8 = self.time_fn(lambda: nl.nl_net_apply(self.net, self.plan, r8, z8), reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         self.launches = None
-        roof = _alu_roof("k_direct2d_rb<float,SYM,2> (CG operator)", 6.0 * nb, t,
-                         FP32_PEAK_TFLOPS, FP32_SRC)
-        roof["algorithmic_per_launch"] = f"{6 * nb:.4g} flop (6 per one-sided ball term)"
+        # the operator as CG applies it: all right-hand sides in one launch
+        roof = _alu_roof(f"k_direct2d_x2s (symmetric CG operator, {self.nrhs} RHS)",
+                         6.0 * nb * self.nrhs, t_op8, FP32_PEAK_TFLOPS, FP32_SRC)
+        roof["algorithmic_per_launch"] = (f"{6 * nb * self.nrhs:.4g} flop (6 per one-sided ball "
+                                          f"term, {self.nrhs} RHS)")
         self.solve(nl.NL_PRECOND_LEARNED)          # leave the learned solution in x
         return roof, {"learned_ms": round(t_l, 3), "learned": self.last,
                       "jacobi_ms": round(t_j, 3), "jacobi": sj,
@@ -752,7 +818,7 @@ class EX(Workload):
 def make_workload(name, dev, seed):
     if name in ("ex1", "ex2"):
         return EX(dev, seed, name)
-    return {"c1": C1, "c2": C2, "c3": C3, "c3b": C3B, "c4": C4, "c4_512": C4L,
+    return {"c1": C1, "c2": C2, "c2k": C2K, "c3": C3, "c3b": C3B, "c4": C4, "c4_512": C4L,
             "c5": C5}[name](dev, seed)
 
 
@@ -849,7 +915,7 @@ def oracle_sample(w, outs, budget_s=20.0):
         return ({"value": round(2 * m / dt / 1e9, 9), "unit": "Gpts/s",
                  "cores": oracle.num_threads(), "kind": "oracle",
                  "sample": f"{m} nodes, direct + literal tree algorithm ({dt:.1f} s)"}, par)
-    # c1, c2, c3: grow a random node sample to fill the budget
+    # c1, c2, c2k, c3: grow a random node sample to fill the budget
     cls = type(w)
     f, n = w.f, w.n
     d = 1 if name == "c1" else 2
@@ -983,7 +1049,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c3b", "c4", "c4_512", "c5", "ex1", "ex2"])
+                    choices=["c1", "c2", "c2k", "c3", "c3b", "c4", "c4_512", "c5", "ex1",
+                             "ex2"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--size", type=int, default=0,
                     help="grid size override for c5 (a smaller case for profiling captures)")
