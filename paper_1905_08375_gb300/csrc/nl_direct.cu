@@ -1031,9 +1031,10 @@ __device__ __forceinline__ void x2s_column(f2_t (&acc)[RB_P], const f2_t (&ui)[R
     }
 }
 
-// Persistent over a largest-first queue of 64 x (TY * RB_P) tiles, as k_direct2d_x2.
+// Persistent over a largest-first queue of 64 x (TY * RB_P) tiles, with two warps per row group
+// splitting the column offsets by sign and adding their partial sums once, as k_direct2d_x2.
 template <int RM, int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(64 * TY)
 k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
                float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
                int nrhs, int *__restrict__ queue)
@@ -1042,7 +1043,7 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
     constexpr int SY = TY * RB_P + 2 * RM + 1;
     constexpr int PL = SX * SY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_item, s_jmin[TY];
+    __shared__ int s_item, s_jmin[2 * TY];
     const int n = a.n, R = a.R;
     float *su = reinterpret_cast<float *>(smem_raw);          // u | b | c | thr + 1
     const int64_t N = a.N;
@@ -1051,6 +1052,8 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
     const float *__restrict__ finv = (const float *)a.fin;
     const float *__restrict__ extv = (const float *)a.ext;
     const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int grp = threadIdx.y >> 1, half = threadIdx.y & 1;
+    f2_t *sx = reinterpret_cast<f2_t *>(smem_raw);           // partial sums, over the tile once read
     const int total = ntiles * nrhs;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(queue, 1);
@@ -1061,7 +1064,7 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         const float *__restrict__ ur = u + (int64_t)z * N;
         const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * (TY * RB_P);
         int jmin = 1 << 30;                          // smallest thr of the staged nodes
-        for (int e = tid; e < PL; e += 32 * TY) {
+        for (int e = tid; e < PL; e += 64 * TY) {
             const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
             float uv = 0.f, bv = 0.f, cv = 0.f, tv = 0.f;
             if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
@@ -1082,12 +1085,12 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         if (threadIdx.x == 0) s_jmin[threadIdx.y] = jmin;
         __syncthreads();
 #pragma unroll
-        for (int w = 0; w < TY; ++w) jmin = min(jmin, s_jmin[w]);
+        for (int w = 0; w < 2 * TY; ++w) jmin = min(jmin, s_jmin[w]);
         const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
-        const int ybase = y0 + threadIdx.y * RB_P;
+        const int ybase = y0 + grp * RB_P;
         f2_t ui[RB_P], acc[RB_P], wi[RB_P], ti[RB_P];
         int tmax = -1, tmin = 1 << 30;
-        const float *ua = su + (threadIdx.y * RB_P + RM) * SX + 2 * threadIdx.x + RM;
+        const float *ua = su + (grp * RB_P + RM) * SX + 2 * threadIdx.x + RM;
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
             const int y = ybase + p;
@@ -1108,7 +1111,8 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         if (tmin == (1 << 30)) tmin = -1;
         const int cmin = min(tmin, jmin);
         const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-        for (int ox = -rx; ox <= rx; ++ox) {
+        const int ox_lo = half ? 0 : -rx, ox_hi = half ? rx : -1;
+        for (int ox = ox_lo; ox <= ox_hi; ++ox) {
             const int ox2 = ox * ox;
             if (ox2 > tmax) continue;
             const int hmax = min(R, isqrt_small(tmax - ox2));
@@ -1117,22 +1121,31 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
             const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
             x2s_column(acc, ui, wi, ti, ua + ox, PL, SX, gcol, ox2, hcore, hmid, hmax);
         }
+        __syncthreads();               // every warp is done with the tile
+        f2_t *xs = sx + grp * RB_P * 32 + threadIdx.x;
+        if (half) {
 #pragma unroll
-        for (int p = 0; p < RB_P; ++p) {
-            const int y = ybase + p;
-            float s0, s1, u0, u1;
-            f2_unpack(acc[p], s0, s1);
-            f2_unpack(ui[p], u0, u1);
-            if (y < n && xa < n) {
-                const int64_t i = xa + (int64_t)n * y;
-                Lu[(int64_t)z * N + i] = finv[i] * (s0 - u0 * extv[i]);
-            }
-            if (y < n && xb < n) {
-                const int64_t i = xb + (int64_t)n * y;
-                Lu[(int64_t)z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+            for (int p = 0; p < RB_P; ++p) xs[p * 32] = acc[p];
+        }
+        __syncthreads();
+        if (!half) {
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) {
+                const int y = ybase + p;
+                float s0, s1, u0, u1;
+                f2_unpack(f2_add(acc[p], xs[p * 32]), s0, s1);
+                f2_unpack(ui[p], u0, u1);
+                if (y < n && xa < n) {
+                    const int64_t i = xa + (int64_t)n * y;
+                    Lu[(int64_t)z * N + i] = finv[i] * (s0 - u0 * extv[i]);
+                }
+                if (y < n && xb < n) {
+                    const int64_t i = xb + (int64_t)n * y;
+                    Lu[(int64_t)z * N + i] = finv[i] * (s1 - u1 * extv[i]);
+                }
             }
         }
-        __syncthreads();               // the tile, s_item and s_jmin are reused by the next item
+        __syncthreads();               // the tile, the partial sums, s_item and s_jmin are reused
     }
     if (tid == 0) {
         __threadfence();
@@ -1148,14 +1161,14 @@ static size_t x2s_smem_bytes()
 
 // symmetric kernel variants: TY warps per tile (shared memory bounds the residency)
 constexpr int X2S_VARIANTS = 2;
-static const int x2s_var_ty[X2S_VARIANTS] = { 2, 4 };
+static const int x2s_var_ty[X2S_VARIANTS] = { 1, 2 };
 
 template <int RM, int TY>
 static nl_status launch_x2s_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
                               int nrhs, const int *order, int ntiles, int *blocks_cache,
                               cudaStream_t st)
 {
-    const dim3 blk(32, TY, 1);
+    const dim3 blk(32, 2 * TY, 1);
     const size_t smem = x2s_smem_bytes<RM, TY>();
     auto kern = k_direct2d_x2s<RM, TY>;
     NL_CUDA_TRY(prep_smem(kern, smem));
@@ -1168,7 +1181,7 @@ static nl_status launch_x2s_t(nl_plan *p, const DirectArgs &a, const float *u, f
     if (items == 0) return NL_OK;
     if (*blocks_cache == 0) {
         int per_sm = 0, dev = 0, sms = 0;
-        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem));
+        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64 * TY, smem));
         NL_CUDA_TRY(cudaGetDevice(&dev));
         NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         *blocks_cache = (per_sm > 0 ? per_sm : 1) * sms;
@@ -1185,8 +1198,8 @@ static nl_status launch_x2s_var(nl_plan *p, int var, const DirectArgs &a, const 
                                 float *Lu, int nrhs, const int *order, int ntiles, int *bc,
                                 cudaStream_t st)
 {
-    if (var == 0) return launch_x2s_t<RM, 2>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    return launch_x2s_t<RM, 4>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (var == 0) return launch_x2s_t<RM, 1>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    return launch_x2s_t<RM, 2>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
 }
 
 static nl_status x2s_launch_any(nl_plan *p, int var, const DirectArgs &a, const float *u,
@@ -2316,9 +2329,9 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
     const int *var_ty = sym ? x2s_var_ty : x2_var_ty;
     NL_CUDA_TRY(cudaMalloc(&p->x2_queue, 2 * sizeof(int)));
     NL_CUDA_TRY(cudaMemsetAsync(p->x2_queue, 0, 2 * sizeof(int), st));
-    // tile heights (row groups of 8) of the two kinds of variant: 1 and 2 row groups for
-    // k_direct2d_x2, 2 and 4 for k_direct2d_x2s
-    const int ty_k[2] = { sym ? 2 : 1, sym ? 4 : 2 };
+    // tile heights (row groups of 8) of the two kinds of variant: 1 and 2 row groups for both
+    // k_direct2d_x2 and k_direct2d_x2s
+    const int ty_k[2] = { 1, 2 };
     int *ord[2] = { nullptr, nullptr };              // tile orders for ty_k[0] and ty_k[1]
     int nt[2] = { 0, 0 }, bc[X2_VARIANTS] = { 0, 0, 0, 0 };
     float ms[X2_VARIANTS] = { 0.f, 0.f, 0.f, 0.f };
@@ -2326,7 +2339,7 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool tune = p->N <= ((int64_t)1 << 24);
     nl_status s = NL_OK;
-    // untuned (very large grids): x2s with TY = 4 (variant 1), x2 with TY = 1 (variant 0)
+    // untuned (very large grids): x2s with TY = 2 (variant 1), x2 with TY = 1 (variant 0)
     int best = sym ? 1 : 0;
     for (int k = 0; k < 2 && s == NL_OK; ++k)
         if (tune || ty_k[k] == var_ty[best]) s = x2_order_for(p, ty_k[k], &ord[k], &nt[k], st);
