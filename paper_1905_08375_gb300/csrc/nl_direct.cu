@@ -1033,8 +1033,8 @@ __device__ __forceinline__ void x2s_column(f2_t (&acc)[RB_P], const f2_t (&ui)[R
 
 // Persistent over a largest-first queue of 64 x (TY * RB_P) tiles, with two warps per row group
 // splitting the column offsets by sign and adding their partial sums once, as k_direct2d_x2.
-template <int RM, int TY>
-__global__ void __launch_bounds__(64 * TY)
+template <int RM, int TY, int MB>
+__global__ void __launch_bounds__(64 * TY, MB)
 k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
                float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
                int nrhs, int *__restrict__ queue)
@@ -1160,17 +1160,17 @@ static size_t x2s_smem_bytes()
 }
 
 // symmetric kernel variants: TY warps per tile (shared memory bounds the residency)
-constexpr int X2S_VARIANTS = 2;
-static const int x2s_var_ty[X2S_VARIANTS] = { 1, 2 };
+constexpr int X2S_VARIANTS = 3;
+static const int x2s_var_ty[X2S_VARIANTS] = { 1, 2, 2 };
 
-template <int RM, int TY>
+template <int RM, int TY, int MB>
 static nl_status launch_x2s_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
                               int nrhs, const int *order, int ntiles, int *blocks_cache,
                               cudaStream_t st)
 {
     const dim3 blk(32, 2 * TY, 1);
     const size_t smem = x2s_smem_bytes<RM, TY>();
-    auto kern = k_direct2d_x2s<RM, TY>;
+    auto kern = k_direct2d_x2s<RM, TY, MB>;
     NL_CUDA_TRY(prep_smem(kern, smem));
     const int tiles_x = (p->n + 63) / 64;
     const int64_t items = (int64_t)ntiles * nrhs;
@@ -1198,8 +1198,9 @@ static nl_status launch_x2s_var(nl_plan *p, int var, const DirectArgs &a, const 
                                 float *Lu, int nrhs, const int *order, int ntiles, int *bc,
                                 cudaStream_t st)
 {
-    if (var == 0) return launch_x2s_t<RM, 1>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    return launch_x2s_t<RM, 2>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (var == 0) return launch_x2s_t<RM, 1, 1>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (var == 1) return launch_x2s_t<RM, 2, 1>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    return launch_x2s_t<RM, 2, 3>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
 }
 
 static nl_status x2s_launch_any(nl_plan *p, int var, const DirectArgs &a, const float *u,
