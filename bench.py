@@ -177,7 +177,8 @@ PROFILED_TRAFFIC = {
 
 def _alu_roof(kernel, flops, ms, peak, src):
     ach = flops / (ms * 1e-3) / 1e12
-    traffic = next((v for k, v in PROFILED_TRAFFIC.items() if kernel.startswith(k)), None)
+    base = kernel.split("<")[0].split(" ")[0]           # the kernel's name without arguments
+    traffic = PROFILED_TRAFFIC.get(base)
     return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
             "peak_source": src}
