@@ -1,4 +1,4 @@
-"""GPU conjugate gradients (nl_cg_solve) on -L x = f, judged by the FP64 oracle residual."""
+"""GPU conjugate gradients (nl_cg_solve) on -L x = f, checked by the FP64 oracle residual."""
 import numpy as np
 import pytest
 import torch

@@ -1,5 +1,5 @@
 """GPU parity of the learned-preconditioner kernels against the numpy oracle, and
-flexible CG with the network (FP64 oracle residual as the judge)."""
+flexible CG with the network (the FP64 oracle residual decides convergence)."""
 import numpy as np
 import pytest
 import torch
