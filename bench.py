@@ -941,6 +941,21 @@ def oracle_sample(w, outs, budget_s=20.0):
 # ---------------------------------------------------------------------------
 # drivers
 # ---------------------------------------------------------------------------
+def max_over_ranks(x, device):
+    """The largest of the ranks' values of x, returned on every rank (all-reduce MAX)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(per_replica_value, ws, higher_is_better):
+    """Replicas only: with every rank timed at the slowest rank's step time, a throughput is the
+    sum over the ws replicas; a time-like metric is the slowest rank's time."""
+    return per_replica_value * (ws if higher_is_better else 1)
+
+
 def run_gpu(args, peaks):
     import torch
     import torch.distributed as dist
@@ -984,10 +999,8 @@ def run_gpu(args, peaks):
         dist.barrier()
     ms_step = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = w.value(ms_step) * (ws if w.higher_is_better else 1)
+        ms_step = max_over_ranks(ms_step, dev)
+    value = whole_job_value(w.value(ms_step), ws, w.higher_is_better)
     reps = max(3, min(steps, 50))
     roof, per = w.kernels(flush, reps)
     e2e = w.e2e(flush, min(steps, 20))
