@@ -54,6 +54,9 @@ def test_library_exports_every_declared_symbol(nl):
     (dict(dim=3, n=8, delta=0.1, family=2), "NL_EUNSUPPORTED"),             # PD is 2-D
     (dict(dim=2, n=8, delta=0.1, family=1, symmetric=True), "NL_EUNSUPPORTED"),
     (dict(dim=2, n=8, delta=0.1, alpha=4.5), "NL_EINVAL"),
+    (dict(dim=2, n=8, delta=0.1, family=3, K=4), "NL_EINVAL"),              # kappa: K 0..3
+    (dict(dim=2, n=8, delta=0.1, family=3, symmetric=True), "NL_EUNSUPPORTED"),
+    (dict(dim=2, n=8, delta=0.1, family=4), "NL_EINVAL"),                   # unknown family
 ])
 def test_plan_validation_errors(nl, kw, status):
     with pytest.raises(nl.NlError) as ei:
