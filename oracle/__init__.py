@@ -15,6 +15,8 @@ from the paper (Tian & Engquist, arXiv 1905.08375):
   moment pyramid and the Step 3 sum of Eq. (3.5), then Eq. (3.3).
 * ``fast_leafset``   -- the same quantity as a plain sum over the leaf cells
   that meet the ball (the union of the panels Algorithm 1 includes).
+* ``fast_sym_leafset`` -- the symmetrised (divergence-type) form of that operator, each half
+  of a pair's weight over its own node's leaf set (a project extension; no fast kernel yet).
 * ``poly_coeffs``    -- the Hermite-matched even polynomial p^{2K} of Sec. 3.
 * ``cg``             -- plain conjugate gradients on -L x = f (Sec. 4 remark).
 * ``convnet``        -- the CG preconditioner network (a project addition the
@@ -86,6 +88,8 @@ def lib():
         L.or_fast_tree.argtypes = [i, i, vp, i, vp, d, i, vp, i, i, vp, vp, vp, i64, vp]
         L.or_fast_leafset.restype = i
         L.or_fast_leafset.argtypes = [i, i, vp, i, vp, d, i, vp, i, i, vp, vp, vp, i64, vp]
+        L.or_fast_sym_leafset.restype = i
+        L.or_fast_sym_leafset.argtypes = [i, i, vp, i, vp, d, i, vp, i, vp, vp, vp, i64]
         L.or_cg.restype = i
         L.or_cg.argtypes = [i, i, i, vp, i, d, i, vp, d, i, vp, vp, vp, vp, vp, d, i,
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -244,6 +248,30 @@ def fast_leafset(u, d, L, delta, K=0, alpha=1.0, scale=1.0, normalize=True, coef
     out, cnt = _fast(lib().or_fast_leafset, u, d, L, delta, K, alpha, scale, normalize, coef, a,
                      self_mode, idx)
     return (out, cnt) if return_counts else out
+
+
+def fast_sym_leafset(u, d, L, delta, K=0, alpha=1.0, scale=1.0, normalize=True,
+                     coef=COEF_NONE, a=None, idx=None):
+    """Symmetrised leaf-set operator of the polynomial kernel (divergence type, a project
+    extension of Sec. 3): sigma h^d sum_k (w_i(k) + w_k(i))/2 (u_k - u_i), each half over its
+    own node's leaf set.  u: [nrhs, N] or [N]."""
+    u = _f64(u)
+    n = 1 << L
+    squeeze = u.ndim == 1
+    u2 = u.reshape(1, -1) if squeeze else u.reshape(u.shape[0], -1)
+    nrhs = u2.shape[0]
+    dl = _delta_field(delta, d, n)
+    p = poly_coeffs(K, alpha)
+    sg = sigma(d, alpha, scale, normalize)
+    a_ = None if a is None else _f64(a).reshape(-1)
+    ix, nix = _idx(idx)
+    M = nix if ix is not None else n ** d
+    out = np.zeros((nrhs, M))
+    rc = lib().or_fast_sym_leafset(d, L, _ptr(dl), K, _ptr(p), sg, coef, _ptr(a_), nrhs,
+                                   _ptr(u2), _ptr(out), _ptr(ix), nix)
+    if rc:
+        raise ValueError(f"or_fast_sym_leafset failed ({rc})")
+    return out[0] if squeeze else out
 
 
 def fast_pd_leafset(u, d, L, delta, c, scale=1.0, idx=None):

@@ -724,6 +724,80 @@ int or_fast_leafset(int d, int L, const double *delta, int K, const double *p, d
 }
 
 /*
+ * Symmetrised leaf-set operator of the polynomial kernel (a project extension: the paper's
+ * fast algorithm, Sec. 3, is stated for C(x), delta(x) only; its case (b) of Sec. 2, the
+ * divergence type with symmetric C and delta, is not covered).  With the leaf-set relation
+ *   k ~ i  iff  cell_k meets the open ball B(x_i, delta_i)
+ * (the quadrature set of Algorithm 1) and the one-sided weight
+ *   w_i(k) = C_ik delta_i^{-(d+2)} p(|x_k - x_i| / delta_i) [k ~ i],
+ * the symmetrised weight of a node pair in Omega is (w_i(k) + w_k(i)) / 2, each half with its
+ * own node's horizon; a cell outside Omega takes a_k = a_i and delta_k = delta_i (so both
+ * halves agree there: the cell-to-node distance is the same both ways) and u_k = 0:
+ *   (L u)_i = sigma h^d sum_{k != i} w^s_ik (u_k - u_i).
+ * C = 1 (coef NONE) or a_i a_k (coef XY).  u, out: [nrhs][N]; idx as above.
+ */
+int or_fast_sym_leafset(int d, int L, const double *delta, int K, const double *p, double sigma,
+                        int coef, const double *a, int nrhs, const double *u, double *out,
+                        const int64_t *idx, int64_t nidx)
+{
+    if (d < 1 || d > 3 || L < 0 || L > 20 || K < 0) return 1;
+    if (coef != OR_COEF_NONE && coef != OR_COEF_XY) return 2;
+    const int n = 1 << L;
+    const int64_t N = num_nodes(d, n);
+    const int64_t M = idx ? nidx : N;
+    const double h = 1.0 / n, hd = pow(h, d);
+    double dmax = 0.0;
+    for (int64_t f = 0; f < N; ++f) if (delta[f] > dmax) dmax = delta[f];
+    const int64_t B = (int64_t)ceil(dmax * n) + 1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < M; ++q) {
+        const int64_t fi = idx ? idx[q] : q;
+        int64_t ci[3];
+        unflatten(fi, d, n, ci);
+        const double di = delta[fi];
+        const double ai = (coef == OR_COEF_XY) ? a[fi] : 1.0;
+        const double R2i4 = 4.0 * ((di * n) * (di * n));
+        const int64_t bz = d > 2 ? B : 0, by = d > 1 ? B : 0;
+        for (int r = 0; r < nrhs; ++r) {
+            const double *ur = u + (int64_t)r * N;
+            double acc = 0.0;
+            for (int64_t oz = -bz; oz <= bz; ++oz)
+                for (int64_t oy = -by; oy <= by; ++oy)
+                    for (int64_t ox = -B; ox <= B; ++ox) {
+                        int64_t o[3] = { ox, oy, oz }, ck[3];
+                        int64_t dmin = 0, o2 = 0;
+                        int inside = 1;
+                        for (int k = 0; k < d; ++k) {
+                            /* half units: cell_k spans [2 c_k, 2 c_k + 2], node i at 2 c_i + 1 */
+                            int64_t lo = 2 * (ci[k] + o[k]), hi = lo + 2, X = 2 * ci[k] + 1;
+                            if (lo > X) dmin += (lo - X) * (lo - X);
+                            else if (hi < X) dmin += (hi - X) * (hi - X);
+                            o2 += o[k] * o[k];
+                            ck[k] = ci[k] + o[k];
+                            if (ck[k] < 0 || ck[k] >= n) inside = 0;
+                        }
+                        if (o2 == 0) continue;
+                        const double rr = sqrt((double)o2) * h;
+                        const int64_t fk = inside ? flatten(ck, d, n) : -1;
+                        const double ak = (coef == OR_COEF_XY && inside) ? a[fk] : ai;
+                        const double dk = inside ? delta[fk] : di;
+                        const double R2k4 = 4.0 * ((dk * n) * (dk * n));
+                        const double wi = ((double)dmin < R2i4)
+                            ? pow(di, -(d + 2.0)) * profile(OR_POLY, 0.0, K, p, rr / di) : 0.0;
+                        const double wk = ((double)dmin < R2k4)
+                            ? pow(dk, -(d + 2.0)) * profile(OR_POLY, 0.0, K, p, rr / dk) : 0.0;
+                        const double w = 0.5 * (wi + wk) * ai * ak;
+                        if (w == 0.0) continue;
+                        const double uk = inside ? ur[fk] : 0.0;
+                        acc += w * (uk - ur[fi]);
+                    }
+            out[(int64_t)r * M + q] = sigma * hd * acc;
+        }
+    }
+    return 0;
+}
+
+/*
  * Fast-path peridynamics (the polynomial micromodulus of the paper's outlook, degree 0):
  * the bond tensor xi xi^T / |xi|^3 of Eq. (1.2) is replaced by xi xi^T p(|xi|/delta_i) /
  * delta_i^3 with p = 1 (p matches s^{-3} at the horizon, as p^{2K} with K = 0 matches
