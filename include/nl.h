@@ -198,29 +198,33 @@ nl_status nl_cg_solve(nl_plan *plan, const void *f, void *x, int nrhs, double rt
                       int precond, nl_cg_stats *stats, void *stream);
 
 /*
- * nl_apply_fast_noalloc -- the fast apply of Sec. 3 with p^{2K} = 1 (K = 0) and C = 1, for
- * callers that must not allocate device memory: a host whose device memory is all handed to
- * its own pool allocator (a library cudaMalloc would fail or fragment the pool), or a caller
- * on a latency-critical path that cannot take the implicit device synchronisation that
+ * nl_apply_fast_noalloc -- the K = 0 (p = 1), C = 1 fast apply, equal to nl_apply_fast on an
+ * NL_POLY, K = 0, NL_COEF_NONE plan with the same horizon, alpha, scale, normalize and self
+ * term.  The paper has no counterpart: this entry point only packages that apply for callers
+ * that must not allocate device memory -- a host whose device memory is all handed to its own
+ * pool allocator (a library cudaMalloc would fail or fragment the pool), or a caller on a
+ * latency-critical path that cannot take the implicit device synchronisation that
  * cudaMalloc/cudaFree may cause.  It creates no plan and calls no cudaMalloc, cudaFree or
- * other allocating routine.  The paper has no counterpart: this is a packaging variant of
- * nl_apply_fast.  Its result equals nl_apply_fast on an NL_POLY, K = 0, NL_COEF_NONE plan.
+ * other allocating routine.
  *
- * Scratch: a file-scope device array of 32 MiB inside the library, held by every GPU on
- * which the library's module is loaded until the process exits.  It bounds the grid:
- * n = 2^L with at most 8192 (1-D), 1024 (2-D) or 64 (3-D) nodes per dimension; larger
- * grids are rejected with NL_EINVAL and a message giving the bytes needed.  The first call
- * made on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls share the
- * array and each call rewrites every part it reads, so no clearing is needed, but calls
- * whose kernels overlap on the GPU (other streams or host threads on the same device) race
- * on it: order them.
+ * Scratch: a file-scope device array of 32 MiB inside the library, held by every GPU on which
+ * the library's module is loaded until the process exits.  It bounds the grid: n = 2^L with
+ * at most 8192 (1-D), 1024 (2-D) or 64 (3-D) nodes per dimension; larger grids are rejected
+ * with NL_EINVAL and a message giving the bytes needed.  Every call looks up the array's
+ * device address (cudaGetSymbolAddress, which allocates nothing) with the caller's device
+ * current.  All calls share the array and each call rewrites every part it reads, so no
+ * clearing is needed, but calls whose kernels overlap on the GPU (other streams or host
+ * threads on the same device) race on it: order them.
  *
- * Arguments: dim 1..3; n nodes per dimension; delta > 0 the constant horizon, used when
- * delta_field is NULL; delta_field a DEVICE pointer to n^dim FP64 horizons (caller-owned,
- * read only) or NULL; alpha, scale, normalize as in nl_kernel (sigma); self_term an nl_self;
- * u, Lu DEVICE pointers, nrhs stacked fields [nrhs][n^dim] of `dtype`.  Stream-ordered and
- * asynchronous.  Errors: NL_EINVAL, NL_EUNSUPPORTED (n not a power of two), NL_ECUDA.
+ * Arguments: dim 1..3; n nodes per dimension; delta the constant horizon, 0 < delta <= 2
+ * (a ball of radius 2 covers Omega), used when delta_field is NULL; delta_field a DEVICE
+ * pointer to n^dim FP64 horizons in the same range (caller-owned, read only; values outside
+ * it, or NaN, are clamped for the geometry so that the work stays bounded, and the result at
+ * such nodes is undefined) or NULL; alpha, scale, normalize as in nl_kernel (sigma);
+ * self_term an nl_self; u, Lu DEVICE pointers, nrhs stacked fields [nrhs][n^dim] of `dtype`
+ * each (the caller guarantees those sizes).  Stream-ordered and asynchronous.
+ * Errors: NL_EINVAL (argument out of range, grid beyond the array), NL_EUNSUPPORTED (n not a
+ * power of two), NL_ECUDA.
  */
 nl_status nl_apply_fast_noalloc(int dim, int n, double delta, const double *delta_field,
                                 double alpha, double scale, int normalize, int self_term,
@@ -275,6 +279,15 @@ nl_status nl_net_prepare_pairs(nl_plan *plan, const double *r, const double *e, 
                                float *x_out, float *e_out, void *stream);
 /* z = M(r) on DEVICE FP64 [nrhs][n^2]. */
 nl_status nl_net_apply(nl_net *net, nl_plan *plan, const double *r, double *z, int nrhs, void *stream);
+/* Training pairs straight from a CG history (nl_cg_history): DEVICE f, x [n^2] (FP64, the
+ * right-hand side and the converged solution) and history [count][n^2] (FP64 iterates x_k)
+ * -> r_k = f + L x_k (FP64 operator) and e_k = x - x_k, then as nl_net_prepare_pairs into
+ * x_out, e_out [count][n^2] (FP32).  Allocates and frees two FP64 work arrays of count n^2
+ * values; synchronises `stream`.  Errors: NL_EINVAL, NL_EUNSUPPORTED (not the symmetric 2-D
+ * scalar operator), NL_ENOMEM, NL_ECUDA. */
+nl_status nl_net_history_pairs(nl_plan *plan, const double *f, const double *x,
+                               const double *history, int count, float *x_out, float *e_out,
+                               void *stream);
 /* Attach (or detach with NULL) the network used by nl_cg_solve with NL_PRECOND_LEARNED. */
 nl_status nl_plan_set_net(nl_plan *plan, nl_net *net);
 /*
@@ -348,6 +361,30 @@ nl_status nl_get_plan_info(const nl_plan *plan, nl_plan_info *info);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *nl_last_error(void);
+
+/*
+ * Failure handling on the host (the paper has no counterpart; these serve callers that must
+ * bound how long the library may block, and tests of the error paths that need no GPU fault).
+ *
+ * nl_set_wait_limit: the limit, in seconds (0 < seconds <= 1e6; 600 by default, process-wide),
+ * of every bounded host wait of the library -- nl_cg_solve, nl_cg_history and
+ * nl_batch_cg_solve wait on each chunk of iterations at most this long and then return
+ * NL_ETIMEOUT.  The chunk's kernels are not stopped: they finish on the solver's stream, so a
+ * caller that got NL_ETIMEOUT synchronises the device before reusing the plan or its buffers.
+ * Errors: NL_EINVAL.
+ *
+ * nl_wait_poll: the bounded wait itself, exported so that a caller can wait on a condition of
+ * its own with the same semantics: calls poll(ctx) about every 50 us until it returns > 0
+ * (NL_OK), < 0 (NL_ECUDA) or `seconds` have passed (NL_ETIMEOUT; seconds <= 0 takes the
+ * limit of nl_set_wait_limit).  poll runs on the calling thread.
+ *
+ * nl_debug_fail_host_alloc: failure injection.  With after >= 0 the host allocation that
+ * follows `after` successful ones inside nl_plan_create fails once (that call returns
+ * NL_ENOMEM and leaves nothing allocated); after < 0 disarms.  Process-wide; for tests.
+ */
+nl_status nl_set_wait_limit(double seconds);
+nl_status nl_wait_poll(int (*poll)(void *ctx), void *ctx, double seconds);
+nl_status nl_debug_fail_host_alloc(int after);
 
 #ifdef __cplusplus
 }

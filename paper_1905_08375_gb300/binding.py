@@ -246,17 +246,25 @@ def nl_apply_fast_noalloc(dim, n, delta, u, Lu, alpha=0.0, scale=1.0, normalize=
     fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
                    ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    N = int(n) ** int(dim)
     if isinstance(delta, (int, float)):
         dconst, dptr = float(delta), None
     else:
         import torch
         if not (delta.is_cuda and delta.dtype == torch.float64 and delta.is_contiguous()):
             raise ValueError("delta field must be a contiguous CUDA float64 tensor")
+        if delta.numel() != N:
+            raise ValueError(f"delta field has {delta.numel()} values, expected n^dim = {N}")
         dconst, dptr = 0.0, ctypes.c_void_p(delta.data_ptr())
     if not (u.is_cuda and Lu.is_cuda and u.is_contiguous() and Lu.is_contiguous()):
         raise ValueError("u and Lu must be contiguous CUDA tensors")
+    if u.dtype != Lu.dtype:
+        raise ValueError(f"u ({u.dtype}) and Lu ({Lu.dtype}) must have the same dtype")
     if nrhs is None:
-        nrhs = u.numel() // (n ** dim)
+        nrhs = u.numel() // N if N > 0 else 0
+    if u.numel() != nrhs * N or Lu.numel() != nrhs * N:
+        raise ValueError(f"u and Lu need nrhs * n^dim = {nrhs * N} elements "
+                         f"(got {u.numel()} and {Lu.numel()})")
     _check(fn(int(dim), int(n), dconst, dptr, float(alpha), float(scale), int(bool(normalize)),
               int(self_term), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(Lu.data_ptr()),
               int(nrhs), _dtype_code(u), _stream_ptr(stream)))
@@ -387,6 +395,24 @@ def nl_net_prepare_pairs(plan: Plan, r, e, xo, eo, stream=None):
                                            ctypes.c_void_p(e.data_ptr()), r.shape[0],
                                            ctypes.c_void_p(xo.data_ptr()),
                                            ctypes.c_void_p(eo.data_ptr()), _stream_ptr(stream)))
+
+
+def nl_net_history_pairs(plan: Plan, f, x, history, count, xo, eo, stream=None):
+    """f, x: CUDA float64 [N]; history: CUDA float64 [>= count, N] (CG iterates);
+    xo, eo: CUDA float32 [count, N].  r_k = f + L x_k and e_k = x - x_k are formed by the
+    library, then scaled as by nl_net_prepare_pairs."""
+    L = _net_fns()
+    fn = L.nl_net_history_pairs
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p] * 5 + [ctypes.c_int] + [ctypes.c_void_p] * 3
+    N = plan.N
+    if f.numel() != N or x.numel() != N or history.numel() < count * N:
+        raise ValueError("f, x need n^2 values and history count * n^2")
+    if xo.numel() < count * N or eo.numel() < count * N:
+        raise ValueError("xo, eo need count * n^2 values")
+    _check(fn(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+              ctypes.c_void_p(history.data_ptr()), int(count), ctypes.c_void_p(xo.data_ptr()),
+              ctypes.c_void_p(eo.data_ptr()), _stream_ptr(stream)))
 
 
 def nl_net_apply(net: Net, plan: Plan, r, z, nrhs=None, stream=None):
@@ -553,3 +579,36 @@ def nl_batch_cg_solve(batch: Batch, f, x, rtol=1e-8, maxit=10000, precond=NL_PRE
     if status not in (NL_OK, NL_ENOTCONV):
         _check(status)
     return out
+
+
+# ---------------------------------------------------------------------------
+# host-side failure handling
+# ---------------------------------------------------------------------------
+WAIT_POLL_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
+
+
+def nl_set_wait_limit(seconds: float):
+    """Limit (s) of the library's bounded host waits (CG chunks); 600 s by default."""
+    fn = lib().nl_set_wait_limit
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_double]
+    _check(fn(float(seconds)))
+
+
+def nl_wait_poll(poll, seconds: float) -> int:
+    """Run the library's bounded wait on a Python condition: poll() -> 1 done, 0 not yet,
+    < 0 error.  Returns the status code (NL_OK, NL_ETIMEOUT or NL_ECUDA)."""
+    fn = lib().nl_wait_poll
+    fn.restype = ctypes.c_int
+    fn.argtypes = [WAIT_POLL_FN, ctypes.c_void_p, ctypes.c_double]
+    cb = WAIT_POLL_FN(lambda _ctx: int(poll()))
+    return int(fn(cb, None, float(seconds)))
+
+
+def nl_debug_fail_host_alloc(after: int):
+    """Make the host allocation after `after` successful ones in nl_plan_create fail once
+    (after < 0 disarms)."""
+    fn = lib().nl_debug_fail_host_alloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int]
+    _check(fn(int(after)))

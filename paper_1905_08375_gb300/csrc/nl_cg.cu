@@ -364,20 +364,28 @@ nl_status nl_cg_state_release(nl_cg_state *c)
 
 nl_status nl_cg_release(nl_plan *p) { return nl_cg_state_release(&p->cg); }
 
-static nl_status wait_bounded(nl_cg_state *c, double seconds)
+struct EventPoll { cudaEvent_t ev; cudaError_t err; };
+
+static int poll_event(void *ctx)
 {
-    const auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t e = cudaEventQuery(c->ev);
-        if (e == cudaSuccess) return NL_OK;
-        if (e != cudaErrorNotReady) return nl_cuda_fail(e, "CG chunk");
-        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (dt > seconds) {
-            nl_set_error("nl_cg_solve: a chunk of iterations did not finish within %.0f s", seconds);
-            return NL_ETIMEOUT;
-        }
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
-    }
+    EventPoll *e = (EventPoll *)ctx;
+    e->err = cudaEventQuery(e->ev);
+    if (e->err == cudaSuccess) return 1;
+    return e->err == cudaErrorNotReady ? 0 : -1;
+}
+
+// bounded host wait on the chunk's event (nl_wait_poll with the library's wait limit): a chunk
+// that does not finish in time returns NL_ETIMEOUT (its kernels keep running on the CG stream)
+static nl_status wait_bounded(nl_cg_state *c)
+{
+    const double lim = nl_wait_limit_seconds();
+    EventPoll ep{ c->ev, cudaSuccess };
+    const nl_status s = nl_wait_poll(poll_event, &ep, lim);
+    if (s == NL_ETIMEOUT)
+        nl_set_error("nl_cg_solve: a chunk of iterations did not finish within %.3g s", lim);
+    else if (s == NL_ECUDA)
+        return nl_cuda_fail(ep.err, "CG chunk");
+    return s;
 }
 
 static nl_status ensure_workspace(nl_cg_state *c, int64_t len, int64_t dlen, int nrhs)
@@ -536,7 +544,7 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
         NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
         NL_CUDA_TRY(cudaEventRecord(c->ev, st));
-        if ((s = wait_bounded(c, 600.0)) != NL_OK) return s;
+        if ((s = wait_bounded(c)) != NL_OK) return s;
         bool all = true;
         for (int r = 0; r < nrhs; ++r) all = all && h[r * S_COUNT + S_CONV] != 0.0;
         const bool out_of_budget = iters >= maxit;
@@ -549,7 +557,7 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
         NL_CUDA_TRY(cudaMemcpyAsync(h, a.sc, (size_t)S_COUNT * nrhs * sizeof(double),
                                     cudaMemcpyDeviceToHost, st));
         NL_CUDA_TRY(cudaEventRecord(c->ev, st));
-        if ((s = wait_bounded(c, 600.0)) != NL_OK) return s;
+        if ((s = wait_bounded(c)) != NL_OK) return s;
         double worst = 0.0;
         for (int r = 0; r < nrhs; ++r) worst = fmax(worst, h[r * S_COUNT + S_TRUE]);
         if (worst <= rtol) { conv_all = true; break; }

@@ -145,6 +145,12 @@ struct nl_plan {
 void nl_set_error(const char *fmt, ...);
 nl_status nl_cuda_fail(cudaError_t e, const char *what);
 
+// ---- host-side failure handling (nl_plan.cu) ----
+// false once, when an injected host-allocation failure is due (nl_debug_fail_host_alloc)
+bool nl_host_alloc_allowed();
+// limit of the bounded host waits (nl_set_wait_limit; 600 s by default)
+double nl_wait_limit_seconds();
+
 #define NL_CUDA_TRY(call)                                                   \
     do {                                                                    \
         cudaError_t _e = (call);                                            \

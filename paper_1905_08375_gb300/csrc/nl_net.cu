@@ -21,6 +21,7 @@
 // reduction over tiles (deterministic).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -1144,6 +1145,57 @@ extern "C" nl_status nl_net_prepare_pairs(nl_plan *p, const double *r, const dou
     cudaFree(part);
     if (ce != cudaSuccess) return nl_cuda_fail(ce, "nl_net_prepare_pairs");
     return NL_OK;
+}
+
+// r_k = f + (L H_k) (L H_k in r on entry), e_k = x - H_k, for k < count
+__global__ void k_hist_residual(const double *__restrict__ f, const double *__restrict__ x,
+                                const double *__restrict__ H, double *__restrict__ r,
+                                double *__restrict__ e, int64_t N, int count)
+{
+    const int64_t tot = N * count;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = g % N;
+        r[g] += f[i];
+        e[g] = x[i] - H[g];
+    }
+}
+
+extern "C" nl_status nl_net_history_pairs(nl_plan *p, const double *f, const double *x,
+                                          const double *history, int count, float *x_out,
+                                          float *e_out, void *stream)
+{
+    if (!nl_plan_ok(p) || !f || !x || !history || !x_out || !e_out || count < 1 ||
+        count > 65535) {
+        nl_set_error("nl_net_history_pairs: bad argument");
+        return NL_EINVAL;
+    }
+    if (p->d != 2 || p->family == NL_PD_BOND || !p->symmetric) {
+        nl_set_error("nl_net_history_pairs: needs the symmetric 2-D scalar operator");
+        return NL_EUNSUPPORTED;
+    }
+    cudaStream_t st = nl_stream(stream);
+    const int64_t N = p->N;
+    double *r = nullptr, *e = nullptr;
+    if (cudaMalloc(&r, (size_t)count * N * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&e, (size_t)count * N * sizeof(double)) != cudaSuccess) {
+        if (r) cudaFree(r);
+        nl_set_error("nl_net_history_pairs: allocation of %d residual fields failed", count);
+        return NL_ENOMEM;
+    }
+    nl_status s = nl_apply(p, history, r, count, NL_F64, stream);
+    if (s == NL_OK) {
+        const int64_t tot = (int64_t)count * N;
+        const unsigned g = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+        k_hist_residual<<<g, 256, 0, st>>>(f, x, history, r, e, N, count);
+        const cudaError_t ce = cudaGetLastError();
+        s = ce == cudaSuccess ? nl_net_prepare_pairs(p, r, e, count, x_out, e_out, stream)
+                              : nl_cuda_fail(ce, "nl_net_history_pairs");
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(r);
+    cudaFree(e);
+    return s;
 }
 
 extern "C" nl_status nl_plan_set_net(nl_plan *p, nl_net *n)

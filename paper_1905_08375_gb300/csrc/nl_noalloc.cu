@@ -13,37 +13,27 @@
 // calls share it: two calls whose kernels overlap on the GPU (different streams, or different
 // host threads, on one device) race on it and must be ordered by the caller.  Every value a
 // call reads from the array is written earlier in the same call, so nothing needs clearing.
-#include <mutex>
-
 #include "nl_internal.cuh"
 
 #define NL_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
-#define NL_NOALLOC_MAX_DEVICES 64
+// Largest horizon accepted, in units of the domain side.  A ball of radius 2 around any node
+// covers Omega (whose diagonal is at most sqrt(3)); the bound keeps 4 (delta n)^2 below 2^30 for
+// every accepted n (so the half-unit geometry stays in 32-bit integers) and the per-node
+// self-term count (O((delta n)^{d-1}) row chords) small.
+#define NL_NOALLOC_MAX_DELTA 2.0
 
 static __device__ __align__(256) unsigned char g_nl_noalloc_scratch[NL_NOALLOC_SCRATCH_BYTES];
 
-// Host-side device addresses of the array, one per device, set on the first call made
-// with that device current.  The array's name in host code is only a stand-in for the
-// symbol; the address a kernel may use comes from cudaGetSymbolAddress.
-static void *g_scratch_addr[NL_NOALLOC_MAX_DEVICES];
-static std::mutex g_scratch_mu;
-
+// The array's name in host code is only a stand-in for the symbol; the address a kernel may
+// use comes from cudaGetSymbolAddress, looked up on every call with the caller's device
+// current (it allocates nothing, and a module reloaded after cudaDeviceReset or a new primary
+// context may place the array at a new address, so no address is cached).
 static nl_status scratch_address(unsigned char **out)
 {
-    int dev = -1;
-    NL_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NL_NOALLOC_MAX_DEVICES) {
-        nl_set_error("nl_apply_fast_noalloc: device index %d beyond %d", dev, NL_NOALLOC_MAX_DEVICES);
-        return NL_EUNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_nl_noalloc_scratch);
-        if (e != cudaSuccess || !p) return nl_cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_scratch_addr[dev] = p;
-    }
-    *out = (unsigned char *)g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_nl_noalloc_scratch);
+    if (e != cudaSuccess || !p) return nl_cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    *out = (unsigned char *)p;
     return NL_OK;
 }
 
@@ -65,6 +55,14 @@ __device__ __forceinline__ double na_delta(const NaArgs &a, int64_t i)
     return a.delta ? a.delta[i] : a.delta_const;
 }
 
+__device__ __forceinline__ int na_isqrt(int x)
+{
+    int r = (int)sqrtf((float)x);
+    while (r > 0 && r * r > x) --r;
+    while ((r + 1) * (r + 1) <= x) ++r;
+    return r;
+}
+
 // per node: threshold (largest integer below 4 R2, R2 = (delta n)^2 in FP64), factor
 // sigma delta^{-(d+2)}, self term (continuous: |S^{d-1}| delta^d / d; discrete: h^d times
 // the number of lattice cells, inside or outside Omega, that meet the open ball)
@@ -73,28 +71,29 @@ __global__ void k_na_nodes(NaArgs a)
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.N) return;
     const double di = na_delta(a, i);
-    const double rho = di * a.n;
+    // field values outside (0, NL_NOALLOC_MAX_DELTA] (or NaN) are clamped for the geometry so
+    // that the work stays bounded; such values are outside the documented range
+    const double rho = fmin(fmax(di * a.n, 0.0), NL_NOALLOC_MAX_DELTA * a.n);
     const double R2 = rho * rho;
-    const int T4 = (int)fmin(ceil(4.0 * R2) - 1.0, 1073741824.0);
+    const int T4 = (int)fmax(ceil(4.0 * R2) - 1.0, -1.0);
     a.thr4[i] = T4;
     a.fac[i] = a.sigma * pow(di, -(a.d + 2.0));
     if (a.self_mode == NL_SELF_PAPER) {
         a.selfS[i] = a.sphere * pow(di, (double)a.d) / a.d;
         return;
     }
+    // lattice cells meeting the open ball: per row (fixed oy, oz) the cells with
+    // (2|ox| - 1)^2 <= rest, i.e. |ox| <= (isqrt(rest) + 1) / 2, plus ox = 0
     const int B = (int)ceil(rho) + 1;
     const int bz = a.d > 2 ? B : 0, by = a.d > 1 ? B : 0;
     long long count = 0;
     for (int oz = -bz; oz <= bz; ++oz) {
-        const int gz = oz ? 2 * abs(oz) - 1 : 0;
+        const long long gz = oz ? 2 * abs(oz) - 1 : 0;
         for (int oy = -by; oy <= by; ++oy) {
-            const int gy = oy ? 2 * abs(oy) - 1 : 0;
-            const int rest = T4 - gz * gz - gy * gy;
+            const long long gy = oy ? 2 * abs(oy) - 1 : 0;
+            const long long rest = (long long)T4 - gz * gz - gy * gy;
             if (rest < 0) continue;
-            for (int ox = -B; ox <= B; ++ox) {
-                const int gx = ox ? 2 * abs(ox) - 1 : 0;
-                if (gx * gx <= rest) ++count;
-            }
+            count += 2 * ((na_isqrt((int)rest) + 1) / 2) + 1;
         }
     }
     a.selfS[i] = a.hd * (double)count;
@@ -129,14 +128,6 @@ __global__ void k_na_level(NaArgs a, int l)
         s += child[cx + (int64_t)nc * (cy + (int64_t)nc * cz)];
     }
     a.pyr[a.lvl_off[l] + f] = s;
-}
-
-__device__ __forceinline__ int na_isqrt(int x)
-{
-    int r = (int)sqrtf((float)x);
-    while (r > 0 && r * r > x) --r;
-    while ((r + 1) * (r + 1) <= x) ++r;
-    return r;
 }
 
 // floor(a / 2^s) and ceil(a / 2^s) for signed a (arithmetic shift rounds toward -inf)
@@ -242,8 +233,9 @@ extern "C" nl_status nl_apply_fast_noalloc(int dim, int n, double delta, const d
                      "nrhs >= 1, dtype F32/F64, self term)");
         return NL_EINVAL;
     }
-    if (!delta_field && !(delta > 0.0 && delta < 1.0e30)) {
-        nl_set_error("nl_apply_fast_noalloc: constant horizon must be > 0 and finite");
+    if (!delta_field && !(delta > 0.0 && delta <= NL_NOALLOC_MAX_DELTA)) {
+        nl_set_error("nl_apply_fast_noalloc: constant horizon must be in (0, %g] (got %g)",
+                     NL_NOALLOC_MAX_DELTA, delta);
         return NL_EINVAL;
     }
     if (!(alpha >= 0.0 && alpha < dim + 2.0)) {

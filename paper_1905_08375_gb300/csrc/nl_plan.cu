@@ -1,7 +1,11 @@
 // nl_plan.cu -- plan creation: validation, horizon data, offset tables,
 // polynomial coefficients, exterior and self terms (host + plan-time kernels).
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <new>
+#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -30,6 +34,65 @@ nl_status nl_cuda_fail(cudaError_t e, const char *what)
 }
 
 extern "C" const char *nl_last_error(void) { return g_err; }
+
+// ------------------------------------------------------------------------
+// failure handling on the host: injected host-allocation failures and the
+// limit of the library's bounded host waits
+// ------------------------------------------------------------------------
+static std::atomic<long long> g_fail_after{ -1 };     // < 0: disarmed
+static std::atomic<long long> g_wait_limit_ns{ 600LL * 1000000000LL };
+
+bool nl_host_alloc_allowed()
+{
+    long long v = g_fail_after.load();
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v != 0;
+    }
+    return true;
+}
+
+extern "C" nl_status nl_debug_fail_host_alloc(int after)
+{
+    g_fail_after.store(after < 0 ? -1 : after);
+    return NL_OK;
+}
+
+extern "C" nl_status nl_set_wait_limit(double seconds)
+{
+    if (!(seconds > 0.0) || seconds > 1.0e6) {
+        nl_set_error("nl_set_wait_limit: need 0 < seconds <= 1e6 (got %g)", seconds);
+        return NL_EINVAL;
+    }
+    g_wait_limit_ns.store((long long)(seconds * 1e9));
+    return NL_OK;
+}
+
+double nl_wait_limit_seconds() { return (double)g_wait_limit_ns.load() * 1e-9; }
+
+extern "C" nl_status nl_wait_poll(int (*poll)(void *ctx), void *ctx, double seconds)
+{
+    if (!poll) {
+        nl_set_error("nl_wait_poll: null poll function");
+        return NL_EINVAL;
+    }
+    if (!(seconds > 0.0)) seconds = nl_wait_limit_seconds();
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const int r = poll(ctx);
+        if (r > 0) return NL_OK;
+        if (r < 0) {
+            nl_set_error("nl_wait_poll: the polled condition reported an error (%d)", r);
+            return NL_ECUDA;
+        }
+        const double dt =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt > seconds) {
+            nl_set_error("bounded wait gave up after %.3g s", seconds);
+            return NL_ETIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
 
 // ------------------------------------------------------------------------
 // constants of the kernel family
@@ -334,7 +397,17 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     }
 
     // ---- host-side horizon scan (validation of Eq. (2.3)) ----
-    std::vector<double> delta(N);
+    if (!nl_host_alloc_allowed()) {
+        nl_set_error("nl_plan_create: host allocation of the horizon scan failed");
+        return NL_ENOMEM;
+    }
+    std::vector<double> delta;
+    try {
+        delta.resize(N);
+    } catch (const std::bad_alloc &) {
+        nl_set_error("nl_plan_create: host allocation of the horizon scan failed");
+        return NL_ENOMEM;
+    }
     for (int64_t i = 0; i < N; ++i) delta[i] = hz->delta_field ? hz->delta_field[i] : hz->delta;
     int Rmax = 0;
     int64_t thr_max = 0;
@@ -363,7 +436,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
             }
     }
 
-    nl_plan *p = (nl_plan *)calloc(1, sizeof(nl_plan));
+    nl_plan *p = nl_host_alloc_allowed() ? (nl_plan *)calloc(1, sizeof(nl_plan)) : nullptr;
     if (!p) {
         nl_set_error("nl_plan_create: host allocation failed");
         return NL_ENOMEM;
@@ -642,7 +715,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
 extern "C" nl_status nl_plan_destroy(nl_plan *p)
 {
     if (!p) return NL_OK;
-    if (p->magic != NL_PLAN_MAGIC) {
+    if (!nl_plan_ok(p)) {
         nl_set_error("nl_plan_destroy: not a plan");
         return NL_EINVAL;
     }

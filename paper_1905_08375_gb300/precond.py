@@ -47,14 +47,10 @@ def collect_pairs(plan, n, seeds, cap=64, rtol=1e-10, device="cuda"):
         cnt, st = nl.nl_cg_history(plan, f, x, hist, rtol=rtol, maxit=100000)
         if cnt < 2:
             continue
-        H = hist[: cnt - 1]                      # drop the last snapshot (~ converged)
-        e = x[None, :] - H
-        Lx = torch.empty_like(H)
-        nl.nl_apply(plan, H, Lx)
-        r = f[None, :] + Lx
-        xo = torch.empty((H.shape[0], n * n), dtype=torch.float32, device=device)
+        count = cnt - 1                          # drop the last snapshot (~ converged)
+        xo = torch.empty((count, n * n), dtype=torch.float32, device=device)
         eo = torch.empty_like(xo)
-        nl.nl_net_prepare_pairs(plan, r.contiguous(), e.contiguous(), xo, eo)
+        nl.nl_net_history_pairs(plan, f, x, hist, count, xo, eo)
         xs.append(xo)
         es.append(eo)
     x = torch.cat(xs).reshape(-1, n, n).contiguous()

@@ -88,3 +88,29 @@ def test_config4_sizes(n):
     st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=50000)
     assert st["converged"] and st["rel_residual"] <= 1e-8, st
     assert oracle_residual_scalar(xt.cpu().numpy(), f, n, fld)[0] <= 1.01e-8
+
+
+def test_wait_limit_runs_out_and_the_plan_recovers():
+    # the host gives up on the first chunk (a wait limit far below one chunk's run time) and
+    # returns NL_ETIMEOUT; the chunk's kernels finish on their own, and after a device
+    # synchronisation the same plan solves normally with the default limit
+    n = 256
+    fld = synth.heterogeneous_2d(n=n, seed=17)
+    f = synth.cg_rhs(n, seed=18, count=4)
+    plan = nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                             coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+    ft = torch.tensor(f, dtype=torch.float64, device=DEV)
+    xt = torch.empty_like(ft)
+    try:
+        nl.nl_set_wait_limit(1e-6)
+        with pytest.raises(nl.NlError) as ei:
+            nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000)
+        assert str(ei.value).startswith("NL_ETIMEOUT"), str(ei.value)
+    finally:
+        torch.cuda.synchronize()
+        nl.nl_set_wait_limit(600.0)
+    st = nl.nl_cg_solve(plan, ft, xt, rtol=1e-8, maxit=20000)
+    assert st["converged"] and st["rel_residual"] <= 1e-8, st
+    res = oracle_residual_scalar(xt.cpu().numpy(), f, n, fld)
+    assert np.all(res <= 1.01e-8), res
+    plan.close()

@@ -199,3 +199,29 @@ def test_two_level_cg_follows_buffer_moves_and_weight_updates():
     assert s3["converged"] and s3["iterations"] == s4["iterations"], (s3, s4)
     assert torch.equal(x3, x4)
     assert not torch.equal(x1, x3)                                 # the weights did change
+
+
+def test_history_pairs_match_pairs_from_oracle_residuals():
+    # nl_net_history_pairs forms r_k = f + L x_k and e_k = x - x_k itself; the same pairs from
+    # the oracle's FP64 residuals through nl_net_prepare_pairs must agree
+    n, count = 32, 3
+    fld, plan, dinv = _sym_plan(n, 31)
+    rng = np.random.default_rng(32)
+    f = synth.gaussian_field(rng, 2, n).reshape(-1)
+    x = synth.gaussian_field(rng, 2, n).reshape(-1)
+    H = np.stack([synth.gaussian_field(rng, 2, n).reshape(-1) for _ in range(count + 1)])
+    Lh = oracle.direct_scalar(H[:count], 2, n, fld["delta"], alpha=1.5, coef=oracle.COEF_XY,
+                              a=fld["a"], symmetric=True)
+    r64 = f[None, :] + Lh
+    e64 = x[None, :] - H[:count]
+    xo_ref = torch.empty((count, n * n), dtype=torch.float32, device=DEV)
+    eo_ref = torch.empty_like(xo_ref)
+    nl.nl_net_prepare_pairs(plan, torch.tensor(r64, device=DEV), torch.tensor(e64, device=DEV),
+                            xo_ref, eo_ref)
+    xo = torch.full_like(xo_ref, float("nan"))
+    eo = torch.full_like(xo_ref, float("nan"))
+    nl.nl_net_history_pairs(plan, torch.tensor(f, device=DEV), torch.tensor(x, device=DEV),
+                            torch.tensor(H, device=DEV), count, xo, eo)
+    for got, ref in ((xo, xo_ref), (eo, eo_ref)):
+        g, r = got.double().cpu().numpy(), ref.double().cpu().numpy()
+        assert np.linalg.norm(g - r) / np.linalg.norm(r) < 1e-6

@@ -1,7 +1,7 @@
 """Pins of the oracle's symmetrised leaf-set operator (the divergence-type form of the Sec. 3
 polynomial operator, a project extension): it reduces to the one-sided leaf-set operator for a
-constant horizon, its matrix is symmetric and negative semi-definite, it annihilates constants
-in the interior, and its transpose half equals a scatter over each node's leaf rows (the form
+constant horizon (globally, and locally where every node that reaches a node has its
+horizon), its matrix is symmetric and negative semi-definite, and its transpose half equals a scatter over each node's leaf rows (the form
 a fast kernel would use)."""
 import numpy as np
 import pytest
@@ -58,11 +58,27 @@ def test_matrix_symmetric_negative_semidefinite(K):
     assert np.abs(B - B.T).max() > 1e-3 * np.abs(B).max()
 
 
-def test_constants_annihilated_in_the_interior():
-    n = 32
-    delta = smooth_delta(n, 1.5, 3.5, seed=5)
-    Lu = oracle.fast_sym_leafset(np.ones(n * n), 2, 5, delta, K=1, alpha=1.0).reshape(n, n)
-    assert np.abs(Lu[6:-6, 6:-6]).max() <= 1e-10 * np.abs(Lu).max()
+@pytest.mark.parametrize("K", [0, 1])
+def test_locally_constant_horizon_matches_one_sided(K):
+    # horizon 2.5h for x < 1/2 and 4.5h beyond: every node k whose leaf set reaches a node i
+    # with x_i < 1/2 - 6h has the horizon of i (exterior cells take it too), so there both
+    # halves of the symmetrised weights equal the one-sided ones and the operators agree on a
+    # field that the weights do not annihilate; near the jump they differ
+    n, L = 32, 5
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    delta = np.where(X < 0.5, 2.5 * h, 4.5 * h).reshape(-1)
+    a = np.exp(0.2 * np.random.default_rng(7).standard_normal(n * n))
+    u = (X ** 2 + 0.5 * Y ** 2 + X * Y).reshape(-1)
+    kw = dict(K=K, alpha=1.0, coef=oracle.COEF_XY, a=a)
+    sym = oracle.fast_sym_leafset(u, 2, L, delta, **kw).reshape(n, n)
+    one = oracle.fast_leafset(u, 2, L, delta, **kw).reshape(n, n)
+    left = x < 0.5 - 6 * h
+    assert np.abs(one[:, left]).min() > 0.0
+    assert np.abs(sym[:, left] - one[:, left]).max() <= 1e-12 * np.abs(one[:, left]).max()
+    jump = np.abs(x - 0.5) < 2 * h
+    assert np.abs(sym[:, jump] - one[:, jump]).max() > 1e-3 * np.abs(one).max()
 
 
 def leaf_run(X, R2x4, dy2):

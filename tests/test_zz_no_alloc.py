@@ -67,3 +67,40 @@ def test_rejects_grids_beyond_the_static_array():
         nl.nl_apply_fast_noalloc(2, 2048, 0.01, u, u.clone(), nrhs=1)
     with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
         nl.nl_apply_fast_noalloc(2, 1000, 0.01, u, u.clone(), nrhs=1)
+
+
+def test_rejects_bad_horizons_and_mismatched_buffers():
+    # host-side checks: the C entry point rejects horizons outside (0, 2]; the binding rejects
+    # buffers whose dtype or size do not match what the kernels would read and write
+    n = 64
+    u = torch.zeros(n * n, dtype=torch.float64, device=DEV)
+    for bad in (0.0, -0.1, 2.5, float("inf"), float("nan")):
+        with pytest.raises(nl.NlError, match="NL_EINVAL"):
+            nl.nl_apply_fast_noalloc(2, n, bad, u, u.clone())
+    with pytest.raises(ValueError, match="same dtype"):
+        nl.nl_apply_fast_noalloc(2, n, 0.1, u, torch.zeros(n * n, dtype=torch.float32, device=DEV))
+    with pytest.raises(ValueError, match="elements"):
+        nl.nl_apply_fast_noalloc(2, n, 0.1, u, torch.zeros(n * n - 1, dtype=torch.float64,
+                                                          device=DEV), nrhs=1)
+    with pytest.raises(ValueError, match="delta field"):
+        nl.nl_apply_fast_noalloc(2, n, torch.full((n * n - 3,), 0.1, dtype=torch.float64,
+                                                  device=DEV), u, u.clone())
+
+
+def test_out_of_range_field_values_stay_bounded():
+    # NaN and huge horizons in a device field are clamped for the geometry: the call finishes
+    # promptly and the other nodes are unaffected
+    n = 64
+    rng = np.random.default_rng(5)
+    dl = np.full(n * n, 3.0 / n)
+    u = torch.tensor(rng.standard_normal(n * n), dtype=torch.float64, device=DEV)
+    ref = torch.empty_like(u)
+    nl.nl_apply_fast_noalloc(2, n, torch.tensor(dl, device=DEV), u, ref)
+    bad = dl.copy()
+    bad[100], bad[2000] = float("nan"), 1.0e12
+    out = torch.empty_like(u)
+    nl.nl_apply_fast_noalloc(2, n, torch.tensor(bad, device=DEV), u, out)
+    torch.cuda.synchronize()
+    keep = np.ones(n * n, dtype=bool)
+    keep[[100, 2000]] = False
+    assert torch.equal(out.cpu()[torch.tensor(keep)], ref.cpu()[torch.tensor(keep)])
