@@ -184,15 +184,47 @@ def _alu_roof(kernel, flops, ms, peak, src):
             "peak_source": src}
 
 
-FP32_SRC = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
-FP64_SRC = "nominal FP64 1.25 TFLOP/s (profiling recipe)"
+FP32_SRC = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measurement)"
+FP64_SRC = "nominal FP64 1.25 TFLOP/s (profiling recipe; no measurement)"
+
+# FMA peaks measured on the device by nl_measure_peaks before the timed region (run_gpu)
+MEASURED_ALU = {}
+
+
+def fp32_peak():
+    """The FP32 roofline denominator: the measured FMA peak (the larger of the scalar and the
+    paired f32x2 chains, as the kernels use both) or, without a measurement, the derived one."""
+    if MEASURED_ALU:
+        a, b = MEASURED_ALU["fp32_tflops"], MEASURED_ALU["fp32x2_tflops"]
+        return max(a, b), (f"measured FMA-chain microbenchmark (nl_measure_peaks): max of scalar "
+                           f"{a:.2f} and paired f32x2 {b:.2f} TFLOP/s")
+    return FP32_PEAK_TFLOPS, FP32_SRC
+
+
+def fp64_peak():
+    if MEASURED_ALU:
+        v = MEASURED_ALU["fp64_tflops"]
+        return v, f"measured FMA-chain microbenchmark (nl_measure_peaks): FP64 {v:.3f} TFLOP/s"
+    return FP64_NOMINAL_TFLOPS, FP64_SRC
 
 
 class C2(Workload):
-    """2-D heterogeneous 1024^2: direct FP32 + fast (K = 0) per step."""
+    """2-D heterogeneous 1024^2: direct FP32 + fast (K = 0) per step; beside the timed step the
+    FP64 applies, every route of the fast algorithm and CG to 1e-8 (learned vs Jacobi) at
+    256^2 are timed and checked against the oracle."""
     name = "c2"
     metric = "L_delta u applies (direct + fast) in Gpts/s on the 2-D heterogeneous 1024^2 grid"
     dtype = "f32 data; exact 64-bit integer partial sums (fast)"
+    # the route of the fast algorithm the timed step uses, and the others timed beside it
+    STEP_ROUTE = "panels"
+    ROUTES = (("panels", "NL_FAST_PANELS", "Sec. 3 as written: Step 2 panel sums level by level, "
+               "Step 3 adds the panels of Algorithm 1 one by one"),
+              ("rowprefix", "NL_FAST_ROWPREFIX", "deviation (f1): per-level row prefix sums, "
+               "each run of Algorithm 1's panels added as one difference"),
+              ("leafrows", "NL_FAST_LEAFROWS", "deviation: the panels of Algorithm 1 tile the "
+               "leaf cells meeting the ball, so each leaf row of the ball is one difference of "
+               "leaf-row prefix sums; the coarse levels are not formed"))
+    FAST_BYTES_PER_NODE = 27        # u 4 + b 4 + out 4 + plan 4 + the pyramid written and read
 
     def setup(self, n=1024):
         nl, torch = self.nl, self.torch
@@ -202,22 +234,32 @@ class C2(Workload):
         f = self.f
         self.direct = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
                                         coef=nl.NL_COEF_XY, a=f["a"])
-        self.fast = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
-                                      coef=nl.NL_COEF_XY, a=f["a"])
-        # the other routes of the same Sec. 3 sums (bitwise equal outputs), timed for reference
-        self.fast_variants = {
+        # every route of the Sec. 3 sums (bitwise equal outputs)
+        self.fast_routes = {
             name: nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
-                                    coef=nl.NL_COEF_XY, a=f["a"], fast_variant=v)
-            for name, v in (("panels", nl.NL_FAST_PANELS), ("rowprefix", nl.NL_FAST_ROWPREFIX))}
+                                    coef=nl.NL_COEF_XY, a=f["a"],
+                                    fast_variant=getattr(nl, const))
+            for name, const, _ in self.ROUTES}
+        self.fast = self.fast_routes[self.STEP_ROUTE]
         self.u = torch.tensor(f["u"][0], dtype=torch.float32, device=self.dev)
         self.out_d = torch.empty_like(self.u)
         self.out_f = torch.empty_like(self.u)
+        self.u64 = torch.tensor(f["u"][0], dtype=torch.float64, device=self.dev)
+        self.out_d64 = torch.empty_like(self.u64)
+        self.out_f64 = torch.empty_like(self.u64)
         self.units = 2 * n * n
         self.launches = 1 + 3             # direct; fast: bounds, fused Step 2, gather
         self.config = {"workload": "2D heterogeneous nonlocal diffusion 1024x1024, "
                                    "delta=h(4+12s), a lognormal sigma 0.5 smoothed 8h, "
                                    "gamma=a(x)a(y)C_delta|xi|^-1.5; direct FP32 apply + fast "
-                                   "(Sec. 3, K=0, p=1) apply per step", "n": n, "points": n * n}
+                                   "(Sec. 3, K=0, p=1, Algorithm 1 panel by panel) apply per "
+                                   "step", "n": n, "points": n * n,
+                       "fast_route": self.STEP_ROUTE}
+        # CG on the symmetrised operator at 256^2 (the second half of the metric): the learned
+        # preconditioner is trained here, before any timing
+        self.cg = C4(self.dev, self.seed)
+        self.cg.peaks = getattr(self, "peaks", None)
+        self.cg.setup()
 
     def step(self):
         self.nl.nl_apply(self.direct, self.u, self.out_d)
@@ -225,42 +267,65 @@ class C2(Workload):
 
     def kernels(self, flush, reps):
         nl = self.nl
-        t_direct = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
-        nl.nl_plan_profile(self.fast, True)
-        t_fast = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u, self.out_f),
-                              min(reps, 60), flush)
-        prof = nl.nl_plan_profile_read(self.fast)
-        nl.nl_plan_profile(self.fast, False)
-        t_s2 = prof["step2_ms"] / max(prof["applies"], 1)
-        t_s3 = prof["step3_ms"] / max(prof["applies"], 1)
         n = self.n
+        N = n * n
+        pk = self.peaks["hbm_gbs"]
+        t_direct = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
+        per = {"direct_fp32_ms": round(t_direct, 4),
+               "direct_gpts": round(N / (t_direct * 1e-3) / 1e9, 4)}
+        routes = {}
+        for name, const, what in self.ROUTES:
+            plan = self.fast_routes[name]
+            nl.nl_plan_profile(plan, True)
+            t = self.time_fn(lambda: nl.nl_apply_fast(plan, self.u, self.out_f), min(reps, 40),
+                             flush)
+            prof = nl.nl_plan_profile_read(plan)
+            nl.nl_plan_profile(plan, False)
+            k = max(prof["applies"], 1)
+            ach = self.FAST_BYTES_PER_NODE * N / (t * 1e-3) / 1e9
+            routes[name] = {"variant": const, "what": what, "ms": round(t, 4),
+                            "step2_ms": round(prof["step2_ms"] / k, 4),
+                            "step3_ms": round(prof["step3_ms"] / k, 4),
+                            "gpts": round(N / (t * 1e-3) / 1e9, 4),
+                            "hbm_frac": round(ach / pk, 4),
+                            "paper_algorithm": name == "panels"}
+        per["fast_routes"] = routes
+        per["fast_route_timed_in_step"] = self.STEP_ROUTE
+        per["fast_ms"] = routes[self.STEP_ROUTE]["ms"]
+        per["fast_gpts"] = routes[self.STEP_ROUTE]["gpts"]
+        per["fast_hbm_bytes_per_node"] = (f"{self.FAST_BYTES_PER_NODE} (u 4, b 4, out 4, plan "
+                                          "4, pyramid 8 written + 8 read, coarse levels 1/3)")
+        # FP64 data: the direct sum in FP64 and the fast apply with FP64 panel sums
+        t_d64 = self.time_fn(lambda: nl.nl_apply(self.direct, self.u64, self.out_d64),
+                             min(reps, 10), flush)
+        t_f64 = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u64, self.out_f64),
+                             min(reps, 10), flush)
+        per.update({"direct_fp64_ms": round(t_d64, 4), "fast_fp64_ms": round(t_f64, 4),
+                    "direct_fp64_gpts": round(N / (t_d64 * 1e-3) / 1e9, 4),
+                    "fast_fp64_gpts": round(N / (t_f64 * 1e-3) / 1e9, 4)})
+        nl.nl_apply(self.direct, self.u64, self.out_d64)
+        nl.nl_apply_fast(self.fast, self.u64, self.out_f64)
+        nl.nl_apply(self.direct, self.u, self.out_d)
+        nl.nl_apply_fast(self.fast, self.u, self.out_f)
+        # CG to relative residual 1e-8, learned two-level preconditioner vs Jacobi
+        _, cgp = self.cg.kernels(flush, 3)
+        per["cg_256_8rhs"] = {k: cgp[k] for k in ("learned_ms", "learned", "jacobi_ms", "jacobi",
+                                                  "learned_speedup_over_jacobi", "training")}
         nb = float(ball_counts(self.f["delta"], n, 2).sum())
         flops = 4.0 * nb
-        per = {"direct_fp32_ms": round(t_direct, 4), "fast_ms": round(t_fast, 4),
-               "fast_step2_ms": round(t_s2, 4), "fast_step3_gather_ms": round(t_s3, 4),
-               "direct_gpts": round(n * n / (t_direct * 1e-3) / 1e9, 4),
-               "fast_gpts": round(n * n / (t_fast * 1e-3) / 1e9, 4),
-               "fast_route": "leaf rows (NL_FAST_LEAFROWS)"}
-        for name, plan in self.fast_variants.items():
-            t = self.time_fn(lambda: nl.nl_apply_fast(plan, self.u, self.out_f),
-                             min(reps, 30), flush)
-            per[f"fast_{name}_ms"] = round(t, 4)
-        nl.nl_apply_fast(self.fast, self.u, self.out_f)
-        if t_direct >= t_s3:
-            roof = _alu_roof("k_direct2d_x2<16,TY> (direct FP32)", flops, t_direct,
-                             FP32_PEAK_TFLOPS, FP32_SRC)
+        t_fast = routes[self.STEP_ROUTE]["ms"]
+        if t_direct >= t_fast:
+            roof = _alu_roof("k_direct2d_x2<16,TY> (direct FP32)", flops, t_direct, *fp32_peak())
             roof["algorithmic_per_launch"] = f"{flops:.4g} flop (4 per neighbour term)"
         else:
-            # Step 3 reads per node: thr4 4 + fastF 8 + selfS 8 + u 4 and writes 4 B; the
-            # leaf-row prefix sums it gathers (8 B per node) come from DRAM once
-            byts = n * n * (4 + 8 + 8 + 4 + 4 + 8)
-            ach = byts / (t_s3 * 1e-3) / 1e9
-            pk = self.peaks["hbm_gbs"]
-            roof = {"kernel": "k_fast_gather_leafrows<2> (Step 3)", "bound": "hbm",
-                    "achieved": round(ach, 2), "peak": pk, "unit": "GB/s",
+            byts = self.FAST_BYTES_PER_NODE * N
+            ach = byts / (t_fast * 1e-3) / 1e9
+            roof = {"kernel": f"fast apply, {self.STEP_ROUTE} route (Step 2 + Step 3)",
+                    "bound": "hbm", "achieved": round(ach, 2), "peak": pk, "unit": "GB/s",
                     "frac": round(ach / pk, 4), "traffic": None,
                     "peak_source": f"{self.peaks['_source']} hbm_gbs",
-                    "algorithmic_per_launch": f"{byts:.4g} B (36 B per node)"}
+                    "algorithmic_per_launch": f"{byts:.4g} B ({self.FAST_BYTES_PER_NODE} B per "
+                                              "node)"}
         return roof, per
 
     def e2e(self, flush, steps):
@@ -283,7 +348,10 @@ class C2(Workload):
 
     def outputs(self):
         return {"direct": self.out_d.double().cpu().numpy(),
-                "fast": self.out_f.double().cpu().numpy()}
+                "fast": self.out_f.double().cpu().numpy(),
+                "direct_fp64": self.out_d64.cpu().numpy(),
+                "fast_fp64": self.out_f64.cpu().numpy(),
+                "cg": self.cg.outputs()}
 
     @staticmethod
     def oracle_step(f, n, idx):
@@ -328,7 +396,7 @@ class C2K(Workload):
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         # per term: t = o2/R2, p = p0 + p1 t, ra g - p, times b_j, u_j - u_i, times, add
         roof = _alu_roof("k_direct_scalar<2,float,KAPPA> (staged tile)", 9.0 * nb, t,
-                         FP32_PEAK_TFLOPS, FP32_SRC)
+                         *fp32_peak())
         roof["algorithmic_per_launch"] = f"{9 * nb:.4g} flop (9 per neighbour term)"
         return roof, {"kappa_direct_fp32_ms": round(t, 4)}
 
@@ -382,8 +450,7 @@ class C1(Workload):
     def kernels(self, flush, reps):
         t = self.time_fn(self.step, reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 1).sum())
-        roof = _alu_roof("k_direct_split<1,double,POWER>", 4.0 * nb, t, FP64_NOMINAL_TFLOPS,
-                         FP64_SRC)
+        roof = _alu_roof("k_direct_split<1,double,POWER>", 4.0 * nb, t, *fp64_peak())
         roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term)"
         return roof, {"direct_fp64_ms": round(t, 4)}
 
@@ -447,8 +514,7 @@ class C3(Workload):
         t_d32 = self.time_fn(lambda: self.nl.nl_apply(self.plan32, self.u, o32), reps, flush)
         t_f32 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan32, self.u, o32), reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
-        roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, FP32_PEAK_TFLOPS,
-                         FP32_SRC)
+        roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, *fp32_peak())
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
         return roof, {"pd_fp32_ms": round(t, 4), "pd_fast_deg0_fp32_ms": round(t_f, 4),
                       "pd_delta32h_direct_fp32_ms": round(t_d32, 4),
@@ -533,7 +599,7 @@ class C3B(Workload):
         if self.last:
             self.launches = 5 * self.last["iterations"] + 8
         roof = _alu_roof("k_batch_pdx2<8,TY> (all 64 instances, one launch)",
-                         14.0 * nb, t, FP32_PEAK_TFLOPS, FP32_SRC)
+                         14.0 * nb, t, *fp32_peak())
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond, all instances)"
         return roof, {"batch_apply_fp32_ms": round(t, 4),
                       "batch_apply_gpts_s": round(self.points / (t * 1e-3) / 1e9, 3),
@@ -625,6 +691,7 @@ class C4(Workload):
         reps = max(3, min(reps, 10))
         sj = self.solve(nl.NL_PRECOND_JACOBI)
         self.jacobi_its = sj["iterations"]
+        self.x_jacobi = self.x.clone()
         t_j = self.time_fn(lambda: self.solve(nl.NL_PRECOND_JACOBI), reps, flush)
         t_l = self.time_fn(lambda: self.solve(nl.NL_PRECOND_LEARNED), reps, flush)
         u = self.torch.randn(self.n * self.n, device=self.dev)
@@ -641,7 +708,7 @@ class C4(Workload):
         self.launches = None
         # the operator as CG applies it: all right-hand sides in one launch
         roof = _alu_roof(f"k_direct2d_x2s (symmetric CG operator, {self.nrhs} RHS)",
-                         6.0 * nb * self.nrhs, t_op8, FP32_PEAK_TFLOPS, FP32_SRC)
+                         6.0 * nb * self.nrhs, t_op8, *fp32_peak())
         roof["algorithmic_per_launch"] = (f"{6 * nb * self.nrhs:.4g} flop (6 per one-sided ball "
                                           f"term, {self.nrhs} RHS)")
         self.solve(nl.NL_PRECOND_LEARNED)          # leave the learned solution in x
@@ -670,7 +737,10 @@ class C4(Workload):
                 "d2h_bytes_per_step": b, "ms_per_step": round(ms, 4)}
 
     def outputs(self):
-        return {"x": self.x.cpu().numpy()}
+        out = {"x": self.x.cpu().numpy()}
+        if getattr(self, "x_jacobi", None) is not None:
+            out["x_jacobi"] = self.x_jacobi.cpu().numpy()
+        return out
 
 
 class C4L(C4):
@@ -714,7 +784,7 @@ class C5(Workload):
         n = self.n
         nb = 8.0 * float(ball_counts(np.full(1, 4.0 / n), n, 3)[0]) * n ** 3
         roof = _alu_roof("k_direct3d_x2<4,4> (slab sweep)", 4.0 * nb, t_d,
-                         FP32_PEAK_TFLOPS, FP32_SRC)
+                         *fp32_peak())
         roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term, 8 RHS)"
         return roof, {"direct_fp32_8rhs_ms": round(t_d, 4), "fast_fp32_8rhs_ms": round(t_f, 4)}
 
@@ -788,8 +858,7 @@ class EX(Workload):
         t_f = self.time_fn(lambda: nl.nl_apply_fast(self.plan, self.u, self.out_f), reps, flush)
         dl = self.delta if not np.isscalar(self.delta) else np.full(self.n ** self.d, self.delta)
         nb = float(ball_counts(dl, self.n, self.d).sum())
-        roof = _alu_roof("k_direct_split (direct FP64)", 4.0 * nb, t_d, FP64_NOMINAL_TFLOPS,
-                         FP64_SRC)
+        roof = _alu_roof("k_direct_split (direct FP64)", 4.0 * nb, t_d, *fp64_peak())
         roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term)"
         return roof, {"direct_fp64_ms": round(t_d, 4), "fast_fp64_ms": round(t_f, 4),
                       "fast_over_direct_speedup": round(t_d / t_f, 2)}
@@ -921,6 +990,7 @@ def oracle_sample(w, outs, budget_s=20.0):
     f, n = w.f, w.n
     d = 1 if name == "c1" else 2
     N = n ** d
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
     idx = rng.choice(N, size=min(N, 256), replace=False)
     cls.oracle_step(f, n, idx)
@@ -931,11 +1001,43 @@ def oracle_sample(w, outs, budget_s=20.0):
     refs, units = cls.oracle_step(f, n, idx2)
     dt = time.perf_counter() - t0
     par = {"sampled_points": m}
-    for k, ref in refs.items():
-        got = outs[k][..., idx2] if outs[k].ndim > 1 else outs[k][idx2]
-        par[f"{k}_rel_l2"] = _rel(got, ref)
-    return ({"value": round(units / dt / 1e9, 9), "unit": "Gpts/s", "cores": oracle.num_threads(),
-             "kind": "oracle", "sample": f"{m} random nodes of the workload ({dt:.1f} s)"}, par)
+    for k, got_all in outs.items():
+        base = k[:-5] if k.endswith("_fp64") else k
+        if base not in refs:
+            continue
+        got = got_all[..., idx2] if got_all.ndim > 1 else got_all[idx2]
+        par[f"{k}_rel_l2"] = _rel(got, refs[base])
+    if "cg" in outs:
+        par.update(cg_residuals(w.cg, outs["cg"]))
+    # the same oracle on one thread, on a sample a tenth of the budget
+    m1 = int(min(N, max(64, 0.1 * budget_s / max(per_pt * cores, 1e-9))))
+    idx1 = rng.choice(N, size=m1, replace=False)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        _, units1 = cls.oracle_step(f, n, idx1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    return ({"value": round(units / dt / 1e9, 9), "unit": "Gpts/s", "cores": cores,
+             "kind": "oracle", "sample": f"{m} random nodes of the workload ({dt:.1f} s)",
+             "single_thread": {"value": round(units1 / dt1 / 1e9, 9), "unit": "Gpts/s",
+                               "cores": 1, "sample": f"{m1} random nodes ({dt1:.1f} s)"}}, par)
+
+
+def cg_residuals(cgw, outs):
+    """FP64 oracle residuals ||f + L x|| / ||f|| of the GPU CG solutions of the CG workload."""
+    import oracle
+    Lx = oracle.direct_scalar(outs["x"], 2, cgw.n, cgw.f["delta"], alpha=1.5,
+                              coef=oracle.COEF_XY, a=cgw.f["a"], symmetric=True)
+    res = np.linalg.norm(cgw.rhs + Lx, axis=1) / np.linalg.norm(cgw.rhs, axis=1)
+    out = {"cg_learned_fp64_oracle_residual_max": float(res.max())}
+    if "x_jacobi" in outs:
+        Lj = oracle.direct_scalar(outs["x_jacobi"], 2, cgw.n, cgw.f["delta"], alpha=1.5,
+                                  coef=oracle.COEF_XY, a=cgw.f["a"], symmetric=True)
+        rj = np.linalg.norm(cgw.rhs + Lj, axis=1) / np.linalg.norm(cgw.rhs, axis=1)
+        out["cg_jacobi_fp64_oracle_residual_max"] = float(rj.max())
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -970,6 +1072,8 @@ def run_gpu(args, peaks):
     if args.size:
         w.size = args.size
     w.peaks = peaks
+    from paper_1905_08375_gb300 import binding as nlb
+    MEASURED_ALU.update(nlb.nl_measure_peaks())       # FMA peaks, before any timing
     w.setup()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -1002,8 +1106,9 @@ def run_gpu(args, peaks):
         ms_step = max_over_ranks(ms_step, dev)
     value = whole_job_value(w.value(ms_step), ws, w.higher_is_better)
     reps = max(3, min(steps, 50))
-    roof, per = w.kernels(flush, reps)
-    e2e = w.e2e(flush, min(steps, 20))
+    with ClockSampler(local) as clk2:
+        roof, per = w.kernels(flush, reps)
+        e2e = w.e2e(flush, min(steps, 20))
     result = dict(metric=w.metric, value=round(value, 6), unit=w.unit, n_gpus=ws, steps=steps,
                   warmup=args.warmup, ms_per_step=round(ms_step, 4),
                   higher_is_better=w.higher_is_better,
@@ -1014,6 +1119,8 @@ def run_gpu(args, peaks):
                   gpu_launches=(w.launches * steps) if w.launches else None,
                   peaks_source=peaks["_source"])
     result["clocks"] = clk.summary()
+    result["clocks_per_path"] = clk2.summary()      # the per-path and end-to-end timings
+    result["alu_peaks_measured"] = {k: round(v, 3) for k, v in MEASURED_ALU.items()}
     return result, w, rank, ws
 
 

@@ -359,6 +359,17 @@ typedef struct {
 
 nl_status nl_get_plan_info(const nl_plan *plan, nl_plan_info *info);
 
+/*
+ * Measured arithmetic peaks of the current device, the denominators of the ALU roofline
+ * fractions reported with the direct sums (the paper, which reports MATLAB wall times, has no
+ * counterpart).  Eight independent FMA chains per thread on 4 x 256 threads per SM; an FMA is
+ * two flops, a paired f32x2 FMA four; best of five launches timed with CUDA events on
+ * `stream` (synchronises it).  Outputs in TFLOP/s: scalar FP32 FMA, paired f32x2 FMA, FP64 FMA.
+ * Allocates and frees a small sink buffer.  Errors: NL_EINVAL (null output), NL_ECUDA.
+ */
+nl_status nl_measure_peaks(double *fp32_tflops, double *fp32x2_tflops, double *fp64_tflops,
+                           void *stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *nl_last_error(void);
 

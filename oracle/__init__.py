@@ -68,6 +68,8 @@ def lib():
         L = ctypes.CDLL(_LIB)
         d, i, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         L.or_num_threads.restype = i
+        L.or_set_threads.restype = None
+        L.or_set_threads.argtypes = [i]
         L.or_sphere_area.restype = d
         L.or_sphere_area.argtypes = [i]
         L.or_sigma.restype = d
@@ -107,6 +109,11 @@ def _ptr(x):
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_threads(t: int) -> None:
+    """OpenMP threads of later oracle calls (for timing; the results do not depend on it)."""
+    lib().or_set_threads(int(t))
 
 
 def sphere_area(d: int) -> float:

@@ -54,6 +54,16 @@ int or_num_threads(void)
 #endif
 }
 
+/* number of OpenMP threads of the following calls (timing only; results do not depend on it) */
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* Small helpers                                                       */
 /* ------------------------------------------------------------------ */

@@ -612,3 +612,13 @@ def nl_debug_fail_host_alloc(after: int):
     fn.restype = ctypes.c_int
     fn.argtypes = [ctypes.c_int]
     _check(fn(int(after)))
+
+
+def nl_measure_peaks(stream=None) -> dict:
+    """Measured FMA peaks of the current device in TFLOP/s (fp32, fp32x2, fp64)."""
+    fn = lib().nl_measure_peaks
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.c_void_p]
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(fn(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream_ptr(stream)))
+    return {"fp32_tflops": a.value, "fp32x2_tflops": b.value, "fp64_tflops": c.value}

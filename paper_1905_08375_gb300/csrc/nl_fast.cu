@@ -755,6 +755,189 @@ __global__ void __launch_bounds__(1024) k_step2_rowprefix(Step2Args a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Step 2 of the panel-by-panel form (Sec. 3 as written) in one launch after k_absmax_parts:
+// one block per band (the leaf rows of one panel row of level lf = L - c) (1) quantises the
+// band's leaf values, (2) sums the 2^d children of every panel of levels L-1 .. lf inside the
+// band, and (3) adds the band's part of every coarser panel with 64-bit integer atomics (those
+// levels were zeroed by k_absmax_parts).  Each panel then holds the integer sum of its leaves,
+// the same integer the level-by-level kernels produce.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_step2_panels(Step2Args a)
+{
+    __shared__ float s_w[32];
+    const int nt = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = nt / 32;
+    float m = 0.f;
+    for (int k = tid; k < a.nparts; k += nt) m = fmaxf(m, a.part[k]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_w[warp] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < nw; ++w) m = fmaxf(m, s_w[w]);
+    if (blockIdx.x == 0 && tid == 0) *a.mx = __float_as_uint(m);
+    int sh = 62;
+    if (m > 0.f) {
+        int e1, e2;
+        frexpf(m, &e1);
+        frexpf((float)a.N, &e2);
+        sh = 62 - e1 - e2;
+    }
+    const int n = a.n, d = a.d, L = a.L, lf = a.lf;
+    const int S = 1 << a.c;
+    const int bands_y = d > 1 ? n / S : 1;
+    const int by = d > 1 ? (int)(blockIdx.x % bands_y) : 0;
+    const int bz = d > 2 ? (int)(blockIdx.x / bands_y) : 0;
+    const int rows_y = d > 1 ? S : 1, rows_z = d > 2 ? S : 1;
+    long long *pyr = a.pyr;
+    // (1) leaf values round(u b 2^sh)
+    {
+        long long *leaf = pyr + a.lvl_off[L];
+        const int64_t cnt = (int64_t)rows_y * rows_z * n;
+        for (int64_t t = tid; t < cnt; t += nt) {
+            const int x = (int)(t % n), r = (int)(t / n);
+            const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
+            const int64_t g = x + (int64_t)n * (iy + (int64_t)n * iz);
+            leaf[g] = __float2ll_rn(ldexpf(a.u[g] * a.b[g], sh));
+        }
+    }
+    __syncthreads();
+    // (2) levels L-1 .. lf inside the band
+    for (int l = L - 1; l >= lf; --l) {
+        const int np = 1 << l, s = 1 << (L - l), nc = 2 * np;
+        const int pr_y = d > 1 ? S / s : 1, pr_z = d > 2 ? S / s : 1;
+        const int items = pr_y * pr_z * np;
+        const long long *child = pyr + a.lvl_off[l + 1];
+        long long *par = pyr + a.lvl_off[l];
+        for (int t = tid; t < items; t += nt) {
+            const int kx = t % np, q = t / np;
+            const int ky = d > 1 ? by * pr_y + q % pr_y : 0;
+            const int kz = d > 2 ? bz * pr_z + q / pr_y : 0;
+            long long v = 0;
+            for (int c = 0; c < (1 << d); ++c) {
+                const int cx = 2 * kx + (c & 1);
+                const int cy = d > 1 ? 2 * ky + ((c >> 1) & 1) : 0;
+                const int cz = d > 2 ? 2 * kz + ((c >> 2) & 1) : 0;
+                v += __ldcg(child + cx + (int64_t)nc * (cy + (int64_t)nc * cz));
+            }
+            par[kx + (int64_t)np * (ky + (int64_t)np * kz)] = v;
+        }
+        __syncthreads();
+    }
+    // (3) the band's part of the coarser panels
+    const int npf = 1 << lf;
+    const long long *pf = pyr + a.lvl_off[lf] + (int64_t)npf * (by + (int64_t)npf * bz);
+    for (int l = lf - 1; l >= 0; --l) {
+        const int np = 1 << l, step = 1 << (lf - l);
+        const int ky = by >> (lf - l), kz = bz >> (lf - l);
+        unsigned long long *par = reinterpret_cast<unsigned long long *>(
+            pyr + a.lvl_off[l] + (int64_t)np * (ky + (int64_t)np * kz));
+        for (int kx = tid; kx < np; kx += nt) {
+            long long v = 0;
+            for (int j = 0; j < step; ++j) v += __ldcg(pf + (int64_t)kx * step + j);
+            atomicAdd(par + kx, (unsigned long long)v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 1 + Step 3 panel by panel (Sec. 3 as written, K = 0, integer route), 1-D and 2-D.
+// Every distance the decomposition compares with the threshold is a half-unit gap 2t - 1
+// between the node and a cell boundary (t >= 1 cells), or 0, so each node first tabulates its
+// chords ch(t) = floor(sqrt(T4 - (2t - 1)^2)) (ch(0) = floor(sqrt(T4))) in shared memory --
+// about R integer square roots -- and every level, panel row and parent row then reads its
+// chord from the table.  Levels whose panels cannot fit in the ball are skipped, the parent
+// row's fully-inside run is shared by its two child rows, and the panels of each run are added
+// one by one from the pyramid.  The integer total equals that of k_fast_gather_i64.
+// ---------------------------------------------------------------------------
+constexpr int GP_THREADS = 128;
+constexpr int GP_CHORDS = 24;
+
+// gap index t of cell boundary c (cells) seen from node row iy: |2c - (2 iy + 1)| = 2t - 1
+__device__ __forceinline__ int gap_t(int c, int iy) { return c > iy ? c - iy : iy - c + 1; }
+
+template <int D>
+__global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels(FastI64Args a,
+                                                                   const float *__restrict__ u,
+                                                                   float *__restrict__ Lu)
+{
+    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
+    const int64_t i = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n, L = a.L;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)(i / n) : 0;
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    const int r0 = isqrt_fast(T4);
+    const int tmax = (r0 + 1) >> 1;          // (2t - 1)^2 <= T4 exactly for t <= tmax
+    int *ch = s_ch + threadIdx.x;
+    if (D > 1) {
+        const int tc = min(tmax, GP_CHORDS - 1);
+        ch[0] = r0;
+        for (int t = 1; t <= tc; ++t) ch[t * GP_THREADS] = isqrt_fast(T4 - sq(2 * t - 1));
+    }
+    auto chord = [&](int t) -> int {
+        if (D == 1) return r0;
+        return t < GP_CHORDS ? ch[t * GP_THREADS] : isqrt_fast(T4 - sq(2 * t - 1));
+    };
+    int lmin = 0;
+    while (lmin < L && (1 << (L - lmin + 1)) > 2 * r0) ++lmin;
+    long long G = 0;
+    for (int l = lmin; l <= L; ++l) {
+        const int np = 1 << l;
+        const int lg = L - l;                // panel side 2^lg cells, 2^(lg+1) half-units
+        const int shf = lg + 1;
+        const bool leaf = (l == L);
+        const long long *__restrict__ lev = a.pyr + a.lvl_off[l];
+        int ylo = 0, yhi = 0;
+        if (D > 1) {
+            if (leaf) {
+                ylo = max(0, iy - tmax);
+                yhi = min(n - 1, iy + tmax);
+            } else {                         // rows whose far edges have t <= tmax
+                ylo = max(0, -((tmax - 1 - iy) >> lg));
+                yhi = min(np - 1, ((iy + tmax) >> lg) - 1);
+            }
+        }
+        int pm = -1, ppa = 1, ppb = 0;
+        for (int ky = ylo; ky <= yhi; ++ky) {
+            int r;
+            if (D == 1) r = r0;
+            else if (leaf) r = chord(ky > iy ? ky - iy : iy - ky);
+            else r = chord(max(gap_t(ky << lg, iy), gap_t((ky + 1) << lg, iy)));
+            int ka, kb;
+            if (leaf) {
+                ka = max(0, -((r - X) >> 1) - 1);
+                kb = min(n - 1, (X + r) >> 1);
+            } else {
+                ka = max(0, -((r - X) >> shf));
+                kb = min(np - 1, ((X + r) >> shf) - 1);
+            }
+            if (ka > kb) continue;
+            if (l > lmin && (ky >> 1) != pm) {       // the parent row's fully-inside run
+                pm = ky >> 1;
+                ppa = 1; ppb = 0;
+                int tp = 0;
+                if (D > 1) tp = max(gap_t(pm << (lg + 1), iy), gap_t((pm + 1) << (lg + 1), iy));
+                if (tp <= tmax) {
+                    const int rp = chord(tp);
+                    const int qa = max(0, -((rp - X) >> (shf + 1)));
+                    const int qb = min((np >> 1) - 1, ((X + rp) >> (shf + 1)) - 1);
+                    if (qa <= qb) { ppa = 2 * qa; ppb = 2 * qb + 1; }
+                }
+            }
+            const long long *__restrict__ row = lev + (int64_t)np * ky;
+            const int b1 = ppa <= ppb ? min(kb, ppa - 1) : kb;
+            for (int k = ka; k <= b1; ++k) G += __ldg(row + k);
+            if (ppa <= ppb)
+                for (int k = max(ka, ppb + 1); k <= kb; ++k) G += __ldg(row + k);
+        }
+    }
+    const int sh = fixed_shift_f32(a.N, a.mx);
+    Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
                                                                const T *__restrict__ u,
@@ -1142,6 +1325,34 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
     return cudaGetLastError();
 }
 
+// Step 2 of the panel-by-panel form: per-block bounds (and the coarse levels zeroed), then one
+// fused build of every level (k_step2_panels).  Bands of 4 leaf rows in 2-D, 8 x 8 in 3-D; in
+// 1-D the single row is the band.
+static cudaError_t step2_panels(nl_plan *p, const float *u, cudaStream_t st)
+{
+    const int d = p->d, L = p->L;
+    long long *pyr = (long long *)p->pyr;
+    unsigned char *aux = (unsigned char *)p->fast_mx;
+    float *part = (float *)(aux + 16);
+    int64_t per = (p->N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
+    if (per < 2048) per = 2048;
+    const int nparts = (int)((p->N + per - 1) / per);
+    int c = 0;
+    if (d == 2) c = std::min(2, L);
+    if (d == 3) c = std::min(3, L);
+    Step2Args a;
+    a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
+    a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
+    a.mx = (unsigned int *)aux; a.pyr = pyr; a.leaf_only = 0; a.wpr = 1;
+    a.leaf = pyr + p->lvl_off[L];
+    for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
+    k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr, p->lvl_off[a.lf]);
+    int64_t bands = 1;
+    for (int q = 1; q < d; ++q) bands *= p->n >> c;
+    k_step2_panels<<<(unsigned)bands, 512, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_t st)
 {
     prof_mark(p, 0, st);
@@ -1149,19 +1360,9 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     long long *pyr = (long long *)p->pyr;           // same buffer, 8-byte entries (M = 1)
     unsigned int *mx = (unsigned int *)p->fast_mx;
     const unsigned gb = (unsigned)((p->N + 255) / 256);
-    if (p->fast_variant == NL_FAST_PANELS) {
-        NL_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned int), st));
-        const unsigned gm = (unsigned)((p->N + 255) / 256 < 1216 ? (p->N + 255) / 256 : 1216);
-        k_absmax_f32<<<gm, 256, 0, st>>>(p->N, u, p->b32, mx);
-        k_pyr_leaf_f32i64<<<gb, 256, 0, st>>>(p->N, u, p->b32, mx, pyr + p->lvl_off[L]);
-    }
-    for (int l = L - 1; l >= 0 && p->fast_variant == NL_FAST_PANELS; --l) {
-        int64_t P = 1;
-        for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
-        const long long *child = pyr + p->lvl_off[l + 1];
-        k_pyr_level_i64<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(d, l, child, pyr + p->lvl_off[l]);
-    }
-    const bool prefix = p->fast_variant != NL_FAST_PANELS;
+    const bool panels = p->fast_variant == NL_FAST_PANELS;
+    if (panels) NL_CUDA_TRY(step2_panels(p, u, st));
+    const bool prefix = !panels;
     const bool leafrows = p->fast_variant == NL_FAST_LEAFROWS;
     if (prefix) {
         NL_CUDA_TRY(step2_rowprefix(p, u, leafrows, st));
@@ -1184,8 +1385,9 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         else if (d == 2) k_fast_gather_rowprefix<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else k_fast_gather_rowprefix<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     } else {
-        if (d == 1) k_fast_gather_i64<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
-        else if (d == 2) k_fast_gather_i64<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        const unsigned gp = (unsigned)((p->N + GP_THREADS - 1) / GP_THREADS);
+        if (d == 1) k_fast_gather_panels<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
+        else if (d == 2) k_fast_gather_panels<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     }
     prof_mark(p, 2, st);
