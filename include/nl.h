@@ -108,7 +108,10 @@ typedef struct {
     const double *delta_field;  /* HOST pointer, n^d values, or NULL; copied at plan time */
     int symmetric;              /* 1: divergence-type symmetrised kernel (Sec. 2 case (b)):
                                    w^s_ij = (w_ij + w_ji)/2, each half with its own
-                                   node's horizon; NL_POWER with NL_COEF_NONE/XY only */
+                                   node's horizon.  NL_POWER with NL_COEF_NONE/XY (direct
+                                   sum), or NL_POLY with K = 0, NL_COEF_NONE/XY and
+                                   NL_SELF_DISCRETE on n = 2^L (fast path: nl_apply_fast and
+                                   nl_cg_solve only) */
 } nl_horizon;
 
 typedef struct {
@@ -170,6 +173,14 @@ nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, 
  *     (L u)_i = h^2 sum_{k in LS(i)} sigma c_ik (xi xi^T / delta_i^3) (u_k - u_i),
  * c_ik = (c_i + c_k)/2, u_k = 0 and c_k = c_i outside Omega; a different operator from
  * nl_apply's, computed from exact 64-bit leaf-row moment sums.
+ * On a symmetric NL_POLY plan (K = 0) it applies the symmetrised leaf-set operator
+ *     (L u)_i = sigma h^d sum_k (w_i(k) + w_k(i))/2 C_ik (u_k - u_i),
+ *     w_i(k) = [cell k meets the open ball of node i] delta_i^{-(d+2)},
+ * k over every lattice cell (u_k = 0, a_k = a_i, delta_k = delta_i outside Omega): the
+ * one-sided fast apply for the first half, and for the second its transpose -- each node
+ * scatters c_k u_k (c_k = a_k delta_k^{-(d+2)}) into per-leaf-row difference arrays (exact
+ * 64-bit integer atomics for FP32 data, FP64 atomics for FP64 data), one prefix sum per row.
+ * Symmetric and negative semi-definite, so nl_cg_solve accepts such a plan (Jacobi).
  * Same layouts and ownership as nl_apply.
  */
 nl_status nl_apply_fast(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, void *stream);
@@ -186,11 +197,11 @@ typedef enum { NL_PRECOND_NONE = 0, NL_PRECOND_JACOBI = 1, NL_PRECOND_LEARNED = 
 
 /*
  * Preconditioned conjugate gradients for -L x = f with the plan's operator
- * (which must be symmetric: a symmetric NL_POWER plan or NL_PD_BOND with a
- * constant horizon).  f, x: DEVICE pointers, FP64, layout as nl_apply;
- * x0 = 0.  Operator applies in FP32, inner products and vector updates in
- * FP64, with the residual recomputed in FP64 (FP64 operator) every
- * `replace_every` iterations so that the reported residual is the true FP64
+ * (which must be symmetric: a symmetric NL_POWER plan (direct sum), a symmetric NL_POLY plan
+ * (the symmetrised fast operator of nl_apply_fast) or NL_PD_BOND with a constant horizon).
+ * f, x: DEVICE pointers, FP64, layout as nl_apply; x0 = 0.  Operator applies in FP32,
+ * inner products and vector updates in FP64, with the residual recomputed in FP64 (FP64
+ * operator) when the recursive one converges, so that the reported residual is the true FP64
  * one.  Blocks until done; the stats are read back on the host.
  * Errors: NL_EINVAL, NL_EUNSUPPORTED (non-symmetric plan), NL_ENOTCONV, NL_ECUDA.
  */

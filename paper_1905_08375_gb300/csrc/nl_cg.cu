@@ -599,12 +599,15 @@ struct PlanOpCtx { nl_plan *p; int nrhs; };
 static nl_status plan_apply(void *ctx, const void *in, void *out, int dtype, cudaStream_t st)
 {
     PlanOpCtx *c = (PlanOpCtx *)ctx;
+    if (c->p->sym_fast) return nl_fast_sym_launch(c->p, in, out, c->nrhs, dtype, st);
     return nl_direct_launch(c->p, in, out, c->nrhs, dtype, st);
 }
 
 static nl_status plan_diag(void *ctx, const double *zin, double *d, cudaStream_t st)
 {
-    return nl_diag_launch(((PlanOpCtx *)ctx)->p, zin, d, st);
+    nl_plan *p = ((PlanOpCtx *)ctx)->p;
+    if (p->sym_fast) return nl_fast_sym_diag(p, d, st);
+    return nl_diag_launch(p, zin, d, st);
 }
 
 static nl_status plan_cg(nl_plan *p, const void *f, void *x, int nrhs, double rtol, int maxit,
@@ -616,12 +619,12 @@ static nl_status plan_cg(nl_plan *p, const void *f, void *x, int nrhs, double rt
         return NL_EINVAL;
     }
     const bool pd = p->family == NL_PD_BOND;
-    if (!(p->symmetric || (pd && p->const_horizon))) {
-        nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER plan, or "
-                     "NL_PD_BOND with a constant horizon)");
+    if (!(p->symmetric || p->sym_fast || (pd && p->const_horizon))) {
+        nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER or "
+                     "NL_POLY plan, or NL_PD_BOND with a constant horizon)");
         return NL_EUNSUPPORTED;
     }
-    if (precond == NL_PRECOND_LEARNED && (pd || p->d != 2)) {
+    if (precond == NL_PRECOND_LEARNED && (pd || p->d != 2 || p->sym_fast)) {
         nl_set_error("nl_cg_solve: NL_PRECOND_LEARNED needs a symmetric 2-D scalar plan");
         return NL_EUNSUPPORTED;
     }

@@ -2133,6 +2133,10 @@ extern "C" nl_status nl_apply(nl_plan *p, const void *u, void *Lu, int nrhs, int
         nl_set_error("nl_apply: need non-null u/Lu, 1 <= nrhs <= 65535, dtype F32/F64");
         return NL_EINVAL;
     }
+    if (p->sym_fast) {
+        nl_set_error("nl_apply: the symmetrised NL_POLY operator is applied by nl_apply_fast");
+        return NL_EUNSUPPORTED;
+    }
     return nl_direct_launch(p, u, Lu, nrhs, dtype, nl_stream(stream));
 }
 

@@ -1549,13 +1549,14 @@ extern "C" nl_status nl_apply_fast(nl_plan *p, const void *u, void *Lu, int nrhs
         return nl_fast_pd_launch(p, (const float *)u, (float *)Lu, nrhs, nl_stream(stream));
     }
     if (p->family != NL_POLY || p->symmetric || p->L < 0 || !p->pyr) {
-        nl_set_error("nl_apply_fast: needs a non-symmetric NL_POLY plan on n = 2^L "
-                     "(d = 3 only with K = 0)");
+        nl_set_error("nl_apply_fast: needs an NL_POLY plan (one-sided, or symmetric with "
+                     "K = 0) on n = 2^L (d = 3 only with K = 0)");
         return NL_EUNSUPPORTED;
     }
     if (p->self_mode == NL_SELF_PAPER && p->coef == NL_COEF_XY) {
         nl_set_error("nl_apply_fast: NL_SELF_PAPER is not defined for NL_COEF_XY");
         return NL_EUNSUPPORTED;
     }
+    if (p->sym_fast) return nl_fast_sym_launch(p, u, Lu, nrhs, dtype, nl_stream(stream));
     return nl_fast_launch(p, u, Lu, nrhs, dtype, nl_stream(stream));
 }

@@ -132,6 +132,15 @@ struct nl_plan {
     long long *leaf_multi;          // leaf-row prefixes of several right-hand sides (grown on
     unsigned char *aux_multi;       // the first apply that needs them) and their scale words
     int leaf_multi_cap;
+    // symmetrised fast path (K = 0): symmetric NL_POLY plans keep symmetric = 0 for the
+    // one-sided machinery and set sym_fast
+    int sym_fast;
+    double *sym_c64; float *sym_c32;   // c_k = a_k delta_k^{-(d+2)}
+    double *sym_T;                     // sum of c_k over the k whose leaf set reaches i
+    double *sym_G64; float *sym_G32;   // sigma h^d a_i
+    double *sym_diag;                  // Jacobi diagonal of -L
+    double *sym_D;                     // difference arrays / row prefix sums (N x 8 bytes)
+    unsigned char *sym_aux;            // scale word and per-block bounds of |c u|
     int prof_on, prof_count;        // per-phase timing of the fast apply
     cudaEvent_t prof_ev[64][3];
     nl_cg_state cg;                 // CG workspace (allocated on the first solve)
@@ -178,6 +187,11 @@ nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cud
 nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
                             cudaStream_t st);
 nl_status nl_diag_launch(nl_plan *p, const double *zin, double *diag, cudaStream_t st);
+nl_status nl_fast_sym_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
+                                cudaStream_t st);
+nl_status nl_fast_sym_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
+                             cudaStream_t st);
+nl_status nl_fast_sym_diag(nl_plan *p, double *diag, cudaStream_t st);
 nl_status nl_cg_release(nl_plan *p);
 nl_status nl_batch_launch(int kind, int shape, int dtype, const void *inst_dev, int ninst,
                           int64_t total, int *counter, const void *u, void *Lu, int Rmax,

@@ -385,8 +385,16 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         nl_set_error("nl_plan_create: NL_COEF_MEAN is for NL_PD_BOND");
         return NL_EINVAL;
     }
-    if (hz->symmetric && (k->family != NL_POWER || k->coef == NL_COEF_X)) {
-        nl_set_error("nl_plan_create: the symmetric variant needs NL_POWER with NL_COEF_NONE/XY");
+    if (hz->symmetric && k->family == NL_POLY) {
+        // the symmetrised polynomial operator: the fast path with p = 1 (nl_apply_fast, CG)
+        if (k->K != 0 || k->coef == NL_COEF_X || k->self_term != NL_SELF_DISCRETE) {
+            nl_set_error("nl_plan_create: the symmetric NL_POLY variant needs K = 0, "
+                         "NL_COEF_NONE/XY and NL_SELF_DISCRETE");
+            return NL_EUNSUPPORTED;
+        }
+    } else if (hz->symmetric && (k->family != NL_POWER || k->coef == NL_COEF_X)) {
+        nl_set_error("nl_plan_create: the symmetric variant needs NL_POWER with NL_COEF_NONE/XY "
+                     "(or NL_POLY with K = 0)");
         return NL_EUNSUPPORTED;
     }
     int64_t N = 1;
@@ -447,6 +455,10 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     p->L = -1;
     for (int l = 0; l <= NL_MAX_LEVELS; ++l) if ((1 << l) == n) p->L = l;
     p->family = k->family; p->coef = k->coef; p->symmetric = hz->symmetric ? 1 : 0;
+    if (p->symmetric && k->family == NL_POLY) {        // one-sided machinery + transpose half
+        p->symmetric = 0;
+        p->sym_fast = 1;
+    }
     p->self_mode = k->self_term;
     p->K = (k->family == NL_POLY || k->family == NL_KAPPA) ? k->K : 0;
     if (k->fast_variant < NL_FAST_AUTO || k->fast_variant > NL_FAST_LEAFROWS) {
@@ -700,7 +712,18 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         k_pd_exterior<<<GB, TB, 0, st>>>(pa, d_a, p->thr, p->off, p->pdext);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan kernels"));
+    if (p->sym_fast && !want_fast) {
+        nl_set_error("nl_plan_create: the symmetric NL_POLY variant needs n = 2^L");
+        return fail_tmp(NL_EUNSUPPORTED);
+    }
     if (want_fast) NL_TMP_TRY(nl_fast_plan_init(p, d_delta, d_a, st));
+    if (p->sym_fast) {
+        if (!p->pyr) {
+            nl_set_error("nl_plan_create: no fast path for this grid (symmetric NL_POLY)");
+            return fail_tmp(NL_EUNSUPPORTED);
+        }
+        NL_TMP_TRY(nl_fast_sym_plan_init(p, d_delta, d_a, st));
+    }
     if (want_fast_pd) NL_TMP_TRY(nl_fast_pd_plan_init(p, d_delta, d_a, st));
     NL_TMP_TRY(nl_direct_plan_init(p, st));
     ce = cudaStreamSynchronize(st);
@@ -726,7 +749,8 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->malpha, p->dinv64, p->rb_g32, p->rb_g64, p->thr_reach, p->fast_mx,
                      p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32, p->leaf_multi,
                      p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux, p->selfQ,
-                     p->fastFh32 };
+                     p->fastFh32, p->sym_c64, p->sym_c32, p->sym_T, p->sym_G64, p->sym_G32,
+                     p->sym_diag, p->sym_D, p->sym_aux };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)
