@@ -404,7 +404,7 @@ def nl_net_history_pairs(plan: Plan, f, x, history, count, xo, eo, stream=None):
     L = _net_fns()
     fn = L.nl_net_history_pairs
     fn.restype = ctypes.c_int
-    fn.argtypes = [ctypes.c_void_p] * 5 + [ctypes.c_int] + [ctypes.c_void_p] * 3
+    fn.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_void_p] * 3
     N = plan.N
     if f.numel() != N or x.numel() != N or history.numel() < count * N:
         raise ValueError("f, x need n^2 values and history count * n^2")

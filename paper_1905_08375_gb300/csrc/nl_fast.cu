@@ -77,14 +77,62 @@ __device__ __host__ __forceinline__ int midx2(int a0, int a1)
     return a1 * (2 * K + 1) - (a1 * (a1 - 1)) / 2 + a0;
 }
 
+// moment index of (a0, a1, a2) in the compact order (a2 outer, a1, a0 inner, sum <= 2K)
+template <int K>
+__device__ __host__ __forceinline__ constexpr int midx3(int a0, int a1, int a2)
+{
+    int idx = 0;
+    for (int c = 0; c < a2; ++c) idx += (2 * K - c + 1) * (2 * K - c + 2) / 2;
+    for (int b = 0; b < a1; ++b) idx += 2 * K - a2 - b + 1;
+    return idx + a0;
+}
+
 // sum over x_k in panel of p(|x_k - x_i|^2 / delta_i^2) v_k from the panel moments:
 // |x_k - x_i|^2 / delta^2 = |B + H t|^2 / (4 R2), B = centre - X, H = half-width
 template <int D, int K>
 __device__ __forceinline__ double panel_poly(const double *mu, const double *pc, int Bx, int By,
-                                             int H, double ir4)
+                                             int Bz, int H, double ir4)
 {
     if constexpr (K == 0) {
         return pc[0] * mu[0];
+    } else if constexpr (D == 3) {
+        // q(t) = p(|B + H t|^2 ir4) as a polynomial in (t0, t1, t2) of degree 2K, by Horner's
+        // rule in s = c000 + sum_a c_a t_a + H2 sum_a t_a^2, kept in the compact moment order
+        // (runtime loops: up to 84 coefficients, so the arrays live in local memory)
+        constexpr int M = (2 * K + 1) * (2 * K + 2) * (2 * K + 3) / 6;
+        const double H2 = (double)H * H * ir4;
+        const double c000 = ((double)Bx * Bx + (double)By * By + (double)Bz * Bz) * ir4;
+        const double c1[3] = { 2.0 * Bx * H * ir4, 2.0 * By * H * ir4, 2.0 * Bz * H * ir4 };
+        double q[M], nq[M];
+#pragma unroll 1
+        for (int e = 0; e < M; ++e) q[e] = 0.0;
+        q[0] = pc[K];
+#pragma unroll 1
+        for (int m = K - 1; m >= 0; --m) {
+            int e = 0;
+#pragma unroll 1
+            for (int c = 0; c <= 2 * K; ++c)
+#pragma unroll 1
+                for (int b = 0; b <= 2 * K - c; ++b)
+#pragma unroll 1
+                    for (int a0 = 0; a0 <= 2 * K - b - c; ++a0, ++e) {
+                        double v = c000 * q[e];
+                        if (a0 >= 1) v += c1[0] * q[e - 1];
+                        if (b >= 1) v += c1[1] * q[midx3<K>(a0, b - 1, c)];
+                        if (c >= 1) v += c1[2] * q[midx3<K>(a0, b, c - 1)];
+                        if (a0 >= 2) v += H2 * q[e - 2];
+                        if (b >= 2) v += H2 * q[midx3<K>(a0, b - 2, c)];
+                        if (c >= 2) v += H2 * q[midx3<K>(a0, b, c - 2)];
+                        nq[e] = v;
+                    }
+            nq[0] += pc[m];
+#pragma unroll 1
+            for (int f = 0; f < M; ++f) q[f] = nq[f];
+        }
+        double v = 0.0;
+#pragma unroll 1
+        for (int e = 0; e < M; ++e) v += q[e] * mu[e];
+        return v;
     } else if constexpr (D == 1) {
         constexpr int E = 2 * K + 1;
         const double c0 = (double)Bx * Bx * ir4, c1 = 2.0 * Bx * H * ir4, c2 = (double)H * H * ir4;
@@ -203,9 +251,10 @@ __device__ __forceinline__ double sum_run(const FastArgs &a, int l, int np, int 
         } else {
             const int H = S / 2;
             const int By = (D > 1) ? ky * S + H - Y : 0;
+            const int Bz = (D > 2) ? kz * S + H - Z : 0;
             for (int k = ka; k <= kb; ++k) {
                 const int Bx = k * S + H - X;
-                s += panel_poly<D, K>(lev + (int64_t)k * a.M, a.poly, Bx, By, H, ir4);
+                s += panel_poly<D, K>(lev + (int64_t)k * a.M, a.poly, Bx, By, Bz, H, ir4);
             }
         }
     }
@@ -1183,9 +1232,9 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
                             cudaStream_t st)
 {
     const int d = p->d, K = p->K, L = p->L;
-    // fast path unavailable (apply reports NL_EUNSUPPORTED): 3-D with K > 0, n not a
-    // power of two, or n > 8192 (integer half-unit geometry is kept within 32 bits)
-    if ((d == 3 && K > 0) || L < 0 || p->n > 8192) return NL_OK;
+    // fast path unavailable (apply reports NL_EUNSUPPORTED): n not a power of two, or
+    // n > 8192 (integer half-unit geometry is kept within 32 bits)
+    if (L < 0 || p->n > 8192) return NL_OK;
     p->M = moments_count(d, K);
     const int M = p->M;
     // multi-indices in the compact order (a2 outer, a1, a0 inner)
@@ -1428,7 +1477,8 @@ static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
         switch (p->K) { case 0: NL_GATHER(2, 0); break; case 1: NL_GATHER(2, 1); break;
                         case 2: NL_GATHER(2, 2); break; default: NL_GATHER(2, 3); }
     } else {
-        NL_GATHER(3, 0);
+        switch (p->K) { case 0: NL_GATHER(3, 0); break; case 1: NL_GATHER(3, 1); break;
+                        case 2: NL_GATHER(3, 2); break; default: NL_GATHER(3, 3); }
     }
 #undef NL_GATHER
     prof_mark(p, 2, st);
@@ -1550,7 +1600,7 @@ extern "C" nl_status nl_apply_fast(nl_plan *p, const void *u, void *Lu, int nrhs
     }
     if (p->family != NL_POLY || p->symmetric || p->L < 0 || !p->pyr) {
         nl_set_error("nl_apply_fast: needs an NL_POLY plan (one-sided, or symmetric with "
-                     "K = 0) on n = 2^L (d = 3 only with K = 0)");
+                     "K = 0) on n = 2^L <= 8192");
         return NL_EUNSUPPORTED;
     }
     if (p->self_mode == NL_SELF_PAPER && p->coef == NL_COEF_XY) {

@@ -124,10 +124,6 @@ def test_unsupported_requests():
     u2 = torch.zeros(256, dtype=torch.float64, device=DEV)
     with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
         nl.nl_apply_fast(p2, u2, torch.empty_like(u2))
-    p3 = nl.nl_plan_create(3, 8, 0.2, family=nl.NL_POLY, K=1)
-    u3 = torch.zeros(512, dtype=torch.float64, device=DEV)
-    with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
-        nl.nl_apply_fast(p3, u3, torch.empty_like(u3))
 
 
 @pytest.mark.parametrize("d,n", [(1, 2048), (2, 128), (2, 256), (3, 32)])
@@ -196,3 +192,36 @@ def test_multi_rhs_leafrows_bitwise_equal_to_single(d, n, nrhs):
     L = int(np.log2(n))
     ref = oracle.fast_leafset(u[-1], d, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a)
     assert rel_l2(many[-1], ref) <= 2e-6
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("K", [1, 2, 3])
+@pytest.mark.parametrize("coef", [nl.NL_COEF_NONE, nl.NL_COEF_XY])
+def test_3d_polynomial_orders(dtype, K, coef):
+    """3-D with K > 0: moments of degree <= 2K in three variables (C(2K+3, 3) per panel)."""
+    n, L = 16, 4
+    rng = np.random.default_rng(30 + K)
+    s = synth.fourier_modes_field(rng, 3, n, modes=4, kmax=2).reshape(-1)
+    delta = (1.3 + 2.4 * s) / n
+    a = np.exp(0.3 * rng.standard_normal(n ** 3)) if coef == nl.NL_COEF_XY else None
+    u = rng.standard_normal((2, n ** 3))
+    plan = nl.nl_plan_create(3, n, delta, family=nl.NL_POLY, alpha=1.0, K=K, coef=coef, a=a)
+    ref = oracle.fast_leafset(u, 3, L, delta, K=K, alpha=1.0, coef=coef, a=a)
+    assert rel_l2(run_fast(plan, u, dtype), ref) <= TOL[dtype]
+    if dtype == torch.float64 and coef == nl.NL_COEF_NONE:
+        idx = sample_idx(n ** 3, 300, seed=K)
+        tree = oracle.fast_tree(u[0], 3, L, delta, K=K, alpha=1.0, idx=idx)
+        assert rel_l2(run_fast(plan, u[0], dtype)[idx], tree) <= 1e-12
+    plan.close()
+
+
+def test_3d_polynomial_large_ball_and_boundary():
+    """A ball larger than Omega (a root-level panel) and a constant horizon, K = 2."""
+    n, L = 8, 3
+    rng = np.random.default_rng(41)
+    u = rng.standard_normal(n ** 3)
+    for delta in (0.3, 1.9):
+        plan = nl.nl_plan_create(3, n, delta, family=nl.NL_POLY, alpha=1.0, K=2)
+        ref = oracle.fast_tree(u, 3, L, delta, K=2, alpha=1.0)
+        assert rel_l2(run_fast(plan, u, torch.float64), ref) <= 1e-12
+        plan.close()

@@ -61,10 +61,11 @@ def test_constant_horizon_other_dimensions(d, n, delta):
 
 
 def test_rejects_grids_beyond_the_static_array():
-    # the size check runs on the host before any launch, so a small buffer stands in
-    u = torch.zeros(8, dtype=torch.float64, device=DEV)
+    # the size check runs on the host before any launch (the buffers are never touched)
+    u = torch.zeros(2048 * 2048, dtype=torch.float64, device=DEV)
     with pytest.raises(nl.NlError, match="NL_EINVAL.*static array"):
         nl.nl_apply_fast_noalloc(2, 2048, 0.01, u, u.clone(), nrhs=1)
+    u = torch.zeros(1000 * 1000, dtype=torch.float64, device=DEV)
     with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
         nl.nl_apply_fast_noalloc(2, 1000, 0.01, u, u.clone(), nrhs=1)
 
