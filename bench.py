@@ -780,13 +780,28 @@ class C5(Workload):
     def kernels(self, flush, reps):
         nl = self.nl
         t_d = self.time_fn(lambda: nl.nl_apply(self.direct, self.u, self.out_d), reps, flush)
+        nl.nl_plan_profile(self.fast, True)
         t_f = self.time_fn(lambda: nl.nl_apply_fast(self.fast, self.u, self.out_f), reps, flush)
+        prof = nl.nl_plan_profile_read(self.fast)
+        nl.nl_plan_profile(self.fast, False)
         n = self.n
+        N = n ** 3
+        k = max(prof["applies"], 1)
+        s2 = prof["step2_ms"] / k
+        # Step 2 of the 8 right-hand sides: per right-hand side u (4) and b (4) read and the
+        # 64-bit leaf-row prefix (8) written, 16 B per node
+        s2_bytes = 8 * 16.0 * N
+        s2_ach = s2_bytes / (s2 * 1e-3) / 1e9
         nb = 8.0 * float(ball_counts(np.full(1, 4.0 / n), n, 3)[0]) * n ** 3
         roof = _alu_roof("k_direct3d_x2<4,4> (slab sweep)", 4.0 * nb, t_d,
                          *fp32_peak())
         roof["algorithmic_per_launch"] = f"{4 * nb:.4g} flop (4 per term, 8 RHS)"
-        return roof, {"direct_fp32_8rhs_ms": round(t_d, 4), "fast_fp32_8rhs_ms": round(t_f, 4)}
+        return roof, {"direct_fp32_8rhs_ms": round(t_d, 4), "fast_fp32_8rhs_ms": round(t_f, 4),
+                      "fast_step2_8rhs_ms": round(s2, 4),
+                      "fast_step3_8rhs_ms": round(prof["step3_ms"] / k, 4),
+                      "fast_step2_hbm_gbs": round(s2_ach, 1),
+                      "fast_step2_hbm_frac": round(s2_ach / self.peaks["hbm_gbs"], 4),
+                      "fast_step2_bytes": f"{s2_bytes:.4g} (16 B per node and right-hand side)"}
 
     def e2e(self, flush, steps):
         torch = self.torch

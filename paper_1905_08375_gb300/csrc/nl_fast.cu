@@ -640,7 +640,28 @@ __global__ void __launch_bounds__(256) k_absmax_parts(int64_t N, const float *__
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int64_t i = t0; i < nzero; i += stride) zero[i] = 0;
-    for (int64_t i = t0; i < N; i += stride) m = fmaxf(m, fabsf(u[i] * b[i]));
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) {
+        // 16-byte loads, four of each field in flight per thread
+        const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(u);
+        const float4 *__restrict__ b4 = reinterpret_cast<const float4 *>(b);
+        const int64_t N4 = N >> 2;
+        for (int64_t i = t0; i < N4; i += 4 * stride) {
+            float4 x[4], y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t j = i + q * stride;
+                x[q] = j < N4 ? u4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                y[q] = j < N4 ? b4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                m = fmaxf(fmaxf(m, fmaxf(fabsf(x[q].x * y[q].x), fabsf(x[q].y * y[q].y))),
+                          fmaxf(fabsf(x[q].z * y[q].z), fabsf(x[q].w * y[q].w)));
+        }
+        done = N4 << 2;
+    }
+    for (int64_t i = done + t0; i < N; i += stride) m = fmaxf(m, fabsf(u[i] * b[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -654,6 +675,10 @@ struct Step2Args {
     int d, n, L, c, lf;              // band: 2^c leaf rows per axis = one panel row of level lf
     int leaf_only;                   // 1: the leaf rows only (leaf-row gather)
     int wpr;                         // warps per leaf row (leaf rows only; n / 256 when > 1)
+    int vec;                         // panel sums: u, b and the leaf level 16-byte aligned,
+                                     // n a multiple of 4 (16-byte loads and stores)
+    int lane_e;                      // leaf rows only, n = 32 lane_e (4 or 8) with 16-byte
+                                     // aligned u and b: lane l holds nodes lane_e l .. + lane_e-1
     int64_t N;
     const float *u, *b;
     const float *part;
@@ -722,7 +747,44 @@ __global__ void __launch_bounds__(1024) k_step2_rowprefix(Step2Args a)
     // registers); each warp's total goes to shared memory and the later segments add the
     // earlier ones' totals before storing.  Otherwise one warp per row, the 32 loads of a
     // 1024-node page issued first, the page scanned 32 nodes at a time.
-    if (a.wpr > 1) {
+    if (a.lane_e) {
+        // n = 32 E: each lane loads its E consecutive nodes with 16-byte loads, scans them in
+        // registers, one warp scan of the lane totals gives the offsets, and the row is stored
+        // through shared memory so that the 8-byte stores are coalesced
+        __shared__ long long s_row[4 * 256];      // at most four warps of n <= 256
+        const int E = a.lane_e;
+        long long *srow = s_row + warp * n;
+        for (int r = warp; r < rows_y * rows_z; r += nw) {
+            const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
+            const int64_t row = (int64_t)n * (iy + (int64_t)n * iz);
+            const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(a.u + row) + lane * (E / 4);
+            const float4 *__restrict__ b4 = reinterpret_cast<const float4 *>(a.b + row) + lane * (E / 4);
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (4 * k < E) {
+                    const float4 x = u4[k], y = b4[k];
+                    v[4 * k] = x.x * y.x; v[4 * k + 1] = x.y * y.y;
+                    v[4 * k + 2] = x.z * y.z; v[4 * k + 3] = x.w * y.w;
+                }
+            }
+            long long q[8], t = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k < E) {
+                    t += __float2ll_rn(ldexpf(v[k], sh));
+                    q[k] = t;
+                }
+            }
+            long long off = warp_incl_scan_ll(t, lane) - t;        // exclusive lane offset
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < E) srow[E * lane + k] = q[k] + off;
+            __syncwarp();
+            for (int x = lane; x < n; x += 32) leaf[row + x] = srow[x];
+            __syncwarp();
+        }
+    } else if (a.wpr > 1) {
         __shared__ long long s_tot[32];
         const int W = a.wpr, part = warp % W, r = warp / W;     // one row per W warps
         const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
@@ -840,7 +902,25 @@ __global__ void __launch_bounds__(1024) k_step2_panels(Step2Args a)
     const int rows_y = d > 1 ? S : 1, rows_z = d > 2 ? S : 1;
     long long *pyr = a.pyr;
     // (1) leaf values round(u b 2^sh)
-    {
+    if (a.vec) {
+        long long *leaf = pyr + a.lvl_off[L];
+        const int64_t cnt4 = (int64_t)rows_y * rows_z * (n >> 2);
+        for (int64_t t = tid; t < cnt4; t += nt) {
+            const int64_t e = 4 * t;
+            const int x = (int)(e % n), r = (int)(e / n);
+            const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
+            const int64_t g = x + (int64_t)n * (iy + (int64_t)n * iz);
+            const float4 uv = *reinterpret_cast<const float4 *>(a.u + g);
+            const float4 bv = *reinterpret_cast<const float4 *>(a.b + g);
+            longlong2 q0, q1;
+            q0.x = __float2ll_rn(ldexpf(uv.x * bv.x, sh));
+            q0.y = __float2ll_rn(ldexpf(uv.y * bv.y, sh));
+            q1.x = __float2ll_rn(ldexpf(uv.z * bv.z, sh));
+            q1.y = __float2ll_rn(ldexpf(uv.w * bv.w, sh));
+            reinterpret_cast<longlong2 *>(leaf + g)[0] = q0;
+            reinterpret_cast<longlong2 *>(leaf + g)[1] = q1;
+        }
+    } else {
         long long *leaf = pyr + a.lvl_off[L];
         const int64_t cnt = (int64_t)rows_y * rows_z * n;
         for (int64_t t = tid; t < cnt; t += nt) {
@@ -1270,6 +1350,7 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
         for (int q = 0; q < d; ++q) P *= ((int64_t)1 << l);
         off += P * M;
     }
+    off = (off + 1) & ~(int64_t)1; // leaf level 16-byte aligned
     p->lvl_off[L] = off;           // leaf level: N values of v
     const int64_t total = off + p->N;
 
@@ -1364,6 +1445,14 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
     a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
     a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
     a.mx = mx; a.pyr = pyr; a.leaf_only = leaf_only ? 1 : 0; a.wpr = wpr;
+    a.lane_e = 0; a.vec = 0;
+    {
+        int rows_blk = 1;
+        for (int q = 1; q < d; ++q) rows_blk <<= c;
+        if (leaf_only && wpr == 1 && rows_blk <= 4 && (p->n == 128 || p->n == 256) &&
+            ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(p->b32)) & 15) == 0)
+            a.lane_e = p->n / 32;
+    }
     a.leaf = leaf_out ? leaf_out : pyr + p->lvl_off[L];
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr,
@@ -1392,8 +1481,11 @@ static cudaError_t step2_panels(nl_plan *p, const float *u, cudaStream_t st)
     Step2Args a;
     a.d = d; a.n = p->n; a.L = L; a.c = c; a.lf = L - c; a.N = p->N;
     a.u = u; a.b = p->b32; a.part = part; a.nparts = nparts;
-    a.mx = (unsigned int *)aux; a.pyr = pyr; a.leaf_only = 0; a.wpr = 1;
+    a.mx = (unsigned int *)aux; a.pyr = pyr; a.leaf_only = 0; a.wpr = 1; a.lane_e = 0;
     a.leaf = pyr + p->lvl_off[L];
+    a.vec = (p->n % 4 == 0 &&
+             ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(p->b32) |
+               reinterpret_cast<uintptr_t>(a.leaf)) & 15) == 0) ? 1 : 0;
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
     k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr, p->lvl_off[a.lf]);
     int64_t bands = 1;
