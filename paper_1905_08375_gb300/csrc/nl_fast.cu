@@ -22,6 +22,7 @@
 // integer below 4 R2_i.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "nl_internal.cuh"
@@ -629,8 +630,10 @@ __global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T 
 // same integer that the level-by-level kernels produce (integer sums are exact and do not
 // depend on the order).
 // ---------------------------------------------------------------------------
+// One bound of |u b| per block, from max |u| and the plan-time bound bmax = max |b| (only u
+// is read): |fl32(u b)| <= max|u| bmax (1 + 2^-24), below fl32(max|u| bmax) (1 + 2^-20).
 __global__ void __launch_bounds__(256) k_absmax_parts(int64_t N, const float *__restrict__ u,
-                                                      const float *__restrict__ b,
+                                                      float bmax,
                                                       float *__restrict__ part,
                                                       long long *__restrict__ zero,
                                                       int64_t nzero)
@@ -641,34 +644,43 @@ __global__ void __launch_bounds__(256) k_absmax_parts(int64_t N, const float *__
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int64_t i = t0; i < nzero; i += stride) zero[i] = 0;
     int64_t done = 0;
-    if (((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b)) & 15) == 0) {
-        // 16-byte loads, four of each field in flight per thread
+    if ((reinterpret_cast<uintptr_t>(u) & 15) == 0) {
+        // 16-byte loads, eight in flight per thread
         const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(u);
-        const float4 *__restrict__ b4 = reinterpret_cast<const float4 *>(b);
         const int64_t N4 = N >> 2;
-        for (int64_t i = t0; i < N4; i += 4 * stride) {
-            float4 x[4], y[4];
+        for (int64_t i = t0; i < N4; i += 8 * stride) {
+            float4 x[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 8; ++q) {
                 const int64_t j = i + q * stride;
                 x[q] = j < N4 ? u4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                y[q] = j < N4 ? b4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                m = fmaxf(fmaxf(m, fmaxf(fabsf(x[q].x * y[q].x), fabsf(x[q].y * y[q].y))),
-                          fmaxf(fabsf(x[q].z * y[q].z), fabsf(x[q].w * y[q].w)));
+            for (int q = 0; q < 8; ++q)
+                m = fmaxf(fmaxf(m, fmaxf(fabsf(x[q].x), fabsf(x[q].y))),
+                          fmaxf(fabsf(x[q].z), fabsf(x[q].w)));
         }
         done = N4 << 2;
     }
-    for (int64_t i = done + t0; i < N; i += stride) m = fmaxf(m, fabsf(u[i] * b[i]));
+    for (int64_t i = done + t0; i < N; i += stride) m = fmaxf(m, fabsf(u[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < 8; ++w) m = fmaxf(m, s_w[w]);
-        part[blockIdx.x] = m * (1.f + 0x1p-20f);
+        part[blockIdx.x] = (m * bmax) * (1.f + 0x1p-20f);
     }
+}
+
+// max |b| over the nodes (plan time), as the bits of a non-negative float
+__global__ void k_max_abs_bits(int64_t N, const float *__restrict__ b, unsigned int *out)
+{
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(b[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
 struct Step2Args {
@@ -874,6 +886,8 @@ __global__ void __launch_bounds__(1024) k_step2_rowprefix(Step2Args a)
 // levels were zeroed by k_absmax_parts).  Each panel then holds the integer sum of its leaves,
 // the same integer the level-by-level kernels produce.
 // ---------------------------------------------------------------------------
+constexpr int STEP2_BAND_MAX = 2048;         // panels of the band's level-lf row kept in smem
+
 __global__ void __launch_bounds__(1024) k_step2_panels(Step2Args a)
 {
     __shared__ float s_w[32];
@@ -953,9 +967,38 @@ __global__ void __launch_bounds__(1024) k_step2_panels(Step2Args a)
         }
         __syncthreads();
     }
-    // (3) the band's part of the coarser panels
+    // (3) the band's part of the coarser panels: the band's row of level lf is halved level by
+    // level in shared memory (pairs of neighbours summed), each level's sums added to the
+    // panels of that level with integer atomics
+    if (lf == 0) return;
     const int npf = 1 << lf;
     const long long *pf = pyr + a.lvl_off[lf] + (int64_t)npf * (by + (int64_t)npf * bz);
+    __shared__ long long s_band[STEP2_BAND_MAX];
+    if (npf <= STEP2_BAND_MAX) {
+        for (int k = tid; k < npf; k += nt) s_band[k] = __ldcg(pf + k);
+        __syncthreads();
+        for (int l = lf - 1; l >= 0; --l) {
+            const int np = 1 << l;
+            const int ky = by >> (lf - l), kz = bz >> (lf - l);
+            unsigned long long *par = reinterpret_cast<unsigned long long *>(
+                pyr + a.lvl_off[l] + (int64_t)np * (ky + (int64_t)np * kz));
+            long long v[4];
+            int cntv = 0;
+            for (int kx = tid; kx < np; kx += nt) {     // read every pair before any write
+                const long long w = s_band[2 * kx] + s_band[2 * kx + 1];
+                if (cntv < 4) v[cntv] = w;
+                ++cntv;
+            }
+            __syncthreads();
+            cntv = 0;
+            for (int kx = tid; kx < np; kx += nt, ++cntv) {
+                s_band[kx] = v[cntv];
+                atomicAdd(par + kx, (unsigned long long)v[cntv]);
+            }
+            __syncthreads();
+        }
+        return;
+    }
     for (int l = lf - 1; l >= 0; --l) {
         const int np = 1 << l, step = 1 << (lf - l);
         const int ky = by >> (lf - l), kz = bz >> (lf - l);
@@ -986,7 +1029,7 @@ constexpr int GP_CHORDS = 24;
 __device__ __forceinline__ int gap_t(int c, int iy) { return c > iy ? c - iy : iy - c + 1; }
 
 template <int D>
-__global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels(FastI64Args a,
+__global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels_lane(FastI64Args a,
                                                                    const float *__restrict__ u,
                                                                    float *__restrict__ Lu)
 {
@@ -1063,6 +1106,110 @@ __global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels(FastI64Args a
                 for (int k = max(ka, ppb + 1); k <= kb; ++k) G += __ldg(row + k);
         }
     }
+    const int sh = fixed_shift_f32(a.N, a.mx);
+    Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
+}
+
+// Warp-uniform form for n >= 32 (the 32 nodes of a warp share their row): every lane walks
+// the union of the warp's levels and panel rows, and each run's panels are added in a loop
+// over the warp's longest run length with the shorter runs predicated off, so control flow
+// never diverges; lane l reads panel ka_l + j, and the lanes' panels are adjacent or shared.
+template <int D>
+__global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels(FastI64Args a,
+                                                                   const float *__restrict__ u,
+                                                                   float *__restrict__ Lu)
+{
+    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
+    const int64_t i0 = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
+    const bool act = i0 < a.N;
+    const int64_t i = act ? i0 : a.N - 1;
+    const int n = a.n, L = a.L;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)(i / n) : 0;           // the same for the whole warp
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    const int r0 = isqrt_fast(T4);
+    const int tmax = (r0 + 1) >> 1;
+    int *ch = s_ch + threadIdx.x;
+    if (D > 1) {
+        const int tc = min(tmax, GP_CHORDS - 1);
+        ch[0] = r0;
+        for (int t = 1; t <= tc; ++t) ch[t * GP_THREADS] = isqrt_fast(T4 - sq(2 * t - 1));
+    }
+    auto chord = [&](int t) -> int {
+        if (D == 1) return r0;
+        return t < GP_CHORDS ? ch[t * GP_THREADS] : isqrt_fast(T4 - sq(2 * t - 1));
+    };
+    int lmin = 0;
+    while (lmin < L && (1 << (L - lmin + 1)) > 2 * r0) ++lmin;
+    const int lmin_w = __reduce_min_sync(0xffffffffu, lmin);
+    const int tmax_w = __reduce_max_sync(0xffffffffu, tmax);
+    long long G = 0;
+    for (int l = lmin_w; l <= L; ++l) {
+        const int np = 1 << l;
+        const int lg = L - l;
+        const int shf = lg + 1;
+        const bool leaf = (l == L);
+        const long long *__restrict__ lev = a.pyr + a.lvl_off[l];
+        int ylo = 0, yhi = 0;
+        if (D > 1) {
+            if (leaf) {
+                ylo = max(0, iy - tmax_w);
+                yhi = min(n - 1, iy + tmax_w);
+            } else {
+                ylo = max(0, -((tmax_w - 1 - iy) >> lg));
+                yhi = min(np - 1, ((iy + tmax_w) >> lg) - 1);
+            }
+        }
+        int pm = -1, ppa = 1, ppb = 0;
+        for (int ky = ylo; ky <= yhi; ++ky) {
+            int t = 0;
+            if (D > 1)
+                t = leaf ? (ky > iy ? ky - iy : iy - ky)
+                         : max(gap_t(ky << lg, iy), gap_t((ky + 1) << lg, iy));
+            int ka = 1, kb = 0;
+            if (l >= lmin && t <= tmax) {
+                const int r = chord(t);
+                if (leaf) {
+                    ka = max(0, -((r - X) >> 1) - 1);
+                    kb = min(n - 1, (X + r) >> 1);
+                } else {
+                    ka = max(0, -((r - X) >> shf));
+                    kb = min(np - 1, ((X + r) >> shf) - 1);
+                }
+            }
+            if (l > lmin_w && (ky >> 1) != pm) {       // the parent row's fully-inside run
+                pm = ky >> 1;
+                ppa = 1; ppb = 0;
+                int tp = 0;
+                if (D > 1) tp = max(gap_t(pm << (lg + 1), iy), gap_t((pm + 1) << (lg + 1), iy));
+                if (l > lmin && tp <= tmax) {
+                    const int rp = chord(tp);
+                    const int qa = max(0, -((rp - X) >> (shf + 1)));
+                    const int qb = min((np >> 1) - 1, ((X + rp) >> (shf + 1)) - 1);
+                    if (qa <= qb) { ppa = 2 * qa; ppb = 2 * qb + 1; }
+                }
+            }
+            const bool split = ppa <= ppb;
+            const int b1 = split ? min(kb, ppa - 1) : kb;
+            const int a2 = split ? max(ka, ppb + 1) : kb + 1;
+            const int len1 = max(0, b1 - ka + 1), len2 = max(0, kb - a2 + 1);
+            const int m1 = __reduce_max_sync(0xffffffffu, len1);
+            const int m2 = __reduce_max_sync(0xffffffffu, len2);
+            const long long *__restrict__ row = lev + (int64_t)np * ky;
+            for (int j = 0; j < m1; j += 2) {
+                const long long v0 = j < len1 ? __ldg(row + ka + j) : 0LL;
+                const long long v1 = j + 1 < len1 ? __ldg(row + ka + j + 1) : 0LL;
+                G += v0 + v1;
+            }
+            for (int j = 0; j < m2; j += 2) {
+                const long long v0 = j < len2 ? __ldg(row + a2 + j) : 0LL;
+                const long long v1 = j + 1 < len2 ? __ldg(row + a2 + j + 1) : 0LL;
+                G += v0 + v1;
+            }
+        }
+    }
+    if (!act) return;
     const int sh = fixed_shift_f32(a.N, a.mx);
     Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
@@ -1390,9 +1537,18 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     k_fast_node<<<gb, 256, 0, st>>>(d, p->n, K, p->coef, p->self_mode, p->N, p->sigma, sphere,
                                     delta_dev, a_dev, p->thr4, d_pc, p->fastF, p->selfS, p->ir4);
     NL_CUDA_TRY(cudaGetLastError());
-    if (K == 0)
+    if (K == 0) {
         k_fixed_consts<<<gb, 256, 0, st>>>(p->N, std::pow(p->h, (double)d), p->fastF, p->selfS,
                                            p->selfQ, p->fastFh32);
+        // the plan-time bound max |b| of the fixed-point scale (word 2 of the aux header)
+        unsigned int *bw = reinterpret_cast<unsigned int *>(p->fast_mx) + 2;
+        const unsigned gm = (unsigned)std::min<int64_t>((p->N + 255) / 256, 1024);
+        k_max_abs_bits<<<gm, 256, 0, st>>>(p->N, p->b32, bw);
+        unsigned int bits = 0;
+        NL_CUDA_TRY(cudaMemcpyAsync(&bits, bw, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        NL_CUDA_TRY(cudaStreamSynchronize(st));
+        memcpy(&p->fast_bmax, &bits, sizeof(float));
+    }
     NL_CUDA_TRY(cudaGetLastError());
     NL_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_pc);
@@ -1455,7 +1611,7 @@ static cudaError_t step2_rowprefix(nl_plan *p, const float *u, bool leaf_only, c
     }
     a.leaf = leaf_out ? leaf_out : pyr + p->lvl_off[L];
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
-    k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr,
+    k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->fast_bmax, part, pyr,
                                            leaf_only ? 0 : p->lvl_off[a.lf]);
     int64_t bands = 1;
     for (int q = 1; q < d; ++q) bands *= p->n >> c;
@@ -1487,7 +1643,7 @@ static cudaError_t step2_panels(nl_plan *p, const float *u, cudaStream_t st)
              ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(p->b32) |
                reinterpret_cast<uintptr_t>(a.leaf)) & 15) == 0) ? 1 : 0;
     for (int l = 0; l <= L; ++l) a.lvl_off[l] = p->lvl_off[l];
-    k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->b32, part, pyr, p->lvl_off[a.lf]);
+    k_absmax_parts<<<nparts, 256, 0, st>>>(p->N, u, p->fast_bmax, part, pyr, p->lvl_off[a.lf]);
     int64_t bands = 1;
     for (int q = 1; q < d; ++q) bands *= p->n >> c;
     k_step2_panels<<<(unsigned)bands, 512, 0, st>>>(a);
@@ -1527,8 +1683,9 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         else k_fast_gather_rowprefix<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     } else {
         const unsigned gp = (unsigned)((p->N + GP_THREADS - 1) / GP_THREADS);
-        if (d == 1) k_fast_gather_panels<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
-        else if (d == 2) k_fast_gather_panels<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
+        if (d == 1) k_fast_gather_panels_lane<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
+        else if (d == 2 && p->n >= 32) k_fast_gather_panels<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
+        else if (d == 2) k_fast_gather_panels_lane<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     }
     prof_mark(p, 2, st);

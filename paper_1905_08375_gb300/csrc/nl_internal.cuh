@@ -127,6 +127,7 @@ struct nl_plan {
     unsigned long long *fast_mx;    // FP32 integer route scratch: word 0 max |v| of the last
                                     // apply (fixed-point scale), word 1 a block ticket, then
                                     // NL_FAST_PARTS per-block maxima (floats, from byte 16)
+    float fast_bmax;                // FP32 integer route: max |b| (bounds |u b| by max |u|)
     double *selfQ;                  // FP32 integer route: selfS / h^d and (float) fastF h^d
     float *fastFh32;
     long long *leaf_multi;          // leaf-row prefixes of several right-hand sides (grown on
