@@ -1110,6 +1110,188 @@ __global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels_lane(FastI64A
     Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
+// ---------------------------------------------------------------------------
+// Step 1 stored (the decomposition of Algorithm 1 as set-up data, as the paper's timings
+// treat it): each node's panels, in the order level, panel row, left part, right part, as
+// runs of consecutive panels of one row, one 32-bit record per run: the run's first panel as
+// a position in the pyramid buffer (27 bits) and its length (5 bits, 1..31; longer runs are
+// split; 0 = no run).  Records are stored warp-interleaved, record r of node 32 w + l at
+// runs[woff[w] + 32 r + l], so a warp reads 128 contiguous bytes per record; wcnt[w] is the
+// largest record count of the warp's nodes.  Step 3 then adds the panels of every record.
+// ---------------------------------------------------------------------------
+constexpr int RUN_POS_BITS = 27;
+constexpr unsigned RUN_POS_MASK = (1u << RUN_POS_BITS) - 1u;
+constexpr int RUN_MAX_LEN = 31;
+
+// calls f(position in the pyramid, length) for every run of node (ix, iy) (1-D or 2-D); ch is
+// this thread's column of a shared-memory chord table (stride GP_THREADS)
+template <int D, typename F>
+__device__ __forceinline__ void visit_runs(int n, int L, const int64_t *lvl_off, int ix, int iy,
+                                           int T4, int *ch, F &&f)
+{
+    const int X = 2 * ix + 1;
+    const int r0 = isqrt_fast(T4);
+    const int tmax = (r0 + 1) >> 1;
+    if (D > 1) {
+        const int tc = min(tmax, GP_CHORDS - 1);
+        ch[0] = r0;
+        for (int t = 1; t <= tc; ++t) ch[t * GP_THREADS] = isqrt_fast(T4 - sq(2 * t - 1));
+    }
+    auto chord = [&](int t) -> int {
+        if (D == 1) return r0;
+        return t < GP_CHORDS ? ch[t * GP_THREADS] : isqrt_fast(T4 - sq(2 * t - 1));
+    };
+    auto emit = [&](int64_t pos, int len) {
+        while (len > 0) {
+            const int m = min(len, RUN_MAX_LEN);
+            f(pos, m);
+            pos += m;
+            len -= m;
+        }
+    };
+    int lmin = 0;
+    while (lmin < L && (1 << (L - lmin + 1)) > 2 * r0) ++lmin;
+    for (int l = lmin; l <= L; ++l) {
+        const int np = 1 << l;
+        const int lg = L - l;
+        const int shf = lg + 1;
+        const bool leaf = (l == L);
+        int ylo = 0, yhi = 0;
+        if (D > 1) {
+            if (leaf) {
+                ylo = max(0, iy - tmax);
+                yhi = min(n - 1, iy + tmax);
+            } else {
+                ylo = max(0, -((tmax - 1 - iy) >> lg));
+                yhi = min(np - 1, ((iy + tmax) >> lg) - 1);
+            }
+        }
+        int pm = -1, ppa = 1, ppb = 0;
+        for (int ky = ylo; ky <= yhi; ++ky) {
+            int r;
+            if (D == 1) r = r0;
+            else if (leaf) r = chord(ky > iy ? ky - iy : iy - ky);
+            else r = chord(max(gap_t(ky << lg, iy), gap_t((ky + 1) << lg, iy)));
+            int ka, kb;
+            if (leaf) {
+                ka = max(0, -((r - X) >> 1) - 1);
+                kb = min(n - 1, (X + r) >> 1);
+            } else {
+                ka = max(0, -((r - X) >> shf));
+                kb = min(np - 1, ((X + r) >> shf) - 1);
+            }
+            if (ka > kb) continue;
+            if (l > lmin && (ky >> 1) != pm) {
+                pm = ky >> 1;
+                ppa = 1; ppb = 0;
+                int tp = 0;
+                if (D > 1) tp = max(gap_t(pm << (lg + 1), iy), gap_t((pm + 1) << (lg + 1), iy));
+                if (tp <= tmax) {
+                    const int rp = chord(tp);
+                    const int qa = max(0, -((rp - X) >> (shf + 1)));
+                    const int qb = min((np >> 1) - 1, ((X + rp) >> (shf + 1)) - 1);
+                    if (qa <= qb) { ppa = 2 * qa; ppb = 2 * qb + 1; }
+                }
+            }
+            const int64_t base = lvl_off[l] + (int64_t)np * ky;
+            if (ppa <= ppb) {
+                emit(base + ka, min(kb, ppa - 1) - ka + 1);
+                const int a2 = max(ka, ppb + 1);
+                emit(base + a2, kb - a2 + 1);
+            } else {
+                emit(base + ka, kb - ka + 1);
+            }
+        }
+    }
+}
+
+struct RunArgs {
+    int n, L;
+    int64_t N;
+    const int *thr4;
+    int64_t lvl_off[NL_MAX_LEVELS + 2];
+};
+
+template <int D>
+__global__ void __launch_bounds__(GP_THREADS) k_runs_count(RunArgs a, int *__restrict__ cnt)
+{
+    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
+    const int64_t i = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
+    if (i >= a.N) return;
+    const int ix = (int)(i % a.n), iy = D > 1 ? (int)(i / a.n) : 0;
+    int c = 0;
+    visit_runs<D>(a.n, a.L, a.lvl_off, ix, iy, a.thr4[i], s_ch + threadIdx.x,
+                  [&](int64_t, int) { ++c; });
+    cnt[i] = c;
+}
+
+template <int D>
+__global__ void __launch_bounds__(GP_THREADS) k_runs_write(RunArgs a, const int64_t *__restrict__ woff,
+                                                           const int *__restrict__ wcnt,
+                                                           unsigned *__restrict__ runs)
+{
+    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
+    const int64_t i = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
+    if (i >= a.N) return;
+    const int ix = (int)(i % a.n), iy = D > 1 ? (int)(i / a.n) : 0;
+    const int64_t w = i >> 5;
+    unsigned *out = runs + woff[w] + (i & 31);
+    int c = 0;
+    visit_runs<D>(a.n, a.L, a.lvl_off, ix, iy, a.thr4[i], s_ch + threadIdx.x,
+                  [&](int64_t pos, int len) {
+                      out[32 * (int64_t)c] = (unsigned)pos | ((unsigned)len << RUN_POS_BITS);
+                      ++c;
+                  });
+    for (; c < wcnt[w]; ++c) out[32 * (int64_t)c] = 0u;
+}
+
+__global__ void k_runs_warp_max(int64_t N, const int *__restrict__ cnt, int *__restrict__ wcnt)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = i < N ? cnt[i] : 0;
+    const int m = __reduce_max_sync(0xffffffffu, c);
+    if ((i & 31) == 0 && i < N) wcnt[i >> 5] = m;
+}
+
+// Step 3 from the stored runs: each lane adds the panels of its records, four records loaded
+// ahead; record r of the warp's nodes is one 128-byte line
+__global__ void __launch_bounds__(256) k_fast_gather_runs(FastI64Args a,
+                                                          const unsigned *__restrict__ runs,
+                                                          const int64_t *__restrict__ woff,
+                                                          const int *__restrict__ wcnt,
+                                                          const float *__restrict__ u,
+                                                          float *__restrict__ Lu)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t w = i >> 5;
+    if ((w << 5) >= a.N) return;                      // whole warps only
+    const unsigned *__restrict__ rec = runs + woff[w] + (i & 31);
+    const int cnt = wcnt[w];
+    const long long *__restrict__ pyr = a.pyr;
+    long long G = 0;
+    int r = 0;
+    for (; r + 4 <= cnt; r += 4) {
+        unsigned q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = __ldcs(rec + 32 * (int64_t)(r + k));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long *p = pyr + (q[k] & RUN_POS_MASK);
+            const int len = (int)(q[k] >> RUN_POS_BITS);
+            for (int j = 0; j < len; ++j) G += __ldg(p + j);
+        }
+    }
+    for (; r < cnt; ++r) {
+        const unsigned q = __ldcs(rec + 32 * (int64_t)r);
+        const long long *p = pyr + (q & RUN_POS_MASK);
+        const int len = (int)(q >> RUN_POS_BITS);
+        for (int j = 0; j < len; ++j) G += __ldg(p + j);
+    }
+    if (i >= a.N) return;
+    const int sh = fixed_shift_f32(a.N, a.mx);
+    Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
+}
+
 // Warp-uniform form for n >= 32 (the 32 nodes of a warp share their row): every lane walks
 // the union of the warp's levels and panel rows, and each run's panels are added in a loop
 // over the warp's longest run length with the shorter runs predicated off, so control flow
@@ -1455,6 +1637,68 @@ static int moments_count(int d, int K)
     return M;
 }
 
+// Step 1 at plan time for the panel-by-panel route (1-D, and 2-D with n >= 32): count every
+// node's runs, take the per-warp maxima and offsets on the host, write the records.  Skipped
+// (the gather then enumerates the decomposition itself) when the pyramid positions need more
+// than 27 bits or the records would exceed 2^28 (1 GiB).
+static nl_status build_runs(nl_plan *p, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    if (p->lvl_off[p->L] + N > (int64_t)RUN_POS_MASK) return NL_OK;
+    RunArgs ra;
+    ra.n = p->n; ra.L = p->L; ra.N = N; ra.thr4 = p->thr4;
+    for (int l = 0; l <= p->L; ++l) ra.lvl_off[l] = p->lvl_off[l];
+    const int64_t nw = (N + 31) / 32;
+    int *cnt = nullptr, *wcnt = nullptr;
+    int64_t *woff = nullptr;
+    unsigned *runs = nullptr;
+    auto fail = [&](nl_status s) {
+        if (cnt) cudaFree(cnt);
+        if (wcnt) cudaFree(wcnt);
+        if (woff) cudaFree(woff);
+        if (runs) cudaFree(runs);
+        return s;
+    };
+    if (cudaMalloc(&cnt, N * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&wcnt, nw * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&woff, nw * sizeof(int64_t)) != cudaSuccess) {
+        nl_set_error("nl_plan_create: allocation for the stored decomposition failed");
+        return fail(NL_ENOMEM);
+    }
+    const unsigned g = (unsigned)((N + GP_THREADS - 1) / GP_THREADS);
+    if (p->d == 1) k_runs_count<1><<<g, GP_THREADS, 0, st>>>(ra, cnt);
+    else k_runs_count<2><<<g, GP_THREADS, 0, st>>>(ra, cnt);
+    k_runs_warp_max<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, cnt, wcnt);
+    std::vector<int> hw(nw);
+    std::vector<int64_t> ho(nw);
+    cudaError_t ce = cudaMemcpyAsync(hw.data(), wcnt, nw * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (counts)"));
+    int64_t tot = 0;
+    for (int64_t w = 0; w < nw; ++w) { ho[w] = tot; tot += 32 * (int64_t)hw[w]; }
+    if (tot > ((int64_t)1 << 28)) return fail(NL_OK);
+    if (cudaMalloc(&runs, std::max<int64_t>(tot, 1) * sizeof(unsigned)) != cudaSuccess) {
+        nl_set_error("nl_plan_create: allocation of %lld run records failed", (long long)tot);
+        return fail(NL_ENOMEM);
+    }
+    ce = cudaMemsetAsync(runs, 0, std::max<int64_t>(tot, 1) * sizeof(unsigned), st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(woff, ho.data(), nw * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (offsets)"));
+    if (p->d == 1) k_runs_write<1><<<g, GP_THREADS, 0, st>>>(ra, woff, wcnt, runs);
+    else k_runs_write<2><<<g, GP_THREADS, 0, st>>>(ra, woff, wcnt, runs);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (records)"));
+    cudaFree(cnt);
+    p->runs = runs;
+    p->runs_woff = woff;
+    p->runs_wcnt = wcnt;
+    p->runs_records = (size_t)tot;
+    p->device_bytes += (size_t)tot * sizeof(unsigned) + nw * (sizeof(int) + sizeof(int64_t));
+    return NL_OK;
+}
+
 nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a_dev,
                             cudaStream_t st)
 {
@@ -1553,6 +1797,8 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     NL_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_pc);
     p->device_bytes -= 8 * sizeof(double);
+    if (K == 0 && p->fast_variant == NL_FAST_PANELS && d <= 2 && (d == 1 || p->n >= 32))
+        return build_runs(p, st);
     return NL_OK;
 }
 
@@ -1683,7 +1929,10 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         else k_fast_gather_rowprefix<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     } else {
         const unsigned gp = (unsigned)((p->N + GP_THREADS - 1) / GP_THREADS);
-        if (d == 1) k_fast_gather_panels_lane<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
+        if (p->runs) {
+            const unsigned gr = (unsigned)(((p->N + 31) / 32 * 32 + 255) / 256);
+            k_fast_gather_runs<<<gr, 256, 0, st>>>(a, p->runs, p->runs_woff, p->runs_wcnt, u, Lu);
+        } else if (d == 1) k_fast_gather_panels_lane<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else if (d == 2 && p->n >= 32) k_fast_gather_panels<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_panels_lane<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else k_fast_gather_i64<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
