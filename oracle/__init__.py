@@ -83,7 +83,7 @@ def lib():
         L.or_pd_direct.restype = i
         L.or_pd_direct.argtypes = [i, i, vp, vp, d, i, vp, vp, vp, i64]
         L.or_fast_pd_leafset.restype = i
-        L.or_fast_pd_leafset.argtypes = [i, i, vp, vp, d, i, vp, vp, vp, i64]
+        L.or_fast_pd_leafset.argtypes = [i, i, vp, vp, d, i, vp, i, vp, vp, vp, i64]
         L.or_tree_decompose.restype = i64
         L.or_tree_decompose.argtypes = [i, i, d, i64, vp, vp, i64, vp]
         L.or_fast_tree.restype = i
@@ -281,9 +281,10 @@ def fast_sym_leafset(u, d, L, delta, K=0, alpha=1.0, scale=1.0, normalize=True,
     return out[0] if squeeze else out
 
 
-def fast_pd_leafset(u, d, L, delta, c, scale=1.0, idx=None):
-    """Fast-path peridynamics of degree 0 over the leaf set of Algorithm 1:
-    h^d sum_{k in LS(i)} scale c_ik (xi xi^T / delta_i^3) (u_k - u_i).
+def fast_pd_leafset(u, d, L, delta, c, scale=1.0, K=0, idx=None):
+    """Fast-path peridynamics over the leaf set of Algorithm 1 with the polynomial
+    micromodulus p^{2K} matched to gamma(s) = s^-3 (K = 0: p = 1):
+    h^d sum_{k in LS(i)} scale c_ik p(|xi|/delta_i) (xi xi^T / delta_i^3) (u_k - u_i).
     u: [nrhs, d, N] or [d, N]."""
     u = _f64(u)
     n = 1 << L
@@ -292,11 +293,12 @@ def fast_pd_leafset(u, d, L, delta, c, scale=1.0, idx=None):
     nrhs = u3.shape[0]
     dl = _delta_field(delta, d, n)
     c_ = _delta_field(c, d, n)
+    pc = poly_coeffs(K, 3.0)
     ix, nix = _idx(idx)
     M = nix if ix is not None else n ** d
     out = np.zeros((nrhs, d, M))
-    rc = lib().or_fast_pd_leafset(d, L, _ptr(dl), _ptr(c_), float(scale), nrhs, _ptr(u3),
-                                  _ptr(out), _ptr(ix), nix)
+    rc = lib().or_fast_pd_leafset(d, L, _ptr(dl), _ptr(c_), float(scale), int(K), _ptr(pc),
+                                  nrhs, _ptr(u3), _ptr(out), _ptr(ix), nix)
     if rc != 0:
         raise ValueError(f"or_fast_pd_leafset failed ({rc})")
     return out[0] if squeeze else out

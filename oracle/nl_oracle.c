@@ -808,19 +808,22 @@ int or_fast_sym_leafset(int d, int L, const double *delta, int K, const double *
 }
 
 /*
- * Fast-path peridynamics (the polynomial micromodulus of the paper's outlook, degree 0):
- * the bond tensor xi xi^T / |xi|^3 of Eq. (1.2) is replaced by xi xi^T p(|xi|/delta_i) /
- * delta_i^3 with p = 1 (p matches s^{-3} at the horizon, as p^{2K} with K = 0 matches
- * gamma), and the sum runs over the leaf set of Algorithm 1 (every leaf cell, inside Omega
- * or not, that meets the open ball of x_i):
- *   (L u)_i = h^d sum_{k in LS(i), k != i} sigma c_ik (xi xi^T / delta_i^3) (u_k - u_i),
- * c_ik = (c_i + c_k)/2, with u_k = 0 and c_k = c_i for cells outside Omega.
- * u, out: [nrhs][d][N].  idx as above.
+ * Fast-path peridynamics (the polynomial micromodulus of the paper's outlook): the bond tensor
+ * xi xi^T / |xi|^3 of Eq. (1.2), i.e. xi xi^T gamma(|xi|/delta_i) / delta_i^3 with the profile
+ * gamma(s) = s^{-3}, is replaced by xi xi^T p^{2K}(|xi|/delta_i) / delta_i^3, p^{2K} the even
+ * polynomial of degree 2K matching s^{-3} and its first K derivatives at s = 1 (the splitting
+ * of Sec. 3 applied to this profile; K = 0 gives p = 1), and the sum runs over the leaf set of
+ * Algorithm 1 (every leaf cell, inside Omega or not, that meets the open ball of x_i):
+ *   (L u)_i = h^d sum_{k in LS(i), k != i} sigma c_ik p(|xi|/delta_i) (xi xi^T / delta_i^3)
+ *             (u_k - u_i),
+ * c_ik = (c_i + c_k)/2, with u_k = 0 and c_k = c_i for cells outside Omega.  p holds p_0..p_K
+ * (p(s) = sum_m p_m s^{2m}).  u, out: [nrhs][d][N].  idx as above.
  */
-int or_fast_pd_leafset(int d, int L, const double *delta, const double *c, double sigma,
-                       int nrhs, const double *u, double *out, const int64_t *idx, int64_t nidx)
+int or_fast_pd_leafset(int d, int L, const double *delta, const double *c, double sigma, int K,
+                       const double *p, int nrhs, const double *u, double *out,
+                       const int64_t *idx, int64_t nidx)
 {
-    if (d < 1 || d > 3 || L < 0 || L > 20) return 1;
+    if (d < 1 || d > 3 || L < 0 || L > 20 || K < 0 || K > 7 || !p) return 1;
     const int n = 1 << L;
     const int64_t N = num_nodes(d, n);
     const int64_t M = idx ? nidx : N;
@@ -860,8 +863,13 @@ int or_fast_pd_leafset(int d, int L, const double *delta, const double *c, doubl
                             const double uj = inside ? ur[(int64_t)k * N + fj] : 0.0;
                             xdu += xi[k] * (uj - ur[(int64_t)k * N + fi]);
                         }
+                        double r2 = 0.0;                  /* |xi|^2 / delta_i^2 */
+                        for (int k = 0; k < d; ++k) r2 += xi[k] * xi[k];
+                        r2 /= di * di;
+                        double w = 0.0, pw = 1.0;          /* p(s) = sum_m p_m s^{2m} */
+                        for (int m = 0; m <= K; ++m) { w += p[m] * pw; pw *= r2; }
                         const double cik = 0.5 * (c[fi] + (inside ? c[fj] : c[fi]));
-                        for (int k = 0; k < d; ++k) acc[k] += cik * xdu * xi[k];
+                        for (int k = 0; k < d; ++k) acc[k] += cik * w * xdu * xi[k];
                     }
             for (int k = 0; k < d; ++k) out[((int64_t)r * d + k) * M + q] = pre * acc[k];
         }

@@ -15,7 +15,8 @@
 // bound (2R + 3)^2 on a leaf set's cells, n^2 C max|q| < 2^61: every per-node sum of
 // differences (over rows, times dy or dy^2) and the final combination with the node's column
 // (o_x = k - kx) then fit in 64-bit integers.  Rows and runs are those of the scalar leaf-row
-// gather (the same half-unit geometry).  2-D, FP32 data.
+// gather (the same half-unit geometry).  2-D, FP32 data.  K = 1, 2 (the polynomial
+// micromodulus p^{2K} matched to s^-3) extend this below with the moments of o_x up to 2K + 2.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -27,6 +28,8 @@ namespace {
 constexpr int FPD_FIELDS = 4;                   // u_x, u_y, c u_x, c u_y
 constexpr int FPD_ARRAYS = 10;                  // ux: P0 P1 P2, uy: P0 P1, cux: P0 P1 P2, cuy: P0 P1
 constexpr int FPD_PARTS = 1024;
+
+struct FpdPoly { double p[8]; };                // p_0 .. p_K of the micromodulus polynomial
 
 __device__ __forceinline__ int isqrt_pd(int x)   // floor(sqrt(x)), 0 <= x < 2^30
 {
@@ -41,7 +44,8 @@ __device__ __forceinline__ int sqi(int v) { return v * v; }
 // plan time: F_i and M_i (FP64) over the whole leaf set
 __global__ void k_fpd_node(int n, int64_t N, double sigma, double h, const double *__restrict__ delta,
                            const double *__restrict__ c, const int *__restrict__ thr4,
-                           double *__restrict__ F, double *__restrict__ M)
+                           double *__restrict__ F, double *__restrict__ M, int K, FpdPoly pc,
+                           double *__restrict__ IR2)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -50,6 +54,8 @@ __global__ void k_fpd_node(int n, int64_t N, double sigma, double h, const doubl
     const int T4 = thr4[i];
     const double ci = c ? c[i] : 1.0;
     double mxx = 0.0, mxy = 0.0, myy = 0.0;
+    const double Ri = delta[i] * n;
+    const double ir2 = 1.0 / (Ri * Ri);
     const int r0 = isqrt_pd(T4);
     const int ylo = -((r0 - Y) >> 1) - 1, yhi = (Y + r0) >> 1;       // rows meeting the ball
     for (int ky = ylo; ky <= yhi; ++ky) {
@@ -64,7 +70,14 @@ __global__ void k_fpd_node(int n, int64_t N, double sigma, double h, const doubl
             const int dx = kx - ix;
             if (dx == 0 && dy == 0) continue;
             const bool in = row_in && kx >= 0 && kx < n;
-            const double w = ci + (in ? (c ? c[(int64_t)ky * n + kx] : 1.0) : ci);
+            double pw = 1.0;                        // p(|o| / R_i), o in cells, R_i = delta_i n
+            if (K > 0) {
+                const double s2 = (double)(dx * dx + dy * dy) * ir2;
+                double t = pc.p[K];
+                for (int m = K - 1; m >= 0; --m) t = t * s2 + pc.p[m];
+                pw = t;
+            }
+            const double w = pw * (ci + (in ? (c ? c[(int64_t)ky * n + kx] : 1.0) : ci));
             mxx += w * dx * dx;
             mxy += w * dx * dy;
             myy += w * dy * dy;
@@ -72,6 +85,7 @@ __global__ void k_fpd_node(int n, int64_t N, double sigma, double h, const doubl
     }
     const double di = delta[i];
     F[i] = sigma * h * h * h * h / (2.0 * di * di * di);
+    if (IR2) IR2[i] = ir2;
     M[3 * i] = mxx; M[3 * i + 1] = mxy; M[3 * i + 2] = myy;
 }
 
@@ -266,15 +280,205 @@ __global__ void __launch_bounds__(256) k_fpd_gather(FpdGatherArgs a, const float
     outy[i] = (float)(Fi * (ci * A[0][1] + A[1][1] - (Mi[1] * uxi + Mi[2] * uyi)));
 }
 
+// ---------------------------------------------------------------------------
+// Polynomial micromodulus, K = 1, 2: the weight p(|o|/R_i) = sum_m beta_m (o_x^2 + o_y^2)^m,
+// beta_m = p_m / R_i^{2m}, expands along a leaf row (o_y fixed) into powers of o_x, so the row
+// needs the run sums of o_x^e q for e = 0 .. 2K+2 (x-type fields) and 0 .. 2K+1 (y-type):
+// from prefix sums of k^m q (k the column) by differences, centred on the node's column with
+// the binomial expansion, all modulo 2^64 (the centred values are small and come out exact).
+// Over the rows they are accumulated, times powers of o_y, into the exact integer sums
+//   Zxe[m][j] = sum dy^{2(m-j)} C_x(2j+2),  Zyo[m][j] = sum dy^{2(m-j)+1} C_y(2j+1),
+//   Zxo[m][j] = sum dy^{2(m-j)+1} C_x(2j+1),  Zye[m][j] = sum dy^{2(m-j)+2} C_y(2j),
+// and once per node A_x = sum_m beta_m sum_j binom(m, j) (Zxe + Zyo),
+// A_y = sum_m beta_m sum_j binom(m, j) (Zxo + Zye) in FP64.  Array layout per group g
+// (0: u, 1: c u): x-type powers 0 .. 2K+2, then y-type powers 0 .. 2K+1 (4K + 5 arrays).
+// Scale: 2^bits >= (2R + 3)^2 (R + 2)^{2K+2} bounds every such sum.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_fpd_scan_k(FpdScanArgs a, int K)
+{
+    __shared__ int s_sh[FPD_FIELDS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        for (int f = 0; f < FPD_FIELDS; ++f) {
+            float m = 0.f;
+            for (int k = lane; k < a.nparts; k += 32) m = fmaxf(m, a.part[f * FPD_PARTS + k]);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) s_sh[f] = fpd_shift(m, a.bits);
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x < FPD_FIELDS) a.shifts[threadIdx.x] = s_sh[threadIdx.x];
+    const int n = a.n;
+    const int per_g = 4 * K + 5;                     // arrays per group
+    const int64_t item = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (item >= (int64_t)n * 2 * per_g) return;
+    const int row = (int)(item / (2 * per_g));
+    const int arr = (int)(item % (2 * per_g));
+    const int g = arr / per_g, r = arr % per_g;
+    const bool xf = r < 2 * K + 3;                   // x-type field of the group
+    const int pw = xf ? r : r - (2 * K + 3);
+    const int f = 2 * g + (xf ? 0 : 1);              // shifts: u_x, u_y, c u_x, c u_y
+    const int64_t base = (int64_t)row * n;
+    const float *__restrict__ src = xf ? a.ux : a.uy;
+    unsigned long long carry = 0ull;
+    long long *P = a.P + (int64_t)arr * a.N + base;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        unsigned long long v = 0ull;
+        if (k < n) {
+            float x = src[base + k];
+            if (g) x *= a.c[base + k];
+            v = (unsigned long long)__float2ll_rn(ldexpf(x, s_sh[f]));
+            for (int e = 0; e < pw; ++e) v *= (unsigned long long)k;        // k^pw q, mod 2^64
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long w = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += w;
+        }
+        v += carry;
+        if (k < n) P[k] = (long long)v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_fpd_gather_k(FpdGatherArgs a, FpdPoly pc,
+                                                      const double *__restrict__ ir2v,
+                                                      const float *__restrict__ ux,
+                                                      const float *__restrict__ uy,
+                                                      float *__restrict__ outx,
+                                                      float *__restrict__ outy)
+{
+    typedef unsigned long long u64;
+    constexpr int EX = 2 * K + 3, EY = 2 * K + 2, PG = EX + EY;
+    constexpr int NJ = (K + 1) * (K + 2) / 2;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int ix = (int)(i % n), iy = (int)(i / n);
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    const int64_t N = a.N;
+    const u64 ki = (u64)ix;
+    // binomial coefficients C(e, m), e <= 2K + 2
+    u64 Z[2][4][NJ];                                  // [g][xe, yo, xo, ye][(m, j)]
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < NJ; ++q) Z[g][t][q] = 0ull;
+    for (int t = 0;; ++t) {
+        const int e = t == 0 ? 0 : sqi(2 * t - 1);
+        if (e > T4) break;
+        const int r = isqrt_pd(T4 - e);
+        const int ka = max(0, -((r - X) >> 1) - 1);
+        const int kb = min(n - 1, (X + r) >> 1);
+        for (int s = 0; s < (t > 0 ? 2 : 1); ++s) {
+            const int dy = s ? -t : t;
+            const int ky = iy + dy;
+            if (ky < 0 || ky >= n) continue;
+            const int64_t row = (int64_t)ky * n;
+            u64 dyp[EX];                              // dy^a, a <= 2K + 2
+            dyp[0] = 1ull;
+#pragma unroll
+            for (int q = 1; q < EX; ++q) dyp[q] = dyp[q - 1] * (u64)(long long)dy;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const long long *Pg = a.P + (int64_t)(g * PG) * N;
+                u64 D[EX], Cx[EX], Cy[EY];
+#pragma unroll
+                for (int m = 0; m < EX; ++m) D[m] = pdiff(Pg + (int64_t)m * N, row, ka, kb);
+#pragma unroll
+                for (int q = 0; q < EX; ++q) {           // centred: sum C(q,m) (-k_i)^{q-m} D_m
+                    u64 acc = 0ull, pk = 1ull;
+#pragma unroll
+                    for (int m = q; m >= 0; --m) {
+                        u64 bin = 1ull;
+#pragma unroll
+                        for (int z = 0; z < q - m; ++z) bin = bin * (u64)(m + 1 + z) / (u64)(1 + z);
+                        const u64 term = bin * pk * D[m];
+                        acc += ((q - m) & 1) ? (u64)(0ull - term) : term;
+                        pk *= ki;
+                    }
+                    Cx[q] = acc;
+                }
+#pragma unroll
+                for (int m = 0; m < EY; ++m) D[m] = pdiff(Pg + (int64_t)(EX + m) * N, row, ka, kb);
+#pragma unroll
+                for (int q = 0; q < EY; ++q) {
+                    u64 acc = 0ull, pk = 1ull;
+#pragma unroll
+                    for (int m = q; m >= 0; --m) {
+                        u64 bin = 1ull;
+#pragma unroll
+                        for (int z = 0; z < q - m; ++z) bin = bin * (u64)(m + 1 + z) / (u64)(1 + z);
+                        const u64 term = bin * pk * D[m];
+                        acc += ((q - m) & 1) ? (u64)(0ull - term) : term;
+                        pk *= ki;
+                    }
+                    Cy[q] = acc;
+                }
+                int q = 0;
+#pragma unroll
+                for (int m = 0; m <= K; ++m)
+#pragma unroll
+                    for (int j = 0; j <= m; ++j, ++q) {
+                        Z[g][0][q] += dyp[2 * (m - j)] * Cx[2 * j + 2];
+                        Z[g][1][q] += dyp[2 * (m - j) + 1] * Cy[2 * j + 1];
+                        Z[g][2][q] += dyp[2 * (m - j) + 1] * Cx[2 * j + 1];
+                        Z[g][3][q] += dyp[2 * (m - j) + 2] * Cy[2 * j];
+                    }
+            }
+        }
+    }
+    const double ir2 = ir2v[i];                     // 1 / R_i^2, R_i = delta_i n
+    double A[2][2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const int sx = a.shifts[2 * g], sy = a.shifts[2 * g + 1];
+        double ax = 0.0, ay = 0.0, beta = 1.0;
+        int q = 0;
+#pragma unroll
+        for (int m = 0; m <= K; ++m) {
+            double bx = 0.0, by = 0.0, bin = 1.0;
+#pragma unroll
+            for (int j = 0; j <= m; ++j, ++q) {
+                bx += bin * (ldexp((double)(long long)Z[g][0][q], -sx) +
+                             ldexp((double)(long long)Z[g][1][q], -sy));
+                by += bin * (ldexp((double)(long long)Z[g][2][q], -sx) +
+                             ldexp((double)(long long)Z[g][3][q], -sy));
+                bin = bin * (m - j) / (j + 1);
+            }
+            ax += pc.p[m] * beta * bx;
+            ay += pc.p[m] * beta * by;
+            beta *= ir2;
+        }
+        A[g][0] = ax;
+        A[g][1] = ay;
+    }
+    const double ci = a.c[i];
+    const double uxi = (double)ux[i], uyi = (double)uy[i];
+    const double *Mi = a.M + 3 * i;
+    const double Fi = a.F[i];
+    outx[i] = (float)(Fi * (ci * A[0][0] + A[1][0] - (Mi[0] * uxi + Mi[1] * uyi)));
+    outy[i] = (float)(Fi * (ci * A[0][1] + A[1][1] - (Mi[1] * uxi + Mi[2] * uyi)));
+}
+
 }  // namespace
 
 // plan-time set-up (2-D NL_PD_BOND plans with n = 2^L <= 8192)
 nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double *c_dev,
                                cudaStream_t st)
 {
-    if (p->d != 2 || p->L < 0 || p->n > 8192 || !p->thr4) return NL_OK;
-    // the sums' range (n^2 (2R + 3)^2) leaves at least 2^13 levels for max|v|
-    if ((double)p->n * p->n * (2.0 * p->Rmax + 3) * (2.0 * p->Rmax + 3) > 0x1p48) return NL_OK;
+    if (p->d != 2 || p->L < 0 || p->n > 8192 || !p->thr4 || p->K > 2) return NL_OK;
+    // 2^bits bounds every per-node integer sum: n^2 (2 Rmax + 3)^2 for K = 0, (2 Rmax + 3)^2
+    // (Rmax + 2)^{2K+2} for K >= 1; at least 2^13 levels must remain for max|v|
+    const double rr = 2.0 * p->Rmax + 3;
+    const double bound = p->K == 0 ? (double)p->n * p->n * rr * rr
+                                   : rr * rr * std::pow(p->Rmax + 2.0, 2.0 * p->K + 2.0);
+    if (bound > 0x1p48) return NL_OK;
     const int64_t N = p->N;
     auto alloc = [&](void **ptr, size_t bytes) -> nl_status {
         if (cudaMalloc(ptr, bytes ? bytes : 1) != cudaSuccess) {
@@ -287,13 +491,16 @@ nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double
     nl_status s;
     if ((s = alloc((void **)&p->fpd_F, N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->fpd_M, 3 * N * sizeof(double))) != NL_OK) return s;
-    if ((s = alloc((void **)&p->fpd_P, (size_t)FPD_ARRAYS * N * sizeof(long long))) != NL_OK) return s;
+    if (p->K > 0 && (s = alloc((void **)&p->fpd_ir2, N * sizeof(double))) != NL_OK) return s;
+    const int arrays = p->K == 0 ? FPD_ARRAYS : 8 * p->K + 10;
+    if ((s = alloc((void **)&p->fpd_P, (size_t)arrays * N * sizeof(long long))) != NL_OK) return s;
     if ((s = alloc((void **)&p->fpd_aux, FPD_FIELDS * FPD_PARTS * sizeof(float) + 64)) != NL_OK) return s;
-    // 2^bits >= n^2 (2 Rmax + 3)^2 bounds every per-node sum (see the header)
-    const double bound = (double)p->n * p->n * (2.0 * p->Rmax + 3) * (2.0 * p->Rmax + 3);
     p->fpd_bits = (int)std::ceil(std::log2(bound));
+    FpdPoly pc;
+    for (int m = 0; m < 8; ++m) pc.p[m] = p->poly[m];
     k_fpd_node<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(p->n, N, p->sigma, p->h, delta_dev,
-                                                           c_dev, p->thr4, p->fpd_F, p->fpd_M);
+                                                           c_dev, p->thr4, p->fpd_F, p->fpd_M,
+                                                           p->K, pc, p->fpd_ir2);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
@@ -303,7 +510,7 @@ nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cud
 {
     if (!p->fpd_P) {
         nl_set_error("nl_apply_fast: the fast peridynamic path needs a 2-D plan with n = 2^L "
-                     "<= 8192");
+                     "<= 8192, K <= 2 and a horizon whose integer sums fit 64 bits");
         return NL_EUNSUPPORTED;
     }
     const int64_t N = p->N;
@@ -320,11 +527,21 @@ nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cud
         sa.n = p->n; sa.bits = p->fpd_bits; sa.nparts = nparts;
         sa.ux = ux; sa.uy = uy; sa.c = p->b32; sa.part = part; sa.shifts = shifts;
         sa.P = p->fpd_P; sa.N = N;
-        k_fpd_scan<<<(unsigned)((p->n + 3) / 4), 128, 0, st>>>(sa);
         FpdGatherArgs ga;
         ga.n = p->n; ga.N = N; ga.thr4 = p->thr4; ga.c = p->b64;
         ga.F = p->fpd_F; ga.M = p->fpd_M; ga.P = p->fpd_P; ga.shifts = shifts;
-        k_fpd_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(ga, ux, uy, ox, oy);
+        if (p->K == 0) {
+            k_fpd_scan<<<(unsigned)((p->n + 3) / 4), 128, 0, st>>>(sa);
+            k_fpd_gather<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(ga, ux, uy, ox, oy);
+        } else {
+            const int64_t items = (int64_t)p->n * 2 * (4 * p->K + 5);
+            k_fpd_scan_k<<<(unsigned)((items + 3) / 4), 128, 0, st>>>(sa, p->K);
+            FpdPoly pc;
+            for (int m = 0; m < 8; ++m) pc.p[m] = p->poly[m];
+            const unsigned gg = (unsigned)((N + 127) / 128);
+            if (p->K == 1) k_fpd_gather_k<1><<<gg, 128, 0, st>>>(ga, pc, p->fpd_ir2, ux, uy, ox, oy);
+            else k_fpd_gather_k<2><<<gg, 128, 0, st>>>(ga, pc, p->fpd_ir2, ux, uy, ox, oy);
+        }
         NL_CUDA_TRY(cudaGetLastError());
     }
     return NL_OK;

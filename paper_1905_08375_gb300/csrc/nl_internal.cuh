@@ -93,6 +93,7 @@ struct nl_plan {
     float *g3d32;                   // 3-D POWER, constant horizon: [2R+1]^3 weights (oy, ox, oz)
     int x3_var;                     // 3-D slab kernel variant (timed at plan creation)
     double *fpd_F, *fpd_M;          // fast-path PD: F_i and M_i (3 per node)
+    double *fpd_ir2;                // fast-path PD, K >= 1: 1 / R_i^2 (R_i = delta_i n)
     long long *fpd_P;               // fast-path PD: ten leaf-row prefix arrays [10][N]
     void *fpd_aux;                  // fast-path PD: per-block bounds and the four scale exponents
     int fpd_bits;                   // fast-path PD: 2^bits >= n^2 (2 Rmax + 3)^2

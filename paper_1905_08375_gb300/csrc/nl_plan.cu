@@ -364,7 +364,8 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         nl_set_error("nl_plan_create: coefficient mode %d needs the field a", k->coef);
         return NL_EINVAL;
     }
-    if ((k->family == NL_POLY || k->family == NL_KAPPA) && (k->K < 0 || k->K > 3)) {
+    if ((k->family == NL_POLY || k->family == NL_KAPPA || k->family == NL_PD_BOND) &&
+        (k->K < 0 || k->K > 3)) {
         nl_set_error("nl_plan_create: K must be 0..3 (got %d)", k->K);
         return NL_EINVAL;
     }
@@ -460,7 +461,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         p->sym_fast = 1;
     }
     p->self_mode = k->self_term;
-    p->K = (k->family == NL_POLY || k->family == NL_KAPPA) ? k->K : 0;
+    p->K = (k->family == NL_POLY || k->family == NL_KAPPA || k->family == NL_PD_BOND) ? k->K : 0;
     if (k->fast_variant < NL_FAST_AUTO || k->fast_variant > NL_FAST_LEAFROWS) {
         nl_set_error("nl_plan_create: unknown fast variant %d", k->fast_variant);
         free(p);
@@ -473,6 +474,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     else
         p->sigma = k->scale * 2.0 * d * (d + 2.0 - k->alpha) / unit_sphere_measure(d);
     if (k->family == NL_POLY || k->family == NL_KAPPA) hermite_poly(p->K, k->alpha, p->poly);
+    if (k->family == NL_PD_BOND) hermite_poly(p->K, 3.0, p->poly);   // micromodulus ~ s^-3
     p->Rmax = Rmax;
     p->thr_max = (int)thr_max;
     p->const_horizon = 1;
@@ -750,7 +752,8 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32, p->leaf_multi,
                      p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux, p->selfQ,
                      p->fastFh32, p->sym_c64, p->sym_c32, p->sym_T, p->sym_G64, p->sym_G32,
-                     p->sym_diag, p->sym_D, p->sym_aux, p->runs, p->runs_woff, p->runs_wcnt };
+                     p->sym_diag, p->sym_D, p->sym_aux, p->runs, p->runs_woff, p->runs_wcnt,
+                     p->fpd_ir2 };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)

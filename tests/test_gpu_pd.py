@@ -84,3 +84,36 @@ def test_fast_pd_512_sampled_and_rejections():
     u2 = torch.zeros(2 * 48 * 48, dtype=torch.float32, device=DEV)
     with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
         nl.nl_apply_fast(p2, u2, torch.empty_like(u2))
+
+
+@pytest.mark.parametrize("K", [1, 2])
+@pytest.mark.parametrize("n,rho,variable", [(64, 8.0, False), (32, 3.0, True), (128, 6.0, True),
+                                            (8, 2.2, False)])
+def test_fast_pd_polynomial_micromodulus(K, n, rho, variable):
+    """The polynomial micromodulus p^{2K} (matched to s^-3 at the horizon) over the leaf set,
+    from exact 64-bit moments of o_x up to 2K + 2, against the oracle."""
+    L = int(np.log2(n))
+    f = synth.pd_2d(n=n, seed=n + 7, radius_cells=rho, nrhs=2)
+    delta = f["delta"]
+    if variable:
+        delta = delta * np.random.default_rng(n + K).uniform(0.6, 1.3, n * n)
+    plan = nl.nl_plan_create(2, n, delta, family=nl.NL_PD_BOND, coef=nl.NL_COEF_MEAN,
+                             a=f["c"], K=K)
+    got = run_fast(plan, f["u"])
+    ref = oracle.fast_pd_leafset(f["u"], 2, L, delta, f["c"], K=K)
+    assert rel_l2(got, ref) <= 2e-6, rel_l2(got, ref)
+
+
+def test_fast_pd_polynomial_512_sampled():
+    n, L, K = 512, 9, 2
+    f = synth.pd_2d(n=n, seed=3, radius_cells=8)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_PD_BOND, coef=nl.NL_COEF_MEAN,
+                             a=f["c"], K=K)
+    got = run_fast(plan, f["u"][0]).reshape(2, -1)
+    idx = np.concatenate([sample_idx(n * n, 1500, seed=4), boundary_idx(2, n, 10, 500, seed=5)])
+    ref = oracle.fast_pd_leafset(f["u"][0], 2, L, f["delta"], f["c"], K=K, idx=idx)
+    assert rel_l2(got[:, idx], ref) <= 2e-6
+    p3 = nl.nl_plan_create(2, 64, 0.1, family=nl.NL_PD_BOND, K=3)
+    u3 = torch.zeros(2 * 64 * 64, dtype=torch.float32, device=DEV)
+    with pytest.raises(nl.NlError, match="NL_EUNSUPPORTED"):
+        nl.nl_apply_fast(p3, u3, torch.empty_like(u3))

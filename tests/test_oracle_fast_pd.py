@@ -1,6 +1,9 @@
-"""Pins for the oracle of the degree-0 fast-path peridynamic operator: the bond tensor
-xi xi^T p(|xi|/delta)/delta^3 with p = 1, summed over the leaf set of Algorithm 1."""
+"""Pins for the oracle of the fast-path peridynamic operator: the bond tensor
+xi xi^T p(|xi|/delta)/delta^3, p = 1 (K = 0) or the polynomial p^{2K} matched to s^-3 at the
+horizon (K >= 1), summed over the leaf set of Algorithm 1."""
+import itertools
 import numpy as np
+import pytest
 
 import oracle
 from paper_1905_08375_gb300 import synth
@@ -91,3 +94,104 @@ def test_leaf_set_is_the_fast_scalar_set():
         if k != node and (a[0, 0] != 0 or b[1, 0] != 0):
             support += 1
     assert support == cnt[0] - 1
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_micromodulus_polynomial_matches_s_minus_3(K):
+    """p^{2K} agrees with s^-3 in value and first K derivatives at s = 1 (checked by
+    differentiating the polynomial and the power independently)."""
+    p = oracle.poly_coeffs(K, 3.0)
+    poly = np.polynomial.Polynomial(np.ravel(np.column_stack([p, np.zeros_like(p)]))[:2 * K + 1])
+    for j in range(K + 1):
+        want = np.prod([-3 - i for i in range(j)]) if j else 1.0       # d^j s^-3 at s = 1
+        assert abs(poly.deriv(j)(1.0) - want) < 1e-11 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_polynomial_continuum_limit(K):
+    """c = 1: u = (x^2, 0) tends to delta^-3 int_{B_delta} xi_x^4 p(|xi|/delta) =
+    (3 pi / 4) delta^3 sum_m p_m / (2m + 6), u = (x y, 0) (y-component) to
+    (pi / 4) delta^3 sum_m p_m / (2m + 6); first order in h (the rim cells of the leaf set)."""
+    delta = 0.25
+    p = oracle.poly_coeffs(K, 3.0)
+    rad = sum(p[m] / (2 * m + 6) for m in range(K + 1))
+    want1, want2 = 0.75 * np.pi * delta ** 3 * rad, 0.25 * np.pi * delta ** 3 * rad
+    errs = []
+    for L in (6, 7, 8):
+        n = 1 << L
+        X = synth.node_coords(2, n)
+        x, y = X[0].reshape(-1), X[1].reshape(-1)
+        c = np.ones(n * n)
+        node = np.array([(n // 2) * n + n // 2])
+        Lu = oracle.fast_pd_leafset(np.stack([x * x, 0 * x]), 2, L, delta, c, K=K, idx=node)
+        e1 = abs(Lu[0, 0] - want1) / abs(want1)
+        Lu = oracle.fast_pd_leafset(np.stack([x * y, 0 * x]), 2, L, delta, c, K=K, idx=node)
+        e2 = abs(Lu[1, 0] - want2) / abs(want2)
+        errs.append(max(e1, e2))
+    assert errs[-1] < 0.1
+    for k in (1, 2):
+        assert 0.35 < errs[k] / errs[k - 1] < 0.65, errs
+
+
+def _brute(u, n, delta, c, K):
+    """Plain numpy restatement on a tiny grid: every lattice cell k within the padded box,
+    kept when its cell meets the open ball of x_i, weight p(|xi|/delta_i)."""
+    h = 1.0 / n
+    p = oracle.poly_coeffs(K, 3.0)
+    out = np.zeros((2, n * n))
+    B = int(np.ceil(delta.max() * n)) + 1
+    for iy, ix in itertools.product(range(n), range(n)):
+        i = iy * n + ix
+        di = delta[i]
+        acc = np.zeros(2)
+        for oy, ox in itertools.product(range(-B, B + 1), repeat=2):
+            if ox == 0 and oy == 0:
+                continue
+            gx = max(abs(ox) - 0.5, 0.0) * h
+            gy = max(abs(oy) - 0.5, 0.0) * h
+            if not gx * gx + gy * gy < di * di:
+                continue
+            kx, ky = ix + ox, iy + oy
+            inside = 0 <= kx < n and 0 <= ky < n
+            k = ky * n + kx if inside else None
+            xi = np.array([ox * h, oy * h])
+            s2 = (xi @ xi) / di ** 2
+            w = sum(p[m] * s2 ** m for m in range(K + 1))
+            uk = u[:, k] if inside else np.zeros(2)
+            cik = 0.5 * (c[i] + (c[k] if inside else c[i]))
+            acc += cik * w * (xi @ (uk - u[:, i])) * xi / di ** 3
+        out[:, i] = h ** 2 * acc
+    return out
+
+
+@pytest.mark.parametrize("K", [0, 2])
+def test_matches_brute_force_on_a_tiny_grid(K):
+    n, L = 8, 3
+    rng = np.random.default_rng(11 + K)
+    delta = rng.uniform(1.3, 3.1, n * n) / n
+    c = rng.uniform(1.0, 10.0, n * n)
+    u = rng.standard_normal((2, n * n))
+    got = oracle.fast_pd_leafset(u, 2, L, delta, c, K=K)
+    want = _brute(u, n, delta, c, K)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_polynomial_rigid_motions_and_symmetry(K):
+    n, L = 8, 3
+    rng = np.random.default_rng(21 + K)
+    c = rng.uniform(1.0, 10.0, n * n)
+    N2 = 2 * n * n
+    A = np.zeros((N2, N2))
+    for k in range(N2):
+        e = np.zeros(N2)
+        e[k] = 1.0
+        A[:, k] = oracle.fast_pd_leafset(e.reshape(2, -1), 2, L, 2.5 / n, c, K=K).reshape(-1)
+    np.testing.assert_allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).max() < 1e-12 * np.abs(A).max()
+    X = synth.node_coords(2, n)
+    x, y = X[0].reshape(-1), X[1].reshape(-1)
+    inner = _interior(2, n, 3)
+    for u in (np.stack([np.full(n * n, 0.7), np.full(n * n, -1.3)]), np.stack([-0.4 * y, 0.4 * x])):
+        Lu = oracle.fast_pd_leafset(u, 2, L, 2.5 / n, c, K=K, idx=inner)
+        assert np.abs(Lu).max() < 1e-10
