@@ -1253,8 +1253,11 @@ __global__ void k_runs_warp_max(int64_t N, const int *__restrict__ cnt, int *__r
     if ((i & 31) == 0 && i < N) wcnt[i >> 5] = m;
 }
 
-// Step 3 from the stored runs: each lane adds the panels of its records, four records loaded
-// ahead; record r of the warp's nodes is one 128-byte line
+// Step 3 from the stored runs: each lane adds the panels of its records.  Software-pipelined
+// for latency: the next four records (one 128-byte line per record and warp) are requested
+// before the current four are used, and the first four panels of each of the current records
+// (runs are mostly that short) are requested together, so about twenty loads are in flight
+// per thread; longer runs finish in a loop.
 __global__ void __launch_bounds__(256) k_fast_gather_runs(FastI64Args a,
                                                           const unsigned *__restrict__ runs,
                                                           const int64_t *__restrict__ woff,
@@ -1269,23 +1272,31 @@ __global__ void __launch_bounds__(256) k_fast_gather_runs(FastI64Args a,
     const int cnt = wcnt[w];
     const long long *__restrict__ pyr = a.pyr;
     long long G = 0;
-    int r = 0;
-    for (; r + 4 <= cnt; r += 4) {
-        unsigned q[4];
+    unsigned q[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = __ldcs(rec + 32 * (int64_t)(r + k));
+    for (int k = 0; k < 4; ++k) q[k] = k < cnt ? __ldcs(rec + 32 * (int64_t)k) : 0u;
+    for (int r = 0; r < cnt; r += 4) {
+        unsigned qn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            qn[k] = r + 4 + k < cnt ? __ldcs(rec + 32 * (int64_t)(r + 4 + k)) : 0u;
+        long long v[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const long long *p = pyr + (q[k] & RUN_POS_MASK);
             const int len = (int)(q[k] >> RUN_POS_BITS);
-            for (int j = 0; j < len; ++j) G += __ldg(p + j);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[k][j] = j < len ? __ldg(p + j) : 0LL;
         }
-    }
-    for (; r < cnt; ++r) {
-        const unsigned q = __ldcs(rec + 32 * (int64_t)r);
-        const long long *p = pyr + (q & RUN_POS_MASK);
-        const int len = (int)(q >> RUN_POS_BITS);
-        for (int j = 0; j < len; ++j) G += __ldg(p + j);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long *p = pyr + (q[k] & RUN_POS_MASK);
+            const int len = (int)(q[k] >> RUN_POS_BITS);
+            for (int j = 4; j < len; ++j) G += __ldg(p + j);
+            G += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = qn[k];
     }
     if (i >= a.N) return;
     const int sh = fixed_shift_f32(a.N, a.mx);
@@ -1493,18 +1504,37 @@ __device__ __forceinline__ long long leaf_run(const long long *__restrict__ row,
     return __ldg(row + kb) - (ka > 0 ? __ldg(row + ka - 1) : 0LL);
 }
 
+// The rows of the ball at gaps t = 1 .. tmax (tmax = (floor(sqrt T4) + 1) / 2 exactly: (2t - 1)^2
+// <= T4 iff t <= tmax) in batches of four row pairs: the chords first, then all sixteen
+// prefix loads of the batch issued together (latency), then the differences.
 template <int D>
 __device__ __forceinline__ long long leaf_plane(const long long *__restrict__ plane, int n,
                                                 int X, int iy, int T4)
 {
-    if (D == 1) return leaf_run(plane, n, X, isqrt_fast(T4));
-    long long G = 0;
-    for (int t = 0;; ++t) {
-        const int e = t == 0 ? 0 : sq(2 * t - 1);
-        if (e > T4) break;
-        const int r = isqrt_fast(T4 - e);
-        if (iy + t < n) G += leaf_run(plane + (int64_t)n * (iy + t), n, X, r);
-        if (t > 0 && iy - t >= 0) G += leaf_run(plane + (int64_t)n * (iy - t), n, X, r);
+    const int r0 = isqrt_fast(T4);
+    if (D == 1) return leaf_run(plane, n, X, r0);
+    long long G = leaf_run(plane + (int64_t)n * iy, n, X, r0);
+    const int tmax = (r0 + 1) >> 1;
+    for (int t0 = 1; t0 <= tmax; t0 += 4) {
+        long long hi[4][2], lo[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int t = t0 + k;
+            const bool ok = t <= tmax;
+            const int r = ok ? isqrt_fast(T4 - sq(2 * t - 1)) : 0;
+            const int ka = max(0, -((r - X) >> 1) - 1);
+            const int kb = min(n - 1, (X + r) >> 1);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int y = s ? iy - t : iy + t;
+                const bool in = ok && y >= 0 && y < n;
+                const long long *row = plane + (int64_t)n * (in ? y : iy);
+                hi[k][s] = in ? __ldg(row + kb) : 0LL;
+                lo[k][s] = (in && ka > 0) ? __ldg(row + ka - 1) : 0LL;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) G += (hi[k][0] - lo[k][0]) + (hi[k][1] - lo[k][1]);
     }
     return G;
 }
