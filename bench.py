@@ -497,6 +497,10 @@ class C3(Workload):
         # like the horizon, the direct sum's like its square
         self.plan32 = nl.nl_plan_create(2, 512, 4.0 * f["delta"], family=nl.NL_PD_BOND,
                                         coef=nl.NL_COEF_MEAN, a=f["c"])
+        # the fast path with the polynomial micromodulus p^4 (K = 2) matched to s^-3
+        self.plan_k2 = nl.nl_plan_create(2, 512, f["delta"], family=nl.NL_PD_BOND,
+                                         coef=nl.NL_COEF_MEAN, a=f["c"], K=2)
+        self.out_k2 = torch.empty_like(self.u)
         self.units = 512 * 512
         self.launches = 1
         self.config = {"workload": "2D linear bond-based PD, 512x512, delta=8h, micromodulus "
@@ -513,12 +517,15 @@ class C3(Workload):
         o32 = self.torch.empty_like(self.u)
         t_d32 = self.time_fn(lambda: self.nl.nl_apply(self.plan32, self.u, o32), reps, flush)
         t_f32 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan32, self.u, o32), reps, flush)
+        t_k2 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan_k2, self.u, self.out_k2),
+                            reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, *fp32_peak())
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
         return roof, {"pd_fp32_ms": round(t, 4), "pd_fast_deg0_fp32_ms": round(t_f, 4),
                       "pd_delta32h_direct_fp32_ms": round(t_d32, 4),
                       "pd_delta32h_fast_deg0_fp32_ms": round(t_f32, 4),
+                      "pd_fast_poly_K2_fp32_ms": round(t_k2, 4),
                       "pd_fast_note": "nl_apply_fast on the PD plan: degree-0 bond tensor "
                                       "xi xi^T / delta^3 over the leaf set (a different "
                                       "operator), exact 64-bit leaf-row moment sums"}
@@ -540,14 +547,17 @@ class C3(Workload):
 
     def outputs(self):
         return {"pd": self.out.double().cpu().numpy().reshape(2, -1),
-                "pd_fast": self.out_f.double().cpu().numpy().reshape(2, -1)}
+                "pd_fast": self.out_f.double().cpu().numpy().reshape(2, -1),
+                "pd_fast_k2": self.out_k2.double().cpu().numpy().reshape(2, -1)}
 
     @staticmethod
     def oracle_step(f, n, idx):
         import oracle
         return {"pd": oracle.pd_direct(f["u"], 2, n, f["delta"], f["c"], idx=idx)[0],
                 "pd_fast": oracle.fast_pd_leafset(f["u"][0], 2, 9, f["delta"], f["c"],
-                                                  idx=idx)}, 2 * len(idx)
+                                                  idx=idx),
+                "pd_fast_k2": oracle.fast_pd_leafset(f["u"][0], 2, 9, f["delta"], f["c"], K=2,
+                                                     idx=idx)}, 2 * len(idx)
 
 
 class C3B(Workload):

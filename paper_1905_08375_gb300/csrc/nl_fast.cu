@@ -1112,26 +1112,44 @@ __global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels_lane(FastI64A
 
 // ---------------------------------------------------------------------------
 // Step 1 stored (the decomposition of Algorithm 1 as set-up data, as the paper's timings
-// treat it): each node's panels, in the order level, panel row, left part, right part, as
-// runs of consecutive panels of one row, one 32-bit record per run: the run's first panel as
-// a position in the pyramid buffer (27 bits) and its length (5 bits, 1..31; longer runs are
-// split; 0 = no run).  Records are stored warp-interleaved, record r of node 32 w + l at
-// runs[woff[w] + 32 r + l], so a warp reads 128 contiguous bytes per record; wcnt[w] is the
-// largest record count of the warp's nodes.  Step 3 then adds the panels of every record.
+// treat it), warp-aligned.  The 32 nodes of a warp share their row (n >= 32) or the single
+// row (1-D); the warp walks the union of its nodes' levels and panel rows, and every (level,
+// panel row, side) of that walk in which some node has panels is one slot: the warp's
+// smallest first-panel position in the pyramid buffer (32 bits, one per warp and slot) and,
+// per node, a 16-bit record (offset from that position: low byte; number of consecutive
+// panels: high byte; 0 = none).  In a slot the nodes' panels are adjacent or shared, so a
+// warp's loads of a slot touch few sectors.  Layout per warp w, from slot offset woff[w]:
+// base[woff + s], rec[(woff + s) * 32 + lane], s < wslots[w].
 // ---------------------------------------------------------------------------
-constexpr int RUN_POS_BITS = 27;
-constexpr unsigned RUN_POS_MASK = (1u << RUN_POS_BITS) - 1u;
-constexpr int RUN_MAX_LEN = 31;
+struct SlotArgs {
+    int n, L;
+    int64_t N;
+    const int *thr4;
+    int64_t lvl_off[NL_MAX_LEVELS + 2];
+};
 
-// calls f(position in the pyramid, length) for every run of node (ix, iy) (1-D or 2-D); ch is
-// this thread's column of a shared-memory chord table (stride GP_THREADS)
-template <int D, typename F>
-__device__ __forceinline__ void visit_runs(int n, int L, const int64_t *lvl_off, int ix, int iy,
-                                           int T4, int *ch, F &&f)
+template <int D, bool WRITE>
+__global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restrict__ wslots,
+                                                      const int64_t *__restrict__ woff,
+                                                      unsigned *__restrict__ base,
+                                                      unsigned short *__restrict__ rec,
+                                                      int *__restrict__ bad)
 {
+    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
+    const int64_t i0 = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
+    const int64_t w = i0 >> 5;
+    if ((w << 5) >= a.N) return;                      // whole warps only
+    const int lane = threadIdx.x & 31;
+    const bool act = i0 < a.N;
+    const int64_t i = act ? i0 : a.N - 1;
+    const int n = a.n, L = a.L;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)(i / n) : 0;
     const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
     const int r0 = isqrt_fast(T4);
     const int tmax = (r0 + 1) >> 1;
+    int *ch = s_ch + threadIdx.x;
     if (D > 1) {
         const int tc = min(tmax, GP_CHORDS - 1);
         ch[0] = r0;
@@ -1141,17 +1159,13 @@ __device__ __forceinline__ void visit_runs(int n, int L, const int64_t *lvl_off,
         if (D == 1) return r0;
         return t < GP_CHORDS ? ch[t * GP_THREADS] : isqrt_fast(T4 - sq(2 * t - 1));
     };
-    auto emit = [&](int64_t pos, int len) {
-        while (len > 0) {
-            const int m = min(len, RUN_MAX_LEN);
-            f(pos, m);
-            pos += m;
-            len -= m;
-        }
-    };
     int lmin = 0;
     while (lmin < L && (1 << (L - lmin + 1)) > 2 * r0) ++lmin;
-    for (int l = lmin; l <= L; ++l) {
+    const int lmin_w = __reduce_min_sync(0xffffffffu, lmin);
+    const int tmax_w = __reduce_max_sync(0xffffffffu, tmax);
+    const int64_t off = WRITE ? woff[w] : 0;
+    int slot = 0, fault = 0;
+    for (int l = lmin_w; l <= L; ++l) {
         const int np = 1 << l;
         const int lg = L - l;
         const int shf = lg + 1;
@@ -1159,144 +1173,123 @@ __device__ __forceinline__ void visit_runs(int n, int L, const int64_t *lvl_off,
         int ylo = 0, yhi = 0;
         if (D > 1) {
             if (leaf) {
-                ylo = max(0, iy - tmax);
-                yhi = min(n - 1, iy + tmax);
+                ylo = max(0, iy - tmax_w);
+                yhi = min(n - 1, iy + tmax_w);
             } else {
-                ylo = max(0, -((tmax - 1 - iy) >> lg));
-                yhi = min(np - 1, ((iy + tmax) >> lg) - 1);
+                ylo = max(0, -((tmax_w - 1 - iy) >> lg));
+                yhi = min(np - 1, ((iy + tmax_w) >> lg) - 1);
             }
         }
         int pm = -1, ppa = 1, ppb = 0;
         for (int ky = ylo; ky <= yhi; ++ky) {
-            int r;
-            if (D == 1) r = r0;
-            else if (leaf) r = chord(ky > iy ? ky - iy : iy - ky);
-            else r = chord(max(gap_t(ky << lg, iy), gap_t((ky + 1) << lg, iy)));
-            int ka, kb;
-            if (leaf) {
-                ka = max(0, -((r - X) >> 1) - 1);
-                kb = min(n - 1, (X + r) >> 1);
-            } else {
-                ka = max(0, -((r - X) >> shf));
-                kb = min(np - 1, ((X + r) >> shf) - 1);
+            int t = 0;
+            if (D > 1)
+                t = leaf ? (ky > iy ? ky - iy : iy - ky)
+                         : max(gap_t(ky << lg, iy), gap_t((ky + 1) << lg, iy));
+            int ka = 1, kb = 0;
+            if (act && l >= lmin && t <= tmax) {
+                const int r = chord(t);
+                if (leaf) {
+                    ka = max(0, -((r - X) >> 1) - 1);
+                    kb = min(n - 1, (X + r) >> 1);
+                } else {
+                    ka = max(0, -((r - X) >> shf));
+                    kb = min(np - 1, ((X + r) >> shf) - 1);
+                }
             }
-            if (ka > kb) continue;
-            if (l > lmin && (ky >> 1) != pm) {
+            if (l > lmin_w && (ky >> 1) != pm) {
                 pm = ky >> 1;
                 ppa = 1; ppb = 0;
                 int tp = 0;
                 if (D > 1) tp = max(gap_t(pm << (lg + 1), iy), gap_t((pm + 1) << (lg + 1), iy));
-                if (tp <= tmax) {
+                if (act && l > lmin && tp <= tmax) {
                     const int rp = chord(tp);
                     const int qa = max(0, -((rp - X) >> (shf + 1)));
                     const int qb = min((np >> 1) - 1, ((X + rp) >> (shf + 1)) - 1);
                     if (qa <= qb) { ppa = 2 * qa; ppb = 2 * qb + 1; }
                 }
             }
-            const int64_t base = lvl_off[l] + (int64_t)np * ky;
-            if (ppa <= ppb) {
-                emit(base + ka, min(kb, ppa - 1) - ka + 1);
-                const int a2 = max(ka, ppb + 1);
-                emit(base + a2, kb - a2 + 1);
-            } else {
-                emit(base + ka, kb - ka + 1);
+            const bool split = ppa <= ppb;
+            const int b1 = split ? min(kb, ppa - 1) : kb;
+            const int a2 = split ? max(ka, ppb + 1) : kb + 1;
+            const int len[2] = { max(0, b1 - ka + 1), max(0, kb - a2 + 1) };
+            const int st[2] = { ka, a2 };
+            const int64_t rowpos = a.lvl_off[l] + (int64_t)np * ky;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const unsigned pos = len[side] > 0 ? (unsigned)(rowpos + st[side]) : 0xffffffffu;
+                const unsigned bmin = __reduce_min_sync(0xffffffffu, pos);
+                if (bmin == 0xffffffffu) continue;           // no node of the warp: no slot
+                if (WRITE) {
+                    unsigned short r = 0;
+                    if (len[side] > 0) {
+                        const unsigned dlt = pos - bmin;
+                        if (dlt > 255u || len[side] > 255) fault = 1;
+                        r = (unsigned short)((dlt & 255u) | ((unsigned)min(len[side], 255) << 8));
+                    }
+                    rec[(off + slot) * 32 + lane] = r;
+                    if (lane == 0) base[off + slot] = bmin;
+                }
+                ++slot;
             }
         }
     }
+    if (!WRITE && lane == 0) wslots[w] = slot;
+    if (WRITE && fault) atomicExch(bad, 1);
 }
 
-struct RunArgs {
-    int n, L;
-    int64_t N;
-    const int *thr4;
-    int64_t lvl_off[NL_MAX_LEVELS + 2];
-};
-
-template <int D>
-__global__ void __launch_bounds__(GP_THREADS) k_runs_count(RunArgs a, int *__restrict__ cnt)
-{
-    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
-    const int64_t i = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
-    if (i >= a.N) return;
-    const int ix = (int)(i % a.n), iy = D > 1 ? (int)(i / a.n) : 0;
-    int c = 0;
-    visit_runs<D>(a.n, a.L, a.lvl_off, ix, iy, a.thr4[i], s_ch + threadIdx.x,
-                  [&](int64_t, int) { ++c; });
-    cnt[i] = c;
-}
-
-template <int D>
-__global__ void __launch_bounds__(GP_THREADS) k_runs_write(RunArgs a, const int64_t *__restrict__ woff,
-                                                           const int *__restrict__ wcnt,
-                                                           unsigned *__restrict__ runs)
-{
-    __shared__ int s_ch[GP_CHORDS * GP_THREADS];
-    const int64_t i = blockIdx.x * (int64_t)GP_THREADS + threadIdx.x;
-    if (i >= a.N) return;
-    const int ix = (int)(i % a.n), iy = D > 1 ? (int)(i / a.n) : 0;
-    const int64_t w = i >> 5;
-    unsigned *out = runs + woff[w] + (i & 31);
-    int c = 0;
-    visit_runs<D>(a.n, a.L, a.lvl_off, ix, iy, a.thr4[i], s_ch + threadIdx.x,
-                  [&](int64_t pos, int len) {
-                      out[32 * (int64_t)c] = (unsigned)pos | ((unsigned)len << RUN_POS_BITS);
-                      ++c;
-                  });
-    for (; c < wcnt[w]; ++c) out[32 * (int64_t)c] = 0u;
-}
-
-__global__ void k_runs_warp_max(int64_t N, const int *__restrict__ cnt, int *__restrict__ wcnt)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int c = i < N ? cnt[i] : 0;
-    const int m = __reduce_max_sync(0xffffffffu, c);
-    if ((i & 31) == 0 && i < N) wcnt[i >> 5] = m;
-}
-
-// Step 3 from the stored runs: each lane adds the panels of its records.  Software-pipelined
-// for latency: the next four records (one 128-byte line per record and warp) are requested
-// before the current four are used, and the first four panels of each of the current records
-// (runs are mostly that short) are requested together, so about twenty loads are in flight
-// per thread; longer runs finish in a loop.
-__global__ void __launch_bounds__(256) k_fast_gather_runs(FastI64Args a,
-                                                          const unsigned *__restrict__ runs,
-                                                          const int64_t *__restrict__ woff,
-                                                          const int *__restrict__ wcnt,
-                                                          const float *__restrict__ u,
-                                                          float *__restrict__ Lu)
+// Step 3 from the stored slots: per slot one broadcast load of the warp's base, one 16-bit
+// record per node, and the node's panels (the first four requested together, longer runs in
+// a loop); the next four slots are requested before the current ones are used.
+__global__ void __launch_bounds__(256) k_fast_gather_slots(FastI64Args a,
+                                                           const unsigned *__restrict__ base,
+                                                           const unsigned short *__restrict__ rec,
+                                                           const int64_t *__restrict__ woff,
+                                                           const int *__restrict__ wslots,
+                                                           const float *__restrict__ u,
+                                                           float *__restrict__ Lu)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t w = i >> 5;
-    if ((w << 5) >= a.N) return;                      // whole warps only
-    const unsigned *__restrict__ rec = runs + woff[w] + (i & 31);
-    const int cnt = wcnt[w];
+    if ((w << 5) >= a.N) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t off = woff[w];
+    const int ns = wslots[w];
     const long long *__restrict__ pyr = a.pyr;
     long long G = 0;
-    unsigned q[4];
+    unsigned b[4];
+    unsigned short q[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = k < cnt ? __ldcs(rec + 32 * (int64_t)k) : 0u;
-    for (int r = 0; r < cnt; r += 4) {
-        unsigned qn[4];
+    for (int k = 0; k < 4; ++k) {
+        b[k] = k < ns ? __ldg(base + off + k) : 0u;
+        q[k] = k < ns ? __ldcs(rec + (off + k) * 32 + lane) : (unsigned short)0;
+    }
+    for (int s = 0; s < ns; s += 4) {
+        unsigned bn[4];
+        unsigned short qn[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            qn[k] = r + 4 + k < cnt ? __ldcs(rec + 32 * (int64_t)(r + 4 + k)) : 0u;
+        for (int k = 0; k < 4; ++k) {
+            const int t = s + 4 + k;
+            bn[k] = t < ns ? __ldg(base + off + t) : 0u;
+            qn[k] = t < ns ? __ldcs(rec + (off + t) * 32 + lane) : (unsigned short)0;
+        }
         long long v[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + (q[k] & RUN_POS_MASK);
-            const int len = (int)(q[k] >> RUN_POS_BITS);
+            const long long *p = pyr + b[k] + (q[k] & 255u);
+            const int len = q[k] >> 8;
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[k][j] = j < len ? __ldg(p + j) : 0LL;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + (q[k] & RUN_POS_MASK);
-            const int len = (int)(q[k] >> RUN_POS_BITS);
+            const long long *p = pyr + b[k] + (q[k] & 255u);
+            const int len = q[k] >> 8;
             for (int j = 4; j < len; ++j) G += __ldg(p + j);
             G += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = qn[k];
+        for (int k = 0; k < 4; ++k) { b[k] = bn[k]; q[k] = qn[k]; }
     }
     if (i >= a.N) return;
     const int sh = fixed_shift_f32(a.N, a.mx);
@@ -1667,65 +1660,72 @@ static int moments_count(int d, int K)
     return M;
 }
 
-// Step 1 at plan time for the panel-by-panel route (1-D, and 2-D with n >= 32): count every
-// node's runs, take the per-warp maxima and offsets on the host, write the records.  Skipped
-// (the gather then enumerates the decomposition itself) when the pyramid positions need more
-// than 27 bits or the records would exceed 2^28 (1 GiB).
-static nl_status build_runs(nl_plan *p, cudaStream_t st)
+// Step 1 at plan time for the panel-by-panel route (1-D with n >= 32, and 2-D with n >= 32):
+// count every warp's slots, offsets on the host, write the slots.  Skipped (the gather then
+// enumerates the decomposition itself) when pyramid positions need more than 32 bits, the
+// slots would exceed 2^23 (about 570 MB), or a node's offset or run length leaves its byte.
+static nl_status build_slots(nl_plan *p, cudaStream_t st)
 {
     const int64_t N = p->N;
-    if (p->lvl_off[p->L] + N > (int64_t)RUN_POS_MASK) return NL_OK;
-    RunArgs ra;
-    ra.n = p->n; ra.L = p->L; ra.N = N; ra.thr4 = p->thr4;
-    for (int l = 0; l <= p->L; ++l) ra.lvl_off[l] = p->lvl_off[l];
+    if (p->lvl_off[p->L] + N >= (int64_t)0xffffffffu) return NL_OK;
+    SlotArgs sa;
+    sa.n = p->n; sa.L = p->L; sa.N = N; sa.thr4 = p->thr4;
+    for (int l = 0; l <= p->L; ++l) sa.lvl_off[l] = p->lvl_off[l];
     const int64_t nw = (N + 31) / 32;
-    int *cnt = nullptr, *wcnt = nullptr;
+    int *wslots = nullptr, *bad = nullptr;
     int64_t *woff = nullptr;
-    unsigned *runs = nullptr;
+    unsigned *base = nullptr;
+    unsigned short *rec = nullptr;
     auto fail = [&](nl_status s) {
-        if (cnt) cudaFree(cnt);
-        if (wcnt) cudaFree(wcnt);
+        if (wslots) cudaFree(wslots);
+        if (bad) cudaFree(bad);
         if (woff) cudaFree(woff);
-        if (runs) cudaFree(runs);
+        if (base) cudaFree(base);
+        if (rec) cudaFree(rec);
         return s;
     };
-    if (cudaMalloc(&cnt, N * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&wcnt, nw * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&woff, nw * sizeof(int64_t)) != cudaSuccess) {
+    if (cudaMalloc(&wslots, nw * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&woff, nw * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&bad, sizeof(int)) != cudaSuccess) {
         nl_set_error("nl_plan_create: allocation for the stored decomposition failed");
         return fail(NL_ENOMEM);
     }
-    const unsigned g = (unsigned)((N + GP_THREADS - 1) / GP_THREADS);
-    if (p->d == 1) k_runs_count<1><<<g, GP_THREADS, 0, st>>>(ra, cnt);
-    else k_runs_count<2><<<g, GP_THREADS, 0, st>>>(ra, cnt);
-    k_runs_warp_max<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, cnt, wcnt);
+    const unsigned g = (unsigned)((nw * 32 + GP_THREADS - 1) / GP_THREADS);
+    if (p->d == 1) k_slots<1, false><<<g, GP_THREADS, 0, st>>>(sa, wslots, woff, base, rec, bad);
+    else k_slots<2, false><<<g, GP_THREADS, 0, st>>>(sa, wslots, woff, base, rec, bad);
     std::vector<int> hw(nw);
     std::vector<int64_t> ho(nw);
-    cudaError_t ce = cudaMemcpyAsync(hw.data(), wcnt, nw * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t ce = cudaMemcpyAsync(hw.data(), wslots, nw * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (counts)"));
     int64_t tot = 0;
-    for (int64_t w = 0; w < nw; ++w) { ho[w] = tot; tot += 32 * (int64_t)hw[w]; }
-    if (tot > ((int64_t)1 << 28)) return fail(NL_OK);
-    if (cudaMalloc(&runs, std::max<int64_t>(tot, 1) * sizeof(unsigned)) != cudaSuccess) {
-        nl_set_error("nl_plan_create: allocation of %lld run records failed", (long long)tot);
+    for (int64_t w = 0; w < nw; ++w) { ho[w] = tot; tot += hw[w]; }
+    if (tot > ((int64_t)1 << 23)) return fail(NL_OK);
+    if (cudaMalloc(&base, std::max<int64_t>(tot, 1) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&rec, std::max<int64_t>(tot, 1) * 32 * sizeof(unsigned short)) != cudaSuccess) {
+        nl_set_error("nl_plan_create: allocation of %lld decomposition slots failed", (long long)tot);
         return fail(NL_ENOMEM);
     }
-    ce = cudaMemsetAsync(runs, 0, std::max<int64_t>(tot, 1) * sizeof(unsigned), st);
+    ce = cudaMemsetAsync(bad, 0, sizeof(int), st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(woff, ho.data(), nw * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (offsets)"));
-    if (p->d == 1) k_runs_write<1><<<g, GP_THREADS, 0, st>>>(ra, woff, wcnt, runs);
-    else k_runs_write<2><<<g, GP_THREADS, 0, st>>>(ra, woff, wcnt, runs);
+    if (p->d == 1) k_slots<1, true><<<g, GP_THREADS, 0, st>>>(sa, wslots, woff, base, rec, bad);
+    else k_slots<2, true><<<g, GP_THREADS, 0, st>>>(sa, wslots, woff, base, rec, bad);
+    int hb = 0;
     ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (records)"));
-    cudaFree(cnt);
-    p->runs = runs;
-    p->runs_woff = woff;
-    p->runs_wcnt = wcnt;
-    p->runs_records = (size_t)tot;
-    p->device_bytes += (size_t)tot * sizeof(unsigned) + nw * (sizeof(int) + sizeof(int64_t));
+    if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (slots)"));
+    if (hb) return fail(NL_OK);
+    cudaFree(bad);
+    p->slot_base = base;
+    p->slot_rec = rec;
+    p->slot_woff = woff;
+    p->slot_count = wslots;
+    p->slots = (size_t)tot;
+    p->device_bytes += (size_t)tot * (sizeof(unsigned) + 32 * sizeof(unsigned short)) +
+                       nw * (sizeof(int) + sizeof(int64_t));
     return NL_OK;
 }
 
@@ -1827,8 +1827,8 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     NL_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_pc);
     p->device_bytes -= 8 * sizeof(double);
-    if (K == 0 && p->fast_variant == NL_FAST_PANELS && d <= 2 && (d == 1 || p->n >= 32))
-        return build_runs(p, st);
+    if (K == 0 && p->fast_variant == NL_FAST_PANELS && d <= 2 && p->n >= 32)
+        return build_slots(p, st);
     return NL_OK;
 }
 
@@ -1959,9 +1959,10 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         else k_fast_gather_rowprefix<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     } else {
         const unsigned gp = (unsigned)((p->N + GP_THREADS - 1) / GP_THREADS);
-        if (p->runs) {
+        if (p->slot_base) {
             const unsigned gr = (unsigned)(((p->N + 31) / 32 * 32 + 255) / 256);
-            k_fast_gather_runs<<<gr, 256, 0, st>>>(a, p->runs, p->runs_woff, p->runs_wcnt, u, Lu);
+            k_fast_gather_slots<<<gr, 256, 0, st>>>(a, p->slot_base, p->slot_rec, p->slot_woff,
+                                                     p->slot_count, u, Lu);
         } else if (d == 1) k_fast_gather_panels_lane<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else if (d == 2 && p->n >= 32) k_fast_gather_panels<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_panels_lane<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);

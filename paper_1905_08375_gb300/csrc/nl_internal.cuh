@@ -129,10 +129,11 @@ struct nl_plan {
                                     // apply (fixed-point scale), word 1 a block ticket, then
                                     // NL_FAST_PARTS per-block maxima (floats, from byte 16)
     float fast_bmax;                // FP32 integer route: max |b| (bounds |u b| by max |u|)
-    unsigned *runs;                 // NL_FAST_PANELS, 1-D/2-D: the stored decomposition as
-    int64_t *runs_woff;             // runs of consecutive panels (warp-interleaved records),
-    int *runs_wcnt;                 // per-warp record offsets and counts
-    size_t runs_records;
+    unsigned *slot_base;            // NL_FAST_PANELS, 1-D/2-D with n >= 32: the stored
+    unsigned short *slot_rec;       // decomposition, warp-aligned slots (per-warp base
+    int64_t *slot_woff;             // positions, per-node 16-bit records), per-warp slot
+    int *slot_count;                // offsets and counts
+    size_t slots;
     double *selfQ;                  // FP32 integer route: selfS / h^d and (float) fastF h^d
     float *fastFh32;
     long long *leaf_multi;          // leaf-row prefixes of several right-hand sides (grown on
