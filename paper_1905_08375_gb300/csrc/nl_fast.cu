@@ -1115,12 +1115,16 @@ __global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels_lane(FastI64A
 // treat it), warp-aligned.  The 32 nodes of a warp share their row (n >= 32) or the single
 // row (1-D); the warp walks the union of its nodes' levels and panel rows, and every (level,
 // panel row, side) of that walk in which some node has panels is one slot: the warp's
-// smallest first-panel position in the pyramid buffer (32 bits, one per warp and slot) and,
+// smallest first-panel position in the pyramid buffer (27 bits, with the slot's longest run
+// in the top five, one word per warp and slot) and,
 // per node, a 16-bit record (offset from that position: low byte; number of consecutive
 // panels: high byte; 0 = none).  In a slot the nodes' panels are adjacent or shared, so a
 // warp's loads of a slot touch few sectors.  Layout per warp w, from slot offset woff[w]:
 // base[woff + s], rec[(woff + s) * 32 + lane], s < wslots[w].
 // ---------------------------------------------------------------------------
+constexpr int SLOT_POS_BITS = 27;              // base word: position | (longest run << 27)
+constexpr unsigned SLOT_POS_MASK = (1u << SLOT_POS_BITS) - 1u;
+
 struct SlotArgs {
     int n, L;
     int64_t N;
@@ -1220,6 +1224,7 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
                 const unsigned pos = len[side] > 0 ? (unsigned)(rowpos + st[side]) : 0xffffffffu;
                 const unsigned bmin = __reduce_min_sync(0xffffffffu, pos);
                 if (bmin == 0xffffffffu) continue;           // no node of the warp: no slot
+                const int lmax = __reduce_max_sync(0xffffffffu, len[side]);
                 if (WRITE) {
                     unsigned short r = 0;
                     if (len[side] > 0) {
@@ -1228,7 +1233,9 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
                         r = (unsigned short)((dlt & 255u) | ((unsigned)min(len[side], 255) << 8));
                     }
                     rec[(off + slot) * 32 + lane] = r;
-                    if (lane == 0) base[off + slot] = bmin;
+                    // the slot's longest run (capped at 31) in the top five bits of the base
+                    if (lane == 0)
+                        base[off + slot] = bmin | ((unsigned)min(lmax, 31) << SLOT_POS_BITS);
                 }
                 ++slot;
             }
@@ -1276,14 +1283,15 @@ __global__ void __launch_bounds__(256) k_fast_gather_slots(FastI64Args a,
         long long v[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + b[k] + (q[k] & 255u);
+            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
             const int len = q[k] >> 8;
+            const int m = (int)(b[k] >> SLOT_POS_BITS);      // the warp's longest run (<= 31)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[k][j] = j < len ? __ldg(p + j) : 0LL;
+            for (int j = 0; j < 4; ++j) v[k][j] = (j < m && j < len) ? __ldg(p + j) : 0LL;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + b[k] + (q[k] & 255u);
+            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
             const int len = q[k] >> 8;
             for (int j = 4; j < len; ++j) G += __ldg(p + j);
             G += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
@@ -1497,37 +1505,18 @@ __device__ __forceinline__ long long leaf_run(const long long *__restrict__ row,
     return __ldg(row + kb) - (ka > 0 ? __ldg(row + ka - 1) : 0LL);
 }
 
-// The rows of the ball at gaps t = 1 .. tmax (tmax = (floor(sqrt T4) + 1) / 2 exactly: (2t - 1)^2
-// <= T4 iff t <= tmax) in batches of four row pairs: the chords first, then all sixteen
-// prefix loads of the batch issued together (latency), then the differences.
 template <int D>
 __device__ __forceinline__ long long leaf_plane(const long long *__restrict__ plane, int n,
                                                 int X, int iy, int T4)
 {
-    const int r0 = isqrt_fast(T4);
-    if (D == 1) return leaf_run(plane, n, X, r0);
-    long long G = leaf_run(plane + (int64_t)n * iy, n, X, r0);
-    const int tmax = (r0 + 1) >> 1;
-    for (int t0 = 1; t0 <= tmax; t0 += 4) {
-        long long hi[4][2], lo[4][2];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = t0 + k;
-            const bool ok = t <= tmax;
-            const int r = ok ? isqrt_fast(T4 - sq(2 * t - 1)) : 0;
-            const int ka = max(0, -((r - X) >> 1) - 1);
-            const int kb = min(n - 1, (X + r) >> 1);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int y = s ? iy - t : iy + t;
-                const bool in = ok && y >= 0 && y < n;
-                const long long *row = plane + (int64_t)n * (in ? y : iy);
-                hi[k][s] = in ? __ldg(row + kb) : 0LL;
-                lo[k][s] = (in && ka > 0) ? __ldg(row + ka - 1) : 0LL;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) G += (hi[k][0] - lo[k][0]) + (hi[k][1] - lo[k][1]);
+    if (D == 1) return leaf_run(plane, n, X, isqrt_fast(T4));
+    long long G = 0;
+    for (int t = 0;; ++t) {
+        const int e = t == 0 ? 0 : sq(2 * t - 1);
+        if (e > T4) break;
+        const int r = isqrt_fast(T4 - e);
+        if (iy + t < n) G += leaf_run(plane + (int64_t)n * (iy + t), n, X, r);
+        if (t > 0 && iy - t >= 0) G += leaf_run(plane + (int64_t)n * (iy - t), n, X, r);
     }
     return G;
 }
@@ -1662,12 +1651,12 @@ static int moments_count(int d, int K)
 
 // Step 1 at plan time for the panel-by-panel route (1-D with n >= 32, and 2-D with n >= 32):
 // count every warp's slots, offsets on the host, write the slots.  Skipped (the gather then
-// enumerates the decomposition itself) when pyramid positions need more than 32 bits, the
+// enumerates the decomposition itself) when pyramid positions need more than 27 bits, the
 // slots would exceed 2^23 (about 570 MB), or a node's offset or run length leaves its byte.
 static nl_status build_slots(nl_plan *p, cudaStream_t st)
 {
     const int64_t N = p->N;
-    if (p->lvl_off[p->L] + N >= (int64_t)0xffffffffu) return NL_OK;
+    if (p->lvl_off[p->L] + N >= (int64_t)SLOT_POS_MASK) return NL_OK;
     SlotArgs sa;
     sa.n = p->n; sa.L = p->L; sa.N = N; sa.thr4 = p->thr4;
     for (int l = 0; l <= p->L; ++l) sa.lvl_off[l] = p->lvl_off[l];
