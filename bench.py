@@ -241,6 +241,9 @@ class C2(Workload):
                                     fast_variant=getattr(nl, const))
             for name, const, _ in self.ROUTES}
         self.fast = self.fast_routes[self.STEP_ROUTE]
+        # the symmetrised (divergence-type) fast operator on the same fields (f4)
+        self.fast_sym = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
+                                          coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
         self.u = torch.tensor(f["u"][0], dtype=torch.float32, device=self.dev)
         self.out_d = torch.empty_like(self.u)
         self.out_f = torch.empty_like(self.u)
@@ -295,6 +298,13 @@ class C2(Workload):
         per["fast_gpts"] = routes[self.STEP_ROUTE]["gpts"]
         per["fast_hbm_bytes_per_node"] = (f"{self.FAST_BYTES_PER_NODE} (u 4, b 4, out 4, plan "
                                           "4, pyramid 8 written + 8 read, coarse levels 1/3)")
+        o_sym = self.torch.empty_like(self.u)
+        t_sym = self.time_fn(lambda: nl.nl_apply_fast(self.fast_sym, self.u, o_sym),
+                             min(reps, 20), flush)
+        per["fast_sym_fp32_ms"] = round(t_sym, 4)
+        per["fast_sym_note"] = ("symmetrised leaf-set operator (K = 0): one-sided fast apply "
+                                "(leaf rows) + transpose scatter into per-row difference "
+                                "arrays with 64-bit integer atomics + row prefix sums")
         # FP64 data: the direct sum in FP64 and the fast apply with FP64 panel sums
         t_d64 = self.time_fn(lambda: nl.nl_apply(self.direct, self.u64, self.out_d64),
                              min(reps, 10), flush)

@@ -508,21 +508,37 @@ __device__ __forceinline__ void x2_load_grp(X2Grp &g, const float *cu, int plane
     }
 }
 
+// Per-output weights of the kappa part of the splitting (Sec. 3) on the paired-column tile,
+// K <= 1: w = ra g(o) - p0 - p1 |o|^2 / R2 = fma(ra, g, fma(bk, |o|^2, c0)), ra = R^alpha,
+// bk = -p1 / R2 per output (the column pair), c0 = -p0.  KAP = false: w = g (NL_POWER).
+struct X2Kap { f2_t ra[RB_P], bk[RB_P], c0; };
+
+template <bool KAP>
+__device__ __forceinline__ f2_t x2_w(const X2Kap &kp, int p, f2_t gg, float o2)
+{
+    if (!KAP) return gg;
+    return f2_fma(kp.ra[p], gg, f2_fma(kp.bk[p], f2_pack(o2, o2), kp.c0));
+}
+
 // rows oy .. oy + 3 (weights g4) for the RB_P (= 8) outputs; the window is (G0, G1) = rows
 // oy .. oy + 7 and G2 holds rows oy + 8 .. oy + 11; every output is inside its ball
+template <bool KAP = false>
 __device__ __forceinline__ void x2_core4(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
                                          const X2Grp &G0, const X2Grp &G1, const X2Grp &G2,
-                                         const float (&g4)[4])
+                                         const float (&g4)[4], const X2Kap &kp, float o2base,
+                                         int oy)
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float g = g4[j];
         const f2_t gg = f2_pack(g, g);
+        const float o2 = KAP ? o2base + (float)((oy + j) * (oy + j)) : 0.f;
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
             const int k = p + j;
             const X2Grp &G = k < 4 ? G0 : (k < 8 ? G1 : G2);
-            acc[p] = f2_fma(f2_mul(G.b[k & 3], gg), f2_sub(G.u[k & 3], ui[p]), acc[p]);
+            acc[p] = f2_fma(f2_mul(G.b[k & 3], x2_w<KAP>(kp, p, gg, o2)),
+                            f2_sub(G.u[k & 3], ui[p]), acc[p]);
         }
     }
 }
@@ -532,16 +548,24 @@ struct X2Thr { int a[RB_P], b[RB_P]; };
 
 // one row (offset oy) for the RB_P outputs from the window (G0, G1); MASK: outputs whose ball
 // does not hold the offset get weight 0
-template <bool MASK>
+template <bool MASK, bool KAP = false>
 __device__ __forceinline__ void x2_row(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
                                        const X2Grp &G0, const X2Grp &G1,
-                                       const X2Thr &thr2, float g, int o2)
+                                       const X2Thr &thr2, float g, int o2, const X2Kap &kp)
 {
 #pragma unroll
     for (int p = 0; p < RB_P; ++p) {
         const X2Grp &G = p < 4 ? G0 : G1;
-        const f2_t gm = MASK ? f2_pack(o2 <= thr2.a[p] ? g : 0.f, o2 <= thr2.b[p] ? g : 0.f)
-                             : f2_pack(g, g);
+        f2_t gm;
+        if (KAP) {
+            float wa, wb;
+            f2_unpack(x2_w<true>(kp, p, f2_pack(g, g), (float)o2), wa, wb);
+            gm = MASK ? f2_pack(o2 <= thr2.a[p] ? wa : 0.f, o2 <= thr2.b[p] ? wb : 0.f)
+                      : f2_pack(wa, wb);
+        } else {
+            gm = MASK ? f2_pack(o2 <= thr2.a[p] ? g : 0.f, o2 <= thr2.b[p] ? g : 0.f)
+                      : f2_pack(g, g);
+        }
         acc[p] = f2_fma(f2_mul(G.b[p & 3], gm), f2_sub(G.u[p & 3], ui[p]), acc[p]);
     }
 }
@@ -566,9 +590,11 @@ __device__ __forceinline__ void x2_slide(X2Grp &G0, X2Grp &G1, const float *cu, 
 // three row groups rotated instead of copied, and each group's four weights loaded one group
 // ahead (indices clamped to the column's last row, so no read leaves the column).  hmin and
 // hmax are the same for the whole warp (its 64 x 8 outputs), so every lane runs the same loops.
+template <bool KAP = false>
 __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
                                           const X2Thr &thr2, const float *cu, int plane, int SX,
-                                          const float *gcol, int ox2, int hmin, int hmax)
+                                          const float *gcol, int ox2, int hmin, int hmax,
+                                          const X2Kap &kp)
 {
     X2Grp G0, G1, G2;
     int oy = -hmax;
@@ -577,7 +603,7 @@ __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB
     // top rim (or every row when no output's ball covers the centre row of this column)
     const int core_lo = hmin >= 0 ? -hmin : hmax + 1;
     for (; oy < core_lo; ++oy) {
-        x2_row<true>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy);
+        x2_row<true, KAP>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy, kp);
         x2_slide(G0, G1, cu, plane, SX, oy, oy < hmax);
     }
     if (hmin >= 0) {
@@ -597,30 +623,30 @@ __device__ __forceinline__ void x2_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB
             if (rem < 4) break;
             x2_load_grp(G2, cu, plane, SX, oy + 8);
             next_g();
-            x2_core4(acc, ui, G0, G1, G2, gc);
+            x2_core4<KAP>(acc, ui, G0, G1, G2, gc, kp, (float)ox2, oy);
             rotate_g();
             oy += 4; rem -= 4;                      // the window is (G1, G2)
             if (rem < 4) { G0 = G1; G1 = G2; break; }
             x2_load_grp(G0, cu, plane, SX, oy + 8);
             next_g();
-            x2_core4(acc, ui, G1, G2, G0, gc);
+            x2_core4<KAP>(acc, ui, G1, G2, G0, gc, kp, (float)ox2, oy);
             rotate_g();
             oy += 4; rem -= 4;                      // the window is (G2, G0)
             if (rem < 4) { G1 = G0; G0 = G2; break; }
             x2_load_grp(G1, cu, plane, SX, oy + 8);
             next_g();
-            x2_core4(acc, ui, G2, G0, G1, gc);
+            x2_core4<KAP>(acc, ui, G2, G0, G1, gc, kp, (float)ox2, oy);
             rotate_g();
             oy += 4; rem -= 4;                      // the window is (G0, G1) again
         }
         for (; oy <= hmin; ++oy) {
-            x2_row<false>(acc, ui, G0, G1, thr2, gcol[oy], 0);
+            x2_row<false, KAP>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy, kp);
             x2_slide(G0, G1, cu, plane, SX, oy, oy < hmax);
         }
     }
     // bottom rim
     for (; oy <= hmax; ++oy) {
-        x2_row<true>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy);
+        x2_row<true, KAP>(acc, ui, G0, G1, thr2, gcol[oy], ox2 + oy * oy, kp);
         x2_slide(G0, G1, cu, plane, SX, oy, oy < hmax);
     }
 }
@@ -722,7 +748,7 @@ __device__ __forceinline__ void x2_column_full(f2_t (&acc)[RB_P], const f2_t (&u
 // (each over its column offsets in increasing order) are added once, ox < 0 part + ox >= 0
 // part, through shared memory.  The weight table |o|^{-alpha} is copied to shared memory once
 // per block.
-template <int RM, int TY, int MB>
+template <int RM, int TY, int MB, bool KAP = false>
 __global__ void __launch_bounds__(64 * TY, MB)
 k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
               float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
@@ -770,9 +796,24 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         const int ybase = y0 + grp * RB_P;
         f2_t ui[RB_P], acc[RB_P];
         X2Thr thr2;
+        X2Kap kp;
         int tmax = -1, tmin = 1 << 30;
         // tile position of output (p = 0, columns xa, xb)
         const float *ua = su + (grp * RB_P + RM) * SX + 2 * threadIdx.x + RM;
+        if (KAP) {
+            const float p0 = (float)a.poly[0], p1 = a.K >= 1 ? (float)a.poly[1] : 0.f;
+            kp.c0 = f2_pack(-p0, -p0);
+            const float *__restrict__ whv = (const float *)a.wh;     // R^alpha
+            const float *__restrict__ irv = (const float *)a.ir;     // 1 / R2
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) {
+                const int y = ybase + p;
+                const bool oa = xa < n && y < n, ob = xb < n && y < n;
+                const int64_t ia = xa + (int64_t)n * y, ib = ia + 1;
+                kp.ra[p] = f2_pack(oa ? whv[ia] : 0.f, ob ? whv[ib] : 0.f);
+                kp.bk[p] = f2_pack(oa ? -p1 * irv[ia] : 0.f, ob ? -p1 * irv[ib] : 0.f);
+            }
+        }
 #pragma unroll
         for (int p = 0; p < RB_P; ++p) {
             const int y = ybase + p;
@@ -800,7 +841,7 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
             const int hmax = min(R, isqrt_small(tmax - ox2));
             const int hmin = (tmin >= ox2) ? min(hmax, isqrt_small(tmin - ox2)) : -1;
             const float *gcol = sg + (ox + R) * (2 * R + 1) + R;       // |oy| <= R
-            x2_column(acc, ui, thr2, ua + ox, SX * SY, SX, gcol, ox2, hmin, hmax);
+            x2_column<KAP>(acc, ui, thr2, ua + ox, SX * SY, SX, gcol, ox2, hmin, hmax, kp);
         }
         __syncthreads();               // every warp is done with the tile
         f2_t *xs = sx + grp * RB_P * 32 + threadIdx.x;
@@ -846,14 +887,14 @@ static size_t x2_smem_bytes()
 constexpr int X2_VARIANTS = 4;
 static const int x2_var_ty[X2_VARIANTS] = { 1, 1, 2, 2 };
 
-template <int RM, int TY, int MB>
+template <int RM, int TY, int MB, bool KAP>
 static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
                              int nrhs, const int *order, int ntiles, int *blocks_cache,
                              cudaStream_t st)
 {
     const dim3 blk(32, 2 * TY, 1);
     const size_t smem = x2_smem_bytes<RM, TY>();
-    auto kern = k_direct2d_x2<RM, TY, MB>;
+    auto kern = k_direct2d_x2<RM, TY, MB, KAP>;
     NL_CUDA_TRY(prep_smem(kern, smem));
     const int tiles_x = (p->n + 63) / 64;
     const int64_t items = (int64_t)ntiles * nrhs;
@@ -876,28 +917,29 @@ static nl_status launch_x2_t(nl_plan *p, const DirectArgs &a, const float *u, fl
     return NL_OK;
 }
 
-template <int RM>
+template <int RM, bool KAP>
 static nl_status launch_x2_var(nl_plan *p, int var, const DirectArgs &a, const float *u,
                                float *Lu, int nrhs, const int *order, int ntiles, int *bc,
                                cudaStream_t st)
 {
     switch (var) {
-    case 0: return launch_x2_t<RM, 1, 6>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    case 1: return launch_x2_t<RM, 1, 8>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    case 2: return launch_x2_t<RM, 2, 3>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
-    default: return launch_x2_t<RM, 2, 4>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 0: return launch_x2_t<RM, 1, 6, KAP>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 1: return launch_x2_t<RM, 1, 8, KAP>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    case 2: return launch_x2_t<RM, 2, 3, KAP>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
+    default: return launch_x2_t<RM, 2, 4, KAP>(p, a, u, Lu, nrhs, order, ntiles, bc, st);
     }
 }
 
+template <bool KAP>
 static nl_status x2_launch_any(nl_plan *p, int var, const DirectArgs &a, const float *u,
                                float *Lu, int nrhs, const int *order, int ntiles, int *bc,
                                cudaStream_t st)
 {
-    if (p->Rmax <= 4) return launch_x2_var<4>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
-    if (p->Rmax <= 8) return launch_x2_var<8>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
-    if (p->Rmax <= 16) return launch_x2_var<16>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
-    if (p->Rmax <= 24) return launch_x2_var<24>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
-    return launch_x2_var<32>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 4) return launch_x2_var<4, KAP>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 8) return launch_x2_var<8, KAP>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 16) return launch_x2_var<16, KAP>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    if (p->Rmax <= 24) return launch_x2_var<24, KAP>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
+    return launch_x2_var<32, KAP>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1724,12 +1766,16 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
     }
     if (p->d == 3 && sizeof(T) == 4 && mode == MODE_POWER && p->g3d32 && p->Rmax <= 8)
         return launch_3d_x2(p, a, (const float *)u, (float *)Lu, nrhs, st);
-    if (p->d == 2 && p->rb2d && sizeof(T) == 4) {
+    if (p->d == 2 && p->rb2d && sizeof(T) == 4 && mode == MODE_KAPPA && p->Rmax <= 32 &&
+        p->x2_order)
+        return x2_launch_any<true>(p, p->x2_var, a, (const float *)u, (float *)Lu, nrhs,
+                                   p->x2_order, p->x2_tiles, &p->x2_blocks, st);
+    if (p->d == 2 && p->rb2d && sizeof(T) == 4 && mode != MODE_KAPPA) {
         if (mode == MODE_POWER && p->Rmax <= 32 && p->x2_order) {
             const float *uf = (const float *)u;
             float *lf = (float *)Lu;
-            return x2_launch_any(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
-                                 &p->x2_blocks, st);
+            return x2_launch_any<false>(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
+                                        &p->x2_blocks, st);
         }
         if (mode == MODE_SYM && p->Rmax <= 32 && p->x2_order)
             return x2s_launch_any(p, p->x2_var, a, (const float *)u, (float *)Lu, nrhs,
@@ -2328,7 +2374,8 @@ static nl_status x3_tune(nl_plan *p, cudaStream_t st)
 nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
 {
     if (p->d == 3) return x3_tune(p, st);
-    if (!(p->d == 2 && p->rb2d && p->family == NL_POWER && p->Rmax <= 32)) return NL_OK;
+    const bool kap = p->family == NL_KAPPA && p->K <= 1;
+    if (!(p->d == 2 && p->rb2d && (p->family == NL_POWER || kap) && p->Rmax <= 32)) return NL_OK;
     const bool sym = p->symmetric != 0;
     const int nvar = sym ? X2S_VARIANTS : X2_VARIANTS;
     const int *var_ty = sym ? x2s_var_ty : x2_var_ty;
@@ -2359,7 +2406,8 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
         auto run = [&](int v) {
             const int k = var_ty[v] == ty_k[0] ? 0 : 1;
             return sym ? x2s_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st)
-                       : x2_launch_any(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st);
+                       : (kap ? x2_launch_any<true>(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st)
+                              : x2_launch_any<false>(p, v, a, u, lu, 1, ord[k], nt[k], &bc[v], st));
         };
         if (s == NL_OK) s = time_variants(nvar, run, ms, e0, e1, st);
         best = 0;

@@ -1248,7 +1248,7 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
 // Step 3 from the stored slots: per slot one broadcast load of the warp's base, one 16-bit
 // record per node, and the node's panels (the first four requested together, longer runs in
 // a loop); the next four slots are requested before the current ones are used.
-__global__ void __launch_bounds__(256) k_fast_gather_slots(FastI64Args a,
+__global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
                                                            const unsigned *__restrict__ base,
                                                            const unsigned short *__restrict__ rec,
                                                            const int64_t *__restrict__ woff,

@@ -525,7 +525,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     p->smem_bytes32 = tile_elems * e32;
     p->smem_bytes64 = tile_elems * e64;
     p->stage = (p->smem_bytes64 <= 200 * 1024) ? 1 : 0;
-    if (d == 2 && k->family != NL_PD_BOND && k->family != NL_KAPPA) {
+    if (d == 2 && k->family != NL_PD_BOND && (k->family != NL_KAPPA || k->K <= 1)) {
         // register-blocked kernel: (32 + 2R) x (32 + 2R + 8) tile + (2R+1)^2 weights
         const size_t t = (size_t)(32 + 2 * B) * (32 + 2 * B + 8);
         const size_t gw = (size_t)(2 * B + 1) * (2 * B + 1);
