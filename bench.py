@@ -405,7 +405,8 @@ class C2K(Workload):
         t = self.time_fn(self.step, reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         # per term: t = o2/R2, p = p0 + p1 t, ra g - p, times b_j, u_j - u_i, times, add
-        roof = _alu_roof("k_direct_scalar<2,float,KAPPA> (staged tile)", 9.0 * nb, t,
+        roof = _alu_roof("k_direct2d_x2<16,TY,MB,kappa> (paired columns, per-output weights)",
+                         9.0 * nb, t,
                          *fp32_peak())
         roof["algorithmic_per_launch"] = f"{9 * nb:.4g} flop (9 per neighbour term)"
         return roof, {"kappa_direct_fp32_ms": round(t, 4)}
@@ -808,9 +809,9 @@ class C5(Workload):
         N = n ** 3
         k = max(prof["applies"], 1)
         s2 = prof["step2_ms"] / k
-        # Step 2 of the 8 right-hand sides: per right-hand side u (4) and b (4) read and the
-        # 64-bit leaf-row prefix (8) written, 16 B per node
-        s2_bytes = 8 * 16.0 * N
+        # Step 2 of the 8 right-hand sides: per right-hand side u (4) read and the 64-bit
+        # leaf-row prefix (8) written, and the coefficient b (4) read once: 100 B per node
+        s2_bytes = (8 * 12.0 + 4.0) * N
         s2_ach = s2_bytes / (s2 * 1e-3) / 1e9
         nb = 8.0 * float(ball_counts(np.full(1, 4.0 / n), n, 3)[0]) * n ** 3
         roof = _alu_roof("k_direct3d_x2<4,4> (slab sweep)", 4.0 * nb, t_d,
@@ -821,7 +822,8 @@ class C5(Workload):
                       "fast_step3_8rhs_ms": round(prof["step3_ms"] / k, 4),
                       "fast_step2_hbm_gbs": round(s2_ach, 1),
                       "fast_step2_hbm_frac": round(s2_ach / self.peaks["hbm_gbs"], 4),
-                      "fast_step2_bytes": f"{s2_bytes:.4g} (16 B per node and right-hand side)"}
+                      "fast_step2_bytes": f"{s2_bytes:.4g} (per node: 12 B per right-hand side + 4 B "
+                                          "of b)"}
 
     def e2e(self, flush, steps):
         torch = self.torch

@@ -683,6 +683,9 @@ __global__ void k_max_abs_bits(int64_t N, const float *__restrict__ b, unsigned 
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
+constexpr int LEAF_MULTI = 8;
+constexpr int LEAF_MULTI_MAX = LEAF_MULTI;
+
 struct Step2Args {
     int d, n, L, c, lf;              // band: 2^c leaf rows per axis = one panel row of level lf
     int leaf_only;                   // 1: the leaf rows only (leaf-row gather)
@@ -1551,9 +1554,138 @@ __global__ void __launch_bounds__(256) k_fast_gather_leafrows(FastI64Args a,
     Lu[i] = (T)fixed_epilogue(G, (float)u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
+// ---------------------------------------------------------------------------
+// Step 2 of the leaf rows for several right-hand sides in three launches (rows of 128 or 256
+// nodes, 16-byte aligned fields): per-block bounds of |u| for every right-hand side, their
+// reduction to one scale word per right-hand side, then one warp per leaf row reading the
+// coefficient b once and every right-hand side's u, each scanned lane-contiguously (as the
+// single right-hand-side path) and stored through shared memory.  Every prefix is the integer
+// the single right-hand-side route writes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_absmax_parts_multi(int64_t N, const float *__restrict__ u,
+                                                            float bmax, unsigned char *aux,
+                                                            int stride)
+{
+    __shared__ float s_w[8];
+    const int q = blockIdx.y;
+    const float *__restrict__ uq = u + (int64_t)q * N;
+    float m = 0.f;
+    const int64_t stride_t = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(uq);
+    const int64_t N4 = N >> 2;                        // N is a multiple of 4 here
+    for (int64_t i = t0; i < N4; i += 8 * stride_t) {
+        float4 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t j = i + k * stride_t;
+            x[k] = j < N4 ? u4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            m = fmaxf(fmaxf(m, fmaxf(fabsf(x[k].x), fabsf(x[k].y))),
+                      fmaxf(fabsf(x[k].z), fabsf(x[k].w)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, s_w[w]);
+        float *part = reinterpret_cast<float *>(aux + (size_t)q * stride + 16);
+        part[blockIdx.x] = (m * bmax) * (1.f + 0x1p-20f);
+    }
+}
+
+// one block per right-hand side: the bound word (first word of its aux) from the parts
+__global__ void __launch_bounds__(256) k_parts_reduce(unsigned char *aux, int stride, int nparts)
+{
+    __shared__ float s_w[8];
+    unsigned char *a = aux + (size_t)blockIdx.x * stride;
+    const float *part = reinterpret_cast<const float *>(a + 16);
+    float m = 0.f;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) m = fmaxf(m, part[k]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, s_w[w]);
+        *reinterpret_cast<unsigned int *>(a) = __float_as_uint(m);
+    }
+}
+
+struct Step2MultiArgs {
+    int d, n, c, count, stride;
+    int64_t N;
+    const float *u, *b;
+    const unsigned char *aux;
+    long long *leaf;                 // [count][N]
+};
+
+__global__ void __launch_bounds__(128) k_step2_leaf_multi(Step2MultiArgs a)
+{
+    __shared__ long long s_row[4 * 256];
+    __shared__ int s_sh[LEAF_MULTI_MAX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid < a.count) {
+        const unsigned int *mx = reinterpret_cast<const unsigned int *>(a.aux + (size_t)tid * a.stride);
+        s_sh[tid] = fixed_shift_f32(a.N, mx);
+    }
+    __syncthreads();
+    const int n = a.n, d = a.d, E = n / 32;
+    const int S = 1 << a.c;
+    const int bands_y = d > 1 ? n / S : 1;
+    const int by = d > 1 ? (int)(blockIdx.x % bands_y) : 0;
+    const int bz = d > 2 ? (int)(blockIdx.x / bands_y) : 0;
+    const int rows_y = d > 1 ? S : 1, rows_z = d > 2 ? S : 1;
+    long long *srow = s_row + warp * n;
+    for (int r = warp; r < rows_y * rows_z; r += nw) {
+        const int iy = by * rows_y + r % rows_y, iz = bz * rows_z + r / rows_y;
+        const int64_t row = (int64_t)n * (iy + (int64_t)n * iz);
+        const float4 *__restrict__ b4 = reinterpret_cast<const float4 *>(a.b + row) + lane * (E / 4);
+        float bv[8];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (4 * k < E) {
+                const float4 y = b4[k];
+                bv[4 * k] = y.x; bv[4 * k + 1] = y.y; bv[4 * k + 2] = y.z; bv[4 * k + 3] = y.w;
+            }
+        }
+        for (int q = 0; q < a.count; ++q) {
+            const int sh = s_sh[q];
+            const float4 *__restrict__ u4 =
+                reinterpret_cast<const float4 *>(a.u + (int64_t)q * a.N + row) + lane * (E / 4);
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (4 * k < E) {
+                    const float4 x = u4[k];
+                    v[4 * k] = x.x * bv[4 * k]; v[4 * k + 1] = x.y * bv[4 * k + 1];
+                    v[4 * k + 2] = x.z * bv[4 * k + 2]; v[4 * k + 3] = x.w * bv[4 * k + 3];
+                }
+            }
+            long long qv[8], t = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k < E) {
+                    t += __float2ll_rn(ldexpf(v[k], sh));
+                    qv[k] = t;
+                }
+            }
+            const long long off = warp_incl_scan_ll(t, lane) - t;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < E) srow[E * lane + k] = qv[k] + off;
+            __syncwarp();
+            long long *out = a.leaf + (int64_t)q * a.N + row;
+            for (int x = lane; x < n; x += 32) out[x] = srow[x];
+            __syncwarp();
+        }
+    }
+}
+
 // Several right-hand sides at once (leaf-row form): the run bounds of a row are computed once
 // and applied to every right-hand side's leaf-row prefix sums (leaf + r * N, scale mx[r]).
-constexpr int LEAF_MULTI = 8;
+
 constexpr int AUX_STRIDE = 16 + NL_FAST_PARTS * 4;     // bytes of one right-hand side's aux
 
 struct LeafMultiArgs {
@@ -2059,10 +2191,33 @@ static nl_status fast_multi_leafrows(nl_plan *p, const float *u, float *Lu, int 
     for (int r0 = 0; r0 < nrhs; r0 += LEAF_MULTI) {
         const int cnt = std::min(LEAF_MULTI, nrhs - r0);
         prof_mark(p, 0, st);
-        for (int q = 0; q < cnt; ++q)
-            NL_CUDA_TRY(step2_rowprefix(p, u + (int64_t)(r0 + q) * p->N, true, st,
-                                        p->leaf_multi + (int64_t)q * p->N,
-                                        p->aux_multi + (size_t)q * AUX_STRIDE));
+        const float *u0 = u + (int64_t)r0 * p->N;
+        const bool fused = p->d > 1 && (p->n == 128 || p->n == 256) &&
+                           ((reinterpret_cast<uintptr_t>(u0) |
+                             reinterpret_cast<uintptr_t>(p->b32)) & 15) == 0;
+        if (fused) {
+            int64_t per = (p->N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
+            if (per < 2048) per = 2048;
+            const int nparts = (int)((p->N + per - 1) / per);
+            k_absmax_parts_multi<<<dim3(nparts, cnt), 256, 0, st>>>(p->N, u0, p->fast_bmax,
+                                                                    p->aux_multi, AUX_STRIDE);
+            k_parts_reduce<<<cnt, 256, 0, st>>>(p->aux_multi, AUX_STRIDE, nparts);
+            Step2MultiArgs sa;
+            sa.d = p->d; sa.n = p->n; sa.c = std::min(p->d == 2 ? 2 : 1, p->L);
+            sa.count = cnt; sa.stride = AUX_STRIDE; sa.N = p->N;
+            sa.u = u0; sa.b = p->b32; sa.aux = p->aux_multi; sa.leaf = p->leaf_multi;
+            int64_t bands = 1;
+            for (int q = 1; q < p->d; ++q) bands *= p->n >> sa.c;
+            int rows = 1;
+            for (int q = 1; q < p->d; ++q) rows <<= sa.c;
+            k_step2_leaf_multi<<<(unsigned)bands, 32 * rows, 0, st>>>(sa);
+            NL_CUDA_TRY(cudaGetLastError());
+        } else {
+            for (int q = 0; q < cnt; ++q)
+                NL_CUDA_TRY(step2_rowprefix(p, u0 + (int64_t)q * p->N, true, st,
+                                            p->leaf_multi + (int64_t)q * p->N,
+                                            p->aux_multi + (size_t)q * AUX_STRIDE));
+        }
         prof_mark(p, 1, st);
         LeafMultiArgs a;
         a.n = p->n; a.count = cnt; a.N = p->N;

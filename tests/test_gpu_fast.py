@@ -175,7 +175,8 @@ def test_fused_step2_bitwise_equal_to_panels(d, n):
     assert rel_l2(outs[0][idx], ref) <= 2e-6
 
 
-@pytest.mark.parametrize("d,n,nrhs", [(2, 64, 3), (2, 128, 9), (3, 16, 5), (1, 1024, 2)])
+@pytest.mark.parametrize("d,n,nrhs", [(2, 64, 3), (2, 128, 9), (3, 16, 5), (1, 1024, 2),
+                                      (2, 256, 2), (3, 128, 3)])
 def test_multi_rhs_leafrows_bitwise_equal_to_single(d, n, nrhs):
     """Several FP32 right-hand sides share one gather launch (per-row run bounds computed once);
     each output is bitwise the one-right-hand-side apply, and matches the oracle."""
@@ -190,8 +191,10 @@ def test_multi_rhs_leafrows_bitwise_equal_to_single(d, n, nrhs):
     for r in range(nrhs):
         np.testing.assert_array_equal(many[r], run_fast(plan, u[r], torch.float32))
     L = int(np.log2(n))
-    ref = oracle.fast_leafset(u[-1], d, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a)
-    assert rel_l2(many[-1], ref) <= 2e-6
+    idx = sample_idx(N, 3000, seed=n) if N > 100000 else np.arange(N)
+    ref = oracle.fast_leafset(u[-1], d, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a,
+                              idx=idx)
+    assert rel_l2(many[-1][idx], ref) <= 2e-6
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
