@@ -366,6 +366,8 @@ typedef struct {
     double sigma;              /* kernel constant */
     double poly[8];            /* p_0 .. p_K of p^{2K} (NL_POLY) */
     size_t device_bytes;       /* device memory owned by the plan */
+    size_t step1_bytes;        /* the stored decomposition of the panel route (read by every
+                                  panel-route apply), 0 if none */
 } nl_plan_info;
 
 nl_status nl_get_plan_info(const nl_plan *plan, nl_plan_info *info);

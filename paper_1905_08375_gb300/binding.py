@@ -58,7 +58,8 @@ class nl_plan_info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
                 ("max_radius", ctypes.c_int), ("num_offsets", ctypes.c_int),
                 ("moments", ctypes.c_int), ("sigma", ctypes.c_double),
-                ("poly", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t)]
+                ("poly", ctypes.c_double * 8), ("device_bytes", ctypes.c_size_t),
+                ("step1_bytes", ctypes.c_size_t)]
 
 
 ENTRY_POINTS = ("nl_plan_create", "nl_plan_destroy", "nl_apply", "nl_apply_fast", "nl_cg_solve",
@@ -233,7 +234,8 @@ def nl_get_plan_info(plan: Plan) -> dict:
     _check(lib().nl_get_plan_info(plan.handle, ctypes.byref(info)))
     return dict(dim=info.dim, n=info.n, levels=info.levels, max_radius=info.max_radius,
                 num_offsets=info.num_offsets, moments=info.moments, sigma=info.sigma,
-                poly=list(info.poly), device_bytes=int(info.device_bytes))
+                poly=list(info.poly), device_bytes=int(info.device_bytes),
+                step1_bytes=int(info.step1_bytes))
 
 
 def nl_apply_fast_noalloc(dim, n, delta, u, Lu, alpha=0.0, scale=1.0, normalize=True,

@@ -1574,15 +1574,15 @@ __global__ void __launch_bounds__(256) k_absmax_parts_multi(int64_t N, const flo
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(uq);
     const int64_t N4 = N >> 2;                        // N is a multiple of 4 here
-    for (int64_t i = t0; i < N4; i += 16 * stride_t) {
-        float4 x[16];
+    for (int64_t i = t0; i < N4; i += 8 * stride_t) {
+        float4 x[8];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 8; ++k) {
             const int64_t j = i + k * stride_t;
             x[k] = j < N4 ? u4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
+        for (int k = 0; k < 8; ++k)
             m = fmaxf(fmaxf(m, fmaxf(fabsf(x[k].x), fabsf(x[k].y))),
                       fmaxf(fabsf(x[k].z), fabsf(x[k].w)));
     }
@@ -1650,29 +1650,15 @@ __global__ void __launch_bounds__(128) k_step2_leaf_multi(Step2MultiArgs a)
                 bv[4 * k] = y.x; bv[4 * k + 1] = y.y; bv[4 * k + 2] = y.z; bv[4 * k + 3] = y.w;
             }
         }
-        // u of the next right-hand side is requested before the current one is scanned
-        float4 xn[2];
-        {
-            const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(a.u + row) + lane * (E / 4);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) if (4 * k < E) xn[k] = u4[k];
-        }
         for (int q = 0; q < a.count; ++q) {
             const int sh = s_sh[q];
-            float4 xc[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) xc[k] = xn[k];
-            if (q + 1 < a.count) {
-                const float4 *__restrict__ u4 = reinterpret_cast<const float4 *>(
-                    a.u + (int64_t)(q + 1) * a.N + row) + lane * (E / 4);
-#pragma unroll
-                for (int k = 0; k < 2; ++k) if (4 * k < E) xn[k] = u4[k];
-            }
+            const float4 *__restrict__ u4 =
+                reinterpret_cast<const float4 *>(a.u + (int64_t)q * a.N + row) + lane * (E / 4);
             float v[8];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (4 * k < E) {
-                    const float4 x = xc[k];
+                    const float4 x = u4[k];
                     v[4 * k] = x.x * bv[4 * k]; v[4 * k + 1] = x.y * bv[4 * k + 1];
                     v[4 * k + 2] = x.z * bv[4 * k + 2]; v[4 * k + 3] = x.w * bv[4 * k + 3];
                 }

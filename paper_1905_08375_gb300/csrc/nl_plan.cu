@@ -776,5 +776,6 @@ extern "C" nl_status nl_get_plan_info(const nl_plan *p, nl_plan_info *info)
     info->moments = p->M; info->sigma = p->sigma;
     for (int m = 0; m < 8; ++m) info->poly[m] = p->poly[m];
     info->device_bytes = p->device_bytes;
+    info->step1_bytes = p->slots * (sizeof(unsigned) + 32 * sizeof(unsigned short));
     return NL_OK;
 }
