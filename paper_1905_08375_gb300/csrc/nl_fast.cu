@@ -1248,6 +1248,23 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
     if (WRITE && fault) atomicExch(bad, 1);
 }
 
+// 64-bit sums split across the pipes: a value v = hi 2^32 + lo adds lo into a 64-bit sum with
+// one mad.wide.u32 (FMA pipe) and hi into a 32-bit sum (ALU); modulo 2^64 the total is
+// lo_sum + 2^32 hi_sum, the same integer as adding the values one by one.
+struct SplitSum {
+    unsigned long long lo = 0ull;
+    unsigned hi = 0u;
+    __device__ __forceinline__ void add(uint2 v)
+    {
+        asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(lo) : "r"(v.x));
+        hi += v.y;
+    }
+    __device__ __forceinline__ long long value() const
+    {
+        return (long long)(lo + ((unsigned long long)hi << 32));
+    }
+};
+
 // Step 3 from the stored slots: per slot one broadcast load of the warp's base, one 16-bit
 // record per node, and the node's panels (the first four requested together, longer runs in
 // a loop); the next four slots are requested before the current ones are used.
@@ -1265,8 +1282,8 @@ __global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
     const int lane = threadIdx.x & 31;
     const int64_t off = woff[w];
     const int ns = wslots[w];
-    const long long *__restrict__ pyr = a.pyr;
-    long long G = 0;
+    const uint2 *__restrict__ pyr = reinterpret_cast<const uint2 *>(a.pyr);
+    SplitSum G;
     unsigned b[4];
     unsigned short q[4];
 #pragma unroll
@@ -1283,28 +1300,29 @@ __global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
             bn[k] = t < ns ? __ldg(base + off + t) : 0u;
             qn[k] = t < ns ? __ldcs(rec + (off + t) * 32 + lane) : (unsigned short)0;
         }
-        long long v[4][4];
+        uint2 v[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
+            const uint2 *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
             const int len = q[k] >> 8;
             const int m = (int)(b[k] >> SLOT_POS_BITS);      // the warp's longest run (<= 31)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[k][j] = (j < m && j < len) ? __ldg(p + j) : 0LL;
+            for (int j = 0; j < 4; ++j) v[k][j] = (j < m && j < len) ? __ldg(p + j) : make_uint2(0u, 0u);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
+            const uint2 *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
             const int len = q[k] >> 8;
-            for (int j = 4; j < len; ++j) G += __ldg(p + j);
-            G += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
+            for (int j = 4; j < len; ++j) G.add(__ldg(p + j));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) G.add(v[k][j]);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) { b[k] = bn[k]; q[k] = qn[k]; }
     }
     if (i >= a.N) return;
     const int sh = fixed_shift_f32(a.N, a.mx);
-    Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
+    Lu[i] = fixed_epilogue(G.value(), u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
 // Warp-uniform form for n >= 32 (the 32 nodes of a warp share their row): every lane walks
@@ -1500,28 +1518,35 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
 // integer total is the one the panel-by-panel and per-level routes add.  Rows iy + t and
 // iy - t (and likewise in z) have the same vertical gap, so they share one chord.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long leaf_run(const long long *__restrict__ row, int n, int X,
-                                              int r)
+// the run of one leaf row as a prefix difference; the two prefix values go to split sums of
+// added and subtracted values (G = P - M at the end, modulo 2^64 the same integer)
+__device__ __forceinline__ void leaf_run(SplitSum &P, SplitSum &M,
+                                         const long long *__restrict__ row, int n, int X, int r)
 {
     const int ka = max(0, -((r - X) >> 1) - 1);
     const int kb = min(n - 1, (X + r) >> 1);
-    return __ldg(row + kb) - (ka > 0 ? __ldg(row + ka - 1) : 0LL);
+    const uint2 *rw = reinterpret_cast<const uint2 *>(row);
+    P.add(__ldg(rw + kb));
+    if (ka > 0) M.add(__ldg(rw + ka - 1));
 }
 
 template <int D>
 __device__ __forceinline__ long long leaf_plane(const long long *__restrict__ plane, int n,
                                                 int X, int iy, int T4)
 {
-    if (D == 1) return leaf_run(plane, n, X, isqrt_fast(T4));
-    long long G = 0;
+    SplitSum P, M;
+    if (D == 1) {
+        leaf_run(P, M, plane, n, X, isqrt_fast(T4));
+        return P.value() - M.value();
+    }
     for (int t = 0;; ++t) {
         const int e = t == 0 ? 0 : sq(2 * t - 1);
         if (e > T4) break;
         const int r = isqrt_fast(T4 - e);
-        if (iy + t < n) G += leaf_run(plane + (int64_t)n * (iy + t), n, X, r);
-        if (t > 0 && iy - t >= 0) G += leaf_run(plane + (int64_t)n * (iy - t), n, X, r);
+        if (iy + t < n) leaf_run(P, M, plane + (int64_t)n * (iy + t), n, X, r);
+        if (t > 0 && iy - t >= 0) leaf_run(P, M, plane + (int64_t)n * (iy - t), n, X, r);
     }
-    return G;
+    return P.value() - M.value();
 }
 
 template <int D, typename T>
