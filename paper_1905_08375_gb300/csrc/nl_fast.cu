@@ -437,19 +437,6 @@ __device__ __forceinline__ int isqrt_fast(int x)
     return h;
 }
 
-// max |u b| in FP32 (b32 = b rounded to FP32), enlarged by 2^-20 relative so that it bounds
-// the FP32 products used below
-__global__ void __launch_bounds__(256) k_absmax_f32(int64_t N, const float *__restrict__ u,
-                                                    const float *__restrict__ b,
-                                                    unsigned int *out)
-{
-    float m = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(u[i] * b[i]));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m * (1.f + 0x1p-20f)));
-}
 
 // scale exponent S with N * max|v| * 2^S < 2^62, from the FP32 bound
 __device__ __forceinline__ int fixed_shift_f32(int64_t N, const unsigned int *mx)
@@ -488,40 +475,8 @@ __global__ void k_fixed_consts(int64_t N, double hd, const double *__restrict__ 
     Fh[i] = (float)(fastF[i] * hd);
 }
 
-// leaf value v = fl32(u b32) as the integer round(v 2^S) (the product 2^S v is exact in FP32)
-__global__ void k_pyr_leaf_f32i64(int64_t N, const float *__restrict__ u,
-                                  const float *__restrict__ b, const unsigned int *mx,
-                                  long long *leaf)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int sh = fixed_shift_f32(N, mx);
-    leaf[i] = __float2ll_rn(ldexpf(u[i] * b[i], sh));
-}
 
 
-__global__ void k_pyr_level_i64(int d, int l, const long long *__restrict__ child,
-                                long long *__restrict__ parent)
-{
-    const int np = 1 << l;
-    int64_t P = np;
-    if (d > 1) P *= np;
-    if (d > 2) P *= np;
-    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= P) return;
-    const int kx = (int)(f % np);
-    const int ky = d > 1 ? (int)((f / np) % np) : 0;
-    const int kz = d > 2 ? (int)(f / ((int64_t)np * np)) : 0;
-    const int nc = 2 * np;
-    long long s = 0;
-    for (int c = 0; c < (1 << d); ++c) {
-        const int cx = 2 * kx + (c & 1);
-        const int cy = d > 1 ? 2 * ky + ((c >> 1) & 1) : 0;
-        const int cz = d > 2 ? 2 * kz + ((c >> 2) & 1) : 0;
-        s += child[cx + (int64_t)nc * (cy + (int64_t)nc * cz)];
-    }
-    parent[f] = s;
-}
 
 struct FastI64Args {
     int n, L;
@@ -1248,23 +1203,6 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
     if (WRITE && fault) atomicExch(bad, 1);
 }
 
-// 64-bit sums split across the pipes: a value v = hi 2^32 + lo adds lo into a 64-bit sum with
-// one mad.wide.u32 (FMA pipe) and hi into a 32-bit sum (ALU); modulo 2^64 the total is
-// lo_sum + 2^32 hi_sum, the same integer as adding the values one by one.
-struct SplitSum {
-    unsigned long long lo = 0ull;
-    unsigned hi = 0u;
-    __device__ __forceinline__ void add(uint2 v)
-    {
-        asm("mad.wide.u32 %0, %1, 1, %0;" : "+l"(lo) : "r"(v.x));
-        hi += v.y;
-    }
-    __device__ __forceinline__ long long value() const
-    {
-        return (long long)(lo + ((unsigned long long)hi << 32));
-    }
-};
-
 // Step 3 from the stored slots: per slot one broadcast load of the warp's base, one 16-bit
 // record per node, and the node's panels (the first four requested together, longer runs in
 // a loop); the next four slots are requested before the current ones are used.
@@ -1282,8 +1220,8 @@ __global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
     const int lane = threadIdx.x & 31;
     const int64_t off = woff[w];
     const int ns = wslots[w];
-    const uint2 *__restrict__ pyr = reinterpret_cast<const uint2 *>(a.pyr);
-    SplitSum G;
+    const long long *__restrict__ pyr = a.pyr;
+    long long G = 0;
     unsigned b[4];
     unsigned short q[4];
 #pragma unroll
@@ -1300,29 +1238,28 @@ __global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
             bn[k] = t < ns ? __ldg(base + off + t) : 0u;
             qn[k] = t < ns ? __ldcs(rec + (off + t) * 32 + lane) : (unsigned short)0;
         }
-        uint2 v[4][4];
+        long long v[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint2 *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
+            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
             const int len = q[k] >> 8;
             const int m = (int)(b[k] >> SLOT_POS_BITS);      // the warp's longest run (<= 31)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[k][j] = (j < m && j < len) ? __ldg(p + j) : make_uint2(0u, 0u);
+            for (int j = 0; j < 4; ++j) v[k][j] = (j < m && j < len) ? __ldg(p + j) : 0LL;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const uint2 *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
+            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
             const int len = q[k] >> 8;
-            for (int j = 4; j < len; ++j) G.add(__ldg(p + j));
-#pragma unroll
-            for (int j = 0; j < 4; ++j) G.add(v[k][j]);
+            for (int j = 4; j < len; ++j) G += __ldg(p + j);
+            G += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) { b[k] = bn[k]; q[k] = qn[k]; }
     }
     if (i >= a.N) return;
     const int sh = fixed_shift_f32(a.N, a.mx);
-    Lu[i] = fixed_epilogue(G.value(), u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
+    Lu[i] = fixed_epilogue(G, u[i], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i], a.hd, sh);
 }
 
 // Warp-uniform form for n >= 32 (the 32 nodes of a warp share their row): every lane walks
@@ -1518,35 +1455,28 @@ __global__ void __launch_bounds__(256) k_fast_gather_rowprefix(FastI64Args a,
 // integer total is the one the panel-by-panel and per-level routes add.  Rows iy + t and
 // iy - t (and likewise in z) have the same vertical gap, so they share one chord.
 // ---------------------------------------------------------------------------
-// the run of one leaf row as a prefix difference; the two prefix values go to split sums of
-// added and subtracted values (G = P - M at the end, modulo 2^64 the same integer)
-__device__ __forceinline__ void leaf_run(SplitSum &P, SplitSum &M,
-                                         const long long *__restrict__ row, int n, int X, int r)
+__device__ __forceinline__ long long leaf_run(const long long *__restrict__ row, int n, int X,
+                                              int r)
 {
     const int ka = max(0, -((r - X) >> 1) - 1);
     const int kb = min(n - 1, (X + r) >> 1);
-    const uint2 *rw = reinterpret_cast<const uint2 *>(row);
-    P.add(__ldg(rw + kb));
-    if (ka > 0) M.add(__ldg(rw + ka - 1));
+    return __ldg(row + kb) - (ka > 0 ? __ldg(row + ka - 1) : 0LL);
 }
 
 template <int D>
 __device__ __forceinline__ long long leaf_plane(const long long *__restrict__ plane, int n,
                                                 int X, int iy, int T4)
 {
-    SplitSum P, M;
-    if (D == 1) {
-        leaf_run(P, M, plane, n, X, isqrt_fast(T4));
-        return P.value() - M.value();
-    }
+    if (D == 1) return leaf_run(plane, n, X, isqrt_fast(T4));
+    long long G = 0;
     for (int t = 0;; ++t) {
         const int e = t == 0 ? 0 : sq(2 * t - 1);
         if (e > T4) break;
         const int r = isqrt_fast(T4 - e);
-        if (iy + t < n) leaf_run(P, M, plane + (int64_t)n * (iy + t), n, X, r);
-        if (t > 0 && iy - t >= 0) leaf_run(P, M, plane + (int64_t)n * (iy - t), n, X, r);
+        if (iy + t < n) G += leaf_run(plane + (int64_t)n * (iy + t), n, X, r);
+        if (t > 0 && iy - t >= 0) G += leaf_run(plane + (int64_t)n * (iy - t), n, X, r);
     }
-    return P.value() - M.value();
+    return G;
 }
 
 template <int D, typename T>
