@@ -582,8 +582,8 @@ __global__ void __launch_bounds__(256) k_fast_gather_i64(FastI64Args a, const T 
 // the scale exponent, quantises and scans the band's leaf rows (a warp per row), (2) builds
 // the levels L-1 .. lf of the band, and (3) adds the band's part of every coarser prefix,
 // P_l[row][k] += P_lf[band][(k + 1) 2^(lf-l) - 1], with integer atomics.  Every value is the
-// same integer that the level-by-level kernels produce (integer sums are exact and do not
-// depend on the order).
+// prefix of the panel sums of its row (integer sums are exact and do not depend on the
+// order in which the atomics land).
 // ---------------------------------------------------------------------------
 // One bound of |u b| per block, from max |u| and the plan-time bound bmax = max |b| (only u
 // is read): |fl32(u b)| <= max|u| bmax (1 + 2^-24), below fl32(max|u| bmax) (1 + 2^-20).
@@ -841,8 +841,8 @@ __global__ void __launch_bounds__(1024) k_step2_rowprefix(Step2Args a)
 // one block per band (the leaf rows of one panel row of level lf = L - c) (1) quantises the
 // band's leaf values, (2) sums the 2^d children of every panel of levels L-1 .. lf inside the
 // band, and (3) adds the band's part of every coarser panel with 64-bit integer atomics (those
-// levels were zeroed by k_absmax_parts).  Each panel then holds the integer sum of its leaves,
-// the same integer the level-by-level kernels produce.
+// levels were zeroed by k_absmax_parts).  Each panel then holds the integer sum of its leaves
+// (exact, whatever the order in which the atomics land).
 // ---------------------------------------------------------------------------
 constexpr int STEP2_BAND_MAX = 2048;         // panels of the band's level-lf row kept in smem
 
