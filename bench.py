@@ -172,6 +172,7 @@ class Workload:
 PROFILED_TRAFFIC = {
     "k_direct2d_x2": 21.03e6,          # c2, variant <16, 2, 4>
     "k_direct_pd_x2": 9.48e6,          # c3, <8, 2>
+    "k_fast_gather_slots": 175.50e6,   # c2, 171.7 MB read + 3.8 MB written
 }
 
 
@@ -332,16 +333,19 @@ class C2(Workload):
             roof = _alu_roof("k_direct2d_x2<16,TY> (direct FP32)", flops, t_direct, *fp32_peak())
             roof["algorithmic_per_launch"] = f"{flops:.4g} flop (4 per neighbour term)"
         else:
-            # the panel route reads the stored decomposition (Step 1 output) once per apply
-            byts = self.FAST_BYTES_PER_NODE * N + step1
-            ach = byts / (t_fast * 1e-3) / 1e9
-            roof = {"kernel": f"fast apply, {self.STEP_ROUTE} route (k_step2_panels + "
-                              "k_fast_gather_slots)",
+            # the dominant kernel is the panel route's Step 3 gather: it reads the stored
+            # decomposition (Step 1 output, step1 bytes), the pyramid (8 B x 4/3 per node) and
+            # u 4 + selfQ 8 + Fh 4 per node, and writes Lu 4 per node
+            t_s3 = routes[self.STEP_ROUTE]["step3_ms"]
+            byts = step1 + (8.0 * 4.0 / 3.0 + 20.0) * N
+            ach = byts / (t_s3 * 1e-3) / 1e9
+            roof = {"kernel": "k_fast_gather_slots (Step 3 of the panel route)",
                     "bound": "hbm", "achieved": round(ach, 2), "peak": pk, "unit": "GB/s",
-                    "frac": round(ach / pk, 4), "traffic": PROFILED_TRAFFIC.get("fast_panels"),
+                    "frac": round(ach / pk, 4),
+                    "traffic": PROFILED_TRAFFIC.get("k_fast_gather_slots"),
                     "peak_source": f"{self.peaks['_source']} hbm_gbs",
-                    "algorithmic_per_launch": f"{byts:.4g} B ({self.FAST_BYTES_PER_NODE} B per "
-                                              f"node + {step1:.4g} B of stored decomposition)"}
+                    "algorithmic_per_launch": f"{byts:.4g} B ({step1:.4g} B of stored "
+                                              "decomposition + 30.7 B per node)"}
         return roof, per
 
     def e2e(self, flush, steps):
