@@ -322,8 +322,7 @@ class C2(Workload):
         nl.nl_apply_fast(self.fast, self.u, self.out_f)
         # CG to relative residual 1e-8, learned two-level preconditioner vs Jacobi
         _, cgp = self.cg.kernels(flush, 3)
-        per["cg_256_8rhs"] = {k: cgp[k] for k in ("learned_ms", "learned", "jacobi_ms", "jacobi",
-                                                  "learned_speedup_over_jacobi", "training")}
+        per["cg_256_8rhs"] = dict(cgp)
         nb = float(ball_counts(self.f["delta"], n, 2).sum())
         flops = 4.0 * nb
         t_fast = routes[self.STEP_ROUTE]["ms"]
@@ -735,6 +734,9 @@ class C4(Workload):
         o8 = self.torch.empty_like(u8)
         t_op8 = self.time_fn(lambda: nl.nl_apply(self.plan, u8, o8), reps, flush)
         t_net8 = self.time_fn(lambda: nl.nl_net_apply(self.net, self.plan, r8, z8), reps, flush)
+        # the FP64 operator of the true-residual checks (all right-hand sides in one launch)
+        t_op64 = self.time_fn(lambda: nl.nl_apply(self.plan, r8, z8), reps, flush)
+        t_opp = self.time_fn(lambda: nl.nl_apply(self.plan, r8, z8, pairs=True), reps, flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         self.launches = None
         # the operator as CG applies it: all right-hand sides in one launch
@@ -742,13 +744,15 @@ class C4(Workload):
                          6.0 * nb * self.nrhs, t_op8, *fp32_peak())
         roof["algorithmic_per_launch"] = (f"{6 * nb * self.nrhs:.4g} flop (6 per one-sided ball "
                                           f"term, {self.nrhs} RHS)")
-        self.solve(nl.NL_PRECOND_LEARNED)          # leave the learned solution in x
-        return roof, {"learned_ms": round(t_l, 3), "learned": self.last,
+        sl = self.solve(nl.NL_PRECOND_LEARNED)     # leave the learned solution in x
+        return roof, {"learned_ms": round(t_l, 3), "learned": sl,
                       "jacobi_ms": round(t_j, 3), "jacobi": sj,
                       "learned_speedup_over_jacobi": round(t_j / t_l, 3),
                       "sym_apply_fp32_ms": round(t, 4),
                       f"sym_apply_fp32_{self.nrhs}rhs_ms": round(t_op8, 4),
                       f"learned_precond_apply_{self.nrhs}rhs_ms": round(t_net8, 4),
+                      f"sym_apply_fp64_{self.nrhs}rhs_ms": round(t_op64, 4),
+                      f"sym_apply_fp64_pairs_{self.nrhs}rhs_ms": round(t_opp, 4),
                       "training": self.train_info}
 
     def e2e(self, flush, steps):

@@ -53,7 +53,12 @@ typedef enum {
     NL_ETIMEOUT = 6       /* a bounded device-side wait gave up */
 } nl_status;
 
-typedef enum { NL_F32 = 0, NL_F64 = 1 } nl_dtype;
+/* NL_F64_PAIRS (nl_apply only, 2-D symmetric NL_POWER plans with Rmax <= 32): FP64 data in
+ * and out, arithmetic on pairs of FP32 numbers (each value hi + lo, 48 significant bits) with
+ * error-free sums and products; each term is within a few 2^-46 of its FP64 value relative
+ * to |g b_j (u_j - u_i)|.  nl_cg_solve computes its true residual this way on such plans.
+ * Other plans: NL_EUNSUPPORTED. */
+typedef enum { NL_F32 = 0, NL_F64 = 1, NL_F64_PAIRS = 2 } nl_dtype;
 
 /* Radial profile gamma(s), s = |xi| / delta_i (Eq. (2.2)):
  *   NL_POWER:   gamma(s) = s^{-alpha}, alpha >= 0 (alpha = 0: constant kernel)
@@ -152,7 +157,7 @@ nl_status nl_plan_destroy(nl_plan *plan);
  * Eq. (1.2).  u, Lu: DEVICE pointers, nrhs stacked fields, layout
  * [nrhs][n^d] (scalar) or [nrhs][d][n^d] (NL_PD_BOND), element type `dtype`.
  * u and Lu must not overlap.  FP32: FP32 products and sums of differences
- * u_j - u_i; FP64: all FP64.
+ * u_j - u_i; FP64: all FP64; NL_F64_PAIRS: FP64 data, FP32-pair arithmetic (above).
  * Errors: NL_EINVAL (null, nrhs < 1, dtype), NL_ECUDA (launch failure).
  */
 nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, void *stream);

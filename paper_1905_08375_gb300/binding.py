@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libnl.so")
 
 NL_OK, NL_EINVAL, NL_EUNSUPPORTED, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT = range(7)
-NL_F32, NL_F64 = 0, 1
+NL_F32, NL_F64, NL_F64_PAIRS = 0, 1, 2
 NL_POWER, NL_POLY, NL_PD_BOND, NL_KAPPA = 0, 1, 2, 3
 NL_COEF_NONE, NL_COEF_X, NL_COEF_XY, NL_COEF_MEAN = 0, 1, 2, 3
 NL_SELF_DISCRETE, NL_SELF_PAPER = 0, 1
@@ -185,7 +185,7 @@ def _cuda_ready():
         return False
 
 
-def _apply(fn, plan, u, Lu, nrhs, stream):
+def _apply(fn, plan, u, Lu, nrhs, stream, dtype=None):
     if not (u.is_cuda and Lu.is_cuda):
         raise ValueError("u and Lu must be CUDA tensors")
     if not (u.is_contiguous() and Lu.is_contiguous()) or u.dtype != Lu.dtype:
@@ -196,13 +196,20 @@ def _apply(fn, plan, u, Lu, nrhs, stream):
         nrhs = u.numel() // per
     if u.numel() != nrhs * per or Lu.numel() != nrhs * per:
         raise ValueError("u/Lu size does not match nrhs * n^d (* d)")
+    code = _dtype_code(u) if dtype is None else dtype
     _check(fn(plan.handle, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(Lu.data_ptr()),
-              int(nrhs), _dtype_code(u), _stream_ptr(stream)))
+              int(nrhs), code, _stream_ptr(stream)))
     return Lu
 
 
-def nl_apply(plan: Plan, u, Lu, nrhs=None, stream=None):
-    """Direct apply on device tensors; returns Lu."""
+def nl_apply(plan: Plan, u, Lu, nrhs=None, stream=None, pairs=False):
+    """Direct apply on device tensors; returns Lu.  pairs=True (FP64 tensors): the
+    FP32-pair arithmetic of NL_F64_PAIRS."""
+    if pairs:
+        import torch
+        if u.dtype != torch.float64:
+            raise ValueError("pairs=True takes FP64 tensors")
+        return _apply(lib().nl_apply, plan, u, Lu, nrhs, stream, NL_F64_PAIRS)
     return _apply(lib().nl_apply, plan, u, Lu, nrhs, stream)
 
 

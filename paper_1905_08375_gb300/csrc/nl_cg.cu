@@ -4,7 +4,8 @@
 // Precision: x, r, z, p and every inner product are FP64; the operator is applied in FP32
 // to an FP32 copy of p (written by the direction update), and its FP32 result enters the
 // FP64 updates.  When the recursive residual of every right-hand side is below the
-// tolerance, the true residual f + L x is recomputed with the FP64 operator; right-hand
+// tolerance, the true residual f + L x is recomputed with the FP64 operator (on 2-D
+// symmetric NL_POWER plans its FP32-pair form, NL_F64_PAIRS); right-hand
 // sides that miss the tolerance restart from that true residual (defect correction), so
 // the reported residual is always the FP64 one.
 //
@@ -475,11 +476,19 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
 
     const unsigned g1 = (unsigned)((op.dinv_len + 255) / 256);
     k_zero<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(len, a.x);
-    if (precond != NL_PRECOND_NONE) {
-        s = op.diag(op.ctx, a.x, dinv, st);
-        if (s != NL_OK) return s;
+    // the Jacobi factors depend on the operator only: formed once per workspace and mode
+    const int dmode = precond != NL_PRECOND_NONE ? 2 : 1;
+    if (c->dinv_at != dinv || c->dinv_mode != dmode) {
+        c->dinv_at = nullptr;
+        if (precond != NL_PRECOND_NONE) {
+            s = op.diag(op.ctx, a.x, dinv, st);
+            if (s != NL_OK) return s;
+        }
+        k_invert<<<g1, 256, 0, st>>>(op.dinv_len, dinv, precond != NL_PRECOND_NONE);
+        NL_CUDA_TRY(cudaGetLastError());
+        c->dinv_at = dinv;
+        c->dinv_mode = dmode;
     }
-    k_invert<<<g1, 256, 0, st>>>(op.dinv_len, dinv, precond != NL_PRECOND_NONE);
     if (flex && (s = nl_net_reserve(op.net, op.net_plan, nrhs, st)) != NL_OK) return s;
     const dim3 grid(NB, nrhs);
     if (flex) {
@@ -600,6 +609,10 @@ static nl_status plan_apply(void *ctx, const void *in, void *out, int dtype, cud
 {
     PlanOpCtx *c = (PlanOpCtx *)ctx;
     if (c->p->sym_fast) return nl_fast_sym_launch(c->p, in, out, c->nrhs, dtype, st);
+    // the true residual: FP32-pair arithmetic where the plan has it (48-bit words, far below
+    // the tolerances CG is asked for), FP64 otherwise
+    if (dtype == NL_F64 && c->p->pair_rm)
+        return nl_pairs_launch(c->p, (const double *)in, (double *)out, c->nrhs, st);
     return nl_direct_launch(c->p, in, out, c->nrhs, dtype, st);
 }
 

@@ -2175,14 +2175,17 @@ extern "C" nl_status nl_apply(nl_plan *p, const void *u, void *Lu, int nrhs, int
         nl_set_error("nl_apply: invalid plan");
         return NL_EINVAL;
     }
-    if (!u || !Lu || nrhs < 1 || nrhs > 65535 || (dtype != NL_F32 && dtype != NL_F64)) {
-        nl_set_error("nl_apply: need non-null u/Lu, 1 <= nrhs <= 65535, dtype F32/F64");
+    if (!u || !Lu || nrhs < 1 || nrhs > 65535 ||
+        (dtype != NL_F32 && dtype != NL_F64 && dtype != NL_F64_PAIRS)) {
+        nl_set_error("nl_apply: need non-null u/Lu, 1 <= nrhs <= 65535, dtype F32/F64/F64_PAIRS");
         return NL_EINVAL;
     }
     if (p->sym_fast) {
         nl_set_error("nl_apply: the symmetrised NL_POLY operator is applied by nl_apply_fast");
         return NL_EUNSUPPORTED;
     }
+    if (dtype == NL_F64_PAIRS)
+        return nl_pairs_launch(p, (const double *)u, (double *)Lu, nrhs, nl_stream(stream));
     return nl_direct_launch(p, u, Lu, nrhs, dtype, nl_stream(stream));
 }
 

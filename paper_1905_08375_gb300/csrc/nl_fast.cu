@@ -1073,15 +1073,15 @@ __global__ void __launch_bounds__(GP_THREADS) k_fast_gather_panels_lane(FastI64A
 // treat it), warp-aligned.  The 32 nodes of a warp share their row (n >= 32) or the single
 // row (1-D); the warp walks the union of its nodes' levels and panel rows, and every (level,
 // panel row, side) of that walk in which some node has panels is one slot: the warp's
-// smallest first-panel position in the pyramid buffer (27 bits, with the slot's longest run
-// in the top five, one word per warp and slot) and,
-// per node, a 16-bit record (offset from that position: low byte; number of consecutive
+// smallest first-panel position in the pyramid buffer (one 32-bit word per warp and slot)
+// and, per node, a 16-bit record (offset from that position: low byte; number of consecutive
 // panels: high byte; 0 = none).  In a slot the nodes' panels are adjacent or shared, so a
-// warp's loads of a slot touch few sectors.  Layout per warp w, from slot offset woff[w]:
-// base[woff + s], rec[(woff + s) * 32 + lane], s < wslots[w].
+// warp's loads of a slot touch few sectors.  The slots of a warp come in groups of four (the
+// last group padded with empty slots: base 0, records 0), so that one 16-byte load gives a
+// group's four base words and one 8-byte load a node's four records.  Layout per warp w, from
+// its group offset woff[w], slot s = 4 g + k < wslots[w]: base[(woff + g) * 4 + k],
+// rec[((woff + g) * 32 + lane) * 4 + k].
 // ---------------------------------------------------------------------------
-constexpr int SLOT_POS_BITS = 27;              // base word: position | (longest run << 27)
-constexpr unsigned SLOT_POS_MASK = (1u << SLOT_POS_BITS) - 1u;
 
 struct SlotArgs {
     int n, L;
@@ -1182,7 +1182,6 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
                 const unsigned pos = len[side] > 0 ? (unsigned)(rowpos + st[side]) : 0xffffffffu;
                 const unsigned bmin = __reduce_min_sync(0xffffffffu, pos);
                 if (bmin == 0xffffffffu) continue;           // no node of the warp: no slot
-                const int lmax = __reduce_max_sync(0xffffffffu, len[side]);
                 if (WRITE) {
                     unsigned short r = 0;
                     if (len[side] > 0) {
@@ -1190,10 +1189,8 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
                         if (dlt > 255u || len[side] > 255) fault = 1;
                         r = (unsigned short)((dlt & 255u) | ((unsigned)min(len[side], 255) << 8));
                     }
-                    rec[(off + slot) * 32 + lane] = r;
-                    // the slot's longest run (capped at 31) in the top five bits of the base
-                    if (lane == 0)
-                        base[off + slot] = bmin | ((unsigned)min(lmax, 31) << SLOT_POS_BITS);
+                    rec[((off + (slot >> 2)) * 32 + lane) * 4 + (slot & 3)] = r;
+                    if (lane == 0) base[off * 4 + slot] = bmin;
                 }
                 ++slot;
             }
@@ -1203,10 +1200,38 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
     if (WRITE && fault) atomicExch(bad, 1);
 }
 
-// Step 3 from the stored slots: per slot one broadcast load of the warp's base, one 16-bit
-// record per node, and the node's panels (the first four requested together, longer runs in
-// a loop); the next four slots are requested before the current ones are used.
-__global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
+// Step 3 from the stored slots, a group of four slots at a time: one broadcast 16-byte load of
+// the group's base words, one 8-byte load of the node's four records, then the node's panels
+// (the first SLOT_RUN_AHEAD of each run requested together, longer runs in a loop); the next
+// group's words are requested before the current ones are used.
+constexpr int SLOT_RUN_AHEAD = 3;     // panels of each run requested together
+constexpr int SLOT_MIN_BLOCKS = 4;    // blocks of 256 per SM (64 registers, no spills)
+
+__device__ __forceinline__ void slot_group(long long &G, const long long *__restrict__ pyr,
+                                           const uint4 b, const uint2 q)
+{
+    constexpr int J = SLOT_RUN_AHEAD;
+    const unsigned bw[4] = { b.x, b.y, b.z, b.w };
+    const unsigned rw[4] = { q.x & 0xffffu, q.x >> 16, q.y & 0xffffu, q.y >> 16 };
+    long long v[4][J];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long *p = pyr + (bw[k] + (rw[k] & 255u));
+        const int len = (int)(rw[k] >> 8);
+#pragma unroll
+        for (int j = 0; j < J; ++j) v[k][j] = j < len ? __ldg(p + j) : 0LL;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const long long *p = pyr + (bw[k] + (rw[k] & 255u));
+        const int len = (int)(rw[k] >> 8);
+        for (int j = J; j < len; ++j) G += __ldg(p + j);
+#pragma unroll
+        for (int j = 0; j < J; ++j) G += v[k][j];
+    }
+}
+
+__global__ void __launch_bounds__(256, SLOT_MIN_BLOCKS) k_fast_gather_slots(FastI64Args a,
                                                            const unsigned *__restrict__ base,
                                                            const unsigned short *__restrict__ rec,
                                                            const int64_t *__restrict__ woff,
@@ -1219,43 +1244,21 @@ __global__ void __launch_bounds__(256, 4) k_fast_gather_slots(FastI64Args a,
     if ((w << 5) >= a.N) return;
     const int lane = threadIdx.x & 31;
     const int64_t off = woff[w];
-    const int ns = wslots[w];
+    const int ng = (wslots[w] + 3) >> 2;
+    const uint4 *__restrict__ b4 = reinterpret_cast<const uint4 *>(base) + off;
+    const uint2 *__restrict__ q4 = reinterpret_cast<const uint2 *>(rec) + off * 32 + lane;
     const long long *__restrict__ pyr = a.pyr;
     long long G = 0;
-    unsigned b[4];
-    unsigned short q[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        b[k] = k < ns ? __ldg(base + off + k) : 0u;
-        q[k] = k < ns ? __ldcs(rec + (off + k) * 32 + lane) : (unsigned short)0;
-    }
-    for (int s = 0; s < ns; s += 4) {
-        unsigned bn[4];
-        unsigned short qn[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = s + 4 + k;
-            bn[k] = t < ns ? __ldg(base + off + t) : 0u;
-            qn[k] = t < ns ? __ldcs(rec + (off + t) * 32 + lane) : (unsigned short)0;
-        }
-        long long v[4][4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
-            const int len = q[k] >> 8;
-            const int m = (int)(b[k] >> SLOT_POS_BITS);      // the warp's longest run (<= 31)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[k][j] = (j < m && j < len) ? __ldg(p + j) : 0LL;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const long long *p = pyr + (b[k] & SLOT_POS_MASK) + (q[k] & 255u);
-            const int len = q[k] >> 8;
-            for (int j = 4; j < len; ++j) G += __ldg(p + j);
-            G += (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { b[k] = bn[k]; q[k] = qn[k]; }
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+    const uint2 z2 = make_uint2(0u, 0u);
+    uint4 b = ng > 0 ? __ldg(b4) : z4;
+    uint2 q = ng > 0 ? __ldcs(q4) : z2;
+    for (int g = 0; g < ng; ++g) {
+        const uint4 bn = g + 1 < ng ? __ldg(b4 + g + 1) : z4;
+        const uint2 qn = g + 1 < ng ? __ldcs(q4 + (int64_t)(g + 1) * 32) : z2;
+        slot_group(G, pyr, b, q);
+        b = bn;
+        q = qn;
     }
     if (i >= a.N) return;
     const int sh = fixed_shift_f32(a.N, a.mx);
@@ -1738,12 +1741,12 @@ static int moments_count(int d, int K)
 
 // Step 1 at plan time for the panel-by-panel route (1-D with n >= 32, and 2-D with n >= 32):
 // count every warp's slots, offsets on the host, write the slots.  Skipped (the gather then
-// enumerates the decomposition itself) when pyramid positions need more than 27 bits, the
+// enumerates the decomposition itself) when pyramid positions need more than 32 bits, the
 // slots would exceed 2^23 (about 570 MB), or a node's offset or run length leaves its byte.
 static nl_status build_slots(nl_plan *p, cudaStream_t st)
 {
     const int64_t N = p->N;
-    if (p->lvl_off[p->L] + N >= (int64_t)SLOT_POS_MASK) return NL_OK;
+    if (p->lvl_off[p->L] + N >= ((int64_t)1 << 32) - 256) return NL_OK;
     SlotArgs sa;
     sa.n = p->n; sa.L = p->L; sa.N = N; sa.thr4 = p->thr4;
     for (int l = 0; l <= p->L; ++l) sa.lvl_off[l] = p->lvl_off[l];
@@ -1774,15 +1777,20 @@ static nl_status build_slots(nl_plan *p, cudaStream_t st)
     cudaError_t ce = cudaMemcpyAsync(hw.data(), wslots, nw * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (counts)"));
-    int64_t tot = 0;
-    for (int64_t w = 0; w < nw; ++w) { ho[w] = tot; tot += hw[w]; }
+    int64_t groups = 0;                   // groups of four slots (woff counts groups)
+    for (int64_t w = 0; w < nw; ++w) { ho[w] = groups; groups += (hw[w] + 3) / 4; }
+    const int64_t tot = 4 * groups;
     if (tot > ((int64_t)1 << 23)) return fail(NL_OK);
-    if (cudaMalloc(&base, std::max<int64_t>(tot, 1) * sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&rec, std::max<int64_t>(tot, 1) * 32 * sizeof(unsigned short)) != cudaSuccess) {
+    const size_t base_bytes = std::max<int64_t>(tot, 4) * sizeof(unsigned);
+    const size_t rec_bytes = std::max<int64_t>(tot, 4) * 32 * sizeof(unsigned short);
+    if (cudaMalloc(&base, base_bytes) != cudaSuccess || cudaMalloc(&rec, rec_bytes) != cudaSuccess) {
         nl_set_error("nl_plan_create: allocation of %lld decomposition slots failed", (long long)tot);
         return fail(NL_ENOMEM);
     }
     ce = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    // the padding slots of each warp's last group stay empty
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(base, 0, base_bytes, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(rec, 0, rec_bytes, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(woff, ho.data(), nw * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     if (ce != cudaSuccess) return fail(nl_cuda_fail(ce, "stored decomposition (offsets)"));

@@ -45,6 +45,8 @@ struct nl_cg_state {
     int graph_precond;
     const void *graph_net;
     uint64_t graph_net_gen;
+    const double *dinv_at;          // where the Jacobi factors were last formed (they are a
+    int dinv_mode;                  // constant of the operator): 1 ones, 2 inverted diagonal
 };
 
 // The operator CG works with: nrhs segments (right-hand sides or batch instances) of the
@@ -150,6 +152,9 @@ struct nl_plan {
     unsigned char *sym_aux;            // scale word and per-block bounds of |c u|
     int prof_on, prof_count;        // per-phase timing of the fast apply
     cudaEvent_t prof_ev[64][3];
+    int pair_rm;                    // NL_F64_PAIRS (2-D symmetric NL_POWER): tile halo, 0 = off
+    float4 *pair_tab;               // offsets (tile offset, |o|^2, g hi, g lo)
+    float4 *pair_bc;                // per node (b hi, b lo, c hi, c lo), c = W/2 b
     nl_cg_state cg;                 // CG workspace (allocated on the first solve)
     double *dinv64;                 // inverse Jacobi diagonal (computed on first use)
     double diag_mean;               // mean of the Jacobi diagonal (with dinv64)
@@ -183,6 +188,10 @@ static inline cudaStream_t nl_stream(void *s) { return reinterpret_cast<cudaStre
 // ---- per-module launchers ----
 nl_status nl_direct_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                            cudaStream_t st);
+nl_status nl_pairs_plan_init(nl_plan *p, const int4 *offs, const double *g, int count,
+                             cudaStream_t st);
+nl_status nl_pairs_launch(const nl_plan *p, const double *u, double *Lu, int nrhs,
+                          cudaStream_t st);
 nl_status nl_pd_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                        cudaStream_t st);
 nl_status nl_fast_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,

@@ -714,6 +714,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         k_pd_exterior<<<GB, TB, 0, st>>>(pa, d_a, p->thr, p->off, p->pdext);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan kernels"));
+    NL_TMP_TRY(nl_pairs_plan_init(p, offs.data(), g64.data(), (int)offs.size(), st));
     if (p->sym_fast && !want_fast) {
         nl_set_error("nl_plan_create: the symmetric NL_POLY variant needs n = 2^L");
         return fail_tmp(NL_EUNSUPPORTED);
@@ -753,7 +754,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux, p->selfQ,
                      p->fastFh32, p->sym_c64, p->sym_c32, p->sym_T, p->sym_G64, p->sym_G32,
                      p->sym_diag, p->sym_D, p->sym_aux, p->slot_base, p->slot_rec, p->slot_woff, p->slot_count,
-                     p->fpd_ir2 };
+                     p->fpd_ir2, p->pair_tab, p->pair_bc };
     for (void *q : ptrs) if (q) cudaFree(q);
     for (int k = 0; k < 64; ++k)
         for (int j = 0; j < 3; ++j)

@@ -50,6 +50,34 @@ def test_unpreconditioned_and_not_converged():
     assert not st2["converged"] and st2["status"] == nl.NL_ENOTCONV
 
 
+def test_solves_in_sequence_match_solves_on_fresh_plans():
+    # the Jacobi factors are formed once per workspace and kept: a sequence of solves that
+    # changes the preconditioner and the number of right-hand sides (so that the workspace
+    # layout moves) gives the iterations and solutions of solves on fresh plans
+    n = 64
+    fld = synth.heterogeneous_2d(n=n, seed=12)
+    f = synth.cg_rhs(n, seed=13, count=3)
+
+    def make():
+        return nl.nl_plan_create(2, n, fld["delta"], family=nl.NL_POWER, alpha=1.5,
+                                 coef=nl.NL_COEF_XY, a=fld["a"], symmetric=True)
+
+    shared = make()
+    for nrhs, pc in [(3, nl.NL_PRECOND_JACOBI), (3, nl.NL_PRECOND_NONE), (1, nl.NL_PRECOND_JACOBI),
+                     (3, nl.NL_PRECOND_JACOBI), (1, nl.NL_PRECOND_NONE)]:
+        ft = torch.tensor(f[:nrhs], dtype=torch.float64, device=DEV)
+        xs = torch.empty_like(ft)
+        xf = torch.empty_like(ft)
+        st_s = nl.nl_cg_solve(shared, ft, xs, rtol=1e-8, maxit=20000, precond=pc)
+        fresh = make()
+        st_f = nl.nl_cg_solve(fresh, ft, xf, rtol=1e-8, maxit=20000, precond=pc)
+        fresh.close()
+        assert st_s["converged"] and st_f["converged"]
+        assert st_s["iterations"] == st_f["iterations"], (nrhs, pc, st_s, st_f)
+        assert torch.equal(xs, xf), (nrhs, pc)
+    shared.close()
+
+
 def test_non_symmetric_plan_rejected():
     n = 32
     fld = synth.heterogeneous_2d(n=n, seed=11)
