@@ -172,7 +172,7 @@ class Workload:
 PROFILED_TRAFFIC = {
     "k_direct2d_x2": 21.03e6,          # c2, variant <16, 2, 4>
     "k_direct_pd_x2": 9.48e6,          # c3, <8, 2>
-    "k_fast_gather_slots": 175.50e6,   # c2, 171.7 MB read + 3.8 MB written
+    "k_fast_gather_slots": 178.37e6,   # c2, 174.9 MB read + 3.5 MB written
 }
 
 
