@@ -740,7 +740,8 @@ class C4(Workload):
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         self.launches = None
         # the operator as CG applies it: all right-hand sides in one launch
-        roof = _alu_roof(f"k_direct2d_x2s (symmetric CG operator, {self.nrhs} RHS)",
+        kname = "k_direct2d_x2r" if self.nrhs >= 2 else "k_direct2d_x2s"
+        roof = _alu_roof(f"{kname} (symmetric CG operator, {self.nrhs} RHS)",
                          6.0 * nb * self.nrhs, t_op8, *fp32_peak())
         roof["algorithmic_per_launch"] = (f"{6 * nb * self.nrhs:.4g} flop (6 per one-sided ball "
                                           f"term, {self.nrhs} RHS)")

@@ -1256,17 +1256,310 @@ static nl_status x2s_launch_any(nl_plan *p, int var, const DirectArgs &a, const 
     return launch_x2s_var<32>(p, var, a, u, Lu, nrhs, order, ntiles, bc, st);
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric FP32 kernel for pairs of right-hand sides (CG applies its operator to all of them at
+// once).  Lane l owns one column and RB_P rows, and each paired f32x2 instruction works on the
+// two right-hand sides of one output, so the weight of a term,
+//   W = (w_i m_i b_j + c_j m_j) g(o),
+// and its masks are formed once (scalar FP32) for both.  A warp covers 32 x RB_P outputs (a
+// narrower spread of horizons than the 64 x RB_P of k_direct2d_x2s, so fewer masked rows), the
+// tile holds (u, u') as one 8-byte plane and b, c, thr + 1 as FP32 planes.  Every output's terms
+// are the same FP32 operations in the same order as in k_direct2d_x2s (rows increasing within a
+// column offset, column offsets increasing within each sign, the two signs added once), so each
+// right-hand side's result is bit for bit the one k_direct2d_x2s gives for it alone.
+// ---------------------------------------------------------------------------
+struct X2rGrp { f2_t u[4]; float b[4], c[4], t[4]; };
+
+template <int NR = 4>
+__device__ __forceinline__ void x2r_load_grp(X2rGrp &g, const f2_t *cu2, const float *cb, int PL,
+                                             int SX, int row)
+{
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int o = (row + k) * SX;
+        g.u[k] = cu2[o];
+        g.b[k] = cb[o];
+        g.c[k] = cb[o + PL];
+        g.t[k] = cb[o + 2 * PL];
+    }
+}
+
+// NJ rows oy .. oy + NJ - 1 for the RB_P outputs; output p at row j reads window entry p + j of
+// (A, B, C) = rows oy .. oy + 11.  LVL 0: no masks, 1: node masks, 2: node and output masks.
+template <int LVL, int NJ>
+__device__ __forceinline__ void x2r_rows(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                         const float (&wi)[RB_P], const float (&ti)[RB_P],
+                                         const X2rGrp &A, const X2rGrp &B, const X2rGrp &C,
+                                         const float *gcol, int oy, float fo)
+{
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const float g = gcol[oy + j];
+        const float o2 = fo + (float)((oy + j) * (oy + j));
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int k = p + j;
+            const X2rGrp &G = k < 4 ? A : (k < 8 ? B : C);
+            const float c = LVL >= 1 ? __fmul_rn(G.c[k & 3], __saturatef(G.t[k & 3] - o2))
+                                     : G.c[k & 3];
+            const float w = LVL >= 2 ? __fmul_rn(wi[p], __saturatef(ti[p] - o2)) : wi[p];
+            const float W = __fmul_rn(__fmaf_rn(w, G.b[k & 3], c), g);
+            acc[p] = f2_fma(f2_pack(W, W), f2_sub(G.u[k & 3], ui[p]), acc[p]);
+        }
+    }
+}
+
+__device__ __forceinline__ void x2r_chunk4(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                           const float (&wi)[RB_P], const float (&ti)[RB_P],
+                                           const X2rGrp &A, const X2rGrp &B, const X2rGrp &C,
+                                           const float *gcol, int oy, float fo, int hcore,
+                                           int hmid)
+{
+    const int m = max(abs(oy), abs(oy + 3));
+    if (m <= hcore) x2r_rows<0, 4>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    else if (m <= hmid) x2r_rows<1, 4>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    else x2r_rows<2, 4>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+}
+
+__device__ __forceinline__ void x2r_tail(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                         const float (&wi)[RB_P], const float (&ti)[RB_P],
+                                         const X2rGrp &A, const X2rGrp &B, X2rGrp &C,
+                                         const f2_t *cu2, const float *cb, int PL, int SX,
+                                         const float *gcol, int oy, float fo, int rem)
+{
+    if (rem == 1) {
+        x2r_rows<2, 1>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    } else if (rem == 2) {
+        x2r_load_grp<1>(C, cu2, cb, PL, SX, oy + 8);
+        x2r_rows<2, 2>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    } else if (rem == 3) {
+        x2r_load_grp<2>(C, cu2, cb, PL, SX, oy + 8);
+        x2r_rows<2, 3>(acc, ui, wi, ti, A, B, C, gcol, oy, fo);
+    }
+}
+
+// one column offset: rows -hmax .. hmax in chunks of four with the three groups rotated, then
+// at most three tail rows (the band limits of x2s_column)
+__device__ __forceinline__ void x2r_column(f2_t (&acc)[RB_P], const f2_t (&ui)[RB_P],
+                                           const float (&wi)[RB_P], const float (&ti)[RB_P],
+                                           const f2_t *cu2, const float *cb, int PL, int SX,
+                                           const float *gcol, int ox2, int hcore, int hmid,
+                                           int hmax)
+{
+    X2rGrp G0, G1, G2;
+    int oy = -hmax;
+    const float fo = (float)ox2;
+    x2r_load_grp(G0, cu2, cb, PL, SX, oy);
+    x2r_load_grp(G1, cu2, cb, PL, SX, oy + 4);
+    for (;;) {
+        if (hmax - oy + 1 < 4) {
+            x2r_tail(acc, ui, wi, ti, G0, G1, G2, cu2, cb, PL, SX, gcol, oy, fo, hmax - oy + 1);
+            break;
+        }
+        x2r_load_grp(G2, cu2, cb, PL, SX, oy + 8);
+        x2r_chunk4(acc, ui, wi, ti, G0, G1, G2, gcol, oy, fo, hcore, hmid);
+        oy += 4;
+        if (hmax - oy + 1 < 4) {
+            x2r_tail(acc, ui, wi, ti, G1, G2, G0, cu2, cb, PL, SX, gcol, oy, fo, hmax - oy + 1);
+            break;
+        }
+        x2r_load_grp(G0, cu2, cb, PL, SX, oy + 8);
+        x2r_chunk4(acc, ui, wi, ti, G1, G2, G0, gcol, oy, fo, hcore, hmid);
+        oy += 4;
+        if (hmax - oy + 1 < 4) {
+            x2r_tail(acc, ui, wi, ti, G2, G0, G1, cu2, cb, PL, SX, gcol, oy, fo, hmax - oy + 1);
+            break;
+        }
+        x2r_load_grp(G1, cu2, cb, PL, SX, oy + 8);
+        x2r_chunk4(acc, ui, wi, ti, G2, G0, G1, gcol, oy, fo, hcore, hmid);
+        oy += 4;
+    }
+}
+
+// Persistent over a largest-first queue of (32 x TY RB_P tile, pair of right-hand sides) items;
+// two warps per row group split the column offsets by sign (as k_direct2d_x2s).
+template <int RM, int TY, int MB>
+__global__ void __launch_bounds__(64 * TY, MB)
+k_direct2d_x2r(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
+               float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
+               int npairs, int *__restrict__ queue)
+{
+    constexpr int SX = 32 + 2 * RM;
+    constexpr int SY = TY * RB_P + 2 * RM + 1;
+    constexpr int PL = SX * SY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item, s_jmin[2 * TY];
+    f2_t *su2 = reinterpret_cast<f2_t *>(smem_raw);          // (u, u') of the pair
+    float *sb = reinterpret_cast<float *>(su2 + PL);         // b | c | thr + 1
+    f2_t *sx = su2;                                          // half sums, over the tile once read
+    const int n = a.n, R = a.R;
+    const int64_t N = a.N;
+    const float *__restrict__ bb = (const float *)a.b;
+    const float *__restrict__ whv = (const float *)a.wh;
+    const float *__restrict__ finv = (const float *)a.fin;
+    const float *__restrict__ extv = (const float *)a.ext;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int grp = threadIdx.y >> 1, half = threadIdx.y & 1;
+    const int total = ntiles * npairs;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int tile = order[item / npairs], z = 2 * (item % npairs);
+        const float *__restrict__ u0 = u + (int64_t)z * N;
+        const float *__restrict__ u1 = u0 + N;
+        const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * (TY * RB_P);
+        int jmin = 1 << 30;
+        for (int e = tid; e < PL; e += 64 * TY) {
+            const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
+            float v0 = 0.f, v1 = 0.f, bv = 0.f, cv = 0.f, tv = 0.f;
+            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
+                const int64_t j = gx + (int64_t)n * gy;
+                const int tj = a.thr[j];
+                v0 = u0[j];
+                v1 = u1[j];
+                bv = bb[j];
+                cv = whv[j] * bv;
+                tv = (float)(tj + 1);
+                jmin = min(jmin, tj);
+            }
+            su2[e] = f2_pack(v0, v1);
+            sb[e] = bv;
+            sb[e + PL] = cv;
+            sb[e + 2 * PL] = tv;
+        }
+        jmin = __reduce_min_sync(0xffffffffu, jmin);
+        if (threadIdx.x == 0) s_jmin[threadIdx.y] = jmin;
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 2 * TY; ++w) jmin = min(jmin, s_jmin[w]);
+        const int x = x0 + threadIdx.x;
+        const int ybase = y0 + grp * RB_P;
+        f2_t ui[RB_P], acc[RB_P];
+        float wi[RB_P], ti[RB_P];
+        int tmax = -1, tmin = 1 << 30;
+        const int base = (grp * RB_P + RM) * SX + threadIdx.x + RM;
+#pragma unroll
+        for (int p = 0; p < RB_P; ++p) {
+            const int y = ybase + p;
+            const bool o = x < n && y < n;
+            const int64_t i = x + (int64_t)n * y;
+            const int t = o ? a.thr[i] : -1;
+            const int r = o ? a.cnt_thr[i] : -1;
+            wi[p] = o ? whv[i] : 0.f;
+            ti[p] = (float)(t + 1);
+            tmax = max(tmax, r);
+            if (o) tmin = min(tmin, t);
+            ui[p] = su2[base + p * SX];
+            acc[p] = f2_pack(0.f, 0.f);
+        }
+        tmax = __reduce_max_sync(0xffffffffu, tmax);
+        tmin = __reduce_min_sync(0xffffffffu, tmin);
+        if (tmin == (1 << 30)) tmin = -1;
+        const int cmin = min(tmin, jmin);
+        const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
+        const int ox_lo = half ? 0 : -rx, ox_hi = half ? rx : -1;
+        for (int ox = ox_lo; ox <= ox_hi; ++ox) {
+            const int ox2 = ox * ox;
+            if (ox2 > tmax) continue;
+            const int hmax = min(R, isqrt_small(tmax - ox2));
+            const int hmid = (tmin >= ox2) ? min(hmax, isqrt_small(tmin - ox2)) : -1;
+            const int hcore = (cmin >= ox2) ? min(hmid, isqrt_small(cmin - ox2)) : -1;
+            const float *gcol = gtab + (ox + R) * (2 * R + 1) + R;     // |oy| <= R
+            x2r_column(acc, ui, wi, ti, su2 + base + ox, sb + base + ox, PL, SX, gcol, ox2, hcore,
+                       hmid, hmax);
+        }
+        __syncthreads();               // every warp is done with the tile
+        f2_t *xs = sx + grp * RB_P * 32 + threadIdx.x;
+        if (half) {
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) xs[p * 32] = acc[p];
+        }
+        __syncthreads();
+        if (!half) {
+#pragma unroll
+            for (int p = 0; p < RB_P; ++p) {
+                const int y = ybase + p;
+                float s0, s1, v0, v1;
+                f2_unpack(f2_add(acc[p], xs[p * 32]), s0, s1);
+                f2_unpack(ui[p], v0, v1);
+                if (y < n && x < n) {
+                    const int64_t i = x + (int64_t)n * y;
+                    Lu[(int64_t)z * N + i] = finv[i] * (s0 - v0 * extv[i]);
+                    Lu[(int64_t)(z + 1) * N + i] = finv[i] * (s1 - v1 * extv[i]);
+                }
+            }
+        }
+        __syncthreads();               // the tile, the half sums, s_item and s_jmin are reused
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) { queue[0] = 0; queue[1] = 0; }
+    }
+}
+
+constexpr int X2R_TY = 2;             // row groups per tile of the pair kernel
+constexpr int X2R_MB = 3;             // blocks per SM (168 registers, no spills)
+
+template <int RM>
+static size_t x2r_smem_bytes()
+{
+    return (size_t)(32 + 2 * RM) * (X2R_TY * RB_P + 2 * RM + 1) * (sizeof(f2_t) + 3 * sizeof(float));
+}
+
+template <int RM>
+static nl_status launch_x2r_t(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                              int npairs, cudaStream_t st)
+{
+    constexpr int TY = X2R_TY;
+    const dim3 blk(32, 2 * TY, 1);
+    const size_t smem = x2r_smem_bytes<RM>();
+    auto kern = k_direct2d_x2r<RM, TY, X2R_MB>;
+    NL_CUDA_TRY(prep_smem(kern, smem));
+    const int tiles_x = (p->n + 31) / 32;
+    const int64_t items = (int64_t)p->x2r_tiles * npairs;
+    if (items >= (int64_t)1 << 31) {
+        nl_set_error("nl_apply: %lld tiles x right-hand-side pairs exceed the tile queue",
+                     (long long)items);
+        return NL_EUNSUPPORTED;
+    }
+    if (items == 0) return NL_OK;
+    if (p->x2r_blocks == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        NL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64 * TY, smem));
+        NL_CUDA_TRY(cudaGetDevice(&dev));
+        NL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        p->x2r_blocks = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int64_t blocks = std::min<int64_t>(p->x2r_blocks, items);
+    kern<<<(unsigned)blocks, blk, smem, st>>>(a, p->rb_g32, u, Lu, p->x2r_order, p->x2r_tiles,
+                                              tiles_x, npairs, p->x2r_queue);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
+static nl_status x2r_launch_any(nl_plan *p, const DirectArgs &a, const float *u, float *Lu,
+                                int npairs, cudaStream_t st)
+{
+    if (p->Rmax <= 4) return launch_x2r_t<4>(p, a, u, Lu, npairs, st);
+    if (p->Rmax <= 8) return launch_x2r_t<8>(p, a, u, Lu, npairs, st);
+    if (p->Rmax <= 16) return launch_x2r_t<16>(p, a, u, Lu, npairs, st);
+    if (p->Rmax <= 24) return launch_x2r_t<24>(p, a, u, Lu, npairs, st);
+    return launch_x2r_t<32>(p, a, u, Lu, npairs, st);
+}
+
 // Tile order for the paired-column kernel: the cost of a 64 x rows tile is the sum of its
 // nodes' ball sizes; tiles are queued largest first.
-__global__ void k_x2_tile_cost(int n, int tiles_x, int rows, const int *__restrict__ cnt,
-                               long long *__restrict__ cost)
+__global__ void k_x2_tile_cost(int n, int tiles_x, int width, int rows,
+                               const int *__restrict__ cnt, long long *__restrict__ cost)
 {
     __shared__ long long s_w[8];
     const int tile = blockIdx.x;
-    const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * rows;
+    const int x0 = (tile % tiles_x) * width, y0 = (tile / tiles_x) * rows;
     long long c = 0;
-    for (int e = threadIdx.x; e < 64 * rows; e += blockDim.x) {
-        const int x = x0 + e % 64, y = y0 + e / 64;
+    for (int e = threadIdx.x; e < width * rows; e += blockDim.x) {
+        const int x = x0 + e % width, y = y0 + e / width;
         if (x < n && y < n) c += cnt[x + (int64_t)n * y];
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -1278,17 +1571,18 @@ __global__ void k_x2_tile_cost(int n, int tiles_x, int rows, const int *__restri
     }
 }
 
-// largest-first order of the 64 x (TY * RB_P) tiles, uploaded to *order_dev
-static nl_status x2_order_for(nl_plan *p, int ty, int **order_dev, int *ntiles, cudaStream_t st)
+// largest-first order of the width x (TY * RB_P) tiles, uploaded to *order_dev
+static nl_status x2_order_for(nl_plan *p, int ty, int **order_dev, int *ntiles, cudaStream_t st,
+                              int width = 64)
 {
     const int rows = ty * RB_P;
-    const int tiles_x = (p->n + 63) / 64, tiles_y = (p->n + rows - 1) / rows;
+    const int tiles_x = (p->n + width - 1) / width, tiles_y = (p->n + rows - 1) / rows;
     const int64_t tiles = (int64_t)tiles_x * tiles_y;
     if (tiles >= (int64_t)1 << 30) return NL_EUNSUPPORTED;
     long long *d_cost = nullptr;
     NL_CUDA_TRY(cudaMalloc(&d_cost, tiles * sizeof(long long)));
     std::vector<long long> cost(tiles);
-    k_x2_tile_cost<<<(unsigned)tiles, 256, 0, st>>>(p->n, tiles_x, rows, p->cnt, d_cost);
+    k_x2_tile_cost<<<(unsigned)tiles, 256, 0, st>>>(p->n, tiles_x, width, rows, p->cnt, d_cost);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cost.data(), d_cost, tiles * sizeof(long long), cudaMemcpyDeviceToHost, st);
@@ -1777,9 +2071,21 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
             return x2_launch_any<false>(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
                                         &p->x2_blocks, st);
         }
-        if (mode == MODE_SYM && p->Rmax <= 32 && p->x2_order)
-            return x2s_launch_any(p, p->x2_var, a, (const float *)u, (float *)Lu, nrhs,
-                                  p->x2_order, p->x2_tiles, &p->x2_blocks, st);
+        if (mode == MODE_SYM && p->Rmax <= 32 && p->x2_order) {
+            // pairs of right-hand sides by the pair kernel, an odd last one by x2s (the same
+            // bits either way)
+            const float *uf = (const float *)u;
+            float *lf = (float *)Lu;
+            if (nrhs >= 2 && p->x2r_order) {
+                nl_status s2 = x2r_launch_any(p, a, uf, lf, nrhs / 2, st);
+                if (s2 != NL_OK || nrhs % 2 == 0) return s2;
+                const int64_t last = (int64_t)(nrhs - 1) * p->N;
+                return x2s_launch_any(p, p->x2_var, a, uf + last, lf + last, 1, p->x2_order,
+                                      p->x2_tiles, &p->x2_blocks, st);
+            }
+            return x2s_launch_any(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
+                                  &p->x2_blocks, st);
+        }
         if (mode == MODE_POWER) return launch_rb_t<T, MODE_POWER>(p, a, u, Lu, nrhs, st);
         if (mode == MODE_POLY) return launch_rb_t<T, MODE_POLY>(p, a, u, Lu, nrhs, st);
         return launch_rb_t<T, MODE_SYM>(p, a, u, Lu, nrhs, st);
@@ -2431,5 +2737,13 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
     p->x2_blocks = bc[best];
     p->x2_var = best;
     p->device_bytes += (size_t)nt[kb] * sizeof(int) + 2 * sizeof(int);
+    if (sym) {
+        // the pair kernel's 32 x (X2R_TY RB_P) tiles and its queue
+        NL_CUDA_TRY(cudaMalloc(&p->x2r_queue, 2 * sizeof(int)));
+        NL_CUDA_TRY(cudaMemsetAsync(p->x2r_queue, 0, 2 * sizeof(int), st));
+        const nl_status so = x2_order_for(p, X2R_TY, &p->x2r_order, &p->x2r_tiles, st, 32);
+        if (so != NL_OK) return so;
+        p->device_bytes += (size_t)p->x2r_tiles * sizeof(int) + 2 * sizeof(int);
+    }
     return NL_OK;
 }

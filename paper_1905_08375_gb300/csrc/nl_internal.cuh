@@ -103,6 +103,8 @@ struct nl_plan {
     int *x2_order, *x2_queue;       // paired-column FP32 kernel: tiles largest first, and the
     int x2_tiles, x2_blocks, x2_var;// work-queue counter + exit ticket; persistent grid size;
                                     // kernel variant (timed at plan creation)
+    int *x2r_order, *x2r_queue;     // symmetric kernel for pairs of right-hand sides: 32-wide
+    int x2r_tiles, x2r_blocks;      // tiles largest first, queue, tile count, grid size
     // per-node device arrays
     int *thr;               // largest integer < R2_i
     int *cnt;               // table entries with o2 <= thr_i (or the symmetric bound)

@@ -67,16 +67,24 @@ def test_2d_symmetric_variant(dtype):
     assert rel_l2(run_direct(plan, f["u"][0], dtype), ref) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("n,nrhs", [(203, 2), (181, 1), (77, 8)])
+@pytest.mark.parametrize("n,nrhs", [(203, 2), (181, 1), (77, 8), (256, 5)])
 def test_2d_symmetric_paired_columns_fp32(n, nrhs):
     """Grids large enough for the paired-column symmetrised kernel, ragged tails, several
-    right-hand sides."""
+    right-hand sides (pairs of them take the two-right-hand-side kernel, an odd last one the
+    single kernel): against the FP64 oracle, and each right-hand side bit for bit its own
+    single apply where one right-hand side also takes the paired-column path (n^2 >= 32768;
+    smaller single applies split each ball over a group of lanes instead)."""
     f = synth.heterogeneous_2d(n=n, seed=n, nrhs=nrhs)
     plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POWER, alpha=1.5,
                              coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
     ref = oracle.direct_scalar(f["u"], 2, n, f["delta"], alpha=1.5, coef=oracle.COEF_XY,
                                a=f["a"], symmetric=True)
-    assert rel_l2(run_direct(plan, f["u"], torch.float32), ref) <= 2e-6
+    got = run_direct(plan, f["u"], torch.float32)
+    assert rel_l2(got, ref) <= 2e-6
+    if nrhs > 1 and n * n >= 32 * 1024:
+        for r in range(nrhs):
+            one = run_direct(plan, f["u"][r], torch.float32)
+            assert np.array_equal(one.reshape(-1), got[r].reshape(-1)), r
 
 
 @pytest.mark.parametrize("n,rmin,rspan", [(190, 2.0, 19.0), (184, 9.0, 0.0), (200, 19.0, 1.5)])
