@@ -9,12 +9,15 @@
 // sides that miss the tolerance restart from that true residual (defect correction), so
 // the reported residual is always the FP64 one.
 //
-// Execution: per right-hand side, NB blocks do grid-stride vector work and write one
-// partial sum each; the next kernel folds the NB partials in a fixed order (same value in
+// Execution: per right-hand side, nb <= NB blocks do grid-stride vector work and write one
+// partial sum each (nb = NB for one right-hand side or uneven segments, fewer per right-hand
+// side when several share the grid); the next kernel folds the nb partials in a fixed order
+// (same value in
 // every block, deterministic).  One iteration is four launches (apply, dot, update,
 // direction); CHUNK iterations plus a convergence check are captured once into a CUDA
 // graph on a plan-owned stream.  The host reads the per-right-hand-side flags from pinned
 // memory after each chunk, with a bounded wait.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <cmath>
@@ -25,7 +28,8 @@
 namespace {
 
 constexpr int RB = 256;     // threads per reduction block
-constexpr int NB = 152;     // reduction blocks per right-hand side (one per SM)
+constexpr int NB = 152;     // reduction blocks per right-hand side at most (one per SM)
+constexpr int CG_GRID_WAVES = 2;   // uniform segments: about CG_GRID_WAVES x NB blocks in all
 constexpr int CHUNK = 16;   // iterations per captured graph
 
 // per right-hand side scalars
@@ -48,12 +52,12 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;   // valid in thread 0
 }
 
-// sum of the NB partials of (slot, rhs), fixed order; valid in every lane of warp 0
-__device__ __forceinline__ double fold(const double *part, int slot, int rhs, int nrhs)
+// sum of the nb partials of (slot, rhs), fixed order; valid in every lane of warp 0
+__device__ __forceinline__ double fold(const double *part, int slot, int rhs, int nrhs, int nb)
 {
     const double *q = part + ((size_t)slot * nrhs + rhs) * NB;
     double s = 0.0;
-    for (int k = threadIdx.x & 31; k < NB; k += 32) s += q[k];
+    for (int k = threadIdx.x & 31; k < nb; k += 32) s += q[k];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
@@ -63,6 +67,7 @@ struct CgArgs {
     const int64_t *seg_off, *seg_len;   // per-segment offsets/lengths, or nullptr
     int dinv_global;      // dinv indexed by the global position (else by k)
     int nrhs;
+    int nb;               // blocks per right-hand side (<= NB)
     double tol;           // on the recursive relative residual
     const double *f;
     double *x, *r, *z, *p, *q64;
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(RB) k_cg_init(CgArgs a)
     const int rhs = blockIdx.y;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0, rr = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB) {
         const double fv = a.f[base + k];
         a.x[base + k] = 0.0;
         a.r[base + k] = fv;
@@ -120,7 +125,7 @@ __global__ void k_cg_init_scalars(CgArgs a)
 {
     const int rhs = blockIdx.x;
     if (threadIdx.x >= 32) return;
-    const double ff = fold(a.part, P_AUX, rhs, a.nrhs);
+    const double ff = fold(a.part, P_AUX, rhs, a.nrhs, a.nb);
     if (threadIdx.x == 0) {
         double *sc = a.sc + (size_t)rhs * S_COUNT;
         sc[S_FF] = ff;
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(RB) k_cg_pz(CgArgs a, int only, double goal)
     const bool redo = only < 0 || a.sc[(size_t)rhs * S_COUNT + S_TRUE] > goal;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB) {
         const int64_t g = base + k;
         const double zv = a.z[g];
         if (redo) {
@@ -156,8 +161,8 @@ __global__ void __launch_bounds__(RB) k_cg_pz(CgArgs a, int only, double goal)
 // Idempotent: repeating it without an update in between changes nothing.
 __device__ __forceinline__ void scalars_after_update(const CgArgs &a, int rhs)
 {
-    const double rz = fold(a.part, P_RZ, rhs, a.nrhs);
-    const double rr = fold(a.part, P_RR, rhs, a.nrhs);
+    const double rz = fold(a.part, P_RZ, rhs, a.nrhs, a.nb);
+    const double rr = fold(a.part, P_RR, rhs, a.nrhs, a.nb);
     if (threadIdx.x == 0) {
         double *sc = a.sc + (size_t)rhs * S_COUNT;
         sc[S_RZ] = rz;
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(RB) k_cg_dot(CgArgs a)
     if (blockIdx.x == 0 && threadIdx.x < 32) scalars_after_update(a, rhs);
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double pq = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB)
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB)
         pq -= a.p[base + k] * (double)a.q32[base + k];
     const double s = block_sum(pq, sh);
     if (threadIdx.x == 0) store_partial(a, P_PQ, rhs, s);
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
     const int rhs = blockIdx.y;
     const double *sc = a.sc + (size_t)rhs * S_COUNT;
     if (threadIdx.x < 32) {
-        const double pq = fold(a.part, P_PQ, rhs, a.nrhs);
+        const double pq = fold(a.part, P_PQ, rhs, a.nrhs, a.nb);
         if (threadIdx.x == 0) {
             const bool live = sc[S_CONV] == 0.0 && pq > 0.0 && sc[S_RZ] > 0.0;
             s_alpha = live ? sc[S_RZ] / pq : 0.0;
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(RB) k_cg_update(CgArgs a)
     const double alpha = s_alpha;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0, rr = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB) {
         const int64_t g = base + k;
         double rv = a.r[g];
         if (alpha != 0.0) {
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(RB) k_cg_rz(CgArgs a)
     const int rhs = blockIdx.y;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB)
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB)
         rz += a.r[base + k] * a.z[base + k];
     const double s = block_sum(rz, sh);
     if (threadIdx.x == 0) store_partial(a, P_RZ, rhs, s);
@@ -250,8 +255,8 @@ __global__ void __launch_bounds__(RB) k_cg_dir(CgArgs a)
     const int rhs = blockIdx.y;
     const double *sc = a.sc + (size_t)rhs * S_COUNT;
     if (threadIdx.x < 32) {
-        const double rz_new = fold(a.part, P_RZ, rhs, a.nrhs);
-        const double rz_mix = FLEX ? fold(a.part, P_AUX, rhs, a.nrhs) : 0.0;
+        const double rz_new = fold(a.part, P_RZ, rhs, a.nrhs, a.nb);
+        const double rz_mix = FLEX ? fold(a.part, P_AUX, rhs, a.nrhs, a.nb) : 0.0;
         if (threadIdx.x == 0) {
             const double rz_old = sc[S_RZ];
             s_beta = (sc[S_CONV] == 0.0 && rz_old > 0.0) ? (rz_new - rz_mix) / rz_old : 0.0;
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(RB) k_cg_dir(CgArgs a)
     __syncthreads();
     const double beta = s_beta;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB) {
         const int64_t g = base + k;
         const double pv = a.z[g] + beta * a.p[g];
         a.p[g] = pv;
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(RB) k_cg_true(CgArgs a)
     const int rhs = blockIdx.y;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double ss = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB) {
         const double t = a.f[base + k] + a.q64[base + k];
         ss += t * t;
     }
@@ -287,7 +292,7 @@ __global__ void k_cg_true_scalars(CgArgs a)
 {
     const int rhs = blockIdx.x;
     if (threadIdx.x >= 32) return;
-    const double ss = fold(a.part, P_AUX, rhs, a.nrhs);
+    const double ss = fold(a.part, P_AUX, rhs, a.nrhs, a.nb);
     if (threadIdx.x == 0) {
         double *sc = a.sc + (size_t)rhs * S_COUNT;
         sc[S_TRUE] = sc[S_FF] > 0.0 ? sqrt(ss / sc[S_FF]) : 0.0;
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(RB) k_cg_restart(CgArgs a, double goal)
     const bool redo = sc[S_TRUE] > goal;
     const int64_t base = seg_base(a, rhs), len = seg_len(a, rhs);
     double rz = 0.0, rr = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)NB * RB) {
+    for (int64_t k = blockIdx.x * (int64_t)RB + threadIdx.x; k < len; k += (int64_t)a.nb * RB) {
         const int64_t g = base + k;
         double rv = a.r[g];
         if (redo) {
@@ -417,7 +422,7 @@ static nl_status ensure_workspace(nl_cg_state *c, int64_t len, int64_t dlen, int
 static nl_status enqueue_chunk(nl_cg_op &op, const CgArgs &a, bool flex, int iters,
                                cudaStream_t st)
 {
-    const dim3 grid(NB, a.nrhs);
+    const dim3 grid(a.nb, a.nrhs);
     for (int it = 0; it < iters; ++it) {
         nl_status s = op.apply(op.ctx, a.p32, a.q32, NL_F32, st);
         if (s != NL_OK) return s;
@@ -469,6 +474,10 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
     a.dinv = dinv;
     a.p32 = c->ws32; a.q32 = a.p32 + len;
     a.part = c->red; a.sc = c->red + (size_t)P_COUNT * nrhs * NB;
+    // uniform segments: about CG_GRID_WAVES x NB blocks over all right-hand sides (each thread
+    // then takes several elements); uneven segments keep NB each
+    a.nb = op.seg_off ? NB
+                      : std::max(16, std::min(NB, (CG_GRID_WAVES * NB + nrhs - 1) / nrhs));
 
     cudaStream_t caller = nl_stream(stream), st = c->stream;
     NL_CUDA_TRY(cudaEventRecord(c->ev, caller));
@@ -490,7 +499,7 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
         c->dinv_mode = dmode;
     }
     if (flex && (s = nl_net_reserve(op.net, op.net_plan, nrhs, st)) != NL_OK) return s;
-    const dim3 grid(NB, nrhs);
+    const dim3 grid(a.nb, nrhs);
     if (flex) {
         k_cg_init<true><<<grid, RB, 0, st>>>(a);
         k_cg_init_scalars<<<nrhs, 32, 0, st>>>(a);

@@ -1204,13 +1204,15 @@ __global__ void __launch_bounds__(GP_THREADS) k_slots(SlotArgs a, int *__restric
 // the group's base words, one 8-byte load of the node's four records, then the node's panels
 // (the first SLOT_RUN_AHEAD of each run requested together, longer runs in a loop); the next
 // group's words are requested before the current ones are used.
-constexpr int SLOT_RUN_AHEAD = 3;     // panels of each run requested together
+constexpr int SLOT_RUN_AHEAD = 3;     // panels of each run requested together (the vote in
+                                      // slot_group tests length bytes >= 4 = SLOT_RUN_AHEAD + 1)
 constexpr int SLOT_MIN_BLOCKS = 4;    // blocks of 256 per SM (64 registers, no spills)
 
 __device__ __forceinline__ void slot_group(long long &G, const long long *__restrict__ pyr,
                                            const uint4 b, const uint2 q)
 {
     constexpr int J = SLOT_RUN_AHEAD;
+    static_assert(J == 3, "the long-run vote below tests length bytes >= 4");
     const unsigned bw[4] = { b.x, b.y, b.z, b.w };
     const unsigned rw[4] = { q.x & 0xffffu, q.x >> 16, q.y & 0xffffu, q.y >> 16 };
     long long v[4][J];
@@ -1223,11 +1225,17 @@ __device__ __forceinline__ void slot_group(long long &G, const long long *__rest
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const long long *p = pyr + (bw[k] + (rw[k] & 255u));
-        const int len = (int)(rw[k] >> 8);
-        for (int j = J; j < len; ++j) G += __ldg(p + j);
 #pragma unroll
         for (int j = 0; j < J; ++j) G += v[k][j];
+    }
+    // runs longer than J panels (a length byte >= 4): one warp vote per group
+    if (__any_sync(0xffffffffu, ((q.x | q.y) & 0xFC00FC00u) != 0u)) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long *p = pyr + (bw[k] + (rw[k] & 255u));
+            const int len = (int)(rw[k] >> 8);
+            for (int j = J; j < len; ++j) G += __ldg(p + j);
+        }
     }
 }
 
