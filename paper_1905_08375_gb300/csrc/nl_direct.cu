@@ -743,10 +743,10 @@ __device__ __forceinline__ void x2_column_full(f2_t (&acc)[RB_P], const f2_t (&u
 // ordered by decreasing cost (the sum of the tile's ball sizes, largest first); the last
 // block to finish resets the queue for the next launch on the stream.  A block has 2 TY
 // warps: warp w takes rows 8 (w / 2) .. 8 (w / 2) + 7 of the tile and the column offsets
-// ox < 0 (w even) or ox >= 0 (w odd), so a tile is half the size of one with a warp per row
+// ox even (w even) or odd (w odd), so a tile is half the size of one with a warp per row
 // group and the per-item costs even out across the SMs.  The two partial sums of an output
-// (each over its column offsets in increasing order) are added once, ox < 0 part + ox >= 0
-// part, through shared memory.  The weight table |o|^{-alpha} is copied to shared memory once
+// (each over its column offsets in increasing order) are added once, even part + odd part,
+// through shared memory.  The weight table |o|^{-alpha} is copied to shared memory once
 // per block.
 template <int RM, int TY, int MB, bool KAP = false>
 __global__ void __launch_bounds__(64 * TY, MB)
@@ -834,8 +834,10 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         }
         if (tmin == (1 << 30)) tmin = -1;
         const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-        const int ox_lo = half ? 0 : -rx, ox_hi = half ? rx : -1;
-        for (int ox = ox_lo; ox <= ox_hi; ++ox) {
+        // the two warps of a row group take the even and the odd column offsets (rows of the
+        // two halves within about 1% of each other, where a split by sign differs by the
+        // centre column)
+        for (int ox = -rx + ((rx + half) & 1); ox <= rx; ox += 2) {
             const int ox2 = ox * ox;
             if (ox2 > tmax) continue;
             const int hmax = min(R, isqrt_small(tmax - ox2));
@@ -1074,7 +1076,7 @@ __device__ __forceinline__ void x2s_column(f2_t (&acc)[RB_P], const f2_t (&ui)[R
 }
 
 // Persistent over a largest-first queue of 64 x (TY * RB_P) tiles, with two warps per row group
-// splitting the column offsets by sign and adding their partial sums once, as k_direct2d_x2.
+// splitting the column offsets by parity and adding their partial sums once, as k_direct2d_x2.
 template <int RM, int TY, int MB>
 __global__ void __launch_bounds__(64 * TY, MB)
 k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
@@ -1153,8 +1155,10 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         if (tmin == (1 << 30)) tmin = -1;
         const int cmin = min(tmin, jmin);
         const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-        const int ox_lo = half ? 0 : -rx, ox_hi = half ? rx : -1;
-        for (int ox = ox_lo; ox <= ox_hi; ++ox) {
+        // the two warps of a row group take the even and the odd column offsets (rows of the
+        // two halves within about 1% of each other, where a split by sign differs by the
+        // centre column)
+        for (int ox = -rx + ((rx + half) & 1); ox <= rx; ox += 2) {
             const int ox2 = ox * ox;
             if (ox2 > tmax) continue;
             const int hmax = min(R, isqrt_small(tmax - ox2));
@@ -1265,7 +1269,7 @@ static nl_status x2s_launch_any(nl_plan *p, int var, const DirectArgs &a, const 
 // narrower spread of horizons than the 64 x RB_P of k_direct2d_x2s, so fewer masked rows), the
 // tile holds (u, u') as one 8-byte plane and b, c, thr + 1 as FP32 planes.  Every output's terms
 // are the same FP32 operations in the same order as in k_direct2d_x2s (rows increasing within a
-// column offset, column offsets increasing within each sign, the two signs added once), so each
+// column offset, column offsets increasing within each parity, the two added once), so each
 // right-hand side's result is bit for bit the one k_direct2d_x2s gives for it alone.
 // ---------------------------------------------------------------------------
 struct X2rGrp { f2_t u[4]; float b[4], c[4], t[4]; };
@@ -1377,7 +1381,7 @@ __device__ __forceinline__ void x2r_column(f2_t (&acc)[RB_P], const f2_t (&ui)[R
 }
 
 // Persistent over a largest-first queue of (32 x TY RB_P tile, pair of right-hand sides) items;
-// two warps per row group split the column offsets by sign (as k_direct2d_x2s).
+// two warps per row group split the column offsets by parity (as k_direct2d_x2s).
 template <int RM, int TY, int MB>
 __global__ void __launch_bounds__(64 * TY, MB)
 k_direct2d_x2r(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
@@ -1459,8 +1463,10 @@ k_direct2d_x2r(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         if (tmin == (1 << 30)) tmin = -1;
         const int cmin = min(tmin, jmin);
         const int rx = min(R, isqrt_small(max(tmax, 0)) + 1);
-        const int ox_lo = half ? 0 : -rx, ox_hi = half ? rx : -1;
-        for (int ox = ox_lo; ox <= ox_hi; ++ox) {
+        // the two warps of a row group take the even and the odd column offsets (rows of the
+        // two halves within about 1% of each other, where a split by sign differs by the
+        // centre column)
+        for (int ox = -rx + ((rx + half) & 1); ox <= rx; ox += 2) {
             const int ox2 = ox * ox;
             if (ox2 > tmax) continue;
             const int hmax = min(R, isqrt_small(tmax - ox2));
