@@ -170,16 +170,17 @@ class Workload:
 # kernel, from one ncu --set full capture of that kernel on the workload; None where no capture
 # of the current kernel exists
 PROFILED_TRAFFIC = {
-    "k_direct2d_x2": None,             # no capture of the current kernel yet
+    "k_direct2d_x2": 21.03e6,          # c2, variant <16, 2, 3>
+    "k_direct2d_x2_kappa": 31.22e6,    # c2k, variant <16, 2, 3, kappa>: 29.4 MB read + 1.8 MB written
     "k_direct_pd_x2": 9.48e6,          # c3, <8, 2>
     "k_fast_gather_slots": 178.52e6,   # c2, 174.8 MB read + 3.7 MB written
 }
 
 
-def _alu_roof(kernel, flops, ms, peak, src):
+def _alu_roof(kernel, flops, ms, peak, src, traffic_key=None):
     ach = flops / (ms * 1e-3) / 1e12
     base = kernel.split("<")[0].split(" ")[0]           # the kernel's name without arguments
-    traffic = PROFILED_TRAFFIC.get(base)
+    traffic = PROFILED_TRAFFIC.get(traffic_key or base)
     return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
             "peak_source": src}
@@ -437,8 +438,7 @@ class C2K(Workload):
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         # per term: t = o2/R2, p = p0 + p1 t, ra g - p, times b_j, u_j - u_i, times, add
         roof = _alu_roof("k_direct2d_x2<16,TY,MB,kappa> (paired columns, per-output weights)",
-                         9.0 * nb, t,
-                         *fp32_peak())
+                         9.0 * nb, t, *fp32_peak(), traffic_key="k_direct2d_x2_kappa")
         roof["algorithmic_per_launch"] = f"{9 * nb:.4g} flop (9 per neighbour term)"
         return roof, {"kappa_direct_fp32_ms": round(t, 4)}
 
