@@ -625,6 +625,14 @@ static nl_status plan_apply(void *ctx, const void *in, void *out, int dtype, cud
     return nl_direct_launch(c->p, in, out, c->nrhs, dtype, st);
 }
 
+// converged right-hand sides: the symmetric paired-column kernels skip their work items
+static void plan_set_skip(void *ctx, const double *flags, int stride)
+{
+    nl_plan *p = ((PlanOpCtx *)ctx)->p;
+    p->skip_flags = flags;
+    p->skip_stride = stride;
+}
+
 static nl_status plan_diag(void *ctx, const double *zin, double *d, cudaStream_t st)
 {
     nl_plan *p = ((PlanOpCtx *)ctx)->p;
@@ -664,10 +672,14 @@ static nl_status plan_cg(nl_plan *p, const void *f, void *x, int nrhs, double rt
     op.apply = plan_apply;
     op.diag = plan_diag;
     op.ctx = &ctx;
+    if (!pd && !p->sym_fast) op.set_skip = plan_set_skip;
     op.state = &p->cg;
     op.net = p->net;
     op.net_plan = p;
-    return nl_cg_run(op, f, x, rtol, maxit, precond, hist, cap, count, stats, stream);
+    const nl_status s = nl_cg_run(op, f, x, rtol, maxit, precond, hist, cap, count, stats,
+                                   stream);
+    plan_set_skip(&ctx, nullptr, 0);      // plain applies compute every right-hand side
+    return s;
 }
 
 extern "C" nl_status nl_cg_solve(nl_plan *p, const void *f, void *x, int nrhs, double rtol,

@@ -37,6 +37,8 @@ struct DirectArgs {
     double pd_scale;
     const double *pdext;
     const float *pdg;         // PD, constant horizon: dense [2R+1][2R+1][3] bond tensors
+    const double *skip;       // symmetric paired-column kernels inside CG: right-hand side z
+    int skip_stride;          // needs no result when skip[z * skip_stride] != 0 (else null)
 };
 
 // MODE_KAPPA: the kappa part of the splitting of Sec. 3, weight ra_i |o|^{-alpha} - p(|o|^2/R2_i)
@@ -1105,6 +1107,10 @@ k_direct2d_x2s(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         const int item = s_item;
         if (item >= total) break;
         const int tile = order[item / nrhs], z = item % nrhs;
+        if (a.skip && a.skip[(int64_t)z * a.skip_stride] != 0.0) {
+            __syncthreads();           // every thread has read s_item before it is reused
+            continue;
+        }
         const float *__restrict__ ur = u + (int64_t)z * N;
         const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * (TY * RB_P);
         int jmin = 1 << 30;                          // smallest thr of the staged nodes
@@ -1411,6 +1417,11 @@ k_direct2d_x2r(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         const int item = s_item;
         if (item >= total) break;
         const int tile = order[item / npairs], z = 2 * (item % npairs);
+        if (a.skip && a.skip[(int64_t)z * a.skip_stride] != 0.0 &&
+            a.skip[(int64_t)(z + 1) * a.skip_stride] != 0.0) {
+            __syncthreads();           // every thread has read s_item before it is reused
+            continue;
+        }
         const float *__restrict__ u0 = u + (int64_t)z * N;
         const float *__restrict__ u1 = u0 + N;
         const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * (TY * RB_P);
@@ -2086,7 +2097,9 @@ static nl_status launch_scalar(nl_plan *p, const DirectArgs &a, const T *u, T *L
                 nl_status s2 = x2r_launch_any(p, a, uf, lf, nrhs / 2, st);
                 if (s2 != NL_OK || nrhs % 2 == 0) return s2;
                 const int64_t last = (int64_t)(nrhs - 1) * p->N;
-                return x2s_launch_any(p, p->x2_var, a, uf + last, lf + last, 1, p->x2_order,
+                DirectArgs al = a;             // the last right-hand side is item 0 of this launch
+                if (al.skip) al.skip += (int64_t)(nrhs - 1) * al.skip_stride;
+                return x2s_launch_any(p, p->x2_var, al, uf + last, lf + last, 1, p->x2_order,
                                       p->x2_tiles, &p->x2_blocks, st);
             }
             return x2s_launch_any(p, p->x2_var, a, uf, lf, nrhs, p->x2_order, p->x2_tiles,
@@ -2417,6 +2430,8 @@ static DirectArgs make_args(const nl_plan *p, int dtype)
     for (int m = 0; m < 8; ++m) a.poly[m] = p->poly[m];
     a.pd_scale = p->sigma * pow(p->h, p->d - 1.0);
     a.pdext = p->pdext;
+    a.skip = p->skip_flags;
+    a.skip_stride = p->skip_stride;
     return a;
 }
 

@@ -105,6 +105,8 @@ struct nl_plan {
                                     // kernel variant (timed at plan creation)
     int *x2r_order, *x2r_queue;     // symmetric kernel for pairs of right-hand sides: 32-wide
     int x2r_tiles, x2r_blocks;      // tiles largest first, queue, tile count, grid size
+    const double *skip_flags;       // set by nl_cg_solve for its iterations only: right-hand
+    int skip_stride;                // sides flagged converged need no FP32 operator result
     // per-node device arrays
     int *thr;               // largest integer < R2_i
     int *cnt;               // table entries with o2 <= thr_i (or the symmetric bound)
