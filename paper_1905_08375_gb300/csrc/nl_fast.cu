@@ -1732,6 +1732,105 @@ __global__ void __launch_bounds__(256) k_fast_gather_leafrows_multi(LeafMultiArg
     }
 }
 
+// Leaf rows in 3-D for a constant horizon (every node's leaf set has the same shape): a block
+// of 32 x 8 x 4 outputs (a thread takes one (x, y) and four z) stages, per right-hand side, the
+// leaf-row prefix sums of every row its outputs reach -- (8 + 2 tm) x (4 + 2 tm) rows of
+// 32 + 2 cm + 1 values, x clamped as the run bounds clamp them (0 before the first cell, the
+// last prefix past the end), rows outside the grid as zeros -- in shared memory, then adds each
+// output's rows as two shared-memory reads.  The row list (offsets of the run ends in the staged
+// tile) is formed once per block.  The integers are those of k_fast_gather_leafrows_multi: the
+// same runs, exact sums.
+constexpr int R3_BX = 32, R3_BY = 8, R3_BZ = 4;
+constexpr int R3_MAX_ROWS = 289;      // (2 tm + 1)^2 with tm <= 8
+
+struct Rows3Args {
+    int n, count;
+    int64_t N;
+    const long long *leaf;            // [count][N] leaf-row prefix sums
+    const unsigned char *aux;         // per right-hand side the scale word, aux_stride apart
+    int aux_stride;
+    const double *fastF, *selfS, *selfQ;
+    const float *Fh;
+    double hd;
+    int T4, tm, cm;                   // common threshold; rows |ty|, |tz| <= tm; runs <= cm
+};
+
+__global__ void __launch_bounds__(256) k_fast_gather_rows3c(Rows3Args a, const float *__restrict__ u,
+                                                            float *__restrict__ Lu)
+{
+    extern __shared__ __align__(16) long long s3[];
+    __shared__ int2 s_off[R3_MAX_ROWS];               // per row: (last, before-first) offsets
+    __shared__ int s_nrow;
+    const int n = a.n, tm = a.tm, cm = a.cm;
+    const int SXX = R3_BX + 2 * cm + 1, SYY = R3_BY + 2 * tm, SZZ = R3_BZ + 2 * tm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x0 = blockIdx.x * R3_BX, y0 = blockIdx.y * R3_BY, z0 = blockIdx.z * R3_BZ;
+    if (tid == 0) {
+        int k = 0;
+        for (int tz = -tm; tz <= tm; ++tz) {
+            const int ez = tz == 0 ? 0 : (2 * abs(tz) - 1) * (2 * abs(tz) - 1);
+            for (int ty = -tm; ty <= tm; ++ty) {
+                const int e = ez + (ty == 0 ? 0 : (2 * abs(ty) - 1) * (2 * abs(ty) - 1));
+                if (e > a.T4 || k >= R3_MAX_ROWS) continue;
+                const int c = (isqrt_fast(a.T4 - e) + 1) >> 1;      // run [x - c, x + c]
+                const int row = (tz * SYY + ty) * SXX;
+                s_off[k] = make_int2(row + c, row - c - 1);
+                ++k;
+            }
+        }
+        s_nrow = k;
+    }
+    const int x = x0 + lane, y = y0 + warp;
+    const int zstride = SYY * SXX;
+    const int centre = (tm * SYY + warp + tm) * SXX + lane + cm + 1;     // output (x, y, z0)
+    for (int q = 0; q < a.count; ++q) {
+        const long long *__restrict__ P = a.leaf + (int64_t)q * a.N;
+        __syncthreads();                          // the row list, or the last tile, is done
+        // one warp per staged row, lanes along x; asynchronous 8-byte copies (zero-filled
+        // outside the grid and before the first cell), all in flight before the one wait
+        for (int rz = warp; rz < SYY * SZZ; rz += 8) {
+            const int yy = rz % SYY, zz = rz / SYY;
+            const int gy = y0 - tm + yy, gz = z0 - tm + zz;
+            long long *dst = s3 + rz * SXX;
+            const bool inside = gy >= 0 && gy < n && gz >= 0 && gz < n;
+            const long long *src = inside ? P + (int64_t)n * (gy + (int64_t)n * gz) : P;
+            for (int xx = lane; xx < SXX; xx += 32) {
+                const int gx = x0 - cm - 1 + xx;
+                const bool ok = inside && gx >= 0;
+                const unsigned d = (unsigned)__cvta_generic_to_shared(dst + xx);
+                const long long *g = ok ? src + min(gx, n - 1) : P;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                             ::"r"(d), "l"(g), "r"(ok ? 8 : 0) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const int nrow = s_nrow;
+        long long G[R3_BZ];
+#pragma unroll
+        for (int zo = 0; zo < R3_BZ; ++zo) G[zo] = 0;
+        for (int k = 0; k < nrow; ++k) {
+            const int2 o = s_off[k];
+#pragma unroll
+            for (int zo = 0; zo < R3_BZ; ++zo)
+                G[zo] += s3[centre + zo * zstride + o.x] - s3[centre + zo * zstride + o.y];
+        }
+        const unsigned int *mx = (const unsigned int *)(a.aux + (size_t)q * a.aux_stride);
+        const int sh = fixed_shift_f32(a.N, mx);
+#pragma unroll
+        for (int zo = 0; zo < R3_BZ; ++zo) {
+            const int z = z0 + zo;
+            if (x < n && y < n && z < n) {
+                const int64_t i = x + (int64_t)n * (y + (int64_t)n * z);
+                const int64_t g = (int64_t)q * a.N + i;
+                Lu[g] = fixed_epilogue(G[zo], u[g], a.selfQ[i], a.Fh[i], a.fastF[i], a.selfS[i],
+                                       a.hd, sh);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1914,6 +2013,24 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
         NL_CUDA_TRY(cudaMemcpyAsync(&bits, bw, sizeof(bits), cudaMemcpyDeviceToHost, st));
         NL_CUDA_TRY(cudaStreamSynchronize(st));
         memcpy(&p->fast_bmax, &bits, sizeof(float));
+        // 3-D, constant horizon: the common threshold and the staged gather's tile geometry
+        p->r3_tm = 0;
+        if (d == 3 && p->const_horizon) {
+            int T4 = -1;
+            NL_CUDA_TRY(cudaMemcpy(&T4, p->thr4, sizeof(int), cudaMemcpyDeviceToHost));
+            int tm = 0;
+            while ((2 * (tm + 1) - 1) * (2 * (tm + 1) - 1) <= T4) ++tm;
+            int r0 = 0;
+            while ((r0 + 1) * (r0 + 1) <= T4) ++r0;
+            const int cm = (r0 + 1) >> 1;
+            const size_t smem = sizeof(long long) * (size_t)(R3_BX + 2 * cm + 1) *
+                                (R3_BY + 2 * tm) * (R3_BZ + 2 * tm);
+            if (T4 >= 0 && tm >= 1 && tm <= 8 && smem <= 160 * 1024) {
+                p->r3_T4 = T4;
+                p->r3_tm = tm;
+                p->r3_cm = cm;
+            }
+        }
     }
     NL_CUDA_TRY(cudaGetLastError());
     NL_CUDA_TRY(cudaStreamSynchronize(st));
@@ -2018,6 +2135,37 @@ static cudaError_t step2_panels(nl_plan *p, const float *u, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// the staged 3-D gather for a constant horizon (k_fast_gather_rows3c) where the plan set it up
+static size_t rows3_smem(const nl_plan *p)
+{
+    return sizeof(long long) * (size_t)(R3_BX + 2 * p->r3_cm + 1) * (R3_BY + 2 * p->r3_tm) *
+           (R3_BZ + 2 * p->r3_tm);
+}
+
+static bool rows3_usable(const nl_plan *p)
+{
+    return p->d == 3 && p->r3_tm > 0 && p->n % R3_BX == 0;
+}
+
+static nl_status launch_rows3(nl_plan *p, const long long *leaf, const unsigned char *aux,
+                              int aux_stride, int count, const float *u, float *Lu,
+                              cudaStream_t st)
+{
+    Rows3Args a;
+    a.n = p->n; a.count = count; a.N = p->N;
+    a.leaf = leaf; a.aux = aux; a.aux_stride = aux_stride;
+    a.fastF = p->fastF; a.selfS = p->selfS; a.selfQ = p->selfQ; a.Fh = p->fastFh32;
+    a.hd = std::pow(p->h, 3.0);
+    a.T4 = p->r3_T4; a.tm = p->r3_tm; a.cm = p->r3_cm;
+    const size_t smem = rows3_smem(p);
+    NL_CUDA_TRY(cudaFuncSetAttribute(k_fast_gather_rows3c,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const dim3 grd((unsigned)(p->n / R3_BX), (unsigned)(p->n / R3_BY), (unsigned)(p->n / R3_BZ));
+    k_fast_gather_rows3c<<<grd, 256, smem, st>>>(a, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
 static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_t st)
 {
     prof_mark(p, 0, st);
@@ -2044,7 +2192,11 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
     if (leafrows) {
         if (d == 1) k_fast_gather_leafrows<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_leafrows<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
-        else k_fast_gather_leafrows<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
+        else if (rows3_usable(p)) {
+            const nl_status s3 = launch_rows3(p, pyr + p->lvl_off[L], (const unsigned char *)mx,
+                                              0, 1, u, Lu, st);
+            if (s3 != NL_OK) return s3;
+        } else k_fast_gather_leafrows<3, float><<<gb, 256, 0, st>>>(a, u, Lu);
     } else if (prefix) {
         if (d == 1) k_fast_gather_rowprefix<1, float><<<gb, 256, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_rowprefix<2, float><<<gb, 256, 0, st>>>(a, u, Lu);
@@ -2200,7 +2352,11 @@ static nl_status fast_multi_leafrows(nl_plan *p, const float *u, float *Lu, int 
         float *lr = Lu + (int64_t)r0 * p->N;
         if (p->d == 1) k_fast_gather_leafrows_multi<1, float><<<gb, 256, 0, st>>>(a, ur, lr);
         else if (p->d == 2) k_fast_gather_leafrows_multi<2, float><<<gb, 256, 0, st>>>(a, ur, lr);
-        else k_fast_gather_leafrows_multi<3, float><<<gb, 256, 0, st>>>(a, ur, lr);
+        else if (rows3_usable(p)) {
+            const nl_status s3 = launch_rows3(p, p->leaf_multi, p->aux_multi, AUX_STRIDE, cnt,
+                                              ur, lr, st);
+            if (s3 != NL_OK) return s3;
+        } else k_fast_gather_leafrows_multi<3, float><<<gb, 256, 0, st>>>(a, ur, lr);
         NL_CUDA_TRY(cudaGetLastError());
         prof_mark(p, 2, st);
     }

@@ -197,6 +197,35 @@ def test_multi_rhs_leafrows_bitwise_equal_to_single(d, n, nrhs):
     assert rel_l2(many[-1][idx], ref) <= 2e-6
 
 
+@pytest.mark.parametrize("n,rho,nrhs", [(32, 4.0, 1), (32, 2.3, 3), (64, 4.0, 8),
+                                          (64, 5.7, 2), (32, 1.2, 1)])
+def test_3d_constant_horizon_staged_rows_bitwise(n, rho, nrhs):
+    """3-D constant horizon (the staged leaf-row gather: one tile of prefix rows per block,
+    every node the same run pattern): bitwise equal to the row-prefix and panel routes, for one
+    and several right-hand sides, and against the FP64 oracle."""
+    L = int(np.log2(n))
+    N = n ** 3
+    rng = np.random.default_rng(int(10 * rho) + n + nrhs)
+    a = np.exp(0.3 * rng.standard_normal(N))
+    u = rng.standard_normal((nrhs, N))
+    outs = {}
+    for name, variant in (("leaf", nl.NL_FAST_LEAFROWS), ("prefix", nl.NL_FAST_ROWPREFIX),
+                          ("panels", nl.NL_FAST_PANELS)):
+        plan = nl.nl_plan_create(3, n, rho / n, family=nl.NL_POLY, alpha=1.0, K=0,
+                                 coef=nl.NL_COEF_XY, a=a, fast_variant=variant)
+        outs[name] = run_fast(plan, u, torch.float32)
+        if name == "leaf" and nrhs > 1:
+            for r in (0, nrhs - 1):
+                np.testing.assert_array_equal(outs[name][r], run_fast(plan, u[r], torch.float32))
+        plan.close()
+    np.testing.assert_array_equal(outs["leaf"], outs["prefix"])
+    np.testing.assert_array_equal(outs["leaf"], outs["panels"])
+    idx = sample_idx(N, 2000, seed=n)
+    ref = oracle.fast_leafset(u[-1], 3, L, rho / n, K=0, alpha=1.0, coef=oracle.COEF_XY, a=a,
+                              idx=idx)
+    assert rel_l2(outs["leaf"].reshape(nrhs, N)[-1][idx], ref) <= 2e-6
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("K", [1, 2, 3])
 @pytest.mark.parametrize("coef", [nl.NL_COEF_NONE, nl.NL_COEF_XY])
