@@ -1734,14 +1734,16 @@ __global__ void __launch_bounds__(256) k_fast_gather_leafrows_multi(LeafMultiArg
 
 // Leaf rows in 3-D for a constant horizon (every node's leaf set has the same shape): a block
 // of 32 x 8 x 4 outputs (a thread takes one (x, y) and four z) stages, per right-hand side, the
-// leaf-row prefix sums of every row its outputs reach -- (8 + 2 tm) x (4 + 2 tm) rows of
-// 32 + 2 cm + 1 values, x clamped as the run bounds clamp them (0 before the first cell, the
-// last prefix past the end), rows outside the grid as zeros -- in shared memory, then adds each
-// output's rows as two shared-memory reads.  The row list (offsets of the run ends in the staged
-// tile) is formed once per block.  The integers are those of k_fast_gather_leafrows_multi: the
-// same runs, exact sums.
+// leaf-row prefix sums of every row its outputs reach -- (8 + 2 TM) x (4 + 2 TM) rows of
+// 32 + 2 TM + 1 values, x clamped as the run bounds clamp them (0 before the first cell, the
+// last prefix past the end), rows outside the grid as zeros -- in shared memory with
+// asynchronous copies, then adds each output's rows as two shared-memory reads.  TM is both
+// the row reach (rows |ty|, |tz| <= TM) and the longest run ((isqrt(T4) + 1) / 2 cells each
+// side), so the tile geometry and every row's position in it are compile-time constants; only
+// a row's run length c (its chord, -1 outside the ball) is read, once for the four z-outputs.
+// The integers are those of k_fast_gather_leafrows_multi: the same runs, exact sums.
 constexpr int R3_BX = 32, R3_BY = 8, R3_BZ = 4;
-constexpr int R3_MAX_ROWS = 289;      // (2 tm + 1)^2 with tm <= 8
+constexpr int R3_TM_MAX = 8;
 
 struct Rows3Args {
     int n, count;
@@ -1752,50 +1754,42 @@ struct Rows3Args {
     const double *fastF, *selfS, *selfQ;
     const float *Fh;
     double hd;
-    int T4, tm, cm;                   // common threshold; rows |ty|, |tz| <= tm; runs <= cm
+    int T4;                           // the common threshold (half units)
 };
 
+template <int TM>
 __global__ void __launch_bounds__(256) k_fast_gather_rows3c(Rows3Args a, const float *__restrict__ u,
                                                             float *__restrict__ Lu)
 {
+    constexpr int SXX = R3_BX + 2 * TM + 1, SYY = R3_BY + 2 * TM, SZZ = R3_BZ + 2 * TM;
+    constexpr int W = 2 * TM + 1;
     extern __shared__ __align__(16) long long s3[];
-    __shared__ int2 s_off[R3_MAX_ROWS];               // per row: (last, before-first) offsets
-    __shared__ int s_nrow;
-    const int n = a.n, tm = a.tm, cm = a.cm;
-    const int SXX = R3_BX + 2 * cm + 1, SYY = R3_BY + 2 * tm, SZZ = R3_BZ + 2 * tm;
+    __shared__ int s_c[W * W];                        // run half-length per (tz, ty), -1: none
+    const int n = a.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * R3_BX, y0 = blockIdx.y * R3_BY, z0 = blockIdx.z * R3_BZ;
-    if (tid == 0) {
-        int k = 0;
-        for (int tz = -tm; tz <= tm; ++tz) {
-            const int ez = tz == 0 ? 0 : (2 * abs(tz) - 1) * (2 * abs(tz) - 1);
-            for (int ty = -tm; ty <= tm; ++ty) {
-                const int e = ez + (ty == 0 ? 0 : (2 * abs(ty) - 1) * (2 * abs(ty) - 1));
-                if (e > a.T4 || k >= R3_MAX_ROWS) continue;
-                const int c = (isqrt_fast(a.T4 - e) + 1) >> 1;      // run [x - c, x + c]
-                const int row = (tz * SYY + ty) * SXX;
-                s_off[k] = make_int2(row + c, row - c - 1);
-                ++k;
-            }
-        }
-        s_nrow = k;
+    for (int k = tid; k < W * W; k += 256) {
+        const int tz = k / W - TM, ty = k % W - TM;
+        const int e = (tz == 0 ? 0 : (2 * abs(tz) - 1) * (2 * abs(tz) - 1)) +
+                      (ty == 0 ? 0 : (2 * abs(ty) - 1) * (2 * abs(ty) - 1));
+        s_c[k] = e <= a.T4 ? (isqrt_fast(a.T4 - e) + 1) >> 1 : -1;
     }
     const int x = x0 + lane, y = y0 + warp;
-    const int zstride = SYY * SXX;
-    const int centre = (tm * SYY + warp + tm) * SXX + lane + cm + 1;     // output (x, y, z0)
+    const long long *centre = s3 + (TM * SYY + warp + TM) * SXX + lane + TM + 1;   // (x, y, z0)
     for (int q = 0; q < a.count; ++q) {
         const long long *__restrict__ P = a.leaf + (int64_t)q * a.N;
-        __syncthreads();                          // the row list, or the last tile, is done
+        __syncthreads();                          // the chords, or the last tile, are done
         // one warp per staged row, lanes along x; asynchronous 8-byte copies (zero-filled
         // outside the grid and before the first cell), all in flight before the one wait
         for (int rz = warp; rz < SYY * SZZ; rz += 8) {
             const int yy = rz % SYY, zz = rz / SYY;
-            const int gy = y0 - tm + yy, gz = z0 - tm + zz;
+            const int gy = y0 - TM + yy, gz = z0 - TM + zz;
             long long *dst = s3 + rz * SXX;
             const bool inside = gy >= 0 && gy < n && gz >= 0 && gz < n;
             const long long *src = inside ? P + (int64_t)n * (gy + (int64_t)n * gz) : P;
+#pragma unroll
             for (int xx = lane; xx < SXX; xx += 32) {
-                const int gx = x0 - cm - 1 + xx;
+                const int gx = x0 - TM - 1 + xx;
                 const bool ok = inside && gx >= 0;
                 const unsigned d = (unsigned)__cvta_generic_to_shared(dst + xx);
                 const long long *g = ok ? src + min(gx, n - 1) : P;
@@ -1806,15 +1800,22 @@ __global__ void __launch_bounds__(256) k_fast_gather_rows3c(Rows3Args a, const f
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        const int nrow = s_nrow;
         long long G[R3_BZ];
 #pragma unroll
         for (int zo = 0; zo < R3_BZ; ++zo) G[zo] = 0;
-        for (int k = 0; k < nrow; ++k) {
-            const int2 o = s_off[k];
 #pragma unroll
-            for (int zo = 0; zo < R3_BZ; ++zo)
-                G[zo] += s3[centre + zo * zstride + o.x] - s3[centre + zo * zstride + o.y];
+        for (int tz = -TM; tz <= TM; ++tz) {
+#pragma unroll
+            for (int ty = -TM; ty <= TM; ++ty) {
+                const int c = s_c[(tz + TM) * W + ty + TM];
+                if (c >= 0) {
+                    const long long *row = centre + (tz * SYY + ty) * SXX;
+                    const long long *hi = row + c, *lo = row - c - 1;
+#pragma unroll
+                    for (int zo = 0; zo < R3_BZ; ++zo)
+                        G[zo] += hi[zo * SYY * SXX] - lo[zo * SYY * SXX];
+                }
+            }
         }
         const unsigned int *mx = (const unsigned int *)(a.aux + (size_t)q * a.aux_stride);
         const int sh = fixed_shift_f32(a.N, mx);
@@ -1836,6 +1837,8 @@ __global__ void __launch_bounds__(256) k_fast_gather_rows3c(Rows3Args a, const f
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+static size_t rows3_smem(int tm);
+
 static int moments_count(int d, int K)
 {
     int M = 0;
@@ -2018,17 +2021,14 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
         if (d == 3 && p->const_horizon) {
             int T4 = -1;
             NL_CUDA_TRY(cudaMemcpy(&T4, p->thr4, sizeof(int), cudaMemcpyDeviceToHost));
-            int tm = 0;
-            while ((2 * (tm + 1) - 1) * (2 * (tm + 1) - 1) <= T4) ++tm;
+            // rows |t| <= tm with (2t - 1)^2 <= T4, runs of at most (isqrt(T4) + 1) / 2 cells
+            // each side: the same bound
             int r0 = 0;
             while ((r0 + 1) * (r0 + 1) <= T4) ++r0;
-            const int cm = (r0 + 1) >> 1;
-            const size_t smem = sizeof(long long) * (size_t)(R3_BX + 2 * cm + 1) *
-                                (R3_BY + 2 * tm) * (R3_BZ + 2 * tm);
-            if (T4 >= 0 && tm >= 1 && tm <= 8 && smem <= 160 * 1024) {
+            const int tm = (r0 + 1) >> 1;
+            if (T4 >= 1 && tm >= 1 && tm <= R3_TM_MAX && rows3_smem(tm) <= 160 * 1024) {
                 p->r3_T4 = T4;
                 p->r3_tm = tm;
-                p->r3_cm = cm;
             }
         }
     }
@@ -2136,15 +2136,27 @@ static cudaError_t step2_panels(nl_plan *p, const float *u, cudaStream_t st)
 }
 
 // the staged 3-D gather for a constant horizon (k_fast_gather_rows3c) where the plan set it up
-static size_t rows3_smem(const nl_plan *p)
+static size_t rows3_smem(int tm)
 {
-    return sizeof(long long) * (size_t)(R3_BX + 2 * p->r3_cm + 1) * (R3_BY + 2 * p->r3_tm) *
-           (R3_BZ + 2 * p->r3_tm);
+    return sizeof(long long) * (size_t)(R3_BX + 2 * tm + 1) * (R3_BY + 2 * tm) * (R3_BZ + 2 * tm);
 }
 
 static bool rows3_usable(const nl_plan *p)
 {
     return p->d == 3 && p->r3_tm > 0 && p->n % R3_BX == 0;
+}
+
+template <int TM>
+static nl_status launch_rows3_t(const nl_plan *p, const Rows3Args &a, const float *u, float *Lu,
+                                cudaStream_t st)
+{
+    const size_t smem = rows3_smem(TM);
+    NL_CUDA_TRY(cudaFuncSetAttribute(k_fast_gather_rows3c<TM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const dim3 grd((unsigned)(p->n / R3_BX), (unsigned)(p->n / R3_BY), (unsigned)(p->n / R3_BZ));
+    k_fast_gather_rows3c<TM><<<grd, 256, smem, st>>>(a, u, Lu);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
 }
 
 static nl_status launch_rows3(nl_plan *p, const long long *leaf, const unsigned char *aux,
@@ -2156,14 +2168,17 @@ static nl_status launch_rows3(nl_plan *p, const long long *leaf, const unsigned 
     a.leaf = leaf; a.aux = aux; a.aux_stride = aux_stride;
     a.fastF = p->fastF; a.selfS = p->selfS; a.selfQ = p->selfQ; a.Fh = p->fastFh32;
     a.hd = std::pow(p->h, 3.0);
-    a.T4 = p->r3_T4; a.tm = p->r3_tm; a.cm = p->r3_cm;
-    const size_t smem = rows3_smem(p);
-    NL_CUDA_TRY(cudaFuncSetAttribute(k_fast_gather_rows3c,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const dim3 grd((unsigned)(p->n / R3_BX), (unsigned)(p->n / R3_BY), (unsigned)(p->n / R3_BZ));
-    k_fast_gather_rows3c<<<grd, 256, smem, st>>>(a, u, Lu);
-    NL_CUDA_TRY(cudaGetLastError());
-    return NL_OK;
+    a.T4 = p->r3_T4;
+    switch (p->r3_tm) {
+    case 1: return launch_rows3_t<1>(p, a, u, Lu, st);
+    case 2: return launch_rows3_t<2>(p, a, u, Lu, st);
+    case 3: return launch_rows3_t<3>(p, a, u, Lu, st);
+    case 4: return launch_rows3_t<4>(p, a, u, Lu, st);
+    case 5: return launch_rows3_t<5>(p, a, u, Lu, st);
+    case 6: return launch_rows3_t<6>(p, a, u, Lu, st);
+    case 7: return launch_rows3_t<7>(p, a, u, Lu, st);
+    default: return launch_rows3_t<8>(p, a, u, Lu, st);
+    }
 }
 
 static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_t st)

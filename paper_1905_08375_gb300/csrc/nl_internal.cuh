@@ -135,8 +135,8 @@ struct nl_plan {
                                     // apply (fixed-point scale), word 1 a block ticket, then
                                     // NL_FAST_PARTS per-block maxima (floats, from byte 16)
     float fast_bmax;                // FP32 integer route: max |b| (bounds |u b| by max |u|)
-    int r3_T4, r3_tm, r3_cm;        // 3-D constant horizon: the common threshold, the row reach
-                                    // and the longest run of the staged leaf-row gather (tm 0: off)
+    int r3_T4, r3_tm;               // 3-D constant horizon: the common threshold and the row
+                                    // reach (= longest run) of the staged gather (tm 0: off)
     unsigned *slot_base;            // NL_FAST_PANELS, 1-D/2-D with n >= 32: the stored
     unsigned short *slot_rec;       // decomposition, warp-aligned slots (per-warp base
     int64_t *slot_woff;             // positions, per-node 16-bit records), per-warp slot
