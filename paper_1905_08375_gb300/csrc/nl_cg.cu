@@ -429,13 +429,9 @@ static nl_status enqueue_chunk(nl_cg_op &op, const CgArgs &a, bool flex, int ite
         k_cg_dot<<<grid, RB, 0, st>>>(a);
         if (flex) {
             k_cg_update<true><<<grid, RB, 0, st>>>(a);
-            // the network's last kernel writes the r.z partials where it can (same sums)
-            NlRzPartials rzp{ a.seg_off ? nullptr : a.part + (size_t)P_RZ * a.nrhs * NB, a.nb,
-                              NB, false };
-            s = nl_net_apply_launch(op.net, op.net_plan, a.r, a.z, a.nrhs, st,
-                                    a.seg_off ? nullptr : &rzp);
+            s = nl_net_apply_launch(op.net, op.net_plan, a.r, a.z, a.nrhs, st);
             if (s != NL_OK) return s;
-            if (!rzp.done) k_cg_rz<<<grid, RB, 0, st>>>(a);
+            k_cg_rz<<<grid, RB, 0, st>>>(a);
             k_cg_dir<true><<<grid, RB, 0, st>>>(a);
         } else {
             k_cg_update<false><<<grid, RB, 0, st>>>(a);

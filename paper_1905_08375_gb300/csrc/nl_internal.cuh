@@ -222,12 +222,8 @@ nl_status nl_batch_fill_inst(nl_plan *const *plans, int count, const int64_t *of
                              int dtype, int kind, void *host_out, int64_t *total_out);
 size_t nl_batch_inst_bytes();
 void nl_invert_launch(int64_t n, double *d, cudaStream_t st);
-// CG's partial sums of r.z written by the network's last kernel (two-level form): per right-hand
-// side nb blocks, block k of right-hand side b writing part[b * stride + k], with the thread-to-
-// element mapping and block reduction of the CG kernels; done is set when they were written
-struct NlRzPartials { double *part; int nb; int stride; bool done; };
 nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,
-                              cudaStream_t st, NlRzPartials *rz = nullptr);
+                              cudaStream_t st);
 nl_status nl_net_reserve(nl_net *n, nl_plan *p, int nrhs, cudaStream_t st);
 bool nl_net_valid(const nl_net *n);
 // changes whenever a buffer address or a launch argument of the network's apply changes

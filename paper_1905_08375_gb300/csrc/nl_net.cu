@@ -460,38 +460,6 @@ __global__ void k_prolong_jacobi(const double *__restrict__ r, const double *__r
     }
 }
 
-// The same z, with CG's partial sums of r.z: per right-hand side nb blocks over its elements in
-// the CG kernels' grid-stride order, reduced as they reduce (so the sums are those the separate
-// r.z kernel forms from the stored z)
-__global__ void __launch_bounds__(256) k_prolong_jacobi_rz(const double *__restrict__ r,
-                                                          const double *__restrict__ dinv,
-                                                          const float *__restrict__ zc, int n,
-                                                          int blk, int nc, double gamma,
-                                                          double *__restrict__ z, int nb,
-                                                          double *__restrict__ part, int stride)
-{
-    __shared__ double sh[8];
-    const int b = blockIdx.y;
-    const int64_t N = (int64_t)n * n;
-    double rz = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)256 + threadIdx.x; k < N; k += (int64_t)nb * 256) {
-        const int y = (int)(k / n), x = (int)(k % n);
-        const size_t g = (size_t)b * N + k;
-        const double zv = dinv[k] * r[g] + gamma * (double)zc[(size_t)b * nc * nc + (y / blk) * nc + x / blk];
-        z[g] = zv;
-        rz += r[g] * zv;
-    }
-    for (int o = 16; o > 0; o >>= 1) rz += __shfl_down_sync(0xffffffffu, rz, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = rz;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double t = (threadIdx.x < 8) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) part[(size_t)b * stride + blockIdx.x] = t;
-    }
-}
-
 // z = x + gamma P zc (FP32, training; x = D^{-1} r in scaled units)
 __global__ void k_prolong_add(const float *__restrict__ x, const float *__restrict__ zc, int n,
                               int blk, int nc, float gamma, float *__restrict__ z)
@@ -1066,9 +1034,8 @@ static nl_status ensure_gram(nl_net *n, int nc, cudaStream_t st)
 }
 
 nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z, int nrhs,
-                              cudaStream_t st, NlRzPartials *rz)
+                              cudaStream_t st)
 {
-    if (rz) rz->done = false;
     const double *dinv = nullptr;
     nl_status s = plan_dinv(p, st, &dinv);
     if (s != NL_OK) return s;
@@ -1091,14 +1058,6 @@ nl_status nl_net_apply_launch(nl_net *n, nl_plan *p, const double *r, double *z,
             zc = t1 + 32 * cb;
             chain_forward(n, rc, a1, a2, u, nrhs, nc, st);
             chain_adjoint(n, u, t2, t1, zc, nrhs, nc, st);
-        }
-        if (rz) {
-            k_prolong_jacobi_rz<<<dim3((unsigned)rz->nb, nrhs), 256, 0, st>>>(
-                r, dinv, zc, p->n, n->block, nc, two_level_gamma(n, p), z, rz->nb, rz->part,
-                rz->stride);
-            NL_CUDA_TRY(cudaGetLastError());
-            rz->done = true;
-            return NL_OK;
         }
         const unsigned gx = (unsigned)((p->N + 255) / 256 < 1024 ? (p->N + 255) / 256 : 1024);
         k_prolong_jacobi<<<dim3(gx, nrhs), 256, 0, st>>>(r, dinv, zc, p->n, n->block, nc,
