@@ -31,6 +31,7 @@ constexpr int RB = 256;     // threads per reduction block
 constexpr int NB = 152;     // reduction blocks per right-hand side at most (one per SM)
 constexpr int CG_GRID_WAVES = 2;   // uniform segments: about CG_GRID_WAVES x NB blocks in all
 constexpr int CHUNK = 16;   // iterations per captured graph
+constexpr int CHUNK_TAIL = 4;   // iterations per graph once convergence is predicted within CHUNK
 
 // per right-hand side scalars
 enum { S_RZ = 0, S_FF, S_RR, S_CONV, S_IT, S_TRUE, S_COUNT = 8 };
@@ -358,6 +359,7 @@ void nl_invert_launch(int64_t n, double *d, cudaStream_t st)
 nl_status nl_cg_state_release(nl_cg_state *c)
 {
     if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+    if (c->graph_exec_tail) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec_tail);
     if (c->ws) cudaFree(c->ws);
     if (c->ws32) cudaFree(c->ws32);
     if (c->red) cudaFree(c->red);
@@ -525,11 +527,13 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
                           (op.net && c->graph_net_gen != nl_net_generation(op.net)))) {
         cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
         c->graph_exec = nullptr;
+        if (c->graph_exec_tail) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec_tail);
+        c->graph_exec_tail = nullptr;
     }
-    if (!c->graph_exec) {
+    auto capture = [&](int iters_in_graph, void **out) -> nl_status {
         cudaGraph_t g = nullptr;
         NL_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        nl_status cs = enqueue_chunk(op, a, flex, CHUNK, st);
+        nl_status cs = enqueue_chunk(op, a, flex, iters_in_graph, st);
         cudaError_t ce = cudaStreamEndCapture(st, &g);
         if (cs != NL_OK) { if (g) cudaGraphDestroy(g); return cs; }
         if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaStreamEndCapture");
@@ -537,7 +541,18 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
         ce = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) return nl_cuda_fail(ce, "cudaGraphInstantiate");
+        *out = ge;
+        return NL_OK;
+    };
+    if (!c->graph_exec) {
+        void *ge = nullptr, *gt = nullptr;
+        if ((s = capture(CHUNK, &ge)) != NL_OK) return s;
+        if ((s = capture(CHUNK_TAIL, &gt)) != NL_OK) {
+            cudaGraphExecDestroy((cudaGraphExec_t)ge);
+            return s;
+        }
         c->graph_exec = ge;
+        c->graph_exec_tail = gt;
         c->graph_nrhs = nrhs;
         c->graph_f = f;
         c->graph_x = x;
@@ -551,9 +566,16 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
     int iters = 0, restarts = 0, snaps = 0;
     bool conv_all = false;
     const int64_t snap_len = op.per ? op.per : len;
+    // shorter chunks once the recursive residual's decay predicts convergence within CHUNK
+    // iterations (never with history snapshots, which keep the CHUNK cadence)
+    bool tail = false;
+    double prev_ratio = 0.0;
+    int last_chunk = CHUNK;
     for (;;) {
-        NL_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, st));
-        iters += CHUNK;
+        last_chunk = tail ? CHUNK_TAIL : CHUNK;
+        NL_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)(tail ? c->graph_exec_tail : c->graph_exec),
+                                    st));
+        iters += last_chunk;
         if (hist && snaps < cap) {
             NL_CUDA_TRY(cudaMemcpyAsync(hist + (size_t)snaps * snap_len, a.x,
                                         snap_len * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -564,9 +586,26 @@ nl_status nl_cg_run(nl_cg_op &op, const void *f, void *x, double rtol, int maxit
         NL_CUDA_TRY(cudaEventRecord(c->ev, st));
         if ((s = wait_bounded(c)) != NL_OK) return s;
         bool all = true;
-        for (int r = 0; r < nrhs; ++r) all = all && h[r * S_COUNT + S_CONV] != 0.0;
+        double ratio = 0.0;                  // largest r.r / f.f over the unconverged
+        for (int r = 0; r < nrhs; ++r) {
+            const double *hr = h + (size_t)r * S_COUNT;
+            if (hr[S_CONV] == 0.0) {
+                all = false;
+                if (hr[S_FF] > 0.0) ratio = fmax(ratio, hr[S_RR] / hr[S_FF]);
+            }
+        }
         const bool out_of_budget = iters >= maxit;
-        if (!all && !out_of_budget) continue;
+        if (!all && !out_of_budget) {
+            if (!hist && !tail && prev_ratio > 0.0 && ratio > 0.0 && ratio < prev_ratio) {
+                const double per_it = std::log(ratio / prev_ratio) / last_chunk;   // < 0
+                const double need = std::log(a.tol * a.tol / ratio) / per_it;
+                if (need < CHUNK) tail = true;
+            }
+            prev_ratio = ratio;
+            continue;
+        }
+        tail = false;
+        prev_ratio = 0.0;
         // true FP64 residual f + L x
         s = op.apply(op.ctx, a.x, a.q64, NL_F64, st);
         if (s != NL_OK) return s;

@@ -38,7 +38,8 @@ struct nl_cg_state {
     double *host; size_t host_elems;
     cudaStream_t stream;
     cudaEvent_t ev;
-    void *graph_exec;               // cudaGraphExec_t
+    void *graph_exec;               // cudaGraphExec_t: CHUNK iterations
+    void *graph_exec_tail;          // the same for CHUNK_TAIL iterations (near convergence)
     int graph_nrhs;
     const void *graph_f, *graph_x;
     double graph_tol;
