@@ -1115,7 +1115,7 @@ def cg_residuals(cgw, outs):
 
 
 # ---------------------------------------------------------------------------
-# drivers
+# rank aggregation and the timed run
 # ---------------------------------------------------------------------------
 def max_over_ranks(x, device):
     """The largest of the ranks' values of x, returned on every rank (all-reduce MAX)."""
