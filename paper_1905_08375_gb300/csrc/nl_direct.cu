@@ -486,6 +486,20 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
     return r;
 }
 
+// asynchronous 4-byte global -> shared copy (zero-filled when !ok), and the wait for all of a
+// thread's outstanding copies
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ int isqrt_small(int x)   // floor(sqrt(x)), 0 <= x < 2^24
 {
     int h = (int)sqrtf((float)x);
@@ -781,17 +795,22 @@ k_direct2d_x2(DirectArgs a, const float *__restrict__ gtab, const float *__restr
         const int tile = order[item / nrhs], z = item % nrhs;
         const float *__restrict__ ur = u + (int64_t)z * N;
         const int x0 = (tile % tiles_x) * 64, y0 = (tile / tiles_x) * (TY * RB_P);
-        for (int e = tid; e < SX * SY; e += 64 * TY) {
-            const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
-            float uv = 0.f, bv = 0.f;
-            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-                const int64_t j = gx + (int64_t)n * gy;
-                uv = ur[j];
-                bv = bb[j];
+        // the halo tile by asynchronous 4-byte copies, one warp per tile row and the lanes along
+        // x, zero-filled off the grid: every copy of the tile is in flight before the one wait
+        for (int row = tid >> 5; row < SY; row += 2 * TY) {
+            const int gy = y0 - RM + row;
+            const bool rin = gy >= 0 && gy < n;
+            const float *__restrict__ urow = ur + (int64_t)n * (rin ? gy : 0);
+            const float *__restrict__ brow = bb + (int64_t)n * (rin ? gy : 0);
+            for (int xx = tid & 31; xx < SX; xx += 32) {
+                const int gx = x0 - RM + xx;
+                const bool ok = rin && gx >= 0 && gx < n;
+                const int cx = ok ? gx : 0;
+                cp_async4(su + row * SX + xx, urow + cx, ok);
+                cp_async4(sb + row * SX + xx, brow + cx, ok);
             }
-            su[e] = uv;
-            sb[e] = bv;
         }
+        cp_async_wait_all();
         __syncthreads();
 
         const int xa = x0 + 2 * threadIdx.x, xb = xa + 1;
