@@ -1411,13 +1411,14 @@ template <int RM, int TY, int MB>
 __global__ void __launch_bounds__(64 * TY, MB)
 k_direct2d_x2r(DirectArgs a, const float *__restrict__ gtab, const float *__restrict__ u,
                float *__restrict__ Lu, const int *__restrict__ order, int ntiles, int tiles_x,
-               int npairs, int *__restrict__ queue)
+               int npairs, int *__restrict__ queue, const float *__restrict__ cpl,
+               const float *__restrict__ tpl, const int *__restrict__ tile_jmin)
 {
     constexpr int SX = 32 + 2 * RM;
     constexpr int SY = TY * RB_P + 2 * RM + 1;
     constexpr int PL = SX * SY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_item, s_jmin[2 * TY];
+    __shared__ int s_item;
     f2_t *su2 = reinterpret_cast<f2_t *>(smem_raw);          // (u, u') of the pair
     float *sb = reinterpret_cast<float *>(su2 + PL);         // b | c | thr + 1
     f2_t *sx = su2;                                          // half sums, over the tile once read
@@ -1444,30 +1445,29 @@ k_direct2d_x2r(DirectArgs a, const float *__restrict__ gtab, const float *__rest
         const float *__restrict__ u0 = u + (int64_t)z * N;
         const float *__restrict__ u1 = u0 + N;
         const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * (TY * RB_P);
-        int jmin = 1 << 30;
-        for (int e = tid; e < PL; e += 64 * TY) {
-            const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
-            float v0 = 0.f, v1 = 0.f, bv = 0.f, cv = 0.f, tv = 0.f;
-            if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-                const int64_t j = gx + (int64_t)n * gy;
-                const int tj = a.thr[j];
-                v0 = u0[j];
-                v1 = u1[j];
-                bv = bb[j];
-                cv = whv[j] * bv;
-                tv = (float)(tj + 1);
-                jmin = min(jmin, tj);
+        // the tile by asynchronous 4-byte copies (one warp per tile row, zero-filled off the
+        // grid): u and u' into the two halves of the pair plane, b, c = (W/2) b and thr + 1 from
+        // their plan planes; the smallest threshold of the staged nodes is a plan constant
+        for (int row = tid >> 5; row < SY; row += 2 * TY) {
+            const int gy = y0 - RM + row;
+            const bool rin = gy >= 0 && gy < n;
+            const int64_t roff = (int64_t)n * (rin ? gy : 0);
+            for (int xx = tid & 31; xx < SX; xx += 32) {
+                const int gx = x0 - RM + xx;
+                const bool ok = rin && gx >= 0 && gx < n;
+                const int64_t j = roff + (ok ? gx : 0);
+                const int e = row * SX + xx;
+                float *pu = reinterpret_cast<float *>(su2 + e);
+                cp_async4(pu, u0 + j, ok);
+                cp_async4(pu + 1, u1 + j, ok);
+                cp_async4(sb + e, bb + j, ok);
+                cp_async4(sb + e + PL, cpl + j, ok);
+                cp_async4(sb + e + 2 * PL, tpl + j, ok);
             }
-            su2[e] = f2_pack(v0, v1);
-            sb[e] = bv;
-            sb[e + PL] = cv;
-            sb[e + 2 * PL] = tv;
         }
-        jmin = __reduce_min_sync(0xffffffffu, jmin);
-        if (threadIdx.x == 0) s_jmin[threadIdx.y] = jmin;
+        const int jmin = tile_jmin[tile];
+        cp_async_wait_all();
         __syncthreads();
-#pragma unroll
-        for (int w = 0; w < 2 * TY; ++w) jmin = min(jmin, s_jmin[w]);
         const int x = x0 + threadIdx.x;
         const int ybase = y0 + grp * RB_P;
         f2_t ui[RB_P], acc[RB_P];
@@ -1570,7 +1570,8 @@ static nl_status launch_x2r_t(nl_plan *p, const DirectArgs &a, const float *u, f
     }
     const int64_t blocks = std::min<int64_t>(p->x2r_blocks, items);
     kern<<<(unsigned)blocks, blk, smem, st>>>(a, p->rb_g32, u, Lu, p->x2r_order, p->x2r_tiles,
-                                              tiles_x, npairs, p->x2r_queue);
+                                              tiles_x, npairs, p->x2r_queue, p->x2r_c32,
+                                              p->x2r_tp1, p->x2r_jmin);
     NL_CUDA_TRY(cudaGetLastError());
     return NL_OK;
 }
@@ -1583,6 +1584,41 @@ static nl_status x2r_launch_any(nl_plan *p, const DirectArgs &a, const float *u,
     if (p->Rmax <= 16) return launch_x2r_t<16>(p, a, u, Lu, npairs, st);
     if (p->Rmax <= 24) return launch_x2r_t<24>(p, a, u, Lu, npairs, st);
     return launch_x2r_t<32>(p, a, u, Lu, npairs, st);
+}
+
+// Plan planes of the pair kernel's tile: c = (W/2) b and thr + 1 per node (the values the tile
+// holds, as the kernel used to form them), and per 32 x rows tile the smallest threshold of the
+// nodes its halo tile stages (columns x0 - rm .. x0 + 31 + rm, rows y0 - rm .. y0 + rows + rm).
+__global__ void k_x2r_planes(int64_t N, const float *__restrict__ wh, const float *__restrict__ b,
+                             const int *__restrict__ thr, float *__restrict__ c,
+                             float *__restrict__ t)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    c[i] = wh[i] * b[i];
+    t[i] = (float)(thr[i] + 1);
+}
+
+__global__ void __launch_bounds__(256) k_x2r_tile_jmin(int n, int tiles_x, int rows, int rm,
+                                                       const int *__restrict__ thr,
+                                                       int *__restrict__ out)
+{
+    __shared__ int s_w[8];
+    const int tile = blockIdx.x;
+    const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * rows;
+    const int sx = 32 + 2 * rm, sy = rows + 2 * rm + 1;
+    int m = 1 << 30;
+    for (int e = threadIdx.x; e < sx * sy; e += blockDim.x) {
+        const int gx = x0 - rm + e % sx, gy = y0 - rm + e / sx;
+        if (gx >= 0 && gx < n && gy >= 0 && gy < n) m = min(m, thr[gx + (int64_t)n * gy]);
+    }
+    m = __reduce_min_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = min(m, s_w[w]);
+        out[tile] = m;
+    }
 }
 
 // Tile order for the paired-column kernel: the cost of a 64 x rows tile is the sum of its
@@ -2784,6 +2820,18 @@ nl_status nl_direct_plan_init(nl_plan *p, cudaStream_t st)
         const nl_status so = x2_order_for(p, X2R_TY, &p->x2r_order, &p->x2r_tiles, st, 32);
         if (so != NL_OK) return so;
         p->device_bytes += (size_t)p->x2r_tiles * sizeof(int) + 2 * sizeof(int);
+        const int rm = p->Rmax <= 4 ? 4 : p->Rmax <= 8 ? 8 : p->Rmax <= 16 ? 16 : p->Rmax <= 24 ? 24 : 32;
+        NL_CUDA_TRY(cudaMalloc(&p->x2r_c32, p->N * sizeof(float)));
+        NL_CUDA_TRY(cudaMalloc(&p->x2r_tp1, p->N * sizeof(float)));
+        NL_CUDA_TRY(cudaMalloc(&p->x2r_jmin, (size_t)p->x2r_tiles * sizeof(int)));
+        p->device_bytes += 2 * p->N * sizeof(float) + (size_t)p->x2r_tiles * sizeof(int);
+        k_x2r_planes<<<(unsigned)((p->N + 255) / 256), 256, 0, st>>>(p->N, p->wh32, p->b32, p->thr,
+                                                                    p->x2r_c32, p->x2r_tp1);
+        k_x2r_tile_jmin<<<(unsigned)p->x2r_tiles, 256, 0, st>>>(p->n, (p->n + 31) / 32,
+                                                                X2R_TY * RB_P, rm, p->thr,
+                                                                p->x2r_jmin);
+        NL_CUDA_TRY(cudaGetLastError());
+        NL_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return NL_OK;
 }

@@ -106,6 +106,8 @@ struct nl_plan {
                                     // kernel variant (timed at plan creation)
     int *x2r_order, *x2r_queue;     // symmetric kernel for pairs of right-hand sides: 32-wide
     int x2r_tiles, x2r_blocks;      // tiles largest first, queue, tile count, grid size
+    float *x2r_c32, *x2r_tp1;       // its tile planes c = (W/2) b and thr + 1 per node, and the
+    int *x2r_jmin;                  // smallest threshold each tile stages
     const double *skip_flags;       // set by nl_cg_solve for its iterations only: right-hand
     int skip_stride;                // sides flagged converged need no FP32 operator result
     // per-node device arrays
