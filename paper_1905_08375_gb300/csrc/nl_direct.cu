@@ -2345,16 +2345,24 @@ __device__ __forceinline__ void pd_x2_stage(const DirectArgs &a, float *sm, int 
     constexpr int SX = 64 + 2 * RM, SY = TY * PD_RB + 2 * RM + 1, PL = SX * SY;
     const int n = a.n;
     const float *__restrict__ cc = (const float *)a.b;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    for (int e = tid; e < PL; e += 32 * TY) {
-        const int gx = x0 - RM + e % SX, gy = y0 - RM + e / SX;
-        float vx = 0.f, vy = 0.f, vc = 0.f, vi = 0.f;
-        if (gx >= 0 && gx < n && gy >= 0 && gy < n) {
-            const int64_t j = gx + (int64_t)n * gy;
-            vx = ux[j]; vy = uy[j]; vc = cc[j]; vi = 1.f;
+    // asynchronous 4-byte copies (one warp per tile row, zero-filled off the grid) for u and c;
+    // the inside indicator is a plain store; the caller's barrier follows the wait
+    for (int row = threadIdx.y; row < SY; row += TY) {
+        const int gy = y0 - RM + row;
+        const bool rin = gy >= 0 && gy < n;
+        const int64_t roff = (int64_t)n * (rin ? gy : 0);
+        for (int xx = threadIdx.x; xx < SX; xx += 32) {
+            const int gx = x0 - RM + xx;
+            const bool ok = rin && gx >= 0 && gx < n;
+            const int64_t j = roff + (ok ? gx : 0);
+            const int e = row * SX + xx;
+            cp_async4(sm + e, ux + j, ok);
+            cp_async4(sm + e + PL, uy + j, ok);
+            cp_async4(sm + e + 2 * PL, cc + j, ok);
+            sm[e + 3 * PL] = ok ? 1.f : 0.f;
         }
-        sm[e] = vx; sm[e + PL] = vy; sm[e + 2 * PL] = vc; sm[e + 3 * PL] = vi;
     }
+    cp_async_wait_all();
 }
 
 template <int RM, int TY>
