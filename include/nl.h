@@ -171,13 +171,14 @@ nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, 
  * Requires family NL_POLY, a non-symmetric horizon, n = 2^L and coefficient
  * NL_COEF_NONE, NL_COEF_X or NL_COEF_XY; else NL_EUNSUPPORTED.
  *
- * On a 2-D NL_PD_BOND plan (n = 2^L <= 8192, FP32 data) it applies the fast-path
- * peridynamic operator of degree 0 (the paper's outlook, Sec. 4): the bond tensor
- * xi xi^T / |xi|^3 replaced by xi xi^T / delta_i^3 (p = 1 matched at the horizon) and the
- * sum taken over the same leaf set,
- *     (L u)_i = h^2 sum_{k in LS(i)} sigma c_ik (xi xi^T / delta_i^3) (u_k - u_i),
+ * On a 2-D NL_PD_BOND plan (n = 2^L <= 8192, FP32 data, K = 0, 1 or 2) it applies the
+ * fast-path peridynamic operator (the paper's outlook, Sec. 4): the bond tensor
+ * xi xi^T / |xi|^3 replaced by xi xi^T p^{2K}(|xi|/delta_i) / delta_i^3, p^{2K} the Sec. 3
+ * polynomial matched to s^{-3} in value and K derivatives at the horizon (K = 0: p = 1),
+ * and the sum taken over the same leaf set,
+ *     (L u)_i = h^2 sum_{k in LS(i)} sigma c_ik (xi xi^T p^{2K} / delta_i^3) (u_k - u_i),
  * c_ik = (c_i + c_k)/2, u_k = 0 and c_k = c_i outside Omega; a different operator from
- * nl_apply's, computed from exact 64-bit leaf-row moment sums.
+ * nl_apply's, computed from exact 64-bit leaf-row moment sums (K = 3: NL_EUNSUPPORTED).
  * On a symmetric NL_POLY plan (K = 0) it applies the symmetrised leaf-set operator
  *     (L u)_i = sigma h^d sum_k (w_i(k) + w_k(i))/2 C_ik (u_k - u_i),
  *     w_i(k) = [cell k meets the open ball of node i] delta_i^{-(d+2)},
