@@ -173,7 +173,7 @@ PROFILED_TRAFFIC = {
     "k_direct2d_x2": 21.03e6,          # c2, variant <16, 2, 3>
     "k_direct2d_x2_kappa": 29.42e6,    # c2k, variant <16, 2, 3, kappa>: 29.42 MB read, 256 B written
     "k_direct_pd_x2": 9.48e6,          # c3, <8, 2>
-    "k_fast_gather_slots": 178.52e6,   # c2, 174.8 MB read + 3.7 MB written
+    "k_fast_gather_slots": 178.53e6,   # c2, 174.85 MB read + 3.68 MB written (32 x 8 node tiles)
 }
 
 

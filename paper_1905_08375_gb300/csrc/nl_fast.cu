@@ -1245,12 +1245,21 @@ __global__ void __launch_bounds__(256, SLOT_MIN_BLOCKS) k_fast_gather_slots(Fast
                                                            const int64_t *__restrict__ woff,
                                                            const int *__restrict__ wslots,
                                                            const float *__restrict__ u,
-                                                           float *__restrict__ Lu)
+                                                           float *__restrict__ Lu, int tiles_x)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t w = i >> 5;
-    if ((w << 5) >= a.N) return;
+    // tiles_x > 0 (2-D): the block's eight warps take the same 32 columns of eight consecutive
+    // rows, so that their balls, and the pyramid panels they read, overlap in the SM's L1
+    // (taller tiles of 16 and 32 rows were measured slower); tiles_x = 0: the warps of a block
+    // take consecutive nodes
     const int lane = threadIdx.x & 31;
+    int64_t w;
+    if (tiles_x > 0)
+        w = ((int64_t)(blockIdx.x / tiles_x) * 8 + (threadIdx.x >> 5)) * tiles_x +
+            blockIdx.x % tiles_x;
+    else
+        w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t i = (w << 5) + lane;
+    if ((w << 5) >= a.N) return;
     const int64_t off = woff[w];
     const int ng = (wslots[w] + 3) >> 2;
     const uint4 *__restrict__ b4 = reinterpret_cast<const uint4 *>(base) + off;
@@ -2220,8 +2229,9 @@ static nl_status fast_one_i64(nl_plan *p, const float *u, float *Lu, cudaStream_
         const unsigned gp = (unsigned)((p->N + GP_THREADS - 1) / GP_THREADS);
         if (p->slot_base) {
             const unsigned gr = (unsigned)(((p->N + 31) / 32 * 32 + 255) / 256);
+            const int tiles_x = (d == 2 && p->n % 32 == 0) ? p->n / 32 : 0;
             k_fast_gather_slots<<<gr, 256, 0, st>>>(a, p->slot_base, p->slot_rec, p->slot_woff,
-                                                     p->slot_count, u, Lu);
+                                                     p->slot_count, u, Lu, tiles_x);
         } else if (d == 1) k_fast_gather_panels_lane<1><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else if (d == 2 && p->n >= 32) k_fast_gather_panels<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
         else if (d == 2) k_fast_gather_panels_lane<2><<<gp, GP_THREADS, 0, st>>>(a, u, Lu);
