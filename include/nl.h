@@ -66,7 +66,9 @@ typedef enum { NL_F32 = 0, NL_F64 = 1, NL_F64_PAIRS = 2 } nl_dtype;
  *               matches s^{-alpha} and its first K derivatives at s = 1
  *               (the splitting of Sec. 3; K = 0 gives p = 1)
  *   NL_PD_BOND: linear peridynamic bond, micromodulus sigma c_ij / |xi|
- *               (Eq. (1.2)); u and Lu then hold d component planes.
+ *               (Eq. (1.2)); u and Lu then hold d component planes.  d = 2 (direct
+ *               operator, fast path, CG); d = 3 with K = 0 and n = 2^L <= 256 for the
+ *               fast path only (nl_apply and nl_cg_solve: NL_EUNSUPPORTED).
  *   NL_KAPPA:   gamma(s) = kappa(s) = s^{-alpha} - p^{2K}(s), the other part of the
  *               splitting of Sec. 3 (s^{-alpha} chi = kappa + p^{2K} chi): singular at
  *               s = 0, C^K at the horizon.  nl_apply only (the direct sum, any d); with the
@@ -179,6 +181,9 @@ nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, 
  *     (L u)_i = h^2 sum_{k in LS(i)} sigma c_ik (xi xi^T p^{2K} / delta_i^3) (u_k - u_i),
  * c_ik = (c_i + c_k)/2, u_k = 0 and c_k = c_i outside Omega; a different operator from
  * nl_apply's, computed from exact 64-bit leaf-row moment sums (K = 3: NL_EUNSUPPORTED).
+ * On a 3-D NL_PD_BOND plan (K = 0, n = 2^L <= 256, FP32 data) the same operator with
+ * xi in R^3 and three component planes (fourteen leaf-row prefix arrays, 112 bytes per node,
+ * owned by the plan).
  * On a symmetric NL_POLY plan (K = 0) it applies the symmetrised leaf-set operator
  *     (L u)_i = sigma h^d sum_k (w_i(k) + w_k(i))/2 C_ik (u_k - u_i),
  *     w_i(k) = [cell k meets the open ball of node i] delta_i^{-(d+2)},

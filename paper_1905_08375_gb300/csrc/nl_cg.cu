@@ -688,6 +688,10 @@ static nl_status plan_cg(nl_plan *p, const void *f, void *x, int nrhs, double rt
         return NL_EINVAL;
     }
     const bool pd = p->family == NL_PD_BOND;
+    if (pd && p->d != 2) {
+        nl_set_error("nl_cg_solve: the peridynamic operator of CG is the 2-D direct one");
+        return NL_EUNSUPPORTED;
+    }
     if (!(p->symmetric || p->sym_fast || (pd && p->const_horizon))) {
         nl_set_error("nl_cg_solve: the operator must be symmetric (symmetric NL_POWER or "
                      "NL_POLY plan, or NL_PD_BOND with a constant horizon)");

@@ -2501,6 +2501,11 @@ static DirectArgs make_args(const nl_plan *p, int dtype)
 nl_status nl_direct_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int dtype,
                            cudaStream_t st)
 {
+    if (p->family == NL_PD_BOND && p->d != 2) {
+        nl_set_error("nl_apply: the direct peridynamic operator is built for d = 2 (a 3-D "
+                     "NL_PD_BOND plan serves nl_apply_fast)");
+        return NL_EUNSUPPORTED;
+    }
     const DirectArgs a = make_args(p, dtype);
     if (p->family == NL_PD_BOND) {
         if (dtype == NL_F32 && p->pd_dense32 && p->Rmax <= 32)

@@ -16,7 +16,8 @@
 // differences (over rows, times dy or dy^2) and the final combination with the node's column
 // (o_x = k - kx) then fit in 64-bit integers.  Rows and runs are those of the scalar leaf-row
 // gather (the same half-unit geometry).  2-D, FP32 data.  K = 1, 2 (the polynomial
-// micromodulus p^{2K} matched to s^-3) extend this below with the moments of o_x up to 2K + 2.
+// micromodulus p^{2K} matched to s^-3) extend this below with the moments of o_x up to 2K + 2,
+// and the 3-D form (K = 0) follows them.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -466,12 +467,302 @@ __global__ void __launch_bounds__(128) k_fpd_gather_k(FpdGatherArgs a, FpdPoly p
     outy[i] = (float)(Fi * (ci * A[0][1] + A[1][1] - (Mi[1] * uxi + Mi[2] * uyi)));
 }
 
+// ---------------------------------------------------------------------------
+// 3-D, K = 0: xi = o h with o = (o_x, o_y, o_z); along a leaf row (o_y, o_z fixed) the x-type
+// field needs the run sums of q, k q, k^2 q and the y- and z-type fields those of q and k q:
+//   (o o^T q)_x = o_x^2 q_x + o_x o_y q_y + o_x o_z q_z,
+//   (o o^T q)_y = o_x o_y q_x + o_y^2 q_y + o_y o_z q_z,
+//   (o o^T q)_z = o_x o_z q_x + o_y o_z q_y + o_z^2 q_z,
+// seven prefix arrays per group (u, c u), fourteen in all, with the rows and runs of the
+// scalar leaf-row gather in 3-D (vertical gap from the row's y and z gaps).  Sums wrap modulo
+// 2^64; 2^bits >= (2R + 3)^3 (R + 2)^2 bounds every per-node combination, which is exact.
+// ---------------------------------------------------------------------------
+constexpr int FPD3_FIELDS = 6;                  // u_x, u_y, u_z, c u_x, c u_y, c u_z
+constexpr int FPD3_ARRAYS = 14;                 // per group: x P0 P1 P2, y P0 P1, z P0 P1
+
+// half-unit gap^2 from a node at 2 i + 1 to cell k (0 for its own cell)
+__device__ __forceinline__ int gap2_pd(int k, int I)
+{
+    const int lo = 2 * k - I, hi = lo + 2;
+    return lo > 0 ? lo * lo : (hi < 0 ? hi * hi : 0);
+}
+
+// plan time, 3-D: F_i = sigma h^5 / (2 delta_i^3) and the six entries of
+// M_i = sum_{k in LS(i)} (c_i + c_k) o o^T (xx, xy, xz, yy, yz, zz; FP64)
+__global__ void k_fpd_node3(int n, int64_t N, double sigma, double h,
+                            const double *__restrict__ delta, const double *__restrict__ c,
+                            const int *__restrict__ thr4, double *__restrict__ F,
+                            double *__restrict__ M)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((int64_t)n * n));
+    const int X = 2 * ix + 1, Y = 2 * iy + 1, Z = 2 * iz + 1;
+    const int T4 = thr4[i];
+    const double ci = c ? c[i] : 1.0;
+    const int r0 = isqrt_pd(T4);
+    double m[6] = { 0, 0, 0, 0, 0, 0 };
+    const int zlo = -((r0 - Z) >> 1) - 1, zhi = (Z + r0) >> 1;
+    const int ylo = -((r0 - Y) >> 1) - 1, yhi = (Y + r0) >> 1;
+    for (int kz = zlo; kz <= zhi; ++kz) {
+        const int ez = gap2_pd(kz, Z);
+        if (ez > T4) continue;
+        for (int ky = ylo; ky <= yhi; ++ky) {
+            const int e = ez + gap2_pd(ky, Y);
+            if (e > T4) continue;
+            const int r = isqrt_pd(T4 - e);
+            const int ka = -((r - X) >> 1) - 1, kb = (X + r) >> 1;
+            const int dy = ky - iy, dz = kz - iz;
+            const bool row_in = ky >= 0 && ky < n && kz >= 0 && kz < n;
+            for (int kx = ka; kx <= kb; ++kx) {
+                const int dx = kx - ix;
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                const bool in = row_in && kx >= 0 && kx < n;
+                const double w =
+                    ci + (in ? (c ? c[((int64_t)kz * n + ky) * n + kx] : 1.0) : ci);
+                m[0] += w * dx * dx; m[1] += w * dx * dy; m[2] += w * dx * dz;
+                m[3] += w * dy * dy; m[4] += w * dy * dz; m[5] += w * dz * dz;
+            }
+        }
+    }
+    const double di = delta[i];
+    F[i] = sigma * h * h * h * h * h / (2.0 * di * di * di);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) M[6 * i + t] = m[t];
+}
+
+// per-block bounds of the six fields (FP32 products), enlarged by 2^-20
+__global__ void __launch_bounds__(256) k_fpd_absmax3(int64_t N, const float *__restrict__ u,
+                                                     const float *__restrict__ c,
+                                                     float *__restrict__ part)
+{
+    __shared__ float s_w[FPD3_FIELDS][8];
+    float m[FPD3_FIELDS] = { 0.f, 0.f, 0.f, 0.f, 0.f, 0.f };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float cc = c[i];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const float v = u[(int64_t)f * N + i];
+            m[f] = fmaxf(m[f], fabsf(v));
+            m[3 + f] = fmaxf(m[3 + f], fabsf(cc * v));
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < FPD3_FIELDS; ++f) {
+        for (int o = 16; o > 0; o >>= 1) m[f] = fmaxf(m[f], __shfl_xor_sync(0xffffffffu, m[f], o));
+        if ((threadIdx.x & 31) == 0) s_w[f][threadIdx.x >> 5] = m[f];
+    }
+    __syncthreads();
+    if (threadIdx.x < FPD3_FIELDS) {
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v = fmaxf(v, s_w[threadIdx.x][w]);
+        part[threadIdx.x * FPD_PARTS + blockIdx.x] = v * (1.f + 0x1p-20f);
+    }
+}
+
+struct Fpd3ScanArgs {
+    int n, bits, nparts;
+    const float *u, *c, *part;          // u: [3][N]
+    int *shifts;                        // [6], written by block 0
+    long long *P;                       // [14][N]
+    int64_t N;
+};
+
+// one warp per leaf row (n^2 rows): the fourteen prefix arrays of the row, each field rounded
+// once to a multiple of 2^-S (its own S), times k and k^2 modulo 2^64, scanned with shuffles
+__global__ void __launch_bounds__(128) k_fpd_scan3(Fpd3ScanArgs a)
+{
+    __shared__ int s_sh[FPD3_FIELDS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        for (int f = 0; f < FPD3_FIELDS; ++f) {
+            float m = 0.f;
+            for (int k = lane; k < a.nparts; k += 32) m = fmaxf(m, a.part[f * FPD_PARTS + k]);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) s_sh[f] = fpd_shift(m, a.bits);
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x < FPD3_FIELDS) a.shifts[threadIdx.x] = s_sh[threadIdx.x];
+    const int n = a.n;
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (row >= (int64_t)n * n) return;
+    const int64_t base = row * n, N = a.N;
+    typedef unsigned long long u64;
+    u64 carry[FPD3_ARRAYS];
+#pragma unroll
+    for (int t = 0; t < FPD3_ARRAYS; ++t) carry[t] = 0ull;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        u64 v[FPD3_ARRAYS];
+        if (k < n) {
+            const float cc = a.c[base + k];
+            const u64 kk = (u64)k;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    float x = a.u[(int64_t)f * N + base + k];
+                    if (g) x *= cc;
+                    const u64 q = (u64)__float2ll_rn(ldexpf(x, s_sh[3 * g + f]));
+                    const int t0 = 7 * g + (f == 0 ? 0 : (f == 1 ? 3 : 5));
+                    v[t0] = q;
+                    v[t0 + 1] = kk * q;
+                    if (f == 0) v[t0 + 2] = kk * kk * q;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < FPD3_ARRAYS; ++t) v[t] = 0ull;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int t = 0; t < FPD3_ARRAYS; ++t) {
+                const u64 w = __shfl_up_sync(0xffffffffu, v[t], o);
+                if (lane >= o) v[t] += w;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < FPD3_ARRAYS; ++t) {
+            v[t] += carry[t];
+            if (k < n) a.P[(int64_t)t * N + base + k] = (long long)v[t];
+            carry[t] = __shfl_sync(0xffffffffu, v[t], 31);
+        }
+    }
+}
+
+// per node: over the leaf rows (dy, dz) of its ball, the run differences of the fourteen
+// arrays, accumulated (times dy, dz, dy^2, dy dz, dz^2) into exact sums modulo 2^64, then
+// centred on the node's column and combined in FP64 with each field's scale
+__global__ void __launch_bounds__(128) k_fpd_gather3(FpdGatherArgs a, const float *__restrict__ u,
+                                                     float *__restrict__ out)
+{
+    typedef unsigned long long u64;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int64_t N = a.N;
+    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((int64_t)n * n));
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    // per group: SX0 SX1 SX2, TY0 TY1 (dy x), TZ0 TZ1 (dz x), UY0 UY1 (dy y), VYY (dy^2 y0),
+    // VYZY (dy dz y0), WZ0 WZ1 (dz z), VZZ (dz^2 z0), VYZZ (dy dz z0)
+    u64 acc[2][15];
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int t = 0; t < 15; ++t) acc[g][t] = 0ull;
+    for (int tz = 0;; ++tz) {
+        const int ez = tz == 0 ? 0 : sqi(2 * tz - 1);
+        if (ez > T4) break;
+        for (int ty = 0;; ++ty) {
+            const int e = ez + (ty == 0 ? 0 : sqi(2 * ty - 1));
+            if (e > T4) break;
+            const int r = isqrt_pd(T4 - e);
+            const int ka = max(0, -((r - X) >> 1) - 1);
+            const int kb = min(n - 1, (X + r) >> 1);
+            for (int sz = 0; sz < (tz > 0 ? 2 : 1); ++sz) {
+                const int dz = sz ? -tz : tz;
+                const int kz = iz + dz;
+                if (kz < 0 || kz >= n) continue;
+                for (int sy = 0; sy < (ty > 0 ? 2 : 1); ++sy) {
+                    const int dy = sy ? -ty : ty;
+                    const int ky = iy + dy;
+                    if (ky < 0 || ky >= n) continue;
+                    const int64_t row = ((int64_t)kz * n + ky) * n;
+                    const u64 uy = (u64)(long long)dy, uz = (u64)(long long)dz;
+                    const u64 uyy = uy * uy, uyz = uy * uz, uzz = uz * uz;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        const long long *Pg = a.P + (int64_t)(7 * g) * N;
+                        const u64 x0 = pdiff(Pg, row, ka, kb), x1 = pdiff(Pg + N, row, ka, kb),
+                                  x2 = pdiff(Pg + 2 * N, row, ka, kb);
+                        const u64 y0 = pdiff(Pg + 3 * N, row, ka, kb),
+                                  y1 = pdiff(Pg + 4 * N, row, ka, kb);
+                        const u64 z0 = pdiff(Pg + 5 * N, row, ka, kb),
+                                  z1 = pdiff(Pg + 6 * N, row, ka, kb);
+                        u64 *A = acc[g];
+                        A[0] += x0; A[1] += x1; A[2] += x2;
+                        A[3] += uy * x0; A[4] += uy * x1;
+                        A[5] += uz * x0; A[6] += uz * x1;
+                        A[7] += uy * y0; A[8] += uy * y1;
+                        A[9] += uyy * y0; A[10] += uyz * y0;
+                        A[11] += uz * z0; A[12] += uz * z1;
+                        A[13] += uzz * z0; A[14] += uyz * z0;
+                    }
+                }
+            }
+        }
+    }
+    const u64 kx = (u64)ix;
+    double R[2][3];                              // [g][component]
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        const u64 *A = acc[g];
+        const int sx = a.shifts[3 * g], sy = a.shifts[3 * g + 1], sz = a.shifts[3 * g + 2];
+        const long long xx = (long long)(A[2] - 2 * kx * A[1] + kx * kx * A[0]);   // o_x^2 q_x
+        const long long yx = (long long)(A[4] - kx * A[3]);                        // o_x o_y q_x
+        const long long zx = (long long)(A[6] - kx * A[5]);                        // o_x o_z q_x
+        const long long xy = (long long)(A[8] - kx * A[7]);                        // o_x o_y q_y
+        const long long yy = (long long)A[9];                                      // o_y^2 q_y
+        const long long zy = (long long)A[10];                                     // o_y o_z q_y
+        const long long xz = (long long)(A[12] - kx * A[11]);                      // o_x o_z q_z
+        const long long zz = (long long)A[13];                                     // o_z^2 q_z
+        const long long yz = (long long)A[14];                                     // o_y o_z q_z
+        R[g][0] = ldexp((double)xx, -sx) + ldexp((double)xy, -sy) + ldexp((double)xz, -sz);
+        R[g][1] = ldexp((double)yx, -sx) + ldexp((double)yy, -sy) + ldexp((double)yz, -sz);
+        R[g][2] = ldexp((double)zx, -sx) + ldexp((double)zy, -sy) + ldexp((double)zz, -sz);
+    }
+    const double ci = a.c[i];
+    const double u0 = (double)u[i], u1 = (double)u[N + i], u2 = (double)u[2 * N + i];
+    const double *Mi = a.M + 6 * i;
+    const double Fi = a.F[i];
+    out[i] = (float)(Fi * (ci * R[0][0] + R[1][0] - (Mi[0] * u0 + Mi[1] * u1 + Mi[2] * u2)));
+    out[N + i] = (float)(Fi * (ci * R[0][1] + R[1][1] - (Mi[1] * u0 + Mi[3] * u1 + Mi[4] * u2)));
+    out[2 * N + i] = (float)(Fi * (ci * R[0][2] + R[1][2] - (Mi[2] * u0 + Mi[4] * u1 + Mi[5] * u2)));
+}
+
 }  // namespace
+
+// plan-time set-up, 3-D (K = 0, n = 2^L <= 256): F, M (six per node), the fourteen prefix
+// arrays (112 bytes per node) and the bounds workspace
+static nl_status fast_pd3_plan_init(nl_plan *p, const double *delta_dev, const double *c_dev,
+                                    cudaStream_t st)
+{
+    if (p->L < 0 || p->n > 256 || !p->thr4 || p->K != 0) return NL_OK;
+    const double rr = 2.0 * p->Rmax + 3;
+    const double bound = rr * rr * rr * (p->Rmax + 2.0) * (p->Rmax + 2.0);
+    if (bound > 0x1p48) return NL_OK;
+    const int64_t N = p->N;
+    auto alloc = [&](void **ptr, size_t bytes) -> nl_status {
+        if (cudaMalloc(ptr, bytes ? bytes : 1) != cudaSuccess) {
+            nl_set_error("cudaMalloc(%zu) for the fast peridynamic path failed", bytes);
+            return NL_ENOMEM;
+        }
+        p->device_bytes += bytes;
+        return NL_OK;
+    };
+    nl_status s;
+    if ((s = alloc((void **)&p->fpd_F, N * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->fpd_M, 6 * N * sizeof(double))) != NL_OK) return s;
+    if ((s = alloc((void **)&p->fpd_P, (size_t)FPD3_ARRAYS * N * sizeof(long long))) != NL_OK)
+        return s;
+    if ((s = alloc((void **)&p->fpd_aux, FPD3_FIELDS * FPD_PARTS * sizeof(float) + 64)) != NL_OK)
+        return s;
+    p->fpd_bits = (int)std::ceil(std::log2(bound));
+    k_fpd_node3<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(p->n, N, p->sigma, p->h, delta_dev,
+                                                            c_dev, p->thr4, p->fpd_F, p->fpd_M);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
 
 // plan-time set-up (2-D NL_PD_BOND plans with n = 2^L <= 8192)
 nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double *c_dev,
                                cudaStream_t st)
 {
+    if (p->d == 3) return fast_pd3_plan_init(p, delta_dev, c_dev, st);
     if (p->d != 2 || p->L < 0 || p->n > 8192 || !p->thr4 || p->K > 2) return NL_OK;
     // 2^bits bounds every per-node integer sum: n^2 (2 Rmax + 3)^2 for K = 0, (2 Rmax + 3)^2
     // (Rmax + 2)^{2K+2} for K >= 1; at least 2^13 levels must remain for max|v|
@@ -509,11 +800,36 @@ nl_status nl_fast_pd_plan_init(nl_plan *p, const double *delta_dev, const double
 nl_status nl_fast_pd_launch(nl_plan *p, const float *u, float *Lu, int nrhs, cudaStream_t st)
 {
     if (!p->fpd_P) {
-        nl_set_error("nl_apply_fast: the fast peridynamic path needs a 2-D plan with n = 2^L "
-                     "<= 8192, K <= 2 and a horizon whose integer sums fit 64 bits");
+        nl_set_error("nl_apply_fast: the fast peridynamic path needs n = 2^L and a horizon "
+                     "whose integer sums fit 64 bits, with n <= 8192 and K <= 2 in 2-D, "
+                     "n <= 256 and K = 0 in 3-D");
         return NL_EUNSUPPORTED;
     }
     const int64_t N = p->N;
+    if (p->d == 3) {
+        float *part = (float *)p->fpd_aux;
+        int *shifts = (int *)((unsigned char *)p->fpd_aux + FPD3_FIELDS * FPD_PARTS * sizeof(float));
+        int64_t per = (N + FPD_PARTS - 1) / FPD_PARTS;
+        if (per < 2048) per = 2048;
+        const int nparts = (int)((N + per - 1) / per);
+        for (int r = 0; r < nrhs; ++r) {
+            const float *ur = u + (int64_t)r * 3 * N;
+            float *lr = Lu + (int64_t)r * 3 * N;
+            k_fpd_absmax3<<<nparts, 256, 0, st>>>(N, ur, p->b32, part);
+            Fpd3ScanArgs sa;
+            sa.n = p->n; sa.bits = p->fpd_bits; sa.nparts = nparts;
+            sa.u = ur; sa.c = p->b32; sa.part = part; sa.shifts = shifts;
+            sa.P = p->fpd_P; sa.N = N;
+            const int64_t rows = (int64_t)p->n * p->n;
+            k_fpd_scan3<<<(unsigned)((rows + 3) / 4), 128, 0, st>>>(sa);
+            FpdGatherArgs ga;
+            ga.n = p->n; ga.N = N; ga.thr4 = p->thr4; ga.c = p->b64;
+            ga.F = p->fpd_F; ga.M = p->fpd_M; ga.P = p->fpd_P; ga.shifts = shifts;
+            k_fpd_gather3<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(ga, ur, lr);
+            NL_CUDA_TRY(cudaGetLastError());
+        }
+        return NL_OK;
+    }
     float *part = (float *)p->fpd_aux;
     int *shifts = (int *)((unsigned char *)p->fpd_aux + FPD_FIELDS * FPD_PARTS * sizeof(float));
     int64_t per = (N + FPD_PARTS - 1) / FPD_PARTS;

@@ -374,8 +374,12 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         return NL_EINVAL;
     }
     if (k->family == NL_PD_BOND) {
-        if (d != 2) {
-            nl_set_error("nl_plan_create: the peridynamic operator is built for d = 2");
+        // 2-D: the direct operator, the fast path and CG; 3-D: the fast path (nl_apply_fast,
+        // K = 0, n = 2^L <= 256) only
+        const bool pow2 = n >= 1 && (n & (n - 1)) == 0;
+        if (d != 2 && !(d == 3 && pow2 && n <= 256 && k->K == 0)) {
+            nl_set_error("nl_plan_create: the peridynamic operator is built for d = 2, and in "
+                         "3-D for the fast path (K = 0, n = 2^L <= 256)");
             return NL_EUNSUPPORTED;
         }
         if (k->coef != NL_COEF_NONE && k->coef != NL_COEF_MEAN) {
@@ -550,7 +554,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
         t32[t] = OffEntry32{ soff, o.w, (float)g, 0 };
         t64[t] = OffEntry64{ soff, o.w, g };
     }
-    if (k->family == NL_PD_BOND) {
+    if (k->family == NL_PD_BOND && d == 2) {
         q32.resize(offs.size());
         q64.resize(offs.size());
         for (size_t t = 0; t < offs.size(); ++t) {
@@ -622,7 +626,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
             ce = cudaMemcpyAsync(p->tab64, t64.data(), t64.size() * sizeof(OffEntry64), cudaMemcpyHostToDevice, st);
         if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "table upload"));
     }
-    if (k->family == NL_PD_BOND) {
+    if (k->family == NL_PD_BOND && d == 2) {
         NL_TMP_TRY(dev_alloc(p, &p->pd32, nt));
         NL_TMP_TRY(dev_alloc(p, &p->pd64, nt));
         NL_TMP_TRY(dev_alloc(p, &p->pdext, 3 * N));
@@ -699,7 +703,8 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     const int TB = 256;
     const unsigned GB = (unsigned)((N + TB - 1) / TB);
     const bool want_fast = (k->family == NL_POLY && p->L >= 0 && !p->symmetric);
-    const bool want_fast_pd = (k->family == NL_PD_BOND && d == 2 && p->L >= 0 && n <= 8192);
+    const bool want_fast_pd = (k->family == NL_PD_BOND && p->L >= 0 &&
+                               ((d == 2 && n <= 8192) || (d == 3 && n <= 256 && k->K == 0)));
     if (want_fast || want_fast_pd) NL_TMP_TRY(dev_alloc(p, &p->thr4, N));
     k_thresholds<<<GB, TB, 0, st>>>(pa, d_delta, p->thr, p->thr4);
     if (p->symmetric) {
@@ -710,7 +715,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     k_node_factors<<<GB, TB, 0, st>>>(pa, d_delta, d_a, p->thr, d_win, p->off, d_g, p->cnt,
                                       p->b32, p->b64, p->fin32, p->fin64, p->ext32, p->ext64,
                                       p->wh32, p->wh64, p->ir32, p->ir64);
-    if (k->family == NL_PD_BOND)
+    if (k->family == NL_PD_BOND && d == 2)
         k_pd_exterior<<<GB, TB, 0, st>>>(pa, d_a, p->thr, p->off, p->pdext);
     ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_tmp(nl_cuda_fail(ce, "plan kernels"));
