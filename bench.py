@@ -543,6 +543,15 @@ class C3(Workload):
         self.plan_k2 = nl.nl_plan_create(2, 512, f["delta"], family=nl.NL_PD_BOND,
                                          coef=nl.NL_COEF_MEAN, a=f["c"], K=2)
         self.out_k2 = torch.empty_like(self.u)
+        # the 3-D fast path (K = 0) on a 128^3 two-phase grid with delta = 4h
+        rng = np.random.default_rng(self.seed + 7)
+        n3 = 128
+        c3 = synth.voronoi_phase(rng, 3, n3)
+        u3 = np.stack([synth.gaussian_field(rng, 3, n3).reshape(-1) for _ in range(3)])
+        self.plan3 = nl.nl_plan_create(3, n3, 4.0 / n3, family=nl.NL_PD_BOND,
+                                       coef=nl.NL_COEF_MEAN, a=c3)
+        self.u3 = torch.tensor(u3, dtype=torch.float32, device=self.dev)
+        self.out3 = torch.empty_like(self.u3)
         self.units = 512 * 512
         self.launches = 1
         self.config = {"workload": "2D linear bond-based PD, 512x512, delta=8h, micromodulus "
@@ -561,6 +570,8 @@ class C3(Workload):
         t_f32 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan32, self.u, o32), reps, flush)
         t_k2 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan_k2, self.u, self.out_k2),
                             reps, flush)
+        t_3 = self.time_fn(lambda: self.nl.nl_apply_fast(self.plan3, self.u3, self.out3), reps,
+                           flush)
         nb = float(ball_counts(self.f["delta"], self.n, 2).sum())
         roof = _alu_roof("k_direct_pd_x2<8,2> (paired columns)", 14.0 * nb, t, *fp32_peak())
         roof["algorithmic_per_launch"] = f"{14 * nb:.4g} flop (14 per bond)"
@@ -568,6 +579,8 @@ class C3(Workload):
                       "pd_delta32h_direct_fp32_ms": round(t_d32, 4),
                       "pd_delta32h_fast_deg0_fp32_ms": round(t_f32, 4),
                       "pd_fast_poly_K2_fp32_ms": round(t_k2, 4),
+                      "pd3d_128_delta4h_fast_deg0_fp32_ms": round(t_3, 4),
+                      "pd3d_128_delta4h_fast_gpts": round(128 ** 3 / t_3 / 1e6, 4),
                       "pd_fast_note": "nl_apply_fast on the PD plan: degree-0 bond tensor "
                                       "xi xi^T / delta^3 over the leaf set (a different "
                                       "operator), exact 64-bit leaf-row moment sums"}
