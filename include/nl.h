@@ -184,13 +184,17 @@ nl_status nl_apply(nl_plan *plan, const void *u, void *Lu, int nrhs, int dtype, 
  * On a 3-D NL_PD_BOND plan (K = 0, n = 2^L <= 256, FP32 data) the same operator with
  * xi in R^3 and three component planes (fourteen leaf-row prefix arrays, 112 bytes per node,
  * owned by the plan).
- * On a symmetric NL_POLY plan (K = 0) it applies the symmetrised leaf-set operator
+ * On a symmetric NL_POLY plan (K = 0..3) it applies the symmetrised leaf-set operator
  *     (L u)_i = sigma h^d sum_k (w_i(k) + w_k(i))/2 C_ik (u_k - u_i),
- *     w_i(k) = [cell k meets the open ball of node i] delta_i^{-(d+2)},
+ *     w_i(k) = [cell k meets the open ball of node i] delta_i^{-(d+2)} p(|x_k - x_i|/delta_i),
  * k over every lattice cell (u_k = 0, a_k = a_i, delta_k = delta_i outside Omega): the
  * one-sided fast apply for the first half, and for the second its transpose -- each node
  * scatters c_k u_k (c_k = a_k delta_k^{-(d+2)}) into per-leaf-row difference arrays (exact
- * 64-bit integer atomics for FP32 data, FP64 atomics for FP64 data), one prefix sum per row.
+ * 64-bit integer atomics for FP32 data, FP64 atomics for FP64 data), one prefix sum per row;
+ * for K >= 1 the run's weights form a polynomial in the target column, whose 2K + 1
+ * coefficients go into difference arrays as two-limb integers (exact for both data types;
+ * 16 (2K + 1) bytes per node owned by the plan; NL_EUNSUPPORTED at plan creation when the
+ * horizon is too large for the limbs).
  * Symmetric and negative semi-definite, so nl_cg_solve accepts such a plan (Jacobi).
  * Same layouts and ownership as nl_apply.
  */

@@ -2425,7 +2425,7 @@ extern "C" nl_status nl_apply_fast(nl_plan *p, const void *u, void *Lu, int nrhs
     }
     if (p->family != NL_POLY || p->symmetric || p->L < 0 || !p->pyr) {
         nl_set_error("nl_apply_fast: needs an NL_POLY plan (one-sided, or symmetric with "
-                     "K = 0) on n = 2^L <= 8192");
+                     "K <= 3) on n = 2^L <= 8192");
         return NL_EUNSUPPORTED;
     }
     if (p->self_mode == NL_SELF_PAPER && p->coef == NL_COEF_XY) {

@@ -1,5 +1,6 @@
 // nl_fast_sym.cu -- the fast path for the symmetrised (divergence-type) polynomial operator,
-// K = 0 (a project extension of Sec. 3, which treats the one-sided C(x) delta(x) form only;
+// K = 0 here and K = 1..3 below (a project extension of Sec. 3, which treats the one-sided
+// C(x) delta(x) form only;
 // the symmetric pairing w_ij + w_ji is the divergence type of Sec. 2 case (b)):
 //
 //   (L u)_i = sigma h^d sum_k (w_i(k) + w_k(i))/2 a_i a_k (u_k - u_i),
@@ -40,10 +41,12 @@ __device__ __forceinline__ int sym_isqrt(int x)
 }
 
 struct SymArgs {
-    int d, n, coef;
+    int d, n, coef, K;
     int64_t N;
     double sigma, hd;
+    double p[8];                      // p_0 .. p_K of p^{2K} (p(s) = sum_m p_m s^{2m})
     const int *thr4;
+    double *ir2;                      // K >= 1: 1 / R_k^2, R_k = delta_k n
     const double *delta, *acoef;      // plan time only (device copies)
     double *c64;                      // c_k = a_k delta_k^{-(d+2)}
     float *c32;
@@ -66,13 +69,27 @@ __global__ void k_sym_coef(SymArgs a)
     const double Gi = a.sigma * a.hd * ai;
     a.G64[i] = Gi;
     a.G32[i] = (float)Gi;
+    if (a.ir2) {
+        const double R = a.delta[i] * a.n;
+        a.ir2[i] = 1.0 / (R * R);
+    }
+}
+
+// p(|o|^2 / R^2) = sum_m p_m (|o|^2 ir2)^m (Horner)
+__device__ __forceinline__ double sym_poly(const SymArgs &a, int o2, double ir2)
+{
+    const double t = (double)o2 * ir2;
+    double w = a.p[a.K];
+    for (int m = a.K - 1; m >= 0; --m) w = w * t + a.p[m];
+    return w;
 }
 
 // Plan time, per node i: T_i by the definition -- every cell k of the box of radius B around i
 // whose own leaf set reaches i (the half-unit gap from node k to cell i, per axis 2|o| - 1, 0
 // for o = 0, squared and summed, at most thr4_k; cells outside Omega take the node's own
-// horizon and coefficient, so there the test is the node's own) -- and the Jacobi diagonal
-//   -L_ii = [fastF_i (selfS_i - h^d b_i) + G_i (T_i - c_i)] / 2.
+// horizon and coefficient, so there the test is the node's own), each with its weight
+// c_k p(|o|^2 / R_k^2) (p = 1 for K = 0) -- and the Jacobi diagonal
+//   -L_ii = [fastF_i (selfS_i - h^d p_0 b_i) + G_i (T_i - p_0 c_i)] / 2.
 __global__ void k_sym_node(SymArgs a, int B)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -94,22 +111,25 @@ __global__ void k_sym_node(SymArgs a, int B)
             const int ky = iy + oy;
             const bool iny = inz && (d < 2 || (ky >= 0 && ky < n));
             const int eyz = gy * gy + gz * gz;
+            const int oyz = oy * oy + oz * oz;
             for (int ox = -B; ox <= B; ++ox) {
                 const int gx = ox ? 2 * abs(ox) - 1 : 0;
                 const int e = gx * gx + eyz;
                 const int kx = ix + ox;
                 if (iny && kx >= 0 && kx < n) {
                     const int64_t k = kx + (int64_t)n * (ky + (int64_t)n * kz);
-                    if (e <= a.thr4[k]) T += a.c64[k];
+                    if (e <= a.thr4[k])
+                        T += a.K ? a.c64[k] * sym_poly(a, ox * ox + oyz, a.ir2[k]) : a.c64[k];
                 } else if (e <= T4i) {
-                    T += ci;
+                    T += a.K ? ci * sym_poly(a, ox * ox + oyz, a.ir2[i]) : ci;
                 }
             }
         }
     }
     const double ai = a.coef == NL_COEF_XY ? a.acoef[i] : 1.0;
     a.T[i] = T;
-    a.diag[i] = 0.5 * (a.fastF[i] * (a.selfS[i] - a.hd * ai) + a.G64[i] * (T - ci));
+    const double p0 = a.K ? a.p[0] : 1.0;
+    a.diag[i] = 0.5 * (a.fastF[i] * (a.selfS[i] - a.hd * p0 * ai) + a.G64[i] * (T - p0 * ci));
 }
 
 // scale exponent from the per-block bounds of |c u| (the arithmetic of the one-sided route)
@@ -297,6 +317,195 @@ __global__ void k_sym_copy_diag(int64_t N, const double *__restrict__ src, doubl
     if (i < N) dst[i] = src[i];
 }
 
+// ---------------------------------------------------------------------------
+// K >= 1: the transpose half with the weights p(|o|^2 / R_k^2) of the source node k.  Along a
+// leaf row of k's leaf set (node offsets o_y, o_z fixed, E = o_y^2 + o_z^2) the weight of the
+// target column x is
+//   sum_m f_m (E + (x - k_x)^2)^m,   f_m = c_k u_k p_m / R_k^{2m},
+// a polynomial of degree 2K in x.  Each f_m, scaled by 2^S', is rounded once to an integer
+// held in two limbs, H 2^B + Lo (0 <= Lo <= 2^B); the coefficients of the polynomial in x are
+// then integer combinations of the limbs (binomials, powers of E and -k_x), exact modulo 2^64,
+// and go into per-row difference arrays (+ at the run's first cell, - one past its last) of the
+// 2K + 1 powers of x and the two limbs.  After the row prefix sums, the target i evaluates
+// sum_e P_e(i) i_x^e per limb, again modulo 2^64: each limb's total is a sum of small
+// weights times bounded integers and fits 63 bits, so both come out exact and
+//   S_i = (H-total 2^B + Lo-total) 2^-S'.
+// The order of the atomics cannot change a bit; FP32 and FP64 data take the same path.
+// ---------------------------------------------------------------------------
+struct SymKArgs {
+    int n, K, limb, lgc;
+    int64_t N;
+    double p[8];
+    const int *thr4;
+    const double *c64, *ir2;
+    long long *P;                     // plane (e, limb): P + (2 e + limb) N
+    const unsigned int *mx;           // bound of max |c u| (FP32 bits)
+};
+
+// S' = S_H + B, S_H = 62 - lgc - e1 with max |c u| < 2^e1 and 2^lgc >= sources per target x
+// the weight bound
+__device__ __forceinline__ int symk_shift(const SymKArgs &a)
+{
+    const float m = __uint_as_float(*a.mx);
+    int e1 = 0;
+    if (m > 0.f) frexpf(m, &e1);
+    return 62 - a.lgc - e1 + a.limb;
+}
+
+__device__ __forceinline__ unsigned long long symk_binom(int m, int j)
+{
+    unsigned long long b = 1ull;
+    for (int z = 0; z < j; ++z) b = b * (unsigned long long)(m - z) / (unsigned long long)(z + 1);
+    return b;
+}
+
+template <int K>
+__device__ __forceinline__ void symk_row(const SymKArgs &a, int64_t rowoff, int X, int r,
+                                         int kx, int E, const unsigned long long (&FH)[K + 1],
+                                         const unsigned long long (&FL)[K + 1])
+{
+    typedef unsigned long long u64;
+    const int n = a.n;
+    const int ka = max(0, -((r - X) >> 1) - 1);
+    const int kb = min(n - 1, (X + r) >> 1);
+    if (ka > kb) return;
+    u64 nk[2 * K + 1], Ep[K + 1];
+    nk[0] = 1ull;
+    for (int q = 1; q <= 2 * K; ++q) nk[q] = nk[q - 1] * (u64)(-(long long)kx);
+    Ep[0] = 1ull;
+    for (int q = 1; q <= K; ++q) Ep[q] = Ep[q - 1] * (u64)E;
+    u64 AH[2 * K + 1], AL[2 * K + 1];
+#pragma unroll
+    for (int e = 0; e <= 2 * K; ++e) { AH[e] = 0ull; AL[e] = 0ull; }
+#pragma unroll
+    for (int m = 0; m <= K; ++m)
+#pragma unroll
+        for (int j = 0; j <= m; ++j) {
+            const u64 c1 = symk_binom(m, j) * Ep[m - j];
+#pragma unroll
+            for (int e = 0; e <= 2 * j; ++e) {
+                const u64 c = c1 * symk_binom(2 * j, e) * nk[2 * j - e];
+                AH[e] += FH[m] * c;
+                AL[e] += FL[m] * c;
+            }
+        }
+    const int64_t N = a.N;
+    unsigned long long *P = reinterpret_cast<unsigned long long *>(a.P);
+#pragma unroll
+    for (int e = 0; e <= 2 * K; ++e) {
+        atomicAdd(P + (2 * e) * N + rowoff + ka, AH[e]);
+        atomicAdd(P + (2 * e + 1) * N + rowoff + ka, AL[e]);
+        if (kb + 1 < n) {
+            atomicAdd(P + (2 * e) * N + rowoff + kb + 1, 0ull - AH[e]);
+            atomicAdd(P + (2 * e + 1) * N + rowoff + kb + 1, 0ull - AL[e]);
+        }
+    }
+}
+
+template <int DIM, int K, typename T>
+__global__ void __launch_bounds__(256) k_symk_scatter(SymKArgs a, const T *__restrict__ u)
+{
+    typedef unsigned long long u64;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= a.N) return;
+    const double v = a.c64[k] * (double)u[k];
+    if (v == 0.0) return;
+    const int sh = symk_shift(a);
+    const double ir2 = a.ir2[k];
+    u64 FH[K + 1], FL[K + 1];
+    double pw = 1.0;
+#pragma unroll
+    for (int m = 0; m <= K; ++m) {
+        const double y = ldexp(v * a.p[m] * pw, sh);
+        const double hi = floor(ldexp(y, -a.limb));
+        FH[m] = (u64)(long long)hi;
+        FL[m] = (u64)llrint(y - ldexp(hi, a.limb));
+        pw *= ir2;
+    }
+    const int n = a.n;
+    const int kx = (int)(k % n);
+    const int ky = DIM > 1 ? (int)((k / n) % n) : 0;
+    const int kz = DIM > 2 ? (int)(k / ((int64_t)n * n)) : 0;
+    const int X = 2 * kx + 1;
+    const int T4 = a.thr4[k];
+    if (DIM == 1) {
+        symk_row<K>(a, 0, X, sym_isqrt(T4), kx, 0, FH, FL);
+        return;
+    }
+    const int64_t pl = (int64_t)n * n;
+    for (int tz = 0; tz <= (DIM > 2 ? n : 0); ++tz) {
+        const int ez = tz == 0 ? 0 : sym_sq(2 * tz - 1);
+        if (ez > T4) break;
+        for (int sz = 0; sz < (DIM > 2 && tz > 0 ? 2 : 1); ++sz) {
+            const int z = DIM > 2 ? (sz ? kz - tz : kz + tz) : 0;
+            if (z < 0 || z >= (DIM > 2 ? n : 1)) continue;
+            for (int ty = 0;; ++ty) {
+                const int e = ez + (ty == 0 ? 0 : sym_sq(2 * ty - 1));
+                if (e > T4) break;
+                const int r = sym_isqrt(T4 - e);
+                const int E = ty * ty + tz * tz;
+                if (ky + ty < n) symk_row<K>(a, pl * z + (int64_t)n * (ky + ty), X, r, kx, E, FH, FL);
+                if (ty > 0 && ky - ty >= 0)
+                    symk_row<K>(a, pl * z + (int64_t)n * (ky - ty), X, r, kx, E, FH, FL);
+            }
+        }
+    }
+}
+
+// per-block bounds of |c u| (FP64 products, rounded up to FP32) and their maximum
+template <typename T>
+__global__ void __launch_bounds__(256) k_symk_absmax(int64_t N, const T *__restrict__ u,
+                                                     const double *__restrict__ c,
+                                                     float *__restrict__ part)
+{
+    __shared__ double s_w[8];
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(c[i] * (double)u[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmax(m, s_w[w]);
+        part[blockIdx.x] = (float)m * (1.f + 0x1p-20f);
+    }
+}
+
+__global__ void k_symk_reduce(const float *__restrict__ part, int nparts, unsigned int *mx)
+{
+    float m = 0.f;
+    for (int k = threadIdx.x; k < nparts; k += 32) m = fmaxf(m, part[k]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *mx = __float_as_uint(m);
+}
+
+// S_i from the prefix sums, then L u = (half1 + half2) / 2 with half2 = G_i (S_i - u_i T_i)
+template <typename T>
+__global__ void k_symk_finish(SymKArgs a, const double *__restrict__ G,
+                              const double *__restrict__ Tsum, const T *__restrict__ u,
+                              T *__restrict__ Lu)
+{
+    typedef unsigned long long u64;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const u64 x = (u64)(i % a.n);
+    const u64 *P = reinterpret_cast<const u64 *>(a.P);
+    u64 SH = 0ull, SL = 0ull, xp = 1ull;
+    for (int e = 0; e <= 2 * a.K; ++e) {
+        SH += P[(2 * e) * a.N + i] * xp;
+        SL += P[(2 * e + 1) * a.N + i] * xp;
+        xp *= x;
+    }
+    const int sh = symk_shift(a);
+    const double S = ldexp((double)(long long)SH, a.limb - sh) + ldexp((double)(long long)SL, -sh);
+    const double h2 = G[i] * (S - (double)u[i] * Tsum[i]);
+    Lu[i] = (T)(0.5 * ((double)Lu[i] + h2));
+}
+
+template <typename T>
+static nl_status symk_launch(nl_plan *p, const T *u, T *Lu, int nrhs, cudaStream_t st);
+
 SymArgs make_sym_args(nl_plan *p)
 {
     SymArgs a;
@@ -308,7 +517,58 @@ SymArgs make_sym_args(nl_plan *p)
     a.c64 = p->sym_c64; a.c32 = p->sym_c32; a.T = p->sym_T;
     a.G64 = p->sym_G64; a.G32 = p->sym_G32; a.diag = p->sym_diag;
     a.fastF = p->fastF; a.selfS = p->selfS;
+    a.K = p->K;
+    for (int m = 0; m < 8; ++m) a.p[m] = p->poly[m];
+    a.ir2 = p->sym_ir2;
     return a;
+}
+
+SymKArgs make_symk_args(nl_plan *p)
+{
+    SymKArgs a;
+    a.n = p->n; a.K = p->K; a.limb = p->sym_limb; a.lgc = p->sym_lgc; a.N = p->N;
+    for (int m = 0; m < 8; ++m) a.p[m] = p->poly[m];
+    a.thr4 = p->thr4; a.c64 = p->sym_c64; a.ir2 = p->sym_ir2; a.P = p->sym_P;
+    a.mx = (const unsigned int *)p->sym_aux;
+    return a;
+}
+
+template <typename T>
+static nl_status symk_launch(nl_plan *p, const T *u, T *Lu, int nrhs, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const int d = p->d, n = p->n, K = p->K;
+    SymKArgs a = make_symk_args(p);
+    const unsigned gb = (unsigned)((N + 255) / 256);
+    const int64_t rows = N / n;
+    const unsigned gr = (unsigned)((rows * 32 + 255) / 256);
+    unsigned int *mx = (unsigned int *)p->sym_aux;
+    float *part = (float *)(p->sym_aux + 16);
+    int64_t per = (N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
+    if (per < 2048) per = 2048;
+    const int nparts = (int)((N + per - 1) / per);
+    const int planes = 2 * (2 * K + 1);
+    for (int r = 0; r < nrhs; ++r) {
+        const T *ur = u + r * N;
+        T *lr = Lu + r * N;
+        NL_CUDA_TRY(cudaMemsetAsync(p->sym_P, 0, (size_t)planes * N * sizeof(long long), st));
+        k_symk_absmax<T><<<nparts, 256, 0, st>>>(N, ur, p->sym_c64, part);
+        k_symk_reduce<<<1, 32, 0, st>>>(part, nparts, mx);
+#define NL_SYMK(DD, KK) k_symk_scatter<DD, KK, T><<<gb, 256, 0, st>>>(a, ur)
+        if (d == 1) {
+            if (K == 1) NL_SYMK(1, 1); else if (K == 2) NL_SYMK(1, 2); else NL_SYMK(1, 3);
+        } else if (d == 2) {
+            if (K == 1) NL_SYMK(2, 1); else if (K == 2) NL_SYMK(2, 2); else NL_SYMK(2, 3);
+        } else {
+            if (K == 1) NL_SYMK(3, 1); else if (K == 2) NL_SYMK(3, 2); else NL_SYMK(3, 3);
+        }
+#undef NL_SYMK
+        for (int q = 0; q < planes; ++q)
+            k_sym_rowscan<long long><<<gr, 256, 0, st>>>(p->sym_P + (int64_t)q * N, n, rows);
+        k_symk_finish<T><<<gb, 256, 0, st>>>(a, p->sym_G64, p->sym_T, ur, lr);
+        NL_CUDA_TRY(cudaGetLastError());
+    }
+    return NL_OK;
 }
 
 }  // namespace
@@ -334,6 +594,27 @@ nl_status nl_fast_sym_plan_init(nl_plan *p, const double *delta_dev, const doubl
     if ((s = alloc((void **)&p->sym_diag, N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->sym_D, N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->sym_aux, 16 + NL_FAST_PARTS * sizeof(float))) != NL_OK) return s;
+    if (p->K >= 1) {
+        // sources reaching a target: at most (2 Rmax + 3)^d; |o|^2 / R_k^2 < (1 + sqrt(d) /
+        // (2 R_min))^2 on a leaf set, so |p| <= sum_m |p_m| rho^m; |o|^2 <= d (Rmax + 1)^2
+        const int d = p->d;
+        const double count = std::pow(2.0 * p->Rmax + 3.0, (double)d);
+        const double rr = 1.0 + std::sqrt((double)d) / (2.0 * std::max(p->rho_min, 1e-3));
+        double pb = 0.0, rp = 1.0;
+        for (int m = 0; m <= p->K; ++m) { pb += std::fabs(p->poly[m]) * rp; rp *= rr * rr; }
+        const double omax2 = d * (p->Rmax + 1.0) * (p->Rmax + 1.0);
+        const double lbound = count * (p->K + 1) * std::pow(omax2, (double)p->K);
+        p->sym_lgc = (int)std::ceil(std::log2(count * pb));
+        p->sym_limb = 62 - (int)std::ceil(std::log2(lbound));
+        if (p->sym_limb < 8 || p->sym_lgc > 40) {
+            nl_set_error("nl_plan_create: the symmetric NL_POLY variant with K >= 1 needs a "
+                         "smaller horizon (integer sums beyond 64 bits)");
+            return NL_EUNSUPPORTED;
+        }
+        if ((s = alloc((void **)&p->sym_ir2, N * sizeof(double))) != NL_OK) return s;
+        if ((s = alloc((void **)&p->sym_P, (size_t)2 * (2 * p->K + 1) * N * sizeof(long long))) != NL_OK)
+            return s;
+    }
     SymArgs a = make_sym_args(p);
     a.delta = delta_dev;
     a.acoef = a_dev;
@@ -358,6 +639,10 @@ nl_status nl_fast_sym_launch(nl_plan *p, const void *u, void *Lu, int nrhs, int 
 {
     nl_status s = nl_fast_launch(p, u, Lu, nrhs, dtype, st);
     if (s != NL_OK) return s;
+    if (p->K >= 1) {
+        if (dtype == NL_F32) return symk_launch<float>(p, (const float *)u, (float *)Lu, nrhs, st);
+        return symk_launch<double>(p, (const double *)u, (double *)Lu, nrhs, st);
+    }
     const int64_t N = p->N;
     const int d = p->d, n = p->n;
     SymArgs a = make_sym_args(p);

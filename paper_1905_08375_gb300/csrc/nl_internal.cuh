@@ -83,6 +83,7 @@ struct nl_plan {
     double poly[8];
     // horizon summary
     int Rmax;               // max ceil(delta_i n)
+    double rho_min;         // min delta_i n
     int const_horizon;      // 1 if every node has the same horizon
     int thr_max;            // max over nodes of the largest integer |o|^2 inside the ball
     int num_off;            // table length (offsets with 0 < |o|^2 <= thr_sym_max)
@@ -159,6 +160,10 @@ struct nl_plan {
     double *sym_diag;                  // Jacobi diagonal of -L
     double *sym_D;                     // difference arrays / row prefix sums (N x 8 bytes)
     unsigned char *sym_aux;            // scale word and per-block bounds of |c u|
+    double *sym_ir2;                   // K >= 1: 1 / R_k^2 (R_k = delta_k n)
+    long long *sym_P;                  // K >= 1: [2K+1][2][N] coefficient difference arrays
+    int sym_limb;                      // K >= 1: bits of the low limb
+    int sym_lgc;                       // K >= 1: ceil(log2(sources per target x weight bound))
     int prof_on, prof_count;        // per-phase timing of the fast apply
     cudaEvent_t prof_ev[64][3];
     int pair_rm;                    // NL_F64_PAIRS (2-D symmetric NL_POWER): tile halo, 0 = off

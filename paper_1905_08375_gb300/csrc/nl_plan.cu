@@ -392,14 +392,14 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     }
     if (hz->symmetric && k->family == NL_POLY) {
         // the symmetrised polynomial operator: the fast path with p = 1 (nl_apply_fast, CG)
-        if (k->K != 0 || k->coef == NL_COEF_X || k->self_term != NL_SELF_DISCRETE) {
-            nl_set_error("nl_plan_create: the symmetric NL_POLY variant needs K = 0, "
+        if (k->coef == NL_COEF_X || k->self_term != NL_SELF_DISCRETE) {
+            nl_set_error("nl_plan_create: the symmetric NL_POLY variant needs "
                          "NL_COEF_NONE/XY and NL_SELF_DISCRETE");
             return NL_EUNSUPPORTED;
         }
     } else if (hz->symmetric && (k->family != NL_POWER || k->coef == NL_COEF_X)) {
-        nl_set_error("nl_plan_create: the symmetric variant needs NL_POWER with NL_COEF_NONE/XY "
-                     "(or NL_POLY with K = 0)");
+        nl_set_error("nl_plan_create: the symmetric variant needs NL_POWER or NL_POLY with "
+                     "NL_COEF_NONE/XY");
         return NL_EUNSUPPORTED;
     }
     int64_t N = 1;
@@ -424,6 +424,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     for (int64_t i = 0; i < N; ++i) delta[i] = hz->delta_field ? hz->delta_field[i] : hz->delta;
     int Rmax = 0;
     int64_t thr_max = 0;
+    double rho_min = 1e300;
     for (int64_t i = 0; i < N; ++i) {
         double di = delta[i];
         if (!(di > 0.0) || !std::isfinite(di)) {
@@ -438,6 +439,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
             return NL_EUNSUPPORTED;
         }
         Rmax = std::max(Rmax, (int)std::ceil(rho));
+        rho_min = std::min(rho_min, rho);
         thr_max = std::max(thr_max, (int64_t)(std::ceil(R2) - 1.0));
     }
     if (k->a) {
@@ -480,6 +482,7 @@ extern "C" nl_status nl_plan_create(nl_plan **out, const nl_grid *grid, const nl
     if (k->family == NL_POLY || k->family == NL_KAPPA) hermite_poly(p->K, k->alpha, p->poly);
     if (k->family == NL_PD_BOND) hermite_poly(p->K, 3.0, p->poly);   // micromodulus ~ s^-3
     p->Rmax = Rmax;
+    p->rho_min = rho_min;
     p->thr_max = (int)thr_max;
     p->const_horizon = 1;
     for (int64_t i = 1; i < N; ++i)
@@ -758,7 +761,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32, p->leaf_multi,
                      p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux, p->selfQ,
                      p->fastFh32, p->sym_c64, p->sym_c32, p->sym_T, p->sym_G64, p->sym_G32,
-                     p->sym_diag, p->sym_D, p->sym_aux, p->slot_base, p->slot_rec, p->slot_woff, p->slot_count,
+                     p->sym_diag, p->sym_D, p->sym_aux, p->sym_ir2, p->sym_P, p->slot_base, p->slot_rec, p->slot_woff, p->slot_count,
                      p->fpd_ir2, p->pair_tab, p->pair_bc, p->x2r_order, p->x2r_queue,
                      p->x2r_c32, p->x2r_tp1, p->x2r_jmin };
     for (void *q : ptrs) if (q) cudaFree(q);

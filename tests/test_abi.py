@@ -53,7 +53,8 @@ def test_library_exports_every_declared_symbol(nl):
     (dict(dim=2, n=8, delta=0.1, coef=2, a=-np.ones(64)), "NL_EINVAL"),     # a <= 0
     (dict(dim=3, n=8, delta=0.1, family=2, K=1), "NL_EUNSUPPORTED"),        # 3-D PD: K = 0
     (dict(dim=3, n=12, delta=0.1, family=2), "NL_EUNSUPPORTED"),            # 3-D PD: n = 2^L
-    (dict(dim=2, n=8, delta=0.1, family=1, K=1, symmetric=True), "NL_EUNSUPPORTED"),
+    (dict(dim=2, n=8, delta=0.1, family=1, K=1, symmetric=True, self_term=1),
+     "NL_EUNSUPPORTED"),                                                   # paper self term
     (dict(dim=2, n=8, delta=0.1, family=1, coef=1, a=np.ones(64), symmetric=True),
      "NL_EUNSUPPORTED"),
     (dict(dim=2, n=8, delta=0.1, alpha=4.5), "NL_EINVAL"),
