@@ -246,6 +246,9 @@ class C2(Workload):
         # the symmetrised (divergence-type) fast operator on the same fields (f4)
         self.fast_sym = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=0,
                                           coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+        # and with the polynomial p^4 (K = 2): two-limb integer coefficients of the target column
+        self.fast_sym_k2 = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5,
+                                             K=2, coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
         self.u = torch.tensor(f["u"][0], dtype=torch.float32, device=self.dev)
         self.out_d = torch.empty_like(self.u)
         self.out_f = torch.empty_like(self.u)
@@ -328,6 +331,9 @@ class C2(Workload):
         t_sym = self.time_fn(lambda: nl.nl_apply_fast(self.fast_sym, self.u, o_sym),
                              min(reps, 20), flush)
         per["fast_sym_fp32_ms"] = round(t_sym, 4)
+        t_sym2 = self.time_fn(lambda: nl.nl_apply_fast(self.fast_sym_k2, self.u, o_sym),
+                              min(reps, 10), flush)
+        per["fast_sym_K2_fp32_ms"] = round(t_sym2, 4)
         per["fast_sym_note"] = ("symmetrised leaf-set operator (K = 0): one-sided fast apply "
                                 "(leaf rows) + transpose scatter into per-row difference "
                                 "arrays with 64-bit integer atomics + row prefix sums")

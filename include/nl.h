@@ -91,8 +91,9 @@ typedef enum { NL_COEF_NONE = 0, NL_COEF_X = 1, NL_COEF_XY = 2, NL_COEF_MEAN = 3
  *       (Example 1 of Sec. 4); not defined for NL_COEF_XY. */
 typedef enum { NL_SELF_DISCRETE = 0, NL_SELF_PAPER = 1 } nl_self;
 
-/* How nl_apply_fast forms the Step 2/3 sums for K = 0 with FP32 data (FP64 data and K > 0
- * always use FP64 panel moments summed panel by panel):
+/* How nl_apply_fast forms the Step 2/3 sums for K = 0 with FP32 data (FP64 data always use
+ * FP64 panel moments summed panel by panel; so does K > 0 except as noted under
+ * NL_FAST_LEAFROWS):
  *   NL_FAST_AUTO (0) = NL_FAST_LEAFROWS
  *   NL_FAST_PANELS (1): exact 64-bit fixed-point panel sums (one rounding of each leaf value
  *       to a multiple of 2^-S chosen from max |a u|), added panel by panel (Sec. 3, Steps 1-3);
@@ -101,7 +102,11 @@ typedef enum { NL_SELF_DISCRETE = 0, NL_SELF_PAPER = 1 } nl_self;
  *   NL_FAST_FP64_PANELS (3): FP64 panel sums added panel by panel, as for FP64 data;
  *   NL_FAST_LEAFROWS (4): the panels of Algorithm 1 tile exactly the leaf cells that meet the
  *       ball, so their sum is taken row by row from the leaf-row prefix sums, one difference
- *       per leaf row -- the same integers again, bitwise the same result. */
+ *       per leaf row -- the same integers again, bitwise the same result.  For K >= 1 with
+ *       FP32 data and d <= 2 (while (2 Rmax + 3)^d (Rmax + 1)^{2K} <= 2^40) the leaf rows
+ *       carry the prefix sums of k^e q (k the column, e <= 2K, modulo 2^64): each row's run
+ *       sums of o_x^{2j} q are exact integers, combined once per node with the polynomial's
+ *       coefficients in FP64 -- the same leaf-set sum as the moment pyramid's, not bitwise. */
 typedef enum { NL_FAST_AUTO = 0, NL_FAST_PANELS = 1, NL_FAST_ROWPREFIX = 2,
                NL_FAST_FP64_PANELS = 3, NL_FAST_LEAFROWS = 4 } nl_fast_variant;
 

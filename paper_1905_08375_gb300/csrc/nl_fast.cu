@@ -1994,12 +1994,22 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     if ((s = alloc((void **)&p->fastF, p->N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->selfS, p->N * sizeof(double))) != NL_OK) return s;
     if ((s = alloc((void **)&p->ir4, p->N * sizeof(double))) != NL_OK) return s;
-    if (K == 0) {
+    // K >= 1, d <= 2: the integer leaf-row route (prefix arrays of k^e q, e <= 2K); 2^bits
+    // bounds a node's exact sums: (2 Rmax + 3)^d cells times (Rmax + 1)^{2K}
+    const double kint_bound = std::pow(2.0 * p->Rmax + 3.0, (double)d) *
+                              std::pow(p->Rmax + 1.0, 2.0 * K);
+    const bool kint = K >= 1 && d <= 2 && kint_bound <= 0x1p40;
+    if (K == 0 || kint) {
         const size_t aux = 16 + NL_FAST_PARTS * sizeof(float);
         if ((s = alloc((void **)&p->fast_mx, aux)) != NL_OK) return s;
         NL_CUDA_TRY(cudaMemsetAsync(p->fast_mx, 0, aux, st));     // the ticket starts at 0
         if ((s = alloc((void **)&p->selfQ, p->N * sizeof(double))) != NL_OK) return s;
         if ((s = alloc((void **)&p->fastFh32, p->N * sizeof(float))) != NL_OK) return s;
+    }
+    if (kint) {
+        if ((s = alloc((void **)&p->kint_P, (size_t)(2 * K + 1) * p->N * sizeof(long long))) != NL_OK)
+            return s;
+        p->kint_bits = (int)std::ceil(std::log2(kint_bound));
     }
     double *d_pc = nullptr;
     if ((s = alloc((void **)&d_pc, 8 * sizeof(double))) != NL_OK) return s;
@@ -2014,7 +2024,7 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
     k_fast_node<<<gb, 256, 0, st>>>(d, p->n, K, p->coef, p->self_mode, p->N, p->sigma, sphere,
                                     delta_dev, a_dev, p->thr4, d_pc, p->fastF, p->selfS, p->ir4);
     NL_CUDA_TRY(cudaGetLastError());
-    if (K == 0) {
+    if (K == 0 || kint) {
         k_fixed_consts<<<gb, 256, 0, st>>>(p->N, std::pow(p->h, (double)d), p->fastF, p->selfS,
                                            p->selfQ, p->fastFh32);
         // the plan-time bound max |b| of the fixed-point scale (word 2 of the aux header)
@@ -2025,6 +2035,8 @@ nl_status nl_fast_plan_init(nl_plan *p, const double *delta_dev, const double *a
         NL_CUDA_TRY(cudaMemcpyAsync(&bits, bw, sizeof(bits), cudaMemcpyDeviceToHost, st));
         NL_CUDA_TRY(cudaStreamSynchronize(st));
         memcpy(&p->fast_bmax, &bits, sizeof(float));
+    }
+    if (K == 0) {
         // 3-D, constant horizon: the common threshold and the staged gather's tile geometry
         p->r3_tm = 0;
         if (d == 3 && p->const_horizon) {
@@ -2144,6 +2156,203 @@ static cudaError_t step2_panels(nl_plan *p, const float *u, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Leaf-row form of the fast apply for K >= 1 (integer route, FP32 data, d <= 2; a deviation of
+// the f1 kind from the FP64 moment pyramid, with the same leaf-set sum).  Along a leaf row of
+// node i (row offset o_y) the weight is p(|o|^2 / R_i^2) = sum_m beta_m (o_y^2 + o_x^2)^m,
+// beta_m = p_m / R_i^{2m}, so the row needs the run sums C_{2j} = sum_run o_x^{2j} q,
+// o_x = k - i_x, j <= K: from prefix sums of k^e q (e <= 2K, modulo 2^64) by differences,
+// centred by the binomial expansion.  They are accumulated, times o_y^{2(m-j)}, into the
+// exact sums Z[m][j] (modulo 2^64; the true values are bounded by 2^bits max|q| < 2^61), and
+// once per node G = sum_m beta_m sum_j binom(m, j) Z[m][j] 2^-S in FP64.  q = round(u b 2^S)
+// as in the K = 0 route.
+// ---------------------------------------------------------------------------
+struct KintArgs {
+    int n, bits, nparts;
+    int64_t N;
+    const float *u, *b, *part;
+    unsigned int *mx;                 // max |u b| bound (FP32 bits), written by the scan
+    long long *P;                     // [2K+1][N]
+    const int *thr4;
+    const double *fastF, *selfS, *ir4;
+    double hd;
+    double p[8];
+};
+
+__device__ __forceinline__ int kint_shift(const KintArgs &a, float m)
+{
+    if (!(m > 0.f)) return 61 - a.bits;
+    int e1;
+    frexpf(m, &e1);
+    return 61 - a.bits - e1;
+}
+
+// one warp per leaf row: the 2K + 1 prefix arrays of k^e q (modulo 2^64)
+template <int K>
+__global__ void __launch_bounds__(128) k_kint_scan(KintArgs a)
+{
+    __shared__ float s_m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        float m = 0.f;
+        for (int k = lane; k < a.nparts; k += 32) m = fmaxf(m, a.part[k]);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_m = m;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.mx = __float_as_uint(s_m);
+    const int sh = kint_shift(a, s_m);
+    const int n = a.n;
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
+    if (row * n >= a.N) return;
+    const int64_t base = row * n;
+    typedef unsigned long long u64;
+    u64 carry[2 * K + 1];
+#pragma unroll
+    for (int e = 0; e <= 2 * K; ++e) carry[e] = 0ull;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        u64 v[2 * K + 1];
+        if (k < n) {
+            const u64 q = (u64)__float2ll_rn(ldexpf(a.u[base + k] * a.b[base + k], sh));
+            v[0] = q;
+#pragma unroll
+            for (int e = 1; e <= 2 * K; ++e) v[e] = v[e - 1] * (u64)k;
+        } else {
+#pragma unroll
+            for (int e = 0; e <= 2 * K; ++e) v[e] = 0ull;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int e = 0; e <= 2 * K; ++e) {
+                const u64 w = __shfl_up_sync(0xffffffffu, v[e], o);
+                if (lane >= o) v[e] += w;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e <= 2 * K; ++e) {
+            v[e] += carry[e];
+            if (k < n) a.P[(int64_t)e * a.N + base + k] = (long long)v[e];
+            carry[e] = __shfl_sync(0xffffffffu, v[e], 31);
+        }
+    }
+}
+
+template <int D, int K>
+__global__ void __launch_bounds__(256) k_kint_gather(KintArgs a, float *__restrict__ Lu)
+{
+    typedef unsigned long long u64;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.N) return;
+    const int n = a.n;
+    const int ix = (int)(i % n);
+    const int iy = D > 1 ? (int)(i / n) : 0;
+    const int X = 2 * ix + 1;
+    const int T4 = a.thr4[i];
+    const int64_t N = a.N;
+    u64 nk[2 * K + 1];                               // (-i_x)^e
+    nk[0] = 1ull;
+#pragma unroll
+    for (int e = 1; e <= 2 * K; ++e) nk[e] = nk[e - 1] * (u64)(-(long long)ix);
+    u64 Z[K + 1][K + 1];
+#pragma unroll
+    for (int m = 0; m <= K; ++m)
+#pragma unroll
+        for (int j = 0; j <= K; ++j) Z[m][j] = 0ull;
+    for (int t = 0;; ++t) {
+        const int e0 = t == 0 ? 0 : (2 * t - 1) * (2 * t - 1);
+        if (e0 > T4 || (D == 1 && t > 0)) break;
+        const int r = isqrt_fast(T4 - e0);
+        const int ka = max(0, -((r - X) >> 1) - 1);
+        const int kb = min(n - 1, (X + r) >> 1);
+        for (int s = 0; s < (t > 0 ? 2 : 1); ++s) {
+            const int dy = s ? -t : t;
+            const int ky = iy + dy;
+            if (ky < 0 || ky >= (D > 1 ? n : 1)) continue;
+            const int64_t row = (int64_t)ky * n;
+            u64 Dd[2 * K + 1];
+#pragma unroll
+            for (int e = 0; e <= 2 * K; ++e) {
+                const long long *Pe = a.P + (int64_t)e * N + row;
+                Dd[e] = (u64)__ldg(Pe + kb) - (ka > 0 ? (u64)__ldg(Pe + ka - 1) : 0ull);
+            }
+            u64 C[K + 1];                            // sum_run (k - i_x)^{2j} q
+#pragma unroll
+            for (int j = 0; j <= K; ++j) {
+                u64 acc = 0ull, bin = 1ull;          // binom(2j, e), e = 0 ..
+#pragma unroll
+                for (int e = 0; e <= 2 * j; ++e) {
+                    acc += bin * nk[2 * j - e] * Dd[e];
+                    bin = bin * (u64)(2 * j - e) / (u64)(e + 1);
+                }
+                C[j] = acc;
+            }
+            const u64 dy2 = (u64)(long long)(dy * dy);
+            u64 dyp[K + 1];
+            dyp[0] = 1ull;
+#pragma unroll
+            for (int q = 1; q <= K; ++q) dyp[q] = dyp[q - 1] * dy2;
+#pragma unroll
+            for (int m = 0; m <= K; ++m)
+#pragma unroll
+                for (int j = 0; j <= m; ++j) Z[m][j] += dyp[m - j] * C[j];
+        }
+    }
+    const int sh = kint_shift(a, __uint_as_float(*a.mx));
+    const double ir2 = 4.0 * a.ir4[i];               // 1 / R_i^2
+    double G = 0.0, beta = 1.0;
+#pragma unroll
+    for (int m = 0; m <= K; ++m) {
+        double zm = 0.0, bin = 1.0;
+#pragma unroll
+        for (int j = 0; j <= m; ++j) {
+            zm += bin * (double)(long long)Z[m][j];
+            bin = bin * (m - j) / (j + 1);
+        }
+        G += a.p[m] * beta * zm;
+        beta *= ir2;
+    }
+    G = ldexp(G, -sh);
+    Lu[i] = (float)(a.fastF[i] * (a.hd * G - (double)a.u[i] * a.selfS[i]));
+}
+
+static nl_status fast_one_kint(nl_plan *p, const float *u, float *Lu, cudaStream_t st)
+{
+    prof_mark(p, 0, st);
+    const int64_t N = p->N;
+    unsigned char *aux = (unsigned char *)p->fast_mx;
+    float *part = (float *)(aux + 16);
+    int64_t per = (N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
+    if (per < 2048) per = 2048;
+    const int nparts = (int)((N + per - 1) / per);
+    KintArgs a;
+    a.n = p->n; a.bits = p->kint_bits; a.nparts = nparts; a.N = N;
+    a.u = u; a.b = p->b32; a.part = part; a.mx = (unsigned int *)aux; a.P = p->kint_P;
+    a.thr4 = p->thr4; a.fastF = p->fastF; a.selfS = p->selfS; a.ir4 = p->ir4;
+    a.hd = std::pow(p->h, (double)p->d);
+    for (int m = 0; m < 8; ++m) a.p[m] = p->poly[m];
+    k_absmax_parts<<<nparts, 256, 0, st>>>(N, u, p->fast_bmax, part, nullptr, 0);
+    const int64_t rows = N / p->n;
+    const unsigned gs = (unsigned)((rows + 3) / 4), gb = (unsigned)((N + 255) / 256);
+    switch (p->K) {
+        case 1: k_kint_scan<1><<<gs, 128, 0, st>>>(a); break;
+        case 2: k_kint_scan<2><<<gs, 128, 0, st>>>(a); break;
+        default: k_kint_scan<3><<<gs, 128, 0, st>>>(a); break;
+    }
+    prof_mark(p, 1, st);
+#define NL_KINT(D, KK) k_kint_gather<D, KK><<<gb, 256, 0, st>>>(a, Lu)
+    if (p->d == 1) {
+        if (p->K == 1) NL_KINT(1, 1); else if (p->K == 2) NL_KINT(1, 2); else NL_KINT(1, 3);
+    } else {
+        if (p->K == 1) NL_KINT(2, 1); else if (p->K == 2) NL_KINT(2, 2); else NL_KINT(2, 3);
+    }
+#undef NL_KINT
+    prof_mark(p, 2, st);
+    NL_CUDA_TRY(cudaGetLastError());
+    return NL_OK;
+}
+
 // the staged 3-D gather for a constant horizon (k_fast_gather_rows3c) where the plan set it up
 static size_t rows3_smem(int tm)
 {
@@ -2247,6 +2456,8 @@ static nl_status fast_one(nl_plan *p, const T *u, T *Lu, cudaStream_t st)
 {
     if (sizeof(T) == 4 && p->K == 0 && p->fast_mx && p->fast_variant != NL_FAST_FP64_PANELS)
         return fast_one_i64(p, (const float *)u, (float *)Lu, st);
+    if (sizeof(T) == 4 && p->K >= 1 && p->kint_P && p->fast_variant == NL_FAST_LEAFROWS)
+        return fast_one_kint(p, (const float *)u, (float *)Lu, st);
     prof_mark(p, 0, st);
     const int d = p->d, L = p->L, M = p->M;
     double *leaf = p->pyr + p->lvl_off[L];

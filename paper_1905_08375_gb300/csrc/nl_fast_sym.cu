@@ -330,10 +330,11 @@ __global__ void k_sym_copy_diag(int64_t N, const double *__restrict__ src, doubl
 // sum_e P_e(i) i_x^e per limb, again modulo 2^64: each limb's total is a sum of small
 // weights times bounded integers and fits 63 bits, so both come out exact and
 //   S_i = (H-total 2^B + Lo-total) 2^-S'.
-// The order of the atomics cannot change a bit; FP32 and FP64 data take the same path.
+// The order of the atomics cannot change a bit.  FP32 data keep the H limb alone (B = 0: one
+// rounding of ~2^-28 of the largest term, far below FP32), FP64 data both.
 // ---------------------------------------------------------------------------
 struct SymKArgs {
-    int n, K, limb, lgc;
+    int n, K, limb, lgc, two;         // two: H and Lo limbs (FP64 data); else H alone, B = 0
     int64_t N;
     double p[8];
     const int *thr4;
@@ -349,7 +350,7 @@ __device__ __forceinline__ int symk_shift(const SymKArgs &a)
     const float m = __uint_as_float(*a.mx);
     int e1 = 0;
     if (m > 0.f) frexpf(m, &e1);
-    return 62 - a.lgc - e1 + a.limb;
+    return 62 - a.lgc - e1 + (a.two ? a.limb : 0);
 }
 
 __device__ __forceinline__ unsigned long long symk_binom(int m, int j)
@@ -359,7 +360,7 @@ __device__ __forceinline__ unsigned long long symk_binom(int m, int j)
     return b;
 }
 
-template <int K>
+template <int K, bool TWO>
 __device__ __forceinline__ void symk_row(const SymKArgs &a, int64_t rowoff, int X, int r,
                                          int kx, int E, const unsigned long long (&FH)[K + 1],
                                          const unsigned long long (&FL)[K + 1])
@@ -386,23 +387,24 @@ __device__ __forceinline__ void symk_row(const SymKArgs &a, int64_t rowoff, int 
             for (int e = 0; e <= 2 * j; ++e) {
                 const u64 c = c1 * symk_binom(2 * j, e) * nk[2 * j - e];
                 AH[e] += FH[m] * c;
-                AL[e] += FL[m] * c;
+                if (TWO) AL[e] += FL[m] * c;
             }
         }
     const int64_t N = a.N;
+    constexpr int LS = TWO ? 2 : 1;             // planes per power of x
     unsigned long long *P = reinterpret_cast<unsigned long long *>(a.P);
 #pragma unroll
     for (int e = 0; e <= 2 * K; ++e) {
-        atomicAdd(P + (2 * e) * N + rowoff + ka, AH[e]);
-        atomicAdd(P + (2 * e + 1) * N + rowoff + ka, AL[e]);
+        atomicAdd(P + (LS * e) * N + rowoff + ka, AH[e]);
+        if (TWO) atomicAdd(P + (2 * e + 1) * N + rowoff + ka, AL[e]);
         if (kb + 1 < n) {
-            atomicAdd(P + (2 * e) * N + rowoff + kb + 1, 0ull - AH[e]);
-            atomicAdd(P + (2 * e + 1) * N + rowoff + kb + 1, 0ull - AL[e]);
+            atomicAdd(P + (LS * e) * N + rowoff + kb + 1, 0ull - AH[e]);
+            if (TWO) atomicAdd(P + (2 * e + 1) * N + rowoff + kb + 1, 0ull - AL[e]);
         }
     }
 }
 
-template <int DIM, int K, typename T>
+template <int DIM, int K, typename T, bool TWO>
 __global__ void __launch_bounds__(256) k_symk_scatter(SymKArgs a, const T *__restrict__ u)
 {
     typedef unsigned long long u64;
@@ -417,9 +419,14 @@ __global__ void __launch_bounds__(256) k_symk_scatter(SymKArgs a, const T *__res
 #pragma unroll
     for (int m = 0; m <= K; ++m) {
         const double y = ldexp(v * a.p[m] * pw, sh);
-        const double hi = floor(ldexp(y, -a.limb));
-        FH[m] = (u64)(long long)hi;
-        FL[m] = (u64)llrint(y - ldexp(hi, a.limb));
+        if (TWO) {
+            const double hi = floor(ldexp(y, -a.limb));
+            FH[m] = (u64)(long long)hi;
+            FL[m] = (u64)llrint(y - ldexp(hi, a.limb));
+        } else {
+            FH[m] = (u64)llrint(y);
+            FL[m] = 0ull;
+        }
         pw *= ir2;
     }
     const int n = a.n;
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(256) k_symk_scatter(SymKArgs a, const T *__res
     const int X = 2 * kx + 1;
     const int T4 = a.thr4[k];
     if (DIM == 1) {
-        symk_row<K>(a, 0, X, sym_isqrt(T4), kx, 0, FH, FL);
+        symk_row<K, TWO>(a, 0, X, sym_isqrt(T4), kx, 0, FH, FL);
         return;
     }
     const int64_t pl = (int64_t)n * n;
@@ -444,9 +451,9 @@ __global__ void __launch_bounds__(256) k_symk_scatter(SymKArgs a, const T *__res
                 if (e > T4) break;
                 const int r = sym_isqrt(T4 - e);
                 const int E = ty * ty + tz * tz;
-                if (ky + ty < n) symk_row<K>(a, pl * z + (int64_t)n * (ky + ty), X, r, kx, E, FH, FL);
+                if (ky + ty < n) symk_row<K, TWO>(a, pl * z + (int64_t)n * (ky + ty), X, r, kx, E, FH, FL);
                 if (ty > 0 && ky - ty >= 0)
-                    symk_row<K>(a, pl * z + (int64_t)n * (ky - ty), X, r, kx, E, FH, FL);
+                    symk_row<K, TWO>(a, pl * z + (int64_t)n * (ky - ty), X, r, kx, E, FH, FL);
             }
         }
     }
@@ -491,14 +498,17 @@ __global__ void k_symk_finish(SymKArgs a, const double *__restrict__ G,
     if (i >= a.N) return;
     const u64 x = (u64)(i % a.n);
     const u64 *P = reinterpret_cast<const u64 *>(a.P);
+    const int ls = a.two ? 2 : 1;
     u64 SH = 0ull, SL = 0ull, xp = 1ull;
     for (int e = 0; e <= 2 * a.K; ++e) {
-        SH += P[(2 * e) * a.N + i] * xp;
-        SL += P[(2 * e + 1) * a.N + i] * xp;
+        SH += P[(ls * e) * a.N + i] * xp;
+        if (a.two) SL += P[(2 * e + 1) * a.N + i] * xp;
         xp *= x;
     }
     const int sh = symk_shift(a);
-    const double S = ldexp((double)(long long)SH, a.limb - sh) + ldexp((double)(long long)SL, -sh);
+    const double S = a.two ? ldexp((double)(long long)SH, a.limb - sh) +
+                                 ldexp((double)(long long)SL, -sh)
+                           : ldexp((double)(long long)SH, -sh);
     const double h2 = G[i] * (S - (double)u[i] * Tsum[i]);
     Lu[i] = (T)(0.5 * ((double)Lu[i] + h2));
 }
@@ -526,7 +536,7 @@ SymArgs make_sym_args(nl_plan *p)
 SymKArgs make_symk_args(nl_plan *p)
 {
     SymKArgs a;
-    a.n = p->n; a.K = p->K; a.limb = p->sym_limb; a.lgc = p->sym_lgc; a.N = p->N;
+    a.n = p->n; a.K = p->K; a.limb = p->sym_limb; a.lgc = p->sym_lgc; a.N = p->N; a.two = 1;
     for (int m = 0; m < 8; ++m) a.p[m] = p->poly[m];
     a.thr4 = p->thr4; a.c64 = p->sym_c64; a.ir2 = p->sym_ir2; a.P = p->sym_P;
     a.mx = (const unsigned int *)p->sym_aux;
@@ -539,6 +549,10 @@ static nl_status symk_launch(nl_plan *p, const T *u, T *Lu, int nrhs, cudaStream
     const int64_t N = p->N;
     const int d = p->d, n = p->n, K = p->K;
     SymKArgs a = make_symk_args(p);
+    // FP32 data: one limb (its rounding, ~2^-28 of the largest term, is far below FP32);
+    // FP64 data: two
+    constexpr bool TWO = sizeof(T) == 8;
+    a.two = TWO ? 1 : 0;
     const unsigned gb = (unsigned)((N + 255) / 256);
     const int64_t rows = N / n;
     const unsigned gr = (unsigned)((rows * 32 + 255) / 256);
@@ -547,14 +561,14 @@ static nl_status symk_launch(nl_plan *p, const T *u, T *Lu, int nrhs, cudaStream
     int64_t per = (N + NL_FAST_PARTS - 1) / NL_FAST_PARTS;
     if (per < 2048) per = 2048;
     const int nparts = (int)((N + per - 1) / per);
-    const int planes = 2 * (2 * K + 1);
+    const int planes = (TWO ? 2 : 1) * (2 * K + 1);
     for (int r = 0; r < nrhs; ++r) {
         const T *ur = u + r * N;
         T *lr = Lu + r * N;
         NL_CUDA_TRY(cudaMemsetAsync(p->sym_P, 0, (size_t)planes * N * sizeof(long long), st));
         k_symk_absmax<T><<<nparts, 256, 0, st>>>(N, ur, p->sym_c64, part);
         k_symk_reduce<<<1, 32, 0, st>>>(part, nparts, mx);
-#define NL_SYMK(DD, KK) k_symk_scatter<DD, KK, T><<<gb, 256, 0, st>>>(a, ur)
+#define NL_SYMK(DD, KK) k_symk_scatter<DD, KK, T, TWO><<<gb, 256, 0, st>>>(a, ur)
         if (d == 1) {
             if (K == 1) NL_SYMK(1, 1); else if (K == 2) NL_SYMK(1, 2); else NL_SYMK(1, 3);
         } else if (d == 2) {

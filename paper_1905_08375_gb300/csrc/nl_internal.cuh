@@ -160,6 +160,8 @@ struct nl_plan {
     double *sym_diag;                  // Jacobi diagonal of -L
     double *sym_D;                     // difference arrays / row prefix sums (N x 8 bytes)
     unsigned char *sym_aux;            // scale word and per-block bounds of |c u|
+    long long *kint_P;                 // one-sided K >= 1, FP32, d <= 2: [2K+1][N] leaf-row
+    int kint_bits;                     // prefix sums of k^e q; 2^bits bounds a node's sums
     double *sym_ir2;                   // K >= 1: 1 / R_k^2 (R_k = delta_k n)
     long long *sym_P;                  // K >= 1: [2K+1][2][N] coefficient difference arrays
     int sym_limb;                      // K >= 1: bits of the low limb

@@ -761,7 +761,7 @@ extern "C" nl_status nl_plan_destroy(nl_plan *p)
                      p->x2_order, p->x2_queue, p->pd_dense32, p->g3d32, p->leaf_multi,
                      p->aux_multi, p->fpd_F, p->fpd_M, p->fpd_P, p->fpd_aux, p->selfQ,
                      p->fastFh32, p->sym_c64, p->sym_c32, p->sym_T, p->sym_G64, p->sym_G32,
-                     p->sym_diag, p->sym_D, p->sym_aux, p->sym_ir2, p->sym_P, p->slot_base, p->slot_rec, p->slot_woff, p->slot_count,
+                     p->sym_diag, p->sym_D, p->sym_aux, p->sym_ir2, p->sym_P, p->kint_P, p->slot_base, p->slot_rec, p->slot_woff, p->slot_count,
                      p->fpd_ir2, p->pair_tab, p->pair_bc, p->x2r_order, p->x2r_queue,
                      p->x2r_c32, p->x2r_tp1, p->x2r_jmin };
     for (void *q : ptrs) if (q) cudaFree(q);

@@ -257,3 +257,47 @@ def test_3d_polynomial_large_ball_and_boundary():
         ref = oracle.fast_tree(u, 3, L, delta, K=2, alpha=1.0)
         assert rel_l2(run_fast(plan, u, torch.float64), ref) <= 1e-12
         plan.close()
+
+
+# ---------------------------------------------------------------------------
+# K >= 1, FP32 data, the default (leaf-row) variant: exact integer run sums of o_x^{2j} q from
+# prefix sums of k^e q; the panel variant keeps the FP64 moment pyramid
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [1, 2, 3])
+@pytest.mark.parametrize("d,n", [(1, 512), (2, 64), (2, 128)])
+@pytest.mark.parametrize("coef,self_mode", [(nl.NL_COEF_NONE, nl.NL_SELF_PAPER),
+                                            (nl.NL_COEF_XY, nl.NL_SELF_DISCRETE)])
+def test_integer_leafrows_k_matches_oracle_and_moments(K, d, n, coef, self_mode):
+    L = int(np.log2(n))
+    if d == 1:
+        f = synth.example2_1d(n=n, delta0=0.25, seed=K)
+        u = np.stack([f["u"], np.sin(np.arange(n) * 0.37)])
+        a = np.exp(0.3 * np.cos(np.arange(n) * 0.11)) if coef == nl.NL_COEF_XY else None
+    else:
+        f = synth.heterogeneous_2d(n=n, seed=5 + K, nrhs=2)
+        u = f["u"]
+        a = f["a"] if coef == nl.NL_COEF_XY else None
+    kw = dict(family=nl.NL_POLY, alpha=1.5, K=K, coef=coef, a=a, self_term=self_mode)
+    plan = nl.nl_plan_create(d, n, f["delta"], **kw)
+    mom = nl.nl_plan_create(d, n, f["delta"], fast_variant=nl.NL_FAST_PANELS, **kw)
+    ref = oracle.fast_leafset(u, d, L, f["delta"], K=K, alpha=1.5, coef=coef, a=a,
+                              self_mode=self_mode)
+    got = run_fast(plan, u, torch.float32)
+    assert rel_l2(got, ref) <= 2e-6, rel_l2(got, ref)
+    assert rel_l2(run_fast(mom, u, torch.float32), ref) <= 2e-6
+    assert np.array_equal(got, run_fast(plan, u, torch.float32))
+    plan.close()
+    mom.close()
+
+
+def test_integer_leafrows_k2_full_size_sampled():
+    n = 1024
+    f = synth.heterogeneous_2d(n=n, seed=9)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=2,
+                             coef=nl.NL_COEF_XY, a=f["a"])
+    got = run_fast(plan, f["u"][0], torch.float32)
+    idx = sample_idx(n * n, 2000, seed=4, extra=(n - 1, n * (n - 1), n * n // 2 + 7))
+    ref = oracle.fast_leafset(f["u"][0], 2, 10, f["delta"], K=2, alpha=1.5, coef=oracle.COEF_XY,
+                              a=f["a"], idx=idx)
+    assert rel_l2(got[idx], ref) <= 2e-6
+    plan.close()

@@ -172,3 +172,18 @@ def test_cg_on_the_polynomial_fast_operator(K):
     res = np.linalg.norm(f + Lx, axis=-1) / np.linalg.norm(f, axis=-1)
     assert np.all(res <= 1.01e-8), res
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_polynomial_full_size_sampled(dtype):
+    # the 1024^2 heterogeneous field (horizons of 4..16 cells): the limbs at their widest
+    n = 1024
+    f = synth.heterogeneous_2d(n=n, seed=4)
+    plan = nl.nl_plan_create(2, n, f["delta"], family=nl.NL_POLY, alpha=1.5, K=2,
+                             coef=nl.NL_COEF_XY, a=f["a"], symmetric=True)
+    got = run(plan, f["u"][0], dtype)
+    idx = sample_idx(n * n, 2000, seed=3, extra=(n - 1, n * (n - 1), n * n // 2 + 7))
+    ref = oracle.fast_sym_leafset(f["u"][0], 2, 10, f["delta"], K=2, alpha=1.5,
+                                  coef=oracle.COEF_XY, a=f["a"], idx=idx)
+    assert rel_l2(got[idx], ref) <= TOL[dtype], rel_l2(got[idx], ref)
+    plan.close()
